@@ -1,0 +1,76 @@
+"""Pins for the oracle's derivatives: the tangent-linear model against
+central finite differences of the forward oracle (exact up to rounding for
+the piecewise-linear limiters while no branch flips), and the adjoint against
+the tangent-linear model through the dot-product identity
+<J v, w> = <v, J^T w>."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+
+def _setup(n=6, seed=4, lim="superbee"):
+    wl = W.config_taylor_green(n=n, seed=seed, nsteps=4, limiter=lim)
+    return wl
+
+
+@pytest.mark.parametrize("lim", ["minmod", "superbee", "smart", "vanleer"])
+@pytest.mark.parametrize("rk", [1, 3])
+def test_tlm_matches_central_differences(lim, rk):
+    wl = _setup(lim=lim)
+    rng = np.random.default_rng(11)
+    v = rng.normal(size=wl.mesh.n_cells)
+    nsteps = 3
+    th_t, dth = oracle.step_tlm(wl.mesh, lim, rk, wl.dt, nsteps, wl.u, wl.theta0, v)
+    eps = 1e-6
+    plus = oracle.step(wl.mesh, lim, rk, wl.dt, nsteps, wl.u, wl.theta0 + eps * v)
+    minus = oracle.step(wl.mesh, lim, rk, wl.dt, nsteps, wl.u, wl.theta0 - eps * v)
+    fd = (plus - minus) / (2 * eps)
+    np.testing.assert_array_equal(th_t, oracle.step(wl.mesh, lim, rk, wl.dt, nsteps, wl.u,
+                                                    wl.theta0))
+    tol = 1e-6 if lim == "vanleer" else 1e-7
+    err = np.linalg.norm(fd - dth) / np.linalg.norm(dth)
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("lim", ["minmod", "superbee", "smart", "vanleer", "upwind", "central"])
+def test_operator_adjoint_dot_product(lim):
+    wl = _setup(lim=lim)
+    mesh = oracle.OracleMesh(wl.mesh)
+    rng = np.random.default_rng(2)
+    th = wl.theta0
+    v = rng.normal(size=mesh.C)
+    w = rng.normal(size=mesh.C)
+    # J v through the tangent-linear model of one Euler step with dt = 1:
+    # (theta + R(theta))' = v + R'(theta) v
+    _, d = oracle.step_tlm(mesh, lim, 1, 1.0, 1, wl.u, th, v)
+    Jv = d - v
+    JTw = oracle.rhs_adjoint(mesh, lim, th, wl.u, w)
+    lhs, rhs = np.dot(Jv, w), np.dot(v, JTw)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(Jv) * np.linalg.norm(w)
+
+
+@pytest.mark.parametrize("rk", [1, 3])
+@pytest.mark.parametrize("lim", ["superbee", "vanleer"])
+def test_gradient_matches_tlm_and_fd(rk, lim):
+    wl = _setup(n=6, lim=lim)
+    tgt = W.smooth_target(wl.mesh.dims, wl.mesh.h, 4)
+    nsteps = 5
+    J, g = oracle.gradient(wl.mesh, lim, rk, wl.dt, nsteps, wl.u, wl.theta0, tgt)
+    thT = oracle.step(wl.mesh, lim, rk, wl.dt, nsteps, wl.u, wl.theta0)
+    assert abs(J - 0.5 * np.sum((thT - tgt) ** 2)) <= 1e-12 * J
+    rng = np.random.default_rng(4)
+    for _ in range(4):
+        v = rng.normal(size=wl.mesh.n_cells)
+        _, dth = oracle.step_tlm(wl.mesh, lim, rk, wl.dt, nsteps, wl.u, wl.theta0, v)
+        dJ_tlm = np.dot(thT - tgt, dth)
+        dJ_adj = np.dot(g, v)
+        assert abs(dJ_adj - dJ_tlm) <= 1e-12 * np.linalg.norm(g) * np.linalg.norm(v)
+        eps = 1e-6
+        Jp = 0.5 * np.sum((oracle.step(wl.mesh, lim, rk, wl.dt, nsteps, wl.u,
+                                       wl.theta0 + eps * v) - tgt) ** 2)
+        Jm = 0.5 * np.sum((oracle.step(wl.mesh, lim, rk, wl.dt, nsteps, wl.u,
+                                       wl.theta0 - eps * v) - tgt) ** 2)
+        fd = (Jp - Jm) / (2 * eps)
+        assert abs(fd - dJ_adj) <= 1e-6 * abs(dJ_adj) + 1e-9

@@ -1,0 +1,319 @@
+"""Seeded synthetic inputs for the flux-limited convection path.
+
+This module only *describes* inputs: mesh topology/geometry as plain arrays,
+velocity fields on faces, initial scalar fields and targets.  It contains none
+of the limiter / flux / time-step arithmetic, so both the CPU oracle and the
+CUDA library can consume what it produces without sharing any of the method.
+
+Conventions shared by every generator (they describe the data, not the method):
+
+* Structured periodic box ``nx x ny x nz`` with spacings ``hx, hy, hz``; cell
+  ``c = i + nx*(j + ny*k)``, centre ``((i+1/2)hx, (j+1/2)hy, (k+1/2)hz)``.
+* Faces exist only along axes whose extent is > 1.  For each such axis (x, y, z
+  in that order) there is one block of ``|C|`` faces; face ``axis_block*|C| + c``
+  sits between ``c0 = c`` and ``c1 = c + e_axis`` (periodic wrap) and its unit
+  normal is ``+e_axis`` (points from c0 to c1).
+* ``u_f`` is the normal velocity component along the stored normal.
+
+The velocity fields are built as discrete curls of a vector potential sampled
+on mesh edges, so the face fluxes are divergence-free cell by cell up to
+round-off (each edge sample enters two faces of every cell with opposite sign).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+
+# --------------------------------------------------------------------------
+# meshes
+# --------------------------------------------------------------------------
+@dataclass
+class Mesh:
+    """Explicit face-based mesh description (host arrays, user ordering)."""
+
+    n_cells: int
+    face_cells: np.ndarray  # int32 [F, 2]  (c0, c1); normal points c0 -> c1
+    normals: np.ndarray  # float64 [F, 3] unit normals
+    areas: np.ndarray  # float64 [F]
+    volumes: np.ndarray  # float64 [C]
+    dims: tuple | None = None  # (nx, ny, nz) for structured meshes
+    h: tuple | None = None  # (hx, hy, hz)
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_faces(self) -> int:
+        return int(self.face_cells.shape[0])
+
+
+def active_axes(dims):
+    return [a for a in range(3) if dims[a] > 1]
+
+
+def structured_mesh(nx: int, ny: int = 1, nz: int = 1, hx: float = 1.0,
+                    hy: float = 1.0, hz: float = 1.0) -> Mesh:
+    """Periodic structured box written out as explicit face arrays."""
+    dims = (nx, ny, nz)
+    n = nx * ny * nz
+    c = np.arange(n, dtype=np.int64)
+    i = c % nx
+    j = (c // nx) % ny
+    k = c // (nx * ny)
+    hs = (hx, hy, hz)
+    fc, nrm, ar = [], [], []
+    for a in active_axes(dims):
+        if a == 0:
+            nb = ((i + 1) % nx) + nx * (j + ny * k)
+        elif a == 1:
+            nb = i + nx * (((j + 1) % ny) + ny * k)
+        else:
+            nb = i + nx * (j + ny * ((k + 1) % nz))
+        fc.append(np.stack([c, nb], axis=1))
+        nv = np.zeros((n, 3))
+        nv[:, a] = 1.0
+        nrm.append(nv)
+        others = [hs[b] for b in range(3) if b != a]
+        ar.append(np.full(n, others[0] * others[1]))
+    if fc:
+        face_cells = np.concatenate(fc).astype(np.int32)
+        normals = np.concatenate(nrm)
+        areas = np.concatenate(ar)
+    else:
+        face_cells = np.zeros((0, 2), np.int32)
+        normals = np.zeros((0, 3))
+        areas = np.zeros(0)
+    volumes = np.full(n, hx * hy * hz)
+    return Mesh(n, face_cells, normals, areas, volumes, dims=dims, h=hs)
+
+
+def permuted_mesh(mesh: Mesh, seed: int, flip_fraction: float = 0.5):
+    """Relabel cells and faces with seeded random permutations and flip the
+    orientation of a seeded subset of faces (c0<->c1, normal negated).
+
+    Returns ``(new_mesh, cell_perm, face_perm, flip)`` where
+    ``new_cell_id = cell_perm[old_cell_id]`` and the new face ``face_perm[f]``
+    is old face ``f``; ``flip[f]`` tells whether old face ``f`` was flipped.
+    Fields map as ``theta_new[cell_perm] = theta_old`` and
+    ``u_new[face_perm] = where(flip, -u_old, u_old)``.
+    """
+    rng = np.random.default_rng(seed)
+    C, F = mesh.n_cells, mesh.n_faces
+    cell_perm = rng.permutation(C).astype(np.int64)
+    face_perm = rng.permutation(F).astype(np.int64)
+    flip = rng.random(F) < flip_fraction
+    fc = cell_perm[mesh.face_cells.astype(np.int64)]
+    fc = np.where(flip[:, None], fc[:, ::-1], fc)
+    nrm = np.where(flip[:, None], -mesh.normals, mesh.normals)
+    new_fc = np.empty_like(fc)
+    new_fc[face_perm] = fc
+    new_n = np.empty_like(nrm)
+    new_n[face_perm] = nrm
+    new_a = np.empty_like(mesh.areas)
+    new_a[face_perm] = mesh.areas
+    new_v = np.empty_like(mesh.volumes)
+    new_v[cell_perm] = mesh.volumes
+    out = Mesh(C, new_fc.astype(np.int32), new_n, new_a, new_v)
+    return out, cell_perm, face_perm, flip
+
+
+def permute_cell_field(theta, cell_perm):
+    out = np.empty_like(theta)
+    out[cell_perm] = theta
+    return out
+
+
+def permute_face_field(u, face_perm, flip):
+    out = np.empty_like(u)
+    out[face_perm] = np.where(flip, -u, u)
+    return out
+
+
+# --------------------------------------------------------------------------
+# velocity fields (discrete curl of an edge-sampled vector potential)
+# --------------------------------------------------------------------------
+def _coords(dims, h):
+    nx, ny, nz = dims
+    hx, hy, hz = h
+    c = np.arange(nx * ny * nz, dtype=np.int64)
+    i = (c % nx).astype(np.float64)
+    j = ((c // nx) % ny).astype(np.float64)
+    k = (c // (nx * ny)).astype(np.float64)
+    return i, j, k, hx, hy, hz
+
+
+def curl_face_velocity(dims, h, potential):
+    """Face normal velocities ``u_f`` (layout of :func:`structured_mesh`) from the
+    discrete curl of a vector potential ``A = potential(axis, x, y, z)``.
+
+    A_x lives on x-edges (x_i, y_{j+1/2}, z_{k+1/2}), A_y on y-edges
+    (x_{i+1/2}, y_j, z_{k+1/2}), A_z on z-edges (x_{i+1/2}, y_{j+1/2}, z_k);
+    the flux through a face is the circulation of A around its four edges
+    (Stokes), divided by the face area.
+    """
+    i, j, k, hx, hy, hz = _coords(dims, h)
+    xc, yc, zc = (i + 0.5) * hx, (j + 0.5) * hy, (k + 0.5) * hz
+    xp, yp, zp = (i + 1.0) * hx, (j + 1.0) * hy, (k + 1.0) * hz
+    xm, ym, zm = i * hx, j * hy, k * hz
+    A = potential
+    out = []
+    axes = active_axes(dims)
+    if 0 in axes:  # x-face (x_{i+1/2}, y_j, z_k): dAz/dy - dAy/dz
+        circ = (hz * (A(2, xp, yp, zc) - A(2, xp, ym, zc))
+                - hy * (A(1, xp, yc, zp) - A(1, xp, yc, zm)))
+        out.append(circ / (hy * hz))
+    if 1 in axes:  # y-face (x_i, y_{j+1/2}, z_k): dAx/dz - dAz/dx
+        circ = (hx * (A(0, xc, yp, zp) - A(0, xc, yp, zm))
+                - hz * (A(2, xp, yp, zc) - A(2, xm, yp, zc)))
+        out.append(circ / (hx * hz))
+    if 2 in axes:  # z-face (x_i, y_j, z_{k+1/2}): dAy/dx - dAx/dy
+        circ = (hy * (A(1, xp, yc, zp) - A(1, xm, yc, zp))
+                - hx * (A(0, xc, yp, zp) - A(0, xc, ym, zp)))
+        out.append(circ / (hx * hy))
+    return np.concatenate(out) if out else np.zeros(0)
+
+
+def taylor_green_potential(axis, x, y, z):
+    """Stream function psi = sin x sin y cos z as the z-component of A; its
+    curl is the Taylor-Green field (sin x cos y cos z, -cos x sin y cos z, 0)."""
+    if axis != 2:
+        return np.zeros_like(x)
+    return np.sin(x) * np.sin(y) * np.cos(z)
+
+
+def fourier_potential(rng, n_modes=8, kmax=4):
+    """Random vector potential: ``n_modes`` Fourier modes with integer wave
+    vectors in {-kmax..kmax}^3 minus 0, N(0,1) amplitudes per component and
+    U(0, 2pi) phases."""
+    ks = []
+    while len(ks) < n_modes:
+        k = rng.integers(-kmax, kmax + 1, 3)
+        if np.any(k != 0):
+            ks.append(k.astype(np.float64))
+    amps = rng.normal(0.0, 1.0, (n_modes, 3))
+    phases = rng.uniform(0.0, TWO_PI, n_modes)
+
+    def A(axis, x, y, z):
+        s = np.zeros_like(x)
+        for m in range(n_modes):
+            s = s + amps[m, axis] * np.sin(ks[m][0] * x + ks[m][1] * y + ks[m][2] * z + phases[m])
+        return s
+
+    return A
+
+
+# --------------------------------------------------------------------------
+# scalar fields
+# --------------------------------------------------------------------------
+def sine_sum_field(dims, h, rng, n_modes=4, kmax=3, amp=0.25):
+    i, j, k, hx, hy, hz = _coords(dims, h)
+    x, y, z = (i + 0.5) * hx, (j + 0.5) * hy, (k + 0.5) * hz
+    th = np.zeros(x.shape)
+    for _ in range(n_modes):
+        while True:
+            kv = rng.integers(-kmax, kmax + 1, 3)
+            if np.any(kv != 0):
+                break
+        a = rng.uniform(0.0, amp)
+        ph = rng.uniform(0.0, TWO_PI)
+        th = th + a * np.sin(kv[0] * x + kv[1] * y + kv[2] * z + ph)
+    return th
+
+
+def cube_step(dims, h, lo=0.5 * math.pi, hi=1.5 * math.pi):
+    i, j, k, hx, hy, hz = _coords(dims, h)
+    x, y, z = (i + 0.5) * hx, (j + 0.5) * hy, (k + 0.5) * hz
+    inside = (x >= lo) & (x <= hi) & (y >= lo) & (y <= hi) & (z >= lo) & (z <= hi)
+    return inside.astype(np.float64)
+
+
+def sine_plus_cube(dims, h, seed):
+    rng = np.random.default_rng(seed)
+    return sine_sum_field(dims, h, rng) + cube_step(dims, h)
+
+
+def max_abs(u):
+    return float(np.max(np.abs(u))) if u.size else 0.0
+
+
+# --------------------------------------------------------------------------
+# the five workloads
+# --------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    theta0: np.ndarray
+    u: np.ndarray
+    dt: float
+    nsteps: int
+    rk_order: int
+    limiter: str
+    extra: dict = field(default_factory=dict)
+
+
+def config_1d(n=1000, seed=0):
+    """1D periodic advection: N uniform cells of width 1/N, u = 1, square wave
+    (1 on [0.25, 0.5]) plus a Gaussian bump at 0.75, CFL 0.5, forward Euler,
+    van Leer, 1000 steps."""
+    h = 1.0 / n
+    mesh = structured_mesh(n, 1, 1, h, 1.0, 1.0)
+    x = (np.arange(n) + 0.5) * h
+    th = ((x >= 0.25) & (x <= 0.5)).astype(np.float64) + np.exp(-((x - 0.75) / 0.05) ** 2)
+    u = np.ones(n)
+    return Workload("1d_n%d_vanleer_euler" % n, mesh, th, u, 0.5 * h, 1000, 1, "vanleer")
+
+
+def config_taylor_green(n=256, seed=1, cfl=0.4, nsteps=100, limiter="superbee"):
+    """3D periodic cube n^3 on [0, 2pi]^3, Taylor-Green velocity from the
+    discrete curl of an edge-sampled stream function, sine-sum plus cube-step
+    scalar, SSP-RK3 at CFL 0.4."""
+    h = TWO_PI / n
+    mesh = structured_mesh(n, n, n, h, h, h)
+    u = curl_face_velocity((n, n, n), (h, h, h), taylor_green_potential)
+    th = sine_plus_cube((n, n, n), (h, h, h), seed)
+    dt = cfl * h / max_abs(u)
+    return Workload("tg%d" % n, mesh, th, u, dt, nsteps, 3, limiter)
+
+
+def batched_box_dims(n_boxes=64, seed=3, lo=32, hi=128):
+    rng = np.random.default_rng(seed)
+    return [tuple(int(v) for v in d) for d in rng.integers(lo, hi + 1, (n_boxes, 3))]
+
+
+def random_box(dims, seed, cfl=0.4):
+    """One batched instance: periodic box [0, 2pi]^3 with its own solenoidal
+    velocity (curl of an 8-mode Fourier potential, normalised to max|u_f| = 1)
+    and its own sine-plus-cube scalar."""
+    rng = np.random.default_rng(seed)
+    h = tuple(TWO_PI / d for d in dims)
+    mesh = structured_mesh(*dims, *h)
+    A = fourier_potential(rng)
+    u = curl_face_velocity(dims, h, A)
+    u = u / max_abs(u)
+    th = sine_sum_field(dims, h, rng) + cube_step(dims, h)
+    dt = cfl * min(h) / max_abs(u)
+    return mesh, th, u, dt
+
+
+def smooth_target(dims, h, seed, n_modes=4, kmax=2):
+    rng = np.random.default_rng(seed + 1000)
+    return sine_sum_field(dims, h, rng, n_modes=n_modes, kmax=kmax, amp=0.5)
+
+
+def random_field(n, seed, scale=1.0):
+    return np.random.default_rng(seed).normal(0.0, scale, n)
+
+
+def mixed_sign_velocity(n_faces, seed, zero_fraction=0.1):
+    """Random face velocities with both signs and some exact zeros (and one
+    negative zero) for upwind-selection tests."""
+    rng = np.random.default_rng(seed)
+    u = rng.normal(0.0, 1.0, n_faces)
+    u[rng.random(n_faces) < zero_fraction] = 0.0
+    if n_faces > 2:
+        u[1] = -0.0
+    return u
