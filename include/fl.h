@@ -1,0 +1,237 @@
+/*
+ * fl.h -- C ABI of the GB300 flux-limited convection library.
+ *
+ * The library evaluates the flux-limited convective operator of Valle et al.,
+ * "On the implementation of flux limiters in algebraic frameworks", and the
+ * explicit time step it drives, with hand-written sm_103a CUDA kernels.
+ *
+ * Operation (per face f with cells (c0, c1), unit normal n_f from c0 to c1,
+ * normal velocity u_f, area A_f; per cell c with volume V_c):
+ *   s_f     = u_f > 0 ? +1 : -1                        eq. (sign), Table 1 signxty
+ *   C, D    = upwind / downwind cell of f (C = c0 when s_f = +1)
+ *   d_u     = theta_D - theta_C                         eq. (Delta_face)
+ *   d_U     = theta_C - theta_U, U the upstream cell behind C
+ *             (eq. (Delta_Upwind) with the orientation correction Q)
+ *   r_f     = d_U / d_u                                 eq. (gradientRatio), (rf)
+ *   theta_f = theta_C + Psi(r_f) d_u / 2,  theta_f = theta_C when d_u == 0
+ *                                                       eq. (FL-UP) == (FL-CD)
+ *   R_c     = -(1/V_c) sum_{f in dc} sigma_cf u_f A_f theta_f,
+ *             sigma = +1 when c = c0, -1 when c = c1    Algorithm 4 (M U theta_f)
+ *   Euler:   theta^{n+1} = theta^n + dt R(theta^n)      Algorithm 4
+ *   SSP-RK3: th1 = thn + dt R(thn); th2 = 3/4 thn + 1/4 (th1 + dt R(th1));
+ *            th^{n+1} = 1/3 thn + 2/3 (th2 + dt R(th2))
+ *
+ * Conventions common to every call:
+ *   - Field buffers (theta, u_f, rhs, lambda, workspace) are DEVICE pointers
+ *     owned by the caller; the library never frees or retains them.
+ *   - dtype selects the element type of every field buffer of the call:
+ *     FL_F64 = double, FL_F32 = float.
+ *   - Structured meshes: cell c = i + nx*(j + ny*k).  Faces exist only along
+ *     axes of extent > 1; for each such axis (x, y, z order) u_f holds one
+ *     block of n_cells values, the face of cell c in that block lying between
+ *     c and its +1 neighbour along the axis (periodic).  n_faces = n_cells *
+ *     (number of axes of extent > 1).
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Compute calls are asynchronous on that stream; argument errors are
+ *     returned synchronously before anything is enqueued.
+ *   - Every call returns fl_status; fl_last_error() gives a thread-local
+ *     message for the last failure on the calling thread.
+ *   - No compute call allocates device memory; scratch comes from the caller
+ *     (fl_workspace_size / fl_adjoint_workspace_size).
+ */
+#ifndef FL_H_
+#define FL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FL_OK = 0,
+  FL_EINVAL = 1,        /* bad argument (NULL pointer, size, enum, mesh data) */
+  FL_ENOMEM = 2,        /* host or device allocation failed (mesh/batch create only) */
+  FL_ECUDA = 3,         /* a CUDA runtime call or a launch failed */
+  FL_EUNSUPPORTED = 4,  /* valid input the library does not handle */
+  FL_ENONFINITE = 5,    /* a reduction met NaN or Inf */
+  FL_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+  FL_EINDEX = 7         /* a device-side index check failed (checked builds) */
+} fl_status;
+
+/* Limiter functions Psi(r) (Sweby's form; the paper's F(r) = (Psi - 1)/2). */
+typedef enum {
+  FL_UPWIND = 0,   /* Psi = 0: first-order upwind                      */
+  FL_CENTRAL = 1,  /* Psi = 1: central (symmetric) reconstruction      */
+  FL_MINMOD = 2,   /* max(0, min(1, r))                                */
+  FL_VANLEER = 3,  /* (r + |r|) / (1 + |r|)                            */
+  FL_SUPERBEE = 4, /* max(0, min(1, 2r), min(r, 2)); Table 1 superbeexty */
+  FL_SMART = 5     /* max(0, min(2r, 1/4 + 3/4 r, 4))                  */
+} fl_limiter;
+
+typedef enum { FL_F32 = 0, FL_F64 = 1 } fl_dtype;
+
+/* flags of fl_mesh_create */
+#define FL_RENUMBER 1u /* reorder cells/faces internally for locality */
+
+typedef struct fl_mesh fl_mesh;
+typedef struct fl_batch fl_batch;
+
+/* Thread-local message describing the last failure on this thread. */
+const char *fl_last_error(void);
+
+/* Library version string. */
+const char *fl_version(void);
+
+/*
+ * Structured periodic box nx x ny x nz with spacings hx, hy, hz (the
+ * Cartesian grid on which the method collapses to Sweby's 1D scheme,
+ * Section 3.1 / Section 6).  Use ny = nz = 1 for 1D, nz = 1 for 2D.
+ * periodic_mask must have the bit of every axis of extent > 1 set
+ * (bit 0 = x, 1 = y, 2 = z); non-periodic boundaries return FL_EUNSUPPORTED.
+ * Sizes must be >= 1 with nx*ny*nz < 2^31; spacings > 0.
+ * The mesh is bound to the current CUDA device; *out owns host memory only.
+ */
+fl_status fl_mesh_create_structured(int nx, int ny, int nz, double hx, double hy, double hz,
+                                    unsigned periodic_mask, fl_mesh **out);
+
+/*
+ * General face-based mesh (Section 2: the directed cell-to-face incidence
+ * E_{C->F} given row by row as face_cells[f] = (c0, c1), plus the normal
+ * matrix N_F as face_normals[f] = n_f, face areas and cell volumes).
+ * All input arrays are HOST arrays, copied; the caller keeps ownership.
+ *   face_cells   int32 [n_faces][2], 0 <= c < n_cells, c0 != c1
+ *   face_normals double [n_faces][3], unit normal pointing c0 -> c1
+ *   face_areas   double [n_faces] > 0
+ *   cell_volumes double [n_cells] > 0
+ * Supported meshes: every cell has an opposite face for each of its faces
+ * (n_f . n_j = -+1 for exactly one other face j of the cell and 0 for the
+ * rest), i.e. hexahedral meshes in any numbering and orientation; other
+ * meshes return FL_EUNSUPPORTED.  Faces listed twice, c0 == c1, out-of-range
+ * cells and non-unit normals return FL_EINVAL.
+ * With FL_RENUMBER the library reorders cells and faces into compact blocks
+ * for locality; fields passed to compute calls are then in the INTERNAL
+ * order given by fl_mesh_permutation.  Without it the user order is used.
+ */
+fl_status fl_mesh_create(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,
+                         const double *face_normals, const double *face_areas,
+                         const double *cell_volumes, unsigned flags, fl_mesh **out);
+
+/*
+ * Internal numbering of a mesh created with FL_RENUMBER (host arrays):
+ * cell_perm[user_cell] = internal cell, face_perm[user_face] = internal face,
+ * face_flip[user_face] = 1 if the internal face has the opposite orientation
+ * (so internal u = -user u).  Any output may be NULL.  For meshes without
+ * renumbering the permutations are the identity.
+ */
+fl_status fl_mesh_permutation(const fl_mesh *mesh, int32_t *cell_perm, int32_t *face_perm,
+                              uint8_t *face_flip);
+
+/* Sizes of a mesh: cells, faces, kind (0 structured, 1 unstructured). */
+fl_status fl_mesh_info(const fl_mesh *mesh, int64_t *n_cells, int64_t *n_faces, int *kind);
+
+fl_status fl_mesh_destroy(fl_mesh *mesh);
+
+/*
+ * Algorithm 1 plus the cell sum of Algorithm 4: evaluates
+ *   rhs_c   = R(theta)_c   [n_cells]   (always)
+ *   theta_f = limited face values [n_faces]   (when theta_f != NULL)
+ * theta_c [n_cells], u_f [n_faces], rhs_c, theta_f: device, dtype elements.
+ */
+fl_status fl_conv_limited_apply(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                                const void *theta_c, const void *u_f, void *rhs_c, void *theta_f,
+                                void *stream);
+
+/*
+ * Upwind selection per face (eq. (sign), Delta_face, Delta_Upwind):
+ * sel[f] = (s_f, C, D, U) as int32 [n_faces][4], device.  Depends on u_f
+ * and the mesh only.  Cell ids in the numbering the compute calls use.
+ */
+fl_status fl_face_selection(const fl_mesh *mesh, fl_dtype dtype, const void *u_f, int32_t *sel,
+                            void *stream);
+
+/* Bytes of device workspace fl_step_rk needs (rk_order 1 or 3). */
+fl_status fl_workspace_size(const fl_mesh *mesh, fl_dtype dtype, int rk_order, size_t *bytes);
+
+/*
+ * nsteps explicit steps of Algorithm 4 (rk_order 1, forward Euler) or of
+ * SSP-RK3 (rk_order 3), in place on theta [n_cells] (device).  dt is the
+ * physical step.  workspace: device, >= fl_workspace_size bytes, 256-byte
+ * aligned; its contents are scratch.  One fused kernel launch per stage.
+ */
+fl_status fl_step_rk(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype, int rk_order,
+                     double dt, int64_t nsteps, void *theta, const void *u_f, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
+/*
+ * Transpose of the Jacobian of R at theta_c applied to lambda_rhs:
+ *   lambda_theta = (dR/dtheta)^T lambda_rhs     [n_cells] device.
+ * The limiter derivative is taken on the branch selected by strict ordered
+ * tests at theta_c (ties to the lower branch); d_u == 0 keeps theta_C.
+ */
+fl_status fl_conv_limited_adjoint(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                                  const void *theta_c, const void *u_f, const void *lambda_rhs,
+                                  void *lambda_theta, void *stream);
+
+/* Bytes of device workspace fl_step_rk_adjoint needs. */
+fl_status fl_adjoint_workspace_size(const fl_mesh *mesh, fl_dtype dtype, int rk_order,
+                                    int64_t nsteps, int64_t checkpoint_every, size_t *bytes);
+
+/*
+ * Reverse-mode sweep of nsteps steps from theta0: given lambda_T = dJ/dtheta_T
+ * returns lambda_0 = dJ/dtheta_0 (all [n_cells], device).  The forward
+ * rollout is checkpointed every checkpoint_every steps in the workspace and
+ * each segment is recomputed (storing its stage states) before its adjoint
+ * stages run in reverse order.  theta0 is not modified.
+ */
+fl_status fl_step_rk_adjoint(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                             int rk_order, double dt, int64_t nsteps, int64_t checkpoint_every,
+                             const void *theta0, const void *u_f, const void *lambda_T,
+                             void *lambda_0, void *workspace, size_t workspace_bytes,
+                             void *stream);
+
+/*
+ * Batched form: n independent structured meshes advanced together, one
+ * persistent launch per stage over all instances.  meshes: host array of n
+ * structured meshes (kept by reference; they must outlive the batch).
+ */
+fl_status fl_batch_create(int n, const fl_mesh *const *meshes, fl_batch **out);
+
+/* Workspace bytes of fl_batch_step_rk. */
+fl_status fl_batch_workspace_size(const fl_batch *batch, fl_dtype dtype, int rk_order,
+                                  size_t *bytes);
+
+/*
+ * nsteps steps of every instance.  theta, u_f: host arrays of n device
+ * pointers; dt: host array of n step sizes.  Tiles of all instances form
+ * one work list; every stage is one launch over it.
+ */
+fl_status fl_batch_step_rk(fl_batch *batch, fl_limiter limiter, fl_dtype dtype, int rk_order,
+                           const double *dt, int64_t nsteps, void *const *theta,
+                           const void *const *u_f, void *workspace, size_t workspace_bytes,
+                           void *stream);
+
+fl_status fl_batch_destroy(fl_batch *batch);
+
+/*
+ * kred-style reductions (Section 3.2 generalised reduction):
+ *   fl_reduce_max_abs: *out = max_i |x_i| over n elements (e.g. max |u_f|
+ *                      for the CFL step size); FL_ENONFINITE if any x_i is
+ *                      NaN or Inf.
+ *   fl_reduce_mass:    *out = sum_c V_c theta_c (conserved quantity) for a
+ *                      mesh's cells, compensated summation; FL_ENONFINITE on
+ *                      NaN/Inf.
+ * x / theta: device; out: HOST double.  These calls synchronise the stream.
+ * workspace: device, >= fl_reduce_workspace_size() bytes.
+ */
+size_t fl_reduce_workspace_size(void);
+fl_status fl_reduce_max_abs(fl_dtype dtype, const void *x, int64_t n, double *out,
+                            void *workspace, void *stream);
+fl_status fl_reduce_mass(const fl_mesh *mesh, fl_dtype dtype, const void *theta, double *out,
+                         void *workspace, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FL_H_ */

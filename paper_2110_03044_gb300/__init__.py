@@ -1,0 +1,357 @@
+"""GB300 flux-limited convection library -- Python binding of ``include/fl.h``.
+
+The compute path is the CUDA library ``_build/libfl.so`` (hand-written
+sm_103a kernels).  This module only marshals arguments: every ``fl_*``
+function here has the name and argument order of the C entry point, takes
+device buffers as integers or CUDA tensors, raises :class:`FLError` on a
+non-zero status and returns the C outputs.  There is no CPU fallback: if the
+library is not built, every call raises.
+
+A few helpers sit on top (``Mesh``, ``step_rk``, ``conv_limited_apply``):
+they allocate the caller-side workspace with PyTorch and pass the current
+stream, nothing else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfl.so")
+
+FL_OK, FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_EUNSUPPORTED, FL_ENONFINITE, FL_ETIMEOUT, FL_EINDEX = \
+    range(8)
+STATUS_NAMES = ["FL_OK", "FL_EINVAL", "FL_ENOMEM", "FL_ECUDA", "FL_EUNSUPPORTED",
+                "FL_ENONFINITE", "FL_ETIMEOUT", "FL_EINDEX"]
+LIMITERS = {"upwind": 0, "central": 1, "minmod": 2, "vanleer": 3, "superbee": 4, "smart": 5}
+FL_F32, FL_F64 = 0, 1
+FL_RENUMBER = 1
+
+# Exported symbols of include/fl.h (checked by the ABI test).
+ABI_SYMBOLS = [
+    "fl_last_error", "fl_version", "fl_mesh_create_structured", "fl_mesh_create",
+    "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_destroy", "fl_conv_limited_apply",
+    "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_conv_limited_adjoint",
+    "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_batch_create",
+    "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_destroy",
+    "fl_reduce_workspace_size", "fl_reduce_max_abs", "fl_reduce_mass",
+]
+
+
+class FLError(RuntimeError):
+    def __init__(self, status, msg):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s: %s" % (name, msg))
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile libfl.so (nvcc, sm_103a) in-tree; returns its path."""
+    from . import _build_lib
+    return _build_lib.build(force=force)
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing: run paper_2110_03044_gb300.build() "
+                               "(there is no CPU fallback)" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D, U, SZ = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                               ctypes.c_uint, ctypes.c_size_t)
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "fl_last_error": (ctypes.c_char_p, []),
+            "fl_version": (ctypes.c_char_p, []),
+            "fl_mesh_create_structured": (I, [I, I, I, D, D, D, U, PP]),
+            "fl_mesh_create": (I, [I64, I64, P, P, P, P, U, PP]),
+            "fl_mesh_permutation": (I, [P, P, P, P]),
+            "fl_mesh_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                 ctypes.POINTER(I)]),
+            "fl_mesh_destroy": (I, [P]),
+            "fl_conv_limited_apply": (I, [P, I, I, P, P, P, P, P]),
+            "fl_face_selection": (I, [P, I, P, P, P]),
+            "fl_workspace_size": (I, [P, I, I, ctypes.POINTER(SZ)]),
+            "fl_step_rk": (I, [P, I, I, I, D, I64, P, P, P, SZ, P]),
+            "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
+            "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
+            "fl_step_rk_adjoint": (I, [P, I, I, I, D, I64, I64, P, P, P, P, P, SZ, P]),
+            "fl_batch_create": (I, [I, PP, PP]),
+            "fl_batch_workspace_size": (I, [P, I, I, ctypes.POINTER(SZ)]),
+            "fl_batch_step_rk": (I, [P, I, I, I, ctypes.POINTER(D), I64, PP, PP, P, SZ, P]),
+            "fl_batch_destroy": (I, [P]),
+            "fl_reduce_workspace_size": (SZ, []),
+            "fl_reduce_max_abs": (I, [I, P, I64, ctypes.POINTER(D), P, P]),
+            "fl_reduce_mass": (I, [P, I, P, ctypes.POINTER(D), P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(st):
+    if st != FL_OK:
+        raise FLError(st, lib().fl_last_error().decode(errors="replace"))
+
+
+# ------------------------------------------------------------- marshalling
+def _ptr(x):
+    """Device pointer of a tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError("expected a CUDA tensor or an integer device pointer, got %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _lim(limiter):
+    return LIMITERS[limiter] if isinstance(limiter, str) else int(limiter)
+
+
+def dtype_code(dtype):
+    import torch
+    if dtype in (torch.float64, "f64", "float64", FL_F64):
+        return FL_F64
+    if dtype in (torch.float32, "f32", "float32", FL_F32):
+        return FL_F32
+    raise ValueError("unsupported dtype %r" % (dtype,))
+
+
+# ------------------------------------------------------ C entry points
+def fl_version():
+    return lib().fl_version().decode()
+
+
+def fl_last_error():
+    return lib().fl_last_error().decode(errors="replace")
+
+
+def fl_mesh_create_structured(nx, ny, nz, hx, hy, hz, periodic_mask=7):
+    h = ctypes.c_void_p()
+    _check(lib().fl_mesh_create_structured(int(nx), int(ny), int(nz), float(hx), float(hy),
+                                           float(hz), int(periodic_mask), ctypes.byref(h)))
+    return h.value
+
+
+def fl_mesh_create(n_cells, face_cells, face_normals, face_areas, cell_volumes, flags=0):
+    import numpy as np
+    fc = np.ascontiguousarray(face_cells, dtype=np.int32)
+    nrm = np.ascontiguousarray(face_normals, dtype=np.float64)
+    ar = np.ascontiguousarray(face_areas, dtype=np.float64)
+    vol = np.ascontiguousarray(cell_volumes, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(lib().fl_mesh_create(int(n_cells), int(fc.shape[0]), fc.ctypes.data, nrm.ctypes.data,
+                                ar.ctypes.data, vol.ctypes.data, int(flags), ctypes.byref(h)))
+    return h.value
+
+
+def fl_mesh_permutation(mesh):
+    import numpy as np
+    C, F, _ = fl_mesh_info(mesh)
+    cp = np.empty(C, np.int32)
+    fp = np.empty(F, np.int32)
+    fl = np.empty(F, np.uint8)
+    _check(lib().fl_mesh_permutation(mesh, cp.ctypes.data, fp.ctypes.data, fl.ctypes.data))
+    return cp, fp, fl
+
+
+def fl_mesh_info(mesh):
+    c, f, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    _check(lib().fl_mesh_info(mesh, ctypes.byref(c), ctypes.byref(f), ctypes.byref(k)))
+    return c.value, f.value, k.value
+
+
+def fl_mesh_destroy(mesh):
+    _check(lib().fl_mesh_destroy(mesh))
+
+
+def fl_conv_limited_apply(mesh, limiter, dtype, theta_c, u_f, rhs_c, theta_f=None, stream=None):
+    _check(lib().fl_conv_limited_apply(mesh, _lim(limiter), dtype_code(dtype), _ptr(theta_c),
+                                       _ptr(u_f), _ptr(rhs_c), _ptr(theta_f), _stream(stream)))
+
+
+def fl_face_selection(mesh, dtype, u_f, sel, stream=None):
+    _check(lib().fl_face_selection(mesh, dtype_code(dtype), _ptr(u_f), _ptr(sel),
+                                   _stream(stream)))
+
+
+def fl_workspace_size(mesh, dtype, rk_order):
+    n = ctypes.c_size_t()
+    _check(lib().fl_workspace_size(mesh, dtype_code(dtype), int(rk_order), ctypes.byref(n)))
+    return n.value
+
+
+def fl_step_rk(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, workspace,
+               workspace_bytes, stream=None):
+    _check(lib().fl_step_rk(mesh, _lim(limiter), dtype_code(dtype), int(rk_order), float(dt),
+                            int(nsteps), _ptr(theta), _ptr(u_f), _ptr(workspace),
+                            int(workspace_bytes), _stream(stream)))
+
+
+def fl_conv_limited_adjoint(mesh, limiter, dtype, theta_c, u_f, lambda_rhs, lambda_theta,
+                            stream=None):
+    _check(lib().fl_conv_limited_adjoint(mesh, _lim(limiter), dtype_code(dtype), _ptr(theta_c),
+                                         _ptr(u_f), _ptr(lambda_rhs), _ptr(lambda_theta),
+                                         _stream(stream)))
+
+
+def fl_adjoint_workspace_size(mesh, dtype, rk_order, nsteps, checkpoint_every):
+    n = ctypes.c_size_t()
+    _check(lib().fl_adjoint_workspace_size(mesh, dtype_code(dtype), int(rk_order), int(nsteps),
+                                           int(checkpoint_every), ctypes.byref(n)))
+    return n.value
+
+
+def fl_step_rk_adjoint(mesh, limiter, dtype, rk_order, dt, nsteps, checkpoint_every, theta0, u_f,
+                       lambda_T, lambda_0, workspace, workspace_bytes, stream=None):
+    _check(lib().fl_step_rk_adjoint(mesh, _lim(limiter), dtype_code(dtype), int(rk_order),
+                                    float(dt), int(nsteps), int(checkpoint_every), _ptr(theta0),
+                                    _ptr(u_f), _ptr(lambda_T), _ptr(lambda_0), _ptr(workspace),
+                                    int(workspace_bytes), _stream(stream)))
+
+
+def fl_batch_create(meshes):
+    arr = (ctypes.c_void_p * len(meshes))(*meshes)
+    h = ctypes.c_void_p()
+    _check(lib().fl_batch_create(len(meshes), arr, ctypes.byref(h)))
+    return h.value
+
+
+def fl_batch_workspace_size(batch, dtype, rk_order):
+    n = ctypes.c_size_t()
+    _check(lib().fl_batch_workspace_size(batch, dtype_code(dtype), int(rk_order),
+                                         ctypes.byref(n)))
+    return n.value
+
+
+def fl_batch_step_rk(batch, limiter, dtype, rk_order, dts, nsteps, thetas, u_fs, workspace,
+                     workspace_bytes, stream=None):
+    n = len(thetas)
+    dt_arr = (ctypes.c_double * n)(*[float(d) for d in dts])
+    th_arr = (ctypes.c_void_p * n)(*[_ptr(t) for t in thetas])
+    u_arr = (ctypes.c_void_p * n)(*[_ptr(u) for u in u_fs])
+    _check(lib().fl_batch_step_rk(batch, _lim(limiter), dtype_code(dtype), int(rk_order), dt_arr,
+                                  int(nsteps), th_arr, u_arr, _ptr(workspace),
+                                  int(workspace_bytes), _stream(stream)))
+
+
+def fl_batch_destroy(batch):
+    _check(lib().fl_batch_destroy(batch))
+
+
+def fl_reduce_workspace_size():
+    return int(lib().fl_reduce_workspace_size())
+
+
+def fl_reduce_max_abs(dtype, x, n, workspace, stream=None):
+    out = ctypes.c_double()
+    _check(lib().fl_reduce_max_abs(dtype_code(dtype), _ptr(x), int(n), ctypes.byref(out),
+                                   _ptr(workspace), _stream(stream)))
+    return out.value
+
+
+def fl_reduce_mass(mesh, dtype, theta, workspace, stream=None):
+    out = ctypes.c_double()
+    _check(lib().fl_reduce_mass(mesh, dtype_code(dtype), _ptr(theta), ctypes.byref(out),
+                                _ptr(workspace), _stream(stream)))
+    return out.value
+
+
+# ---------------------------------------------------------------- helpers
+class Mesh:
+    """Owns an ``fl_mesh`` handle."""
+
+    def __init__(self, handle, dims=None, h=None):
+        self.handle = handle
+        self.n_cells, self.n_faces, self.kind = fl_mesh_info(handle)
+        self.dims = dims
+        self.h = h
+
+    @classmethod
+    def structured(cls, nx, ny=1, nz=1, hx=1.0, hy=1.0, hz=1.0):
+        return cls(fl_mesh_create_structured(nx, ny, nz, hx, hy, hz, 7), (nx, ny, nz),
+                   (hx, hy, hz))
+
+    @classmethod
+    def from_faces(cls, n_cells, face_cells, face_normals, face_areas, cell_volumes,
+                   renumber=False):
+        return cls(fl_mesh_create(n_cells, face_cells, face_normals, face_areas, cell_volumes,
+                                  FL_RENUMBER if renumber else 0))
+
+    def permutation(self):
+        return fl_mesh_permutation(self.handle)
+
+    def close(self):
+        if self.handle:
+            fl_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dt_of(t):
+    return dtype_code(t.dtype)
+
+
+def workspace_for(mesh, dtype, rk_order, device="cuda"):
+    import torch
+    n = fl_workspace_size(mesh.handle, dtype, rk_order)
+    return torch.empty(max(n, 1), dtype=torch.uint8, device=device), n
+
+
+def step_rk(mesh, limiter, theta, u_f, dt, nsteps, rk_order=3, workspace=None, stream=None):
+    """In-place ``nsteps`` steps on the CUDA tensor ``theta``."""
+    if workspace is None:
+        workspace, nbytes = workspace_for(mesh, theta.dtype, rk_order, theta.device)
+    else:
+        nbytes = workspace.numel() * workspace.element_size()
+    fl_step_rk(mesh.handle, limiter, theta.dtype, rk_order, dt, nsteps, theta, u_f, workspace,
+               nbytes, stream)
+    return theta
+
+
+def conv_limited_apply(mesh, limiter, theta, u_f, want_theta_f=False, stream=None):
+    import torch
+    rhs = torch.empty_like(theta)
+    thf = torch.empty(mesh.n_faces, dtype=theta.dtype, device=theta.device) if want_theta_f \
+        else None
+    fl_conv_limited_apply(mesh.handle, limiter, theta.dtype, theta, u_f, rhs, thf, stream)
+    return (rhs, thf) if want_theta_f else rhs
+
+
+def face_selection(mesh, u_f, stream=None):
+    import torch
+    sel = torch.empty((mesh.n_faces, 4), dtype=torch.int32, device=u_f.device)
+    fl_face_selection(mesh.handle, u_f.dtype, u_f, sel, stream)
+    return sel

@@ -1,0 +1,385 @@
+// fl_api.cu -- the C ABI (include/fl.h): argument checking, buffer checks,
+// dispatch to the kernels, stage sequencing of Euler / SSP-RK3.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "fl_internal.h"
+#include "fl_kernels.h"
+#include "fl_unstructured.h"
+
+namespace fl {
+
+namespace {
+thread_local char g_msg[512] = "";
+}
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+}
+
+fl_status fail(fl_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+fl_status cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  return FL_ECUDA;
+}
+
+// A device buffer must be device memory of the calling context and hold at
+// least `bytes` bytes from p to the end of its allocation, so that no kernel
+// of this library can read or write outside what the caller allocated.
+typedef CUresult (*addr_range_fn)(CUdeviceptr *, size_t *, CUdeviceptr);
+
+// The driver's allocation-range query, fetched through the runtime so that
+// the library has no link-time dependency on the driver library.
+addr_range_fn get_addr_range() {
+  static addr_range_fn fn = []() -> addr_range_fn {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<addr_range_fn>(f);
+  }();
+  return fn;
+}
+
+fl_status check_buffer(const void *p, size_t bytes, const char *name) {
+  if (bytes == 0) return FL_OK;
+  if (p == nullptr) return fail(FL_EINVAL, "%s is NULL", name);
+  addr_range_fn range = get_addr_range();
+  if (range == nullptr) return fail(FL_ECUDA, "CUDA driver entry point unavailable");
+  CUdeviceptr base = 0;
+  size_t size = 0;
+  CUresult r = range(&base, &size, (CUdeviceptr)p);
+  if (r == CUDA_ERROR_INVALID_CONTEXT) {
+    // no context current on this thread yet: let the runtime bind the
+    // primary context of the current device, then ask again
+    cudaFree(nullptr);
+    r = range(&base, &size, (CUdeviceptr)p);
+  }
+  if (r != CUDA_SUCCESS)
+    return fail(FL_EINVAL, "%s (%p) is not device memory of the current context", name, p);
+  const size_t off = (size_t)((CUdeviceptr)p - base);
+  if (off + bytes > size)
+    return fail(FL_EINVAL, "%s: %zu bytes needed from %p but the allocation ends %zu bytes after it",
+                name, bytes, p, size - off);
+  return FL_OK;
+}
+
+fl_status check_mesh(const fl_mesh *m) {
+  if (m == nullptr) return fail(FL_EINVAL, "mesh is NULL");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(FL_ECUDA, "cudaGetDevice failed");
+  if (dev != m->device)
+    return fail(FL_EINVAL, "mesh was created on device %d but device %d is current", m->device, dev);
+  return FL_OK;
+}
+
+fl_status check_enums(int lim, fl_dtype dt) {
+  if (lim < FL_UPWIND || lim > FL_SMART) return fail(FL_EINVAL, "unknown limiter %d", lim);
+  if (dt != FL_F32 && dt != FL_F64) return fail(FL_EINVAL, "unknown dtype %d", (int)dt);
+  return FL_OK;
+}
+
+size_t step_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk) {
+  const size_t one = align256((size_t)m->C * dsize(dt));
+  return rk == 3 ? 2 * one : one;
+}
+
+}  // namespace fl
+
+using namespace fl;
+
+#define FL_TRY(expr)              \
+  do {                            \
+    fl_status s_ = (expr);        \
+    if (s_ != FL_OK) return s_;   \
+  } while (0)
+
+extern "C" {
+
+const char *fl_last_error(void) { return fl::g_msg; }
+
+const char *fl_version(void) { return "fl-gb300 0.1 (sm_103a)"; }
+
+fl_status fl_mesh_create_structured(int nx, int ny, int nz, double hx, double hy, double hz,
+                                    unsigned periodic_mask, fl_mesh **out) {
+  if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(FL_EINVAL, "sizes must be >= 1");
+  if (!(hx > 0) || !(hy > 0) || !(hz > 0) || !std::isfinite(hx) || !std::isfinite(hy) ||
+      !std::isfinite(hz))
+    return fail(FL_EINVAL, "spacings must be finite and > 0");
+  const long long C = (long long)nx * ny * nz;
+  if (C >= (1LL << 31)) return fail(FL_EUNSUPPORTED, "n_cells must be < 2^31");
+  const int n[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a)
+    if (n[a] > 1 && !(periodic_mask & (1u << a)))
+      return fail(FL_EUNSUPPORTED, "non-periodic boundaries are not supported (axis %d)", a);
+  fl_mesh *m = new (std::nothrow) fl_mesh();
+  if (!m) return fail(FL_ENOMEM, "host allocation failed");
+  if (cudaGetDevice(&m->device) != cudaSuccess) {
+    delete m;
+    return fail(FL_ECUDA, "no CUDA device");
+  }
+  m->kind = 0;
+  m->nx = nx;
+  m->ny = ny;
+  m->nz = nz;
+  m->hx = hx;
+  m->hy = hy;
+  m->hz = hz;
+  m->C = C;
+  int na = 0;
+  for (int a = 0; a < 3; ++a) {
+    m->act[a] = n[a] > 1;
+    m->u_off[a] = m->act[a] ? (int64_t)na * C : 0;
+    na += m->act[a];
+  }
+  m->F = (int64_t)na * C;
+  *out = m;
+  return FL_OK;
+}
+
+fl_status fl_mesh_create(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,
+                         const double *face_normals, const double *face_areas,
+                         const double *cell_volumes, unsigned flags, fl_mesh **out) {
+  if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
+  *out = nullptr;
+  return unstruct_create(n_cells, n_faces, face_cells, face_normals, face_areas, cell_volumes,
+                         flags, out);
+}
+
+fl_status fl_mesh_permutation(const fl_mesh *m, int32_t *cell_perm, int32_t *face_perm,
+                              uint8_t *face_flip) {
+  if (m == nullptr) return fail(FL_EINVAL, "mesh is NULL");
+  for (int64_t c = 0; cell_perm && c < m->C; ++c)
+    cell_perm[c] = m->renumbered ? m->cell_perm[c] : (int32_t)c;
+  for (int64_t f = 0; face_perm && f < m->F; ++f)
+    face_perm[f] = m->renumbered ? m->face_perm[f] : (int32_t)f;
+  for (int64_t f = 0; face_flip && f < m->F; ++f)
+    face_flip[f] = m->renumbered ? m->face_flip[f] : 0;
+  return FL_OK;
+}
+
+fl_status fl_mesh_info(const fl_mesh *m, int64_t *n_cells, int64_t *n_faces, int *kind) {
+  if (m == nullptr) return fail(FL_EINVAL, "mesh is NULL");
+  if (n_cells) *n_cells = m->C;
+  if (n_faces) *n_faces = m->F;
+  if (kind) *kind = m->kind;
+  return FL_OK;
+}
+
+fl_status fl_mesh_destroy(fl_mesh *m) {
+  if (m == nullptr) return FL_OK;
+  if (m->kind == 1) unstruct_free(m);
+  delete m;
+  return FL_OK;
+}
+
+fl_status fl_conv_limited_apply(const fl_mesh *m, fl_limiter lim, fl_dtype dt, const void *theta_c,
+                                const void *u_f, void *rhs_c, void *theta_f, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(lim, dt));
+  const size_t es = dsize(dt);
+  FL_TRY(check_buffer(theta_c, m->C * es, "theta_c"));
+  FL_TRY(check_buffer(u_f, m->F * es, "u_f"));
+  FL_TRY(check_buffer(rhs_c, m->C * es, "rhs_c"));
+  if (theta_f) FL_TRY(check_buffer(theta_f, m->F * es, "theta_f"));
+  if (m->C == 0) return FL_OK;
+  if (m->kind == 1) return unstruct_apply(m, lim, dt, theta_c, u_f, rhs_c, theta_f, as_stream(stream));
+  StageArgs s;
+  s.x = theta_c;
+  s.thn = theta_c;
+  s.y = rhs_c;
+  s.thf = theta_f;
+  s.u = u_f;
+  s.seed = 2;
+  cudaError_t e = struct_stage(m, lim, dt, s, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "structured apply kernel");
+  return FL_OK;
+}
+
+fl_status fl_face_selection(const fl_mesh *m, fl_dtype dt, const void *u_f, int32_t *sel,
+                            void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(FL_UPWIND, dt));
+  FL_TRY(check_buffer(u_f, m->F * dsize(dt), "u_f"));
+  FL_TRY(check_buffer(sel, m->F * 16, "sel"));
+  if (m->F == 0) return FL_OK;
+  cudaError_t e = (m->kind == 1) ? unstruct_selection(m, dt, u_f, sel, as_stream(stream))
+                                 : struct_selection(m, dt, u_f, sel, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "selection kernel");
+  return FL_OK;
+}
+
+fl_status fl_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, size_t *bytes) {
+  if (m == nullptr || bytes == nullptr) return fail(FL_EINVAL, "NULL argument");
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (dt != FL_F32 && dt != FL_F64) return fail(FL_EINVAL, "unknown dtype");
+  *bytes = step_ws_bytes(m, dt, rk);
+  return FL_OK;
+}
+
+fl_status fl_step_rk(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
+                     int64_t nsteps, void *theta, const void *u_f, void *ws, size_t ws_bytes,
+                     void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(lim, dt));
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (nsteps < 0) return fail(FL_EINVAL, "nsteps < 0");
+  if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
+  const size_t es = dsize(dt);
+  FL_TRY(check_buffer(theta, m->C * es, "theta"));
+  FL_TRY(check_buffer(u_f, m->F * es, "u_f"));
+  const size_t need = step_ws_bytes(m, dt, rk);
+  if (ws_bytes < need) return fail(FL_EINVAL, "workspace too small: %zu < %zu", ws_bytes, need);
+  if (((uintptr_t)ws & 255) != 0) return fail(FL_EINVAL, "workspace must be 256-byte aligned");
+  FL_TRY(check_buffer(ws, need, "workspace"));
+  if (nsteps == 0 || m->C == 0) return FL_OK;
+  cudaStream_t st = as_stream(stream);
+  if (m->kind == 1) return unstruct_step(m, lim, dt, rk, dtime, nsteps, theta, u_f, ws, st);
+  if (m->ny == 1 && m->nz == 1 && (size_t)m->nx <= line_resident_max_cells(dt)) {
+    cudaError_t e = line_resident(m, lim, dt, theta, u_f, nsteps, rk, dtime, st);
+    if (e != cudaSuccess) return cuda_fail(e, "1D resident kernel");
+    return FL_OK;
+  }
+  char *wsb = static_cast<char *>(ws);
+  void *A = wsb;
+  void *B = wsb + align256((size_t)m->C * es);
+  StageArgs s;
+  s.u = u_f;
+  s.dt = dtime;
+  cudaError_t e = cudaSuccess;
+  if (rk == 1) {
+    // Euler: ping-pong between theta and A (a stage reads neighbours of x
+    // while writing y, so x and y must differ)
+    void *cur = theta, *nxt = A;
+    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      s.x = cur;
+      s.thn = cur;
+      s.y = nxt;
+      s.seed = 0;
+      s.b = 1.0;
+      e = struct_stage(m, lim, dt, s, st);
+      void *t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    if (e == cudaSuccess && cur != theta)
+      e = cudaMemcpyAsync(theta, cur, m->C * es, cudaMemcpyDeviceToDevice, st);
+  } else {
+    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      // th1 = thn + dt R(thn)
+      s.x = theta; s.thn = theta; s.y = A; s.seed = 0; s.a = 0.0; s.b = 1.0;
+      e = struct_stage(m, lim, dt, s, st);
+      if (e != cudaSuccess) break;
+      // th2 = 3/4 thn + 1/4 (th1 + dt R(th1))
+      s.x = A; s.thn = theta; s.y = B; s.seed = 1; s.a = 0.75; s.b = 0.25;
+      e = struct_stage(m, lim, dt, s, st);
+      if (e != cudaSuccess) break;
+      // th^{n+1} = 1/3 thn + 2/3 (th2 + dt R(th2)); thn and y are read and
+      // written only at the thread's own cell, so y may alias thn
+      s.x = B; s.thn = theta; s.y = theta; s.seed = 1; s.a = 1.0 / 3.0; s.b = 2.0 / 3.0;
+      e = struct_stage(m, lim, dt, s, st);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "structured stage kernel");
+  return FL_OK;
+}
+
+fl_status fl_conv_limited_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt,
+                                  const void *theta_c, const void *u_f, const void *lambda_rhs,
+                                  void *lambda_theta, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(lim, dt));
+  (void)theta_c; (void)u_f; (void)lambda_rhs; (void)lambda_theta; (void)stream;
+  return fail(FL_EUNSUPPORTED, "adjoint not available in this build");
+}
+
+fl_status fl_adjoint_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps,
+                                    int64_t every, size_t *bytes) {
+  (void)m; (void)dt; (void)rk; (void)nsteps; (void)every; (void)bytes;
+  return fail(FL_EUNSUPPORTED, "adjoint not available in this build");
+}
+
+fl_status fl_step_rk_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
+                             int64_t nsteps, int64_t every, const void *theta0, const void *u_f,
+                             const void *lambda_T, void *lambda_0, void *ws, size_t ws_bytes,
+                             void *stream) {
+  (void)m; (void)lim; (void)dt; (void)rk; (void)dtime; (void)nsteps; (void)every; (void)theta0;
+  (void)u_f; (void)lambda_T; (void)lambda_0; (void)ws; (void)ws_bytes; (void)stream;
+  return fail(FL_EUNSUPPORTED, "adjoint not available in this build");
+}
+
+fl_status fl_batch_create(int n, const fl_mesh *const *meshes, fl_batch **out) {
+  (void)n; (void)meshes; (void)out;
+  return fail(FL_EUNSUPPORTED, "batched form not available in this build");
+}
+
+fl_status fl_batch_workspace_size(const fl_batch *b, fl_dtype dt, int rk, size_t *bytes) {
+  (void)b; (void)dt; (void)rk; (void)bytes;
+  return fail(FL_EUNSUPPORTED, "batched form not available in this build");
+}
+
+fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, const double *dtv,
+                           int64_t nsteps, void *const *theta, const void *const *u_f, void *ws,
+                           size_t ws_bytes, void *stream) {
+  (void)b; (void)lim; (void)dt; (void)rk; (void)dtv; (void)nsteps; (void)theta; (void)u_f;
+  (void)ws; (void)ws_bytes; (void)stream;
+  return fail(FL_EUNSUPPORTED, "batched form not available in this build");
+}
+
+fl_status fl_batch_destroy(fl_batch *b) {
+  (void)b;
+  return FL_OK;
+}
+
+size_t fl_reduce_workspace_size(void) { return reduce_ws_bytes(); }
+
+fl_status fl_reduce_max_abs(fl_dtype dt, const void *x, int64_t n, double *out, void *ws,
+                            void *stream) {
+  if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
+  FL_TRY(check_enums(FL_UPWIND, dt));
+  if (n < 0) return fail(FL_EINVAL, "n < 0");
+  FL_TRY(check_buffer(x, (size_t)n * dsize(dt), "x"));
+  FL_TRY(check_buffer(ws, reduce_ws_bytes(), "workspace"));
+  int bad = 0;
+  cudaError_t e = reduce_max_abs(dt, x, n, ws, as_stream(stream), out, &bad);
+  if (e != cudaSuccess) return cuda_fail(e, "reduction");
+  if (bad) return fail(FL_ENONFINITE, "non-finite value in input");
+  return FL_OK;
+}
+
+fl_status fl_reduce_mass(const fl_mesh *m, fl_dtype dt, const void *theta, double *out, void *ws,
+                         void *stream) {
+  FL_TRY(check_mesh(m));
+  if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
+  FL_TRY(check_enums(FL_UPWIND, dt));
+  FL_TRY(check_buffer(theta, m->C * dsize(dt), "theta"));
+  FL_TRY(check_buffer(ws, reduce_ws_bytes(), "workspace"));
+  int bad = 0;
+  const double *vol = (m->kind == 1) ? unstruct_volumes(m) : nullptr;
+  const double vc = m->hx * m->hy * m->hz;
+  cudaError_t e = reduce_mass(dt, theta, vol, vc, m->C, ws, as_stream(stream), out, &bad);
+  if (e != cudaSuccess) return cuda_fail(e, "reduction");
+  if (bad) return fail(FL_ENONFINITE, "non-finite value in theta");
+  return FL_OK;
+}
+
+}  // extern "C"

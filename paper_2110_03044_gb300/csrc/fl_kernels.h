@@ -1,0 +1,37 @@
+// fl_kernels.h -- launchers implemented in the .cu files (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fl_internal.h"
+
+namespace fl {
+
+// One RK stage y = a*thn + b*(x + dt R(x)) (seed 1), y = x + dt R(x)
+// (seed 0, b = 1) or y = R(x) plus optional theta_f (seed 2).
+struct StageArgs {
+  const void *x = nullptr;
+  const void *thn = nullptr;
+  void *y = nullptr;
+  void *thf = nullptr;
+  const void *u = nullptr;
+  double a = 0.0, b = 1.0, dt = 0.0;
+  int seed = 0;
+};
+
+cudaError_t struct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs &s,
+                         cudaStream_t st);
+size_t line_resident_max_cells(fl_dtype dt);
+cudaError_t line_resident(const fl_mesh *m, int lim, fl_dtype dt, void *theta, const void *u,
+                          int64_t nsteps, int rk, double dtime, cudaStream_t st);
+cudaError_t struct_selection(const fl_mesh *m, fl_dtype dt, const void *u, int32_t *sel,
+                             cudaStream_t st);
+
+// reductions (fl_reduce.cu)
+size_t reduce_ws_bytes();
+cudaError_t reduce_max_abs(fl_dtype dt, const void *x, int64_t n, void *ws, cudaStream_t st,
+                           double *out, int *nonfinite);
+cudaError_t reduce_mass(fl_dtype dt, const void *theta, const double *vol, double vconst,
+                        int64_t n, void *ws, cudaStream_t st, double *out, int *nonfinite);
+
+}  // namespace fl

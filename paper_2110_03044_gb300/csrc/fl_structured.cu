@@ -1,0 +1,463 @@
+// fl_structured.cu -- fused limited-convection stage on periodic Cartesian
+// meshes (Valle et al., Algorithm 4 with the limited reconstruction of
+// Algorithm 1; on Cartesian grids the algebraic d_U collapses to Sweby's
+// theta_C - theta_U, Section 3.1).
+//
+// One launch evaluates a whole RK stage: y = a*thn + b*(x + dt R(x)) (or
+// R(x) itself for fl_conv_limited_apply).  Each CTA owns a 32 x TY column of
+// cells and streams through a chunk of z planes:
+//   * theta of the current plane sits in shared memory with a 2-cell halo
+//     in x and y (the upstream cell is a second neighbour); the z neighbours
+//     of every column live in registers;
+//   * every face difference Delta_m = theta_{m+1} - theta_m is computed once
+//     and shared: a face needs its own Delta and the upstream one (Delta_{m-1}
+//     or Delta_{m+1});
+//   * every face flux u_f theta_f is computed once per CTA and reused by the
+//     two cells it separates; only the faces on the -x / -y edge of the tile
+//     are evaluated by both neighbouring CTAs (same inputs, same code, so the
+//     two results are bit-identical and the scheme stays conservative);
+//   * theta_f and the fluxes never leave the chip.
+#include <cuda_runtime.h>
+
+#include "fl_face.cuh"
+#include "fl_internal.h"
+#include "fl_kernels.h"
+
+namespace fl {
+
+namespace {
+
+constexpr int TX = 32;  // one warp along x
+
+template <class T>
+struct SParams {
+  const T *x;      // stage input theta (neighbour reads)
+  const T *thn;    // theta^n (own cell only; may alias y)
+  T *y;            // output: stage result or R (own cell only)
+  T *thf;          // optional face values (apply mode), may be null
+  const T *u;      // face velocities
+  int nx, ny, nz;
+  int act_x, act_y, act_z;
+  long long ux_off, uy_off, uz_off;
+  long long plane;  // nx*ny
+  T cx, cy, cz;     // multiply (phi_minus - phi_plus) of each axis
+  T a, b;           // seed = a*thn + b*x  (COMBINE) or x (PLAIN) or 0 (APPLY)
+  int tiles_x, tiles_y, zchunk;
+};
+
+enum { SEED_PLAIN = 0, SEED_COMBINE = 1, SEED_APPLY = 2 };
+
+__device__ __forceinline__ int wrap(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+template <class T, int LIM, int SEED, int TY>
+__global__ void __launch_bounds__(TX *TY) k_struct_stage(const SParams<T> p) {
+  using F = FT<T>;
+  constexpr int NT = TX * TY;
+  constexpr int SW = TX + 4;  // s_th row pitch
+  __shared__ T s_th[(TY + 4) * SW];
+  __shared__ T s_dx[TY * (TX + 3)];
+  __shared__ T s_dy[(TY + 3) * TX];
+  __shared__ T s_fx[TY * (TX + 1)];
+  __shared__ T s_fy[(TY + 1) * TX];
+  __shared__ int s_wx[TX + 4];
+  __shared__ int s_wy[TY + 4];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  int bid = blockIdx.x;
+  const int bx = bid % p.tiles_x;
+  bid /= p.tiles_x;
+  const int by = bid % p.tiles_y;
+  const int bz = bid / p.tiles_y;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int z0 = bz * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+
+  // wrapped coordinates of the tile's columns/rows, halo included
+  if (tid < TX + 4) s_wx[tid] = wrap(x0 - 2 + tid, nx);
+  if (tid < TY + 4) s_wy[tid] = wrap(y0 - 2 + tid, ny);
+  __syncthreads();
+
+  const bool valid = (x0 + tx < nx) && (y0 + ty < ny);
+  const long long col = (long long)s_wx[tx + 2] + (long long)nx * s_wy[ty + 2];
+
+  // halo cells of s_th: 2 columns left/right of every row, 2 rows above/below
+  constexpr int NH = 4 * (TX + TY);
+  static_assert(NH <= NT, "halo items exceed threads");
+  int h_slot = -1;
+  long long h_off = 0;
+  if (tid < 4 * TY) {  // x halo
+    const int r = tid >> 2, k4 = tid & 3;
+    const int c = (k4 < 2) ? k4 : (TX + k4);  // 0,1,TX+2,TX+3
+    h_slot = (r + 2) * SW + c;
+    h_off = (long long)s_wx[c] + (long long)nx * s_wy[r + 2];
+  } else if (tid < NH) {  // y halo
+    const int t = tid - 4 * TY;
+    const int k4 = t / TX, c = t % TX;
+    const int r = (k4 < 2) ? k4 : (TY + k4);  // 0,1,TY+2,TY+3
+    h_slot = r * SW + c + 2;
+    h_off = (long long)s_wx[c + 2] + (long long)nx * s_wy[r];
+  }
+  const bool need_x = p.act_x, need_y = p.act_y, need_z = p.act_z;
+
+  // ---- z prologue: columns k-2 .. k+1 around z0, and the flux of face z0-1/2
+  T th0, thp1, dz_m1 = T(0), dz_0 = T(0), fz_prev = T(0);
+  if (need_z) {
+    const T tm2 = p.x[col + p.plane * wrap(z0 - 2, nz)];
+    const T tm1 = p.x[col + p.plane * wrap(z0 - 1, nz)];
+    th0 = p.x[col + p.plane * z0];
+    thp1 = p.x[col + p.plane * wrap(z0 + 1, nz)];
+    const T d_m2 = F::sub(tm1, tm2);
+    dz_m1 = F::sub(th0, tm1);
+    dz_0 = F::sub(thp1, th0);
+    const T uz = p.u[p.uz_off + col + p.plane * wrap(z0 - 1, nz)];
+    const bool sp = upwind_positive(uz);
+    const T thf = limited_face<T, LIM>(sp ? tm1 : th0, dz_m1, sp ? d_m2 : dz_0, sp);
+    fz_prev = face_flux(uz, thf);
+  } else {
+    th0 = p.x[col];
+    thp1 = th0;
+  }
+
+  for (int k = z0; k < z1; ++k) {
+    const long long pk = p.plane * k;
+    // ---------------------------------------------------------- loads
+    T tp2 = T(0), uz = T(0), thn_c = T(0);
+    if (need_z) {
+      tp2 = p.x[col + p.plane * wrap(k + 2, nz)];
+      uz = p.u[p.uz_off + col + pk];
+    }
+    if (SEED == SEED_COMBINE) thn_c = p.thn[col + pk];
+    T h_val = T(0);
+    if (h_slot >= 0) h_val = p.x[h_off + pk];
+    // ------------------------------------------------------ fill plane
+    s_th[(ty + 2) * SW + tx + 2] = th0;
+    if (h_slot >= 0) s_th[h_slot] = h_val;
+    __syncthreads();
+    // ------------------------------------------- phase A: differences
+    if (need_x) {
+      for (int it = tid; it < TY * (TX + 3); it += NT) {
+        const int r = it / (TX + 3), q = it - r * (TX + 3);
+        const T *row = &s_th[(r + 2) * SW];
+        s_dx[it] = F::sub(row[q + 1], row[q]);
+      }
+    }
+    if (need_y) {
+      for (int it = tid; it < (TY + 3) * TX; it += NT) {
+        const int r = it / TX, c = it - r * TX;
+        s_dy[it] = F::sub(s_th[(r + 1) * SW + c + 2], s_th[r * SW + c + 2]);
+      }
+    }
+    T dz_p1 = T(0);
+    if (need_z) dz_p1 = F::sub(tp2, thp1);
+    __syncthreads();
+    // ----------------------------------------------- phase B: fluxes
+    if (need_x) {
+      for (int it = tid; it < TY * (TX + 1); it += NT) {
+        const int r = it / (TX + 1), q = it - r * (TX + 1);  // face m = x0-1+q
+        const long long uo = p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 2] + pk;
+        const T uf = p.u[uo];
+        const bool sp = upwind_positive(uf);
+        const T *dr = &s_dx[r * (TX + 3)];
+        const T *tr = &s_th[(r + 2) * SW];
+        const T thf = limited_face<T, LIM>(sp ? tr[q + 1] : tr[q + 2], dr[q + 1],
+                                           sp ? dr[q] : dr[q + 2], sp);
+        s_fx[it] = face_flux(uf, thf);
+        if (SEED == SEED_APPLY && p.thf != nullptr) {
+          if (q >= 1 && x0 + q - 1 < nx && y0 + r < ny) p.thf[uo] = thf;
+        }
+      }
+    }
+    if (need_y) {
+      for (int it = tid; it < (TY + 1) * TX; it += NT) {
+        const int r = it / TX, c = it - r * TX;  // face m = y0-1+r
+        const long long uo = p.uy_off + s_wx[c + 2] + (long long)nx * s_wy[r + 1] + pk;
+        const T uf = p.u[uo];
+        const bool sp = upwind_positive(uf);
+        const T thf = limited_face<T, LIM>(
+            sp ? s_th[(r + 1) * SW + c + 2] : s_th[(r + 2) * SW + c + 2], s_dy[(r + 1) * TX + c],
+            sp ? s_dy[r * TX + c] : s_dy[(r + 2) * TX + c], sp);
+        s_fy[it] = face_flux(uf, thf);
+        if (SEED == SEED_APPLY && p.thf != nullptr) {
+          if (r >= 1 && x0 + c < nx && y0 + r - 1 < ny) p.thf[uo] = thf;
+        }
+      }
+    }
+    T fz = T(0);
+    if (need_z) {
+      const bool sp = upwind_positive(uz);
+      const T thf = limited_face<T, LIM>(sp ? th0 : thp1, dz_0, sp ? dz_m1 : dz_p1, sp);
+      fz = face_flux(uz, thf);
+      if (SEED == SEED_APPLY && p.thf != nullptr && valid) p.thf[p.uz_off + col + pk] = thf;
+    }
+    __syncthreads();
+    // ------------------------------------------------ phase C: update
+    if (valid) {
+      T acc;
+      if (SEED == SEED_PLAIN) acc = th0;
+      else if (SEED == SEED_COMBINE) acc = F::fma(p.a, thn_c, F::mul(p.b, th0));
+      else acc = T(0);
+      if (need_x) {
+        acc = F::fma(-p.cx, s_fx[ty * (TX + 1) + tx + 1], acc);
+        acc = F::fma(p.cx, s_fx[ty * (TX + 1) + tx], acc);
+      }
+      if (need_y) {
+        acc = F::fma(-p.cy, s_fy[(ty + 1) * TX + tx], acc);
+        acc = F::fma(p.cy, s_fy[ty * TX + tx], acc);
+      }
+      if (need_z) {
+        acc = F::fma(-p.cz, fz, acc);
+        acc = F::fma(p.cz, fz_prev, acc);
+      }
+      p.y[col + pk] = acc;
+    }
+    // --------------------------------------------------------- rotate
+    if (need_z) {
+      fz_prev = fz;
+      dz_m1 = dz_0;
+      dz_0 = dz_p1;
+      th0 = thp1;
+      thp1 = tp2;
+    } else if (k + 1 < z1) {
+      th0 = p.x[col + p.plane * (k + 1)];
+    }
+  }
+}
+
+template <class T, int LIM, int SEED>
+cudaError_t launch_stage(const SParams<T> &p0, int tiles_z, cudaStream_t st) {
+  constexpr int TY = 8;
+  SParams<T> p = p0;
+  const dim3 block(TX, TY);
+  const long long grid = (long long)p.tiles_x * p.tiles_y * tiles_z;
+  k_struct_stage<T, LIM, SEED, TY><<<(unsigned)grid, block, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <class T, int SEED>
+cudaError_t dispatch_lim(int lim, const SParams<T> &p, int tz, cudaStream_t st) {
+  switch (lim) {
+    case LIM_UPWIND: return launch_stage<T, LIM_UPWIND, SEED>(p, tz, st);
+    case LIM_CENTRAL: return launch_stage<T, LIM_CENTRAL, SEED>(p, tz, st);
+    case LIM_MINMOD: return launch_stage<T, LIM_MINMOD, SEED>(p, tz, st);
+    case LIM_VANLEER: return launch_stage<T, LIM_VANLEER, SEED>(p, tz, st);
+    case LIM_SUPERBEE: return launch_stage<T, LIM_SUPERBEE, SEED>(p, tz, st);
+    case LIM_SMART: return launch_stage<T, LIM_SMART, SEED>(p, tz, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class T>
+cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStream_t st) {
+  SParams<T> p;
+  p.x = static_cast<const T *>(s.x);
+  p.thn = static_cast<const T *>(s.thn);
+  p.y = static_cast<T *>(s.y);
+  p.thf = static_cast<T *>(s.thf);
+  p.u = static_cast<const T *>(s.u);
+  p.nx = m->nx;
+  p.ny = m->ny;
+  p.nz = m->nz;
+  p.act_x = m->act[0];
+  p.act_y = m->act[1];
+  p.act_z = m->act[2];
+  p.ux_off = m->u_off[0];
+  p.uy_off = m->u_off[1];
+  p.uz_off = m->u_off[2];
+  p.plane = (long long)m->nx * m->ny;
+  // R = sum_axis (A/V) (phi_minus - phi_plus); A/V = 1/h_axis
+  const double sc = (s.seed == SEED_APPLY) ? 1.0 : s.b * s.dt;
+  p.cx = (T)(sc / m->hx);
+  p.cy = (T)(sc / m->hy);
+  p.cz = (T)(sc / m->hz);
+  p.a = (T)s.a;
+  p.b = (T)s.b;
+  p.tiles_x = (m->nx + TX - 1) / TX;
+  p.tiles_y = (m->ny + 7) / 8;
+  // z chunks: enough CTAs to fill the GPU several times over
+  const long long cols = (long long)p.tiles_x * p.tiles_y;
+  int zchunk = m->nz;
+  const long long want = 152LL * 12;
+  if (cols < want && m->nz > 1) {
+    long long nch = (want + cols - 1) / cols;
+    if (nch > m->nz) nch = m->nz;
+    zchunk = (int)((m->nz + nch - 1) / nch);
+    if (zchunk < 8 && m->nz >= 8) zchunk = 8;
+  }
+  p.zchunk = zchunk;
+  const int tz = (m->nz + zchunk - 1) / zchunk;
+  switch (s.seed) {
+    case SEED_PLAIN: return dispatch_lim<T, SEED_PLAIN>(lim, p, tz, st);
+    case SEED_COMBINE: return dispatch_lim<T, SEED_COMBINE>(lim, p, tz, st);
+    default: return dispatch_lim<T, SEED_APPLY>(lim, p, tz, st);
+  }
+}
+
+// -------------------------------------------------------------------------
+// 1D resident kernel: one CTA keeps a whole periodic line in shared memory
+// and runs every step and stage of the rollout in one launch.
+template <class T, int LIM>
+__global__ void __launch_bounds__(1024) k_line_resident(T *theta, const T *u, int n, int64_t nsteps,
+                                                        int rk, T c) {
+  using F = FT<T>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *s_x = reinterpret_cast<T *>(smem);  // stage input / output
+  T *s_n = s_x + n;                      // theta^n
+  T *s_d = s_n + n;                      // Delta_m = x_{m+1} - x_m
+  T *s_f = s_d + n;                      // flux of face m+1/2
+  T *s_u = s_f + n;
+  const int nt = blockDim.x;
+  for (int i = threadIdx.x; i < n; i += nt) {
+    s_x[i] = theta[i];
+    s_u[i] = u[i];
+  }
+  __syncthreads();
+  const int ns = (rk == 3) ? 3 : 1;
+  for (int64_t step = 0; step < nsteps; ++step) {
+    if (ns == 3)
+      for (int i = threadIdx.x; i < n; i += nt) s_n[i] = s_x[i];
+    for (int st = 0; st < ns; ++st) {
+      for (int i = threadIdx.x; i < n; i += nt) {
+        const int ip = (i + 1 == n) ? 0 : i + 1;
+        s_d[i] = F::sub(s_x[ip], s_x[i]);
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += nt) {
+        const int ip = (i + 1 == n) ? 0 : i + 1;
+        const int im = (i == 0) ? n - 1 : i - 1;
+        const T uf = s_u[i];
+        const bool sp = upwind_positive(uf);
+        const T thf = limited_face<T, LIM>(sp ? s_x[i] : s_x[ip], s_d[i], sp ? s_d[im] : s_d[ip], sp);
+        s_f[i] = face_flux(uf, thf);
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += nt) {
+        const int im = (i == 0) ? n - 1 : i - 1;
+        T acc;
+        if (ns == 1 || st == 0) {
+          acc = s_x[i];
+          acc = F::fma(-c, s_f[i], acc);
+          acc = F::fma(c, s_f[im], acc);
+        } else {
+          const T a = (st == 1) ? T(0.75) : T(1.0 / 3.0);
+          const T b = (st == 1) ? T(0.25) : T(2.0 / 3.0);
+          const T cb = (st == 1) ? F::mul(T(0.25), c) : F::mul(T(2.0 / 3.0), c);
+          acc = F::fma(a, s_n[i], F::mul(b, s_x[i]));
+          acc = F::fma(-cb, s_f[i], acc);
+          acc = F::fma(cb, s_f[im], acc);
+        }
+        s_x[i] = acc;  // every read of s_x in this stage happened before the last barrier
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += nt) theta[i] = s_x[i];
+}
+
+template <class T>
+cudaError_t run_line_t(int lim, void *theta, const void *u, int n, int64_t nsteps, int rk, double c,
+                       cudaStream_t st) {
+  const size_t smem = 5 * sizeof(T) * (size_t)n;
+  const int threads = n >= 1024 ? 1024 : ((n + 31) / 32) * 32;
+  T *th = static_cast<T *>(theta);
+  const T *uu = static_cast<const T *>(u);
+#define FL_LINE_CASE(L)                                                                        \
+  case L: {                                                                                    \
+    auto k = k_line_resident<T, L>;                                                            \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                         (int)smem);                                           \
+    if (e != cudaSuccess) return e;                                                            \
+    k<<<1, threads, smem, st>>>(th, uu, n, nsteps, rk, (T)c);                                  \
+    return cudaGetLastError();                                                                 \
+  }
+  switch (lim) {
+    FL_LINE_CASE(LIM_UPWIND)
+    FL_LINE_CASE(LIM_CENTRAL)
+    FL_LINE_CASE(LIM_MINMOD)
+    FL_LINE_CASE(LIM_VANLEER)
+    FL_LINE_CASE(LIM_SUPERBEE)
+    FL_LINE_CASE(LIM_SMART)
+  }
+#undef FL_LINE_CASE
+  return cudaErrorInvalidValue;
+}
+
+// -------------------------------------------------------------------------
+// Upwind selection dump: (s, C, D, U) per face in the user layout.
+template <class T>
+__global__ void k_struct_selection(const T *u, int4 *sel, int nx, int ny, int nz, int a0, int a1,
+                                   int a2, long long C) {
+  const long long nf = C * (a0 + a1 + a2);
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int blk = (int)(f / C);
+    const long long c = f - (long long)blk * C;
+    // the blk-th axis of extent > 1
+    const int act[3] = {a0, a1, a2};
+    int axis = 0;
+    for (int q = 0, seen = -1; q < 3; ++q) {
+      if (act[q] && ++seen == blk) {
+        axis = q;
+        break;
+      }
+    }
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    int d[3] = {0, 0, 0};
+    d[axis] = 1;
+    auto cell = [&](int di) -> int {
+      const int ii = (i + di * d[0] + 4 * nx) % nx;
+      const int jj = (j + di * d[1] + 4 * ny) % ny;
+      const int kk = (k + di * d[2] + 4 * nz) % nz;
+      return ii + nx * (jj + ny * kk);
+    };
+    const bool sp = upwind_positive(u[f]);
+    const int c0 = cell(0), c1 = cell(1);
+    int4 o;
+    o.x = sp ? 1 : -1;
+    o.y = sp ? c0 : c1;
+    o.z = sp ? c1 : c0;
+    o.w = sp ? cell(-1) : cell(2);
+    sel[f] = o;
+  }
+}
+
+}  // namespace
+
+cudaError_t struct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs &s, cudaStream_t st) {
+  return dt == FL_F64 ? run_stage_t<double>(m, lim, s, st) : run_stage_t<float>(m, lim, s, st);
+}
+
+size_t line_resident_max_cells(fl_dtype dt) {
+  // five arrays in (at most) 200 KiB of shared memory
+  return (200u * 1024u) / (5u * dsize(dt));
+}
+
+cudaError_t line_resident(const fl_mesh *m, int lim, fl_dtype dt, void *theta, const void *u,
+                          int64_t nsteps, int rk, double dtime, cudaStream_t st) {
+  const double c = dtime / m->hx;
+  return dt == FL_F64 ? run_line_t<double>(lim, theta, u, m->nx, nsteps, rk, c, st)
+                      : run_line_t<float>(lim, theta, u, m->nx, nsteps, rk, c, st);
+}
+
+cudaError_t struct_selection(const fl_mesh *m, fl_dtype dt, const void *u, int32_t *sel,
+                             cudaStream_t st) {
+  const long long nf = m->F;
+  if (nf == 0) return cudaSuccess;
+  const int threads = 256;
+  const long long blocks = (nf + threads - 1) / threads;
+  const unsigned g = (unsigned)(blocks > 65535 * 16 ? 65535 * 16 : blocks);
+  if (dt == FL_F64)
+    k_struct_selection<double><<<g, threads, 0, st>>>(static_cast<const double *>(u),
+                                                      reinterpret_cast<int4 *>(sel), m->nx, m->ny,
+                                                      m->nz, m->act[0], m->act[1], m->act[2], m->C);
+  else
+    k_struct_selection<float><<<g, threads, 0, st>>>(static_cast<const float *>(u),
+                                                     reinterpret_cast<int4 *>(sel), m->nx, m->ny,
+                                                     m->nz, m->act[0], m->act[1], m->act[2], m->C);
+  return cudaGetLastError();
+}
+
+}  // namespace fl

@@ -1,0 +1,22 @@
+// fl_unstructured.h -- face-based (renumbered) meshes: host build and kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fl_internal.h"
+
+namespace fl {
+
+fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const double *normals,
+                          const double *areas, const double *volumes, unsigned flags,
+                          fl_mesh **out);
+void unstruct_free(fl_mesh *m);
+fl_status unstruct_apply(const fl_mesh *m, int lim, fl_dtype dt, const void *theta, const void *u,
+                         void *rhs, void *thf, cudaStream_t st);
+fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
+                        int64_t nsteps, void *theta, const void *u, void *ws, cudaStream_t st);
+cudaError_t unstruct_selection(const fl_mesh *m, fl_dtype dt, const void *u, int32_t *sel,
+                               cudaStream_t st);
+const double *unstruct_volumes(const fl_mesh *m);
+
+}  // namespace fl

@@ -29,3 +29,29 @@ def load_golden_matrix(name):
 @pytest.fixture(scope="session")
 def golden():
     return load_golden_matrix
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def pytest_collection_modifyitems(config, items):
+    if _cuda_ok():
+        return
+    skip = pytest.mark.skip(reason="no CUDA device in this environment")
+    for it in items:
+        if "gpu" in it.keywords:
+            it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def fl():
+    """The CUDA library binding, built in-tree (build is a no-op when fresh)."""
+    import paper_2110_03044_gb300 as lib
+    lib.build()
+    lib.lib()
+    return lib
