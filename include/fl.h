@@ -165,6 +165,26 @@ fl_status fl_step_rk(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype, in
                      size_t workspace_bytes, void *stream);
 
 /*
+ * fl_step_rk without a workspace argument, for callers that may not allocate
+ * device memory at all (plugin hosts that own the whole device memory pool,
+ * real-time loops that cannot pay for an allocation's device-wide
+ * synchronisation, deployments whose memory is fixed at start-up).  The paper
+ * has no counterpart: this is a deployment convenience of the library.
+ * Same arguments and results as fl_step_rk; the stage buffers come from a
+ * fixed area inside the library image of FL_NOALLOC_SCRATCH_BYTES per GPU,
+ * held by every GPU that loads the library until the process exits.  Meshes
+ * whose fl_workspace_size exceeds that return FL_EINVAL and nothing runs.
+ * The first call on each device looks up the area's device address, so make
+ * it before any stream capture.  All calls share the area: calls whose GPU
+ * work overlaps in time race and must be ordered by the caller.  The call
+ * allocates nothing (no cudaMalloc, no library allocator).
+ */
+#define FL_NOALLOC_SCRATCH_BYTES (32u << 20)
+fl_status fl_step_rk_noalloc(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                             int rk_order, double dt, int64_t nsteps, void *theta,
+                             const void *u_f, void *stream);
+
+/*
  * Transpose of the Jacobian of R at theta_c applied to lambda_rhs:
  *   lambda_theta = (dR/dtheta)^T lambda_rhs     [n_cells] device.
  * The limiter derivative is taken on the branch selected by strict ordered

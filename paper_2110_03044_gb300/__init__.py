@@ -32,7 +32,8 @@ FL_RENUMBER = 1
 ABI_SYMBOLS = [
     "fl_last_error", "fl_version", "fl_mesh_create_structured", "fl_mesh_create",
     "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_destroy", "fl_conv_limited_apply",
-    "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_conv_limited_adjoint",
+    "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_noalloc",
+    "fl_conv_limited_adjoint",
     "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_batch_create",
     "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_destroy",
     "fl_reduce_workspace_size", "fl_reduce_max_abs", "fl_reduce_mass",
@@ -84,6 +85,7 @@ def lib():
             "fl_face_selection": (I, [P, I, P, P, P]),
             "fl_workspace_size": (I, [P, I, I, ctypes.POINTER(SZ)]),
             "fl_step_rk": (I, [P, I, I, I, D, I64, P, P, P, SZ, P]),
+            "fl_step_rk_noalloc": (I, [P, I, I, I, D, I64, P, P, P]),
             "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
             "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
             "fl_step_rk_adjoint": (I, [P, I, I, I, D, I64, I64, P, P, P, P, P, SZ, P]),
@@ -213,6 +215,14 @@ def fl_step_rk(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, workspace
     _check(lib().fl_step_rk(mesh, _lim(limiter), dtype_code(dtype), int(rk_order), float(dt),
                             int(nsteps), _ptr(theta), _ptr(u_f), _ptr(workspace),
                             int(workspace_bytes), _stream(stream)))
+
+
+def fl_step_rk_noalloc(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, stream=None):
+    """fl_step_rk for callers that cannot allocate device memory: the stage
+    buffers come from the library's built-in scratch area (see fl.h)."""
+    _check(lib().fl_step_rk_noalloc(mesh, _lim(limiter), dtype_code(dtype), int(rk_order),
+                                    float(dt), int(nsteps), _ptr(theta), _ptr(u_f),
+                                    _stream(stream)))
 
 
 def fl_conv_limited_adjoint(mesh, limiter, dtype, theta_c, u_f, lambda_rhs, lambda_theta,
