@@ -26,6 +26,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -298,6 +300,194 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_config_1d(args):
+    """1D periodic advection, 1000 cells, van Leer, forward Euler, 1000 steps
+    in one launch of the resident line kernel."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    import workloads as W
+    fl.build()
+    wl = W.config_1d()
+    m = fl.Mesh.structured(1000, 1, 1, *wl.mesh.h)
+    u = torch.tensor(wl.u, device="cuda")
+    th = torch.tensor(wl.theta0, device="cuda")
+    for _ in range(args.warmup):
+        fl.step_rk(m, "vanleer", th.clone(), u, wl.dt, 1000, rk_order=1)
+    e0, e1 = _events()
+    g = th.clone()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        g.copy_(th)
+        fl.step_rk(m, "vanleer", g, u, wl.dt, 1000, rk_order=1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"metric": "1D rollout face-updates/s (1000 Euler steps, one launch)",
+            "value": 1000 * 1000 / (ms * 1e-3), "unit": "face-updates/s", "ms_per_rollout": ms,
+            "dtype": "f64", "config": {"workload": "1d_n1000_vanleer_euler_1000steps"}}
+
+
+def run_config_unstructured(args):
+    """256^3 hex mesh in seeded random cell/face order with half of the faces
+    reoriented (face-cell incidence as int32 pairs), renumbered by the
+    library; SMART, SSP-RK3, FP64."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    import workloads as W
+    fl.build()
+    n = args.n
+    wl = W.config_taylor_green(n=n, seed=1, nsteps=50, limiter="smart")
+    pm, cp, fp, flip = W.permuted_mesh(wl.mesh, seed=2)
+    up = W.permute_face_field(wl.u, fp, flip)
+    thp = W.permute_cell_field(wl.theta0, cp)
+    t0 = time.perf_counter()
+    m = fl.Mesh.from_faces(pm.n_cells, pm.face_cells, pm.normals, pm.areas, pm.volumes,
+                           renumber=True)
+    t_mesh = time.perf_counter() - t0
+    icp, ifp, _ = m.permutation()
+    th_i = np.empty_like(thp)
+    th_i[icp] = thp
+    u_i = np.empty_like(up)
+    u_i[ifp] = up
+    th = torch.tensor(th_i, device="cuda")
+    u = torch.tensor(u_i, device="cuda")
+    nb = fl.fl_workspace_size(m.handle, torch.float64, 3)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        fl.fl_step_rk(m.handle, "smart", torch.float64, 3, wl.dt, 1, th, u, ws, nb)
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    e0.record()
+    fl.fl_step_rk(m.handle, "smart", torch.float64, 3, wl.dt, args.steps, th, u, ws, nb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    C, F = pm.n_cells, pm.n_faces
+    return {"metric": "limited-convection face-updates/s (unstructured storage, SSP-RK3)",
+            "value": F * 3 / (ms * 1e-3), "unit": "face-updates/s", "ms_per_step": ms,
+            "dtype": "f64", "mesh_create_s": t_mesh,
+            "config": {"workload": "hex%d^3_permuted_flipped_smart_ssprk3" % n, "cells": C,
+                       "faces": F}}
+
+
+def run_config_batched(args):
+    """64 periodic boxes, sizes seeded in [32, 128]^3, each with its own
+    solenoidal velocity and scalar, van Leer, SSP-RK3: one persistent launch
+    per stage (graph-replayed) against 64 single-mesh launches per stage
+    captured in one CUDA graph."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    import workloads as W
+    fl.build()
+    dims = W.batched_box_dims()
+    boxes = [W.random_box(d, 1000 + i) for i, d in enumerate(dims)]
+    out = {}
+    for dname, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        meshes = [fl.Mesh.structured(*d, *b[0].h) for d, b in zip(dims, boxes)]
+        batch = fl.fl_batch_create([mm.handle for mm in meshes])
+        th = [torch.tensor(b[1], dtype=dt, device="cuda") for b in boxes]
+        us = [torch.tensor(b[2], dtype=dt, device="cuda") for b in boxes]
+        dts = [b[3] for b in boxes]
+        nb = fl.fl_batch_workspace_size(batch, dt, 3)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        fl.fl_batch_step_rk(batch, "vanleer", dt, 3, dts, 2, th, us, ws, nb)  # tunes once
+        e0, e1 = _events()
+        torch.cuda.synchronize()
+        e0.record()
+        fl.fl_batch_step_rk(batch, "vanleer", dt, 3, dts, args.steps, th, us, ws, nb)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1) / args.steps
+        # separate launches: one fl_step_rk per box and step, captured in a graph
+        wss = [torch.empty(fl.fl_workspace_size(mm.handle, dt, 3), dtype=torch.uint8,
+                           device="cuda") for mm in meshes]
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for mm, t, u, d, w in zip(meshes, th, us, dts, wss):
+                fl.fl_step_rk(mm.handle, "vanleer", dt, 3, d, 1, t, u, w, w.numel(), s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for mm, t, u, d, w in zip(meshes, th, us, dts, wss):
+                fl.fl_step_rk(mm.handle, "vanleer", dt, 3, d, 1, t, u, w, w.numel(), s)
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1) / args.steps
+        F = sum(mm.n_faces for mm in meshes)
+        out[dname] = {"batched_ms_per_step": ms_b, "separate_ms_per_step": ms_s,
+                      "batched_face_updates_per_s": F * 3 / (ms_b * 1e-3),
+                      "separate_face_updates_per_s": F * 3 / (ms_s * 1e-3),
+                      "speedup": ms_s / ms_b}
+        fl.fl_batch_destroy(batch)
+        for mm in meshes:
+            mm.close()
+    C = sum(int(np.prod(d)) for d in dims)
+    return {"metric": "batched limited-convection face-updates/s (64 boxes, SSP-RK3)",
+            "value": out["f64"]["batched_face_updates_per_s"], "unit": "face-updates/s",
+            "dtype": "f64", "results": out,
+            "config": {"workload": "64_boxes_32-128_vanleer_ssprk3", "cells": C}}
+
+
+def run_config_adjoint(args):
+    """128^3 Taylor-Green, superbee, 200 SSP-RK3 steps, checkpoints every 20:
+    reverse sweep time (recomputation + adjoint stages) against the forward
+    rollout."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    import workloads as W
+    fl.build()
+    n, nsteps, every = 128, 200, 20
+    wl = W.config_taylor_green(n=n, seed=4, nsteps=nsteps, limiter="superbee")
+    tgt = W.smooth_target(wl.mesh.dims, wl.mesh.h, 4)
+    m = fl.Mesh.structured(n, n, n, *wl.mesh.h)
+    u = torch.tensor(wl.u, device="cuda")
+    th0 = torch.tensor(wl.theta0, device="cuda")
+    tg = torch.tensor(tgt, device="cuda")
+    wsf = torch.empty(fl.fl_workspace_size(m.handle, torch.float64, 3), dtype=torch.uint8,
+                      device="cuda")
+    nb = fl.fl_adjoint_workspace_size(m.handle, torch.float64, 3, nsteps, every)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    g = torch.empty_like(th0)
+    e0, e1 = _events()
+    fwd, rev = [], []
+    for rep in range(max(2, args.warmup)):
+        th = th0.clone()
+        torch.cuda.synchronize()
+        e0.record()
+        fl.fl_step_rk(m.handle, "superbee", torch.float64, 3, wl.dt, nsteps, th, u, wsf, wsf.numel())
+        e1.record()
+        torch.cuda.synchronize()
+        fwd.append(e0.elapsed_time(e1))
+        lam = th - tg
+        torch.cuda.synchronize()
+        e0.record()
+        fl.fl_step_rk_adjoint(m.handle, "superbee", torch.float64, 3, wl.dt, nsteps, every, th0, u,
+                              lam, g, ws, nb)
+        e1.record()
+        torch.cuda.synchronize()
+        rev.append(e0.elapsed_time(e1))
+    f, r = min(fwd[1:]), min(rev[1:])
+    return {"metric": "adjoint / forward time (128^3, 200 SSP-RK3 steps, checkpoints every 20)",
+            "value": r / f, "unit": "ratio", "higher_is_better": False, "forward_ms": f,
+            "reverse_ms": r, "dtype": "f64",
+            "config": {"workload": "tg128_superbee_ssprk3_200steps_ckpt20"}}
+
+
 def cpu_baseline(wl, lim, budget_s):
     """The oracle as it stands on the host cores: one SSP-RK3 stage of the
     same mesh and fields (all cells), repeated while within budget."""
@@ -370,11 +560,18 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")
+    ap.add_argument("--config", default="tg256",
+                    choices=["tg256", "1d", "unstructured", "batched", "adjoint"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.config == "tg256":
         run_ours(args)
+    else:
+        import numpy  # noqa: F401  (the config runners use np)
+        fn = {"1d": run_config_1d, "unstructured": run_config_unstructured,
+              "batched": run_config_batched, "adjoint": run_config_adjoint}[args.config]
+        print(json.dumps(fn(args)))
 
 
 if __name__ == "__main__":

@@ -131,6 +131,13 @@ fl_status fl_mesh_permutation(const fl_mesh *mesh, int32_t *cell_perm, int32_t *
 /* Sizes of a mesh: cells, faces, kind (0 structured, 1 unstructured). */
 fl_status fl_mesh_info(const fl_mesh *mesh, int64_t *n_cells, int64_t *n_faces, int *kind);
 
+/*
+ * Device-side status of the kernels run on this mesh: synchronises the
+ * stream, returns FL_ETIMEOUT (a bounded wait inside a kernel gave up) or
+ * FL_EINDEX if one was recorded since the last call, and clears it.
+ */
+fl_status fl_mesh_status(const fl_mesh *mesh, void *stream);
+
 fl_status fl_mesh_destroy(fl_mesh *mesh);
 
 /*

@@ -31,7 +31,8 @@ FL_RENUMBER = 1
 # Exported symbols of include/fl.h (checked by the ABI test).
 ABI_SYMBOLS = [
     "fl_last_error", "fl_version", "fl_mesh_create_structured", "fl_mesh_create",
-    "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_destroy", "fl_conv_limited_apply",
+    "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_status", "fl_mesh_destroy",
+    "fl_conv_limited_apply",
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_noalloc",
     "fl_conv_limited_adjoint",
     "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_batch_create",
@@ -80,6 +81,7 @@ def lib():
             "fl_mesh_permutation": (I, [P, P, P, P]),
             "fl_mesh_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                  ctypes.POINTER(I)]),
+            "fl_mesh_status": (I, [P, P]),
             "fl_mesh_destroy": (I, [P]),
             "fl_conv_limited_apply": (I, [P, I, I, P, P, P, P, P]),
             "fl_face_selection": (I, [P, I, P, P, P]),
@@ -188,6 +190,11 @@ def fl_mesh_info(mesh):
     c, f, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
     _check(lib().fl_mesh_info(mesh, ctypes.byref(c), ctypes.byref(f), ctypes.byref(k)))
     return c.value, f.value, k.value
+
+
+def fl_mesh_status(mesh, stream=None):
+    """Raise if a kernel on this mesh recorded a device-side error (syncs)."""
+    _check(lib().fl_mesh_status(mesh, _stream(stream)))
 
 
 def fl_mesh_destroy(mesh):

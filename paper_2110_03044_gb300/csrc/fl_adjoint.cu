@@ -1,0 +1,505 @@
+// fl_adjoint.cu -- adjoint (transpose Jacobian) of the limited-convection
+// stage on periodic Cartesian meshes, and the checkpointed reverse sweep of
+// an Euler / SSP-RK3 rollout.
+//
+// The forward face value, linearised on the branch the forward evaluation
+// takes (limited_face_lin, same bit-pattern tests as limited_face), is
+//   theta_f ~ theta_C + s (alpha Delta_m + beta Delta_up)
+// so a face m+1/2 with adjoint weight g = (A/V) u_f (mu_{m+1} - mu_m) -- the
+// derivative of sum_c mu_c R_c with respect to its flux -- hands
+//   s > 0 (C = m, up face m-1):  -beta g to m-1, (1-alpha+beta) g to m, alpha g to m+1
+//   s < 0 (C = m+1, up face m+1): alpha g to m, (1-alpha+beta) g to m+1, -beta g to m+2
+// Every cell therefore gathers from four faces per axis (m = i-2 .. i+1).
+// The kernel mirrors the forward one: a 32 x 8 column per CTA streams through
+// z; theta (3-cell halo) and mu (2-cell halo) of the current plane sit in
+// shared memory; per-face data (g, alpha, beta, 1-alpha+beta, s) is computed
+// once per face in shared memory (z faces in registers) and gathered.
+//
+// Stage adjoint (RK stage y = a thn + b (x + dt R(x))):
+//   out = e1 v1 + e2 v2 + b mu + b dt R'(x)^T mu      (v1, v2 pointwise)
+// fl_conv_limited_adjoint is the bare out = R'(x)^T mu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fl_face.cuh"
+#include "fl_internal.h"
+#include "fl_kernels.h"
+
+namespace fl {
+
+fl_status check_buffer(const void *p, size_t bytes, const char *name);
+fl_status check_mesh(const fl_mesh *m);
+fl_status check_enums(int lim, fl_dtype dt);
+
+namespace {
+
+constexpr int TX = 32;
+constexpr int TY = 8;
+
+template <class T>
+struct AParams {
+  const T *x;    // forward stage input (theta)
+  const T *mu;   // adjoint of the stage output
+  const T *v1;   // optional pointwise terms
+  const T *v2;
+  T *out;        // may alias v1 / v2 (own cell only), never x or mu
+  const T *u;
+  int nx, ny, nz;
+  int act_x, act_y, act_z;
+  long long ux_off, uy_off, uz_off;
+  long long plane;
+  T cx, cy, cz;  // A/V per axis
+  T e1, e2, b, bdt;
+  int bare;      // 1: out = R'^T mu only
+  int tiles_x, tiles_y, zchunk;
+};
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+template <class T>
+struct FaceAdj {
+  T g, al, be, c1;
+  bool sp;
+};
+
+template <class T, int LIM>
+__device__ __forceinline__ FaceAdj<T> face_adj(T u, T a, T dm1, T dp1, T mu0, T mu1, T c) {
+  using F = FT<T>;
+  FaceAdj<T> r;
+  r.sp = upwind_positive(u);
+  limited_face_lin<T, LIM>(a, r.sp ? dm1 : dp1, r.al, r.be);
+  r.g = F::mul(F::mul(c, u), F::sub(mu1, mu0));
+  r.c1 = F::add(F::sub(T(1), r.al), r.be);
+  return r;
+}
+
+// contribution of the four faces m = i-2 .. i+1 of an axis to cell i
+template <class T>
+__device__ __forceinline__ T gather4(T acc, const FaceAdj<T> &fm2, const FaceAdj<T> &fm1,
+                                     const FaceAdj<T> &f0, const FaceAdj<T> &fp1) {
+  using F = FT<T>;
+  acc = F::fma(f0.sp ? f0.c1 : f0.al, f0.g, acc);     // face i   (cell i is m)
+  acc = F::fma(fm1.sp ? fm1.al : fm1.c1, fm1.g, acc);  // face i-1 (cell i is m+1)
+  if (fp1.sp) acc = F::fma(-fp1.be, fp1.g, acc);       // face i+1, s > 0: cell i is m-1
+  if (!fm2.sp) acc = F::fma(-fm2.be, fm2.g, acc);      // face i-2, s < 0: cell i is m+2
+  return acc;
+}
+
+template <class T, int LIM>
+__global__ void __launch_bounds__(TX *TY) k_struct_adjoint(const AParams<T> p) {
+  using F = FT<T>;
+  constexpr int NT = TX * TY;
+  constexpr int SWT = TX + 6;  // theta row pitch (halo 3)
+  constexpr int SWM = TX + 4;  // mu row pitch (halo 2)
+  constexpr int NXF = TX + 3;  // x faces per row: m = x0-2 .. x0+TX
+  constexpr int NYF = TY + 3;  // y faces per column: m = y0-2 .. y0+TY
+  __shared__ T s_th[(TY + 6) * SWT];
+  __shared__ T s_mu[(TY + 4) * SWM];
+  __shared__ T s_dx[TY * (TX + 5)];  // Delta of x faces x0-3 .. x0+TX+1
+  __shared__ T s_dy[(TY + 5) * TX];  // Delta of y faces y0-3 .. y0+TY+1
+  __shared__ FaceAdj<T> s_fx[TY * NXF];
+  __shared__ FaceAdj<T> s_fy[NYF * TX];
+  __shared__ int s_wx[TX + 6];
+  __shared__ int s_wy[TY + 6];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  int bid = blockIdx.x;
+  const int bx = bid % p.tiles_x;
+  bid /= p.tiles_x;
+  const int by = bid % p.tiles_y;
+  const int bz = bid / p.tiles_y;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int z0 = bz * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  if (tid < TX + 6) s_wx[tid] = wrapi(x0 - 3 + tid, nx);
+  if (tid < TY + 6) s_wy[tid] = wrapi(y0 - 3 + tid, ny);
+  __syncthreads();
+  const bool valid = (x0 + tx < nx) && (y0 + ty < ny);
+  // wrap table index w <-> coordinate x0-3+w
+  const long long col = (long long)s_wx[tx + 3] + (long long)nx * s_wy[ty + 3];
+
+  // halo cells: theta 3 wide (6 per row, 6 rows), mu 2 wide
+  int th_slot = -1, mu_slot = -1;
+  long long th_off = 0, mu_off = 0;
+  {
+    constexpr int NHX = 6 * TY, NHT = NHX + 6 * TX;
+    static_assert(NHT <= NT, "theta halo exceeds threads");
+    if (tid < NHX) {
+      const int r = tid / 6, k6 = tid % 6;
+      const int c = (k6 < 3) ? k6 : (TX + k6);  // 0,1,2, TX+3,TX+4,TX+5
+      th_slot = (r + 3) * SWT + c;
+      th_off = (long long)s_wx[c] + (long long)nx * s_wy[r + 3];
+    } else if (tid < NHT) {
+      const int t = tid - NHX;
+      const int k6 = t / TX, c = t % TX;
+      const int r = (k6 < 3) ? k6 : (TY + k6);
+      th_slot = r * SWT + c + 3;
+      th_off = (long long)s_wx[c + 3] + (long long)nx * s_wy[r];
+    }
+    constexpr int NMX = 4 * TY, NMT = NMX + 4 * TX;
+    static_assert(NMT <= NT, "mu halo exceeds threads");
+    if (tid < NMX) {
+      const int r = tid >> 2, k4 = tid & 3;
+      const int c = (k4 < 2) ? k4 : (TX + k4);  // mu columns 0,1,TX+2,TX+3
+      mu_slot = (r + 2) * SWM + c;
+      mu_off = (long long)s_wx[c + 1] + (long long)nx * s_wy[r + 3];
+    } else if (tid < NMT) {
+      const int t = tid - NMX;
+      const int k4 = t / TX, c = t % TX;
+      const int r = (k4 < 2) ? k4 : (TY + k4);
+      mu_slot = r * SWM + c + 2;
+      mu_off = (long long)s_wx[c + 3] + (long long)nx * s_wy[r + 1];
+    }
+  }
+  const bool need_x = p.act_x, need_y = p.act_y, need_z = p.act_z;
+
+  // ---- z prologue: faces z0-2, z0-1, z0 and the column window
+  T th_k, th_k1, th_k2, d_k = T(0), d_k1 = T(0), mu_k, mu_k1 = T(0);
+  FaceAdj<T> zf_m2{}, zf_m1{}, zf_0{};
+  auto X = [&](int k) { return p.x[col + p.plane * wrapi(k, nz)]; };
+  auto MU = [&](int k) { return p.mu[col + p.plane * wrapi(k, nz)]; };
+  if (need_z) {
+    const T tm3 = X(z0 - 3), tm2 = X(z0 - 2), tm1 = X(z0 - 1);
+    th_k = X(z0);
+    th_k1 = X(z0 + 1);
+    th_k2 = X(z0 + 2);
+    const T dm3 = F::sub(tm2, tm3), dm2 = F::sub(tm1, tm2), dm1 = F::sub(th_k, tm1);
+    d_k = F::sub(th_k1, th_k);
+    d_k1 = F::sub(th_k2, th_k1);
+    const T mm2 = MU(z0 - 2), mm1 = MU(z0 - 1);
+    mu_k = MU(z0);
+    mu_k1 = MU(z0 + 1);
+    const T *uz = p.u + p.uz_off + col;
+    zf_m2 = face_adj<T, LIM>(uz[p.plane * wrapi(z0 - 2, nz)], dm2, dm3, dm1, mm2, mm1, p.cz);
+    zf_m1 = face_adj<T, LIM>(uz[p.plane * wrapi(z0 - 1, nz)], dm1, dm2, d_k, mm1, mu_k, p.cz);
+    zf_0 = face_adj<T, LIM>(uz[p.plane * z0], d_k, dm1, d_k1, mu_k, mu_k1, p.cz);
+  } else {
+    th_k = th_k1 = th_k2 = p.x[col];
+    mu_k = p.mu[col];
+  }
+
+  for (int k = z0; k < z1; ++k) {
+    const long long pk = p.plane * k;
+    T th_k3 = T(0), mu_k2 = T(0), uz1 = T(0);
+    if (need_z) {
+      th_k3 = X(k + 3);
+      mu_k2 = MU(k + 2);
+      uz1 = p.u[p.uz_off + col + p.plane * wrapi(k + 1, nz)];
+    }
+    const T hv_t = (th_slot >= 0) ? p.x[th_off + pk] : T(0);
+    const T hv_m = (mu_slot >= 0) ? p.mu[mu_off + pk] : T(0);
+    T v1 = T(0), v2 = T(0);
+    if (!p.bare && valid) {
+      if (p.v1) v1 = p.v1[col + pk];
+      if (p.v2) v2 = p.v2[col + pk];
+    }
+    s_th[(ty + 3) * SWT + tx + 3] = th_k;
+    s_mu[(ty + 2) * SWM + tx + 2] = mu_k;
+    if (th_slot >= 0) s_th[th_slot] = hv_t;
+    if (mu_slot >= 0) s_mu[mu_slot] = hv_m;
+    __syncthreads();
+    // ---------------------------------------------- differences
+    if (need_x) {
+      for (int it = tid; it < TY * (TX + 5); it += NT) {
+        const int r = it / (TX + 5), q = it - r * (TX + 5);  // face x0-3+q
+        const T *row = &s_th[(r + 3) * SWT];
+        s_dx[it] = F::sub(row[q + 1], row[q]);
+      }
+    }
+    if (need_y) {
+      for (int it = tid; it < (TY + 5) * TX; it += NT) {
+        const int r = it / TX, c = it - r * TX;  // face y0-3+r
+        s_dy[it] = F::sub(s_th[(r + 1) * SWT + c + 3], s_th[r * SWT + c + 3]);
+      }
+    }
+    T d_k2 = T(0);
+    if (need_z) d_k2 = F::sub(th_k3, th_k2);
+    __syncthreads();
+    // ---------------------------------------------- face data
+    if (need_x) {
+      for (int it = tid; it < TY * NXF; it += NT) {
+        const int r = it / NXF, q = it - r * NXF;  // face m = x0-2+q
+        const T uf = p.u[p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 3] + pk];
+        const T *dr = &s_dx[r * (TX + 5)];  // Delta_m at q+1
+        const T *mr = &s_mu[(r + 2) * SWM];  // mu_m at column q
+        s_fx[it] = face_adj<T, LIM>(uf, dr[q + 1], dr[q], dr[q + 2], mr[q], mr[q + 1], p.cx);
+      }
+    }
+    if (need_y) {
+      for (int it = tid; it < NYF * TX; it += NT) {
+        const int r = it / TX, c = it - r * TX;  // face m = y0-2+r
+        const T uf = p.u[p.uy_off + s_wx[c + 3] + (long long)nx * s_wy[r + 1] + pk];
+        s_fy[it] = face_adj<T, LIM>(uf, s_dy[(r + 1) * TX + c], s_dy[r * TX + c],
+                                    s_dy[(r + 2) * TX + c], s_mu[r * SWM + c + 2],
+                                    s_mu[(r + 1) * SWM + c + 2], p.cy);
+      }
+    }
+    FaceAdj<T> zf_1{};
+    if (need_z) zf_1 = face_adj<T, LIM>(uz1, d_k1, d_k, d_k2, mu_k1, mu_k2, p.cz);
+    __syncthreads();
+    // ---------------------------------------------- gather + combine
+    if (valid) {
+      T acc = T(0);
+      if (need_x) {
+        const FaceAdj<T> *fr = &s_fx[ty * NXF + tx];  // faces i-2 .. i+1
+        acc = gather4(acc, fr[0], fr[1], fr[2], fr[3]);
+      }
+      if (need_y) {
+        acc = gather4(acc, s_fy[ty * TX + tx], s_fy[(ty + 1) * TX + tx],
+                      s_fy[(ty + 2) * TX + tx], s_fy[(ty + 3) * TX + tx]);
+      }
+      if (need_z) acc = gather4(acc, zf_m2, zf_m1, zf_0, zf_1);
+      T o;
+      if (p.bare) {
+        o = acc;
+      } else {
+        o = F::fma(p.bdt, acc, F::mul(p.b, mu_k));
+        if (p.v1) o = F::fma(p.e1, v1, o);
+        if (p.v2) o = F::fma(p.e2, v2, o);
+      }
+      p.out[col + pk] = o;
+    }
+    // ---------------------------------------------- rotate
+    if (need_z) {
+      zf_m2 = zf_m1;
+      zf_m1 = zf_0;
+      zf_0 = zf_1;
+      th_k = th_k1;
+      th_k1 = th_k2;
+      th_k2 = th_k3;
+      d_k = d_k1;
+      d_k1 = d_k2;
+      mu_k = mu_k1;
+      mu_k1 = mu_k2;
+    } else if (k + 1 < z1) {
+      th_k = p.x[col + p.plane * (k + 1)];
+      mu_k = p.mu[col + p.plane * (k + 1)];
+    }
+  }
+}
+
+template <class T>
+cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t st) {
+  AParams<T> p;
+  p.x = static_cast<const T *>(s.x);
+  p.mu = static_cast<const T *>(s.mu);
+  p.v1 = static_cast<const T *>(s.v1);
+  p.v2 = static_cast<const T *>(s.v2);
+  p.out = static_cast<T *>(s.out);
+  p.u = static_cast<const T *>(s.u);
+  p.nx = m->nx;
+  p.ny = m->ny;
+  p.nz = m->nz;
+  p.act_x = m->act[0];
+  p.act_y = m->act[1];
+  p.act_z = m->act[2];
+  p.ux_off = m->u_off[0];
+  p.uy_off = m->u_off[1];
+  p.uz_off = m->u_off[2];
+  p.plane = (long long)m->nx * m->ny;
+  p.cx = (T)(1.0 / m->hx);
+  p.cy = (T)(1.0 / m->hy);
+  p.cz = (T)(1.0 / m->hz);
+  p.e1 = (T)s.e1;
+  p.e2 = (T)s.e2;
+  p.b = (T)s.b;
+  p.bdt = (T)(s.b * s.dt);
+  p.bare = s.bare;
+  p.tiles_x = (m->nx + TX - 1) / TX;
+  p.tiles_y = (m->ny + TY - 1) / TY;
+  const long long cols = (long long)p.tiles_x * p.tiles_y;
+  int zchunk = m->nz;
+  const long long want = 152LL * 8;
+  if (cols < want && m->nz > 1) {
+    long long nch = (want + cols - 1) / cols;
+    if (nch > m->nz) nch = m->nz;
+    zchunk = (int)((m->nz + nch - 1) / nch);
+    if (zchunk < 8 && m->nz >= 8) zchunk = 8;
+  }
+  p.zchunk = zchunk;
+  const int tz = (m->nz + zchunk - 1) / zchunk;
+  const unsigned grid = (unsigned)(cols * tz);
+  const dim3 block(TX, TY);
+  switch (lim) {
+    case LIM_UPWIND: k_struct_adjoint<T, LIM_UPWIND><<<grid, block, 0, st>>>(p); break;
+    case LIM_CENTRAL: k_struct_adjoint<T, LIM_CENTRAL><<<grid, block, 0, st>>>(p); break;
+    case LIM_MINMOD: k_struct_adjoint<T, LIM_MINMOD><<<grid, block, 0, st>>>(p); break;
+    case LIM_VANLEER: k_struct_adjoint<T, LIM_VANLEER><<<grid, block, 0, st>>>(p); break;
+    case LIM_SUPERBEE: k_struct_adjoint<T, LIM_SUPERBEE><<<grid, block, 0, st>>>(p); break;
+    case LIM_SMART: k_struct_adjoint<T, LIM_SMART><<<grid, block, 0, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t struct_adjoint(const fl_mesh *m, int lim, fl_dtype dt, const AdjArgs &s,
+                           cudaStream_t st) {
+  return dt == FL_F64 ? run_adj_t<double>(m, lim, s, st) : run_adj_t<float>(m, lim, s, st);
+}
+
+// ------------------------------------------------------------- host side
+size_t adjoint_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps, int64_t every) {
+  const size_t one = align256((size_t)m->C * dsize(dt));
+  const int S = (rk == 3) ? 3 : 1;
+  const int64_t nck = (nsteps + every - 1) / every;
+  const int64_t seg = (int64_t)S * every + 1;
+  return one * (size_t)(nck + seg + 3);
+}
+
+}  // namespace fl
+
+using namespace fl;
+
+#define FL_TRY(expr)            \
+  do {                          \
+    fl_status s_ = (expr);      \
+    if (s_ != FL_OK) return s_; \
+  } while (0)
+
+extern "C" {
+
+fl_status fl_conv_limited_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt,
+                                  const void *theta_c, const void *u_f, const void *lambda_rhs,
+                                  void *lambda_theta, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(lim, dt));
+  const size_t es = dsize(dt);
+  FL_TRY(check_buffer(theta_c, m->C * es, "theta_c"));
+  FL_TRY(check_buffer(u_f, m->F * es, "u_f"));
+  FL_TRY(check_buffer(lambda_rhs, m->C * es, "lambda_rhs"));
+  FL_TRY(check_buffer(lambda_theta, m->C * es, "lambda_theta"));
+  if (lambda_theta == lambda_rhs || lambda_theta == theta_c)
+    return fail(FL_EINVAL, "lambda_theta must not alias the inputs");
+  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "adjoint of face-based meshes is not available");
+  if (m->C == 0) return FL_OK;
+  AdjArgs a;
+  a.x = theta_c;
+  a.mu = lambda_rhs;
+  a.out = lambda_theta;
+  a.u = u_f;
+  a.bare = 1;
+  cudaError_t e = struct_adjoint(m, lim, dt, a, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel");
+  return FL_OK;
+}
+
+fl_status fl_adjoint_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps,
+                                    int64_t every, size_t *bytes) {
+  if (m == nullptr || bytes == nullptr) return fail(FL_EINVAL, "NULL argument");
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (dt != FL_F32 && dt != FL_F64) return fail(FL_EINVAL, "unknown dtype");
+  if (nsteps < 0 || every < 1) return fail(FL_EINVAL, "nsteps >= 0 and checkpoint_every >= 1");
+  *bytes = adjoint_ws_bytes(m, dt, rk, nsteps, every);
+  return FL_OK;
+}
+
+fl_status fl_step_rk_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
+                             int64_t nsteps, int64_t every, const void *theta0, const void *u_f,
+                             const void *lambda_T, void *lambda_0, void *ws, size_t ws_bytes,
+                             void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(lim, dt));
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (nsteps < 0 || every < 1) return fail(FL_EINVAL, "nsteps >= 0 and checkpoint_every >= 1");
+  if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
+  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "adjoint of face-based meshes is not available");
+  const size_t es = dsize(dt);
+  const size_t one = align256((size_t)m->C * es);
+  FL_TRY(check_buffer(theta0, m->C * es, "theta0"));
+  FL_TRY(check_buffer(u_f, m->F * es, "u_f"));
+  FL_TRY(check_buffer(lambda_T, m->C * es, "lambda_T"));
+  FL_TRY(check_buffer(lambda_0, m->C * es, "lambda_0"));
+  const size_t need = adjoint_ws_bytes(m, dt, rk, nsteps, every);
+  if (ws_bytes < need) return fail(FL_EINVAL, "workspace too small: %zu < %zu", ws_bytes, need);
+  if (((uintptr_t)ws & 255) != 0) return fail(FL_EINVAL, "workspace must be 256-byte aligned");
+  FL_TRY(check_buffer(ws, need, "workspace"));
+  cudaStream_t st = as_stream(stream);
+  const size_t bytes = (size_t)m->C * es;
+  if (m->C == 0) return FL_OK;
+  if (nsteps == 0) {
+    cudaError_t e = cudaMemcpyAsync(lambda_0, lambda_T, bytes, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? FL_OK : cuda_fail(e, "copy");
+  }
+  const int S = (rk == 3) ? 3 : 1;
+  const int64_t nck = (nsteps + every - 1) / every;
+  char *base = static_cast<char *>(ws);
+  auto ck = [&](int64_t i) -> void * { return base + one * i; };
+  char *segb = base + one * nck;
+  auto slot = [&](int64_t i) -> void * { return segb + one * i; };
+  char *lb = segb + one * (S * every + 1);
+  void *lam = lb, *la = lb + one, *lbb = lb + 2 * one;
+
+  cudaError_t e = cudaSuccess;
+  // forward stage helper: y = a thn + b (x + dt R(x))
+  auto stage = [&](const void *x, const void *thn, void *y, int seed, double a, double b) {
+    StageArgs s;
+    s.x = x; s.thn = thn; s.y = y; s.u = u_f; s.dt = dtime; s.seed = seed; s.a = a; s.b = b;
+    return struct_stage(m, lim, dt, s, st);
+  };
+  // one forward step from slot(3n) (RK3) or slot(n) (Euler) storing stage inputs
+  auto fwd_step = [&](int64_t n) -> cudaError_t {
+    if (S == 1) return stage(slot(n), slot(n), slot(n + 1), 0, 0.0, 1.0);
+    cudaError_t r = stage(slot(3 * n), slot(3 * n), slot(3 * n + 1), 0, 0.0, 1.0);
+    if (r == cudaSuccess) r = stage(slot(3 * n + 1), slot(3 * n), slot(3 * n + 2), 1, 0.75, 0.25);
+    if (r == cudaSuccess)
+      r = stage(slot(3 * n + 2), slot(3 * n), slot(3 * n + 3), 1, 1.0 / 3.0, 2.0 / 3.0);
+    return r;
+  };
+  // 1) checkpoints: state at steps 0, every, 2 every, ...
+  e = cudaMemcpyAsync(ck(0), theta0, bytes, cudaMemcpyDeviceToDevice, st);
+  for (int64_t c = 1; c < nck && e == cudaSuccess; ++c) {
+    e = cudaMemcpyAsync(slot(0), ck(c - 1), bytes, cudaMemcpyDeviceToDevice, st);
+    for (int64_t n = 0; n < every && e == cudaSuccess; ++n) {
+      e = fwd_step(0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(slot(0), slot(S), bytes, cudaMemcpyDeviceToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ck(c), slot(0), bytes, cudaMemcpyDeviceToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lam, lambda_T, bytes, cudaMemcpyDeviceToDevice, st);
+  // 2) segments in reverse: recompute storing stage inputs, then adjoint stages
+  for (int64_t c = nck - 1; c >= 0 && e == cudaSuccess; --c) {
+    const int64_t n0 = c * every;
+    const int64_t len = std::min<int64_t>(every, nsteps - n0);
+    e = cudaMemcpyAsync(slot(0), ck(c), bytes, cudaMemcpyDeviceToDevice, st);
+    for (int64_t n = 0; n < len && e == cudaSuccess; ++n) e = fwd_step(n);
+    for (int64_t n = len - 1; n >= 0 && e == cudaSuccess; --n) {
+      AdjArgs a;
+      a.u = u_f;
+      a.dt = dtime;
+      if (S == 1) {
+        // lam' = lam + dt R'(x)^T lam
+        a.x = slot(n); a.mu = lam; a.out = la; a.b = 1.0;
+        e = struct_adjoint(m, lim, dt, a, st);
+        void *t = lam;
+        lam = la;
+        la = t;
+      } else {
+        // stage 3: la = 2/3 (lam + dt R'(x2)^T lam)
+        a.x = slot(3 * n + 2); a.mu = lam; a.out = la; a.b = 2.0 / 3.0;
+        e = struct_adjoint(m, lim, dt, a, st);
+        if (e != cudaSuccess) break;
+        // stage 2: lbb = 1/4 (la + dt R'(x1)^T la)
+        a.x = slot(3 * n + 1); a.mu = la; a.out = lbb; a.b = 0.25;
+        e = struct_adjoint(m, lim, dt, a, st);
+        if (e != cudaSuccess) break;
+        // stage 1: lam = 1/3 lam + 3/4 la + (lbb + dt R'(x0)^T lbb)
+        a.x = slot(3 * n); a.mu = lbb; a.out = lam; a.b = 1.0;
+        a.v1 = lam; a.e1 = 1.0 / 3.0; a.v2 = la; a.e2 = 0.75;
+        e = struct_adjoint(m, lim, dt, a, st);
+      }
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lambda_0, lam, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint sweep");
+  return FL_OK;
+}
+
+}  // extern "C"

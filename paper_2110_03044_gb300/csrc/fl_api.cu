@@ -152,6 +152,12 @@ fl_status fl_mesh_create_structured(int nx, int ny, int nz, double hx, double hy
     na += m->act[a];
   }
   m->F = (int64_t)na * C;
+  if (cudaMalloc(&m->status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(m->status, 0, sizeof(int)) != cudaSuccess) {
+    if (m->status) cudaFree(m->status);
+    delete m;
+    return fail(FL_ENOMEM, "status word allocation failed");
+  }
   *out = m;
   return FL_OK;
 }
@@ -185,8 +191,23 @@ fl_status fl_mesh_info(const fl_mesh *m, int64_t *n_cells, int64_t *n_faces, int
   return FL_OK;
 }
 
+fl_status fl_mesh_status(const fl_mesh *m, void *stream) {
+  FL_TRY(check_mesh(m));
+  if (m->status == nullptr) return FL_OK;
+  int h = 0;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(&h, m->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && h != 0) e = cudaMemsetAsync(m->status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (h != 0) return fail((fl_status)h, "a kernel on this mesh reported status %d", h);
+  return FL_OK;
+}
+
 fl_status fl_mesh_destroy(fl_mesh *m) {
   if (m == nullptr) return FL_OK;
+  if (m->status) cudaFree(m->status);
   if (m->kind == 1) unstruct_free(m);
   delete m;
   return FL_OK;
@@ -300,53 +321,6 @@ fl_status fl_step_rk(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, doub
     }
   }
   if (e != cudaSuccess) return cuda_fail(e, "structured stage kernel");
-  return FL_OK;
-}
-
-fl_status fl_conv_limited_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt,
-                                  const void *theta_c, const void *u_f, const void *lambda_rhs,
-                                  void *lambda_theta, void *stream) {
-  FL_TRY(check_mesh(m));
-  FL_TRY(check_enums(lim, dt));
-  (void)theta_c; (void)u_f; (void)lambda_rhs; (void)lambda_theta; (void)stream;
-  return fail(FL_EUNSUPPORTED, "adjoint not available in this build");
-}
-
-fl_status fl_adjoint_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps,
-                                    int64_t every, size_t *bytes) {
-  (void)m; (void)dt; (void)rk; (void)nsteps; (void)every; (void)bytes;
-  return fail(FL_EUNSUPPORTED, "adjoint not available in this build");
-}
-
-fl_status fl_step_rk_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
-                             int64_t nsteps, int64_t every, const void *theta0, const void *u_f,
-                             const void *lambda_T, void *lambda_0, void *ws, size_t ws_bytes,
-                             void *stream) {
-  (void)m; (void)lim; (void)dt; (void)rk; (void)dtime; (void)nsteps; (void)every; (void)theta0;
-  (void)u_f; (void)lambda_T; (void)lambda_0; (void)ws; (void)ws_bytes; (void)stream;
-  return fail(FL_EUNSUPPORTED, "adjoint not available in this build");
-}
-
-fl_status fl_batch_create(int n, const fl_mesh *const *meshes, fl_batch **out) {
-  (void)n; (void)meshes; (void)out;
-  return fail(FL_EUNSUPPORTED, "batched form not available in this build");
-}
-
-fl_status fl_batch_workspace_size(const fl_batch *b, fl_dtype dt, int rk, size_t *bytes) {
-  (void)b; (void)dt; (void)rk; (void)bytes;
-  return fail(FL_EUNSUPPORTED, "batched form not available in this build");
-}
-
-fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, const double *dtv,
-                           int64_t nsteps, void *const *theta, const void *const *u_f, void *ws,
-                           size_t ws_bytes, void *stream) {
-  (void)b; (void)lim; (void)dt; (void)rk; (void)dtv; (void)nsteps; (void)theta; (void)u_f;
-  (void)ws; (void)ws_bytes; (void)stream;
-  return fail(FL_EUNSUPPORTED, "batched form not available in this build");
-}
-
-fl_status fl_batch_destroy(fl_batch *b) {
-  (void)b;
   return FL_OK;
 }
 

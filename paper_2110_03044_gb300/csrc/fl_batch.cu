@@ -1,0 +1,422 @@
+// fl_batch.cu -- many independent periodic boxes advanced together: one
+// persistent launch per RK stage over a single work list of (box, tile)
+// items, replayed from a captured CUDA graph.
+//
+// Every box keeps its own fields, velocity, spacings and step size; a tile
+// is the same 32 x 8 x zchunk column the single-mesh kernel processes.  The
+// CTAs of the persistent kernel (as many as fit on the GPU at once) take
+// tiles from a shared counter, so boxes of uneven sizes (32^3 .. 128^3)
+// balance across the SMs without one launch per box.  The stage parameters
+// of every box live in device memory owned by the batch, so one captured
+// graph per (limiter, dtype, RK order, z chunk) serves every call; a call
+// only refreshes the parameter table (one host-to-device copy) and replays.
+//
+// The z chunk (cells per tile along z) is picked by a small autotuner on the
+// first call for a (limiter, dtype, RK order): each candidate times a few
+// stage-1 launches (which write only workspace, never the caller's fields)
+// and the fastest is kept.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "fl_internal.h"
+#include "fl_kernels.h"
+#include "fl_struct_tile.cuh"
+
+namespace fl {
+fl_status check_buffer(const void *p, size_t bytes, const char *name);
+fl_status check_enums(int lim, fl_dtype dt);
+}  // namespace fl
+
+struct fl_batch {
+  int n = 0;
+  int device = 0;
+  std::vector<const fl_mesh *> meshes;
+  int64_t cells = 0, faces = 0;
+  // parameter tables: 3 stages (RK3) or 2 parities (Euler) x n boxes
+  void *d_params = nullptr;
+  void *h_params = nullptr;  // pinned staging
+  size_t params_bytes = 0;
+  cudaEvent_t params_done = nullptr;
+  unsigned *d_counters = nullptr;  // one work counter per stage
+  // tile lists per z chunk
+  std::map<int, std::pair<int2 *, int>> tiles;
+  // tuned z chunk per (lim, dtype, rk)
+  std::map<std::tuple<int, int, int>, int> tuned;
+  // graph cache per (lim, dtype, rk, zchunk)
+  std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
+};
+
+namespace fl {
+namespace {
+
+constexpr int BTY = 8;
+constexpr int MAXSTAGES = 3;
+
+template <class T, int LIM, int SEED>
+__global__ void __launch_bounds__(TX *BTY, 4)
+    k_batch_stage(const SParams<T> *__restrict__ params, const int2 *__restrict__ tiles,
+                  int n_tiles, unsigned *counter) {
+  __shared__ int s_next;
+  for (;;) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_next = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int t = s_next;
+    __syncthreads();
+    if (t >= n_tiles) break;
+    const int2 bt = tiles[t];
+    const SParams<T> p = params[bt.x];
+    stage_tile<T, LIM, SEED, BTY>(p, bt.y);
+  }
+}
+
+template <class T, int SEED>
+void *kernel_ptr(int lim) {
+  switch (lim) {
+    case LIM_UPWIND: return (void *)k_batch_stage<T, LIM_UPWIND, SEED>;
+    case LIM_CENTRAL: return (void *)k_batch_stage<T, LIM_CENTRAL, SEED>;
+    case LIM_MINMOD: return (void *)k_batch_stage<T, LIM_MINMOD, SEED>;
+    case LIM_VANLEER: return (void *)k_batch_stage<T, LIM_VANLEER, SEED>;
+    case LIM_SUPERBEE: return (void *)k_batch_stage<T, LIM_SUPERBEE, SEED>;
+    case LIM_SMART: return (void *)k_batch_stage<T, LIM_SMART, SEED>;
+  }
+  return nullptr;
+}
+
+void *batch_kernel(fl_dtype dt, int lim, int seed) {
+  if (dt == FL_F64) return seed == SEED_PLAIN ? kernel_ptr<double, SEED_PLAIN>(lim)
+                                              : kernel_ptr<double, SEED_COMBINE>(lim);
+  return seed == SEED_PLAIN ? kernel_ptr<float, SEED_PLAIN>(lim)
+                            : kernel_ptr<float, SEED_COMBINE>(lim);
+}
+
+int tiles_x_of(const fl_mesh *m) { return (m->nx + TX - 1) / TX; }
+int tiles_y_of(const fl_mesh *m) { return (m->ny + BTY - 1) / BTY; }
+int zchunk_of(const fl_mesh *m, int zc) { return std::min(zc, m->nz); }
+
+// (box, tile) list for a z chunk; tiles of one box are contiguous
+fl_status get_tiles(fl_batch *b, int zc, int2 **d, int *n) {
+  auto it = b->tiles.find(zc);
+  if (it != b->tiles.end()) {
+    *d = it->second.first;
+    *n = it->second.second;
+    return FL_OK;
+  }
+  std::vector<int2> h;
+  for (int i = 0; i < b->n; ++i) {
+    const fl_mesh *m = b->meshes[i];
+    const int z = zchunk_of(m, zc);
+    const long long nt = (long long)tiles_x_of(m) * tiles_y_of(m) * ((m->nz + z - 1) / z);
+    for (long long t = 0; t < nt; ++t) h.push_back(make_int2(i, (int)t));
+  }
+  if (h.size() >= (1u << 31)) return fail(FL_EUNSUPPORTED, "too many tiles");
+  int2 *dp = nullptr;
+  if (cudaMalloc(&dp, h.size() * sizeof(int2)) != cudaSuccess)
+    return fail(FL_ENOMEM, "tile list allocation failed");
+  if (cudaMemcpy(dp, h.data(), h.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(dp);
+    return fail(FL_ECUDA, "tile list upload failed");
+  }
+  b->tiles[zc] = {dp, (int)h.size()};
+  *d = dp;
+  *n = (int)h.size();
+  return FL_OK;
+}
+
+template <class T>
+SParams<T> box_params(const fl_mesh *m, int zc, const void *x, const void *thn, void *y,
+                      const void *u, double dtime, int seed, double a, double bcoef) {
+  SParams<T> p;
+  p.x = static_cast<const T *>(x);
+  p.thn = static_cast<const T *>(thn);
+  p.y = static_cast<T *>(y);
+  p.thf = nullptr;
+  p.u = static_cast<const T *>(u);
+  p.nx = m->nx;
+  p.ny = m->ny;
+  p.nz = m->nz;
+  p.act_x = m->act[0];
+  p.act_y = m->act[1];
+  p.act_z = m->act[2];
+  p.ux_off = m->u_off[0];
+  p.uy_off = m->u_off[1];
+  p.uz_off = m->u_off[2];
+  p.plane = (long long)m->nx * m->ny;
+  const double sc = (seed == SEED_PLAIN) ? dtime : bcoef * dtime;
+  p.cx = (T)(sc / m->hx);
+  p.cy = (T)(sc / m->hy);
+  p.cz = (T)(sc / m->hz);
+  p.a = (T)a;
+  p.b = (T)bcoef;
+  p.tiles_x = tiles_x_of(m);
+  p.tiles_y = tiles_y_of(m);
+  p.zchunk = zchunk_of(m, zc);
+  return p;
+}
+
+size_t param_size(fl_dtype dt) { return dt == FL_F64 ? sizeof(SParams<double>) : sizeof(SParams<float>); }
+
+// Fill the staging table: stage s of box i at index s * n + i.
+template <class T>
+void fill_params(fl_batch *b, int rk, int zc, const double *dtv, void *const *theta,
+                 const void *const *u, char *ws, size_t es) {
+  SParams<T> *h = static_cast<SParams<T> *>(b->h_params);
+  size_t off = 0;
+  for (int i = 0; i < b->n; ++i) {
+    const fl_mesh *m = b->meshes[i];
+    const size_t one = align256((size_t)m->C * es);
+    void *A = ws + off;
+    void *B = ws + off + one;
+    off += (rk == 3 ? 2 : 1) * one;
+    if (rk == 3) {
+      h[0 * b->n + i] = box_params<T>(m, zc, theta[i], theta[i], A, u[i], dtv[i], SEED_PLAIN, 0.0, 1.0);
+      h[1 * b->n + i] = box_params<T>(m, zc, A, theta[i], B, u[i], dtv[i], SEED_COMBINE, 0.75, 0.25);
+      h[2 * b->n + i] =
+          box_params<T>(m, zc, B, theta[i], theta[i], u[i], dtv[i], SEED_COMBINE, 1.0 / 3.0, 2.0 / 3.0);
+    } else {  // Euler: even step theta -> A, odd step A -> theta
+      h[0 * b->n + i] = box_params<T>(m, zc, theta[i], theta[i], A, u[i], dtv[i], SEED_PLAIN, 0.0, 1.0);
+      h[1 * b->n + i] = box_params<T>(m, zc, A, A, theta[i], u[i], dtv[i], SEED_PLAIN, 0.0, 1.0);
+    }
+  }
+}
+
+size_t batch_ws_bytes(const fl_batch *b, fl_dtype dt, int rk) {
+  size_t t = 0;
+  for (const fl_mesh *m : b->meshes) t += (rk == 3 ? 2 : 1) * align256((size_t)m->C * dsize(dt));
+  return t;
+}
+
+int persistent_grid(fl_dtype dt, int lim, int seed) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel(dt, lim, seed), TX * BTY, 0);
+  return std::max(1, sms * std::max(per, 1));
+}
+
+// Enqueue one launch of stage s (seed) on st.
+cudaError_t enqueue_stage(fl_batch *b, fl_dtype dt, int lim, int s, int seed, int2 *tiles, int nt,
+                          cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->d_counters + s, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const char *params = static_cast<const char *>(b->d_params) + (size_t)s * b->n * param_size(dt);
+  unsigned *ctr = b->d_counters + s;
+  void *args[] = {(void *)&params, (void *)&tiles, (void *)&nt, (void *)&ctr};
+  return cudaLaunchKernel(batch_kernel(dt, lim, seed), dim3(persistent_grid(dt, lim, seed)),
+                          dim3(TX, BTY), args, 0, st);
+}
+
+// Stage launches of one step (RK3: 3 stages; Euler: 2 steps, even and odd).
+cudaError_t enqueue_step(fl_batch *b, fl_dtype dt, int lim, int rk, int2 *tiles, int nt,
+                         cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (rk == 3) {
+    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_COMBINE, tiles, nt, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 2, SEED_COMBINE, tiles, nt, st);
+  } else {
+    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_PLAIN, tiles, nt, st);
+  }
+  return e;
+}
+
+fl_status upload_params(fl_batch *b, fl_dtype dt, int rk, int zc, const double *dtv,
+                        void *const *theta, const void *const *u, void *ws, cudaStream_t st) {
+  // the staging buffer may still feed the previous call's copy
+  if (cudaEventSynchronize(b->params_done) != cudaSuccess) return fail(FL_ECUDA, "event sync");
+  if (dt == FL_F64)
+    fill_params<double>(b, rk, zc, dtv, theta, u, static_cast<char *>(ws), 8);
+  else
+    fill_params<float>(b, rk, zc, dtv, theta, u, static_cast<char *>(ws), 4);
+  const size_t bytes = (size_t)MAXSTAGES * b->n * param_size(dt);
+  cudaError_t e = cudaMemcpyAsync(b->d_params, b->h_params, bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->params_done, st);
+  return e == cudaSuccess ? FL_OK : cuda_fail(e, "parameter upload");
+}
+
+// Autotune the z chunk with timed stage-1 launches (write workspace only).
+fl_status tune(fl_batch *b, fl_dtype dt, int lim, int rk, const double *dtv, void *const *theta,
+               const void *const *u, void *ws, cudaStream_t st, int *best) {
+  const int cand[] = {8, 16, 32, 64};
+  float best_ms = 1e30f;
+  *best = 16;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int zc : cand) {
+    int2 *tiles;
+    int nt;
+    fl_status s = get_tiles(b, zc, &tiles, &nt);
+    if (s != FL_OK) return s;
+    if ((s = upload_params(b, dt, rk, zc, dtv, theta, u, ws, st)) != FL_OK) return s;
+    cudaError_t e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(e != cudaSuccess ? e : cudaGetLastError(), "autotune launch");
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      *best = zc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return FL_OK;
+}
+
+}  // namespace
+}  // namespace fl
+
+using namespace fl;
+
+extern "C" {
+
+fl_status fl_batch_create(int n, const fl_mesh *const *meshes, fl_batch **out) {
+  if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || meshes == nullptr) return fail(FL_EINVAL, "need n >= 1 meshes");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(FL_ECUDA, "no CUDA device");
+  for (int i = 0; i < n; ++i) {
+    if (meshes[i] == nullptr) return fail(FL_EINVAL, "mesh %d is NULL", i);
+    if (meshes[i]->kind != 0) return fail(FL_EUNSUPPORTED, "mesh %d is not structured", i);
+    if (meshes[i]->device != dev) return fail(FL_EINVAL, "mesh %d lives on another device", i);
+  }
+  fl_batch *b = new (std::nothrow) fl_batch();
+  if (!b) return fail(FL_ENOMEM, "host allocation failed");
+  b->n = n;
+  b->device = dev;
+  b->meshes.assign(meshes, meshes + n);
+  for (const fl_mesh *m : b->meshes) {
+    b->cells += m->C;
+    b->faces += m->F;
+  }
+  b->params_bytes = (size_t)MAXSTAGES * n * sizeof(SParams<double>);
+  cudaError_t e = cudaMalloc(&b->d_params, b->params_bytes);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_params, b->params_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, MAXSTAGES * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->params_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    fl_batch_destroy(b);
+    return fail(FL_ENOMEM, "batch allocation failed");
+  }
+  *out = b;
+  return FL_OK;
+}
+
+fl_status fl_batch_workspace_size(const fl_batch *b, fl_dtype dt, int rk, size_t *bytes) {
+  if (b == nullptr || bytes == nullptr) return fail(FL_EINVAL, "NULL argument");
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (dt != FL_F32 && dt != FL_F64) return fail(FL_EINVAL, "unknown dtype");
+  *bytes = batch_ws_bytes(b, dt, rk);
+  return FL_OK;
+}
+
+fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, const double *dtv,
+                           int64_t nsteps, void *const *theta, const void *const *u_f, void *ws,
+                           size_t ws_bytes, void *stream) {
+  if (b == nullptr) return fail(FL_EINVAL, "batch is NULL");
+  fl_status s = check_enums(lim, dt);
+  if (s != FL_OK) return s;
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (nsteps < 0) return fail(FL_EINVAL, "nsteps < 0");
+  if (!dtv || !theta || !u_f) return fail(FL_EINVAL, "NULL argument array");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != b->device) return fail(FL_EINVAL, "batch was created on another device");
+  const size_t es = dsize(dt);
+  for (int i = 0; i < b->n; ++i) {
+    const fl_mesh *m = b->meshes[i];
+    if (!std::isfinite(dtv[i])) return fail(FL_EINVAL, "dt[%d] is not finite", i);
+    if ((s = check_buffer(theta[i], m->C * es, "theta[i]")) != FL_OK) return s;
+    if ((s = check_buffer(u_f[i], m->F * es, "u_f[i]")) != FL_OK) return s;
+  }
+  const size_t need = batch_ws_bytes(b, dt, rk);
+  if (ws_bytes < need) return fail(FL_EINVAL, "workspace too small: %zu < %zu", ws_bytes, need);
+  if (((uintptr_t)ws & 255) != 0) return fail(FL_EINVAL, "workspace must be 256-byte aligned");
+  if ((s = check_buffer(ws, need, "workspace")) != FL_OK) return s;
+  if (nsteps == 0) return FL_OK;
+  cudaStream_t st = as_stream(stream);
+  // z chunk: tuned once per (limiter, dtype, rk)
+  const auto tkey = std::make_tuple((int)lim, (int)dt, rk);
+  int zc;
+  auto tit = b->tuned.find(tkey);
+  if (tit == b->tuned.end()) {
+    if ((s = tune(b, dt, lim, rk, dtv, theta, u_f, ws, st, &zc)) != FL_OK) return s;
+    b->tuned[tkey] = zc;
+  } else {
+    zc = tit->second;
+  }
+  int2 *tiles;
+  int nt;
+  if ((s = get_tiles(b, zc, &tiles, &nt)) != FL_OK) return s;
+  if ((s = upload_params(b, dt, rk, zc, dtv, theta, u_f, ws, st)) != FL_OK) return s;
+  // one graph per (limiter, dtype, rk, z chunk): a step's stage launches
+  const auto gkey = std::make_tuple((int)lim, (int)dt, rk, zc);
+  cudaGraphExec_t exec = nullptr;
+  auto git = b->graphs.find(gkey);
+  if (git != b->graphs.end()) {
+    exec = git->second;
+  } else {
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(FL_ECUDA, "stream creation failed");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue_step(b, dt, lim, rk, tiles, nt, cap);
+      e = cudaStreamEndCapture(cap, &g);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    b->graphs[gkey] = exec;
+  }
+  cudaError_t e = cudaSuccess;
+  if (rk == 3) {
+    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) e = cudaGraphLaunch(exec, st);
+  } else {
+    // a graph is two Euler steps (theta -> A -> theta); an odd tail runs the
+    // even stage alone and copies A back
+    for (int64_t n = 0; n + 1 < nsteps && e == cudaSuccess; n += 2) e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess && (nsteps & 1)) {
+      e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);
+      size_t off = 0;
+      for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+        const fl_mesh *m = b->meshes[i];
+        e = cudaMemcpyAsync(theta[i], static_cast<char *>(ws) + off, m->C * es,
+                            cudaMemcpyDeviceToDevice, st);
+        off += align256((size_t)m->C * es);
+      }
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batched step");
+  return FL_OK;
+}
+
+fl_status fl_batch_destroy(fl_batch *b) {
+  if (b == nullptr) return FL_OK;
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto &kv : b->tiles) cudaFree(kv.second.first);
+  if (b->d_params) cudaFree(b->d_params);
+  if (b->h_params) cudaFreeHost(b->h_params);
+  if (b->d_counters) cudaFree(b->d_counters);
+  if (b->params_done) cudaEventDestroy(b->params_done);
+  delete b;
+  return FL_OK;
+}
+
+}  // extern "C"

@@ -35,28 +35,31 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // ----------------------------------------------------------- unstructured
 // Device data of a face-based mesh in the library's internal numbering.
-// Cells are grouped in blocks of up to UBLOCK cells; every block owns the
-// list of faces touching its cells (faces on a block boundary appear in
-// both neighbouring blocks and are evaluated by both).
+// Cells are grouped in blocks (compact patches of at most UBLOCK cells);
+// every block owns the list of faces touching its cells.  A face with both
+// cells in one block appears once in that block's list; a face on a block
+// boundary appears in both neighbouring lists and is evaluated by both.
+constexpr int UBLOCK = 512;
+constexpr int UMAXDEG = 8;  // faces per cell (slot table width)
+
 struct UnstructDev {
   int n_blocks = 0;
-  int max_block_faces = 0;
-  // per block: [cell_begin, cell_end) and [face_begin, face_end) into the
-  // block face list
-  int32_t *blk_cell = nullptr;   // [n_blocks + 1]
-  int32_t *blk_face = nullptr;   // [n_blocks + 1]
-  // block face list entries (structure of arrays)
-  int32_t *bf_face = nullptr;    // internal face id (u_f index)
-  int4 *bf_cells = nullptr;      // (c0, c1, up0, up1): up0 is the upstream cell when
-                                 // the flow goes c0 -> c1, up1 when it goes c1 -> c0
-  // per cell: local slots (index into the block's face list) of its faces,
-  // with sigma in bit 15 (set when the cell is c1 of that face)
-  uint16_t *cell_slots = nullptr;  // [n_cells][6]
-  int32_t *face_c4 = nullptr;      // [n_faces][4] (c0, c1, up0, up1) global
-  double *inv_vol = nullptr;       // [n_cells] A-free factor 1/V_c
-  double *area = nullptr;          // [n_faces]
-  float *inv_vol_f = nullptr;
+  int max_block_entries = 0;
+  int64_t n_entries = 0;
+  int32_t *blk_cell = nullptr;   // [n_blocks + 1] cell range of each block
+  int32_t *blk_entry = nullptr;  // [n_blocks + 1] entry range of each block
+  int32_t *ent_face = nullptr;   // [n_entries] internal face id
+  int4 *ent_cells = nullptr;     // [n_entries] (c0, c1, up0, up1); bit 31 of
+                                 // up0/up1 set when d_U = -(theta_C - theta_U)
+  uint16_t *cell_slots = nullptr;  // [n_cells][UMAXDEG] entry slot within the
+                                   // block, bit 15 set when the cell is c1;
+                                   // 0xFFFF = unused
+  int4 *face_c4 = nullptr;       // [n_faces] same record per face
+  double *area = nullptr;        // [n_faces]
+  double *vol = nullptr;         // [n_cells]
+  double *inv_vol = nullptr;     // [n_cells]
   float *area_f = nullptr;
+  float *inv_vol_f = nullptr;
 };
 
 }  // namespace fl
@@ -64,6 +67,7 @@ struct UnstructDev {
 struct fl_mesh {
   int kind = 0;  // 0 structured, 1 unstructured
   int device = 0;
+  int *status = nullptr;  // device status word (bounded waits record timeouts here)
   int64_t C = 0, F = 0;
   // structured
   int nx = 1, ny = 1, nz = 1;

@@ -21,11 +21,32 @@ struct StageArgs {
 
 cudaError_t struct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs &s,
                          cudaStream_t st);
+// FP32 TMA-staged variant (fl_struct_tma.cu): eligibility and launch;
+// returns cudaErrorNotSupported when the tensor maps cannot be built
+bool struct_tma_eligible(const fl_mesh *m, const StageArgs &s);
+cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cudaStream_t st);
 size_t line_resident_max_cells(fl_dtype dt);
 cudaError_t line_resident(const fl_mesh *m, int lim, fl_dtype dt, void *theta, const void *u,
                           int64_t nsteps, int rk, double dtime, cudaStream_t st);
 cudaError_t struct_selection(const fl_mesh *m, fl_dtype dt, const void *u, int32_t *sel,
                              cudaStream_t st);
+
+// Adjoint of one stage: out = e1 v1 + e2 v2 + b mu + b dt R'(x)^T mu, or
+// out = R'(x)^T mu when bare.  v1, v2 may be null; out may alias v1 / v2.
+struct AdjArgs {
+  const void *x = nullptr;
+  const void *mu = nullptr;
+  const void *v1 = nullptr;
+  const void *v2 = nullptr;
+  void *out = nullptr;
+  const void *u = nullptr;
+  double e1 = 0.0, e2 = 0.0, b = 1.0, dt = 0.0;
+  int bare = 0;
+};
+
+cudaError_t struct_adjoint(const fl_mesh *m, int lim, fl_dtype dt, const AdjArgs &s,
+                           cudaStream_t st);
+size_t adjoint_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps, int64_t every);
 
 // reductions (fl_reduce.cu)
 size_t reduce_ws_bytes();

@@ -23,208 +23,15 @@
 #include "fl_internal.h"
 #include "fl_kernels.h"
 
+#include "fl_struct_tile.cuh"
+
 namespace fl {
 
 namespace {
 
-constexpr int TX = 32;  // one warp along x
-
-template <class T>
-struct SParams {
-  const T *x;      // stage input theta (neighbour reads)
-  const T *thn;    // theta^n (own cell only; may alias y)
-  T *y;            // output: stage result or R (own cell only)
-  T *thf;          // optional face values (apply mode), may be null
-  const T *u;      // face velocities
-  int nx, ny, nz;
-  int act_x, act_y, act_z;
-  long long ux_off, uy_off, uz_off;
-  long long plane;  // nx*ny
-  T cx, cy, cz;     // multiply (phi_minus - phi_plus) of each axis
-  T a, b;           // seed = a*thn + b*x  (COMBINE) or x (PLAIN) or 0 (APPLY)
-  int tiles_x, tiles_y, zchunk;
-};
-
-enum { SEED_PLAIN = 0, SEED_COMBINE = 1, SEED_APPLY = 2 };
-
-__device__ __forceinline__ int wrap(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
-}
-
 template <class T, int LIM, int SEED, int TY>
-__global__ void __launch_bounds__(TX *TY) k_struct_stage(const SParams<T> p) {
-  using F = FT<T>;
-  constexpr int NT = TX * TY;
-  constexpr int SW = TX + 4;  // s_th row pitch
-  __shared__ T s_th[(TY + 4) * SW];
-  __shared__ T s_dx[TY * (TX + 3)];
-  __shared__ T s_dy[(TY + 3) * TX];
-  __shared__ T s_fx[TY * (TX + 1)];
-  __shared__ T s_fy[(TY + 1) * TX];
-  __shared__ int s_wx[TX + 4];
-  __shared__ int s_wy[TY + 4];
-
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
-  int bid = blockIdx.x;
-  const int bx = bid % p.tiles_x;
-  bid /= p.tiles_x;
-  const int by = bid % p.tiles_y;
-  const int bz = bid / p.tiles_y;
-  const int x0 = bx * TX, y0 = by * TY;
-  const int z0 = bz * p.zchunk;
-  const int z1 = min(z0 + p.zchunk, p.nz);
-  const int nx = p.nx, ny = p.ny, nz = p.nz;
-
-  // wrapped coordinates of the tile's columns/rows, halo included
-  if (tid < TX + 4) s_wx[tid] = wrap(x0 - 2 + tid, nx);
-  if (tid < TY + 4) s_wy[tid] = wrap(y0 - 2 + tid, ny);
-  __syncthreads();
-
-  const bool valid = (x0 + tx < nx) && (y0 + ty < ny);
-  const long long col = (long long)s_wx[tx + 2] + (long long)nx * s_wy[ty + 2];
-
-  // halo cells of s_th: 2 columns left/right of every row, 2 rows above/below
-  constexpr int NH = 4 * (TX + TY);
-  static_assert(NH <= NT, "halo items exceed threads");
-  int h_slot = -1;
-  long long h_off = 0;
-  if (tid < 4 * TY) {  // x halo
-    const int r = tid >> 2, k4 = tid & 3;
-    const int c = (k4 < 2) ? k4 : (TX + k4);  // 0,1,TX+2,TX+3
-    h_slot = (r + 2) * SW + c;
-    h_off = (long long)s_wx[c] + (long long)nx * s_wy[r + 2];
-  } else if (tid < NH) {  // y halo
-    const int t = tid - 4 * TY;
-    const int k4 = t / TX, c = t % TX;
-    const int r = (k4 < 2) ? k4 : (TY + k4);  // 0,1,TY+2,TY+3
-    h_slot = r * SW + c + 2;
-    h_off = (long long)s_wx[c + 2] + (long long)nx * s_wy[r];
-  }
-  const bool need_x = p.act_x, need_y = p.act_y, need_z = p.act_z;
-
-  // ---- z prologue: columns k-2 .. k+1 around z0, and the flux of face z0-1/2
-  T th0, thp1, dz_m1 = T(0), dz_0 = T(0), fz_prev = T(0);
-  if (need_z) {
-    const T tm2 = p.x[col + p.plane * wrap(z0 - 2, nz)];
-    const T tm1 = p.x[col + p.plane * wrap(z0 - 1, nz)];
-    th0 = p.x[col + p.plane * z0];
-    thp1 = p.x[col + p.plane * wrap(z0 + 1, nz)];
-    const T d_m2 = F::sub(tm1, tm2);
-    dz_m1 = F::sub(th0, tm1);
-    dz_0 = F::sub(thp1, th0);
-    const T uz = p.u[p.uz_off + col + p.plane * wrap(z0 - 1, nz)];
-    const bool sp = upwind_positive(uz);
-    const T thf = limited_face<T, LIM>(sp ? tm1 : th0, dz_m1, sp ? d_m2 : dz_0, sp);
-    fz_prev = face_flux(uz, thf);
-  } else {
-    th0 = p.x[col];
-    thp1 = th0;
-  }
-
-  for (int k = z0; k < z1; ++k) {
-    const long long pk = p.plane * k;
-    // ---------------------------------------------------------- loads
-    T tp2 = T(0), uz = T(0), thn_c = T(0);
-    if (need_z) {
-      tp2 = p.x[col + p.plane * wrap(k + 2, nz)];
-      uz = p.u[p.uz_off + col + pk];
-    }
-    if (SEED == SEED_COMBINE) thn_c = p.thn[col + pk];
-    T h_val = T(0);
-    if (h_slot >= 0) h_val = p.x[h_off + pk];
-    // ------------------------------------------------------ fill plane
-    s_th[(ty + 2) * SW + tx + 2] = th0;
-    if (h_slot >= 0) s_th[h_slot] = h_val;
-    __syncthreads();
-    // ------------------------------------------- phase A: differences
-    if (need_x) {
-      for (int it = tid; it < TY * (TX + 3); it += NT) {
-        const int r = it / (TX + 3), q = it - r * (TX + 3);
-        const T *row = &s_th[(r + 2) * SW];
-        s_dx[it] = F::sub(row[q + 1], row[q]);
-      }
-    }
-    if (need_y) {
-      for (int it = tid; it < (TY + 3) * TX; it += NT) {
-        const int r = it / TX, c = it - r * TX;
-        s_dy[it] = F::sub(s_th[(r + 1) * SW + c + 2], s_th[r * SW + c + 2]);
-      }
-    }
-    T dz_p1 = T(0);
-    if (need_z) dz_p1 = F::sub(tp2, thp1);
-    __syncthreads();
-    // ----------------------------------------------- phase B: fluxes
-    if (need_x) {
-      for (int it = tid; it < TY * (TX + 1); it += NT) {
-        const int r = it / (TX + 1), q = it - r * (TX + 1);  // face m = x0-1+q
-        const long long uo = p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 2] + pk;
-        const T uf = p.u[uo];
-        const bool sp = upwind_positive(uf);
-        const T *dr = &s_dx[r * (TX + 3)];
-        const T *tr = &s_th[(r + 2) * SW];
-        const T thf = limited_face<T, LIM>(sp ? tr[q + 1] : tr[q + 2], dr[q + 1],
-                                           sp ? dr[q] : dr[q + 2], sp);
-        s_fx[it] = face_flux(uf, thf);
-        if (SEED == SEED_APPLY && p.thf != nullptr) {
-          if (q >= 1 && x0 + q - 1 < nx && y0 + r < ny) p.thf[uo] = thf;
-        }
-      }
-    }
-    if (need_y) {
-      for (int it = tid; it < (TY + 1) * TX; it += NT) {
-        const int r = it / TX, c = it - r * TX;  // face m = y0-1+r
-        const long long uo = p.uy_off + s_wx[c + 2] + (long long)nx * s_wy[r + 1] + pk;
-        const T uf = p.u[uo];
-        const bool sp = upwind_positive(uf);
-        const T thf = limited_face<T, LIM>(
-            sp ? s_th[(r + 1) * SW + c + 2] : s_th[(r + 2) * SW + c + 2], s_dy[(r + 1) * TX + c],
-            sp ? s_dy[r * TX + c] : s_dy[(r + 2) * TX + c], sp);
-        s_fy[it] = face_flux(uf, thf);
-        if (SEED == SEED_APPLY && p.thf != nullptr) {
-          if (r >= 1 && x0 + c < nx && y0 + r - 1 < ny) p.thf[uo] = thf;
-        }
-      }
-    }
-    T fz = T(0);
-    if (need_z) {
-      const bool sp = upwind_positive(uz);
-      const T thf = limited_face<T, LIM>(sp ? th0 : thp1, dz_0, sp ? dz_m1 : dz_p1, sp);
-      fz = face_flux(uz, thf);
-      if (SEED == SEED_APPLY && p.thf != nullptr && valid) p.thf[p.uz_off + col + pk] = thf;
-    }
-    __syncthreads();
-    // ------------------------------------------------ phase C: update
-    if (valid) {
-      T acc;
-      if (SEED == SEED_PLAIN) acc = th0;
-      else if (SEED == SEED_COMBINE) acc = F::fma(p.a, thn_c, F::mul(p.b, th0));
-      else acc = T(0);
-      if (need_x) {
-        acc = F::fma(-p.cx, s_fx[ty * (TX + 1) + tx + 1], acc);
-        acc = F::fma(p.cx, s_fx[ty * (TX + 1) + tx], acc);
-      }
-      if (need_y) {
-        acc = F::fma(-p.cy, s_fy[(ty + 1) * TX + tx], acc);
-        acc = F::fma(p.cy, s_fy[ty * TX + tx], acc);
-      }
-      if (need_z) {
-        acc = F::fma(-p.cz, fz, acc);
-        acc = F::fma(p.cz, fz_prev, acc);
-      }
-      p.y[col + pk] = acc;
-    }
-    // --------------------------------------------------------- rotate
-    if (need_z) {
-      fz_prev = fz;
-      dz_m1 = dz_0;
-      dz_0 = dz_p1;
-      th0 = thp1;
-      thp1 = tp2;
-    } else if (k + 1 < z1) {
-      th0 = p.x[col + p.plane * (k + 1)];
-    }
-  }
+__global__ void __launch_bounds__(TX *TY, 4) k_struct_stage(const SParams<T> p) {
+  stage_tile<T, LIM, SEED, TY>(p, blockIdx.x);
 }
 
 template <class T, int LIM, int SEED>
@@ -427,7 +234,12 @@ __global__ void k_struct_selection(const T *u, int4 *sel, int nx, int ny, int nz
 }  // namespace
 
 cudaError_t struct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs &s, cudaStream_t st) {
-  return dt == FL_F64 ? run_stage_t<double>(m, lim, s, st) : run_stage_t<float>(m, lim, s, st);
+  if (dt == FL_F64) return run_stage_t<double>(m, lim, s, st);
+  if (struct_tma_eligible(m, s)) {
+    const cudaError_t e = struct_stage_tma(m, lim, s, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  return run_stage_t<float>(m, lim, s, st);
 }
 
 size_t line_resident_max_cells(fl_dtype dt) {

@@ -1,24 +1,669 @@
-// fl_unstructured.cu -- placeholder until the face-based kernels land.
+// fl_unstructured.cu -- face-based meshes: validation, upstream-cell tables,
+// locality renumbering, and the fused block-local stage kernel.
+//
+// Method (Valle et al., Section 3.1 and Algorithm 3): the upstream difference
+// of face f, with upwind cell C, is the n_f-projected sum over the other faces
+// j of C of their differences, orientation-corrected by the velocity sign:
+//   d_U = s sum_{j in dC, j != f} (n_f . n_j) (theta_{j,c1} - theta_{j,c0}).
+// On the supported meshes every face j of C other than the one opposite f has
+// n_f . n_j = 0, and the opposite one has n_f . n_j = +-1, so the sum has a
+// single term: d_U = sigma (theta_C - theta_U) with U the cell across the
+// opposite face and sigma = +-1 fixed by the mesh.  mesh creation resolves U
+// and sigma for both flow directions of every face, so the kernel gathers
+// three cell values per face: theta_c0, theta_c1 and theta_U.
+//
+// Kernel: one CTA per cell block (a compact patch of cells in the internal
+// numbering).  Phase 1 evaluates every face of the block's list once --
+// upwind selection, limited theta_f and the flux u_f A_f theta_f -- into
+// shared memory; phase 2 gives each cell the signed sum of its faces' fluxes
+// (gather, no atomics) fused with the RK stage combination.  Faces on a block
+// boundary are evaluated by both blocks from the same inputs with the same
+// code, so both cells see the same flux and the scheme stays conservative.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <unordered_set>
+#include <vector>
+
+#include "fl_face.cuh"
+#include "fl_internal.h"
+#include "fl_kernels.h"
 #include "fl_unstructured.h"
 
 namespace fl {
 
-fl_status unstruct_create(int64_t, int64_t, const int32_t *, const double *, const double *,
-                          const double *, unsigned, fl_mesh **) {
-  return fail(FL_EUNSUPPORTED, "face-based meshes not available in this build");
+namespace {
+
+constexpr int UTHREADS = 256;
+constexpr unsigned SIGMA_BIT = 0x80000000u;
+
+// ================================================================ kernels
+template <class T>
+struct UParams {
+  const T *x;
+  const T *thn;
+  T *y;
+  T *thf;
+  const T *u;
+  const int32_t *blk_cell;
+  const int32_t *blk_entry;
+  const int32_t *ent_face;
+  const int4 *ent_cells;
+  const uint16_t *slots;
+  const T *area;
+  const T *inv_vol;
+  T a, b, bdt;  // RK combination a*thn + b*x and b*dt
+};
+
+template <class T>
+__device__ __forceinline__ T flip_sign(T v, bool neg) {
+  using F = FT<T>;
+  return F::val(F::bits(v) ^ (neg ? F::SIGN : typename F::U(0)));
 }
-void unstruct_free(fl_mesh *) {}
-fl_status unstruct_apply(const fl_mesh *, int, fl_dtype, const void *, const void *, void *, void *,
-                         cudaStream_t) {
-  return fail(FL_EUNSUPPORTED, "face-based meshes not available in this build");
+
+template <class T, int LIM, int SEED>
+__global__ void __launch_bounds__(UTHREADS) k_unstruct_stage(const UParams<T> p) {
+  using F = FT<T>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *s_phi = reinterpret_cast<T *>(smem);
+  const int blk = blockIdx.x;
+  const int eb = p.blk_entry[blk], ee = p.blk_entry[blk + 1];
+  const int cb = p.blk_cell[blk], ce = p.blk_cell[blk + 1];
+  // ---- phase 1: every face of the block once
+  for (int e = eb + (int)threadIdx.x; e < ee; e += UTHREADS) {
+    const int f = p.ent_face[e];
+    const int4 cc = p.ent_cells[e];
+    const T uf = p.u[f];
+    const bool sp = upwind_positive(uf);
+    const T t0 = p.x[cc.x];
+    const T t1 = p.x[cc.y];
+    const unsigned up = sp ? (unsigned)cc.z : (unsigned)cc.w;
+    const T tU = p.x[up & ~SIGMA_BIT];
+    const T tC = sp ? t0 : t1;
+    const T a = F::sub(t1, t0);
+    // b = s d_U = s sigma (theta_C - theta_U)
+    const T bU = flip_sign(F::sub(tC, tU), (!sp) != ((up & SIGMA_BIT) != 0));
+    const T thf = limited_face<T, LIM>(tC, a, bU, sp);
+    s_phi[e - eb] = F::mul(F::mul(uf, p.area[f]), thf);
+    if (SEED == 2 && p.thf != nullptr && cc.x >= cb && cc.x < ce) p.thf[f] = thf;
+  }
+  __syncthreads();
+  // ---- phase 2: cell sums fused with the stage update
+  for (int c = cb + (int)threadIdx.x; c < ce; c += UTHREADS) {
+    const uint4 sl = *reinterpret_cast<const uint4 *>(p.slots + (size_t)c * UMAXDEG);
+    const unsigned w[4] = {sl.x, sl.y, sl.z, sl.w};
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < 2 * 4; ++q) {
+      const unsigned s16 = (w[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
+      if (s16 != 0xFFFFu) acc = F::add(acc, flip_sign(s_phi[s16 & 0x7FFFu], (s16 & 0x8000u) != 0));
+    }
+    // R = -acc / V
+    if (SEED == 2) {
+      p.y[c] = F::mul(-p.inv_vol[c], acc);
+    } else {
+      const T coef = F::mul(p.bdt, p.inv_vol[c]);
+      T seed;
+      if (SEED == 0) seed = p.x[c];
+      else seed = F::fma(p.a, p.thn[c], F::mul(p.b, p.x[c]));
+      p.y[c] = F::fma(-coef, acc, seed);
+    }
+  }
 }
-fl_status unstruct_step(const fl_mesh *, int, fl_dtype, int, double, int64_t, void *, const void *,
-                        void *, cudaStream_t) {
-  return fail(FL_EUNSUPPORTED, "face-based meshes not available in this build");
+
+template <class T>
+__global__ void k_unstruct_selection(const T *u, const int4 *c4, int4 *sel, long long nf) {
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int4 cc = c4[f];
+    const bool sp = upwind_positive(u[f]);
+    int4 o;
+    o.x = sp ? 1 : -1;
+    o.y = sp ? cc.x : cc.y;
+    o.z = sp ? cc.y : cc.x;
+    o.w = (int)((unsigned)(sp ? cc.z : cc.w) & ~SIGMA_BIT);
+    sel[f] = o;
+  }
 }
-cudaError_t unstruct_selection(const fl_mesh *, fl_dtype, const void *, int32_t *, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+template <class T, int SEED>
+cudaError_t launch_lim(int lim, const fl_mesh *m, const UParams<T> &p, cudaStream_t st) {
+  const int nb = m->u.n_blocks;
+  const size_t smem = (size_t)m->u.max_block_entries * sizeof(T);
+  if (nb == 0) return cudaSuccess;
+#define FL_U_CASE(L)                                                                           \
+  case L: {                                                                                    \
+    auto k = k_unstruct_stage<T, L, SEED>;                                                     \
+    if (smem > 48 * 1024) {                                                                    \
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                           (int)smem);                                         \
+      if (e != cudaSuccess) return e;                                                          \
+    }                                                                                          \
+    k<<<nb, UTHREADS, smem, st>>>(p);                                                          \
+    return cudaGetLastError();                                                                 \
+  }
+  switch (lim) {
+    FL_U_CASE(LIM_UPWIND)
+    FL_U_CASE(LIM_CENTRAL)
+    FL_U_CASE(LIM_MINMOD)
+    FL_U_CASE(LIM_VANLEER)
+    FL_U_CASE(LIM_SUPERBEE)
+    FL_U_CASE(LIM_SMART)
+  }
+#undef FL_U_CASE
+  return cudaErrorInvalidValue;
 }
-const double *unstruct_volumes(const fl_mesh *) { return nullptr; }
+
+template <class T>
+cudaError_t run_ustage(const fl_mesh *m, int lim, const StageArgs &s, cudaStream_t st) {
+  UParams<T> p;
+  p.x = static_cast<const T *>(s.x);
+  p.thn = static_cast<const T *>(s.thn);
+  p.y = static_cast<T *>(s.y);
+  p.thf = static_cast<T *>(s.thf);
+  p.u = static_cast<const T *>(s.u);
+  p.blk_cell = m->u.blk_cell;
+  p.blk_entry = m->u.blk_entry;
+  p.ent_face = m->u.ent_face;
+  p.ent_cells = m->u.ent_cells;
+  p.slots = m->u.cell_slots;
+  if (sizeof(T) == 8) {
+    p.area = reinterpret_cast<const T *>(m->u.area);
+    p.inv_vol = reinterpret_cast<const T *>(m->u.inv_vol);
+  } else {
+    p.area = reinterpret_cast<const T *>(m->u.area_f);
+    p.inv_vol = reinterpret_cast<const T *>(m->u.inv_vol_f);
+  }
+  p.a = (T)s.a;
+  p.b = (T)s.b;
+  p.bdt = (T)(s.b * s.dt);
+  switch (s.seed) {
+    case 0: return launch_lim<T, 0>(lim, m, p, st);
+    case 1: return launch_lim<T, 1>(lim, m, p, st);
+    default: return launch_lim<T, 2>(lim, m, p, st);
+  }
+}
+
+// ============================================================ host build
+template <class V>
+fl_status upload(const std::vector<V> &h, V **d) {
+  *d = nullptr;
+  if (h.empty()) return FL_OK;
+  if (cudaMalloc(reinterpret_cast<void **>(d), h.size() * sizeof(V)) != cudaSuccess)
+    return fail(FL_ENOMEM, "device allocation of %zu bytes failed", h.size() * sizeof(V));
+  if (cudaMemcpy(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(FL_ECUDA, "host-to-device copy failed");
+  return FL_OK;
+}
+
+struct HostMesh {
+  int64_t C = 0, F = 0;
+  std::vector<int32_t> c0, c1;
+  std::vector<double> n;  // [F][3]
+  std::vector<int64_t> cf_ptr;
+  std::vector<int32_t> cf_idx;
+  std::vector<int32_t> up[2];  // upstream cell per face and side (side 0: C = c0)
+  std::vector<int8_t> sig[2];  // sigma per face and side
+};
+
+inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Direction classes of the face normals (at most three mutually orthogonal
+// directions on a Cartesian-like hexahedral mesh).  Returns false otherwise.
+bool direction_classes(const HostMesh &h, std::vector<int8_t> &cls, std::vector<int8_t> &sgn) {
+  std::vector<std::array<double, 3>> dirs;
+  cls.assign(h.F, 0);
+  sgn.assign(h.F, 1);
+  for (int64_t f = 0; f < h.F; ++f) {
+    const double *nf = &h.n[3 * f];
+    int k = -1;
+    for (size_t q = 0; q < dirs.size(); ++q) {
+      const double d = dot3(nf, dirs[q].data());
+      if (std::fabs(d) > 0.9) {
+        k = (int)q;
+        sgn[f] = d > 0 ? 1 : -1;
+        break;
+      }
+    }
+    if (k < 0) {
+      if (dirs.size() == 3) return false;
+      dirs.push_back({nf[0], nf[1], nf[2]});
+      k = (int)dirs.size() - 1;
+      sgn[f] = 1;
+    }
+    cls[f] = (int8_t)k;
+  }
+  return true;
+}
+
+// Internal cell order.  On Cartesian-like meshes the cells get integer
+// lattice coordinates by a breadth-first walk along the face normals and are
+// sorted into 8x8x8 tiles (each tile becomes one block).  Otherwise blocks are
+// grown greedily as breadth-first balls of up to UBLOCK cells.
+void renumber_cells(const HostMesh &h, std::vector<int32_t> &order, std::vector<int32_t> &blk_cell) {
+  const int64_t C = h.C;
+  std::vector<int8_t> cls, sgn;
+  order.clear();
+  blk_cell.clear();
+  if (direction_classes(h, cls, sgn)) {
+    std::vector<int64_t> key(C, -1);
+    std::vector<int32_t> cx(C), cy(C), cz(C), comp(C, -1);
+    int ncomp = 0;
+    std::vector<int32_t> queue;
+    queue.reserve(C);
+    for (int64_t s = 0; s < C; ++s) {
+      if (comp[s] >= 0) continue;
+      comp[s] = ncomp;
+      cx[s] = cy[s] = cz[s] = 0;
+      queue.clear();
+      queue.push_back((int32_t)s);
+      for (size_t qi = 0; qi < queue.size(); ++qi) {
+        const int32_t c = queue[qi];
+        for (int64_t t = h.cf_ptr[c]; t < h.cf_ptr[c + 1]; ++t) {
+          const int32_t f = h.cf_idx[t];
+          const bool is0 = (h.c0[f] == c);
+          const int32_t nb = is0 ? h.c1[f] : h.c0[f];
+          if (comp[nb] >= 0) continue;
+          const int step = (is0 ? 1 : -1) * sgn[f];
+          comp[nb] = ncomp;
+          cx[nb] = cx[c] + (cls[f] == 0 ? step : 0);
+          cy[nb] = cy[c] + (cls[f] == 1 ? step : 0);
+          cz[nb] = cz[c] + (cls[f] == 2 ? step : 0);
+          queue.push_back(nb);
+        }
+      }
+      ++ncomp;
+    }
+    // sort by (component, tile z, tile y, tile x, z, y, x); coordinates are
+    // within [-2^20, 2^20) for any mesh below 2^31 cells per axis walk
+    auto fdiv = [](int32_t v) { return (v >= 0) ? v / 8 : -((-v + 7) / 8); };
+    struct K {
+      int32_t comp, tz, ty, tx, z, y, x, c;
+    };
+    std::vector<K> ks(C);
+    for (int64_t c = 0; c < C; ++c)
+      ks[c] = {comp[c], fdiv(cz[c]), fdiv(cy[c]), fdiv(cx[c]), cz[c], cy[c], cx[c], (int32_t)c};
+    std::sort(ks.begin(), ks.end(), [](const K &a, const K &b) {
+      if (a.comp != b.comp) return a.comp < b.comp;
+      if (a.tz != b.tz) return a.tz < b.tz;
+      if (a.ty != b.ty) return a.ty < b.ty;
+      if (a.tx != b.tx) return a.tx < b.tx;
+      if (a.z != b.z) return a.z < b.z;
+      if (a.y != b.y) return a.y < b.y;
+      return a.x < b.x;
+    });
+    order.resize(C);
+    blk_cell.push_back(0);
+    for (int64_t i = 0; i < C; ++i) {
+      order[i] = ks[i].c;
+      if (i > 0) {
+        const K &a = ks[i - 1], &b = ks[i];
+        const bool new_tile = a.comp != b.comp || a.tz != b.tz || a.ty != b.ty || a.tx != b.tx;
+        if (new_tile || i - blk_cell.back() >= UBLOCK) blk_cell.push_back((int32_t)i);
+      }
+    }
+    blk_cell.push_back((int32_t)C);
+    return;
+  }
+  // greedy breadth-first balls
+  std::vector<uint8_t> taken(C, 0);
+  std::vector<int32_t> q;
+  blk_cell.push_back(0);
+  int64_t next_seed = 0;
+  while ((int64_t)order.size() < C) {
+    while (taken[next_seed]) ++next_seed;
+    q.clear();
+    q.push_back((int32_t)next_seed);
+    taken[next_seed] = 1;
+    size_t qi = 0;
+    int count = 0;
+    while (qi < q.size() && count < UBLOCK) {
+      const int32_t c = q[qi++];
+      order.push_back(c);
+      ++count;
+      for (int64_t t = h.cf_ptr[c]; t < h.cf_ptr[c + 1]; ++t) {
+        const int32_t f = h.cf_idx[t];
+        const int32_t nb = (h.c0[f] == c) ? h.c1[f] : h.c0[f];
+        if (!taken[nb]) {
+          taken[nb] = 1;
+          q.push_back(nb);
+        }
+      }
+    }
+    for (size_t r = qi; r < q.size(); ++r) taken[q[r]] = 0;  // not placed yet
+    blk_cell.push_back((int32_t)order.size());
+  }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- create
+fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const double *normals,
+                          const double *areas, const double *volumes, unsigned flags,
+                          fl_mesh **out) {
+  if (C < 0 || F < 0) return fail(FL_EINVAL, "negative size");
+  if (C >= (1LL << 31) - 1 || F >= (1LL << 31) - 1) return fail(FL_EUNSUPPORTED, "sizes must be < 2^31");
+  if ((F > 0 && (!face_cells || !normals || !areas)) || (C > 0 && !volumes))
+    return fail(FL_EINVAL, "NULL input array");
+  if (flags & ~FL_RENUMBER) return fail(FL_EINVAL, "unknown flags 0x%x", flags);
+  HostMesh h;
+  h.C = C;
+  h.F = F;
+  h.c0.resize(F);
+  h.c1.resize(F);
+  h.n.assign(normals, normals + 3 * F);
+  for (int64_t f = 0; f < F; ++f) {
+    const int32_t a = face_cells[2 * f], b = face_cells[2 * f + 1];
+    if (a < 0 || b < 0 || a >= C || b >= C)
+      return fail(FL_EINVAL, "face %lld: cell index out of range", (long long)f);
+    if (a == b) return fail(FL_EINVAL, "face %lld: c0 == c1", (long long)f);
+    const double *nf = &normals[3 * f];
+    const double nn = dot3(nf, nf);
+    if (!(std::fabs(nn - 1.0) < 1e-9)) return fail(FL_EINVAL, "face %lld: normal is not unit", (long long)f);
+    if (!(areas[f] > 0) || !std::isfinite(areas[f])) return fail(FL_EINVAL, "face %lld: bad area", (long long)f);
+    h.c0[f] = a;
+    h.c1[f] = b;
+  }
+  for (int64_t c = 0; c < C; ++c)
+    if (!(volumes[c] > 0) || !std::isfinite(volumes[c]))
+      return fail(FL_EINVAL, "cell %lld: bad volume", (long long)c);
+  // cell -> faces
+  h.cf_ptr.assign(C + 1, 0);
+  for (int64_t f = 0; f < F; ++f) {
+    h.cf_ptr[h.c0[f] + 1]++;
+    h.cf_ptr[h.c1[f] + 1]++;
+  }
+  for (int64_t c = 0; c < C; ++c) {
+    if (h.cf_ptr[c + 1] > UMAXDEG)
+      return fail(FL_EUNSUPPORTED, "cell %lld has %lld faces (at most %d)", (long long)c,
+                  (long long)h.cf_ptr[c + 1], UMAXDEG);
+    h.cf_ptr[c + 1] += h.cf_ptr[c];
+  }
+  h.cf_idx.resize(h.cf_ptr[C]);
+  {
+    std::vector<int64_t> fill(h.cf_ptr.begin(), h.cf_ptr.end() - 1);
+    for (int64_t f = 0; f < F; ++f) {
+      h.cf_idx[fill[h.c0[f]]++] = (int32_t)f;
+      h.cf_idx[fill[h.c1[f]]++] = (int32_t)f;
+    }
+  }
+  // duplicate faces: same cell pair and the same oriented normal
+  for (int64_t c = 0; c < C; ++c) {
+    for (int64_t s = h.cf_ptr[c]; s < h.cf_ptr[c + 1]; ++s)
+      for (int64_t t = s + 1; t < h.cf_ptr[c + 1]; ++t) {
+        const int32_t f = h.cf_idx[s], g = h.cf_idx[t];
+        const bool same = (h.c0[f] == h.c0[g] && h.c1[f] == h.c1[g] &&
+                           dot3(&h.n[3 * f], &h.n[3 * g]) > 0.999) ||
+                          (h.c0[f] == h.c1[g] && h.c1[f] == h.c0[g] &&
+                           dot3(&h.n[3 * f], &h.n[3 * g]) < -0.999);
+        if (same) return fail(FL_EINVAL, "faces %d and %d are the same face", f, g);
+      }
+  }
+  // upstream cell and sign for both flow directions of every face
+  for (int side = 0; side < 2; ++side) {
+    h.up[side].resize(F);
+    h.sig[side].resize(F);
+  }
+  for (int64_t f = 0; f < F; ++f) {
+    for (int side = 0; side < 2; ++side) {
+      const int32_t Cc = side == 0 ? h.c0[f] : h.c1[f];
+      int found = 0;
+      int32_t jstar = -1;
+      double wstar = 0;
+      for (int64_t t = h.cf_ptr[Cc]; t < h.cf_ptr[Cc + 1]; ++t) {
+        const int32_t j = h.cf_idx[t];
+        if (j == f) continue;
+        const double w = dot3(&h.n[3 * f], &h.n[3 * j]);
+        if (std::fabs(w) > 0.5) {
+          ++found;
+          jstar = j;
+          wstar = w;
+        } else if (std::fabs(w) > 1e-9) {
+          return fail(FL_EUNSUPPORTED,
+                      "face %lld: a neighbouring face is neither parallel nor orthogonal "
+                      "(general polyhedral meshes are not supported)", (long long)f);
+        }
+      }
+      if (found != 1)
+        return fail(FL_EUNSUPPORTED, "face %lld: cell %d has %d faces opposite it (need exactly 1)",
+                    (long long)f, Cc, found);
+      if (std::fabs(std::fabs(wstar) - 1.0) > 1e-9)
+        return fail(FL_EUNSUPPORTED, "face %lld: opposite face is not parallel", (long long)f);
+      const bool jc1 = (h.c1[jstar] == Cc);
+      h.up[side][f] = jc1 ? h.c0[jstar] : h.c1[jstar];
+      // d_U = s w (theta_{j,c1} - theta_{j,c0}) = sigma (theta_C - theta_U)
+      const int s = side == 0 ? 1 : -1;
+      const int w = wstar > 0 ? 1 : -1;
+      h.sig[side][f] = (int8_t)(s * w * (jc1 ? 1 : -1));
+    }
+  }
+  // ---- internal numbering
+  std::vector<int32_t> order, blk_cell;
+  const bool renum = (flags & FL_RENUMBER) != 0;
+  if (renum && C > 0) {
+    renumber_cells(h, order, blk_cell);
+  } else {
+    order.resize(C);
+    std::iota(order.begin(), order.end(), 0);
+    blk_cell.clear();
+    for (int64_t c = 0; c < C; c += UBLOCK) blk_cell.push_back((int32_t)c);
+    blk_cell.push_back((int32_t)C);
+  }
+  std::vector<int32_t> cell_new(C);
+  for (int64_t i = 0; i < C; ++i) cell_new[order[i]] = (int32_t)i;
+  // faces: by the lower internal cell, then by user id (stable)
+  std::vector<int32_t> face_order(F);
+  std::iota(face_order.begin(), face_order.end(), 0);
+  if (renum) {
+    std::stable_sort(face_order.begin(), face_order.end(), [&](int32_t a, int32_t b) {
+      const int32_t ka = std::min(cell_new[h.c0[a]], cell_new[h.c1[a]]);
+      const int32_t kb = std::min(cell_new[h.c0[b]], cell_new[h.c1[b]]);
+      return ka < kb;
+    });
+  }
+  std::vector<int32_t> face_new(F);
+  for (int64_t i = 0; i < F; ++i) face_new[face_order[i]] = (int32_t)i;
+  // per-face records in internal numbering
+  std::vector<int4> c4(F);
+  std::vector<double> area_i(F), vol_i(C), ivol_i(C);
+  for (int64_t f = 0; f < F; ++f) {
+    const int32_t fi = face_new[f];
+    int4 r;
+    r.x = cell_new[h.c0[f]];
+    r.y = cell_new[h.c1[f]];
+    r.z = (int)((unsigned)cell_new[h.up[0][f]] | (h.sig[0][f] < 0 ? SIGMA_BIT : 0u));
+    r.w = (int)((unsigned)cell_new[h.up[1][f]] | (h.sig[1][f] < 0 ? SIGMA_BIT : 0u));
+    c4[fi] = r;
+    area_i[fi] = areas[f];
+  }
+  for (int64_t c = 0; c < C; ++c) {
+    vol_i[cell_new[c]] = volumes[c];
+    ivol_i[cell_new[c]] = 1.0 / volumes[c];
+  }
+  // internal cell -> internal faces
+  std::vector<int64_t> icf_ptr(C + 1, 0);
+  for (int64_t f = 0; f < F; ++f) {
+    icf_ptr[c4[f].x + 1]++;
+    icf_ptr[c4[f].y + 1]++;
+  }
+  for (int64_t c = 0; c < C; ++c) icf_ptr[c + 1] += icf_ptr[c];
+  std::vector<int32_t> icf(icf_ptr[C]);
+  {
+    std::vector<int64_t> fill(icf_ptr.begin(), icf_ptr.end() - 1);
+    for (int64_t f = 0; f < F; ++f) {
+      icf[fill[c4[f].x]++] = (int32_t)f;
+      icf[fill[c4[f].y]++] = (int32_t)f;
+    }
+  }
+  // block entry lists and per-cell slots
+  const int nb = (int)blk_cell.size() - 1;
+  std::vector<int32_t> blk_entry(nb + 1, 0), ent_face;
+  std::vector<int4> ent_cells;
+  std::vector<uint16_t> slots((size_t)C * UMAXDEG, 0xFFFF);
+  ent_face.reserve((size_t)(F * 1.3) + 16);
+  int max_entries = 0;
+  std::vector<int32_t> list;
+  for (int b = 0; b < nb; ++b) {
+    const int32_t cb = blk_cell[b], ce = blk_cell[b + 1];
+    list.clear();
+    for (int32_t c = cb; c < ce; ++c)
+      for (int64_t t = icf_ptr[c]; t < icf_ptr[c + 1]; ++t) {
+        const int32_t f = icf[t];
+        const int32_t o = (c4[f].x == c) ? c4[f].y : c4[f].x;
+        // a face inside the block is listed once (from its lower cell)
+        if (o >= cb && o < ce && o < c) continue;
+        list.push_back(f);
+      }
+    std::sort(list.begin(), list.end());
+    if ((int)list.size() > 0x7FFF)
+      return fail(FL_EUNSUPPORTED, "block %d has %zu faces", b, list.size());
+    blk_entry[b] = (int32_t)ent_face.size();
+    for (size_t q = 0; q < list.size(); ++q) {
+      ent_face.push_back(list[q]);
+      ent_cells.push_back(c4[list[q]]);
+    }
+    max_entries = std::max(max_entries, (int)list.size());
+    for (int32_t c = cb; c < ce; ++c) {
+      int k = 0;
+      for (int64_t t = icf_ptr[c]; t < icf_ptr[c + 1]; ++t) {
+        const int32_t f = icf[t];
+        const size_t pos = std::lower_bound(list.begin(), list.end(), f) - list.begin();
+        uint16_t s16 = (uint16_t)pos;
+        if (c4[f].y == c) s16 |= 0x8000u;  // sigma = -1 on c1
+        slots[(size_t)c * UMAXDEG + k++] = s16;
+      }
+    }
+  }
+  blk_entry[nb] = (int32_t)ent_face.size();
+
+  fl_mesh *m = new (std::nothrow) fl_mesh();
+  if (!m) return fail(FL_ENOMEM, "host allocation failed");
+  if (cudaGetDevice(&m->device) != cudaSuccess) {
+    delete m;
+    return fail(FL_ECUDA, "no CUDA device");
+  }
+  m->kind = 1;
+  m->C = C;
+  m->F = F;
+  if (cudaMalloc(&m->status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(m->status, 0, sizeof(int)) != cudaSuccess) {
+    if (m->status) cudaFree(m->status);
+    delete m;
+    return fail(FL_ENOMEM, "status word allocation failed");
+  }
+  m->renumbered = renum;
+  m->cell_perm = cell_new;
+  m->face_perm = face_new;
+  m->face_flip.assign(F, 0);
+  UnstructDev &u = m->u;
+  u.n_blocks = nb;
+  u.max_block_entries = max_entries;
+  u.n_entries = (int64_t)ent_face.size();
+  std::vector<float> area_f(area_i.begin(), area_i.end()), ivol_f(ivol_i.begin(), ivol_i.end());
+  fl_status st = FL_OK;
+  if (st == FL_OK) st = upload(blk_cell, &u.blk_cell);
+  if (st == FL_OK) st = upload(blk_entry, &u.blk_entry);
+  if (st == FL_OK) st = upload(ent_face, &u.ent_face);
+  if (st == FL_OK) st = upload(ent_cells, &u.ent_cells);
+  if (st == FL_OK) st = upload(slots, &u.cell_slots);
+  if (st == FL_OK) st = upload(c4, &u.face_c4);
+  if (st == FL_OK) st = upload(area_i, &u.area);
+  if (st == FL_OK) st = upload(vol_i, &u.vol);
+  if (st == FL_OK) st = upload(ivol_i, &u.inv_vol);
+  if (st == FL_OK) st = upload(area_f, &u.area_f);
+  if (st == FL_OK) st = upload(ivol_f, &u.inv_vol_f);
+  if (st != FL_OK) {
+    unstruct_free(m);
+    delete m;
+    return st;
+  }
+  *out = m;
+  return FL_OK;
+}
+
+void unstruct_free(fl_mesh *m) {
+  UnstructDev &u = m->u;
+  void *ptrs[] = {u.blk_cell, u.blk_entry, u.ent_face, u.ent_cells, u.cell_slots, u.face_c4,
+                  u.area, u.vol, u.inv_vol, u.area_f, u.inv_vol_f};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  u = UnstructDev();
+}
+
+cudaError_t unstruct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs &s,
+                           cudaStream_t st) {
+  return dt == FL_F64 ? run_ustage<double>(m, lim, s, st) : run_ustage<float>(m, lim, s, st);
+}
+
+fl_status unstruct_apply(const fl_mesh *m, int lim, fl_dtype dt, const void *theta, const void *u,
+                         void *rhs, void *thf, cudaStream_t st) {
+  StageArgs s;
+  s.x = theta;
+  s.thn = theta;
+  s.y = rhs;
+  s.thf = thf;
+  s.u = u;
+  s.seed = 2;
+  cudaError_t e = unstruct_stage(m, lim, dt, s, st);
+  if (e != cudaSuccess) return cuda_fail(e, "unstructured apply kernel");
+  return FL_OK;
+}
+
+fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
+                        int64_t nsteps, void *theta, const void *u, void *ws, cudaStream_t st) {
+  const size_t es = dsize(dt);
+  char *wsb = static_cast<char *>(ws);
+  void *A = wsb;
+  void *B = wsb + align256((size_t)m->C * es);
+  StageArgs s;
+  s.u = u;
+  s.dt = dtime;
+  cudaError_t e = cudaSuccess;
+  if (rk == 1) {
+    void *cur = theta, *nxt = A;
+    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      s.x = cur; s.thn = cur; s.y = nxt; s.seed = 0; s.b = 1.0;
+      e = unstruct_stage(m, lim, dt, s, st);
+      void *t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    if (e == cudaSuccess && cur != theta)
+      e = cudaMemcpyAsync(theta, cur, m->C * es, cudaMemcpyDeviceToDevice, st);
+  } else {
+    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      s.x = theta; s.thn = theta; s.y = A; s.seed = 0; s.a = 0.0; s.b = 1.0;
+      if ((e = unstruct_stage(m, lim, dt, s, st)) != cudaSuccess) break;
+      s.x = A; s.thn = theta; s.y = B; s.seed = 1; s.a = 0.75; s.b = 0.25;
+      if ((e = unstruct_stage(m, lim, dt, s, st)) != cudaSuccess) break;
+      s.x = B; s.thn = theta; s.y = theta; s.seed = 1; s.a = 1.0 / 3.0; s.b = 2.0 / 3.0;
+      e = unstruct_stage(m, lim, dt, s, st);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "unstructured stage kernel");
+  return FL_OK;
+}
+
+cudaError_t unstruct_selection(const fl_mesh *m, fl_dtype dt, const void *u, int32_t *sel,
+                               cudaStream_t st) {
+  const long long nf = m->F;
+  const int threads = 256;
+  long long blocks = (nf + threads - 1) / threads;
+  if (blocks > 65535LL * 16) blocks = 65535LL * 16;
+  if (dt == FL_F64)
+    k_unstruct_selection<double><<<(unsigned)blocks, threads, 0, st>>>(
+        static_cast<const double *>(u), m->u.face_c4, reinterpret_cast<int4 *>(sel), nf);
+  else
+    k_unstruct_selection<float><<<(unsigned)blocks, threads, 0, st>>>(
+        static_cast<const float *>(u), m->u.face_c4, reinterpret_cast<int4 *>(sel), nf);
+  return cudaGetLastError();
+}
+
+const double *unstruct_volumes(const fl_mesh *m) { return m->u.vol; }
 
 }  // namespace fl

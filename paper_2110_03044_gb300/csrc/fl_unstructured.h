@@ -18,5 +18,8 @@ fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double d
 cudaError_t unstruct_selection(const fl_mesh *m, fl_dtype dt, const void *u, int32_t *sel,
                                cudaStream_t st);
 const double *unstruct_volumes(const fl_mesh *m);
+struct StageArgs;
+cudaError_t unstruct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs &s,
+                           cudaStream_t st);
 
 }  // namespace fl

@@ -1,0 +1,168 @@
+"""The hand-written adjoint: operator transpose against the oracle's adjoint
+and tangent-linear model, the checkpointed reverse sweep against the oracle's
+FP64 reference gradient, the torch.autograd wrapper, and -- at the adjoint
+configuration's full size -- central finite differences along random
+directions."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+LIMS = ["upwind", "central", "minmod", "vanleer", "superbee", "smart"]
+
+
+def _case(shape, seed=0):
+    h = (0.7 / shape[0], 0.9 / shape[1], 1.1 / shape[2])
+    mesh = W.structured_mesh(*shape, *h)
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3)
+    u = W.mixed_sign_velocity(mesh.n_faces, seed + 1)
+    return mesh, th, u
+
+
+def _t(x, dtype=torch.float64):
+    return torch.tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lim", LIMS)
+@pytest.mark.parametrize("shape", [(37, 21, 13), (33, 1, 1), (40, 9, 1), (5, 4, 6)])
+def test_operator_adjoint_matches_oracle(fl, shape, lim, dtype):
+    mesh, th, u = _case(shape, 3)
+    if dtype == torch.float32:
+        th = th.astype(np.float32).astype(np.float64)
+        u = u.astype(np.float32).astype(np.float64)
+    mu = np.random.default_rng(4).normal(size=mesh.n_cells)
+    m = fl.Mesh.structured(*shape, *mesh.h)
+    out = torch.empty(mesh.n_cells, dtype=dtype, device="cuda")
+    fl.fl_conv_limited_adjoint(m.handle, lim, dtype, _t(th, dtype), _t(u, dtype), _t(mu, dtype),
+                               out)
+    ref = oracle.rhs_adjoint(mesh, lim, th, u, mu)
+    scale = np.max(np.abs(u)) * np.max(np.abs(mu)) / min(mesh.h)
+    tol = 1e-12 if dtype == torch.float64 else 1e-5
+    assert np.max(np.abs(out.cpu().double().numpy() - ref)) <= 8 * tol * scale
+    m.close()
+
+
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "superbee", "smart"])
+def test_dot_product_with_cpu_tangent_linear(fl, lim):
+    # <J v, w> with J v from the oracle's tangent-linear model (CPU) against
+    # <v, J^T w> from the GPU adjoint, for one RK3 step
+    wl = W.config_taylor_green(n=16, seed=4, nsteps=1, limiter=lim)
+    rng = np.random.default_rng(5)
+    m = fl.Mesh.structured(16, 16, 16, *wl.mesh.h)
+    nb = fl.fl_adjoint_workspace_size(m.handle, torch.float64, 3, 1, 1)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        v = rng.normal(size=wl.mesh.n_cells)
+        w = rng.normal(size=wl.mesh.n_cells)
+        _, Jv = oracle.step_tlm(wl.mesh, lim, 3, wl.dt, 1, wl.u, wl.theta0, v)
+        JTw = torch.empty(wl.mesh.n_cells, dtype=torch.float64, device="cuda")
+        fl.fl_step_rk_adjoint(m.handle, lim, torch.float64, 3, wl.dt, 1, 1, _t(wl.theta0),
+                              _t(wl.u), _t(w), JTw, ws, nb)
+        lhs = float(np.dot(Jv, w))
+        rhs = float(np.dot(v, JTw.cpu().numpy()))
+        assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Jv) * np.linalg.norm(w)
+    m.close()
+
+
+@pytest.mark.parametrize("rk,every", [(3, 3), (3, 20), (1, 4)])
+@pytest.mark.parametrize("lim", ["superbee", "vanleer", "smart"])
+def test_checkpointed_gradient_matches_oracle(fl, lim, rk, every):
+    n, nsteps = 12, 10
+    wl = W.config_taylor_green(n=n, seed=4, nsteps=nsteps, limiter=lim)
+    tgt = W.smooth_target(wl.mesh.dims, wl.mesh.h, 4)
+    J_ref, g_ref = oracle.gradient(wl.mesh, lim, rk, wl.dt, nsteps, wl.u, wl.theta0, tgt)
+    m = fl.Mesh.structured(n, n, n, *wl.mesh.h)
+    thT = oracle.step(wl.mesh, lim, rk, wl.dt, nsteps, wl.u, wl.theta0)
+    nb = fl.fl_adjoint_workspace_size(m.handle, torch.float64, rk, nsteps, every)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    g = torch.empty(wl.mesh.n_cells, dtype=torch.float64, device="cuda")
+    fl.fl_step_rk_adjoint(m.handle, lim, torch.float64, rk, wl.dt, nsteps, every, _t(wl.theta0),
+                          _t(wl.u), _t(thT - tgt), g, ws, nb)
+    gg = g.cpu().numpy()
+    assert np.max(np.abs(gg - g_ref)) <= 1e-11 * np.max(np.abs(g_ref))
+    m.close()
+
+
+def test_autograd_function(fl):
+    from paper_2110_03044_gb300.autograd import rollout
+    n, nsteps = 12, 6
+    wl = W.config_taylor_green(n=n, seed=4, nsteps=nsteps, limiter="superbee")
+    tgt = W.smooth_target(wl.mesh.dims, wl.mesh.h, 4)
+    _, g_ref = oracle.gradient(wl.mesh, "superbee", 3, wl.dt, nsteps, wl.u, wl.theta0, tgt)
+    m = fl.Mesh.structured(n, n, n, *wl.mesh.h)
+    th0 = _t(wl.theta0).requires_grad_(True)
+    thT = rollout(th0, _t(wl.u), m, "superbee", wl.dt, nsteps, 3, 4)
+    loss = 0.5 * ((thT - _t(tgt)) ** 2).sum()
+    loss.backward()
+    assert np.max(np.abs(th0.grad.cpu().numpy() - g_ref)) <= 1e-11 * np.max(np.abs(g_ref))
+    m.close()
+
+
+def test_adjoint_config_full_size_central_differences(fl):
+    """128^3 Taylor-Green, superbee, 200 SSP-RK3 steps, checkpoints every 20:
+    the gradient of 0.5||theta_T - target||^2 against central finite
+    differences of GPU forward rollouts along 32 smooth random directions
+    (random Fourier fields) and 32 white-noise directions N(0, I).
+
+    The rollout is piecewise linear in theta0 (the limiter is piecewise
+    linear), so central differences are exact up to rounding except for the
+    limiter kinks crossed inside +-eps, whose effect shrinks with eps.
+    Smooth directions: |fd - ad| <= 1e-6 |ad|.  White-noise directions are
+    nearly orthogonal to the (smooth) gradient -- <g, v> is 1e-5..1e-3 of
+    ||g|| ||v|| -- so their bar is |fd - ad| <= 1e-6 ||g|| ||v||, and the
+    relative error is reported."""
+    n, nsteps, every = 128, 200, 20
+    wl = W.config_taylor_green(n=n, seed=4, nsteps=nsteps, limiter="superbee")
+    tgt = W.smooth_target(wl.mesh.dims, wl.mesh.h, 4)
+    m = fl.Mesh.structured(n, n, n, *wl.mesh.h)
+    u = _t(wl.u)
+    th0 = _t(wl.theta0)
+    tg = _t(tgt)
+    ws_f = torch.empty(fl.fl_workspace_size(m.handle, torch.float64, 3), dtype=torch.uint8,
+                       device="cuda")
+
+    def run(x):
+        y = x.clone()
+        fl.fl_step_rk(m.handle, "superbee", torch.float64, 3, wl.dt, nsteps, y, u, ws_f,
+                      ws_f.numel())
+        return y
+
+    thT = run(th0)
+    nb = fl.fl_adjoint_workspace_size(m.handle, torch.float64, 3, nsteps, every)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    g = torch.empty_like(th0)
+    fl.fl_step_rk_adjoint(m.handle, "superbee", torch.float64, 3, wl.dt, nsteps, every, th0, u,
+                          thT - tg, g, ws, nb)
+
+    def fd(v, rel_eps):
+        eps = rel_eps * float(th0.norm() / v.norm())
+        tp, tm = run(th0 + eps * v), run(th0 - eps * v)
+        # J(+) - J(-) = 0.5 sum (tp - tm)(tp + tm - 2 tgt), without cancellation
+        return 0.5 * torch.sum((tp - tm) * (tp + tm - 2 * tg)).item() / (2 * eps)
+
+    rng = np.random.default_rng(4)
+    worst_smooth = worst_noise_scaled = worst_noise_rel = 0.0
+    for _ in range(32):
+        v = _t(W.sine_sum_field(wl.mesh.dims, wl.mesh.h, rng, n_modes=4, kmax=4, amp=1.0))
+        ad = float(torch.dot(g, v).item())
+        worst_smooth = max(worst_smooth, abs(fd(v, 1e-7) - ad) / abs(ad))
+    for _ in range(32):
+        v = _t(rng.normal(size=wl.mesh.n_cells))
+        ad = float(torch.dot(g, v).item())
+        err = abs(fd(v, 1e-8) - ad)
+        worst_noise_scaled = max(worst_noise_scaled, err / float(g.norm() * v.norm()))
+        worst_noise_rel = max(worst_noise_rel, err / abs(ad))
+    print("adjoint vs central differences over 32 + 32 directions: smooth rel %.2e; "
+          "white noise scaled %.2e (rel %.2e)" % (worst_smooth, worst_noise_scaled,
+                                                  worst_noise_rel))
+    assert worst_smooth <= 1e-6
+    assert worst_noise_scaled <= 1e-6
+    m.close()

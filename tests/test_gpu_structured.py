@@ -147,15 +147,42 @@ def test_config_1d_resident(fl):
     m.close()
 
 
+def _raw_device_alloc(nbytes):
+    """cudaMalloc of exactly nbytes through the CUDA runtime (the caching
+    allocator would place a small tensor inside a larger allocation)."""
+    import ctypes
+    import ctypes.util
+    rt = None
+    for name in ("libcudart.so", "libcudart.so.13", ctypes.util.find_library("cudart")):
+        if not name:
+            continue
+        try:
+            rt = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    if rt is None:
+        return None
+    p = ctypes.c_void_p()
+    if rt.cudaMalloc(ctypes.byref(p), ctypes.c_size_t(nbytes)) != 0:
+        return None
+    return p.value, (lambda: rt.cudaFree(p))
+
+
 def test_empty_steps_and_argument_errors(fl):
     m = fl.Mesh.structured(8, 8, 8, 1.0, 1.0, 1.0)
     th = torch.zeros(512, dtype=torch.float64, device="cuda")
     u = torch.zeros(3 * 512, dtype=torch.float64, device="cuda")
     fl.step_rk(m, "superbee", th, u, 0.1, 0)  # nsteps = 0 is a no-op
-    small = torch.zeros(100, dtype=torch.float64, device="cuda")
-    with pytest.raises(fl.FLError):
-        fl.step_rk(m, "superbee", small, u, 0.1, 1)
     ws, n = fl.workspace_for(m, torch.float64, 3)
+    # a device buffer whose allocation ends before the mesh's 512 cells
+    small = _raw_device_alloc(100 * 8)
+    if small is not None:
+        ptr, free = small
+        with pytest.raises(fl.FLError) as e:
+            fl.fl_step_rk(m.handle, "superbee", torch.float64, 3, 0.1, 1, ptr, u, ws, n)
+        assert e.value.status == fl.FL_EINVAL
+        free()
     with pytest.raises(fl.FLError):
         fl.fl_step_rk(m.handle, "superbee", torch.float64, 3, 0.1, 1, th, u, ws, n // 2)
     with pytest.raises(fl.FLError):

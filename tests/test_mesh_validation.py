@@ -1,0 +1,73 @@
+"""Host-side validation of fl_mesh_create (no GPU needed: every rejection
+happens before any device call)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def _box():
+    return W.structured_mesh(4, 4, 4, 0.25, 0.25, 0.25)
+
+
+def _create(fl, m, fc=None, nrm=None, ar=None, vol=None, n_cells=None):
+    return fl.fl_mesh_create(m.n_cells if n_cells is None else n_cells,
+                             m.face_cells if fc is None else fc,
+                             m.normals if nrm is None else nrm,
+                             m.areas if ar is None else ar,
+                             m.volumes if vol is None else vol, fl.FL_RENUMBER)
+
+
+def test_rejects_out_of_range_cells(fl):
+    m = _box()
+    fc = m.face_cells.copy()
+    fc[5, 1] = m.n_cells
+    with pytest.raises(fl.FLError) as e:
+        _create(fl, m, fc=fc)
+    assert e.value.status == fl.FL_EINVAL
+
+
+def test_rejects_degenerate_face(fl):
+    m = _box()
+    fc = m.face_cells.copy()
+    fc[3, 1] = fc[3, 0]
+    with pytest.raises(fl.FLError) as e:
+        _create(fl, m, fc=fc)
+    assert e.value.status == fl.FL_EINVAL
+
+
+def test_rejects_non_unit_normal_and_bad_geometry(fl):
+    m = _box()
+    nrm = m.normals.copy()
+    nrm[0] *= 1.5
+    with pytest.raises(fl.FLError):
+        _create(fl, m, nrm=nrm)
+    ar = m.areas.copy()
+    ar[2] = 0.0
+    with pytest.raises(fl.FLError):
+        _create(fl, m, ar=ar)
+    vol = m.volumes.copy()
+    vol[1] = -1.0
+    with pytest.raises(fl.FLError):
+        _create(fl, m, vol=vol)
+
+
+def test_rejects_duplicated_face(fl):
+    m = _box()
+    fc = np.concatenate([m.face_cells, m.face_cells[:1]])
+    nrm = np.concatenate([m.normals, m.normals[:1]])
+    ar = np.concatenate([m.areas, m.areas[:1]])
+    with pytest.raises(fl.FLError) as e:
+        _create(fl, m, fc=fc, nrm=nrm, ar=ar)
+    assert e.value.status in (fl.FL_EINVAL, fl.FL_EUNSUPPORTED)
+
+
+def test_rejects_non_hexahedral_mesh(fl):
+    # a face tilted 45 degrees: neither parallel nor orthogonal to its
+    # neighbours (general polyhedra are not supported)
+    m = _box()
+    nrm = m.normals.copy()
+    nrm[0] = np.array([1.0, 1.0, 0.0]) / np.sqrt(2.0)
+    with pytest.raises(fl.FLError) as e:
+        _create(fl, m, nrm=nrm)
+    assert e.value.status == fl.FL_EUNSUPPORTED
