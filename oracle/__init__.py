@@ -27,6 +27,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "fl_oracle.cpp")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
+# The mutation test (tests/test_oracle_mutations.py) points this at a
+# deliberately broken build to show that the pins reject it.
+MUTANT_LIB = os.environ.get("FL_ORACLE_MUTANT_LIB")
 
 LIMITERS = {"upwind": 0, "central": 1, "minmod": 2, "vanleer": 3, "superbee": 4, "smart": 5}
 
@@ -54,8 +57,11 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        build()
-        lib = ctypes.CDLL(LIB)
+        if MUTANT_LIB:
+            lib = ctypes.CDLL(MUTANT_LIB)
+        else:
+            build()
+            lib = ctypes.CDLL(LIB)
         P = ctypes.c_void_p
         i64 = ctypes.c_int64
         I = ctypes.c_int
