@@ -26,8 +26,9 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
-#include <queue>
-#include <unordered_set>
+#include <atomic>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "fl_face.cuh"
@@ -190,6 +191,72 @@ cudaError_t run_ustage(const fl_mesh *m, int lim, const StageArgs &s, cudaStream
 }
 
 // ============================================================ host build
+// Run fn(begin, end) over [0, n) on the host cores (mesh set-up only).
+template <class Fn>
+void parallel_for(int64_t n, Fn fn) {
+  unsigned nt = std::thread::hardware_concurrency();
+  nt = std::max(1u, std::min(nt, 64u));
+  if (n < 50000 || nt == 1) {
+    fn((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> ts;
+  const int64_t chunk = (n + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    const int64_t a = (int64_t)t * chunk, b = std::min(n, a + chunk);
+    if (a < b) ts.emplace_back(fn, a, b);
+  }
+  for (auto &th : ts) th.join();
+}
+
+// First error raised inside a parallel loop.
+struct ErrSink {
+  std::atomic<int> set{0};
+  fl_status st = FL_OK;
+  char msg[256] = "";
+  std::mutex mu;
+  void put(fl_status s, const char *fmt, long long a, long long b = 0) {
+    std::lock_guard<std::mutex> lock(mu);
+    if (set.load()) return;
+    st = s;
+    snprintf(msg, sizeof(msg), fmt, a, b);
+    set.store(1);
+  }
+};
+
+// Sort in parallel: chunks sorted concurrently, then merged pairwise.
+template <class It, class Cmp>
+void parallel_sort(It first, It last, Cmp cmp) {
+  const int64_t n = last - first;
+  unsigned nt = std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
+  if (n < 200000 || nt == 1) {
+    std::sort(first, last, cmp);
+    return;
+  }
+  std::vector<int64_t> cut;
+  for (unsigned t = 0; t <= nt; ++t) cut.push_back(n * (int64_t)t / nt);
+  {
+    std::vector<std::thread> ts;
+    for (unsigned t = 0; t < nt; ++t)
+      ts.emplace_back([&, t] { std::sort(first + cut[t], first + cut[t + 1], cmp); });
+    for (auto &th : ts) th.join();
+  }
+  while (cut.size() > 2) {
+    std::vector<int64_t> next;
+    std::vector<std::thread> ts;
+    for (size_t i = 0; i + 2 < cut.size(); i += 2) {
+      ts.emplace_back([&, i] {
+        std::inplace_merge(first + cut[i], first + cut[i + 1], first + cut[i + 2], cmp);
+      });
+      next.push_back(cut[i]);
+    }
+    if (cut.size() % 2 == 0) next.push_back(cut[cut.size() - 2]);
+    next.push_back(cut.back());
+    for (auto &th : ts) th.join();
+    cut.swap(next);
+  }
+}
+
 template <class V>
 fl_status upload(const std::vector<V> &h, V **d) {
   *d = nullptr;
@@ -279,33 +346,39 @@ void renumber_cells(const HostMesh &h, std::vector<int32_t> &order, std::vector<
       }
       ++ncomp;
     }
-    // sort by (component, tile z, tile y, tile x, z, y, x); coordinates are
-    // within [-2^20, 2^20) for any mesh below 2^31 cells per axis walk
+    // sort by (component, tile z, tile y, tile x) and, inside a tile, by
+    // (z, y, x): one packed 64-bit tile key plus a 9-bit in-tile index
     auto fdiv = [](int32_t v) { return (v >= 0) ? v / 8 : -((-v + 7) / 8); };
+    int32_t lo[3] = {0, 0, 0};
+    for (int64_t c = 0; c < C; ++c) {
+      lo[0] = std::min(lo[0], fdiv(cx[c]));
+      lo[1] = std::min(lo[1], fdiv(cy[c]));
+      lo[2] = std::min(lo[2], fdiv(cz[c]));
+    }
     struct K {
-      int32_t comp, tz, ty, tx, z, y, x, c;
+      uint64_t tile;
+      uint32_t in_tile;
+      int32_t c;
     };
     std::vector<K> ks(C);
-    for (int64_t c = 0; c < C; ++c)
-      ks[c] = {comp[c], fdiv(cz[c]), fdiv(cy[c]), fdiv(cx[c]), cz[c], cy[c], cx[c], (int32_t)c};
-    std::sort(ks.begin(), ks.end(), [](const K &a, const K &b) {
-      if (a.comp != b.comp) return a.comp < b.comp;
-      if (a.tz != b.tz) return a.tz < b.tz;
-      if (a.ty != b.ty) return a.ty < b.ty;
-      if (a.tx != b.tx) return a.tx < b.tx;
-      if (a.z != b.z) return a.z < b.z;
-      if (a.y != b.y) return a.y < b.y;
-      return a.x < b.x;
+    for (int64_t c = 0; c < C; ++c) {
+      const uint64_t tx = (uint64_t)(fdiv(cx[c]) - lo[0]);
+      const uint64_t ty = (uint64_t)(fdiv(cy[c]) - lo[1]);
+      const uint64_t tz = (uint64_t)(fdiv(cz[c]) - lo[2]);
+      // components < 2^13, tile coordinates < 2^17 each
+      const uint64_t key = ((uint64_t)comp[c] << 51) | (tz << 34) | (ty << 17) | tx;
+      const uint32_t loc = (uint32_t)(((cz[c] & 7) << 6) | ((cy[c] & 7) << 3) | (cx[c] & 7));
+      ks[c] = {key, loc, (int32_t)c};
+    }
+    parallel_sort(ks.begin(), ks.end(), [](const K &a, const K &b) {
+      return a.tile != b.tile ? a.tile < b.tile : a.in_tile < b.in_tile;
     });
     order.resize(C);
     blk_cell.push_back(0);
     for (int64_t i = 0; i < C; ++i) {
       order[i] = ks[i].c;
-      if (i > 0) {
-        const K &a = ks[i - 1], &b = ks[i];
-        const bool new_tile = a.comp != b.comp || a.tz != b.tz || a.ty != b.ty || a.tx != b.tx;
-        if (new_tile || i - blk_cell.back() >= UBLOCK) blk_cell.push_back((int32_t)i);
-      }
+      if (i > 0 && (ks[i].tile != ks[i - 1].tile || i - blk_cell.back() >= UBLOCK))
+        blk_cell.push_back((int32_t)i);
     }
     blk_cell.push_back((int32_t)C);
     return;
@@ -357,22 +430,29 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   h.c0.resize(F);
   h.c1.resize(F);
   h.n.assign(normals, normals + 3 * F);
-  for (int64_t f = 0; f < F; ++f) {
-    const int32_t a = face_cells[2 * f], b = face_cells[2 * f + 1];
-    if (a < 0 || b < 0 || a >= C || b >= C)
-      return fail(FL_EINVAL, "face %lld: cell index out of range", (long long)f);
-    if (a == b) return fail(FL_EINVAL, "face %lld: c0 == c1", (long long)f);
-    const double *nf = &normals[3 * f];
-    const double nn = dot3(nf, nf);
-    if (!(std::fabs(nn - 1.0) < 1e-9)) return fail(FL_EINVAL, "face %lld: normal is not unit", (long long)f);
-    if (!(areas[f] > 0) || !std::isfinite(areas[f])) return fail(FL_EINVAL, "face %lld: bad area", (long long)f);
-    h.c0[f] = a;
-    h.c1[f] = b;
-  }
-  for (int64_t c = 0; c < C; ++c)
-    if (!(volumes[c] > 0) || !std::isfinite(volumes[c]))
-      return fail(FL_EINVAL, "cell %lld: bad volume", (long long)c);
-  // cell -> faces
+  ErrSink err;
+  parallel_for(F, [&](int64_t lo, int64_t hi) {
+    for (int64_t f = lo; f < hi && !err.set.load(); ++f) {
+      const int32_t a = face_cells[2 * f], b = face_cells[2 * f + 1];
+      if (a < 0 || b < 0 || a >= C || b >= C)
+        return err.put(FL_EINVAL, "face %lld: cell index out of range", f);
+      if (a == b) return err.put(FL_EINVAL, "face %lld: c0 == c1", f);
+      const double *nf = &normals[3 * f];
+      if (!(std::fabs(dot3(nf, nf) - 1.0) < 1e-9))
+        return err.put(FL_EINVAL, "face %lld: normal is not unit", f);
+      if (!(areas[f] > 0) || !std::isfinite(areas[f]))
+        return err.put(FL_EINVAL, "face %lld: bad area", f);
+      h.c0[f] = a;
+      h.c1[f] = b;
+    }
+  });
+  parallel_for(C, [&](int64_t lo, int64_t hi) {
+    for (int64_t c = lo; c < hi && !err.set.load(); ++c)
+      if (!(volumes[c] > 0) || !std::isfinite(volumes[c]))
+        return err.put(FL_EINVAL, "cell %lld: bad volume", c);
+  });
+  if (err.set.load()) return fail(err.st, "%s", err.msg);
+  // cell -> faces (each list in ascending face id)
   h.cf_ptr.assign(C + 1, 0);
   for (int64_t f = 0; f < F; ++f) {
     h.cf_ptr[h.c0[f] + 1]++;
@@ -392,56 +472,66 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
       h.cf_idx[fill[h.c1[f]]++] = (int32_t)f;
     }
   }
-  // duplicate faces: same cell pair and the same oriented normal
-  for (int64_t c = 0; c < C; ++c) {
-    for (int64_t s = h.cf_ptr[c]; s < h.cf_ptr[c + 1]; ++s)
-      for (int64_t t = s + 1; t < h.cf_ptr[c + 1]; ++t) {
-        const int32_t f = h.cf_idx[s], g = h.cf_idx[t];
-        const bool same = (h.c0[f] == h.c0[g] && h.c1[f] == h.c1[g] &&
-                           dot3(&h.n[3 * f], &h.n[3 * g]) > 0.999) ||
-                          (h.c0[f] == h.c1[g] && h.c1[f] == h.c0[g] &&
-                           dot3(&h.n[3 * f], &h.n[3 * g]) < -0.999);
-        if (same) return fail(FL_EINVAL, "faces %d and %d are the same face", f, g);
-      }
-  }
-  // upstream cell and sign for both flow directions of every face
+  // duplicate faces (same cell pair and the same oriented normal), then the
+  // upstream cell and sign for both flow directions of every face, cell by
+  // cell: for each face f of cell C, the one other face j of C with
+  // n_f . n_j = +-1 (all others must be orthogonal to f)
   for (int side = 0; side < 2; ++side) {
-    h.up[side].resize(F);
-    h.sig[side].resize(F);
+    h.up[side].assign(F, -1);
+    h.sig[side].assign(F, 0);
   }
-  for (int64_t f = 0; f < F; ++f) {
-    for (int side = 0; side < 2; ++side) {
-      const int32_t Cc = side == 0 ? h.c0[f] : h.c1[f];
-      int found = 0;
-      int32_t jstar = -1;
-      double wstar = 0;
-      for (int64_t t = h.cf_ptr[Cc]; t < h.cf_ptr[Cc + 1]; ++t) {
-        const int32_t j = h.cf_idx[t];
-        if (j == f) continue;
-        const double w = dot3(&h.n[3 * f], &h.n[3 * j]);
-        if (std::fabs(w) > 0.5) {
-          ++found;
-          jstar = j;
-          wstar = w;
-        } else if (std::fabs(w) > 1e-9) {
-          return fail(FL_EUNSUPPORTED,
-                      "face %lld: a neighbouring face is neither parallel nor orthogonal "
-                      "(general polyhedral meshes are not supported)", (long long)f);
-        }
+  parallel_for(C, [&](int64_t lo, int64_t hi) {
+    double nrm[UMAXDEG][3];
+    int32_t fl_[UMAXDEG];
+    for (int64_t Cc = lo; Cc < hi && !err.set.load(); ++Cc) {
+      const int deg = (int)(h.cf_ptr[Cc + 1] - h.cf_ptr[Cc]);
+      for (int a = 0; a < deg; ++a) {
+        fl_[a] = h.cf_idx[h.cf_ptr[Cc] + a];
+        for (int d = 0; d < 3; ++d) nrm[a][d] = h.n[3 * (int64_t)fl_[a] + d];
       }
-      if (found != 1)
-        return fail(FL_EUNSUPPORTED, "face %lld: cell %d has %d faces opposite it (need exactly 1)",
-                    (long long)f, Cc, found);
-      if (std::fabs(std::fabs(wstar) - 1.0) > 1e-9)
-        return fail(FL_EUNSUPPORTED, "face %lld: opposite face is not parallel", (long long)f);
-      const bool jc1 = (h.c1[jstar] == Cc);
-      h.up[side][f] = jc1 ? h.c0[jstar] : h.c1[jstar];
-      // d_U = s w (theta_{j,c1} - theta_{j,c0}) = sigma (theta_C - theta_U)
-      const int s = side == 0 ? 1 : -1;
-      const int w = wstar > 0 ? 1 : -1;
-      h.sig[side][f] = (int8_t)(s * w * (jc1 ? 1 : -1));
+      for (int a = 0; a < deg; ++a)
+        for (int b = a + 1; b < deg; ++b) {
+          const int32_t f = fl_[a], g = fl_[b];
+          const double w = dot3(nrm[a], nrm[b]);
+          const bool same = (h.c0[f] == h.c0[g] && h.c1[f] == h.c1[g] && w > 0.999) ||
+                            (h.c0[f] == h.c1[g] && h.c1[f] == h.c0[g] && w < -0.999);
+          if (same) return err.put(FL_EINVAL, "faces %lld and %lld are the same face", f, g);
+        }
+      for (int a = 0; a < deg; ++a) {
+        const int32_t f = fl_[a];
+        int found = 0, bstar = -1;
+        double wstar = 0;
+        for (int b = 0; b < deg; ++b) {
+          if (b == a) continue;
+          const double w = dot3(nrm[a], nrm[b]);
+          if (std::fabs(w) > 0.5) {
+            ++found;
+            bstar = b;
+            wstar = w;
+          } else if (std::fabs(w) > 1e-9) {
+            return err.put(FL_EUNSUPPORTED,
+                           "face %lld: a neighbouring face is neither parallel nor orthogonal "
+                           "(general polyhedral meshes are not supported)", f);
+          }
+        }
+        if (found != 1)
+          return err.put(FL_EUNSUPPORTED, "face %lld: %lld faces of its cell are opposite it "
+                         "(need exactly 1)", f, found);
+        if (std::fabs(std::fabs(wstar) - 1.0) > 1e-9)
+          return err.put(FL_EUNSUPPORTED, "face %lld: opposite face is not parallel", f);
+        const int32_t j = fl_[bstar];
+        // side 0: C is c0 of f (flow c0 -> c1); side 1: C is c1 of f
+        const int side = (h.c0[f] == Cc) ? 0 : 1;
+        const bool jc1 = (h.c1[j] == Cc);
+        h.up[side][f] = jc1 ? h.c0[j] : h.c1[j];
+        // d_U = s w (theta_{j,c1} - theta_{j,c0}) = sigma (theta_C - theta_U)
+        const int sgn = side == 0 ? 1 : -1;
+        const int w = wstar > 0 ? 1 : -1;
+        h.sig[side][f] = (int8_t)(sgn * w * (jc1 ? 1 : -1));
+      }
     }
-  }
+  });
+  if (err.set.load()) return fail(err.st, "%s", err.msg);
   // ---- internal numbering
   std::vector<int32_t> order, blk_cell;
   const bool renum = (flags & FL_RENUMBER) != 0;
@@ -456,22 +546,28 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   }
   std::vector<int32_t> cell_new(C);
   for (int64_t i = 0; i < C; ++i) cell_new[order[i]] = (int32_t)i;
-  // faces: by the lower internal cell, then by user id (stable)
+  // faces: by the lower internal cell, then by user id (a stable counting
+  // sort on the owner cell)
   std::vector<int32_t> face_order(F);
-  std::iota(face_order.begin(), face_order.end(), 0);
   if (renum) {
-    std::stable_sort(face_order.begin(), face_order.end(), [&](int32_t a, int32_t b) {
-      const int32_t ka = std::min(cell_new[h.c0[a]], cell_new[h.c1[a]]);
-      const int32_t kb = std::min(cell_new[h.c0[b]], cell_new[h.c1[b]]);
-      return ka < kb;
-    });
+    std::vector<int64_t> cnt(C + 1, 0);
+    std::vector<int32_t> owner(F);
+    for (int64_t f = 0; f < F; ++f) {
+      owner[f] = std::min(cell_new[h.c0[f]], cell_new[h.c1[f]]);
+      cnt[owner[f] + 1]++;
+    }
+    for (int64_t c = 0; c < C; ++c) cnt[c + 1] += cnt[c];
+    for (int64_t f = 0; f < F; ++f) face_order[cnt[owner[f]]++] = (int32_t)f;
+  } else {
+    std::iota(face_order.begin(), face_order.end(), 0);
   }
   std::vector<int32_t> face_new(F);
   for (int64_t i = 0; i < F; ++i) face_new[face_order[i]] = (int32_t)i;
   // per-face records in internal numbering
   std::vector<int4> c4(F);
   std::vector<double> area_i(F), vol_i(C), ivol_i(C);
-  for (int64_t f = 0; f < F; ++f) {
+  parallel_for(F, [&](int64_t lo, int64_t hi) {
+  for (int64_t f = lo; f < hi; ++f) {
     const int32_t fi = face_new[f];
     int4 r;
     r.x = cell_new[h.c0[f]];
@@ -481,6 +577,7 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
     c4[fi] = r;
     area_i[fi] = areas[f];
   }
+  });
   for (int64_t c = 0; c < C; ++c) {
     vol_i[cell_new[c]] = volumes[c];
     ivol_i[cell_new[c]] = 1.0 / volumes[c];
@@ -500,15 +597,12 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
       icf[fill[c4[f].y]++] = (int32_t)f;
     }
   }
-  // block entry lists and per-cell slots
+  // block entry lists and per-cell slots: blocks are independent, so the
+  // lists are built in parallel (count, prefix sum, fill)
   const int nb = (int)blk_cell.size() - 1;
-  std::vector<int32_t> blk_entry(nb + 1, 0), ent_face;
-  std::vector<int4> ent_cells;
+  std::vector<int32_t> blk_entry(nb + 1, 0);
   std::vector<uint16_t> slots((size_t)C * UMAXDEG, 0xFFFF);
-  ent_face.reserve((size_t)(F * 1.3) + 16);
-  int max_entries = 0;
-  std::vector<int32_t> list;
-  for (int b = 0; b < nb; ++b) {
+  auto block_list = [&](int b, std::vector<int32_t> &list) {
     const int32_t cb = blk_cell[b], ce = blk_cell[b + 1];
     list.clear();
     for (int32_t c = cb; c < ce; ++c)
@@ -520,26 +614,44 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
         list.push_back(f);
       }
     std::sort(list.begin(), list.end());
-    if ((int)list.size() > 0x7FFF)
-      return fail(FL_EUNSUPPORTED, "block %d has %zu faces", b, list.size());
-    blk_entry[b] = (int32_t)ent_face.size();
-    for (size_t q = 0; q < list.size(); ++q) {
-      ent_face.push_back(list[q]);
-      ent_cells.push_back(c4[list[q]]);
+  };
+  parallel_for(nb, [&](int64_t lo, int64_t hi) {
+    std::vector<int32_t> list;
+    for (int64_t b = lo; b < hi; ++b) {
+      block_list((int)b, list);
+      blk_entry[b + 1] = (int32_t)list.size();
     }
-    max_entries = std::max(max_entries, (int)list.size());
-    for (int32_t c = cb; c < ce; ++c) {
-      int k = 0;
-      for (int64_t t = icf_ptr[c]; t < icf_ptr[c + 1]; ++t) {
-        const int32_t f = icf[t];
-        const size_t pos = std::lower_bound(list.begin(), list.end(), f) - list.begin();
-        uint16_t s16 = (uint16_t)pos;
-        if (c4[f].y == c) s16 |= 0x8000u;  // sigma = -1 on c1
-        slots[(size_t)c * UMAXDEG + k++] = s16;
+  });
+  int max_entries = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (blk_entry[b + 1] > 0x7FFF)
+      return fail(FL_EUNSUPPORTED, "block %d has %d faces", b, blk_entry[b + 1]);
+    max_entries = std::max(max_entries, (int)blk_entry[b + 1]);
+    blk_entry[b + 1] += blk_entry[b];
+  }
+  std::vector<int32_t> ent_face(blk_entry[nb]);
+  std::vector<int4> ent_cells(blk_entry[nb]);
+  parallel_for(nb, [&](int64_t lo, int64_t hi) {
+    std::vector<int32_t> list;
+    for (int64_t b = lo; b < hi; ++b) {
+      block_list((int)b, list);
+      const int32_t e0 = blk_entry[b];
+      for (size_t q = 0; q < list.size(); ++q) {
+        ent_face[e0 + q] = list[q];
+        ent_cells[e0 + q] = c4[list[q]];
+      }
+      for (int32_t c = blk_cell[b]; c < blk_cell[b + 1]; ++c) {
+        int k = 0;
+        for (int64_t t = icf_ptr[c]; t < icf_ptr[c + 1]; ++t) {
+          const int32_t f = icf[t];
+          const size_t pos = std::lower_bound(list.begin(), list.end(), f) - list.begin();
+          uint16_t s16 = (uint16_t)pos;
+          if (c4[f].y == c) s16 |= 0x8000u;  // sigma = -1 on c1
+          slots[(size_t)c * UMAXDEG + k++] = s16;
+        }
       }
     }
-  }
-  blk_entry[nb] = (int32_t)ent_face.size();
+  });
 
   fl_mesh *m = new (std::nothrow) fl_mesh();
   if (!m) return fail(FL_ENOMEM, "host allocation failed");
