@@ -1,24 +1,27 @@
 // fl_struct_tma.cu -- FP32 fused limited-convection stage with TMA-staged
-// planes, for periodic Cartesian meshes with nx % 4 == 0, nx >= 32 and (when
-// y is active) ny >= 8; other shapes use the kernel of fl_structured.cu.
+// planes, for periodic Cartesian meshes with nx % 4 == 0, nx >= 128 and
+// ny >= 8; other shapes use the kernel of fl_structured.cu.
 //
 // Same method as fl_structured.cu (Valle et al., Algorithm 4 with the
-// limited face values of Algorithm 1, Sweby's stencil on Cartesian grids);
-// this variant is built for the bandwidth-bound FP32 case:
-//   * one thread per cell of a 32 x 8 column, streaming through z;
-//   * for every plane, one elected thread issues the TMA tile copies
-//     (cp.async.bulk.tensor) of the plane's theta tile and its periodic halos
-//     (4-wide x boxes and 2-row y boxes at wrapped coordinates), the three
-//     u_f tiles with their -x / -y halo faces and theta^n, all completing on
-//     the slot's mbarrier; a ring of 4 slots keeps three planes in flight
-//     beyond the one being computed;
-//   * the z neighbours of a column come from plain loads two planes ahead;
-//   * each thread evaluates both x faces and both y faces of its cell
-//     (recomputing a neighbour's face costs a few FP32 operations and saves
-//     the shared-memory exchange and its barriers); the z face below comes
-//     from the previous plane in a register.  The two threads that evaluate
-//     a face do so with the same code on the same values, so the flux is
-//     bit-identical on both sides and the update conserves;
+// limited face values of Algorithm 1, Sweby's stencil on Cartesian grids).
+// FP32 is bandwidth-bound on this part, so the kernel is built to spend few
+// instructions per cell and keep several planes of loads in flight:
+//   * a CTA owns a 128 x 8 column of cells and streams through z; a thread
+//     owns four consecutive x cells of one row (128-bit loads and stores);
+//   * one elected thread issues, per plane, the TMA tile copies
+//     (cp.async.bulk.tensor) of the theta tile and its periodic halos
+//     (4-wide x boxes, one-row y boxes at wrapped coordinates), the u_f
+//     tiles with their -x / -y halo faces and theta^n, completing on the
+//     slot's mbarrier; a ring of 3 slots keeps two planes in flight;
+//   * x neighbours move between lanes by warp shuffles (only the warp-edge
+//     lanes read the halo boxes); each x face is evaluated once, the -x
+//     face of a lane's first cell arriving by shuffle from the lane to its
+//     left (lane 0 evaluates its own);
+//   * each thread evaluates both y faces of its cells (the +y face of one
+//     row is the -y face of the next, computed by another warp from the same
+//     values with the same code, so both sides see bit-identical fluxes) and
+//     the +z face; the -z face is the previous plane's, kept in a register;
+//   * the limiter runs on FP32 min/max (limited_face_native);
 //   * one barrier per plane, before the slot is refilled.
 // Every mbarrier wait is bounded: on expiry the CTA records FL_ETIMEOUT in
 // the mesh status word, waits (bounded again) for its copies in flight and
@@ -34,20 +37,20 @@ namespace fl {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, RING = 4;
+constexpr int TX = 128, VX = 4, LANES = TX / VX, TY = 8, RING = 3;
 // slot layout (bytes); every TMA destination is 128-byte aligned
-constexpr int OFF_TH = 0;      // [8][32] theta
-constexpr int OFF_XL = 1024;   // [8][4]  theta x0-4 .. x0-1
-constexpr int OFF_XR = 1152;   // [8][4]  theta x0+w .. x0+w+3
-constexpr int OFF_YT = 1280;   // [2][32] theta rows y0-2, y0-1
-constexpr int OFF_YB = 1536;   // [2][32] theta rows y0+h, y0+h+1
-constexpr int OFF_UX = 1792;   // [8][32] u of +x faces
-constexpr int OFF_UXH = 2816;  // [8][4]  u of x faces x0-4 .. x0-1
-constexpr int OFF_UY = 2944;   // [8][32] u of +y faces
-constexpr int OFF_UYH = 3968;  // [2][32] u of y faces of rows y0-2, y0-1
-constexpr int OFF_UZ = 4224;   // [8][32] u of +z faces
-constexpr int OFF_THN = 5248;  // [8][32] theta^n
-constexpr int SLOT = 6272;
+constexpr int OFF_TH = 0;       // [8][128] theta
+constexpr int OFF_XL = 4096;    // [8][4]   theta x0-4 .. x0-1
+constexpr int OFF_XR = 4224;    // [8][4]   theta x0+w .. x0+w+3
+constexpr int OFF_YT = 4352;    // [2][128] theta rows y0-2, y0-1
+constexpr int OFF_YB = 5376;    // [2][128] theta rows y0+h, y0+h+1 (one box each)
+constexpr int OFF_UX = 6400;    // [8][128] u of +x faces
+constexpr int OFF_UXH = 10496;  // [8][4]   u of x faces x0-4 .. x0-1
+constexpr int OFF_UY = 10624;   // [8][128] u of +y faces
+constexpr int OFF_UYH = 14720;  // [1][128] u of y faces of row y0-1
+constexpr int OFF_UZ = 15232;   // [8][128] u of +z faces
+constexpr int OFF_THN = 19328;  // [8][128] theta^n
+constexpr int SLOT = 23424;
 constexpr long long WAIT_LIMIT = 1LL << 22;  // try_wait polls before giving up
 
 struct TParams {
@@ -55,7 +58,7 @@ struct TParams {
   const float *u;
   float *y;
   int nx, ny, nz;
-  int act_x, act_y, act_z;
+  int act_z;
   int bx_u, by_u, bz_u;  // u_f block of each axis
   long long uz_off;
   float cx, cy, cz, a, b;
@@ -117,21 +120,29 @@ __device__ __forceinline__ int wrapv(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// flux of a face from its Delta a, the two candidate upstream Deltas and
+// the two candidate upwind values (picked by the sign of u)
 template <int LIM>
-__device__ __forceinline__ float flux(float u, float thC, float a, float b, bool sp) {
-  return face_flux(u, limited_face<float, LIM>(thC, a, b, sp));
+__device__ __forceinline__ float flux(float u, float thC_pos, float thC_neg, float a, float b_pos,
+                                      float b_neg) {
+  const bool sp = upwind_positive(u);
+  return __fmul_rn(u, limited_face_native<LIM>(sp ? thC_pos : thC_neg, a, sp ? b_pos : b_neg, sp));
+}
+
+__device__ __forceinline__ float4 ld4(const unsigned char *base, int off_bytes) {
+  return *reinterpret_cast<const float4 *>(base + off_bytes);
 }
 
 template <int LIM, int SEED>
-__global__ void __launch_bounds__(TX *TY) k_struct_stage_tma(
+__global__ void __launch_bounds__(LANES *TY, 3) k_struct_stage_tma(
     const TParams p, const __grid_constant__ CUtensorMap m_th,
-    const __grid_constant__ CUtensorMap m_thx, const __grid_constant__ CUtensorMap m_thy,
-    const __grid_constant__ CUtensorMap m_u, const __grid_constant__ CUtensorMap m_ux,
-    const __grid_constant__ CUtensorMap m_uy, const __grid_constant__ CUtensorMap m_thn) {
-  using F = FT<float>;
+    const __grid_constant__ CUtensorMap m_thx, const __grid_constant__ CUtensorMap m_thy2,
+    const __grid_constant__ CUtensorMap m_thy1, const __grid_constant__ CUtensorMap m_u,
+    const __grid_constant__ CUtensorMap m_ux, const __grid_constant__ CUtensorMap m_uy1,
+    const __grid_constant__ CUtensorMap m_thn) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[RING];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  const int lane = threadIdx.x, ty = threadIdx.y, tid = lane + LANES * ty;
   int bid = blockIdx.x;
   const int bx = bid % p.tiles_x;
   bid /= p.tiles_x;
@@ -142,9 +153,10 @@ __global__ void __launch_bounds__(TX *TY) k_struct_stage_tma(
   const int z1 = min(z0 + p.zchunk, p.nz);
   const int L = z1 - z0;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
-  const int w = min(TX, nx - x0), h = min(TY, ny - y0);
-  const bool valid = tx < w && ty < h;
-  const bool ax = p.act_x, ay = p.act_y, az = p.act_z;
+  const int w = min(TX, nx - x0), h = min(TY, ny - y0);  // w is a multiple of 4
+  const int last_lane = w / VX - 1;
+  const bool valid = lane <= last_lane && ty < h;
+  const bool az = p.act_z;
 
   // ---- producer: plane q (relative to z0) into slot q % RING
   auto issue = [&](int q) {
@@ -152,27 +164,23 @@ __global__ void __launch_bounds__(TX *TY) k_struct_stage_tma(
     unsigned char *s = smem + slot * SLOT;
     uint64_t *bar = &bars[slot];
     const int pz = z0 + q;
-    uint32_t bytes = 1024;
-    if (ax) bytes += 256 + 1024 + 128;
-    if (ay) bytes += 512 + 1024 + 256;
-    if (az) bytes += 1024;
-    if (SEED == 1) bytes += 1024;
+    uint32_t bytes = 4096 + 256 + 1024 + 1024 + 4096 + 128 + 4096 + 512;
+    if (az) bytes += 4096;
+    if (SEED == 1) bytes += 4096;
     // the slot was last read through the generic proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect(bar, bytes);
     tma3(s + OFF_TH, &m_th, bar, x0, y0, pz);
-    if (ax) {
-      tma3(s + OFF_XL, &m_thx, bar, wrapv(x0 - 4, nx), y0, pz);
-      tma3(s + OFF_XR, &m_thx, bar, wrapv(x0 + w, nx), y0, pz);
-      tma4(s + OFF_UX, &m_u, bar, x0, y0, pz, p.bx_u);
-      tma4(s + OFF_UXH, &m_ux, bar, wrapv(x0 - 4, nx), y0, pz, p.bx_u);
-    }
-    if (ay) {
-      tma3(s + OFF_YT, &m_thy, bar, x0, wrapv(y0 - 2, ny), pz);
-      tma3(s + OFF_YB, &m_thy, bar, x0, wrapv(y0 + h, ny), pz);
-      tma4(s + OFF_UY, &m_u, bar, x0, y0, pz, p.by_u);
-      tma4(s + OFF_UYH, &m_uy, bar, x0, wrapv(y0 - 2, ny), pz, p.by_u);
-    }
+    tma3(s + OFF_XL, &m_thx, bar, wrapv(x0 - 4, nx), y0, pz);
+    tma3(s + OFF_XR, &m_thx, bar, wrapv(x0 + w, nx), y0, pz);
+    tma3(s + OFF_YT, &m_thy2, bar, x0, wrapv(y0 - 2, ny), pz);
+    // the two rows below may straddle the periodic end: one box each
+    tma3(s + OFF_YB, &m_thy1, bar, x0, wrapv(y0 + h, ny), pz);
+    tma3(s + OFF_YB + 512, &m_thy1, bar, x0, wrapv(y0 + h + 1, ny), pz);
+    tma4(s + OFF_UX, &m_u, bar, x0, y0, pz, p.bx_u);
+    tma4(s + OFF_UXH, &m_ux, bar, wrapv(x0 - 4, nx), y0, pz, p.bx_u);
+    tma4(s + OFF_UY, &m_u, bar, x0, y0, pz, p.by_u);
+    tma4(s + OFF_UYH, &m_uy1, bar, x0, wrapv(y0 - 1, ny), pz, p.by_u);
     if (az) tma4(s + OFF_UZ, &m_u, bar, x0, y0, pz, p.bz_u);
     if (SEED == 1) tma3(s + OFF_THN, &m_thn, bar, x0, y0, pz);
   };
@@ -194,107 +202,164 @@ __global__ void __launch_bounds__(TX *TY) k_struct_stage_tma(
   if (tid == 0)
     for (int q = 0; q < min(RING, L); ++q) issue(q);
 
-  // ---- z window by plain loads (column clamped for invalid threads)
+  // ---- z window of the thread's four cells by plain 128-bit loads
   const long long plane = (long long)nx * ny;
-  const long long col = (long long)min(x0 + tx, nx - 1) + (long long)nx * min(y0 + ty, ny - 1);
-  auto X = [&](int k) { return p.x[col + plane * wrapv(k, nz)]; };
-  float th0 = X(z0), thp1 = 0.f, thp2 = 0.f, pf = 0.f, dz_m1 = 0.f, dz_0 = 0.f, fz_prev = 0.f;
+  const int cxv = min(x0 + VX * lane, nx - VX), cyv = min(y0 + ty, ny - 1);
+  const long long col = (long long)cxv + (long long)nx * cyv;
+  auto X4 = [&](int k) {
+    return *reinterpret_cast<const float4 *>(p.x + col + plane * wrapv(k, nz));
+  };
+  float th0[4], thp1[4] = {0, 0, 0, 0}, thp2[4] = {0, 0, 0, 0}, dzm[4] = {0, 0, 0, 0},
+        dz0[4] = {0, 0, 0, 0}, fzp[4] = {0, 0, 0, 0};
+  float4 pf = make_float4(0, 0, 0, 0);
+  {
+    const float4 c0 = X4(z0);
+    th0[0] = c0.x;
+    th0[1] = c0.y;
+    th0[2] = c0.z;
+    th0[3] = c0.w;
+  }
   if (az) {
-    const float tm2 = X(z0 - 2), tm1 = X(z0 - 1);
-    thp1 = X(z0 + 1);
-    thp2 = X(z0 + 2);
-    pf = X(z0 + 3);
-    const float d_m2 = F::sub(tm1, tm2);
-    dz_m1 = F::sub(th0, tm1);
-    dz_0 = F::sub(thp1, th0);
-    const float uzm = p.u[p.uz_off + col + plane * wrapv(z0 - 1, nz)];
-    const bool sp = upwind_positive(uzm);
-    fz_prev = flux<LIM>(uzm, sp ? tm1 : th0, dz_m1, sp ? d_m2 : dz_0, sp);
+    const float4 m2 = X4(z0 - 2), m1 = X4(z0 - 1), p1 = X4(z0 + 1), p2 = X4(z0 + 2);
+    pf = X4(z0 + 3);
+    const float4 um = *reinterpret_cast<const float4 *>(p.u + p.uz_off + col +
+                                                         plane * wrapv(z0 - 1, nz));
+    const float tm2[4] = {m2.x, m2.y, m2.z, m2.w}, tm1[4] = {m1.x, m1.y, m1.z, m1.w};
+    const float tp1[4] = {p1.x, p1.y, p1.z, p1.w}, tp2[4] = {p2.x, p2.y, p2.z, p2.w};
+    const float uzm[4] = {um.x, um.y, um.z, um.w};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      thp1[v] = tp1[v];
+      thp2[v] = tp2[v];
+      const float d_m2 = __fsub_rn(tm1[v], tm2[v]);
+      dzm[v] = __fsub_rn(th0[v], tm1[v]);
+      dz0[v] = __fsub_rn(thp1[v], th0[v]);
+      fzp[v] = flux<LIM>(uzm[v], tm1[v], th0[v], dzm[v], d_m2, dz0[v]);
+    }
   }
   {
-    const bool ok = (L > 0) ? mbar_wait(&bars[0], 0) : true;
+    const bool ok = mbar_wait(&bars[0], 0);
     if (__syncthreads_or(!ok)) {
       bail(0, min(RING, L));
       return;
     }
   }
 
+  const int rowb = ty * TX * 4 + lane * VX * 4;  // byte offset of the thread's cells in a row tile
   for (int q = 0; q < L; ++q) {
     const int k = z0 + q;
     const unsigned char *s = smem + (q % RING) * SLOT;
-    const float *sth = reinterpret_cast<const float *>(s + OFF_TH);
-    // next z neighbour two planes ahead (plain load, used next iteration)
-    float pf_next = 0.f;
-    if (az && q + 1 < L) pf_next = X(k + 4);
-    float acc;
-    if (SEED == 0) acc = th0;
-    else if (SEED == 1)
-      acc = F::fma(p.a, reinterpret_cast<const float *>(s + OFF_THN)[ty * TX + tx], F::mul(p.b, th0));
-    else acc = 0.f;
-    if (ax) {
+    float4 pf_next = make_float4(0, 0, 0, 0);
+    if (az && q + 1 < L) pf_next = X4(k + 4);
+    float acc[4];
+    if (SEED == 1) {
+      const float4 tn = ld4(s, OFF_THN + rowb);
+      const float tnv[4] = {tn.x, tn.y, tn.z, tn.w};
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v] = __fmaf_rn(p.a, tnv[v], __fmul_rn(p.b, th0[v]));
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v] = th0[v];
+    }
+    // ------------------------------------------------------ x faces
+    {
+      const float4 c = ld4(s, OFF_TH + rowb);
+      float t[8];  // theta at offsets -2 .. 5 from the first cell
+      t[2] = c.x;
+      t[3] = c.y;
+      t[4] = c.z;
+      t[5] = c.w;
+      const float l2 = __shfl_up_sync(0xffffffffu, c.z, 1);
+      const float l1 = __shfl_up_sync(0xffffffffu, c.w, 1);
+      const float r0 = __shfl_down_sync(0xffffffffu, c.x, 1);
+      const float r1 = __shfl_down_sync(0xffffffffu, c.y, 1);
       const float *xl = reinterpret_cast<const float *>(s + OFF_XL) + ty * 4;
       const float *xr = reinterpret_cast<const float *>(s + OFF_XR) + ty * 4;
-      const float *row = sth + ty * TX;
-      float t[5];
+      t[0] = (lane == 0) ? xl[2] : l2;
+      t[1] = (lane == 0) ? xl[3] : l1;
+      t[6] = (lane == last_lane) ? xr[0] : r0;
+      t[7] = (lane == last_lane) ? xr[1] : r1;
+      float d[7];  // d[m + 2] = Delta of face m (between offsets m and m + 1)
 #pragma unroll
-      for (int d = -2; d <= 2; ++d) {
-        const int c = tx + d;
-        t[d + 2] = (c < 0) ? xl[4 + c] : ((c < w) ? row[c] : xr[min(c - w, 3)]);
-      }
-      const float *ux = reinterpret_cast<const float *>(s + OFF_UX) + ty * TX;
-      const float up = ux[tx];
-      const float um = (tx > 0) ? ux[tx - 1] : reinterpret_cast<const float *>(s + OFF_UXH)[ty * 4 + 3];
-      const float dm2 = F::sub(t[1], t[0]), dm1 = F::sub(t[2], t[1]);
-      const float d0 = F::sub(t[3], t[2]), dp1 = F::sub(t[4], t[3]);
-      const bool spm = upwind_positive(um), spp = upwind_positive(up);
-      const float fm = flux<LIM>(um, spm ? t[1] : t[2], dm1, spm ? dm2 : d0, spm);
-      const float fp = flux<LIM>(up, spp ? t[2] : t[3], d0, spp ? dm1 : dp1, spp);
-      acc = F::fma(-p.cx, fp, acc);
-      acc = F::fma(p.cx, fm, acc);
-    }
-    if (ay) {
-      const float *yt = reinterpret_cast<const float *>(s + OFF_YT);
-      const float *yb = reinterpret_cast<const float *>(s + OFF_YB);
-      float t[5];
+      for (int m = -2; m <= 4; ++m) d[m + 2] = __fsub_rn(t[m + 3], t[m + 2]);
+      const float4 ux = ld4(s, OFF_UX + rowb);
+      const float uv[4] = {ux.x, ux.y, ux.z, ux.w};
+      float fx[5];  // fx[m + 1] = flux of face m, m = -1 .. 3
 #pragma unroll
-      for (int d = -2; d <= 2; ++d) {
-        const int r = ty + d;
-        t[d + 2] = (r < 0) ? yt[(2 + r) * TX + tx]
-                           : ((r < h) ? sth[r * TX + tx] : yb[min(r - h, 1) * TX + tx]);
+      for (int m = 0; m < 4; ++m)
+        fx[m + 1] = flux<LIM>(uv[m], t[m + 2], t[m + 3], d[m + 2], d[m + 1], d[m + 3]);
+      fx[0] = __shfl_up_sync(0xffffffffu, fx[4], 1);
+      if (lane == 0) {
+        const float um = reinterpret_cast<const float *>(s + OFF_UXH)[ty * 4 + 3];
+        fx[0] = flux<LIM>(um, t[1], t[2], d[1], d[0], d[2]);
       }
-      const float *uy = reinterpret_cast<const float *>(s + OFF_UY);
-      const float up = uy[ty * TX + tx];
-      const float um = (ty > 0) ? uy[(ty - 1) * TX + tx]
-                                : reinterpret_cast<const float *>(s + OFF_UYH)[TX + tx];
-      const float dm2 = F::sub(t[1], t[0]), dm1 = F::sub(t[2], t[1]);
-      const float d0 = F::sub(t[3], t[2]), dp1 = F::sub(t[4], t[3]);
-      const bool spm = upwind_positive(um), spp = upwind_positive(up);
-      const float fm = flux<LIM>(um, spm ? t[1] : t[2], dm1, spm ? dm2 : d0, spm);
-      const float fp = flux<LIM>(up, spp ? t[2] : t[3], d0, spp ? dm1 : dp1, spp);
-      acc = F::fma(-p.cy, fp, acc);
-      acc = F::fma(p.cy, fm, acc);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        acc[v] = __fmaf_rn(-p.cx, fx[v + 1], acc[v]);
+        acc[v] = __fmaf_rn(p.cx, fx[v], acc[v]);
+      }
     }
-    float fz = 0.f, dz_p1 = 0.f;
-    if (az) {
-      const float uz = reinterpret_cast<const float *>(s + OFF_UZ)[ty * TX + tx];
-      dz_p1 = F::sub(thp2, thp1);
-      const bool sp = upwind_positive(uz);
-      fz = flux<LIM>(uz, sp ? th0 : thp1, dz_0, sp ? dz_m1 : dz_p1, sp);
-      acc = F::fma(-p.cz, fz, acc);
-      acc = F::fma(p.cz, fz_prev, acc);
+    // ------------------------------------------------------ y faces
+    {
+      float4 r4[5];  // rows ty-2 .. ty+2 at the thread's four columns
+#pragma unroll
+      for (int dd = -2; dd <= 2; ++dd) {
+        const int r = ty + dd;
+        int off;
+        if (r < 0) off = OFF_YT + (2 + r) * TX * 4;
+        else if (r < h) off = OFF_TH + r * TX * 4;
+        else off = OFF_YB + min(r - h, 1) * TX * 4;
+        r4[dd + 2] = ld4(s, off + lane * VX * 4);
+      }
+      const float4 up4 = ld4(s, OFF_UY + rowb);
+      const float4 um4 = (ty > 0) ? ld4(s, OFF_UY + rowb - TX * 4) : ld4(s, OFF_UYH + lane * VX * 4);
+      const float upv[4] = {up4.x, up4.y, up4.z, up4.w}, umv[4] = {um4.x, um4.y, um4.z, um4.w};
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float yv[5] = {(&r4[0].x)[v], (&r4[1].x)[v], (&r4[2].x)[v], (&r4[3].x)[v],
+                             (&r4[4].x)[v]};
+        const float dm2 = __fsub_rn(yv[1], yv[0]), dm1 = __fsub_rn(yv[2], yv[1]);
+        const float d0 = __fsub_rn(yv[3], yv[2]), dp1 = __fsub_rn(yv[4], yv[3]);
+        const float fm = flux<LIM>(umv[v], yv[1], yv[2], dm1, dm2, d0);
+        const float fp = flux<LIM>(upv[v], yv[2], yv[3], d0, dm1, dp1);
+        acc[v] = __fmaf_rn(-p.cy, fp, acc[v]);
+        acc[v] = __fmaf_rn(p.cy, fm, acc[v]);
+      }
     }
-    if (valid) p.y[col + plane * k] = acc;
-    // rotate the z window
+    // ------------------------------------------------------ z face
+    float dzp[4] = {0, 0, 0, 0}, fz[4] = {0, 0, 0, 0};
     if (az) {
-      fz_prev = fz;
-      dz_m1 = dz_0;
-      dz_0 = dz_p1;
-      th0 = thp1;
-      thp1 = thp2;
-      thp2 = pf;
+      const float4 uz4 = ld4(s, OFF_UZ + rowb);
+      const float uzv[4] = {uz4.x, uz4.y, uz4.z, uz4.w};
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        dzp[v] = __fsub_rn(thp2[v], thp1[v]);
+        fz[v] = flux<LIM>(uzv[v], th0[v], thp1[v], dz0[v], dzm[v], dzp[v]);
+        acc[v] = __fmaf_rn(-p.cz, fz[v], acc[v]);
+        acc[v] = __fmaf_rn(p.cz, fzp[v], acc[v]);
+      }
+    }
+    if (valid)
+      *reinterpret_cast<float4 *>(p.y + col + plane * k) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    // ------------------------------------------------------ rotate z
+    if (az) {
+      const float pv[4] = {pf.x, pf.y, pf.z, pf.w};
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        fzp[v] = fz[v];
+        dzm[v] = dz0[v];
+        dz0[v] = dzp[v];
+        th0[v] = thp1[v];
+        thp1[v] = thp2[v];
+        thp2[v] = pv[v];
+      }
       pf = pf_next;
     } else if (q + 1 < L) {
-      th0 = X(k + 1);
+      const float4 c0 = X4(k + 1);
+      th0[0] = c0.x;
+      th0[1] = c0.y;
+      th0[2] = c0.z;
+      th0[3] = c0.w;
     }
     // wait for the next plane, then let the producer refill this slot
     const bool ok = (q + 1 < L) ? mbar_wait(&bars[(q + 1) % RING], parity(q + 1)) : true;
@@ -339,8 +404,14 @@ template <int LIM, int SEED>
 cudaError_t launch(const TParams &p, const CUtensorMap *maps, unsigned grid, cudaStream_t st) {
   auto k = k_struct_stage_tma<LIM, SEED>;
   const int smem = RING * SLOT;
-  k<<<grid, dim3(TX, TY), smem, st>>>(p, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
-                                      maps[6]);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k<<<grid, dim3(LANES, TY), smem, st>>>(p, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
+                                         maps[6], maps[7]);
   return cudaGetLastError();
 }
 
@@ -362,8 +433,8 @@ cudaError_t launch_lim(int lim, const TParams &p, const CUtensorMap *maps, unsig
 
 bool struct_tma_eligible(const fl_mesh *m, const StageArgs &s) {
   if (m->kind != 0 || s.seed == 2) return false;
-  if (m->nx % 4 != 0 || m->nx < 32 || m->ny < 8) return false;
-  if (!m->act[0] || !m->status) return false;
+  if (m->nx % 4 != 0 || m->nx < TX || m->ny < TY) return false;
+  if (!m->status) return false;
   const uintptr_t mask = 15;
   if (((uintptr_t)s.x & mask) || ((uintptr_t)s.u & mask) || ((uintptr_t)s.y & mask)) return false;
   if (s.seed == 1 && ((uintptr_t)s.thn & mask)) return false;
@@ -378,12 +449,14 @@ cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cuda
   const cuuint64_t s3[2] = {(cuuint64_t)nx * 4, plane * 4};
   const cuuint64_t d4[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nblk};
   const cuuint64_t s4[3] = {(cuuint64_t)nx * 4, plane * 4, plane * nz * 4};
-  const cuuint32_t bmain[4] = {32, 8, 1, 1}, bx[4] = {4, 8, 1, 1}, by[4] = {32, 2, 1, 1};
-  alignas(64) CUtensorMap maps[7];
+  const cuuint32_t bmain[4] = {TX, TY, 1, 1}, bx[4] = {4, TY, 1, 1}, by2[4] = {TX, 2, 1, 1},
+                   by1[4] = {TX, 1, 1, 1};
+  alignas(64) CUtensorMap maps[8];
   bool ok = encode(&maps[0], s.x, 3, d3, s3, bmain) && encode(&maps[1], s.x, 3, d3, s3, bx) &&
-            encode(&maps[2], s.x, 3, d3, s3, by) && encode(&maps[3], s.u, 4, d4, s4, bmain) &&
-            encode(&maps[4], s.u, 4, d4, s4, bx) && encode(&maps[5], s.u, 4, d4, s4, by);
-  if (ok) ok = encode(&maps[6], s.seed == 1 ? s.thn : s.x, 3, d3, s3, bmain);
+            encode(&maps[2], s.x, 3, d3, s3, by2) && encode(&maps[3], s.x, 3, d3, s3, by1) &&
+            encode(&maps[4], s.u, 4, d4, s4, bmain) && encode(&maps[5], s.u, 4, d4, s4, bx) &&
+            encode(&maps[6], s.u, 4, d4, s4, by1) &&
+            encode(&maps[7], s.seed == 1 ? s.thn : s.x, 3, d3, s3, bmain);
   if (!ok) return cudaErrorNotSupported;  // caller falls back to the plain kernel
   TParams p;
   p.x = static_cast<const float *>(s.x);
@@ -392,8 +465,6 @@ cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cuda
   p.nx = nx;
   p.ny = ny;
   p.nz = nz;
-  p.act_x = m->act[0];
-  p.act_y = m->act[1];
   p.act_z = m->act[2];
   p.bx_u = (int)(m->u_off[0] / m->C);
   p.by_u = (int)(m->u_off[1] / m->C);
@@ -414,8 +485,10 @@ cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cuda
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_struct_stage_tma<LIM_SUPERBEE, 1>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, RING * SLOT);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_struct_stage_tma<LIM_SUPERBEE, 1>,
-                                                  TX * TY, RING * SLOT);
+                                                  LANES * TY, RING * SLOT);
     resident = sms * (per > 0 ? per : 1);
   }
   long long nch = (4LL * resident + cols - 1) / cols;
