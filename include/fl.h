@@ -219,6 +219,28 @@ fl_status fl_step_rk_adjoint(const fl_mesh *mesh, fl_limiter limiter, fl_dtype d
                              void *stream);
 
 /*
+ * The two halves of fl_step_rk_adjoint, for callers that run the forward
+ * rollout themselves (e.g. an autograd forward pass) and want the reverse
+ * sweep without rerunning the checkpointing pass:
+ *   fl_step_rk_checkpointed advances theta (in place, nsteps steps) and
+ *     stores a checkpoint every checkpoint_every steps in the workspace;
+ *   fl_step_rk_adjoint_from_checkpoints then runs the reverse sweep from
+ *     those checkpoints (same mesh, limiter, dtype, rk_order, dt, nsteps,
+ *     checkpoint_every, u_f and workspace, contents untouched in between).
+ * Workspace: fl_adjoint_workspace_size bytes.
+ */
+fl_status fl_step_rk_checkpointed(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                                  int rk_order, double dt, int64_t nsteps,
+                                  int64_t checkpoint_every, void *theta, const void *u_f,
+                                  void *workspace, size_t workspace_bytes, void *stream);
+fl_status fl_step_rk_adjoint_from_checkpoints(const fl_mesh *mesh, fl_limiter limiter,
+                                              fl_dtype dtype, int rk_order, double dt,
+                                              int64_t nsteps, int64_t checkpoint_every,
+                                              const void *u_f, const void *lambda_T,
+                                              void *lambda_0, void *workspace,
+                                              size_t workspace_bytes, void *stream);
+
+/*
  * Batched form: n independent structured meshes advanced together, one
  * persistent launch per stage over all instances.  meshes: host array of n
  * structured meshes (kept by reference; they must outlive the batch).

@@ -35,7 +35,8 @@ ABI_SYMBOLS = [
     "fl_conv_limited_apply",
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_noalloc",
     "fl_conv_limited_adjoint",
-    "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_batch_create",
+    "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_checkpointed",
+    "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
     "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_destroy",
     "fl_reduce_workspace_size", "fl_reduce_max_abs", "fl_reduce_mass",
 ]
@@ -91,6 +92,9 @@ def lib():
             "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
             "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
             "fl_step_rk_adjoint": (I, [P, I, I, I, D, I64, I64, P, P, P, P, P, SZ, P]),
+            "fl_step_rk_checkpointed": (I, [P, I, I, I, D, I64, I64, P, P, P, SZ, P]),
+            "fl_step_rk_adjoint_from_checkpoints": (I, [P, I, I, I, D, I64, I64, P, P, P, P,
+                                                         SZ, P]),
             "fl_batch_create": (I, [I, PP, PP]),
             "fl_batch_workspace_size": (I, [P, I, I, ctypes.POINTER(SZ)]),
             "fl_batch_step_rk": (I, [P, I, I, I, ctypes.POINTER(D), I64, PP, PP, P, SZ, P]),
@@ -252,6 +256,23 @@ def fl_step_rk_adjoint(mesh, limiter, dtype, rk_order, dt, nsteps, checkpoint_ev
                                     float(dt), int(nsteps), int(checkpoint_every), _ptr(theta0),
                                     _ptr(u_f), _ptr(lambda_T), _ptr(lambda_0), _ptr(workspace),
                                     int(workspace_bytes), _stream(stream)))
+
+
+def fl_step_rk_checkpointed(mesh, limiter, dtype, rk_order, dt, nsteps, checkpoint_every,
+                            theta, u_f, workspace, workspace_bytes, stream=None):
+    _check(lib().fl_step_rk_checkpointed(mesh, _lim(limiter), dtype_code(dtype), int(rk_order),
+                                         float(dt), int(nsteps), int(checkpoint_every),
+                                         _ptr(theta), _ptr(u_f), _ptr(workspace),
+                                         int(workspace_bytes), _stream(stream)))
+
+
+def fl_step_rk_adjoint_from_checkpoints(mesh, limiter, dtype, rk_order, dt, nsteps,
+                                        checkpoint_every, u_f, lambda_T, lambda_0, workspace,
+                                        workspace_bytes, stream=None):
+    _check(lib().fl_step_rk_adjoint_from_checkpoints(
+        mesh, _lim(limiter), dtype_code(dtype), int(rk_order), float(dt), int(nsteps),
+        int(checkpoint_every), _ptr(u_f), _ptr(lambda_T), _ptr(lambda_0), _ptr(workspace),
+        int(workspace_bytes), _stream(stream)))
 
 
 def fl_batch_create(meshes):

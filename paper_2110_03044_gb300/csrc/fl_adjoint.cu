@@ -60,37 +60,113 @@ __device__ __forceinline__ int wrapi(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
-template <class T>
+// Per-face adjoint data: the weight g and the branch coefficients.  For the
+// piecewise-linear limiters the coefficients are constants of the branch, so
+// only a small branch code is kept (fewer registers for the z faces and less
+// shared memory); van Leer keeps its computed alpha, beta, 1 - alpha + beta.
+template <class T, int LIM>
 struct FaceAdj {
-  T g, al, be, c1;
-  bool sp;
+  T g;
+  int code;  // bits 0-2: branch, bit 3: s > 0
+  __device__ __forceinline__ bool sp() const { return (code & 8) != 0; }
+  // (alpha, beta, 1 - alpha + beta) of each branch; branch 0 = inactive
+  __device__ __forceinline__ T al() const {
+    const int b = code & 7;
+    if (LIM == LIM_CENTRAL) return b ? T(0.5) : T(0);
+    if (LIM == LIM_MINMOD) return b == 2 ? T(0.5) : T(0);
+    if (LIM == LIM_SUPERBEE) return b == 2 ? T(0.5) : (b == 4 ? T(1) : T(0));
+    if (LIM == LIM_SMART) return b == 1 ? T(2) : (b == 3 ? T(0.125) : T(0));
+    return T(0);
+  }
+  __device__ __forceinline__ T be() const {
+    const int b = code & 7;
+    if (LIM == LIM_MINMOD) return b == 1 ? T(0.5) : T(0);
+    if (LIM == LIM_SUPERBEE) return b == 1 ? T(1) : (b == 3 ? T(0.5) : T(0));
+    if (LIM == LIM_SMART) return b == 2 ? T(1) : (b == 3 ? T(0.375) : T(0));
+    return T(0);
+  }
+  __device__ __forceinline__ T c1() const {
+    const int b = code & 7;
+    if (LIM == LIM_CENTRAL) return b ? T(0.5) : T(1);
+    if (LIM == LIM_MINMOD) return b == 1 ? T(1.5) : (b == 2 ? T(0.5) : T(1));
+    if (LIM == LIM_SUPERBEE)
+      return b == 1 ? T(2) : (b == 2 ? T(0.5) : (b == 3 ? T(1.5) : (b == 4 ? T(0) : T(1))));
+    if (LIM == LIM_SMART) return b == 1 ? T(-1) : (b == 2 ? T(2) : (b == 3 ? T(1.25) : T(1)));
+    return T(1);
+  }
 };
 
+template <class T>
+struct FaceAdj<T, LIM_VANLEER> {
+  T g, a_, b_, c_;
+  bool s_;
+  __device__ __forceinline__ bool sp() const { return s_; }
+  __device__ __forceinline__ T al() const { return a_; }
+  __device__ __forceinline__ T be() const { return b_; }
+  __device__ __forceinline__ T c1() const { return c_; }
+};
+
+// branch code of limited_face for (a, b): the same bit-pattern tests
 template <class T, int LIM>
-__device__ __forceinline__ FaceAdj<T> face_adj(T u, T a, T dm1, T dp1, T mu0, T mu1, T c) {
+__device__ __forceinline__ int lin_code(T a, T b) {
   using F = FT<T>;
-  FaceAdj<T> r;
-  r.sp = upwind_positive(u);
-  limited_face_lin<T, LIM>(a, r.sp ? dm1 : dp1, r.al, r.be);
-  r.g = F::mul(F::mul(c, u), F::sub(mu1, mu0));
-  r.c1 = F::add(F::sub(T(1), r.al), r.be);
+  using U = typename F::U;
+  using I = typename F::I;
+  if (LIM == LIM_UPWIND) return 0;
+  const U A = F::bits(a);
+  const U sa = A & F::SIGN;
+  const U q = A ^ sa;
+  const U p = F::bits(b) ^ sa;
+  if (LIM == LIM_CENTRAL) return 1;
+  if (!(((I)p > 0) && (q != 0))) return 0;
+  if (LIM == LIM_MINMOD) return (p <= q) ? 1 : 2;
+  if (LIM == LIM_SUPERBEE) {
+    if (p + F::EXP1 <= q) return 1;
+    if (p <= q) return 2;
+    if (p <= q + F::EXP1) return 3;
+    return 4;
+  }
+  // LIM_SMART
+  const T m = F::fma(T(0.375), F::val(p), F::mul(T(0.125), F::val(q)));
+  const U M = F::bits(m);
+  const U t = (p <= M) ? p : M;
+  if ((q + F::EXP1) < t) return 1;
+  if (p <= M) return 2;
+  return 3;
+}
+
+// c is the axis coefficient A/V; with PRE the velocities arrive already
+// multiplied by it (one product per face saved in every adjoint stage)
+template <class T, int LIM, bool PRE>
+__device__ __forceinline__ FaceAdj<T, LIM> face_adj(T u, T a, T dm1, T dp1, T mu0, T mu1, T c) {
+  using F = FT<T>;
+  FaceAdj<T, LIM> r;
+  const bool sp = upwind_positive(u);
+  const T b = sp ? dm1 : dp1;
+  if constexpr (LIM == LIM_VANLEER) {
+    limited_face_lin<T, LIM>(a, b, r.a_, r.b_, r.c_);
+    r.s_ = sp;
+  } else {
+    r.code = lin_code<T, LIM>(a, b) | (sp ? 8 : 0);
+  }
+  r.g = PRE ? F::mul(u, F::sub(mu1, mu0)) : F::mul(F::mul(c, u), F::sub(mu1, mu0));
   return r;
 }
 
 // contribution of the four faces m = i-2 .. i+1 of an axis to cell i
-template <class T>
-__device__ __forceinline__ T gather4(T acc, const FaceAdj<T> &fm2, const FaceAdj<T> &fm1,
-                                     const FaceAdj<T> &f0, const FaceAdj<T> &fp1) {
+template <class T, int LIM>
+__device__ __forceinline__ T gather4(T acc, const FaceAdj<T, LIM> &fm2, const FaceAdj<T, LIM> &fm1,
+                                     const FaceAdj<T, LIM> &f0, const FaceAdj<T, LIM> &fp1) {
   using F = FT<T>;
-  acc = F::fma(f0.sp ? f0.c1 : f0.al, f0.g, acc);     // face i   (cell i is m)
-  acc = F::fma(fm1.sp ? fm1.al : fm1.c1, fm1.g, acc);  // face i-1 (cell i is m+1)
-  if (fp1.sp) acc = F::fma(-fp1.be, fp1.g, acc);       // face i+1, s > 0: cell i is m-1
-  if (!fm2.sp) acc = F::fma(-fm2.be, fm2.g, acc);      // face i-2, s < 0: cell i is m+2
+  acc = F::fma(f0.sp() ? f0.c1() : f0.al(), f0.g, acc);     // face i   (cell i is m)
+  acc = F::fma(fm1.sp() ? fm1.al() : fm1.c1(), fm1.g, acc);  // face i-1 (cell i is m+1)
+  if (fp1.sp()) acc = F::fma(-fp1.be(), fp1.g, acc);         // face i+1, s > 0: cell i is m-1
+  if (!fm2.sp()) acc = F::fma(-fm2.be(), fm2.g, acc);        // face i-2, s < 0: cell i is m+2
   return acc;
 }
 
-template <class T, int LIM>
-__global__ void __launch_bounds__(TX *TY) k_struct_adjoint(const AParams<T> p) {
+template <class T, int LIM, bool PRE>
+__global__ void __launch_bounds__(TX *TY, 3) k_struct_adjoint(const AParams<T> p) {
   using F = FT<T>;
   constexpr int NT = TX * TY;
   constexpr int SWT = TX + 6;  // theta row pitch (halo 3)
@@ -101,8 +177,8 @@ __global__ void __launch_bounds__(TX *TY) k_struct_adjoint(const AParams<T> p) {
   __shared__ T s_mu[(TY + 4) * SWM];
   __shared__ T s_dx[TY * (TX + 5)];  // Delta of x faces x0-3 .. x0+TX+1
   __shared__ T s_dy[(TY + 5) * TX];  // Delta of y faces y0-3 .. y0+TY+1
-  __shared__ FaceAdj<T> s_fx[TY * NXF];
-  __shared__ FaceAdj<T> s_fy[NYF * TX];
+  __shared__ FaceAdj<T, LIM> s_fx[TY * NXF];
+  __shared__ FaceAdj<T, LIM> s_fy[NYF * TX];
   __shared__ int s_wx[TX + 6];
   __shared__ int s_wy[TY + 6];
 
@@ -160,7 +236,7 @@ __global__ void __launch_bounds__(TX *TY) k_struct_adjoint(const AParams<T> p) {
 
   // ---- z prologue: faces z0-2, z0-1, z0 and the column window
   T th_k, th_k1, th_k2, d_k = T(0), d_k1 = T(0), mu_k, mu_k1 = T(0);
-  FaceAdj<T> zf_m2{}, zf_m1{}, zf_0{};
+  FaceAdj<T, LIM> zf_m2{}, zf_m1{}, zf_0{};
   auto X = [&](int k) { return p.x[col + p.plane * wrapi(k, nz)]; };
   auto MU = [&](int k) { return p.mu[col + p.plane * wrapi(k, nz)]; };
   if (need_z) {
@@ -175,9 +251,9 @@ __global__ void __launch_bounds__(TX *TY) k_struct_adjoint(const AParams<T> p) {
     mu_k = MU(z0);
     mu_k1 = MU(z0 + 1);
     const T *uz = p.u + p.uz_off + col;
-    zf_m2 = face_adj<T, LIM>(uz[p.plane * wrapi(z0 - 2, nz)], dm2, dm3, dm1, mm2, mm1, p.cz);
-    zf_m1 = face_adj<T, LIM>(uz[p.plane * wrapi(z0 - 1, nz)], dm1, dm2, d_k, mm1, mu_k, p.cz);
-    zf_0 = face_adj<T, LIM>(uz[p.plane * z0], d_k, dm1, d_k1, mu_k, mu_k1, p.cz);
+    zf_m2 = face_adj<T, LIM, PRE>(uz[p.plane * wrapi(z0 - 2, nz)], dm2, dm3, dm1, mm2, mm1, p.cz);
+    zf_m1 = face_adj<T, LIM, PRE>(uz[p.plane * wrapi(z0 - 1, nz)], dm1, dm2, d_k, mm1, mu_k, p.cz);
+    zf_0 = face_adj<T, LIM, PRE>(uz[p.plane * z0], d_k, dm1, d_k1, mu_k, mu_k1, p.cz);
   } else {
     th_k = th_k1 = th_k2 = p.x[col];
     mu_k = p.mu[col];
@@ -227,26 +303,26 @@ __global__ void __launch_bounds__(TX *TY) k_struct_adjoint(const AParams<T> p) {
         const T uf = p.u[p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 3] + pk];
         const T *dr = &s_dx[r * (TX + 5)];  // Delta_m at q+1
         const T *mr = &s_mu[(r + 2) * SWM];  // mu_m at column q
-        s_fx[it] = face_adj<T, LIM>(uf, dr[q + 1], dr[q], dr[q + 2], mr[q], mr[q + 1], p.cx);
+        s_fx[it] = face_adj<T, LIM, PRE>(uf, dr[q + 1], dr[q], dr[q + 2], mr[q], mr[q + 1], p.cx);
       }
     }
     if (need_y) {
       for (int it = tid; it < NYF * TX; it += NT) {
         const int r = it / TX, c = it - r * TX;  // face m = y0-2+r
         const T uf = p.u[p.uy_off + s_wx[c + 3] + (long long)nx * s_wy[r + 1] + pk];
-        s_fy[it] = face_adj<T, LIM>(uf, s_dy[(r + 1) * TX + c], s_dy[r * TX + c],
+        s_fy[it] = face_adj<T, LIM, PRE>(uf, s_dy[(r + 1) * TX + c], s_dy[r * TX + c],
                                     s_dy[(r + 2) * TX + c], s_mu[r * SWM + c + 2],
                                     s_mu[(r + 1) * SWM + c + 2], p.cy);
       }
     }
-    FaceAdj<T> zf_1{};
-    if (need_z) zf_1 = face_adj<T, LIM>(uz1, d_k1, d_k, d_k2, mu_k1, mu_k2, p.cz);
+    FaceAdj<T, LIM> zf_1{};
+    if (need_z) zf_1 = face_adj<T, LIM, PRE>(uz1, d_k1, d_k, d_k2, mu_k1, mu_k2, p.cz);
     __syncthreads();
     // ---------------------------------------------- gather + combine
     if (valid) {
       T acc = T(0);
       if (need_x) {
-        const FaceAdj<T> *fr = &s_fx[ty * NXF + tx];  // faces i-2 .. i+1
+        const FaceAdj<T, LIM> *fr = &s_fx[ty * NXF + tx];  // faces i-2 .. i+1
         acc = gather4(acc, fr[0], fr[1], fr[2], fr[3]);
       }
       if (need_y) {
@@ -291,7 +367,7 @@ cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t 
   p.v1 = static_cast<const T *>(s.v1);
   p.v2 = static_cast<const T *>(s.v2);
   p.out = static_cast<T *>(s.out);
-  p.u = static_cast<const T *>(s.u);
+  p.u = static_cast<const T *>(s.cu ? s.cu : s.u);
   p.nx = m->nx;
   p.ny = m->ny;
   p.nz = m->nz;
@@ -325,19 +401,62 @@ cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t 
   const int tz = (m->nz + zchunk - 1) / zchunk;
   const unsigned grid = (unsigned)(cols * tz);
   const dim3 block(TX, TY);
+#define FL_ADJ_CASE(L)                                                     \
+  case L:                                                                  \
+    if (s.cu) k_struct_adjoint<T, L, true><<<grid, block, 0, st>>>(p);     \
+    else k_struct_adjoint<T, L, false><<<grid, block, 0, st>>>(p);         \
+    break;
   switch (lim) {
-    case LIM_UPWIND: k_struct_adjoint<T, LIM_UPWIND><<<grid, block, 0, st>>>(p); break;
-    case LIM_CENTRAL: k_struct_adjoint<T, LIM_CENTRAL><<<grid, block, 0, st>>>(p); break;
-    case LIM_MINMOD: k_struct_adjoint<T, LIM_MINMOD><<<grid, block, 0, st>>>(p); break;
-    case LIM_VANLEER: k_struct_adjoint<T, LIM_VANLEER><<<grid, block, 0, st>>>(p); break;
-    case LIM_SUPERBEE: k_struct_adjoint<T, LIM_SUPERBEE><<<grid, block, 0, st>>>(p); break;
-    case LIM_SMART: k_struct_adjoint<T, LIM_SMART><<<grid, block, 0, st>>>(p); break;
+    FL_ADJ_CASE(LIM_UPWIND)
+    FL_ADJ_CASE(LIM_CENTRAL)
+    FL_ADJ_CASE(LIM_MINMOD)
+    FL_ADJ_CASE(LIM_VANLEER)
+    FL_ADJ_CASE(LIM_SUPERBEE)
+    FL_ADJ_CASE(LIM_SMART)
     default: return cudaErrorInvalidValue;
   }
+#undef FL_ADJ_CASE
   return cudaGetLastError();
 }
 
+// cu_f = (A/V)_axis u_f, keeping the sign of u_f (a product that would
+// underflow to zero keeps the smallest value of the right sign)
+template <class T>
+__global__ void k_prescale(const T *u, T *cu, long long C, int nblk, T c0, T c1, T c2) {
+  const long long n = C * nblk;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(f / C);
+    const T c = b == 0 ? c0 : (b == 1 ? c1 : c2);
+    T v = FT<T>::mul(c, u[f]);
+    if (upwind_positive(u[f]) && !upwind_positive(v)) v = FT<T>::val(1);
+    cu[f] = v;
+  }
+}
+
 }  // namespace
+
+cudaError_t struct_prescale(const fl_mesh *m, fl_dtype dt, const void *u, void *cu,
+                            cudaStream_t st) {
+  double c[3] = {1, 1, 1};
+  int nb = 0;
+  const double h[3] = {m->hx, m->hy, m->hz};
+  for (int a = 0; a < 3; ++a)
+    if (m->act[a]) c[nb++] = 1.0 / h[a];
+  if (nb == 0) return cudaSuccess;
+  const long long n = m->C * nb;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152LL * 32) blocks = 152LL * 32;
+  if (dt == FL_F64)
+    k_prescale<double><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const double *>(u),
+                                                          static_cast<double *>(cu), m->C, nb,
+                                                          c[0], c[1], c[2]);
+  else
+    k_prescale<float><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const float *>(u),
+                                                         static_cast<float *>(cu), m->C, nb,
+                                                         (float)c[0], (float)c[1], (float)c[2]);
+  return cudaGetLastError();
+}
 
 cudaError_t struct_adjoint(const fl_mesh *m, int lim, fl_dtype dt, const AdjArgs &s,
                            cudaStream_t st) {
@@ -350,7 +469,8 @@ size_t adjoint_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps, i
   const int S = (rk == 3) ? 3 : 1;
   const int64_t nck = (nsteps + every - 1) / every;
   const int64_t seg = (int64_t)S * every + 1;
-  return one * (size_t)(nck + seg + 3);
+  // checkpoints | segment stage states | 3 adjoint vectors | prescaled u_f
+  return one * (size_t)(nck + seg + 3) + align256((size_t)m->F * dsize(dt));
 }
 
 }  // namespace fl
@@ -400,10 +520,47 @@ fl_status fl_adjoint_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, int64
   return FL_OK;
 }
 
-fl_status fl_step_rk_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
-                             int64_t nsteps, int64_t every, const void *theta0, const void *u_f,
-                             const void *lambda_T, void *lambda_0, void *ws, size_t ws_bytes,
-                             void *stream) {
+}  // extern "C"
+
+namespace {
+
+// Everything the two checkpointed entry points share: argument checks and
+// the workspace layout [checkpoints | segment stage states | 3 adjoints].
+struct Sweep {
+  const fl_mesh *m;
+  int lim;
+  fl_dtype dt;
+  int rk, S;
+  double dtime;
+  int64_t nsteps, every, nck;
+  size_t one, bytes;
+  char *base;
+  const void *u;
+  cudaStream_t st;
+  void *ck(int64_t i) const { return base + one * i; }
+  void *slot(int64_t i) const { return base + one * (nck + i); }
+  void *lam(int i) const { return base + one * (nck + S * every + 1 + i); }
+  void *cu() const { return base + one * (nck + S * every + 1 + 3); }
+  cudaError_t stage(const void *x, const void *thn, void *y, int seed, double a, double b) const {
+    StageArgs s;
+    s.x = x; s.thn = thn; s.y = y; s.u = u; s.dt = dtime; s.seed = seed; s.a = a; s.b = b;
+    return struct_stage(m, lim, dt, s, st);
+  }
+  // one forward step from slot(S n) storing its stage inputs; the step's
+  // result lands in slot(S (n + 1))
+  cudaError_t fwd_step(int64_t n) const {
+    if (S == 1) return stage(slot(n), slot(n), slot(n + 1), 0, 0.0, 1.0);
+    cudaError_t r = stage(slot(3 * n), slot(3 * n), slot(3 * n + 1), 0, 0.0, 1.0);
+    if (r == cudaSuccess) r = stage(slot(3 * n + 1), slot(3 * n), slot(3 * n + 2), 1, 0.75, 0.25);
+    if (r == cudaSuccess)
+      r = stage(slot(3 * n + 2), slot(3 * n), slot(3 * n + 3), 1, 1.0 / 3.0, 2.0 / 3.0);
+    return r;
+  }
+};
+
+fl_status sweep_setup(Sweep &w, const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
+                      int64_t nsteps, int64_t every, const void *u_f, void *ws, size_t ws_bytes,
+                      void *stream) {
   FL_TRY(check_mesh(m));
   FL_TRY(check_enums(lim, dt));
   if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
@@ -411,93 +568,137 @@ fl_status fl_step_rk_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int 
   if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
   if (m->kind != 0) return fail(FL_EUNSUPPORTED, "adjoint of face-based meshes is not available");
   const size_t es = dsize(dt);
-  const size_t one = align256((size_t)m->C * es);
-  FL_TRY(check_buffer(theta0, m->C * es, "theta0"));
   FL_TRY(check_buffer(u_f, m->F * es, "u_f"));
-  FL_TRY(check_buffer(lambda_T, m->C * es, "lambda_T"));
-  FL_TRY(check_buffer(lambda_0, m->C * es, "lambda_0"));
   const size_t need = adjoint_ws_bytes(m, dt, rk, nsteps, every);
   if (ws_bytes < need) return fail(FL_EINVAL, "workspace too small: %zu < %zu", ws_bytes, need);
   if (((uintptr_t)ws & 255) != 0) return fail(FL_EINVAL, "workspace must be 256-byte aligned");
   FL_TRY(check_buffer(ws, need, "workspace"));
-  cudaStream_t st = as_stream(stream);
-  const size_t bytes = (size_t)m->C * es;
-  if (m->C == 0) return FL_OK;
-  if (nsteps == 0) {
-    cudaError_t e = cudaMemcpyAsync(lambda_0, lambda_T, bytes, cudaMemcpyDeviceToDevice, st);
-    return e == cudaSuccess ? FL_OK : cuda_fail(e, "copy");
-  }
-  const int S = (rk == 3) ? 3 : 1;
-  const int64_t nck = (nsteps + every - 1) / every;
-  char *base = static_cast<char *>(ws);
-  auto ck = [&](int64_t i) -> void * { return base + one * i; };
-  char *segb = base + one * nck;
-  auto slot = [&](int64_t i) -> void * { return segb + one * i; };
-  char *lb = segb + one * (S * every + 1);
-  void *lam = lb, *la = lb + one, *lbb = lb + 2 * one;
+  w.m = m;
+  w.lim = lim;
+  w.dt = dt;
+  w.rk = rk;
+  w.S = (rk == 3) ? 3 : 1;
+  w.dtime = dtime;
+  w.nsteps = nsteps;
+  w.every = every;
+  w.nck = (nsteps + every - 1) / every;
+  w.one = align256((size_t)m->C * es);
+  w.bytes = (size_t)m->C * es;
+  w.base = static_cast<char *>(ws);
+  w.u = u_f;
+  w.st = as_stream(stream);
+  return FL_OK;
+}
 
-  cudaError_t e = cudaSuccess;
-  // forward stage helper: y = a thn + b (x + dt R(x))
-  auto stage = [&](const void *x, const void *thn, void *y, int seed, double a, double b) {
-    StageArgs s;
-    s.x = x; s.thn = thn; s.y = y; s.u = u_f; s.dt = dtime; s.seed = seed; s.a = a; s.b = b;
-    return struct_stage(m, lim, dt, s, st);
-  };
-  // one forward step from slot(3n) (RK3) or slot(n) (Euler) storing stage inputs
-  auto fwd_step = [&](int64_t n) -> cudaError_t {
-    if (S == 1) return stage(slot(n), slot(n), slot(n + 1), 0, 0.0, 1.0);
-    cudaError_t r = stage(slot(3 * n), slot(3 * n), slot(3 * n + 1), 0, 0.0, 1.0);
-    if (r == cudaSuccess) r = stage(slot(3 * n + 1), slot(3 * n), slot(3 * n + 2), 1, 0.75, 0.25);
-    if (r == cudaSuccess)
-      r = stage(slot(3 * n + 2), slot(3 * n), slot(3 * n + 3), 1, 1.0 / 3.0, 2.0 / 3.0);
-    return r;
-  };
-  // 1) checkpoints: state at steps 0, every, 2 every, ...
-  e = cudaMemcpyAsync(ck(0), theta0, bytes, cudaMemcpyDeviceToDevice, st);
-  for (int64_t c = 1; c < nck && e == cudaSuccess; ++c) {
-    e = cudaMemcpyAsync(slot(0), ck(c - 1), bytes, cudaMemcpyDeviceToDevice, st);
-    for (int64_t n = 0; n < every && e == cudaSuccess; ++n) {
-      e = fwd_step(0);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(slot(0), slot(S), bytes, cudaMemcpyDeviceToDevice, st);
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ck(c), slot(0), bytes, cudaMemcpyDeviceToDevice, st);
+// forward rollout in the segment slots, copying theta to checkpoint c at
+// every multiple of `every`; theta0 in, theta_T out (may alias)
+cudaError_t sweep_forward(const Sweep &w, const void *theta0, void *thetaT) {
+  cudaError_t e = cudaMemcpyAsync(w.slot(0), theta0, w.bytes, cudaMemcpyDeviceToDevice, w.st);
+  for (int64_t n = 0; n < w.nsteps && e == cudaSuccess; ++n) {
+    if (n % w.every == 0)
+      e = cudaMemcpyAsync(w.ck(n / w.every), w.slot(0), w.bytes, cudaMemcpyDeviceToDevice, w.st);
+    if (e == cudaSuccess) e = w.fwd_step(0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(w.slot(0), w.slot(w.S), w.bytes, cudaMemcpyDeviceToDevice, w.st);
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(lam, lambda_T, bytes, cudaMemcpyDeviceToDevice, st);
-  // 2) segments in reverse: recompute storing stage inputs, then adjoint stages
-  for (int64_t c = nck - 1; c >= 0 && e == cudaSuccess; --c) {
-    const int64_t n0 = c * every;
-    const int64_t len = std::min<int64_t>(every, nsteps - n0);
-    e = cudaMemcpyAsync(slot(0), ck(c), bytes, cudaMemcpyDeviceToDevice, st);
-    for (int64_t n = 0; n < len && e == cudaSuccess; ++n) e = fwd_step(n);
+  if (e == cudaSuccess && thetaT != nullptr)
+    e = cudaMemcpyAsync(thetaT, w.slot(0), w.bytes, cudaMemcpyDeviceToDevice, w.st);
+  return e;
+}
+
+// reverse sweep from the checkpoints: lambda_T in, lambda_0 out
+cudaError_t sweep_reverse(const Sweep &w, const void *lambda_T, void *lambda_0) {
+  void *lam = w.lam(0), *la = w.lam(1), *lbb = w.lam(2);
+  cudaError_t e = cudaMemcpyAsync(lam, lambda_T, w.bytes, cudaMemcpyDeviceToDevice, w.st);
+  if (e == cudaSuccess) e = struct_prescale(w.m, w.dt, w.u, w.cu(), w.st);
+  for (int64_t c = w.nck - 1; c >= 0 && e == cudaSuccess; --c) {
+    const int64_t len = std::min<int64_t>(w.every, w.nsteps - c * w.every);
+    e = cudaMemcpyAsync(w.slot(0), w.ck(c), w.bytes, cudaMemcpyDeviceToDevice, w.st);
+    for (int64_t n = 0; n < len && e == cudaSuccess; ++n) e = w.fwd_step(n);
     for (int64_t n = len - 1; n >= 0 && e == cudaSuccess; --n) {
       AdjArgs a;
-      a.u = u_f;
-      a.dt = dtime;
-      if (S == 1) {
+      a.u = w.u;
+      a.cu = w.cu();
+      a.dt = w.dtime;
+      if (w.S == 1) {
         // lam' = lam + dt R'(x)^T lam
-        a.x = slot(n); a.mu = lam; a.out = la; a.b = 1.0;
-        e = struct_adjoint(m, lim, dt, a, st);
+        a.x = w.slot(n); a.mu = lam; a.out = la; a.b = 1.0;
+        e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
         void *t = lam;
         lam = la;
         la = t;
       } else {
         // stage 3: la = 2/3 (lam + dt R'(x2)^T lam)
-        a.x = slot(3 * n + 2); a.mu = lam; a.out = la; a.b = 2.0 / 3.0;
-        e = struct_adjoint(m, lim, dt, a, st);
+        a.x = w.slot(3 * n + 2); a.mu = lam; a.out = la; a.b = 2.0 / 3.0;
+        e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
         if (e != cudaSuccess) break;
         // stage 2: lbb = 1/4 (la + dt R'(x1)^T la)
-        a.x = slot(3 * n + 1); a.mu = la; a.out = lbb; a.b = 0.25;
-        e = struct_adjoint(m, lim, dt, a, st);
+        a.x = w.slot(3 * n + 1); a.mu = la; a.out = lbb; a.b = 0.25;
+        e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
         if (e != cudaSuccess) break;
         // stage 1: lam = 1/3 lam + 3/4 la + (lbb + dt R'(x0)^T lbb)
-        a.x = slot(3 * n); a.mu = lbb; a.out = lam; a.b = 1.0;
+        a.x = w.slot(3 * n); a.mu = lbb; a.out = lam; a.b = 1.0;
         a.v1 = lam; a.e1 = 1.0 / 3.0; a.v2 = la; a.e2 = 0.75;
-        e = struct_adjoint(m, lim, dt, a, st);
+        e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
       }
     }
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(lambda_0, lam, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lambda_0, lam, w.bytes, cudaMemcpyDeviceToDevice, w.st);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+fl_status fl_step_rk_checkpointed(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
+                                  double dtime, int64_t nsteps, int64_t every, void *theta,
+                                  const void *u_f, void *ws, size_t ws_bytes, void *stream) {
+  Sweep w;
+  FL_TRY(sweep_setup(w, m, lim, dt, rk, dtime, nsteps, every, u_f, ws, ws_bytes, stream));
+  FL_TRY(check_buffer(theta, m->C * dsize(dt), "theta"));
+  if (m->C == 0 || nsteps == 0) return FL_OK;
+  cudaError_t e = sweep_forward(w, theta, theta);
+  if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward");
+  return FL_OK;
+}
+
+fl_status fl_step_rk_adjoint_from_checkpoints(const fl_mesh *m, fl_limiter lim, fl_dtype dt,
+                                              int rk, double dtime, int64_t nsteps, int64_t every,
+                                              const void *u_f, const void *lambda_T,
+                                              void *lambda_0, void *ws, size_t ws_bytes,
+                                              void *stream) {
+  Sweep w;
+  FL_TRY(sweep_setup(w, m, lim, dt, rk, dtime, nsteps, every, u_f, ws, ws_bytes, stream));
+  const size_t es = dsize(dt);
+  FL_TRY(check_buffer(lambda_T, m->C * es, "lambda_T"));
+  FL_TRY(check_buffer(lambda_0, m->C * es, "lambda_0"));
+  if (m->C == 0) return FL_OK;
+  cudaError_t e = (nsteps == 0)
+                      ? cudaMemcpyAsync(lambda_0, lambda_T, w.bytes, cudaMemcpyDeviceToDevice, w.st)
+                      : sweep_reverse(w, lambda_T, lambda_0);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint sweep");
+  return FL_OK;
+}
+
+fl_status fl_step_rk_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
+                             int64_t nsteps, int64_t every, const void *theta0, const void *u_f,
+                             const void *lambda_T, void *lambda_0, void *ws, size_t ws_bytes,
+                             void *stream) {
+  Sweep w;
+  FL_TRY(sweep_setup(w, m, lim, dt, rk, dtime, nsteps, every, u_f, ws, ws_bytes, stream));
+  const size_t es = dsize(dt);
+  FL_TRY(check_buffer(theta0, m->C * es, "theta0"));
+  FL_TRY(check_buffer(lambda_T, m->C * es, "lambda_T"));
+  FL_TRY(check_buffer(lambda_0, m->C * es, "lambda_0"));
+  if (m->C == 0) return FL_OK;
+  cudaError_t e = cudaSuccess;
+  if (nsteps == 0) {
+    e = cudaMemcpyAsync(lambda_0, lambda_T, w.bytes, cudaMemcpyDeviceToDevice, w.st);
+  } else {
+    e = sweep_forward(w, theta0, nullptr);
+    if (e == cudaSuccess) e = sweep_reverse(w, lambda_T, lambda_0);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "adjoint sweep");
   return FL_OK;
 }

@@ -40,6 +40,7 @@ struct AdjArgs {
   const void *v2 = nullptr;
   void *out = nullptr;
   const void *u = nullptr;
+  const void *cu = nullptr;  // u_f pre-multiplied by A/V of its axis, or null
   double e1 = 0.0, e2 = 0.0, b = 1.0, dt = 0.0;
   int bare = 0;
 };
