@@ -137,6 +137,7 @@ def run_ours(args):
     import torch
 
     import paper_2110_03044_gb300 as fl
+    from paper_2110_03044_gb300.replicas import whole_job_rate
 
     ws_, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -179,15 +180,10 @@ def run_ours(args):
         if dist:
             dist.barrier()
         time.sleep(0.25)
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     stages = 3 * args.steps
+    # units of all ranks / the slowest rank's time (replicas: no exchange)
+    value, ms = whole_job_rate(F * stages, ev0.elapsed_time(ev1), device="cuda")
     launch_ms = ms / stages
-    face_updates = F * stages * ws_
-    value = face_updates / (ms * 1e-3)
 
     # ---- roofline of the stage kernel (all launches in the region are it)
     hbm_peak, peak_kind = peaks()
@@ -387,9 +383,18 @@ def run_config_batched(args):
 
     import paper_2110_03044_gb300 as fl
     import workloads as W
+    from paper_2110_03044_gb300.replicas import lpt_partition, whole_job_rate
+    ws_, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     fl.build()
-    dims = W.batched_box_dims()
-    boxes = [W.random_box(d, 1000 + i) for i, d in enumerate(dims)]
+    all_dims = W.batched_box_dims()
+    # boxes split across ranks by cell count (no exchange between boxes)
+    mine = lpt_partition([int(np.prod(d)) for d in all_dims], ws_)[rank]
+    dims = [all_dims[i] for i in mine]
+    boxes = [W.random_box(all_dims[i], 1000 + i) for i in mine]
     out = {}
     for dname, dt in (("f64", torch.float64), ("f32", torch.float32)):
         meshes = [fl.Mesh.structured(*d, *b[0].h) for d, b in zip(dims, boxes)]
@@ -402,11 +407,15 @@ def run_config_batched(args):
         fl.fl_batch_step_rk(batch, "vanleer", dt, 3, dts, 2, th, us, ws, nb)  # tunes once
         e0, e1 = _events()
         torch.cuda.synchronize()
+        if ws_ > 1:
+            dist.barrier()
         e0.record()
         fl.fl_batch_step_rk(batch, "vanleer", dt, 3, dts, args.steps, th, us, ws, nb)
         e1.record()
         torch.cuda.synchronize()
-        ms_b = e0.elapsed_time(e1) / args.steps
+        F = sum(mm.n_faces for mm in meshes)
+        rate_b, ms_tot = whole_job_rate(F * 3 * args.steps, e0.elapsed_time(e1), device="cuda")
+        ms_b = ms_tot / args.steps
         # separate launches: one fl_step_rk per box and step, captured in a graph
         wss = [torch.empty(fl.fl_workspace_size(mm.handle, dt, 3), dtype=torch.uint8,
                            device="cuda") for mm in meshes]
@@ -421,25 +430,33 @@ def run_config_batched(args):
                 fl.fl_step_rk(mm.handle, "vanleer", dt, 3, d, 1, t, u, w, w.numel(), s)
         g.replay()
         torch.cuda.synchronize()
+        if ws_ > 1:
+            dist.barrier()
         e0.record()
         for _ in range(args.steps):
             g.replay()
         e1.record()
         torch.cuda.synchronize()
-        ms_s = e0.elapsed_time(e1) / args.steps
-        F = sum(mm.n_faces for mm in meshes)
+        rate_s, ms_tot = whole_job_rate(F * 3 * args.steps, e0.elapsed_time(e1), device="cuda")
+        ms_s = ms_tot / args.steps
         out[dname] = {"batched_ms_per_step": ms_b, "separate_ms_per_step": ms_s,
-                      "batched_face_updates_per_s": F * 3 / (ms_b * 1e-3),
-                      "separate_face_updates_per_s": F * 3 / (ms_s * 1e-3),
+                      "batched_face_updates_per_s": rate_b,
+                      "separate_face_updates_per_s": rate_s,
                       "speedup": ms_s / ms_b}
         fl.fl_batch_destroy(batch)
         for mm in meshes:
             mm.close()
-    C = sum(int(np.prod(d)) for d in dims)
+    C = sum(int(np.prod(d)) for d in all_dims)
+    if ws_ > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
     return {"metric": "batched limited-convection face-updates/s (64 boxes, SSP-RK3)",
             "value": out["f64"]["batched_face_updates_per_s"], "unit": "face-updates/s",
-            "dtype": "f64", "results": out,
-            "config": {"workload": "64_boxes_32-128_vanleer_ssprk3", "cells": C}}
+            "n_gpus": ws_, "scaling": "strong", "dtype": "f64", "results": out,
+            "config": {"workload": "64_boxes_32-128_vanleer_ssprk3", "cells": C,
+                       "parallelism": "boxes split by LPT" if ws_ > 1 else "single"}}
 
 
 def run_config_adjoint(args):
@@ -464,7 +481,7 @@ def run_config_adjoint(args):
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
     g = torch.empty_like(th0)
     e0, e1 = _events()
-    fwd, rev = [], []
+    fwd, ckf, rev, tot = [], [], [], []
     for rep in range(max(2, args.warmup)):
         th = th0.clone()
         torch.cuda.synchronize()
@@ -473,18 +490,33 @@ def run_config_adjoint(args):
         e1.record()
         torch.cuda.synchronize()
         fwd.append(e0.elapsed_time(e1))
+        # forward rollout storing checkpoints, then the reverse sweep
+        th = th0.clone()
+        e0.record()
+        fl.fl_step_rk_checkpointed(m.handle, "superbee", torch.float64, 3, wl.dt, nsteps, every,
+                                   th, u, ws, nb)
+        e1.record()
+        torch.cuda.synchronize()
+        ckf.append(e0.elapsed_time(e1))
         lam = th - tg
         torch.cuda.synchronize()
         e0.record()
-        fl.fl_step_rk_adjoint(m.handle, "superbee", torch.float64, 3, wl.dt, nsteps, every, th0, u,
-                              lam, g, ws, nb)
+        fl.fl_step_rk_adjoint_from_checkpoints(m.handle, "superbee", torch.float64, 3, wl.dt,
+                                               nsteps, every, u, lam, g, ws, nb)
         e1.record()
         torch.cuda.synchronize()
         rev.append(e0.elapsed_time(e1))
-    f, r = min(fwd[1:]), min(rev[1:])
+        e0.record()
+        fl.fl_step_rk_adjoint(m.handle, "superbee", torch.float64, 3, wl.dt, nsteps, every, th0,
+                              u, lam, g, ws, nb)
+        e1.record()
+        torch.cuda.synchronize()
+        tot.append(e0.elapsed_time(e1))
+    f, c, r, t = min(fwd[1:]), min(ckf[1:]), min(rev[1:]), min(tot[1:])
     return {"metric": "adjoint / forward time (128^3, 200 SSP-RK3 steps, checkpoints every 20)",
             "value": r / f, "unit": "ratio", "higher_is_better": False, "forward_ms": f,
-            "reverse_ms": r, "dtype": "f64",
+            "checkpointed_forward_ms": c, "reverse_sweep_ms": r,
+            "one_call_gradient_ms": t, "gradient_over_forward": (c + r) / f, "dtype": "f64",
             "config": {"workload": "tg128_superbee_ssprk3_200steps_ckpt20"}}
 
 
@@ -571,7 +603,9 @@ def main():
         import numpy  # noqa: F401  (the config runners use np)
         fn = {"1d": run_config_1d, "unstructured": run_config_unstructured,
               "batched": run_config_batched, "adjoint": run_config_adjoint}[args.config]
-        print(json.dumps(fn(args)))
+        line = fn(args)
+        if line is not None:
+            print(json.dumps(line))
 
 
 if __name__ == "__main__":
