@@ -172,6 +172,21 @@ fl_status fl_step_rk(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype, in
                      size_t workspace_bytes, void *stream);
 
 /*
+ * fl_step_rk for a time-modulated flow: stage s of step n advects with the
+ * face velocity g[n * S + s] * u_f (S = 1 for Euler, 3 for SSP-RK3), the
+ * form of the reversing deformation flow of Section 4.1 (eq. rhodonea),
+ * whose velocity is a fixed field times cos(pi t / T).  g: host array of
+ * nsteps * S finite factors, read before the call returns.  A negative
+ * factor reverses every face's upwind side (the sign of g u_f decides, so
+ * u_f = 0 still selects -1).  Same workspace, ownership and errors as
+ * fl_step_rk; a non-finite factor returns FL_EINVAL before any launch.
+ */
+fl_status fl_step_rk_modulated(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                               int rk_order, double dt, int64_t nsteps, void *theta,
+                               const void *u_f, const double *g, void *workspace,
+                               size_t workspace_bytes, void *stream);
+
+/*
  * fl_step_rk without a workspace argument, for callers that may not allocate
  * device memory at all (plugin hosts that own the whole device memory pool,
  * real-time loops that cannot pay for an allocation's device-wide
@@ -180,7 +195,10 @@ fl_status fl_step_rk(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype, in
  * Same arguments and results as fl_step_rk; the stage buffers come from a
  * fixed area inside the library image of FL_NOALLOC_SCRATCH_BYTES per GPU,
  * held by every GPU that loads the library until the process exits.  Meshes
- * whose fl_workspace_size exceeds that return FL_EINVAL and nothing runs.
+ * whose RK stage buffers (|C| values for Euler, two blocks of |C| for SSP-RK3,
+ * each rounded up to 256 bytes) exceed that return FL_EINVAL and nothing
+ * runs.  (fl_step_rk's FP64 workspace also holds a pre-scaled copy of u_f;
+ * this entry point runs the same stages without it.)
  * The first call on each device looks up the area's device address, so make
  * it before any stream capture.  All calls share the area: calls whose GPU
  * work overlaps in time race and must be ordered by the caller.  The call

@@ -33,7 +33,8 @@ ABI_SYMBOLS = [
     "fl_last_error", "fl_version", "fl_mesh_create_structured", "fl_mesh_create",
     "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_status", "fl_mesh_destroy",
     "fl_conv_limited_apply",
-    "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_noalloc",
+    "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_modulated",
+    "fl_step_rk_noalloc",
     "fl_conv_limited_adjoint",
     "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_checkpointed",
     "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
@@ -88,6 +89,7 @@ def lib():
             "fl_face_selection": (I, [P, I, P, P, P]),
             "fl_workspace_size": (I, [P, I, I, ctypes.POINTER(SZ)]),
             "fl_step_rk": (I, [P, I, I, I, D, I64, P, P, P, SZ, P]),
+            "fl_step_rk_modulated": (I, [P, I, I, I, D, I64, P, P, P, P, SZ, P]),
             "fl_step_rk_noalloc": (I, [P, I, I, I, D, I64, P, P, P]),
             "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
             "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
@@ -226,6 +228,21 @@ def fl_step_rk(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, workspace
     _check(lib().fl_step_rk(mesh, _lim(limiter), dtype_code(dtype), int(rk_order), float(dt),
                             int(nsteps), _ptr(theta), _ptr(u_f), _ptr(workspace),
                             int(workspace_bytes), _stream(stream)))
+
+
+def fl_step_rk_modulated(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, g, workspace,
+                         workspace_bytes, stream=None):
+    """fl_step_rk where stage s of step n advects with g[n * S + s] * u_f;
+    ``g`` is a host sequence of nsteps * S floats (S = 1 Euler, 3 SSP-RK3)."""
+    import numpy as np
+    S = 1 if int(rk_order) == 1 else 3
+    gg = np.ascontiguousarray(np.asarray(g, dtype=np.float64).ravel())
+    if gg.size < int(nsteps) * S:
+        raise ValueError("need nsteps * stages velocity factors")
+    _check(lib().fl_step_rk_modulated(mesh, _lim(limiter), dtype_code(dtype), int(rk_order),
+                                      float(dt), int(nsteps), _ptr(theta), _ptr(u_f),
+                                      gg.ctypes.data_as(ctypes.c_void_p), _ptr(workspace),
+                                      int(workspace_bytes), _stream(stream)))
 
 
 def fl_step_rk_noalloc(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, stream=None):
@@ -376,6 +393,19 @@ def step_rk(mesh, limiter, theta, u_f, dt, nsteps, rk_order=3, workspace=None, s
         nbytes = workspace.numel() * workspace.element_size()
     fl_step_rk(mesh.handle, limiter, theta.dtype, rk_order, dt, nsteps, theta, u_f, workspace,
                nbytes, stream)
+    return theta
+
+
+def step_rk_modulated(mesh, limiter, theta, u_f, dt, nsteps, g, rk_order=1, workspace=None,
+                      stream=None):
+    """In-place ``nsteps`` steps on ``theta`` with the stage velocities
+    g[n * S + s] * u_f (a time-modulated flow)."""
+    if workspace is None:
+        workspace, nbytes = workspace_for(mesh, theta.dtype, rk_order, theta.device)
+    else:
+        nbytes = workspace.numel() * workspace.element_size()
+    fl_step_rk_modulated(mesh.handle, limiter, theta.dtype, rk_order, dt, nsteps, theta, u_f, g,
+                         workspace, nbytes, stream)
     return theta
 
 

@@ -36,6 +36,9 @@ namespace {
 
 constexpr int TX = 32;
 constexpr int TY = 8;
+#ifndef FL_ADJ_MINB
+#define FL_ADJ_MINB 3
+#endif
 
 template <class T>
 struct AParams {
@@ -54,6 +57,21 @@ struct AParams {
   int bare;      // 1: out = R'^T mu only
   int tiles_x, tiles_y, zchunk;
 };
+
+// asynchronous global -> shared copy of one element (no register staging)
+template <class T>
+__device__ __forceinline__ void cp_async1(T *dst, const T *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "n"(sizeof(T))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
 
 __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
@@ -104,6 +122,47 @@ struct FaceAdj<T, LIM_VANLEER> {
   __device__ __forceinline__ T al() const { return a_; }
   __device__ __forceinline__ T be() const { return b_; }
   __device__ __forceinline__ T c1() const { return c_; }
+};
+
+// Shared-memory face table in structure-of-arrays form (consecutive faces of
+// a row are read by consecutive threads: one 8-byte word per thread, no bank
+// conflicts).
+template <class T, int LIM, int N>
+struct FaceSmem {
+  T g[N];
+  int code[N];
+  __device__ __forceinline__ void put(int i, const FaceAdj<T, LIM> &f) {
+    g[i] = f.g;
+    code[i] = f.code;
+  }
+  __device__ __forceinline__ FaceAdj<T, LIM> get(int i) const {
+    FaceAdj<T, LIM> f;
+    f.g = g[i];
+    f.code = code[i];
+    return f;
+  }
+};
+
+template <class T, int N>
+struct FaceSmem<T, LIM_VANLEER, N> {
+  T g[N], a[N], b[N], c[N];
+  unsigned char s[N];
+  __device__ __forceinline__ void put(int i, const FaceAdj<T, LIM_VANLEER> &f) {
+    g[i] = f.g;
+    a[i] = f.a_;
+    b[i] = f.b_;
+    c[i] = f.c_;
+    s[i] = f.s_;
+  }
+  __device__ __forceinline__ FaceAdj<T, LIM_VANLEER> get(int i) const {
+    FaceAdj<T, LIM_VANLEER> f;
+    f.g = g[i];
+    f.a_ = a[i];
+    f.b_ = b[i];
+    f.c_ = c[i];
+    f.s_ = s[i] != 0;
+    return f;
+  }
 };
 
 // branch code of limited_face for (a, b): the same bit-pattern tests
@@ -166,7 +225,7 @@ __device__ __forceinline__ T gather4(T acc, const FaceAdj<T, LIM> &fm2, const Fa
 }
 
 template <class T, int LIM, bool PRE>
-__global__ void __launch_bounds__(TX *TY, 3) k_struct_adjoint(const AParams<T> p) {
+__global__ void __launch_bounds__(TX *TY, FL_ADJ_MINB) k_struct_adjoint(const AParams<T> p) {
   using F = FT<T>;
   constexpr int NT = TX * TY;
   constexpr int SWT = TX + 6;  // theta row pitch (halo 3)
@@ -177,8 +236,12 @@ __global__ void __launch_bounds__(TX *TY, 3) k_struct_adjoint(const AParams<T> p
   __shared__ T s_mu[(TY + 4) * SWM];
   __shared__ T s_dx[TY * (TX + 5)];  // Delta of x faces x0-3 .. x0+TX+1
   __shared__ T s_dy[(TY + 5) * TX];  // Delta of y faces y0-3 .. y0+TY+1
-  __shared__ FaceAdj<T, LIM> s_fx[TY * NXF];
-  __shared__ FaceAdj<T, LIM> s_fy[NYF * TX];
+  __shared__ FaceSmem<T, LIM, TY * NXF> s_fx;
+  __shared__ FaceSmem<T, LIM, NYF * TX> s_fy;
+  // u of the x faces (m = x0-2 .. x0+TX) and y faces (m = y0-2 .. y0+TY) of
+  // a plane, double-buffered: plane k+1 is copied in while k is processed
+  __shared__ T s_uxb[2][TY * NXF];
+  __shared__ T s_uyb[2][NYF * TX];
   __shared__ int s_wx[TX + 6];
   __shared__ int s_wy[TY + 6];
 
@@ -233,6 +296,41 @@ __global__ void __launch_bounds__(TX *TY, 3) k_struct_adjoint(const AParams<T> p
     }
   }
   const bool need_x = p.act_x, need_y = p.act_y, need_z = p.act_z;
+  // u of the plane's faces, copied one plane ahead (cp.async): every thread
+  // its own +x and +y face; threads tid < 3 (TX + TY) one halo face each (x
+  // faces x0-2, x0-1, x0+TX of every row, y faces y0-2, y0-1, y0+TY of every
+  // column)
+  int hu_slot = -1;
+  long long hu_off = 0;
+  bool hu_x = false;
+  {
+    constexpr int NUX = 3 * TY, NUT = NUX + 3 * TX;
+    static_assert(NUT <= NT, "u halo exceeds threads");
+    if (tid < NUX) {
+      if (need_x) {
+        const int r = tid / 3, k3 = tid % 3;
+        const int q = (k3 < 2) ? k3 : TX + 2;  // face x0-2+q
+        hu_slot = r * NXF + q;
+        hu_off = p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 3];
+        hu_x = true;
+      }
+    } else if (tid < NUT) {
+      if (need_y) {
+        const int t = tid - NUX;
+        const int k3 = t / TX, c = t % TX;
+        const int r = (k3 < 2) ? k3 : TY + 2;  // face y0-2+r
+        hu_slot = r * TX + c;
+        hu_off = p.uy_off + s_wx[c + 3] + (long long)nx * s_wy[r + 1];
+      }
+    }
+  }
+  auto load_u = [&](long long pk, int buf) {
+    if (need_x) cp_async1(&s_uxb[buf][ty * NXF + tx + 2], p.u + p.ux_off + col + pk);
+    if (need_y) cp_async1(&s_uyb[buf][(ty + 2) * TX + tx], p.u + p.uy_off + col + pk);
+    if (hu_slot >= 0) cp_async1(hu_x ? &s_uxb[buf][hu_slot] : &s_uyb[buf][hu_slot], p.u + hu_off + pk);
+    cp_async_commit();
+  };
+  load_u(p.plane * z0, z0 & 1);
 
   // ---- z prologue: faces z0-2, z0-1, z0 and the column window
   T th_k, th_k1, th_k2, d_k = T(0), d_k1 = T(0), mu_k, mu_k1 = T(0);
@@ -278,6 +376,13 @@ __global__ void __launch_bounds__(TX *TY, 3) k_struct_adjoint(const AParams<T> p
     s_mu[(ty + 2) * SWM + tx + 2] = mu_k;
     if (th_slot >= 0) s_th[th_slot] = hv_t;
     if (mu_slot >= 0) s_mu[mu_slot] = hv_m;
+    // this plane's u copies are complete (the barrier publishes them); the
+    // next plane's go to the other buffer, last read before the previous
+    // plane's final barrier
+    cp_async_wait_all();
+    if (k + 1 < z1) load_u(pk + p.plane, (k + 1) & 1);
+    const T *s_ux = s_uxb[k & 1];
+    const T *s_uy = s_uyb[k & 1];
     __syncthreads();
     // ---------------------------------------------- differences
     if (need_x) {
@@ -300,19 +405,19 @@ __global__ void __launch_bounds__(TX *TY, 3) k_struct_adjoint(const AParams<T> p
     if (need_x) {
       for (int it = tid; it < TY * NXF; it += NT) {
         const int r = it / NXF, q = it - r * NXF;  // face m = x0-2+q
-        const T uf = p.u[p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 3] + pk];
+        const T uf = s_ux[it];
         const T *dr = &s_dx[r * (TX + 5)];  // Delta_m at q+1
         const T *mr = &s_mu[(r + 2) * SWM];  // mu_m at column q
-        s_fx[it] = face_adj<T, LIM, PRE>(uf, dr[q + 1], dr[q], dr[q + 2], mr[q], mr[q + 1], p.cx);
+        s_fx.put(it, face_adj<T, LIM, PRE>(uf, dr[q + 1], dr[q], dr[q + 2], mr[q], mr[q + 1], p.cx));
       }
     }
     if (need_y) {
       for (int it = tid; it < NYF * TX; it += NT) {
         const int r = it / TX, c = it - r * TX;  // face m = y0-2+r
-        const T uf = p.u[p.uy_off + s_wx[c + 3] + (long long)nx * s_wy[r + 1] + pk];
-        s_fy[it] = face_adj<T, LIM, PRE>(uf, s_dy[(r + 1) * TX + c], s_dy[r * TX + c],
-                                    s_dy[(r + 2) * TX + c], s_mu[r * SWM + c + 2],
-                                    s_mu[(r + 1) * SWM + c + 2], p.cy);
+        const T uf = s_uy[it];
+        s_fy.put(it, face_adj<T, LIM, PRE>(uf, s_dy[(r + 1) * TX + c], s_dy[r * TX + c],
+                                           s_dy[(r + 2) * TX + c], s_mu[r * SWM + c + 2],
+                                           s_mu[(r + 1) * SWM + c + 2], p.cy));
       }
     }
     FaceAdj<T, LIM> zf_1{};
@@ -322,12 +427,12 @@ __global__ void __launch_bounds__(TX *TY, 3) k_struct_adjoint(const AParams<T> p
     if (valid) {
       T acc = T(0);
       if (need_x) {
-        const FaceAdj<T, LIM> *fr = &s_fx[ty * NXF + tx];  // faces i-2 .. i+1
-        acc = gather4(acc, fr[0], fr[1], fr[2], fr[3]);
+        const int i = ty * NXF + tx;  // faces i-2 .. i+1
+        acc = gather4(acc, s_fx.get(i), s_fx.get(i + 1), s_fx.get(i + 2), s_fx.get(i + 3));
       }
       if (need_y) {
-        acc = gather4(acc, s_fy[ty * TX + tx], s_fy[(ty + 1) * TX + tx],
-                      s_fy[(ty + 2) * TX + tx], s_fy[(ty + 3) * TX + tx]);
+        acc = gather4(acc, s_fy.get(ty * TX + tx), s_fy.get((ty + 1) * TX + tx),
+                      s_fy.get((ty + 2) * TX + tx), s_fy.get((ty + 3) * TX + tx));
       }
       if (need_z) acc = gather4(acc, zf_m2, zf_m1, zf_0, zf_1);
       T o;
@@ -384,19 +489,14 @@ cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t 
   p.e1 = (T)s.e1;
   p.e2 = (T)s.e2;
   p.b = (T)s.b;
-  p.bdt = (T)(s.b * s.dt);
+  p.bdt = (T)(s.cu_dt ? s.b : s.b * s.dt);
   p.bare = s.bare;
   p.tiles_x = (m->nx + TX - 1) / TX;
   p.tiles_y = (m->ny + TY - 1) / TY;
   const long long cols = (long long)p.tiles_x * p.tiles_y;
-  int zchunk = m->nz;
-  const long long want = 152LL * 8;
-  if (cols < want && m->nz > 1) {
-    long long nch = (want + cols - 1) / cols;
-    if (nch > m->nz) nch = m->nz;
-    zchunk = (int)((m->nz + nch - 1) / nch);
-    if (zchunk < 8 && m->nz >= 8) zchunk = 8;
-  }
+  const int resident = resident_ctas(
+      reinterpret_cast<const void *>(&k_struct_adjoint<T, LIM_SUPERBEE, true>), TX * TY, 0);
+  const int zchunk = pick_zchunk(cols, m->nz, resident, 3);
   p.zchunk = zchunk;
   const int tz = (m->nz + zchunk - 1) / zchunk;
   const unsigned grid = (unsigned)(cols * tz);
@@ -419,44 +519,7 @@ cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t 
   return cudaGetLastError();
 }
 
-// cu_f = (A/V)_axis u_f, keeping the sign of u_f (a product that would
-// underflow to zero keeps the smallest value of the right sign)
-template <class T>
-__global__ void k_prescale(const T *u, T *cu, long long C, int nblk, T c0, T c1, T c2) {
-  const long long n = C * nblk;
-  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n;
-       f += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(f / C);
-    const T c = b == 0 ? c0 : (b == 1 ? c1 : c2);
-    T v = FT<T>::mul(c, u[f]);
-    if (upwind_positive(u[f]) && !upwind_positive(v)) v = FT<T>::val(1);
-    cu[f] = v;
-  }
-}
-
 }  // namespace
-
-cudaError_t struct_prescale(const fl_mesh *m, fl_dtype dt, const void *u, void *cu,
-                            cudaStream_t st) {
-  double c[3] = {1, 1, 1};
-  int nb = 0;
-  const double h[3] = {m->hx, m->hy, m->hz};
-  for (int a = 0; a < 3; ++a)
-    if (m->act[a]) c[nb++] = 1.0 / h[a];
-  if (nb == 0) return cudaSuccess;
-  const long long n = m->C * nb;
-  long long blocks = (n + 255) / 256;
-  if (blocks > 152LL * 32) blocks = 152LL * 32;
-  if (dt == FL_F64)
-    k_prescale<double><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const double *>(u),
-                                                          static_cast<double *>(cu), m->C, nb,
-                                                          c[0], c[1], c[2]);
-  else
-    k_prescale<float><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const float *>(u),
-                                                         static_cast<float *>(cu), m->C, nb,
-                                                         (float)c[0], (float)c[1], (float)c[2]);
-  return cudaGetLastError();
-}
 
 cudaError_t struct_adjoint(const fl_mesh *m, int lim, fl_dtype dt, const AdjArgs &s,
                            cudaStream_t st) {
@@ -469,7 +532,7 @@ size_t adjoint_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps, i
   const int S = (rk == 3) ? 3 : 1;
   const int64_t nck = (nsteps + every - 1) / every;
   const int64_t seg = (int64_t)S * every + 1;
-  // checkpoints | segment stage states | 3 adjoint vectors | prescaled u_f
+  // checkpoints | segment stage states | 3 adjoint vectors | pre-scaled u_f
   return one * (size_t)(nck + seg + 3) + align256((size_t)m->F * dsize(dt));
 }
 
@@ -540,10 +603,18 @@ struct Sweep {
   void *ck(int64_t i) const { return base + one * i; }
   void *slot(int64_t i) const { return base + one * (nck + i); }
   void *lam(int i) const { return base + one * (nck + S * every + 1 + i); }
+  // w_f = dt (A/V) u_f when dt > 0 (the forward stages fold their flux
+  // product with it and the adjoint stages take b instead of b dt), else
+  // (A/V) u_f for the adjoint stages only
   void *cu() const { return base + one * (nck + S * every + 1 + 3); }
+  bool cu_dt() const { return dtime > 0; }
+  cudaError_t prescale() const {
+    return struct_scale_faces(m, dt, u, cu(), cu_dt() ? dtime : 1.0, st);
+  }
   cudaError_t stage(const void *x, const void *thn, void *y, int seed, double a, double b) const {
     StageArgs s;
     s.x = x; s.thn = thn; s.y = y; s.u = u; s.dt = dtime; s.seed = seed; s.a = a; s.b = b;
+    if (cu_dt()) s.w = cu();
     return struct_stage(m, lim, dt, s, st);
   }
   // one forward step from slot(S n) storing its stage inputs; the step's
@@ -593,7 +664,9 @@ fl_status sweep_setup(Sweep &w, const fl_mesh *m, int lim, fl_dtype dt, int rk, 
 // forward rollout in the segment slots, copying theta to checkpoint c at
 // every multiple of `every`; theta0 in, theta_T out (may alias)
 cudaError_t sweep_forward(const Sweep &w, const void *theta0, void *thetaT) {
-  cudaError_t e = cudaMemcpyAsync(w.slot(0), theta0, w.bytes, cudaMemcpyDeviceToDevice, w.st);
+  cudaError_t e = w.prescale();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w.slot(0), theta0, w.bytes, cudaMemcpyDeviceToDevice, w.st);
   for (int64_t n = 0; n < w.nsteps && e == cudaSuccess; ++n) {
     if (n % w.every == 0)
       e = cudaMemcpyAsync(w.ck(n / w.every), w.slot(0), w.bytes, cudaMemcpyDeviceToDevice, w.st);
@@ -610,7 +683,7 @@ cudaError_t sweep_forward(const Sweep &w, const void *theta0, void *thetaT) {
 cudaError_t sweep_reverse(const Sweep &w, const void *lambda_T, void *lambda_0) {
   void *lam = w.lam(0), *la = w.lam(1), *lbb = w.lam(2);
   cudaError_t e = cudaMemcpyAsync(lam, lambda_T, w.bytes, cudaMemcpyDeviceToDevice, w.st);
-  if (e == cudaSuccess) e = struct_prescale(w.m, w.dt, w.u, w.cu(), w.st);
+  if (e == cudaSuccess) e = w.prescale();
   for (int64_t c = w.nck - 1; c >= 0 && e == cudaSuccess; --c) {
     const int64_t len = std::min<int64_t>(w.every, w.nsteps - c * w.every);
     e = cudaMemcpyAsync(w.slot(0), w.ck(c), w.bytes, cudaMemcpyDeviceToDevice, w.st);
@@ -619,6 +692,7 @@ cudaError_t sweep_reverse(const Sweep &w, const void *lambda_T, void *lambda_0) 
       AdjArgs a;
       a.u = w.u;
       a.cu = w.cu();
+      a.cu_dt = w.cu_dt();
       a.dt = w.dtime;
       if (w.S == 1) {
         // lam' = lam + dt R'(x)^T lam

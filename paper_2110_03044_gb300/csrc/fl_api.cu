@@ -3,6 +3,10 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -96,9 +100,54 @@ fl_status check_enums(int lim, fl_dtype dt) {
   return FL_OK;
 }
 
-size_t step_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk) {
+int resident_ctas(const void *kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(kernel, dev);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int sms = 0, per = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess ||
+      per < 1)
+    per = 1;
+  cache[key] = sms * per;
+  return sms * per;
+}
+
+int pick_zchunk(long long cols, int nz, long long resident, int prologue) {
+  if (nz <= 1 || cols <= 0) return nz < 1 ? 1 : nz;
+  if (resident < 1) resident = 1;
+  long long best_cost = -1;
+  int best = nz;
+  for (int tz = 1; tz <= nz; ++tz) {
+    const int chunk = (nz + tz - 1) / tz;
+    if ((nz + chunk - 1) / chunk != tz) continue;  // each distinct chunk length once
+    const long long waves = (cols * tz + resident - 1) / resident;
+    const long long cost = waves * (chunk + prologue);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = chunk;
+    }
+  }
+  return best;
+}
+
+// RK stage buffers only (what fl_step_rk_noalloc needs)
+size_t step_stage_bytes(const fl_mesh *m, fl_dtype dt, int rk) {
   const size_t one = align256((size_t)m->C * dsize(dt));
   return rk == 3 ? 2 * one : one;
+}
+
+// stage buffers plus, where struct_step uses it, the pre-scaled velocity
+size_t step_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk) {
+  size_t b = step_stage_bytes(m, dt, rk);
+  if (struct_step_prescales(m, dt)) b += align256((size_t)m->F * dsize(dt));
+  return b;
 }
 
 }  // namespace fl
@@ -257,9 +306,14 @@ fl_status fl_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, size_t *bytes
   return FL_OK;
 }
 
-fl_status fl_step_rk(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
-                     int64_t nsteps, void *theta, const void *u_f, void *ws, size_t ws_bytes,
-                     void *stream) {
+}  // extern "C"
+
+namespace {
+
+// fl_step_rk and fl_step_rk_modulated: gfac (host, nsteps x stages) or null
+fl_status step_rk_impl(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
+                       int64_t nsteps, void *theta, const void *u_f, const double *gfac,
+                       void *ws, size_t ws_bytes, void *stream) {
   FL_TRY(check_mesh(m));
   FL_TRY(check_enums(lim, dt));
   if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
@@ -272,10 +326,17 @@ fl_status fl_step_rk(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, doub
   if (ws_bytes < need) return fail(FL_EINVAL, "workspace too small: %zu < %zu", ws_bytes, need);
   if (((uintptr_t)ws & 255) != 0) return fail(FL_EINVAL, "workspace must be 256-byte aligned");
   FL_TRY(check_buffer(ws, need, "workspace"));
+  if (gfac != nullptr) {
+    const int64_t ng = nsteps * (rk == 3 ? 3 : 1);
+    for (int64_t i = 0; i < ng; ++i)
+      if (!std::isfinite(gfac[i])) return fail(FL_EINVAL, "velocity factor %lld is not finite",
+                                               (long long)i);
+  }
   if (nsteps == 0 || m->C == 0) return FL_OK;
   cudaStream_t st = as_stream(stream);
-  if (m->kind == 1) return unstruct_step(m, lim, dt, rk, dtime, nsteps, theta, u_f, ws, st);
-  if (m->ny == 1 && m->nz == 1 && (size_t)m->nx <= line_resident_max_cells(dt)) {
+  if (m->kind == 1) return unstruct_step(m, lim, dt, rk, dtime, nsteps, theta, u_f, ws, st, gfac);
+  if (gfac == nullptr && m->ny == 1 && m->nz == 1 &&
+      (size_t)m->nx <= line_resident_max_cells(dt)) {
     cudaError_t e = line_resident(m, lim, dt, theta, u_f, nsteps, rk, dtime, st);
     if (e != cudaSuccess) return cuda_fail(e, "1D resident kernel");
     return FL_OK;
@@ -283,45 +344,28 @@ fl_status fl_step_rk(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, doub
   char *wsb = static_cast<char *>(ws);
   void *A = wsb;
   void *B = wsb + align256((size_t)m->C * es);
-  StageArgs s;
-  s.u = u_f;
-  s.dt = dtime;
-  cudaError_t e = cudaSuccess;
-  if (rk == 1) {
-    // Euler: ping-pong between theta and A (a stage reads neighbours of x
-    // while writing y, so x and y must differ)
-    void *cur = theta, *nxt = A;
-    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      s.x = cur;
-      s.thn = cur;
-      s.y = nxt;
-      s.seed = 0;
-      s.b = 1.0;
-      e = struct_stage(m, lim, dt, s, st);
-      void *t = cur;
-      cur = nxt;
-      nxt = t;
-    }
-    if (e == cudaSuccess && cur != theta)
-      e = cudaMemcpyAsync(theta, cur, m->C * es, cudaMemcpyDeviceToDevice, st);
-  } else {
-    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      // th1 = thn + dt R(thn)
-      s.x = theta; s.thn = theta; s.y = A; s.seed = 0; s.a = 0.0; s.b = 1.0;
-      e = struct_stage(m, lim, dt, s, st);
-      if (e != cudaSuccess) break;
-      // th2 = 3/4 thn + 1/4 (th1 + dt R(th1))
-      s.x = A; s.thn = theta; s.y = B; s.seed = 1; s.a = 0.75; s.b = 0.25;
-      e = struct_stage(m, lim, dt, s, st);
-      if (e != cudaSuccess) break;
-      // th^{n+1} = 1/3 thn + 2/3 (th2 + dt R(th2)); thn and y are read and
-      // written only at the thread's own cell, so y may alias thn
-      s.x = B; s.thn = theta; s.y = theta; s.seed = 1; s.a = 1.0 / 3.0; s.b = 2.0 / 3.0;
-      e = struct_stage(m, lim, dt, s, st);
-    }
-  }
+  void *W = struct_step_prescales(m, dt) ? wsb + step_stage_bytes(m, dt, rk) : nullptr;
+  const cudaError_t e =
+      struct_step(m, lim, dt, rk, dtime, nsteps, theta, u_f, A, B, W, st, gfac);
   if (e != cudaSuccess) return cuda_fail(e, "structured stage kernel");
   return FL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fl_status fl_step_rk(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
+                     int64_t nsteps, void *theta, const void *u_f, void *ws, size_t ws_bytes,
+                     void *stream) {
+  return step_rk_impl(m, lim, dt, rk, dtime, nsteps, theta, u_f, nullptr, ws, ws_bytes, stream);
+}
+
+fl_status fl_step_rk_modulated(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
+                               double dtime, int64_t nsteps, void *theta, const void *u_f,
+                               const double *g, void *ws, size_t ws_bytes, void *stream) {
+  if (g == nullptr && nsteps > 0) return fail(FL_EINVAL, "velocity factors are NULL");
+  return step_rk_impl(m, lim, dt, rk, dtime, nsteps, theta, u_f, g, ws, ws_bytes, stream);
 }
 
 size_t fl_reduce_workspace_size(void) { return reduce_ws_bytes(); }

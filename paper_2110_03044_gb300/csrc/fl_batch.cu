@@ -57,7 +57,7 @@ namespace {
 constexpr int BTY = 8;
 constexpr int MAXSTAGES = 3;
 
-template <class T, int LIM, int SEED>
+template <class T, int LIM, int SEED, bool PRE>
 __global__ void __launch_bounds__(TX *BTY, 4)
     k_batch_stage(const SParams<T> *__restrict__ params, const int2 *__restrict__ tiles,
                   int n_tiles, unsigned *counter) {
@@ -70,29 +70,38 @@ __global__ void __launch_bounds__(TX *BTY, 4)
     if (t >= n_tiles) break;
     const int2 bt = tiles[t];
     const SParams<T> p = params[bt.x];
-    stage_tile<T, LIM, SEED, BTY>(p, bt.y);
+    stage_tile<T, LIM, SEED, BTY, PRE>(p, bt.y);
   }
 }
 
-template <class T, int SEED>
+template <class T, int SEED, bool PRE>
 void *kernel_ptr(int lim) {
   switch (lim) {
-    case LIM_UPWIND: return (void *)k_batch_stage<T, LIM_UPWIND, SEED>;
-    case LIM_CENTRAL: return (void *)k_batch_stage<T, LIM_CENTRAL, SEED>;
-    case LIM_MINMOD: return (void *)k_batch_stage<T, LIM_MINMOD, SEED>;
-    case LIM_VANLEER: return (void *)k_batch_stage<T, LIM_VANLEER, SEED>;
-    case LIM_SUPERBEE: return (void *)k_batch_stage<T, LIM_SUPERBEE, SEED>;
-    case LIM_SMART: return (void *)k_batch_stage<T, LIM_SMART, SEED>;
+    case LIM_UPWIND: return (void *)k_batch_stage<T, LIM_UPWIND, SEED, PRE>;
+    case LIM_CENTRAL: return (void *)k_batch_stage<T, LIM_CENTRAL, SEED, PRE>;
+    case LIM_MINMOD: return (void *)k_batch_stage<T, LIM_MINMOD, SEED, PRE>;
+    case LIM_VANLEER: return (void *)k_batch_stage<T, LIM_VANLEER, SEED, PRE>;
+    case LIM_SUPERBEE: return (void *)k_batch_stage<T, LIM_SUPERBEE, SEED, PRE>;
+    case LIM_SMART: return (void *)k_batch_stage<T, LIM_SMART, SEED, PRE>;
   }
   return nullptr;
 }
 
-void *batch_kernel(fl_dtype dt, int lim, int seed) {
-  if (dt == FL_F64) return seed == SEED_PLAIN ? kernel_ptr<double, SEED_PLAIN>(lim)
-                                              : kernel_ptr<double, SEED_COMBINE>(lim);
-  return seed == SEED_PLAIN ? kernel_ptr<float, SEED_PLAIN>(lim)
-                            : kernel_ptr<float, SEED_COMBINE>(lim);
+// pre: FP64 boxes fold the flux product into the cell update with the
+// pre-scaled velocity w = dt (A/V) u of every box (as fl_step_rk does)
+void *batch_kernel(fl_dtype dt, int lim, int seed, bool pre) {
+  if (dt == FL_F64) {
+    if (pre)
+      return seed == SEED_PLAIN ? kernel_ptr<double, SEED_PLAIN, true>(lim)
+                                : kernel_ptr<double, SEED_COMBINE, true>(lim);
+    return seed == SEED_PLAIN ? kernel_ptr<double, SEED_PLAIN, false>(lim)
+                              : kernel_ptr<double, SEED_COMBINE, false>(lim);
+  }
+  return seed == SEED_PLAIN ? kernel_ptr<float, SEED_PLAIN, false>(lim)
+                            : kernel_ptr<float, SEED_COMBINE, false>(lim);
 }
+
+bool batch_prescales(fl_dtype dt) { return dt == FL_F64; }
 
 int tiles_x_of(const fl_mesh *m) { return (m->nx + TX - 1) / TX; }
 int tiles_y_of(const fl_mesh *m) { return (m->ny + BTY - 1) / BTY; }
@@ -152,6 +161,8 @@ SParams<T> box_params(const fl_mesh *m, int zc, const void *x, const void *thn, 
   p.cz = (T)(sc / m->hz);
   p.a = (T)a;
   p.b = (T)bcoef;
+  p.g = (T)1;
+  p.flip = 0;
   p.tiles_x = tiles_x_of(m);
   p.tiles_y = tiles_y_of(m);
   p.zchunk = zchunk_of(m, zc);
@@ -160,10 +171,18 @@ SParams<T> box_params(const fl_mesh *m, int zc, const void *x, const void *thn, 
 
 size_t param_size(fl_dtype dt) { return dt == FL_F64 ? sizeof(SParams<double>) : sizeof(SParams<float>); }
 
-// Fill the staging table: stage s of box i at index s * n + i.
+// Workspace of box i: its RK stage buffers, then (pre) its w_f.
+size_t box_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk) {
+  size_t t = (rk == 3 ? 2 : 1) * align256((size_t)m->C * dsize(dt));
+  if (batch_prescales(dt)) t += align256((size_t)m->F * dsize(dt));
+  return t;
+}
+
+// Fill the staging table: stage s of box i at index s * n + i.  With pre,
+// every stage reads the box's w_f (left in its workspace by prescale_boxes).
 template <class T>
 void fill_params(fl_batch *b, int rk, int zc, const double *dtv, void *const *theta,
-                 const void *const *u, char *ws, size_t es) {
+                 const void *const *u, char *ws, size_t es, bool pre) {
   SParams<T> *h = static_cast<SParams<T> *>(b->h_params);
   size_t off = 0;
   for (int i = 0; i < b->n; ++i) {
@@ -171,68 +190,80 @@ void fill_params(fl_batch *b, int rk, int zc, const double *dtv, void *const *th
     const size_t one = align256((size_t)m->C * es);
     void *A = ws + off;
     void *B = ws + off + one;
-    off += (rk == 3 ? 2 : 1) * one;
+    const void *uw = pre ? static_cast<const void *>(ws + off + (rk == 3 ? 2 : 1) * one) : u[i];
+    off += box_ws_bytes(m, es == 8 ? FL_F64 : FL_F32, rk);
     if (rk == 3) {
-      h[0 * b->n + i] = box_params<T>(m, zc, theta[i], theta[i], A, u[i], dtv[i], SEED_PLAIN, 0.0, 1.0);
-      h[1 * b->n + i] = box_params<T>(m, zc, A, theta[i], B, u[i], dtv[i], SEED_COMBINE, 0.75, 0.25);
+      h[0 * b->n + i] = box_params<T>(m, zc, theta[i], theta[i], A, uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
+      h[1 * b->n + i] = box_params<T>(m, zc, A, theta[i], B, uw, dtv[i], SEED_COMBINE, 0.75, 0.25);
       h[2 * b->n + i] =
-          box_params<T>(m, zc, B, theta[i], theta[i], u[i], dtv[i], SEED_COMBINE, 1.0 / 3.0, 2.0 / 3.0);
+          box_params<T>(m, zc, B, theta[i], theta[i], uw, dtv[i], SEED_COMBINE, 1.0 / 3.0, 2.0 / 3.0);
     } else {  // Euler: even step theta -> A, odd step A -> theta
-      h[0 * b->n + i] = box_params<T>(m, zc, theta[i], theta[i], A, u[i], dtv[i], SEED_PLAIN, 0.0, 1.0);
-      h[1 * b->n + i] = box_params<T>(m, zc, A, A, theta[i], u[i], dtv[i], SEED_PLAIN, 0.0, 1.0);
+      h[0 * b->n + i] = box_params<T>(m, zc, theta[i], theta[i], A, uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
+      h[1 * b->n + i] = box_params<T>(m, zc, A, A, theta[i], uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
     }
   }
 }
 
 size_t batch_ws_bytes(const fl_batch *b, fl_dtype dt, int rk) {
   size_t t = 0;
-  for (const fl_mesh *m : b->meshes) t += (rk == 3 ? 2 : 1) * align256((size_t)m->C * dsize(dt));
+  for (const fl_mesh *m : b->meshes) t += box_ws_bytes(m, dt, rk);
   return t;
 }
 
-int persistent_grid(fl_dtype dt, int lim, int seed) {
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel(dt, lim, seed), TX * BTY, 0);
-  return std::max(1, sms * std::max(per, 1));
+// w_f = dt_i (A/V) u_f of every box into its workspace (once per call)
+cudaError_t prescale_boxes(fl_batch *b, fl_dtype dt, int rk, const double *dtv,
+                           const void *const *u, char *ws, cudaStream_t st) {
+  size_t off = 0;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+    const fl_mesh *m = b->meshes[i];
+    const size_t one = align256((size_t)m->C * dsize(dt));
+    e = struct_scale_faces(m, dt, u[i], ws + off + (rk == 3 ? 2 : 1) * one, dtv[i], st);
+    off += box_ws_bytes(m, dt, rk);
+  }
+  return e;
+}
+
+int persistent_grid(fl_dtype dt, int lim, int seed, bool pre) {
+  return resident_ctas(batch_kernel(dt, lim, seed, pre), TX * BTY, 0);
 }
 
 // Enqueue one launch of stage s (seed) on st.
-cudaError_t enqueue_stage(fl_batch *b, fl_dtype dt, int lim, int s, int seed, int2 *tiles, int nt,
-                          cudaStream_t st) {
+cudaError_t enqueue_stage(fl_batch *b, fl_dtype dt, int lim, int s, int seed, bool pre,
+                          int2 *tiles, int nt, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b->d_counters + s, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const char *params = static_cast<const char *>(b->d_params) + (size_t)s * b->n * param_size(dt);
   unsigned *ctr = b->d_counters + s;
   void *args[] = {(void *)&params, (void *)&tiles, (void *)&nt, (void *)&ctr};
-  return cudaLaunchKernel(batch_kernel(dt, lim, seed), dim3(persistent_grid(dt, lim, seed)),
-                          dim3(TX, BTY), args, 0, st);
+  return cudaLaunchKernel(batch_kernel(dt, lim, seed, pre),
+                          dim3(persistent_grid(dt, lim, seed, pre)), dim3(TX, BTY), args, 0, st);
 }
 
 // Stage launches of one step (RK3: 3 stages; Euler: 2 steps, even and odd).
-cudaError_t enqueue_step(fl_batch *b, fl_dtype dt, int lim, int rk, int2 *tiles, int nt,
+cudaError_t enqueue_step(fl_batch *b, fl_dtype dt, int lim, int rk, bool pre, int2 *tiles, int nt,
                          cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (rk == 3) {
-    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);
-    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_COMBINE, tiles, nt, st);
-    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 2, SEED_COMBINE, tiles, nt, st);
+    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_COMBINE, pre, tiles, nt, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 2, SEED_COMBINE, pre, tiles, nt, st);
   } else {
-    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);
-    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_PLAIN, tiles, nt, st);
+    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_PLAIN, pre, tiles, nt, st);
   }
   return e;
 }
 
 fl_status upload_params(fl_batch *b, fl_dtype dt, int rk, int zc, const double *dtv,
-                        void *const *theta, const void *const *u, void *ws, cudaStream_t st) {
+                        void *const *theta, const void *const *u, void *ws, bool pre,
+                        cudaStream_t st) {
   // the staging buffer may still feed the previous call's copy
   if (cudaEventSynchronize(b->params_done) != cudaSuccess) return fail(FL_ECUDA, "event sync");
   if (dt == FL_F64)
-    fill_params<double>(b, rk, zc, dtv, theta, u, static_cast<char *>(ws), 8);
+    fill_params<double>(b, rk, zc, dtv, theta, u, static_cast<char *>(ws), 8, pre);
   else
-    fill_params<float>(b, rk, zc, dtv, theta, u, static_cast<char *>(ws), 4);
+    fill_params<float>(b, rk, zc, dtv, theta, u, static_cast<char *>(ws), 4, pre);
   const size_t bytes = (size_t)MAXSTAGES * b->n * param_size(dt);
   cudaError_t e = cudaMemcpyAsync(b->d_params, b->h_params, bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(b->params_done, st);
@@ -241,7 +272,7 @@ fl_status upload_params(fl_batch *b, fl_dtype dt, int rk, int zc, const double *
 
 // Autotune the z chunk with timed stage-1 launches (write workspace only).
 fl_status tune(fl_batch *b, fl_dtype dt, int lim, int rk, const double *dtv, void *const *theta,
-               const void *const *u, void *ws, cudaStream_t st, int *best) {
+               const void *const *u, void *ws, bool pre, cudaStream_t st, int *best) {
   const int cand[] = {8, 16, 32, 64};
   float best_ms = 1e30f;
   *best = 16;
@@ -253,10 +284,11 @@ fl_status tune(fl_batch *b, fl_dtype dt, int lim, int rk, const double *dtv, voi
     int nt;
     fl_status s = get_tiles(b, zc, &tiles, &nt);
     if (s != FL_OK) return s;
-    if ((s = upload_params(b, dt, rk, zc, dtv, theta, u, ws, st)) != FL_OK) return s;
-    cudaError_t e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);  // warm-up
+    if ((s = upload_params(b, dt, rk, zc, dtv, theta, u, ws, pre, st)) != FL_OK) return s;
+    cudaError_t e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);  // warm-up
     cudaEventRecord(e0, st);
-    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+      e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);
     cudaEventRecord(e1, st);
     if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
       cudaEventDestroy(e0);
@@ -348,12 +380,19 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
   if ((s = check_buffer(ws, need, "workspace")) != FL_OK) return s;
   if (nsteps == 0) return FL_OK;
   cudaStream_t st = as_stream(stream);
-  // z chunk: tuned once per (limiter, dtype, rk)
-  const auto tkey = std::make_tuple((int)lim, (int)dt, rk);
+  // pre-scaled velocities (FP64) when every dt is positive (keeps signs)
+  bool pre = batch_prescales(dt);
+  for (int i = 0; i < b->n && pre; ++i) pre = dtv[i] > 0;
+  if (pre) {
+    const cudaError_t e = prescale_boxes(b, dt, rk, dtv, u_f, static_cast<char *>(ws), st);
+    if (e != cudaSuccess) return cuda_fail(e, "velocity pre-scaling");
+  }
+  // z chunk: tuned once per (limiter, dtype, rk, pre)
+  const auto tkey = std::make_tuple((int)lim, (int)dt * 2 + (pre ? 1 : 0), rk);
   int zc;
   auto tit = b->tuned.find(tkey);
   if (tit == b->tuned.end()) {
-    if ((s = tune(b, dt, lim, rk, dtv, theta, u_f, ws, st, &zc)) != FL_OK) return s;
+    if ((s = tune(b, dt, lim, rk, dtv, theta, u_f, ws, pre, st, &zc)) != FL_OK) return s;
     b->tuned[tkey] = zc;
   } else {
     zc = tit->second;
@@ -361,9 +400,9 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
   int2 *tiles;
   int nt;
   if ((s = get_tiles(b, zc, &tiles, &nt)) != FL_OK) return s;
-  if ((s = upload_params(b, dt, rk, zc, dtv, theta, u_f, ws, st)) != FL_OK) return s;
-  // one graph per (limiter, dtype, rk, z chunk): a step's stage launches
-  const auto gkey = std::make_tuple((int)lim, (int)dt, rk, zc);
+  if ((s = upload_params(b, dt, rk, zc, dtv, theta, u_f, ws, pre, st)) != FL_OK) return s;
+  // one graph per (limiter, dtype + pre, rk, z chunk): a step's stage launches
+  const auto gkey = std::make_tuple((int)lim, (int)dt * 2 + (pre ? 1 : 0), rk, zc);
   cudaGraphExec_t exec = nullptr;
   auto git = b->graphs.find(gkey);
   if (git != b->graphs.end()) {
@@ -375,7 +414,7 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = enqueue_step(b, dt, lim, rk, tiles, nt, cap);
+      cudaError_t e2 = enqueue_step(b, dt, lim, rk, pre, tiles, nt, cap);
       e = cudaStreamEndCapture(cap, &g);
       if (e2 != cudaSuccess) e = e2;
     }
@@ -393,13 +432,13 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
     // even stage alone and copies A back
     for (int64_t n = 0; n + 1 < nsteps && e == cudaSuccess; n += 2) e = cudaGraphLaunch(exec, st);
     if (e == cudaSuccess && (nsteps & 1)) {
-      e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, tiles, nt, st);
+      e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);
       size_t off = 0;
       for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         const fl_mesh *m = b->meshes[i];
         e = cudaMemcpyAsync(theta[i], static_cast<char *>(ws) + off, m->C * es,
                             cudaMemcpyDeviceToDevice, st);
-        off += align256((size_t)m->C * es);
+        off += box_ws_bytes(m, dt, rk);
       }
     }
   }

@@ -29,6 +29,18 @@ fl_status cuda_fail(cudaError_t e, const char *what);
     if (e_ != cudaSuccess) return ::fl::cuda_fail(e_, what); \
   } while (0)
 
+// ------------------------------------------------------------ launch shape
+// CTAs of `kernel` (with `threads` threads and `smem` dynamic bytes) that fit
+// on the current device at once: occupancy per SM x SMs, cached per kernel.
+int resident_ctas(const void *kernel, int threads, size_t smem);
+
+// z-chunk length for a kernel that streams `cols` tile columns through nz
+// planes, one CTA per (column, chunk): the chunk minimising
+//   ceil(CTAs / resident) x (planes per chunk + prologue)
+// i.e. whole waves of co-resident CTAs, each paying its z-prologue (the
+// planes it loads before its first output plane) once.
+int pick_zchunk(long long cols, int nz, long long resident, int prologue);
+
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 inline size_t dsize(fl_dtype t) { return t == FL_F64 ? 8 : 4; }
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }

@@ -15,7 +15,9 @@ struct StageArgs {
   void *y = nullptr;
   void *thf = nullptr;
   const void *u = nullptr;
+  const void *w = nullptr;  // dt (A/V) u_f, or null (see struct_scale_faces)
   double a = 0.0, b = 1.0, dt = 0.0;
+  double g = 1.0;  // velocity factor of the stage: the flow is g u_f
   int seed = 0;
 };
 
@@ -25,6 +27,17 @@ cudaError_t struct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs
 // returns cudaErrorNotSupported when the tensor maps cannot be built
 bool struct_tma_eligible(const fl_mesh *m, const StageArgs &s);
 cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cudaStream_t st);
+// w_f = (fac / h_axis) u_f over the mesh's face blocks (sign kept on underflow)
+cudaError_t struct_scale_faces(const fl_mesh *m, fl_dtype dt, const void *u, void *w, double fac,
+                               cudaStream_t st);
+// whether struct_step uses a pre-scaled velocity buffer for this mesh / dtype
+bool struct_step_prescales(const fl_mesh *m, fl_dtype dt);
+// nsteps Euler / SSP-RK3 steps through struct_stage; A (and B for RK3) hold
+// |C| values each; W (|F| values, or null) receives dt (A/V) u_f; gfac (host,
+// nsteps x stages, or null) gives each stage's velocity factor
+cudaError_t struct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
+                        int64_t nsteps, void *theta, const void *u, void *A, void *B, void *W,
+                        cudaStream_t st, const double *gfac = nullptr);
 size_t line_resident_max_cells(fl_dtype dt);
 cudaError_t line_resident(const fl_mesh *m, int lim, fl_dtype dt, void *theta, const void *u,
                           int64_t nsteps, int rk, double dtime, cudaStream_t st);
@@ -41,6 +54,7 @@ struct AdjArgs {
   void *out = nullptr;
   const void *u = nullptr;
   const void *cu = nullptr;  // u_f pre-multiplied by A/V of its axis, or null
+  int cu_dt = 0;             // cu also carries the factor dt (then b replaces b dt)
   double e1 = 0.0, e2 = 0.0, b = 1.0, dt = 0.0;
   int bare = 0;
 };

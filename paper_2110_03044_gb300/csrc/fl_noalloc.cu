@@ -36,7 +36,7 @@ namespace fl {
 fl_status check_buffer(const void *p, size_t bytes, const char *name);
 fl_status check_mesh(const fl_mesh *m);
 fl_status check_enums(int lim, fl_dtype dt);
-size_t step_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk);
+size_t step_stage_bytes(const fl_mesh *m, fl_dtype dt, int rk);
 }  // namespace fl
 
 namespace {
@@ -83,7 +83,9 @@ extern "C" fl_status fl_step_rk_noalloc(const fl_mesh *m, fl_limiter lim, fl_dty
   const size_t es = dsize(dt);
   if ((st = check_buffer(theta, m->C * es, "theta")) != FL_OK) return st;
   if ((st = check_buffer(u_f, m->F * es, "u_f")) != FL_OK) return st;
-  const size_t need = step_ws_bytes(m, dt, rk);
+  // the stage buffers only: this entry point runs without the pre-scaled
+  // velocity buffer of fl_step_rk
+  const size_t need = step_stage_bytes(m, dt, rk);
   if (need > (size_t)FL_NOALLOC_SCRATCH_BYTES)
     return fail(FL_EINVAL,
                 "mesh needs %zu bytes of scratch but the built-in area holds %zu; "
@@ -102,31 +104,7 @@ extern "C" fl_status fl_step_rk_noalloc(const fl_mesh *m, fl_limiter lim, fl_dty
   char *wsb = static_cast<char *>(ws);
   void *A = wsb;
   void *B = wsb + align256((size_t)m->C * es);
-  StageArgs a;
-  a.u = u_f;
-  a.dt = dtime;
-  cudaError_t e = cudaSuccess;
-  if (rk == 1) {
-    void *cur = theta, *nxt = A;
-    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      a.x = cur; a.thn = cur; a.y = nxt; a.seed = 0; a.b = 1.0;
-      e = struct_stage(m, lim, dt, a, s);
-      void *t = cur;
-      cur = nxt;
-      nxt = t;
-    }
-    if (e == cudaSuccess && cur != theta)
-      e = cudaMemcpyAsync(theta, cur, m->C * es, cudaMemcpyDeviceToDevice, s);
-  } else {
-    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      a.x = theta; a.thn = theta; a.y = A; a.seed = 0; a.a = 0.0; a.b = 1.0;
-      if ((e = struct_stage(m, lim, dt, a, s)) != cudaSuccess) break;
-      a.x = A; a.thn = theta; a.y = B; a.seed = 1; a.a = 0.75; a.b = 0.25;
-      if ((e = struct_stage(m, lim, dt, a, s)) != cudaSuccess) break;
-      a.x = B; a.thn = theta; a.y = theta; a.seed = 1; a.a = 1.0 / 3.0; a.b = 2.0 / 3.0;
-      e = struct_stage(m, lim, dt, a, s);
-    }
-  }
+  const cudaError_t e = struct_step(m, lim, dt, rk, dtime, nsteps, theta, u_f, A, B, nullptr, s);
   if (e != cudaSuccess) return cuda_fail(e, "structured stage kernel");
   return FL_OK;
 }

@@ -25,6 +25,8 @@ struct SParams {
   long long plane;  // nx*ny
   T cx, cy, cz;     // multiply (phi_minus - phi_plus) of each axis
   T a, b;           // seed = a*thn + b*x  (COMBINE) or x (PLAIN) or 0 (APPLY)
+  T g;              // MOD: velocity factor of the stage (see stage_tile)
+  unsigned long long flip;  // sign mask toggled into u before the upwind test (g < 0)
   int tiles_x, tiles_y, zchunk;
 };
 
@@ -35,18 +37,31 @@ __device__ __forceinline__ int wrap(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
-template <class T, int LIM, int SEED, int TY>
+// PRE: p.u holds w_f = dt (A/V) u_f (pre-scaled once per call, same sign as
+// u_f) and p.cx/cy/cz are unused.  Each face then keeps theta_f instead of
+// its flux, and a cell adds w theta_f of its six faces with one fma each:
+// the flux product is folded into the cell update (12 FP64 operations per
+// cell and stage instead of 15).  The two cells of a face use the same w and
+// theta_f, so the update stays conservative to rounding.  s_ux / s_uy are
+// then read by the cell update too and are double-buffered by plane parity.
+//
+// A stage whose velocity is g u_f (a time-modulated flow) toggles the sign of
+// every u before its upwind test when g < 0 (p.flip).  Without PRE, g is part
+// of p.cx/cy/cz; with PRE and MOD the six w theta_f terms are summed first
+// and added as x + g S.
+template <class T, int LIM, int SEED, int TY, bool PRE = false, bool MOD = false>
 __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
   using F = FT<T>;
   constexpr int NT = TX * TY;
   constexpr int SW = TX + 4;  // s_th row pitch
+  constexpr int NUB = PRE ? 2 : 1;
   __shared__ T s_th[(TY + 4) * SW];
   __shared__ T s_dx[TY * (TX + 3)];
   __shared__ T s_dy[(TY + 3) * TX];
   __shared__ T s_fx[TY * (TX + 1)];
   __shared__ T s_fy[(TY + 1) * TX];
-  __shared__ T s_ux[TY * (TX + 1)];  // u of x faces m = x0-1 .. x0+TX-1
-  __shared__ T s_uy[(TY + 1) * TX];  // u of y faces m = y0-1 .. y0+TY-1
+  __shared__ T s_uxb[NUB][TY * (TX + 1)];  // u of x faces m = x0-1 .. x0+TX-1
+  __shared__ T s_uyb[NUB][(TY + 1) * TX];  // u of y faces m = y0-1 .. y0+TY-1
   __shared__ int s_wx[TX + 4];
   __shared__ int s_wy[TY + 4];
 
@@ -123,7 +138,7 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
   Plane cur{}, nxt{};
 
   // ---- z prologue: columns k-2 .. k+1 around z0, and the flux of face z0-1/2
-  T th0, thp1, thp2 = T(0), dz_m1 = T(0), dz_0 = T(0), fz_prev = T(0);
+  T th0, thp1, thp2 = T(0), dz_m1 = T(0), dz_0 = T(0), fz_prev = T(0), wz_prev = T(0);
   if (need_z) {
     const T tm2 = p.x[col + p.plane * wrap(z0 - 2, nz)];
     const T tm1 = p.x[col + p.plane * wrap(z0 - 1, nz)];
@@ -134,9 +149,10 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
     dz_m1 = F::sub(th0, tm1);
     dz_0 = F::sub(thp1, th0);
     const T uz = p.u[p.uz_off + col + p.plane * wrap(z0 - 1, nz)];
-    const bool sp = upwind_positive(uz);
+    const bool sp = upwind_positive(sign_toggled(uz, p.flip));
     const T thf = limited_face<T, LIM>(sp ? tm1 : th0, dz_m1, sp ? d_m2 : dz_0, sp);
-    fz_prev = face_flux(uz, thf);
+    fz_prev = PRE ? thf : face_flux(uz, thf);
+    wz_prev = uz;
   } else {
     th0 = p.x[col];
     thp1 = th0;
@@ -145,6 +161,8 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
 
   for (int k = z0; k < z1; ++k) {
     const long long pk = p.plane * k;
+    T *s_ux = s_uxb[PRE ? (k & 1) : 0];
+    T *s_uy = s_uyb[PRE ? (k & 1) : 0];
     // -------------------------------------------- fill plane k
     s_th[(ty + 2) * SW + tx + 2] = th0;
     if (h_slot >= 0) s_th[h_slot] = cur.h;
@@ -183,12 +201,12 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
       for (int it = tid; it < TY * (TX + 1); it += NT) {
         const int r = it / (TX + 1), q = it - r * (TX + 1);  // face m = x0-1+q
         const T uf = s_ux[it];
-        const bool sp = upwind_positive(uf);
+        const bool sp = upwind_positive(sign_toggled(uf, p.flip));
         const T *dr = &s_dx[r * (TX + 3)];
         const T *tr = &s_th[(r + 2) * SW];
         const T thf = limited_face<T, LIM>(sp ? tr[q + 1] : tr[q + 2], dr[q + 1],
                                            sp ? dr[q] : dr[q + 2], sp);
-        s_fx[it] = face_flux(uf, thf);
+        s_fx[it] = PRE ? thf : face_flux(uf, thf);
         if (SEED == SEED_APPLY && p.thf != nullptr) {
           if (q >= 1 && x0 + q - 1 < nx && y0 + r < ny)
             p.thf[p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 2] + pk] = thf;
@@ -199,11 +217,11 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
       for (int it = tid; it < (TY + 1) * TX; it += NT) {
         const int r = it / TX, c = it - r * TX;  // face m = y0-1+r
         const T uf = s_uy[it];
-        const bool sp = upwind_positive(uf);
+        const bool sp = upwind_positive(sign_toggled(uf, p.flip));
         const T thf = limited_face<T, LIM>(
             sp ? s_th[(r + 1) * SW + c + 2] : s_th[(r + 2) * SW + c + 2], s_dy[(r + 1) * TX + c],
             sp ? s_dy[r * TX + c] : s_dy[(r + 2) * TX + c], sp);
-        s_fy[it] = face_flux(uf, thf);
+        s_fy[it] = PRE ? thf : face_flux(uf, thf);
         if (SEED == SEED_APPLY && p.thf != nullptr) {
           if (r >= 1 && x0 + c < nx && y0 + r - 1 < ny)
             p.thf[p.uy_off + s_wx[c + 2] + (long long)nx * s_wy[r + 1] + pk] = thf;
@@ -212,14 +230,33 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
     }
     T fz = T(0);
     if (need_z) {
-      const bool sp = upwind_positive(cur.uz);
+      const bool sp = upwind_positive(sign_toggled(cur.uz, p.flip));
       const T thf = limited_face<T, LIM>(sp ? th0 : thp1, dz_0, sp ? dz_m1 : dz_p1, sp);
-      fz = face_flux(cur.uz, thf);
+      fz = PRE ? thf : face_flux(cur.uz, thf);
       if (SEED == SEED_APPLY && p.thf != nullptr && valid) p.thf[p.uz_off + col + pk] = thf;
     }
     __syncthreads();
     // ------------------------------------------------ phase C: update
-    if (valid) {
+    if (PRE && valid) {
+      // y = x + sum (w theta_f)_minus - (w theta_f)_plus, then the RK blend
+      T acc = MOD ? T(0) : th0;
+      if (need_x) {
+        const int i = ty * (TX + 1) + tx;
+        acc = F::fma(-s_ux[i + 1], s_fx[i + 1], acc);
+        acc = F::fma(s_ux[i], s_fx[i], acc);
+      }
+      if (need_y) {
+        acc = F::fma(-s_uy[(ty + 1) * TX + tx], s_fy[(ty + 1) * TX + tx], acc);
+        acc = F::fma(s_uy[ty * TX + tx], s_fy[ty * TX + tx], acc);
+      }
+      if (need_z) {
+        acc = F::fma(-cur.uz, fz, acc);
+        acc = F::fma(wz_prev, fz_prev, acc);
+      }
+      if (MOD) acc = F::fma(p.g, acc, th0);
+      if (SEED == SEED_COMBINE) acc = F::fma(p.b, acc, F::mul(p.a, cur.thn));
+      p.y[col + pk] = acc;
+    } else if (valid) {
       T acc;
       if (SEED == SEED_PLAIN) acc = th0;
       else if (SEED == SEED_COMBINE) acc = F::fma(p.a, cur.thn, F::mul(p.b, th0));
@@ -239,6 +276,7 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
       p.y[col + pk] = acc;
     }
     // --------------------------------------------------------- rotate
+    if (need_z) wz_prev = cur.uz;
     cur = nxt;
     if (need_z) {
       fz_prev = fz;

@@ -6,13 +6,17 @@
 // limited face values of Algorithm 1, Sweby's stencil on Cartesian grids).
 // FP32 is bandwidth-bound on this part, so the kernel is built to spend few
 // instructions per cell and keep several planes of loads in flight:
-//   * a CTA owns a 128 x 8 column of cells and streams through z; a thread
-//     owns four consecutive x cells of one row (128-bit loads and stores);
-//   * one elected thread issues, per plane, the TMA tile copies
-//     (cp.async.bulk.tensor) of the theta tile and its periodic halos
+//   * a CTA owns a 128 x 8 column of cells and streams through z; a consumer
+//     thread owns four consecutive x cells of one row (128-bit loads and
+//     stores);
+//   * a ninth warp is the producer: one lane issues, per plane, the TMA tile
+//     copies (cp.async.bulk.tensor) of the theta tile and its periodic halos
 //     (4-wide x boxes, one-row y boxes at wrapped coordinates), the u_f
 //     tiles with their -x / -y halo faces and theta^n, completing on the
-//     slot's mbarrier; a ring of 3 slots keeps two planes in flight;
+//     slot's "full" mbarrier; a ring of 3 slots keeps two planes in flight;
+//   * consumer warps never wait for one another: each waits on the slot's
+//     full barrier, computes, and arrives on the slot's "empty" barrier,
+//     which the producer waits on before refilling the slot;
 //   * x neighbours move between lanes by warp shuffles (only the warp-edge
 //     lanes read the halo boxes); each x face is evaluated once, the -x
 //     face of a lane's first cell arriving by shuffle from the lane to its
@@ -21,11 +25,10 @@
 //     row is the -y face of the next, computed by another warp from the same
 //     values with the same code, so both sides see bit-identical fluxes) and
 //     the +z face; the -z face is the previous plane's, kept in a register;
-//   * the limiter runs on FP32 min/max (limited_face_native);
-//   * one barrier per plane, before the slot is refilled.
-// Every mbarrier wait is bounded: on expiry the CTA records FL_ETIMEOUT in
-// the mesh status word, waits (bounded again) for its copies in flight and
-// returns.
+//   * the limiter runs on FP32 min/max (limited_face_native).
+// Every mbarrier wait is bounded: on expiry the warp records FL_ETIMEOUT in
+// the mesh status word and stops; the producer stops issuing and waits
+// (bounded again) for the copies it has in flight before it returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -37,7 +40,14 @@ namespace fl {
 
 namespace {
 
-constexpr int TX = 128, VX = 4, LANES = TX / VX, TY = 8, RING = 3;
+constexpr int TX = 128, VX = 4, LANES = TX / VX, TY = 8;
+#ifndef FL_TMA_RING
+#define FL_TMA_RING 4
+#endif
+#ifndef FL_TMA_MINB
+#define FL_TMA_MINB 2
+#endif
+constexpr int RING = FL_TMA_RING, MINB = FL_TMA_MINB;
 // slot layout (bytes); every TMA destination is 128-byte aligned
 constexpr int OFF_TH = 0;       // [8][128] theta
 constexpr int OFF_XL = 4096;    // [8][4]   theta x0-4 .. x0-1
@@ -121,11 +131,12 @@ __device__ __forceinline__ int wrapv(int v, int n) {
 }
 
 // flux of a face from its Delta a, the two candidate upstream Deltas and
-// the two candidate upwind values (picked by the sign of u)
+// the two candidate upwind values (picked by the sign of u: u > 0 is false
+// for 0, -0 and NaN, the selection rule of the scalar path)
 template <int LIM>
 __device__ __forceinline__ float flux(float u, float thC_pos, float thC_neg, float a, float b_pos,
                                       float b_neg) {
-  const bool sp = upwind_positive(u);
+  const bool sp = u > 0.0f;
   return __fmul_rn(u, limited_face_native<LIM>(sp ? thC_pos : thC_neg, a, sp ? b_pos : b_neg, sp));
 }
 
@@ -133,16 +144,27 @@ __device__ __forceinline__ float4 ld4(const unsigned char *base, int off_bytes) 
   return *reinterpret_cast<const float4 *>(base + off_bytes);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(bar)) : "memory");
+}
+
+// k mod n for k in [0, 2n) without a division (n >= 4 here in practice)
+__device__ __forceinline__ int wrap_up(int k, int n) {
+  if (k >= n) k -= n;
+  return k < n ? k : k % n;
+}
+
 template <int LIM, int SEED>
-__global__ void __launch_bounds__(LANES *TY, 3) k_struct_stage_tma(
+__global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
     const TParams p, const __grid_constant__ CUtensorMap m_th,
     const __grid_constant__ CUtensorMap m_thx, const __grid_constant__ CUtensorMap m_thy2,
     const __grid_constant__ CUtensorMap m_thy1, const __grid_constant__ CUtensorMap m_u,
     const __grid_constant__ CUtensorMap m_ux, const __grid_constant__ CUtensorMap m_uy1,
     const __grid_constant__ CUtensorMap m_thn) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[RING];
-  const int lane = threadIdx.x, ty = threadIdx.y, tid = lane + LANES * ty;
+  __shared__ __align__(8) uint64_t full[RING];
+  __shared__ __align__(8) uint64_t empty[RING];
+  const int lane = threadIdx.x, ty = threadIdx.y;
   int bid = blockIdx.x;
   const int bx = bid % p.tiles_x;
   bid /= p.tiles_x;
@@ -154,60 +176,71 @@ __global__ void __launch_bounds__(LANES *TY, 3) k_struct_stage_tma(
   const int L = z1 - z0;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int w = min(TX, nx - x0), h = min(TY, ny - y0);  // w is a multiple of 4
-  const int last_lane = w / VX - 1;
-  const bool valid = lane <= last_lane && ty < h;
   const bool az = p.act_z;
+  auto parity = [](int q) { return (uint32_t)((q / RING) & 1); };
 
-  // ---- producer: plane q (relative to z0) into slot q % RING
-  auto issue = [&](int q) {
-    const int slot = q % RING;
-    unsigned char *s = smem + slot * SLOT;
-    uint64_t *bar = &bars[slot];
-    const int pz = z0 + q;
-    uint32_t bytes = 4096 + 256 + 1024 + 1024 + 4096 + 128 + 4096 + 512;
-    if (az) bytes += 4096;
-    if (SEED == 1) bytes += 4096;
-    // the slot was last read through the generic proxy
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect(bar, bytes);
-    tma3(s + OFF_TH, &m_th, bar, x0, y0, pz);
-    tma3(s + OFF_XL, &m_thx, bar, wrapv(x0 - 4, nx), y0, pz);
-    tma3(s + OFF_XR, &m_thx, bar, wrapv(x0 + w, nx), y0, pz);
-    tma3(s + OFF_YT, &m_thy2, bar, x0, wrapv(y0 - 2, ny), pz);
-    // the two rows below may straddle the periodic end: one box each
-    tma3(s + OFF_YB, &m_thy1, bar, x0, wrapv(y0 + h, ny), pz);
-    tma3(s + OFF_YB + 512, &m_thy1, bar, x0, wrapv(y0 + h + 1, ny), pz);
-    tma4(s + OFF_UX, &m_u, bar, x0, y0, pz, p.bx_u);
-    tma4(s + OFF_UXH, &m_ux, bar, wrapv(x0 - 4, nx), y0, pz, p.bx_u);
-    tma4(s + OFF_UY, &m_u, bar, x0, y0, pz, p.by_u);
-    tma4(s + OFF_UYH, &m_uy1, bar, x0, wrapv(y0 - 1, ny), pz, p.by_u);
-    if (az) tma4(s + OFF_UZ, &m_u, bar, x0, y0, pz, p.bz_u);
-    if (SEED == 1) tma3(s + OFF_THN, &m_thn, bar, x0, y0, pz);
-  };
-  auto parity = [&](int q) { return (uint32_t)((q / RING) & 1); };
-  // give up: record the timeout, wait (bounded) for the copies in flight
-  auto bail = [&](int lo, int hi) {
-    if (tid == 0) {
-      atomicExch(p.status, (int)FL_ETIMEOUT);
-      for (int q = lo; q < hi; ++q) (void)mbar_wait(&bars[q % RING], parity(q));
+  if (lane == 0 && ty == 0) {
+    for (int i = 0; i < RING; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], TY);  // one arrival per consumer warp
     }
-    __syncthreads();
-  };
-
-  if (tid == 0) {
-    for (int i = 0; i < RING; ++i) mbar_init(&bars[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (tid == 0)
-    for (int q = 0; q < min(RING, L); ++q) issue(q);
 
-  // ---- z window of the thread's four cells by plain 128-bit loads
+  // ================================================================ producer
+  if (ty == TY) {
+    if (lane != 0) return;
+    // wrapped halo coordinates, fixed for the CTA
+    const int cxl = wrapv(x0 - 4, nx), cxr = wrapv(x0 + w, nx);
+    const int cyt = wrapv(y0 - 2, ny), cyh = wrapv(y0 - 1, ny);
+    const int cyb0 = wrapv(y0 + h, ny), cyb1 = wrapv(y0 + h + 1, ny);
+    uint32_t bytes = 4096 + 256 + 1024 + 1024 + 4096 + 128 + 4096 + 512;
+    if (az) bytes += 4096;
+    if (SEED == 1) bytes += 4096;
+    int issued = 0;
+    for (int q = 0; q < L; ++q) {
+      const int slot = q % RING;
+      if (q >= RING && !mbar_wait(&empty[slot], parity(q - RING))) {
+        atomicExch(p.status, (int)FL_ETIMEOUT);
+        break;
+      }
+      unsigned char *s = smem + slot * SLOT;
+      uint64_t *bar = &full[slot];
+      const int pz = z0 + q;
+      // the slot was last read through the generic proxy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect(bar, bytes);
+      tma3(s + OFF_TH, &m_th, bar, x0, y0, pz);
+      tma3(s + OFF_XL, &m_thx, bar, cxl, y0, pz);
+      tma3(s + OFF_XR, &m_thx, bar, cxr, y0, pz);
+      tma3(s + OFF_YT, &m_thy2, bar, x0, cyt, pz);
+      // the two rows below may straddle the periodic end: one box each
+      tma3(s + OFF_YB, &m_thy1, bar, x0, cyb0, pz);
+      tma3(s + OFF_YB + 512, &m_thy1, bar, x0, cyb1, pz);
+      tma4(s + OFF_UX, &m_u, bar, x0, y0, pz, p.bx_u);
+      tma4(s + OFF_UXH, &m_ux, bar, cxl, y0, pz, p.bx_u);
+      tma4(s + OFF_UY, &m_u, bar, x0, y0, pz, p.by_u);
+      tma4(s + OFF_UYH, &m_uy1, bar, x0, cyh, pz, p.by_u);
+      if (az) tma4(s + OFF_UZ, &m_u, bar, x0, y0, pz, p.bz_u);
+      if (SEED == 1) tma3(s + OFF_THN, &m_thn, bar, x0, y0, pz);
+      issued = q + 1;
+    }
+    // before the CTA may end: the last copy issued into each slot has landed
+    for (int q = max(0, issued - RING); q < issued; ++q)
+      if (!mbar_wait(&full[q % RING], parity(q))) atomicExch(p.status, (int)FL_ETIMEOUT);
+    return;
+  }
+
+  // =============================================================== consumers
+  const int last_lane = w / VX - 1;
+  const bool valid = lane <= last_lane && ty < h;
+  // z window of the thread's four cells by plain 128-bit loads
   const long long plane = (long long)nx * ny;
   const int cxv = min(x0 + VX * lane, nx - VX), cyv = min(y0 + ty, ny - 1);
   const long long col = (long long)cxv + (long long)nx * cyv;
-  auto X4 = [&](int k) {
-    return *reinterpret_cast<const float4 *>(p.x + col + plane * wrapv(k, nz));
+  auto X4 = [&](int k) {  // k in [0, nz)
+    return *reinterpret_cast<const float4 *>(p.x + col + plane * k);
   };
   float th0[4], thp1[4] = {0, 0, 0, 0}, thp2[4] = {0, 0, 0, 0}, dzm[4] = {0, 0, 0, 0},
         dz0[4] = {0, 0, 0, 0}, fzp[4] = {0, 0, 0, 0};
@@ -220,8 +253,9 @@ __global__ void __launch_bounds__(LANES *TY, 3) k_struct_stage_tma(
     th0[3] = c0.w;
   }
   if (az) {
-    const float4 m2 = X4(z0 - 2), m1 = X4(z0 - 1), p1 = X4(z0 + 1), p2 = X4(z0 + 2);
-    pf = X4(z0 + 3);
+    const float4 m2 = X4(wrapv(z0 - 2, nz)), m1 = X4(wrapv(z0 - 1, nz));
+    const float4 p1 = X4(wrapv(z0 + 1, nz)), p2 = X4(wrapv(z0 + 2, nz));
+    pf = X4(wrapv(z0 + 3, nz));
     const float4 um = *reinterpret_cast<const float4 *>(p.u + p.uz_off + col +
                                                          plane * wrapv(z0 - 1, nz));
     const float tm2[4] = {m2.x, m2.y, m2.z, m2.w}, tm1[4] = {m1.x, m1.y, m1.z, m1.w};
@@ -237,20 +271,37 @@ __global__ void __launch_bounds__(LANES *TY, 3) k_struct_stage_tma(
       fzp[v] = flux<LIM>(uzm[v], tm1[v], th0[v], dzm[v], d_m2, dz0[v]);
     }
   }
-  {
-    const bool ok = mbar_wait(&bars[0], 0);
-    if (__syncthreads_or(!ok)) {
-      bail(0, min(RING, L));
-      return;
-    }
-  }
 
   const int rowb = ty * TX * 4 + lane * VX * 4;  // byte offset of the thread's cells in a row tile
+  // y rows ty-2 .. ty+2 of the slot (fixed per thread)
+  int yoff[5];
+#pragma unroll
+  for (int dd = -2; dd <= 2; ++dd) {
+    const int r = ty + dd;
+    int off;
+    if (r < 0) off = OFF_YT + (2 + r) * TX * 4;
+    else if (r < h) off = OFF_TH + r * TX * 4;
+    else off = OFF_YB + min(r - h, 1) * TX * 4;
+    yoff[dd + 2] = off + lane * VX * 4;
+  }
+  const int umoff = (ty > 0) ? OFF_UY + rowb - TX * 4 : OFF_UYH + lane * VX * 4;
+  int knext = wrap_up(z0 + 4, nz);  // plane of the next z-window load
   for (int q = 0; q < L; ++q) {
     const int k = z0 + q;
-    const unsigned char *s = smem + (q % RING) * SLOT;
+    const int slot = q % RING;
     float4 pf_next = make_float4(0, 0, 0, 0);
-    if (az && q + 1 < L) pf_next = X4(k + 4);
+    if (az && q + 1 < L) {
+      pf_next = X4(knext);
+      knext = (knext + 1 == nz) ? 0 : knext + 1;
+    }
+    {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], parity(q)));
+      if (!ok) {
+        if (lane == 0) atomicExch(p.status, (int)FL_ETIMEOUT);
+        return;
+      }
+    }
+    const unsigned char *s = smem + slot * SLOT;
     float acc[4];
     if (SEED == 1) {
       const float4 tn = ld4(s, OFF_THN + rowb);
@@ -303,16 +354,9 @@ __global__ void __launch_bounds__(LANES *TY, 3) k_struct_stage_tma(
     {
       float4 r4[5];  // rows ty-2 .. ty+2 at the thread's four columns
 #pragma unroll
-      for (int dd = -2; dd <= 2; ++dd) {
-        const int r = ty + dd;
-        int off;
-        if (r < 0) off = OFF_YT + (2 + r) * TX * 4;
-        else if (r < h) off = OFF_TH + r * TX * 4;
-        else off = OFF_YB + min(r - h, 1) * TX * 4;
-        r4[dd + 2] = ld4(s, off + lane * VX * 4);
-      }
+      for (int dd = 0; dd < 5; ++dd) r4[dd] = ld4(s, yoff[dd]);
       const float4 up4 = ld4(s, OFF_UY + rowb);
-      const float4 um4 = (ty > 0) ? ld4(s, OFF_UY + rowb - TX * 4) : ld4(s, OFF_UYH + lane * VX * 4);
+      const float4 um4 = ld4(s, umoff);
       const float upv[4] = {up4.x, up4.y, up4.z, up4.w}, umv[4] = {um4.x, um4.y, um4.z, um4.w};
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -339,6 +383,9 @@ __global__ void __launch_bounds__(LANES *TY, 3) k_struct_stage_tma(
         acc[v] = __fmaf_rn(p.cz, fzp[v], acc[v]);
       }
     }
+    // this warp is done with the slot
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[slot]);
     if (valid)
       *reinterpret_cast<float4 *>(p.y + col + plane * k) = make_float4(acc[0], acc[1], acc[2], acc[3]);
     // ------------------------------------------------------ rotate z
@@ -361,13 +408,6 @@ __global__ void __launch_bounds__(LANES *TY, 3) k_struct_stage_tma(
       th0[2] = c0.z;
       th0[3] = c0.w;
     }
-    // wait for the next plane, then let the producer refill this slot
-    const bool ok = (q + 1 < L) ? mbar_wait(&bars[(q + 1) % RING], parity(q + 1)) : true;
-    if (__syncthreads_or(!ok)) {
-      bail(q + 1, min(q + RING, L));
-      return;
-    }
-    if (tid == 0 && q + RING < L) issue(q + RING);
   }
 }
 
@@ -410,7 +450,7 @@ cudaError_t launch(const TParams &p, const CUtensorMap *maps, unsigned grid, cud
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k<<<grid, dim3(LANES, TY), smem, st>>>(p, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
+  k<<<grid, dim3(LANES, TY + 1), smem, st>>>(p, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
                                          maps[6], maps[7]);
   return cudaGetLastError();
 }
@@ -432,7 +472,9 @@ cudaError_t launch_lim(int lim, const TParams &p, const CUtensorMap *maps, unsig
 }  // namespace
 
 bool struct_tma_eligible(const fl_mesh *m, const StageArgs &s) {
-  if (m->kind != 0 || s.seed == 2) return false;
+  // a negative velocity factor (reversed flow) needs the flipped upwind
+  // test of the plain kernel
+  if (m->kind != 0 || s.seed == 2 || !(s.g >= 0)) return false;
   if (m->nx % 4 != 0 || m->nx < TX || m->ny < TY) return false;
   if (!m->status) return false;
   const uintptr_t mask = 15;
@@ -470,7 +512,7 @@ cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cuda
   p.by_u = (int)(m->u_off[1] / m->C);
   p.bz_u = (int)(m->u_off[2] / m->C);
   p.uz_off = m->u_off[2];
-  const double sc = (s.seed == 0) ? s.dt : s.b * s.dt;
+  const double sc = ((s.seed == 0) ? s.dt : s.b * s.dt) * s.g;
   p.cx = (float)(sc / m->hx);
   p.cy = (float)(sc / m->hy);
   p.cz = (float)(sc / m->hz);
@@ -479,23 +521,19 @@ cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cuda
   p.tiles_x = (nx + TX - 1) / TX;
   p.tiles_y = (ny + TY - 1) / TY;
   const long long cols = (long long)p.tiles_x * p.tiles_y;
-  // about four waves of resident CTAs: zchunk = nz / ceil(4 * resident / cols)
-  static int resident = 0;
-  if (resident == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_struct_stage_tma<LIM_SUPERBEE, 1>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, RING * SLOT);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_struct_stage_tma<LIM_SUPERBEE, 1>,
-                                                  LANES * TY, RING * SLOT);
-    resident = sms * (per > 0 ? per : 1);
+  // whole waves of co-resident CTAs (the occupancy query needs the kernel's
+  // dynamic shared-memory limit raised first)
+  static bool attr_q = false;
+  if (!attr_q) {
+    if (cudaFuncSetAttribute(k_struct_stage_tma<LIM_SUPERBEE, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             RING * SLOT) != cudaSuccess)
+      return cudaErrorNotSupported;
+    attr_q = true;
   }
-  long long nch = (4LL * resident + cols - 1) / cols;
-  if (nch > nz) nch = nz;
-  if (nch < 1) nch = 1;
-  int zchunk = (int)((nz + nch - 1) / nch);
-  if (zchunk < 8) zchunk = (nz < 8) ? nz : 8;
+  const int resident = resident_ctas(reinterpret_cast<const void *>(&k_struct_stage_tma<LIM_SUPERBEE, 1>),
+                                     LANES * (TY + 1), RING * SLOT);
+  const int zchunk = pick_zchunk(cols, nz, resident, 3);
   p.zchunk = zchunk;
   p.status = m->status;
   const unsigned grid = (unsigned)(cols * ((nz + zchunk - 1) / zchunk));

@@ -29,42 +29,62 @@ namespace fl {
 
 namespace {
 
-template <class T, int LIM, int SEED, int TY>
+template <class T, int LIM, int SEED, int TY, bool PRE, bool MOD>
 __global__ void __launch_bounds__(TX *TY, 4) k_struct_stage(const SParams<T> p) {
-  stage_tile<T, LIM, SEED, TY>(p, blockIdx.x);
+  stage_tile<T, LIM, SEED, TY, PRE, MOD>(p, blockIdx.x);
 }
 
-template <class T, int LIM, int SEED>
+template <class T, int LIM, int SEED, bool PRE, bool MOD>
 cudaError_t launch_stage(const SParams<T> &p0, int tiles_z, cudaStream_t st) {
   constexpr int TY = 8;
   SParams<T> p = p0;
   const dim3 block(TX, TY);
   const long long grid = (long long)p.tiles_x * p.tiles_y * tiles_z;
-  k_struct_stage<T, LIM, SEED, TY><<<(unsigned)grid, block, 0, st>>>(p);
+  k_struct_stage<T, LIM, SEED, TY, PRE, MOD><<<(unsigned)grid, block, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-template <class T, int SEED>
+template <class T, int SEED, bool PRE, bool MOD = false>
 cudaError_t dispatch_lim(int lim, const SParams<T> &p, int tz, cudaStream_t st) {
   switch (lim) {
-    case LIM_UPWIND: return launch_stage<T, LIM_UPWIND, SEED>(p, tz, st);
-    case LIM_CENTRAL: return launch_stage<T, LIM_CENTRAL, SEED>(p, tz, st);
-    case LIM_MINMOD: return launch_stage<T, LIM_MINMOD, SEED>(p, tz, st);
-    case LIM_VANLEER: return launch_stage<T, LIM_VANLEER, SEED>(p, tz, st);
-    case LIM_SUPERBEE: return launch_stage<T, LIM_SUPERBEE, SEED>(p, tz, st);
-    case LIM_SMART: return launch_stage<T, LIM_SMART, SEED>(p, tz, st);
+    case LIM_UPWIND: return launch_stage<T, LIM_UPWIND, SEED, PRE, MOD>(p, tz, st);
+    case LIM_CENTRAL: return launch_stage<T, LIM_CENTRAL, SEED, PRE, MOD>(p, tz, st);
+    case LIM_MINMOD: return launch_stage<T, LIM_MINMOD, SEED, PRE, MOD>(p, tz, st);
+    case LIM_VANLEER: return launch_stage<T, LIM_VANLEER, SEED, PRE, MOD>(p, tz, st);
+    case LIM_SUPERBEE: return launch_stage<T, LIM_SUPERBEE, SEED, PRE, MOD>(p, tz, st);
+    case LIM_SMART: return launch_stage<T, LIM_SMART, SEED, PRE, MOD>(p, tz, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// w_f = fac_axis u_f for every face block; a product that underflows keeps
+// the sign of u_f (smallest subnormal), so the upwind test of w_f equals the
+// upwind test of u_f whenever every fac_axis > 0
+template <class T>
+__global__ void k_scale_faces(const T *u, T *w, long long C, int nblk, T f0, T f1, T f2) {
+  using F = FT<T>;
+  const long long n = C * nblk;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n;
+       f += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(f / C);
+    const T c = b == 0 ? f0 : (b == 1 ? f1 : f2);
+    const T uf = u[f];
+    T v = F::mul(c, uf);
+    if (upwind_positive(uf) && !upwind_positive(v)) v = F::val(1);
+    w[f] = v;
+  }
 }
 
 template <class T>
 cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStream_t st) {
   SParams<T> p;
+  // pre-scaled velocities: FP64 stage updates (not the bare operator)
+  const bool pre = s.w != nullptr && sizeof(T) == 8 && s.seed != SEED_APPLY;
   p.x = static_cast<const T *>(s.x);
   p.thn = static_cast<const T *>(s.thn);
   p.y = static_cast<T *>(s.y);
   p.thf = static_cast<T *>(s.thf);
-  p.u = static_cast<const T *>(s.u);
+  p.u = static_cast<const T *>(pre ? s.w : s.u);
   p.nx = m->nx;
   p.ny = m->ny;
   p.nz = m->nz;
@@ -75,8 +95,13 @@ cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStrea
   p.uy_off = m->u_off[1];
   p.uz_off = m->u_off[2];
   p.plane = (long long)m->nx * m->ny;
-  // R = sum_axis (A/V) (phi_minus - phi_plus); A/V = 1/h_axis
-  const double sc = (s.seed == SEED_APPLY) ? 1.0 : s.b * s.dt;
+  // R = sum_axis (A/V) (phi_minus - phi_plus); A/V = 1/h_axis; a velocity
+  // factor g scales the fluxes and, when negative, flips every upwind side
+  const double g = (s.seed == SEED_APPLY) ? 1.0 : s.g;
+  const bool mod = pre && g != 1.0;
+  const double sc = (s.seed == SEED_APPLY) ? 1.0 : s.b * s.dt * (pre ? 1.0 : g);
+  p.g = (T)g;
+  p.flip = (g < 0) ? (sizeof(T) == 8 ? 0x8000000000000000ull : 0x80000000ull) : 0ull;
   p.cx = (T)(sc / m->hx);
   p.cy = (T)(sc / m->hy);
   p.cz = (T)(sc / m->hz);
@@ -84,22 +109,30 @@ cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStrea
   p.b = (T)s.b;
   p.tiles_x = (m->nx + TX - 1) / TX;
   p.tiles_y = (m->ny + 7) / 8;
-  // z chunks: enough CTAs to fill the GPU several times over
+  // z chunks: whole waves of co-resident CTAs (the occupancy of the PLAIN
+  // kernel stands for all variants: same block, similar registers)
   const long long cols = (long long)p.tiles_x * p.tiles_y;
-  int zchunk = m->nz;
-  const long long want = 152LL * 12;
-  if (cols < want && m->nz > 1) {
-    long long nch = (want + cols - 1) / cols;
-    if (nch > m->nz) nch = m->nz;
-    zchunk = (int)((m->nz + nch - 1) / nch);
-    if (zchunk < 8 && m->nz >= 8) zchunk = 8;
-  }
+  const int resident =
+      resident_ctas(reinterpret_cast<const void *>(&k_struct_stage<T, LIM_SUPERBEE, SEED_PLAIN, 8,
+                                                                   false, false>),
+                    TX * 8, 0);
+  const int zchunk = pick_zchunk(cols, m->nz, resident, 2);
   p.zchunk = zchunk;
   const int tz = (m->nz + zchunk - 1) / zchunk;
+  if constexpr (sizeof(T) == 8) {
+    if (pre && mod) {
+      if (s.seed == SEED_PLAIN) return dispatch_lim<T, SEED_PLAIN, true, true>(lim, p, tz, st);
+      return dispatch_lim<T, SEED_COMBINE, true, true>(lim, p, tz, st);
+    }
+    if (pre) {
+      if (s.seed == SEED_PLAIN) return dispatch_lim<T, SEED_PLAIN, true>(lim, p, tz, st);
+      return dispatch_lim<T, SEED_COMBINE, true>(lim, p, tz, st);
+    }
+  }
   switch (s.seed) {
-    case SEED_PLAIN: return dispatch_lim<T, SEED_PLAIN>(lim, p, tz, st);
-    case SEED_COMBINE: return dispatch_lim<T, SEED_COMBINE>(lim, p, tz, st);
-    default: return dispatch_lim<T, SEED_APPLY>(lim, p, tz, st);
+    case SEED_PLAIN: return dispatch_lim<T, SEED_PLAIN, false>(lim, p, tz, st);
+    case SEED_COMBINE: return dispatch_lim<T, SEED_COMBINE, false>(lim, p, tz, st);
+    default: return dispatch_lim<T, SEED_APPLY, false>(lim, p, tz, st);
   }
 }
 
@@ -240,6 +273,87 @@ cudaError_t struct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs
     if (e != cudaErrorNotSupported) return e;
   }
   return run_stage_t<float>(m, lim, s, st);
+}
+
+cudaError_t struct_scale_faces(const fl_mesh *m, fl_dtype dt, const void *u, void *w, double fac,
+                               cudaStream_t st) {
+  double f[3] = {1, 1, 1};
+  int nb = 0;
+  const double h[3] = {m->hx, m->hy, m->hz};
+  for (int a = 0; a < 3; ++a)
+    if (m->act[a]) f[nb++] = fac / h[a];
+  if (nb == 0 || m->C == 0) return cudaSuccess;
+  const long long n = m->C * nb;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152LL * 32) blocks = 152LL * 32;
+  if (dt == FL_F64)
+    k_scale_faces<double><<<(unsigned)blocks, 256, 0, st>>>(
+        static_cast<const double *>(u), static_cast<double *>(w), m->C, nb, f[0], f[1], f[2]);
+  else
+    k_scale_faces<float><<<(unsigned)blocks, 256, 0, st>>>(
+        static_cast<const float *>(u), static_cast<float *>(w), m->C, nb, (float)f[0],
+        (float)f[1], (float)f[2]);
+  return cudaGetLastError();
+}
+
+bool struct_step_prescales(const fl_mesh *m, fl_dtype dt) {
+  return m->kind == 0 && dt == FL_F64 &&
+         !(m->ny == 1 && m->nz == 1 && (size_t)m->nx <= line_resident_max_cells(dt));
+}
+
+cudaError_t struct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
+                        int64_t nsteps, void *theta, const void *u, void *A, void *B, void *W,
+                        cudaStream_t st, const double *gfac) {
+  const size_t es = dsize(dt);
+  StageArgs s;
+  s.u = u;
+  s.dt = dtime;
+  cudaError_t e = cudaSuccess;
+  // FP64 folds the flux product into the cell update with w = dt (A/V) u,
+  // computed once per call (dt > 0 keeps the sign of every u_f)
+  if (W != nullptr && dtime > 0 && struct_step_prescales(m, dt)) {
+    e = struct_scale_faces(m, dt, u, W, dtime, st);
+    if (e != cudaSuccess) return e;
+    s.w = W;
+  }
+  if (rk == 1) {
+    // Euler: ping-pong between theta and A (a stage reads neighbours of x
+    // while writing y, so x and y must differ)
+    void *cur = theta, *nxt = A;
+    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      s.x = cur;
+      s.thn = cur;
+      s.y = nxt;
+      s.seed = 0;
+      s.b = 1.0;
+      s.g = gfac ? gfac[n] : 1.0;
+      e = struct_stage(m, lim, dt, s, st);
+      void *t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    if (e == cudaSuccess && cur != theta)
+      e = cudaMemcpyAsync(theta, cur, m->C * es, cudaMemcpyDeviceToDevice, st);
+    return e;
+  }
+  for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
+    // th1 = thn + dt R(thn)
+    s.x = theta; s.thn = theta; s.y = A; s.seed = 0; s.a = 0.0; s.b = 1.0;
+    s.g = gfac ? gfac[3 * n] : 1.0;
+    e = struct_stage(m, lim, dt, s, st);
+    if (e != cudaSuccess) break;
+    // th2 = 3/4 thn + 1/4 (th1 + dt R(th1))
+    s.x = A; s.thn = theta; s.y = B; s.seed = 1; s.a = 0.75; s.b = 0.25;
+    s.g = gfac ? gfac[3 * n + 1] : 1.0;
+    e = struct_stage(m, lim, dt, s, st);
+    if (e != cudaSuccess) break;
+    // th^{n+1} = 1/3 thn + 2/3 (th2 + dt R(th2)); thn and y are read and
+    // written only at the thread's own cell, so y may alias thn
+    s.x = B; s.thn = theta; s.y = theta; s.seed = 1; s.a = 1.0 / 3.0; s.b = 2.0 / 3.0;
+    s.g = gfac ? gfac[3 * n + 2] : 1.0;
+    e = struct_stage(m, lim, dt, s, st);
+  }
+  return e;
 }
 
 size_t line_resident_max_cells(fl_dtype dt) {

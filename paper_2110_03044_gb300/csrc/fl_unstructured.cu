@@ -58,7 +58,8 @@ struct UParams {
   const uint16_t *slots;
   const T *area;
   const T *inv_vol;
-  T a, b, bdt;  // RK combination a*thn + b*x and b*dt
+  T a, b, bdt;  // RK combination a*thn + b*x and b*dt (times the velocity factor)
+  unsigned long long flip;  // sign mask toggled into u_f before the upwind test
 };
 
 template <class T>
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(UTHREADS) k_unstruct_stage(const UParams<T> p)
     const int f = p.ent_face[e];
     const int4 cc = p.ent_cells[e];
     const T uf = p.u[f];
-    const bool sp = upwind_positive(uf);
+    const bool sp = upwind_positive(sign_toggled(uf, p.flip));
     const T t0 = p.x[cc.x];
     const T t1 = p.x[cc.y];
     const unsigned up = sp ? (unsigned)cc.z : (unsigned)cc.w;
@@ -182,7 +183,11 @@ cudaError_t run_ustage(const fl_mesh *m, int lim, const StageArgs &s, cudaStream
   }
   p.a = (T)s.a;
   p.b = (T)s.b;
-  p.bdt = (T)(s.b * s.dt);
+  // the flow of this stage is g u_f: fluxes scale by g, and g < 0 flips
+  // every face's upwind side (the bare operator has g = 1)
+  const double g = (s.seed == 2) ? 1.0 : s.g;
+  p.bdt = (T)(s.b * s.dt * g);
+  p.flip = (g < 0) ? (sizeof(T) == 8 ? 0x8000000000000000ull : 0x80000000ull) : 0ull;
   switch (s.seed) {
     case 0: return launch_lim<T, 0>(lim, m, p, st);
     case 1: return launch_lim<T, 1>(lim, m, p, st);
@@ -727,7 +732,8 @@ fl_status unstruct_apply(const fl_mesh *m, int lim, fl_dtype dt, const void *the
 }
 
 fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
-                        int64_t nsteps, void *theta, const void *u, void *ws, cudaStream_t st) {
+                        int64_t nsteps, void *theta, const void *u, void *ws, cudaStream_t st,
+                        const double *gfac) {
   const size_t es = dsize(dt);
   char *wsb = static_cast<char *>(ws);
   void *A = wsb;
@@ -740,6 +746,7 @@ fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double d
     void *cur = theta, *nxt = A;
     for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
       s.x = cur; s.thn = cur; s.y = nxt; s.seed = 0; s.b = 1.0;
+      s.g = gfac ? gfac[n] : 1.0;
       e = unstruct_stage(m, lim, dt, s, st);
       void *t = cur;
       cur = nxt;
@@ -750,10 +757,13 @@ fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double d
   } else {
     for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
       s.x = theta; s.thn = theta; s.y = A; s.seed = 0; s.a = 0.0; s.b = 1.0;
+      s.g = gfac ? gfac[3 * n] : 1.0;
       if ((e = unstruct_stage(m, lim, dt, s, st)) != cudaSuccess) break;
       s.x = A; s.thn = theta; s.y = B; s.seed = 1; s.a = 0.75; s.b = 0.25;
+      s.g = gfac ? gfac[3 * n + 1] : 1.0;
       if ((e = unstruct_stage(m, lim, dt, s, st)) != cudaSuccess) break;
       s.x = B; s.thn = theta; s.y = theta; s.seed = 1; s.a = 1.0 / 3.0; s.b = 2.0 / 3.0;
+      s.g = gfac ? gfac[3 * n + 2] : 1.0;
       e = unstruct_stage(m, lim, dt, s, st);
     }
   }
