@@ -53,12 +53,15 @@ def stage_bytes_per_cell(es, stage):
     return es * (1 + 3 + 1 + (1 if stage > 0 else 0))
 
 
-# FP64 operations per cell of one stage in this formulation: per face one
-# difference, one fma (theta_f) and one product (flux); per cell six fmas
-# (the six face fluxes) and two more for the RK combination of stages 2-3.
+# FP64 operations per cell of one stage in the kernel's formulation: per
+# face one difference and the limited face value (one fma for minmod /
+# superbee / central, three for SMART, four with the division for van Leer);
+# per cell six fmas w theta_f (the flux product folded into the update with
+# the pre-scaled velocity w = dt (A/V) u) and two more for the RK blend of
+# stages 2-3.  Superbee: 12 + 14 + 14 = 40 per SSP-RK3 step.
 def stage_fp64_ops_per_cell(lim, stage):
-    per_face = {"upwind": 1, "central": 3, "minmod": 3, "superbee": 3, "smart": 5,
-                "vanleer": 6}[lim]
+    per_face = {"upwind": 1, "central": 2, "minmod": 2, "superbee": 2, "smart": 4,
+                "vanleer": 5}[lim]
     return 3 * per_face + 6 + (2 if stage > 0 else 0)
 
 
@@ -287,7 +290,9 @@ def run_ours(args):
         "roofline": roof,
         "roofline_hbm": roof_hbm,
         "stage_launch_ms": launch_ms,
-        "gpu_launches": stages,
+        # the stage launches plus, in FP64, the one velocity pre-scaling
+        # launch of the fl_step_rk call
+        "gpu_launches": stages + (1 if args.dtype == "f64" else 0),
         "clocks": clk.summary(),
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -520,6 +525,74 @@ def run_config_adjoint(args):
             "config": {"workload": "tg128_superbee_ssprk3_200steps_ckpt20"}}
 
 
+def run_config_deformation(args):
+    """Section 4.1: the sphere in the reversing deformation flow (eq.
+    rhodonea) on n^3 hexahedra, superbee, forward Euler, the whole period
+    t in [0, 3] as one fl_step_rk_modulated call.  Reports face-updates/s of
+    the rollout and the benchmark's own checks: mass drift, bounds, and the
+    L1 distance between theta(T) and the initial sphere."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    import workloads as W
+    fl.build()
+    n = args.n
+    t0 = time.perf_counter()
+    wl = W.config_deformation(n)
+    t_gen = time.perf_counter() - t0
+    g = wl.extra["g"]
+    m = fl.Mesh.structured(n, n, n, *wl.mesh.h)
+    u = torch.tensor(wl.u, device="cuda")
+    th0 = torch.tensor(wl.theta0, device="cuda")
+    ws, nb = fl.workspace_for(m, torch.float64, 1)
+    th = th0.clone()
+    warm = min(wl.nsteps, 20)
+    fl.fl_step_rk_modulated(m.handle, "superbee", torch.float64, 1, wl.dt, warm, th, u, g[:warm],
+                            ws, nb)
+    th.copy_(th0)
+    e0, e1 = _events()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record()
+        fl.fl_step_rk_modulated(m.handle, "superbee", torch.float64, 1, wl.dt, wl.nsteps, th, u, g,
+                                ws, nb)
+        e1.record()
+        torch.cuda.synchronize()
+        time.sleep(0.25)
+    ms = e0.elapsed_time(e1)
+    out = th.cpu().numpy()
+    F = m.n_faces
+    m0 = float(wl.theta0.sum())
+    ops = stage_fp64_ops_per_cell("superbee", 0) + 1  # + the velocity factor
+    ach = ops * m.n_cells * wl.nsteps / (ms * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        threads = oracle.set_threads(os.cpu_count() or 1)
+        om = oracle.OracleMesh(wl.mesh)
+        k, t1 = 0, time.perf_counter()
+        y = wl.theta0
+        while time.perf_counter() - t1 < args.cpu_budget / 2 and k < 50:
+            y = oracle.step_modulated(om, "superbee", 1, wl.dt, 1, wl.u, g[k:k + 1], y)
+            k += 1
+        el = time.perf_counter() - t1
+        cpu = {"value": F * k / el, "unit": "face-updates/s", "cores": threads, "kind": "oracle",
+               "sample": "%d forward-Euler steps of the %d^3 mesh, FP64, OpenMP" % (k, n)}
+    return {"metric": "deformation benchmark face-updates/s (Section 4.1, superbee, Euler)",
+            "value": F * wl.nsteps / (ms * 1e-3), "unit": "face-updates/s",
+            "ms_per_step": ms / wl.nsteps, "rollout_ms": ms, "steps": wl.nsteps, "dtype": "f64",
+            "roofline": {"bound": "alu", "achieved": round(ach, 4),
+                         "peak": round(FP64_OPS_PEAK / 1e12, 4), "unit": "T FP64 ops/s",
+                         "frac": round(ach * 1e12 / FP64_OPS_PEAK, 4), "traffic": None},
+            "checks": {"mass_rel_drift": abs(float(out.sum()) - m0) / m0,
+                       "min": float(out.min()), "max": float(out.max()),
+                       "l1_theta_T_vs_sphere": float(np.sum(np.abs(out - wl.theta0)) / n ** 3)},
+            "gpu_launches": wl.nsteps + 1, "clocks": clk.summary(), "cpu_baseline": cpu,
+            "workload_gen_s": t_gen,
+            "config": {"workload": "deformation_sphere_%d^3_T3_superbee_euler" % n,
+                       "cells": m.n_cells, "dt": wl.dt, "courant_outflow": 0.5}}
+
+
 def cpu_baseline(wl, lim, budget_s):
     """The oracle as it stands on the host cores: one SSP-RK3 stage of the
     same mesh and fields (all cells), repeated while within budget."""
@@ -593,7 +666,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")
     ap.add_argument("--config", default="tg256",
-                    choices=["tg256", "1d", "unstructured", "batched", "adjoint"])
+                    choices=["tg256", "1d", "unstructured", "batched", "adjoint", "deformation"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -602,7 +675,8 @@ def main():
     else:
         import numpy  # noqa: F401  (the config runners use np)
         fn = {"1d": run_config_1d, "unstructured": run_config_unstructured,
-              "batched": run_config_batched, "adjoint": run_config_adjoint}[args.config]
+              "batched": run_config_batched, "adjoint": run_config_adjoint,
+              "deformation": run_config_deformation}[args.config]
         line = fn(args)
         if line is not None:
             print(json.dumps(line))

@@ -75,6 +75,7 @@ def _load():
         lib.orc_rhs.argtypes = [P, I, P, P, P]
         lib.orc_step.argtypes = [P, I, I, D, i64, P, P]
         lib.orc_stage.argtypes = [P, I, I, I, D, P, P, P, P]
+        lib.orc_step_modulated.argtypes = [P, I, I, D, i64, P, P, P]
         lib.orc_step_tlm.argtypes = [P, I, I, D, i64, P, P, P]
         lib.orc_rhs_adjoint.argtypes = [P, I, P, P, P, P]
         lib.orc_gradient.argtypes = [P, I, I, D, i64, P, P, P, P, P]
@@ -171,6 +172,23 @@ def step(mesh, lim, rk, dt, nsteps, u, theta):
     th = _f64(theta).copy()
     uu = _f64(u)
     rc = _load().orc_step(om.h, lim_id(lim), int(rk), float(dt), int(nsteps), _ptr(uu), _ptr(th))
+    if rc:
+        raise ValueError(_lib.orc_last_error().decode())
+    return th
+
+
+def step_modulated(mesh, lim, rk, dt, nsteps, u, g, theta):
+    """nsteps steps where stage s of step n uses the velocity g[n*S + s] * u
+    (S = 1 for Euler, 3 for SSP-RK3)."""
+    om = _om(mesh)
+    th = _f64(theta).copy()
+    uu = _f64(u)
+    S = 1 if int(rk) == 1 else 3
+    gg = _f64(g).ravel()
+    if gg.size < int(nsteps) * S:
+        raise ValueError("need nsteps * stages velocity factors")
+    rc = _load().orc_step_modulated(om.h, lim_id(lim), int(rk), float(dt), int(nsteps), _ptr(uu),
+                                    _ptr(gg), _ptr(th))
     if rc:
         raise ValueError(_lib.orc_last_error().decode())
     return th

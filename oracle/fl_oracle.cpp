@@ -384,6 +384,35 @@ int orc_step(const void *h, int lim, int rk, double dt, int64_t nsteps, const do
   return 0;
 }
 
+// nsteps steps with a time-modulated velocity: stage s of step n uses the
+// face velocity g[n * S + s] * u_f (S = 1 for Euler, 3 for SSP-RK3), the form
+// of the reversing deformation flow of Section 4.1 (eq. rhodonea), whose
+// velocity is a fixed field times cos(pi t / T).  Everything else is orc_step.
+int orc_step_modulated(const void *h, int lim, int rk, double dt, int64_t nsteps, const double *u,
+                       const double *g, double *th) {
+  const OMesh &m = *static_cast<const OMesh *>(h);
+  if (rk != 1 && rk != 3) { set_err("rk must be 1 or 3"); return 1; }
+  const int S = (rk == 1) ? 1 : 3;
+  std::vector<double> thn(m.C), a(m.C), b(m.C), R(m.C), scratch(m.F), us(m.F);
+  auto scaled = [&](int64_t n, int st) {
+    const double gs = g[n * S + st];
+#pragma omp parallel for schedule(static)
+    for (int64_t f = 0; f < m.F; ++f) us[f] = gs * u[f];
+    return us.data();
+  };
+  for (int64_t n = 0; n < nsteps; ++n) {
+    std::memcpy(thn.data(), th, sizeof(double) * m.C);
+    if (rk == 1) {
+      stage(m, lim, 1, 0, dt, thn.data(), thn.data(), scaled(n, 0), th, R.data(), scratch.data());
+    } else {
+      stage(m, lim, 3, 0, dt, thn.data(), thn.data(), scaled(n, 0), a.data(), R.data(), scratch.data());
+      stage(m, lim, 3, 1, dt, thn.data(), a.data(), scaled(n, 1), b.data(), R.data(), scratch.data());
+      stage(m, lim, 3, 2, dt, thn.data(), b.data(), scaled(n, 2), th, R.data(), scratch.data());
+    }
+  }
+  return 0;
+}
+
 // One RK stage: y = a*thn + b*(x + dt R(x)) with (a, b) of stage st.
 int orc_stage(const void *h, int lim, int rk, int st, double dt, const double *thn, const double *x,
               const double *u, double *y) {

@@ -99,6 +99,37 @@ def test_step_parity_per_step(fl, shape, lim, rk, dtype):
     m.close()
 
 
+# shapes the FP32 TMA-staged kernel takes (nx % 4 == 0, nx >= 128, ny >= 8):
+# ragged x tile (132 = 128 + 4), ragged y tile (9, 11), one or two planes
+# (fewer than the ring's slots), a 2D mesh, and z chunks over 40 planes
+TMA_SHAPES = [(128, 8, 5), (132, 9, 7), (256, 11, 3), (128, 16, 1), (136, 8, 2), (128, 8, 40)]
+
+
+@pytest.mark.parametrize("rk", [1, 3])
+@pytest.mark.parametrize("lim", LIMS)
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+def test_step_parity_tma_shapes_fp32(fl, shape, lim, rk):
+    mesh, th, u = _mesh_inputs(shape, seed=7)
+    u = u * 0.3
+    dt = 0.4 * min(mesh.h) / np.max(np.abs(u)) / 3
+    th = th.astype(np.float32).astype(np.float64)
+    u = u.astype(np.float32).astype(np.float64)
+    m = fl.Mesh.structured(*shape, *mesh.h)
+    ud = _dev(u, torch.float32)
+    cur = th
+    mass0 = float(np.sum(th))
+    for _ in range(2):
+        ref = oracle.step(mesh, lim, rk, dt, 1, u, cur)
+        g = _dev(cur, torch.float32)
+        fl.step_rk(m, lim, g, ud, dt, 1, rk_order=rk)
+        got = g.cpu().double().numpy()
+        assert _rel(got, ref) <= TOL[torch.float32]
+        cur = got
+    # FP32 sums of many cells: conservation to the accumulated rounding
+    assert abs(float(np.sum(cur)) - mass0) <= 1e-5 * np.sum(np.abs(th))
+    m.close()
+
+
 @pytest.mark.parametrize("lim", ["minmod", "vanleer", "superbee", "smart"])
 def test_multi_step_rollout_fp64(fl, lim):
     wl = W.config_taylor_green(n=24, seed=1, nsteps=10, limiter=lim)

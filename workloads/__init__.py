@@ -279,6 +279,83 @@ def config_taylor_green(n=256, seed=1, cfl=0.4, nsteps=100, limiter="superbee"):
     return Workload("tg%d" % n, mesh, th, u, dt, nsteps, 3, limiter)
 
 
+def deformation_potential(n):
+    """Vector potential of the reversing 3D deformation flow of Section 4.1
+    (eq. rhodonea) on [0, 1]^3 at t = 0:
+        A = (0, -sin^2(pi x) sin(2 pi y) sin^2(pi z) / pi,
+                 sin^2(pi x) sin^2(pi y) sin(2 pi z) / pi),
+    whose curl is the paper's (u, v, w) without the factor cos(pi t / T).
+    Sample coordinates are snapped to the n-cell half-integer lattice and
+    wrapped into [0, 1), so every sample on the periodic seam is exactly zero
+    and no discrete flux crosses the domain boundary."""
+    def snap(x):
+        return np.mod(np.rint(2.0 * x * n) / 2.0, n) / n
+
+    def A(axis, x, y, z):
+        if axis == 0:
+            return np.zeros_like(x)
+        xs, ys, zs = snap(x), snap(y), snap(z)
+        sx, sy, sz = np.sin(math.pi * xs), np.sin(math.pi * ys), np.sin(math.pi * zs)
+        if axis == 1:
+            return -(sx * sx) * np.sin(TWO_PI * ys) * (sz * sz) / math.pi
+        return (sx * sx) * (sy * sy) * np.sin(TWO_PI * zs) / math.pi
+    return A
+
+
+def sphere_indicator(n, centre=(0.35, 0.35, 0.35), radius=0.15):
+    """1 in the cells of [0, 1]^3 (n^3) whose centre lies in the sphere, else 0."""
+    h = 1.0 / n
+    i, j, k, _, _, _ = _coords((n, n, n), (h, h, h))
+    x, y, z = (i + 0.5) * h, (j + 0.5) * h, (k + 0.5) * h
+    r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2
+    return (r2 <= radius * radius).astype(np.float64)
+
+
+def max_outflow_rate(dims, h, u):
+    """max over cells of sum_{outflow faces} |u_f| A_f / V_c (1 / time units)
+    for a structured mesh's face velocities (layout of structured_mesh)."""
+    nx, ny, nz = dims
+    C = nx * ny * nz
+    rate = np.zeros((nz, ny, nx))
+    for b, ax in enumerate(active_axes(dims)):
+        uf = u[b * C:(b + 1) * C].reshape(nz, ny, nx)
+        roll_axis = 2 - ax  # x varies fastest
+        out_plus = np.maximum(uf, 0.0)                          # through the + face
+        out_minus = np.maximum(-np.roll(uf, 1, axis=roll_axis), 0.0)  # through the - face
+        rate += (out_plus + out_minus) / h[ax]
+    return float(rate.max())
+
+
+def modulation_factors(nsteps, dt, rk, period, t0=0.0):
+    """cos(pi t / T) at the stage times of nsteps Euler (t_n) or SSP-RK3
+    (t_n, t_n + dt, t_n + dt / 2) steps, flattened as [n * stages + s]."""
+    t = t0 + dt * np.arange(nsteps, dtype=np.float64)
+    if rk == 1:
+        st = t[:, None]
+    else:
+        st = np.stack([t, t + dt, t + 0.5 * dt], axis=1)
+    return np.cos(math.pi * st / period).ravel()
+
+
+def config_deformation(n=72, courant=0.5, period=3.0, rk=1, limiter="superbee"):
+    """Section 4.1: a sphere (r = 0.15 at (0.35, 0.35, 0.35)) in [0, 1]^3 on
+    n^3 hexahedra, deformed by eq. rhodonea for t in [0, T], T = 3, forward
+    Euler (Algorithm 5) with superbee.  The velocity at time t is
+    cos(pi t / T) u_f with u_f the discrete curl of deformation_potential;
+    dt makes the largest per-cell outflow Courant number `courant` and divides
+    T into a whole number of steps (the flow reverses, so theta(T) returns
+    to the sphere up to the scheme's error)."""
+    h = 1.0 / n
+    mesh = structured_mesh(n, n, n, h, h, h)
+    u = curl_face_velocity((n, n, n), (h, h, h), deformation_potential(n))
+    th = sphere_indicator(n)
+    dt = courant / max_outflow_rate((n, n, n), (h, h, h), u)
+    nsteps = int(math.ceil(period / dt))
+    dt = period / nsteps
+    return Workload("deformation%d" % n, mesh, th, u, dt, nsteps, rk, limiter,
+                    extra={"period": period, "g": modulation_factors(nsteps, dt, rk, period)})
+
+
 def batched_box_dims(n_boxes=64, seed=3, lo=32, hi=128):
     rng = np.random.default_rng(seed)
     return [tuple(int(v) for v in d) for d in rng.integers(lo, hi + 1, (n_boxes, 3))]
