@@ -38,6 +38,18 @@ FALLBACK_HBM = 6800.0
 FP64_OPS_PEAK = 2 * 152 * 2.070e9
 
 
+# DRAM bytes (read + write) per launch of the dominant stage kernel at 256^3,
+# from one ncu capture of the current kernels (profiles/ keeps the summaries):
+# FP64 superbee, RK stages 2-3 (65 % of the step's kernel time); FP32
+# superbee TMA kernel, RK stage 1.  Keyed by (dtype, limiter, n).
+NCU_TRAFFIC = {
+    ("f64", "superbee", 256): (809.4e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
+                               "algorithmic 805.3e6 (48 B x 16.8M cells)"),
+    ("f32", "superbee", 256): (330.5e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
+                               "algorithmic 335.5e6 (20 B x 16.8M cells)"),
+}
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as fh:
@@ -190,17 +202,21 @@ def run_ours(args):
 
     # ---- roofline of the stage kernel (all launches in the region are it)
     hbm_peak, peak_kind = peaks()
+    traffic, traffic_note = args.traffic, None
+    if traffic is None and (args.dtype, lim, n) in NCU_TRAFFIC:
+        traffic, traffic_note = NCU_TRAFFIC[(args.dtype, lim, n)]
     bytes_step = sum(stage_bytes_per_cell(es, s) for s in range(3)) * C
     gbs = bytes_step * args.steps / (ms * 1e-3) / 1e9
     ops_step = sum(stage_fp64_ops_per_cell(lim, s) for s in range(3)) * C
     roof_hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(gbs / hbm_peak, 4), "traffic": args.traffic,
+                "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
+                "traffic_kernel": traffic_note,
                 "peak_kind": peak_kind + " copy bandwidth"}
     if args.dtype == "f64":
         ach = ops_step * args.steps / (ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_OPS_PEAK / 1e12, 4),
                 "unit": "T FP64 ops/s", "frac": round(ach * 1e12 / FP64_OPS_PEAK, 4),
-                "traffic": args.traffic,
+                "traffic": traffic, "traffic_kernel": traffic_note,
                 "peak_kind": "FP64 pipe, 2 ops/clk/SM x 152 SMs x 2070 MHz (nominal)"}
     else:
         roof = roof_hbm
