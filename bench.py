@@ -609,6 +609,104 @@ def run_config_deformation(args):
                        "cells": m.n_cells, "dt": wl.dt, "courant_outflow": 0.5}}
 
 
+# Algorithmic HBM bytes of one forward-Euler step of the algebraic chain
+# (each kernel reads its operands and writes its result once; the gathered
+# vector of an SpMV counted once, as in the paper's full-hit column).
+def algebraic_step_bytes(C, F, wT, wM):
+    ell = 12  # 8-byte value + 4-byte column
+    b = 0
+    b += 2 * ell * F + 8 * C + 8 * F            # d <- E theta
+    b += 3 * 8 * F                              # d <- Q d
+    b += wT * ell * F + 8 * C + 8 * F           # r <- T theta
+    b += 3 * 8 * F                              # r <- Q r
+    b += wT * ell * F + 8 * C + 2 * 8 * F       # r <- r + (-S) theta
+    b += 3 * 8 * F                              # r <- r / d
+    b += 3 * 8 * F                              # t <- F(r) d
+    b += 2 * ell * F + 8 * C + 2 * 8 * F        # t <- t + Pi theta
+    b += 3 * 8 * F                              # phi <- u t
+    b += wM * ell * C + 8 * F + 8 * C           # R <- M phi
+    b += 3 * 8 * C                              # theta <- theta + dt R
+    return b
+
+
+def run_config_algebraic(args):
+    """The paper's stencil-vs-algebraic comparison (Section 3's Table 2 and
+    its roofline study) on GB300: one forward-Euler superbee step of the
+    Taylor-Green field on n^3, as the fused stencil kernel (fl_step_rk) and
+    as the algebraic chain of Algorithm 1 + Algorithm 5 (8 SpMV / kbin
+    launches for theta_f, 3 for the update), both FP64."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    import workloads as W
+    fl.build()
+    n = args.n
+    h = 2 * np.pi / n
+    wl = W.config_taylor_green(n=n, seed=1, nsteps=1, limiter="superbee")
+    mesh = wl.mesh
+    dt = wl.dt
+    u = torch.tensor(wl.u, device="cuda")
+    th0 = torch.tensor(wl.theta0, device="cuda")
+    C, F = mesh.n_cells, mesh.n_faces
+    reps = max(3, args.steps)
+    e0, e1 = _events()
+    # fused
+    m = fl.Mesh.structured(n, n, n, h, h, h)
+    ws, nb = fl.workspace_for(m, torch.float64, 1)
+    th = th0.clone()
+    fl.fl_step_rk(m.handle, "superbee", torch.float64, 1, dt, 2, th, u, ws, nb)
+    torch.cuda.synchronize()
+    e0.record()
+    fl.fl_step_rk(m.handle, "superbee", torch.float64, 1, dt, reps, th, u, ws, nb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_fused = e0.elapsed_time(e1) / reps
+    fused_out = None
+    m.close()
+    del ws
+    # algebraic
+    t0 = time.perf_counter()
+    a = fl.Algebraic(C, mesh.face_cells, mesh.normals, mesh.areas, mesh.volumes)
+    t_asm = time.perf_counter() - t0
+    nnz, width, mbytes = a.info()
+    ta = th0.clone()
+    a.step_euler("superbee", ta, u, dt, 2)
+    torch.cuda.synchronize()
+    e0.record()
+    a.step_euler("superbee", ta, u, dt, reps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_alg = e0.elapsed_time(e1) / reps
+    # the two paths agree (one step from the same state)
+    tf = th0.clone()
+    m = fl.Mesh.structured(n, n, n, h, h, h)
+    fl.step_rk(m, "superbee", tf, u, dt, 1, rk_order=1)
+    tb = th0.clone()
+    a.step_euler("superbee", tb, u, dt, 1)
+    agree = float((tf - tb).abs().max() / tf.abs().max())
+    m.close()
+    a.close()
+    hbm_peak, _ = peaks()
+    b_alg = algebraic_step_bytes(C, F, width[1], width[4])
+    b_fused = 5 * 8 * C  # theta + u_f (3 faces) + theta out per cell
+    gbs_alg = b_alg / (ms_alg * 1e-3) / 1e9
+    gbs_fused = b_fused / (ms_fused * 1e-3) / 1e9
+    return {"metric": "stencil vs algebraic forward-Euler step (superbee, FP64)",
+            "value": ms_alg / ms_fused, "unit": "algebraic time / fused time",
+            "higher_is_better": False, "dtype": "f64",
+            "fused": {"ms_per_step": ms_fused, "face_updates_per_s": F / (ms_fused * 1e-3),
+                      "algorithmic_bytes_per_cell": b_fused / C, "hbm_gbs": gbs_fused,
+                      "hbm_frac": gbs_fused / hbm_peak},
+            "algebraic": {"ms_per_step": ms_alg, "face_updates_per_s": F / (ms_alg * 1e-3),
+                          "algorithmic_bytes_per_cell": b_alg / C, "hbm_gbs": gbs_alg,
+                          "hbm_frac": gbs_alg / hbm_peak, "launches_per_step": 11,
+                          "matrix_bytes": mbytes, "nnz": dict(zip(["E", "T", "-S", "Pi", "M"], nnz)),
+                          "assembly_s": t_asm},
+            "paths_agree_rel": agree,
+            "config": {"workload": "taylor_green_%d^3_euler_superbee" % n, "cells": C,
+                       "faces": F}}
+
+
 def cpu_baseline(wl, lim, budget_s):
     """The oracle as it stands on the host cores: one SSP-RK3 stage of the
     same mesh and fields (all cells), repeated while within budget."""
@@ -682,7 +780,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")
     ap.add_argument("--config", default="tg256",
-                    choices=["tg256", "1d", "unstructured", "batched", "adjoint", "deformation"])
+                    choices=["tg256", "1d", "unstructured", "batched", "adjoint", "deformation",
+                             "algebraic"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -692,7 +791,8 @@ def main():
         import numpy  # noqa: F401  (the config runners use np)
         fn = {"1d": run_config_1d, "unstructured": run_config_unstructured,
               "batched": run_config_batched, "adjoint": run_config_adjoint,
-              "deformation": run_config_deformation}[args.config]
+              "deformation": run_config_deformation,
+              "algebraic": run_config_algebraic}[args.config]
         line = fn(args)
         if line is not None:
             print(json.dumps(line))

@@ -158,6 +158,53 @@ fl_status fl_conv_limited_apply(const fl_mesh *mesh, fl_limiter limiter, fl_dtyp
 fl_status fl_face_selection(const fl_mesh *mesh, fl_dtype dtype, const void *u_f, int32_t *sel,
                             void *stream);
 
+/*
+ * ---------------------------------------------------------------------------
+ * The algebraic formulation (Section 3, Algorithm 1 and Algorithm 5): the
+ * flux limiter built from sparse matrix-vector products (ELLPACK, 8-byte
+ * values and 4-byte column indices) and pointwise kernels only, as a
+ * comparison baseline for the fused stencil kernels (the paper's stencil
+ * vs algebraic study, Table 2 and its performance analysis).  FP64 only.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct fl_alg fl_alg;
+
+/*
+ * Assemble, on the current device, the matrices of Algorithm 1 and of the
+ * update of Algorithm 5 from an explicit face-based mesh (host arrays, the
+ * layout of fl_mesh_create): E (|F| x |C|, eq. Tfc), T and -S (the two
+ * precomputed operators after eq. SimplifiedDeltaUpstream, stored with the
+ * sign that gives d_U = (Q T - S) theta for both flow directions), Pi
+ * (eq. sCF) and M = V^-1 E^T diag(A) (|C| x |F|).  Rows keep every
+ * structural entry (zero coefficients included).  Returns FL_EINVAL for
+ * out-of-range cells, self-loops, non-positive areas or volumes;
+ * FL_ENOMEM when device memory runs out.  The handle owns its device
+ * memory until fl_alg_destroy.
+ */
+fl_status fl_alg_create(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,
+                        const double *normals, const double *areas, const double *volumes,
+                        fl_alg **out);
+fl_status fl_alg_destroy(fl_alg *alg);
+/* Per matrix (E, T, -S, Pi, M): structural non-zeros, ELLPACK width; total
+ * device bytes of the five matrices.  Any output pointer may be NULL. */
+fl_status fl_alg_info(const fl_alg *alg, int64_t *nnz /*[5]*/, int32_t *width /*[5]*/,
+                      size_t *bytes);
+/* Device workspace bytes of fl_alg_face_values / fl_alg_step_euler. */
+fl_status fl_alg_workspace_size(const fl_alg *alg, size_t *bytes);
+/*
+ * Algorithm 1 as 4 SpMV + 4 pointwise launches: theta_f [n_faces] from
+ * theta [n_cells] and u_f [n_faces] (device, FP64, the mesh's order).
+ * u_f = 0, -0 and NaN select -1; d_u == 0 gives the upwind value.
+ */
+fl_status fl_alg_face_values(const fl_alg *alg, fl_limiter limiter, const void *theta,
+                             const void *u_f, void *theta_f, void *workspace,
+                             size_t workspace_bytes, void *stream);
+/* Algorithm 5: nsteps forward-Euler steps theta <- theta + dt M U(u_f) theta_f
+ * in place (Algorithm 1, then U, M and the update as 1 SpMV + 2 pointwise). */
+fl_status fl_alg_step_euler(const fl_alg *alg, fl_limiter limiter, double dt, int64_t nsteps,
+                            void *theta, const void *u_f, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
 /* Bytes of device workspace fl_step_rk needs (rk_order 1 or 3). */
 fl_status fl_workspace_size(const fl_mesh *mesh, fl_dtype dtype, int rk_order, size_t *bytes);
 

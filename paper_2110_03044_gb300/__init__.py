@@ -39,6 +39,8 @@ ABI_SYMBOLS = [
     "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_checkpointed",
     "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
     "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_destroy",
+    "fl_alg_create", "fl_alg_destroy", "fl_alg_info", "fl_alg_workspace_size",
+    "fl_alg_face_values", "fl_alg_step_euler",
     "fl_reduce_workspace_size", "fl_reduce_max_abs", "fl_reduce_mass",
 ]
 
@@ -101,6 +103,12 @@ def lib():
             "fl_batch_workspace_size": (I, [P, I, I, ctypes.POINTER(SZ)]),
             "fl_batch_step_rk": (I, [P, I, I, I, ctypes.POINTER(D), I64, PP, PP, P, SZ, P]),
             "fl_batch_destroy": (I, [P]),
+            "fl_alg_create": (I, [I64, I64, P, P, P, P, ctypes.POINTER(P)]),
+            "fl_alg_destroy": (I, [P]),
+            "fl_alg_info": (I, [P, P, P, ctypes.POINTER(SZ)]),
+            "fl_alg_workspace_size": (I, [P, ctypes.POINTER(SZ)]),
+            "fl_alg_face_values": (I, [P, I, P, P, P, P, SZ, P]),
+            "fl_alg_step_euler": (I, [P, I, D, I64, P, P, P, SZ, P]),
             "fl_reduce_workspace_size": (SZ, []),
             "fl_reduce_max_abs": (I, [I, P, I64, ctypes.POINTER(D), P, P]),
             "fl_reduce_mass": (I, [P, I, P, ctypes.POINTER(D), P, P]),
@@ -321,6 +329,54 @@ def fl_batch_destroy(batch):
     _check(lib().fl_batch_destroy(batch))
 
 
+def fl_alg_create(n_cells, face_cells, normals, areas, volumes):
+    """Matrices of the algebraic formulation (E, T, -S, Pi, M in ELLPACK) on
+    the current device from host face arrays; returns the handle."""
+    import numpy as np
+    fc = np.ascontiguousarray(face_cells, dtype=np.int32)
+    nrm = np.ascontiguousarray(normals, dtype=np.float64)
+    ar = np.ascontiguousarray(areas, dtype=np.float64)
+    vol = np.ascontiguousarray(volumes, dtype=np.float64)
+    h = ctypes.c_void_p()
+    vp = ctypes.c_void_p
+    _check(lib().fl_alg_create(int(n_cells), int(fc.shape[0]), fc.ctypes.data_as(vp),
+                               nrm.ctypes.data_as(vp), ar.ctypes.data_as(vp),
+                               vol.ctypes.data_as(vp), ctypes.byref(h)))
+    return h.value
+
+
+def fl_alg_destroy(alg):
+    _check(lib().fl_alg_destroy(alg))
+
+
+def fl_alg_info(alg):
+    """(nnz[5], width[5], device bytes) for E, T, -S, Pi, M."""
+    nnz = (ctypes.c_int64 * 5)()
+    width = (ctypes.c_int32 * 5)()
+    b = ctypes.c_size_t()
+    _check(lib().fl_alg_info(alg, nnz, width, ctypes.byref(b)))
+    return list(nnz), list(width), b.value
+
+
+def fl_alg_workspace_size(alg):
+    n = ctypes.c_size_t()
+    _check(lib().fl_alg_workspace_size(alg, ctypes.byref(n)))
+    return n.value
+
+
+def fl_alg_face_values(alg, limiter, theta, u_f, theta_f, workspace, workspace_bytes,
+                       stream=None):
+    _check(lib().fl_alg_face_values(alg, _lim(limiter), _ptr(theta), _ptr(u_f), _ptr(theta_f),
+                                    _ptr(workspace), int(workspace_bytes), _stream(stream)))
+
+
+def fl_alg_step_euler(alg, limiter, dt, nsteps, theta, u_f, workspace, workspace_bytes,
+                      stream=None):
+    _check(lib().fl_alg_step_euler(alg, _lim(limiter), float(dt), int(nsteps), _ptr(theta),
+                                   _ptr(u_f), _ptr(workspace), int(workspace_bytes),
+                                   _stream(stream)))
+
+
 def fl_reduce_workspace_size():
     return int(lib().fl_reduce_workspace_size())
 
@@ -407,6 +463,39 @@ def step_rk_modulated(mesh, limiter, theta, u_f, dt, nsteps, g, rk_order=1, work
     fl_step_rk_modulated(mesh.handle, limiter, theta.dtype, rk_order, dt, nsteps, theta, u_f, g,
                          workspace, nbytes, stream)
     return theta
+
+
+class Algebraic:
+    """The algebraic formulation (Algorithm 1 / Algorithm 5 as SpMV + kbin)
+    of a face-based mesh, FP64, for comparison with the fused kernels."""
+
+    def __init__(self, n_cells, face_cells, normals, areas, volumes):
+        import torch
+        self.handle = fl_alg_create(n_cells, face_cells, normals, areas, volumes)
+        self.n_cells = int(n_cells)
+        self.n_faces = int(len(areas))
+        nb = fl_alg_workspace_size(self.handle)
+        self.ws = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+        self.ws_bytes = nb
+
+    def info(self):
+        return fl_alg_info(self.handle)
+
+    def face_values(self, limiter, theta, u_f, stream=None):
+        import torch
+        out = torch.empty(self.n_faces, dtype=torch.float64, device=theta.device)
+        fl_alg_face_values(self.handle, limiter, theta, u_f, out, self.ws, self.ws_bytes, stream)
+        return out
+
+    def step_euler(self, limiter, theta, u_f, dt, nsteps, stream=None):
+        fl_alg_step_euler(self.handle, limiter, dt, nsteps, theta, u_f, self.ws, self.ws_bytes,
+                          stream)
+        return theta
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fl_alg_destroy(self.handle)
+            self.handle = None
 
 
 def conv_limited_apply(mesh, limiter, theta, u_f, want_theta_f=False, stream=None):
