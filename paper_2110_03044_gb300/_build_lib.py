@@ -20,8 +20,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfl.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
-              "-I" + INCLUDE]
+# host code keeps separate multiplies and adds (no contraction), so that mesh
+# set-up arithmetic such as n_f . n_j is the plain IEEE expression
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
+              "-ffp-contract=off", "-Xptxas", "-v", "-I" + INCLUDE]
 
 
 def _nvcc():

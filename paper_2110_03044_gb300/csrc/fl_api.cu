@@ -334,7 +334,11 @@ fl_status step_rk_impl(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, do
   }
   if (nsteps == 0 || m->C == 0) return FL_OK;
   cudaStream_t st = as_stream(stream);
-  if (m->kind == 1) return unstruct_step(m, lim, dt, rk, dtime, nsteps, theta, u_f, ws, st, gfac);
+  if (m->kind == 1) {
+    void *W = struct_step_prescales(m, dt) ? static_cast<char *>(ws) + step_stage_bytes(m, dt, rk)
+                                           : nullptr;
+    return unstruct_step(m, lim, dt, rk, dtime, nsteps, theta, u_f, ws, st, gfac, W);
+  }
   if (gfac == nullptr && m->ny == 1 && m->nz == 1 &&
       (size_t)m->nx <= line_resident_max_cells(dt)) {
     cudaError_t e = line_resident(m, lim, dt, theta, u_f, nsteps, rk, dtime, st);

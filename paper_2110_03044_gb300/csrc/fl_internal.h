@@ -72,6 +72,13 @@ struct UnstructDev {
   double *inv_vol = nullptr;     // [n_cells]
   float *area_f = nullptr;
   float *inv_vol_f = nullptr;
+  // general polyhedra (a cell face with no single opposite face): per face
+  // and side (0: C = c0, 1: C = c1) kg pairs (cell, coefficient) with
+  // s d_U = sum_k coef_k (theta_{cell_k} - theta_C); padding has coef 0
+  int kg = 0;
+  int32_t *gen_cell = nullptr;   // [n_faces][2][kg]
+  double *gen_coef = nullptr;    // [n_faces][2][kg]
+  float *gen_coef_f = nullptr;
 };
 
 }  // namespace fl

@@ -29,14 +29,20 @@ namespace fl {
 
 namespace {
 
+// rows of cells per CTA (a tile is 32 x STY); 4 CTAs of 256 threads per SM
+#ifndef FL_STRUCT_TY
+#define FL_STRUCT_TY 8
+#endif
+constexpr int STY = FL_STRUCT_TY;
+
 template <class T, int LIM, int SEED, int TY, bool PRE, bool MOD>
-__global__ void __launch_bounds__(TX *TY, 4) k_struct_stage(const SParams<T> p) {
+__global__ void __launch_bounds__(TX *TY, 32 / TY) k_struct_stage(const SParams<T> p) {
   stage_tile<T, LIM, SEED, TY, PRE, MOD>(p, blockIdx.x);
 }
 
 template <class T, int LIM, int SEED, bool PRE, bool MOD>
 cudaError_t launch_stage(const SParams<T> &p0, int tiles_z, cudaStream_t st) {
-  constexpr int TY = 8;
+  constexpr int TY = STY;
   SParams<T> p = p0;
   const dim3 block(TX, TY);
   const long long grid = (long long)p.tiles_x * p.tiles_y * tiles_z;
@@ -108,14 +114,14 @@ cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStrea
   p.a = (T)s.a;
   p.b = (T)s.b;
   p.tiles_x = (m->nx + TX - 1) / TX;
-  p.tiles_y = (m->ny + 7) / 8;
+  p.tiles_y = (m->ny + STY - 1) / STY;
   // z chunks: whole waves of co-resident CTAs (the occupancy of the PLAIN
   // kernel stands for all variants: same block, similar registers)
   const long long cols = (long long)p.tiles_x * p.tiles_y;
   const int resident =
-      resident_ctas(reinterpret_cast<const void *>(&k_struct_stage<T, LIM_SUPERBEE, SEED_PLAIN, 8,
+      resident_ctas(reinterpret_cast<const void *>(&k_struct_stage<T, LIM_SUPERBEE, SEED_PLAIN, STY,
                                                                    false, false>),
-                    TX * 8, 0);
+                    TX * STY, 0);
   const int zchunk = pick_zchunk(cols, m->nz, resident, 2);
   p.zchunk = zchunk;
   const int tz = (m->nz + zchunk - 1) / zchunk;
@@ -297,8 +303,9 @@ cudaError_t struct_scale_faces(const fl_mesh *m, fl_dtype dt, const void *u, voi
 }
 
 bool struct_step_prescales(const fl_mesh *m, fl_dtype dt) {
-  return m->kind == 0 && dt == FL_F64 &&
-         !(m->ny == 1 && m->nz == 1 && (size_t)m->nx <= line_resident_max_cells(dt));
+  if (dt != FL_F64) return false;
+  if (m->kind == 1) return true;  // face-based meshes: w_f = dt A_f u_f
+  return !(m->ny == 1 && m->nz == 1 && (size_t)m->nx <= line_resident_max_cells(dt));
 }
 
 cudaError_t struct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,

@@ -12,6 +12,12 @@
 // and sigma for both flow directions of every face, so the kernel gathers
 // three cell values per face: theta_c0, theta_c1 and theta_U.
 //
+// Meshes of other polyhedra (tetrahedra, prisms, mixed) have faces without a
+// single opposite face; for them mesh creation stores, per face and flow
+// direction, every other face j of the upwind cell as a pair (the cell
+// across j, coefficient (n_f . n_j) eps_j), eps_j = +1 when C is c0 of j,
+// so that s d_U = sum_j coef_j (theta_j - theta_C), and the kernel sums it.
+//
 // Kernel: one CTA per cell block (a compact patch of cells in the internal
 // numbering).  Phase 1 evaluates every face of the block's list once --
 // upwind selection, limited theta_f and the flux u_f A_f theta_f -- into
@@ -59,7 +65,11 @@ struct UParams {
   const T *area;
   const T *inv_vol;
   T a, b, bdt;  // RK combination a*thn + b*x and b*dt (times the velocity factor)
+  T g;          // PRE: velocity factor of the stage
   unsigned long long flip;  // sign mask toggled into u_f before the upwind test
+  const int32_t *gen_cell;  // GEN: general upstream stencil (see UnstructDev)
+  const T *gen_coef;
+  int kg;
 };
 
 template <class T>
@@ -68,7 +78,11 @@ __device__ __forceinline__ T flip_sign(T v, bool neg) {
   return F::val(F::bits(v) ^ (neg ? F::SIGN : typename F::U(0)));
 }
 
-template <class T, int LIM, int SEED>
+// PRE: p.u holds w_f = dt A_f u_f (pre-scaled once per call, same signs);
+// phase 1 keeps theta_f and w_f of every face, and phase 2 adds w theta_f of
+// each of the cell's faces with one fma -- the two flux products per face
+// disappear.  The block's shared memory then holds both arrays.
+template <class T, int LIM, int SEED, bool PRE, bool GEN>
 __global__ void __launch_bounds__(UTHREADS) k_unstruct_stage(const UParams<T> p) {
   using F = FT<T>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -84,17 +98,53 @@ __global__ void __launch_bounds__(UTHREADS) k_unstruct_stage(const UParams<T> p)
     const bool sp = upwind_positive(sign_toggled(uf, p.flip));
     const T t0 = p.x[cc.x];
     const T t1 = p.x[cc.y];
-    const unsigned up = sp ? (unsigned)cc.z : (unsigned)cc.w;
-    const T tU = p.x[up & ~SIGMA_BIT];
     const T tC = sp ? t0 : t1;
     const T a = F::sub(t1, t0);
-    // b = s d_U = s sigma (theta_C - theta_U)
-    const T bU = flip_sign(F::sub(tC, tU), (!sp) != ((up & SIGMA_BIT) != 0));
+    T bU;
+    if (GEN) {
+      // b = s d_U = sum_j coef_j (theta_j - theta_C) over the other faces of C
+      const size_t base = ((size_t)f * 2 + (sp ? 0 : 1)) * (size_t)p.kg;
+      bU = T(0);
+      for (int k = 0; k < p.kg; ++k)
+        bU = F::fma(p.gen_coef[base + k], F::sub(p.x[p.gen_cell[base + k]], tC), bU);
+    } else {
+      const unsigned up = sp ? (unsigned)cc.z : (unsigned)cc.w;
+      const T tU = p.x[up & ~SIGMA_BIT];
+      // b = s d_U = s sigma (theta_C - theta_U)
+      bU = flip_sign(F::sub(tC, tU), (!sp) != ((up & SIGMA_BIT) != 0));
+    }
     const T thf = limited_face<T, LIM>(tC, a, bU, sp);
-    s_phi[e - eb] = F::mul(F::mul(uf, p.area[f]), thf);
+    if (PRE) {
+      s_phi[e - eb] = thf;
+      s_phi[(ee - eb) + (e - eb)] = uf;
+    } else {
+      s_phi[e - eb] = F::mul(F::mul(uf, p.area[f]), thf);
+    }
     if (SEED == 2 && p.thf != nullptr && cc.x >= cb && cc.x < ce) p.thf[f] = thf;
   }
   __syncthreads();
+  if (PRE) {
+    // phase 2 with the folded flux product: y = x - (g / V) sum sigma w theta_f
+    const T *s_w = s_phi + (ee - eb);
+    for (int c = cb + (int)threadIdx.x; c < ce; c += UTHREADS) {
+      const uint4 sl = *reinterpret_cast<const uint4 *>(p.slots + (size_t)c * UMAXDEG);
+      const unsigned w[4] = {sl.x, sl.y, sl.z, sl.w};
+      T acc = T(0);
+#pragma unroll
+      for (int q = 0; q < 2 * 4; ++q) {
+        const unsigned s16 = (w[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
+        if (s16 != 0xFFFFu) {
+          const unsigned k = s16 & 0x7FFFu;
+          acc = F::fma(flip_sign(s_w[k], (s16 & 0x8000u) != 0), s_phi[k], acc);
+        }
+      }
+      const T coef = F::mul(p.g, p.inv_vol[c]);
+      T out = F::fma(-coef, acc, p.x[c]);
+      if (SEED == 1) out = F::fma(p.b, out, F::mul(p.a, p.thn[c]));
+      p.y[c] = out;
+    }
+    return;
+  }
   // ---- phase 2: cell sums fused with the stage update
   for (int c = cb + (int)threadIdx.x; c < ce; c += UTHREADS) {
     const uint4 sl = *reinterpret_cast<const uint4 *>(p.slots + (size_t)c * UMAXDEG);
@@ -118,6 +168,19 @@ __global__ void __launch_bounds__(UTHREADS) k_unstruct_stage(const UParams<T> p)
   }
 }
 
+// w_f = (u_f A_f) dt; a product that underflows keeps the sign of u_f
+__global__ void k_scale_area(const double *u, const double *area, double *w, long long nf,
+                             double dt) {
+  using F = FT<double>;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
+       f += (long long)gridDim.x * blockDim.x) {
+    const double uf = u[f];
+    double v = F::mul(F::mul(uf, area[f]), dt);
+    if (upwind_positive(uf) && !upwind_positive(v)) v = F::val(1);
+    w[f] = v;
+  }
+}
+
 template <class T>
 __global__ void k_unstruct_selection(const T *u, const int4 *c4, int4 *sel, long long nf) {
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
@@ -128,19 +191,21 @@ __global__ void k_unstruct_selection(const T *u, const int4 *c4, int4 *sel, long
     o.x = sp ? 1 : -1;
     o.y = sp ? cc.x : cc.y;
     o.z = sp ? cc.y : cc.x;
-    o.w = (int)((unsigned)(sp ? cc.z : cc.w) & ~SIGMA_BIT);
+    const unsigned upv = (unsigned)(sp ? cc.z : cc.w);
+    // general polyhedra: -1 unless exactly one other face of C has n_f . n_j != 0
+    o.w = (upv == 0xFFFFFFFFu) ? -1 : (int)(upv & ~SIGMA_BIT);
     sel[f] = o;
   }
 }
 
-template <class T, int SEED>
+template <class T, int SEED, bool PRE, bool GEN>
 cudaError_t launch_lim(int lim, const fl_mesh *m, const UParams<T> &p, cudaStream_t st) {
   const int nb = m->u.n_blocks;
-  const size_t smem = (size_t)m->u.max_block_entries * sizeof(T);
+  const size_t smem = (size_t)m->u.max_block_entries * sizeof(T) * (PRE ? 2 : 1);
   if (nb == 0) return cudaSuccess;
 #define FL_U_CASE(L)                                                                           \
   case L: {                                                                                    \
-    auto k = k_unstruct_stage<T, L, SEED>;                                                     \
+    auto k = k_unstruct_stage<T, L, SEED, PRE, GEN>;                                           \
     if (smem > 48 * 1024) {                                                                    \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                            (int)smem);                                         \
@@ -161,6 +226,22 @@ cudaError_t launch_lim(int lim, const fl_mesh *m, const UParams<T> &p, cudaStrea
   return cudaErrorInvalidValue;
 }
 
+template <class T, bool GEN>
+cudaError_t dispatch_seed(int lim, const fl_mesh *m, const UParams<T> &p, int seed, bool pre,
+                          cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    if (pre) {
+      if (seed == 0) return launch_lim<T, 0, true, GEN>(lim, m, p, st);
+      return launch_lim<T, 1, true, GEN>(lim, m, p, st);
+    }
+  }
+  switch (seed) {
+    case 0: return launch_lim<T, 0, false, GEN>(lim, m, p, st);
+    case 1: return launch_lim<T, 1, false, GEN>(lim, m, p, st);
+    default: return launch_lim<T, 2, false, GEN>(lim, m, p, st);
+  }
+}
+
 template <class T>
 cudaError_t run_ustage(const fl_mesh *m, int lim, const StageArgs &s, cudaStream_t st) {
   UParams<T> p;
@@ -168,7 +249,8 @@ cudaError_t run_ustage(const fl_mesh *m, int lim, const StageArgs &s, cudaStream
   p.thn = static_cast<const T *>(s.thn);
   p.y = static_cast<T *>(s.y);
   p.thf = static_cast<T *>(s.thf);
-  p.u = static_cast<const T *>(s.u);
+  const bool pre = s.w != nullptr && sizeof(T) == 8 && s.seed != 2;
+  p.u = static_cast<const T *>(pre ? s.w : s.u);
   p.blk_cell = m->u.blk_cell;
   p.blk_entry = m->u.blk_entry;
   p.ent_face = m->u.ent_face;
@@ -187,12 +269,14 @@ cudaError_t run_ustage(const fl_mesh *m, int lim, const StageArgs &s, cudaStream
   // every face's upwind side (the bare operator has g = 1)
   const double g = (s.seed == 2) ? 1.0 : s.g;
   p.bdt = (T)(s.b * s.dt * g);
+  p.g = (T)g;
   p.flip = (g < 0) ? (sizeof(T) == 8 ? 0x8000000000000000ull : 0x80000000ull) : 0ull;
-  switch (s.seed) {
-    case 0: return launch_lim<T, 0>(lim, m, p, st);
-    case 1: return launch_lim<T, 1>(lim, m, p, st);
-    default: return launch_lim<T, 2>(lim, m, p, st);
-  }
+  p.kg = m->u.kg;
+  p.gen_cell = m->u.gen_cell;
+  p.gen_coef = (sizeof(T) == 8) ? reinterpret_cast<const T *>(m->u.gen_coef)
+                                : reinterpret_cast<const T *>(m->u.gen_coef_f);
+  if (m->u.kg > 0) return dispatch_seed<T, true>(lim, m, p, s.seed, pre, st);
+  return dispatch_seed<T, false>(lim, m, p, s.seed, pre, st);
 }
 
 // ============================================================ host build
@@ -485,6 +569,7 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
     h.up[side].assign(F, -1);
     h.sig[side].assign(F, 0);
   }
+  std::atomic<bool> general(false);
   parallel_for(C, [&](int64_t lo, int64_t hi) {
     double nrm[UMAXDEG][3];
     int32_t fl_[UMAXDEG];
@@ -514,16 +599,14 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
             bstar = b;
             wstar = w;
           } else if (std::fabs(w) > 1e-9) {
-            return err.put(FL_EUNSUPPORTED,
-                           "face %lld: a neighbouring face is neither parallel nor orthogonal "
-                           "(general polyhedral meshes are not supported)", f);
+            found = -1;  // neither parallel nor orthogonal: a general polyhedron
+            break;
           }
         }
-        if (found != 1)
-          return err.put(FL_EUNSUPPORTED, "face %lld: %lld faces of its cell are opposite it "
-                         "(need exactly 1)", f, found);
-        if (std::fabs(std::fabs(wstar) - 1.0) > 1e-9)
-          return err.put(FL_EUNSUPPORTED, "face %lld: opposite face is not parallel", f);
+        if (found != 1 || std::fabs(std::fabs(wstar) - 1.0) > 1e-9) {
+          general.store(true);
+          continue;
+        }
         const int32_t j = fl_[bstar];
         // side 0: C is c0 of f (flow c0 -> c1); side 1: C is c1 of f
         const int side = (h.c0[f] == Cc) ? 0 : 1;
@@ -537,6 +620,43 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
     }
   });
   if (err.set.load()) return fail(err.st, "%s", err.msg);
+  // ---- general polyhedra: the weighted upstream stencil of every face and
+  // side (the oracle's definition: all other faces j of C, weight n_f . n_j)
+  int kg = 0;
+  std::vector<int32_t> gcell;
+  std::vector<double> gcoef;
+  if (general.load()) {
+    for (int64_t c = 0; c < C; ++c) kg = std::max<int>(kg, (int)(h.cf_ptr[c + 1] - h.cf_ptr[c]) - 1);
+    kg = std::max(kg, 1);
+    gcell.assign((size_t)F * 2 * kg, 0);
+    gcoef.assign((size_t)F * 2 * kg, 0.0);
+    parallel_for(F, [&](int64_t lo, int64_t hi) {
+      for (int64_t f = lo; f < hi; ++f)
+        for (int side = 0; side < 2; ++side) {
+          const int32_t Cc = side == 0 ? h.c0[f] : h.c1[f];
+          const size_t base = ((size_t)f * 2 + side) * kg;
+          int k = 0, nonzero = 0;
+          int32_t U = -1;
+          for (int64_t q = h.cf_ptr[Cc]; q < h.cf_ptr[Cc + 1]; ++q) {
+            const int32_t j = h.cf_idx[q];
+            if (j == f) continue;
+            const double w = dot3(&h.n[3 * f], &h.n[3 * (int64_t)j]);
+            const bool c_is_c0 = (h.c0[j] == Cc);
+            const int32_t other = c_is_c0 ? h.c1[j] : h.c0[j];
+            gcell[base + k] = other;
+            gcoef[base + k] = c_is_c0 ? w : -w;
+            ++k;
+            if (w != 0.0) {
+              ++nonzero;
+              U = other;
+            }
+          }
+          for (; k < kg; ++k) gcell[base + k] = Cc;  // coef 0: no contribution
+          h.up[side][f] = (nonzero == 1) ? U : -1;
+          h.sig[side][f] = 1;
+        }
+    });
+  }
   // ---- internal numbering
   std::vector<int32_t> order, blk_cell;
   const bool renum = (flags & FL_RENUMBER) != 0;
@@ -577,8 +697,12 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
     int4 r;
     r.x = cell_new[h.c0[f]];
     r.y = cell_new[h.c1[f]];
-    r.z = (int)((unsigned)cell_new[h.up[0][f]] | (h.sig[0][f] < 0 ? SIGMA_BIT : 0u));
-    r.w = (int)((unsigned)cell_new[h.up[1][f]] | (h.sig[1][f] < 0 ? SIGMA_BIT : 0u));
+    // (general polyhedra: the single upstream cell where one exists, else -1;
+    // the kernel reads the weighted stencil instead)
+    r.z = h.up[0][f] < 0 ? -1
+                         : (int)((unsigned)cell_new[h.up[0][f]] | (h.sig[0][f] < 0 ? SIGMA_BIT : 0u));
+    r.w = h.up[1][f] < 0 ? -1
+                         : (int)((unsigned)cell_new[h.up[1][f]] | (h.sig[1][f] < 0 ? SIGMA_BIT : 0u));
     c4[fi] = r;
     area_i[fi] = areas[f];
   }
@@ -694,6 +818,25 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   if (st == FL_OK) st = upload(ivol_i, &u.inv_vol);
   if (st == FL_OK) st = upload(area_f, &u.area_f);
   if (st == FL_OK) st = upload(ivol_f, &u.inv_vol_f);
+  if (st == FL_OK && kg > 0) {
+    // the stencil in internal numbering: rows by internal face, cells renamed
+    std::vector<int32_t> gc((size_t)F * 2 * kg);
+    std::vector<double> gw((size_t)F * 2 * kg);
+    parallel_for(F, [&](int64_t lo, int64_t hi) {
+      for (int64_t f = lo; f < hi; ++f) {
+        const size_t src = (size_t)f * 2 * kg, dst = (size_t)face_new[f] * 2 * kg;
+        for (int q = 0; q < 2 * kg; ++q) {
+          gc[dst + q] = cell_new[gcell[src + q]];
+          gw[dst + q] = gcoef[src + q];
+        }
+      }
+    });
+    std::vector<float> gwf(gw.begin(), gw.end());
+    u.kg = kg;
+    st = upload(gc, &u.gen_cell);
+    if (st == FL_OK) st = upload(gw, &u.gen_coef);
+    if (st == FL_OK) st = upload(gwf, &u.gen_coef_f);
+  }
   if (st != FL_OK) {
     unstruct_free(m);
     delete m;
@@ -706,7 +849,8 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
 void unstruct_free(fl_mesh *m) {
   UnstructDev &u = m->u;
   void *ptrs[] = {u.blk_cell, u.blk_entry, u.ent_face, u.ent_cells, u.cell_slots, u.face_c4,
-                  u.area, u.vol, u.inv_vol, u.area_f, u.inv_vol_f};
+                  u.area, u.vol, u.inv_vol, u.area_f, u.inv_vol_f, u.gen_cell, u.gen_coef,
+                  u.gen_coef_f};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   u = UnstructDev();
@@ -733,7 +877,7 @@ fl_status unstruct_apply(const fl_mesh *m, int lim, fl_dtype dt, const void *the
 
 fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
                         int64_t nsteps, void *theta, const void *u, void *ws, cudaStream_t st,
-                        const double *gfac) {
+                        const double *gfac, void *W) {
   const size_t es = dsize(dt);
   char *wsb = static_cast<char *>(ws);
   void *A = wsb;
@@ -742,6 +886,16 @@ fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double d
   s.u = u;
   s.dt = dtime;
   cudaError_t e = cudaSuccess;
+  // FP64: w_f = dt A_f u_f once per call (dt > 0 keeps every sign)
+  if (W != nullptr && dt == FL_F64 && dtime > 0 && m->F > 0) {
+    long long blocks = (m->F + 255) / 256;
+    if (blocks > 152LL * 32) blocks = 152LL * 32;
+    k_scale_area<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const double *>(u), m->u.area,
+                                                   static_cast<double *>(W), m->F, dtime);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "velocity pre-scaling");
+    s.w = W;
+  }
   if (rk == 1) {
     void *cur = theta, *nxt = A;
     for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {

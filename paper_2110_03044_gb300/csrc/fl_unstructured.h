@@ -15,7 +15,7 @@ fl_status unstruct_apply(const fl_mesh *m, int lim, fl_dtype dt, const void *the
                          void *rhs, void *thf, cudaStream_t st);
 fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
                         int64_t nsteps, void *theta, const void *u, void *ws, cudaStream_t st,
-                        const double *gfac = nullptr);
+                        const double *gfac = nullptr, void *W = nullptr);
 cudaError_t unstruct_selection(const fl_mesh *m, fl_dtype dt, const void *u, int32_t *sel,
                                cudaStream_t st);
 const double *unstruct_volumes(const fl_mesh *m);

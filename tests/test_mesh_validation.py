@@ -62,12 +62,24 @@ def test_rejects_duplicated_face(fl):
     assert e.value.status in (fl.FL_EINVAL, fl.FL_EUNSUPPORTED)
 
 
-def test_rejects_non_hexahedral_mesh(fl):
-    # a face tilted 45 degrees: neither parallel nor orthogonal to its
-    # neighbours (general polyhedra are not supported)
-    m = _box()
-    nrm = m.normals.copy()
-    nrm[0] = np.array([1.0, 1.0, 0.0]) / np.sqrt(2.0)
+def test_general_polyhedra_pass_host_validation(fl):
+    # tetrahedra have no opposite faces: the mesh takes the general
+    # weighted upstream stencil, and every host-side check passes (on a
+    # machine without a GPU creation stops only at the device step)
+    import workloads as W
+    m = W.tet_mesh(3)
     with pytest.raises(fl.FLError) as e:
-        _create(fl, m, nrm=nrm)
-    assert e.value.status == fl.FL_EUNSUPPORTED
+        _create(fl, m)
+    assert e.value.status == fl.FL_ECUDA
+
+
+def test_rejects_cells_with_too_many_faces(fl):
+    # more than 8 faces on one cell: beyond the per-cell slot table
+    m = _box()
+    extra = 4
+    fc = np.concatenate([m.face_cells, np.tile(m.face_cells[:1], (extra, 1))])
+    nrm = np.concatenate([m.normals, np.tile(m.normals[:1], (extra, 1))])
+    ar = np.concatenate([m.areas, np.tile(m.areas[:1], extra)])
+    with pytest.raises(fl.FLError) as e:
+        _create(fl, m, fc=fc, nrm=nrm, ar=ar)
+    assert e.value.status in (fl.FL_EINVAL, fl.FL_EUNSUPPORTED)

@@ -90,6 +90,110 @@ def structured_mesh(nx: int, ny: int = 1, nz: int = 1, hx: float = 1.0,
     return Mesh(n, face_cells, normals, areas, volumes, dims=dims, h=hs)
 
 
+# --------------------------------------------------------------------------
+# general (non-hexahedral) periodic meshes
+# --------------------------------------------------------------------------
+def _lattice_id(v, n):
+    v = np.mod(v, n)
+    return v[..., 0] + n * (v[..., 1] + n * v[..., 2])
+
+
+def _box_origins(n):
+    o = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), -1)
+    return o.transpose(2, 1, 0, 3).reshape(-1, 3)  # x fastest
+
+
+def polyhedral_mesh(n, h, face_groups, volumes):
+    """Face-based periodic mesh of the box [0, n h)^3 from cells given by
+    their faces: ``face_groups`` is a list of (cell index [m], polygon
+    vertices [m, nv, 3]) in integer lattice coordinates (unwrapped, so each
+    polygon is geometrically intact).  Faces are matched by their wrapped
+    vertex sets; every face must be shared by exactly two cells.  The normal
+    is the unit Newell normal, oriented from c0 (first occurrence) to c1."""
+    c0s, c1s, nrms, areas = [], [], [], []
+    centroid_sum = np.zeros((len(volumes), 3))
+    centroid_cnt = np.zeros(len(volumes))
+    for cells, poly in face_groups:
+        np.add.at(centroid_sum, cells, poly.mean(axis=1) * h)
+        np.add.at(centroid_cnt, cells, 1.0)
+    cen = centroid_sum / centroid_cnt[:, None]
+    for cells, poly in face_groups:
+        m, nv, _ = poly.shape
+        keys = np.sort(_lattice_id(poly, n), axis=1)
+        _, inv, cnt = np.unique(keys, axis=0, return_inverse=True, return_counts=True)
+        inv = inv.ravel()
+        if not np.all(cnt == 2):
+            raise ValueError("a face is not shared by exactly two cells")
+        order = np.argsort(inv, kind="stable")
+        first, second = order[0::2], order[1::2]
+        P = poly[first].astype(np.float64) * h
+        nrm = np.zeros((len(first), 3))
+        for a in range(nv):
+            p, q = P[:, a], P[:, (a + 1) % nv]
+            nrm[:, 0] += (p[:, 1] - q[:, 1]) * (p[:, 2] + q[:, 2])
+            nrm[:, 1] += (p[:, 2] - q[:, 2]) * (p[:, 0] + q[:, 0])
+            nrm[:, 2] += (p[:, 0] - q[:, 0]) * (p[:, 1] + q[:, 1])
+        a2 = np.linalg.norm(nrm, axis=1)
+        unit = nrm / a2[:, None]
+        c0 = cells[first]
+        outward = np.einsum("ij,ij->i", unit, P.mean(axis=1) - cen[c0]) > 0
+        unit[~outward] *= -1.0
+        unit[unit == 0.0] = 0.0  # no negative zeros
+        c0s.append(c0)
+        c1s.append(cells[second])
+        nrms.append(unit)
+        areas.append(0.5 * a2)
+    fc = np.stack([np.concatenate(c0s), np.concatenate(c1s)], axis=1).astype(np.int32)
+    return Mesh(len(volumes), fc, np.concatenate(nrms), np.concatenate(areas),
+                np.asarray(volumes, dtype=np.float64))
+
+
+def tet_mesh(n, h=None):
+    """Periodic box of n^3 cubes, each split into the 6 tetrahedra of the
+    Kuhn (Freudenthal) triangulation around its main diagonal, which match
+    across cube faces: 6 n^3 cells with 4 triangular faces each."""
+    h = 1.0 / n if h is None else h
+    e = np.eye(3, dtype=np.int64)
+    tets = []
+    for p in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        v1 = e[p[0]]
+        v2 = v1 + e[p[1]]
+        tets.append(np.stack([np.zeros(3, dtype=np.int64), v1, v2, np.ones(3, dtype=np.int64)]))
+    tets = np.stack(tets)                                       # [6, 4, 3]
+    o = _box_origins(n)
+    verts = (o[:, None, None, :] + tets[None]).reshape(-1, 4, 3)
+    nc = verts.shape[0]
+    poly = np.stack([verts[:, [1, 2, 3]], verts[:, [0, 2, 3]], verts[:, [0, 1, 3]],
+                     verts[:, [0, 1, 2]]], axis=1).reshape(-1, 3, 3)
+    cells = np.repeat(np.arange(nc), 4)
+    return polyhedral_mesh(n, h, [(cells, poly)], np.full(nc, h ** 3 / 6.0))
+
+
+def prism_mesh(n, h=None):
+    """Periodic box of n^3 cubes, each split along its xy diagonal into two
+    triangular prisms: 2 n^3 cells with 2 triangular and 3 quadrilateral
+    faces each (axis-aligned and diagonal quads)."""
+    h = 1.0 / n if h is None else h
+    tris = np.array([[[0, 0], [1, 0], [1, 1]], [[0, 0], [1, 1], [0, 1]]], dtype=np.int64)
+    o = _box_origins(n)
+    nc = 2 * o.shape[0]
+    tri_polys, quad_polys, tri_cells, quad_cells = [], [], [], []
+    for t in range(2):
+        base = np.concatenate([tris[t], np.zeros((3, 1), dtype=np.int64)], axis=1)   # z = 0
+        top = base + np.array([0, 0, 1])
+        cell = 2 * np.arange(o.shape[0]) + t
+        tri_polys += [o[:, None, :] + base[None], o[:, None, :] + top[None]]
+        tri_cells += [cell, cell]
+        for a in range(3):
+            b = (a + 1) % 3
+            q = np.stack([base[a], base[b], top[b], top[a]])
+            quad_polys.append(o[:, None, :] + q[None])
+            quad_cells.append(cell)
+    groups = [(np.concatenate(tri_cells), np.concatenate(tri_polys)),
+              (np.concatenate(quad_cells), np.concatenate(quad_polys))]
+    return polyhedral_mesh(n, h, groups, np.full(nc, h ** 3 / 2.0))
+
+
 def permuted_mesh(mesh: Mesh, seed: int, flip_fraction: float = 0.5):
     """Relabel cells and faces with seeded random permutations and flip the
     orientation of a seeded subset of faces (c0<->c1, normal negated).
