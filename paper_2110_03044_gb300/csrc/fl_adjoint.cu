@@ -54,6 +54,7 @@ struct AParams {
   long long plane;
   T cx, cy, cz;  // A/V per axis
   T e1, e2, b, bdt;
+  const unsigned char *codes;  // branch codes of the forward stage (layout of u), or null
   int bare;      // 1: out = R'^T mu only
   int tiles_x, tiles_y, zchunk;
 };
@@ -164,35 +165,6 @@ struct FaceSmem<T, LIM_VANLEER, N> {
     return f;
   }
 };
-
-// branch code of limited_face for (a, b): the same bit-pattern tests
-template <class T, int LIM>
-__device__ __forceinline__ int lin_code(T a, T b) {
-  using F = FT<T>;
-  using U = typename F::U;
-  using I = typename F::I;
-  if (LIM == LIM_UPWIND) return 0;
-  const U A = F::bits(a);
-  const U sa = A & F::SIGN;
-  const U q = A ^ sa;
-  const U p = F::bits(b) ^ sa;
-  if (LIM == LIM_CENTRAL) return 1;
-  if (!(((I)p > 0) && (q != 0))) return 0;
-  if (LIM == LIM_MINMOD) return (p <= q) ? 1 : 2;
-  if (LIM == LIM_SUPERBEE) {
-    if (p + F::EXP1 <= q) return 1;
-    if (p <= q) return 2;
-    if (p <= q + F::EXP1) return 3;
-    return 4;
-  }
-  // LIM_SMART
-  const T m = F::fma(T(0.375), F::val(p), F::mul(T(0.125), F::val(q)));
-  const U M = F::bits(m);
-  const U t = (p <= M) ? p : M;
-  if ((q + F::EXP1) < t) return 1;
-  if (p <= M) return 2;
-  return 3;
-}
 
 // c is the axis coefficient A/V; with PRE the velocities arrive already
 // multiplied by it (one product per face saved in every adjoint stage)
@@ -464,6 +436,212 @@ __global__ void __launch_bounds__(TX *TY, FL_ADJ_MINB) k_struct_adjoint(const AP
   }
 }
 
+
+// The stage adjoint from stored branch codes: the forward stage that read x
+// (run with codes on, in the reverse sweep's recomputation) left the branch
+// code of every face, so this kernel needs neither x nor its differences --
+// per face only g = w (mu_{m+1} - mu_m) and the code.  Same tiles, halos,
+// gather and combination as k_struct_adjoint; two barriers per plane.
+// Piecewise-linear limiters only (u holds w, the pre-scaled velocity).
+template <class T, int LIM>
+__global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParams<T> p) {
+  using F = FT<T>;
+  constexpr int NT = TX * TY;
+  constexpr int SWM = TX + 4;  // mu row pitch (halo 2)
+  constexpr int NXF = TX + 3;  // x faces per row: m = x0-2 .. x0+TX
+  constexpr int NYF = TY + 3;  // y faces per column: m = y0-2 .. y0+TY
+  __shared__ T s_mu[(TY + 4) * SWM];
+  __shared__ FaceSmem<T, LIM, TY * NXF> s_fx;
+  __shared__ FaceSmem<T, LIM, NYF * TX> s_fy;
+  __shared__ T s_uxb[2][TY * NXF];
+  __shared__ T s_uyb[2][NYF * TX];
+  __shared__ unsigned char s_cx[TY * NXF];
+  __shared__ unsigned char s_cy[NYF * TX];
+  __shared__ int s_wx[TX + 6];
+  __shared__ int s_wy[TY + 6];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  int bid = blockIdx.x;
+  const int bx = bid % p.tiles_x;
+  bid /= p.tiles_x;
+  const int by = bid % p.tiles_y;
+  const int bz = bid / p.tiles_y;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int z0 = bz * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  if (tid < TX + 6) s_wx[tid] = wrapi(x0 - 3 + tid, nx);
+  if (tid < TY + 6) s_wy[tid] = wrapi(y0 - 3 + tid, ny);
+  __syncthreads();
+  const bool valid = (x0 + tx < nx) && (y0 + ty < ny);
+  const long long col = (long long)s_wx[tx + 3] + (long long)nx * s_wy[ty + 3];
+  const bool need_x = p.act_x, need_y = p.act_y, need_z = p.act_z;
+
+  // mu halo (2 wide)
+  int mu_slot = -1;
+  long long mu_off = 0;
+  {
+    constexpr int NMX = 4 * TY, NMT = NMX + 4 * TX;
+    static_assert(NMT <= NT, "mu halo exceeds threads");
+    if (tid < NMX) {
+      const int r = tid >> 2, k4 = tid & 3;
+      const int c = (k4 < 2) ? k4 : (TX + k4);
+      mu_slot = (r + 2) * SWM + c;
+      mu_off = (long long)s_wx[c + 1] + (long long)nx * s_wy[r + 3];
+    } else if (tid < NMT) {
+      const int t = tid - NMX;
+      const int k4 = t / TX, c = t % TX;
+      const int r = (k4 < 2) ? k4 : (TY + k4);
+      mu_slot = r * SWM + c + 2;
+      mu_off = (long long)s_wx[c + 3] + (long long)nx * s_wy[r + 1];
+    }
+  }
+  // faces of the plane: every thread its own +x and +y face, threads
+  // tid < 3 (TX + TY) one halo face each (u by cp.async, codes by registers)
+  int hu_slot = -1;
+  long long hu_off = 0;
+  bool hu_x = false;
+  {
+    constexpr int NUX = 3 * TY, NUT = NUX + 3 * TX;
+    static_assert(NUT <= NT, "u halo exceeds threads");
+    if (tid < NUX) {
+      if (need_x) {
+        const int r = tid / 3, k3 = tid % 3;
+        const int q = (k3 < 2) ? k3 : TX + 2;
+        hu_slot = r * NXF + q;
+        hu_off = p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 3];
+        hu_x = true;
+      }
+    } else if (tid < NUT) {
+      if (need_y) {
+        const int t = tid - NUX;
+        const int k3 = t / TX, c = t % TX;
+        const int r = (k3 < 2) ? k3 : TY + 2;
+        hu_slot = r * TX + c;
+        hu_off = p.uy_off + s_wx[c + 3] + (long long)nx * s_wy[r + 1];
+      }
+    }
+  }
+  unsigned cx_n = 0, cy_n = 0, ch_n = 0;
+  auto load_face = [&](long long pk, int buf) {
+    if (need_x) {
+      cp_async1(&s_uxb[buf][ty * NXF + tx + 2], p.u + p.ux_off + col + pk);
+      cx_n = p.codes[p.ux_off + col + pk];
+    }
+    if (need_y) {
+      cp_async1(&s_uyb[buf][(ty + 2) * TX + tx], p.u + p.uy_off + col + pk);
+      cy_n = p.codes[p.uy_off + col + pk];
+    }
+    if (hu_slot >= 0) {
+      cp_async1(hu_x ? &s_uxb[buf][hu_slot] : &s_uyb[buf][hu_slot], p.u + hu_off + pk);
+      ch_n = p.codes[hu_off + pk];
+    }
+    cp_async_commit();
+  };
+  load_face(p.plane * z0, z0 & 1);
+
+  // ---- z prologue: faces z0-2, z0-1, z0 from the mu column and the codes
+  T mu_k, mu_k1 = T(0);
+  FaceAdj<T, LIM> zf_m2{}, zf_m1{}, zf_0{};
+  auto MU = [&](int k) { return p.mu[col + p.plane * wrapi(k, nz)]; };
+  auto ZF = [&](int k, T m0, T m1) {
+    const long long i = p.uz_off + col + p.plane * wrapi(k, nz);
+    FaceAdj<T, LIM> f;
+    f.g = F::mul(p.u[i], F::sub(m1, m0));
+    f.code = p.codes[i];
+    return f;
+  };
+  if (need_z) {
+    const T mm2 = MU(z0 - 2), mm1 = MU(z0 - 1);
+    mu_k = MU(z0);
+    mu_k1 = MU(z0 + 1);
+    zf_m2 = ZF(z0 - 2, mm2, mm1);
+    zf_m1 = ZF(z0 - 1, mm1, mu_k);
+    zf_0 = ZF(z0, mu_k, mu_k1);
+  } else {
+    mu_k = p.mu[col];
+  }
+
+  for (int k = z0; k < z1; ++k) {
+    const long long pk = p.plane * k;
+    T mu_k2 = T(0);
+    if (need_z) mu_k2 = MU(k + 2);
+    const T hv_m = (mu_slot >= 0) ? p.mu[mu_off + pk] : T(0);
+    T v1 = T(0), v2 = T(0);
+    if (!p.bare && valid) {
+      if (p.v1) v1 = p.v1[col + pk];
+      if (p.v2) v2 = p.v2[col + pk];
+    }
+    s_mu[(ty + 2) * SWM + tx + 2] = mu_k;
+    if (mu_slot >= 0) s_mu[mu_slot] = hv_m;
+    if (need_x) s_cx[ty * NXF + tx + 2] = (unsigned char)cx_n;
+    if (need_y) s_cy[(ty + 2) * TX + tx] = (unsigned char)cy_n;
+    if (hu_slot >= 0) {
+      if (hu_x) s_cx[hu_slot] = (unsigned char)ch_n;
+      else s_cy[hu_slot] = (unsigned char)ch_n;
+    }
+    cp_async_wait_all();
+    if (k + 1 < z1) load_face(pk + p.plane, (k + 1) & 1);
+    const T *s_ux = s_uxb[k & 1];
+    const T *s_uy = s_uyb[k & 1];
+    FaceAdj<T, LIM> zf_1{};
+    if (need_z) zf_1 = ZF(k + 1, mu_k1, mu_k2);
+    __syncthreads();
+    // ---------------------------------------------- face data
+    if (need_x) {
+      for (int it = tid; it < TY * NXF; it += NT) {
+        const int r = it / NXF, q = it - r * NXF;  // face m = x0-2+q
+        const T *mr = &s_mu[(r + 2) * SWM];
+        FaceAdj<T, LIM> f;
+        f.g = F::mul(s_ux[it], F::sub(mr[q + 1], mr[q]));
+        f.code = s_cx[it];
+        s_fx.put(it, f);
+      }
+    }
+    if (need_y) {
+      for (int it = tid; it < NYF * TX; it += NT) {
+        const int r = it / TX, c = it - r * TX;  // face m = y0-2+r
+        FaceAdj<T, LIM> f;
+        f.g = F::mul(s_uy[it], F::sub(s_mu[(r + 1) * SWM + c + 2], s_mu[r * SWM + c + 2]));
+        f.code = s_cy[it];
+        s_fy.put(it, f);
+      }
+    }
+    __syncthreads();
+    // ---------------------------------------------- gather + combine
+    if (valid) {
+      T acc = T(0);
+      if (need_x) {
+        const int i = ty * NXF + tx;
+        acc = gather4(acc, s_fx.get(i), s_fx.get(i + 1), s_fx.get(i + 2), s_fx.get(i + 3));
+      }
+      if (need_y) {
+        acc = gather4(acc, s_fy.get(ty * TX + tx), s_fy.get((ty + 1) * TX + tx),
+                      s_fy.get((ty + 2) * TX + tx), s_fy.get((ty + 3) * TX + tx));
+      }
+      if (need_z) acc = gather4(acc, zf_m2, zf_m1, zf_0, zf_1);
+      T o;
+      if (p.bare) {
+        o = acc;
+      } else {
+        o = F::fma(p.bdt, acc, F::mul(p.b, mu_k));
+        if (p.v1) o = F::fma(p.e1, v1, o);
+        if (p.v2) o = F::fma(p.e2, v2, o);
+      }
+      p.out[col + pk] = o;
+    }
+    if (need_z) {
+      zf_m2 = zf_m1;
+      zf_m1 = zf_0;
+      zf_0 = zf_1;
+      mu_k = mu_k1;
+      mu_k1 = mu_k2;
+    } else if (k + 1 < z1) {
+      mu_k = p.mu[col + p.plane * (k + 1)];
+    }
+  }
+}
+
 template <class T>
 cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t st) {
   AParams<T> p;
@@ -491,9 +669,27 @@ cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t 
   p.b = (T)s.b;
   p.bdt = (T)(s.cu_dt ? s.b : s.b * s.dt);
   p.bare = s.bare;
+  p.codes = static_cast<const unsigned char *>(s.codes);
   p.tiles_x = (m->nx + TX - 1) / TX;
   p.tiles_y = (m->ny + TY - 1) / TY;
   const long long cols = (long long)p.tiles_x * p.tiles_y;
+  if (s.codes != nullptr && s.cu != nullptr && lim != LIM_VANLEER) {
+    // the stage's branch codes are stored: no theta, no differences
+    const int res = resident_ctas(
+        reinterpret_cast<const void *>(&k_struct_adjoint_codes<T, LIM_SUPERBEE>), TX * TY, 0);
+    p.zchunk = pick_zchunk(cols, m->nz, res, 2);
+    const unsigned g = (unsigned)(cols * ((m->nz + p.zchunk - 1) / p.zchunk));
+    const dim3 blk(TX, TY);
+    switch (lim) {
+      case LIM_UPWIND: k_struct_adjoint_codes<T, LIM_UPWIND><<<g, blk, 0, st>>>(p); break;
+      case LIM_CENTRAL: k_struct_adjoint_codes<T, LIM_CENTRAL><<<g, blk, 0, st>>>(p); break;
+      case LIM_MINMOD: k_struct_adjoint_codes<T, LIM_MINMOD><<<g, blk, 0, st>>>(p); break;
+      case LIM_SUPERBEE: k_struct_adjoint_codes<T, LIM_SUPERBEE><<<g, blk, 0, st>>>(p); break;
+      case LIM_SMART: k_struct_adjoint_codes<T, LIM_SMART><<<g, blk, 0, st>>>(p); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   const int resident = resident_ctas(
       reinterpret_cast<const void *>(&k_struct_adjoint<T, LIM_SUPERBEE, true>), TX * TY, 0);
   const int zchunk = pick_zchunk(cols, m->nz, resident, 3);
@@ -532,8 +728,10 @@ size_t adjoint_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps, i
   const int S = (rk == 3) ? 3 : 1;
   const int64_t nck = (nsteps + every - 1) / every;
   const int64_t seg = (int64_t)S * every + 1;
-  // checkpoints | segment stage states | 3 adjoint vectors | pre-scaled u_f
-  return one * (size_t)(nck + seg + 3) + align256((size_t)m->F * dsize(dt));
+  // checkpoints | segment stage states | 3 adjoint vectors | pre-scaled u_f |
+  // branch codes of the segment's stages (one byte per face and stage)
+  return one * (size_t)(nck + seg + 3) + align256((size_t)m->F * dsize(dt)) +
+         align256((size_t)m->F * (size_t)(S * every));
 }
 
 }  // namespace fl
@@ -608,23 +806,37 @@ struct Sweep {
   // (A/V) u_f for the adjoint stages only
   void *cu() const { return base + one * (nck + S * every + 1 + 3); }
   bool cu_dt() const { return dtime > 0; }
+  // branch codes of stage i = S n + s of the segment (FP64 pre-scaled
+  // stages of the piecewise-linear limiters: the adjoint reads them instead
+  // of recomputing the forward stage's differences)
+  bool use_codes() const { return dt == FL_F64 && cu_dt() && lim != LIM_VANLEER; }
+  unsigned char *codes(int64_t i) const {
+    return reinterpret_cast<unsigned char *>(base + one * (nck + S * every + 1 + 3) +
+                                             align256((size_t)m->F * dsize(dt))) +
+           (size_t)m->F * i;
+  }
   cudaError_t prescale() const {
     return struct_scale_faces(m, dt, u, cu(), cu_dt() ? dtime : 1.0, st);
   }
-  cudaError_t stage(const void *x, const void *thn, void *y, int seed, double a, double b) const {
+  cudaError_t stage(const void *x, const void *thn, void *y, int seed, double a, double b,
+                    void *code_out = nullptr) const {
     StageArgs s;
     s.x = x; s.thn = thn; s.y = y; s.u = u; s.dt = dtime; s.seed = seed; s.a = a; s.b = b;
     if (cu_dt()) s.w = cu();
+    s.codes = code_out;
     return struct_stage(m, lim, dt, s, st);
   }
-  // one forward step from slot(S n) storing its stage inputs; the step's
-  // result lands in slot(S (n + 1))
-  cudaError_t fwd_step(int64_t n) const {
-    if (S == 1) return stage(slot(n), slot(n), slot(n + 1), 0, 0.0, 1.0);
-    cudaError_t r = stage(slot(3 * n), slot(3 * n), slot(3 * n + 1), 0, 0.0, 1.0);
-    if (r == cudaSuccess) r = stage(slot(3 * n + 1), slot(3 * n), slot(3 * n + 2), 1, 0.75, 0.25);
+  // one forward step from slot(S n) storing its stage inputs (and, when
+  // `codes_on`, their branch codes); the result lands in slot(S (n + 1))
+  cudaError_t fwd_step(int64_t n, bool codes_on = false) const {
+    auto cd = [&](int64_t i) -> void * { return codes_on ? codes(i) : nullptr; };
+    if (S == 1) return stage(slot(n), slot(n), slot(n + 1), 0, 0.0, 1.0, cd(n));
+    cudaError_t r = stage(slot(3 * n), slot(3 * n), slot(3 * n + 1), 0, 0.0, 1.0, cd(3 * n));
     if (r == cudaSuccess)
-      r = stage(slot(3 * n + 2), slot(3 * n), slot(3 * n + 3), 1, 1.0 / 3.0, 2.0 / 3.0);
+      r = stage(slot(3 * n + 1), slot(3 * n), slot(3 * n + 2), 1, 0.75, 0.25, cd(3 * n + 1));
+    if (r == cudaSuccess)
+      r = stage(slot(3 * n + 2), slot(3 * n), slot(3 * n + 3), 1, 1.0 / 3.0, 2.0 / 3.0,
+                cd(3 * n + 2));
     return r;
   }
 };
@@ -687,7 +899,9 @@ cudaError_t sweep_reverse(const Sweep &w, const void *lambda_T, void *lambda_0) 
   for (int64_t c = w.nck - 1; c >= 0 && e == cudaSuccess; --c) {
     const int64_t len = std::min<int64_t>(w.every, w.nsteps - c * w.every);
     e = cudaMemcpyAsync(w.slot(0), w.ck(c), w.bytes, cudaMemcpyDeviceToDevice, w.st);
-    for (int64_t n = 0; n < len && e == cudaSuccess; ++n) e = w.fwd_step(n);
+    const bool codes = w.use_codes();
+    for (int64_t n = 0; n < len && e == cudaSuccess; ++n) e = w.fwd_step(n, codes);
+    auto cd = [&](int64_t i) -> const void * { return codes ? w.codes(i) : nullptr; };
     for (int64_t n = len - 1; n >= 0 && e == cudaSuccess; --n) {
       AdjArgs a;
       a.u = w.u;
@@ -696,22 +910,22 @@ cudaError_t sweep_reverse(const Sweep &w, const void *lambda_T, void *lambda_0) 
       a.dt = w.dtime;
       if (w.S == 1) {
         // lam' = lam + dt R'(x)^T lam
-        a.x = w.slot(n); a.mu = lam; a.out = la; a.b = 1.0;
+        a.x = w.slot(n); a.mu = lam; a.out = la; a.b = 1.0; a.codes = cd(n);
         e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
         void *t = lam;
         lam = la;
         la = t;
       } else {
         // stage 3: la = 2/3 (lam + dt R'(x2)^T lam)
-        a.x = w.slot(3 * n + 2); a.mu = lam; a.out = la; a.b = 2.0 / 3.0;
+        a.x = w.slot(3 * n + 2); a.mu = lam; a.out = la; a.b = 2.0 / 3.0; a.codes = cd(3 * n + 2);
         e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
         if (e != cudaSuccess) break;
         // stage 2: lbb = 1/4 (la + dt R'(x1)^T la)
-        a.x = w.slot(3 * n + 1); a.mu = la; a.out = lbb; a.b = 0.25;
+        a.x = w.slot(3 * n + 1); a.mu = la; a.out = lbb; a.b = 0.25; a.codes = cd(3 * n + 1);
         e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
         if (e != cudaSuccess) break;
         // stage 1: lam = 1/3 lam + 3/4 la + (lbb + dt R'(x0)^T lbb)
-        a.x = w.slot(3 * n); a.mu = lbb; a.out = lam; a.b = 1.0;
+        a.x = w.slot(3 * n); a.mu = lbb; a.out = lam; a.b = 1.0; a.codes = cd(3 * n);
         a.v1 = lam; a.e1 = 1.0 / 3.0; a.v2 = la; a.e2 = 0.75;
         e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
       }

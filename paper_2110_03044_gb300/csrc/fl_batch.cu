@@ -163,6 +163,7 @@ SParams<T> box_params(const fl_mesh *m, int zc, const void *x, const void *thn, 
   p.b = (T)bcoef;
   p.g = (T)1;
   p.flip = 0;
+  p.codes = nullptr;
   p.tiles_x = tiles_x_of(m);
   p.tiles_y = tiles_y_of(m);
   p.zchunk = zchunk_of(m, zc);

@@ -18,6 +18,7 @@ struct StageArgs {
   const void *w = nullptr;  // dt (A/V) u_f, or null (see struct_scale_faces)
   double a = 0.0, b = 1.0, dt = 0.0;
   double g = 1.0;  // velocity factor of the stage: the flow is g u_f
+  void *codes = nullptr;  // FP64 pre-scaled stages: branch code per face out (or null)
   int seed = 0;
 };
 
@@ -55,6 +56,7 @@ struct AdjArgs {
   const void *u = nullptr;
   const void *cu = nullptr;  // u_f pre-multiplied by A/V of its axis, or null
   int cu_dt = 0;             // cu also carries the factor dt (then b replaces b dt)
+  const void *codes = nullptr;  // branch codes of the forward stage at x, or null
   double e1 = 0.0, e2 = 0.0, b = 1.0, dt = 0.0;
   int bare = 0;
 };

@@ -27,6 +27,7 @@ struct SParams {
   T a, b;           // seed = a*thn + b*x  (COMBINE) or x (PLAIN) or 0 (APPLY)
   T g;              // MOD: velocity factor of the stage (see stage_tile)
   unsigned long long flip;  // sign mask toggled into u before the upwind test (g < 0)
+  unsigned char *codes;     // CODES: branch code per face (layout of u), or null
   int tiles_x, tiles_y, zchunk;
 };
 
@@ -49,7 +50,12 @@ __device__ __forceinline__ int wrap(int v, int n) {
 // every u before its upwind test when g < 0 (p.flip).  Without PRE, g is part
 // of p.cx/cy/cz; with PRE and MOD the six w theta_f terms are summed first
 // and added as x + g S.
-template <class T, int LIM, int SEED, int TY, bool PRE = false, bool MOD = false>
+//
+// CODES: the tile also writes, for every face it owns, the branch code of
+// its limited value (lin_code, bit 3 = s > 0), which the adjoint of the same
+// stage reads instead of recomputing theta's differences.
+template <class T, int LIM, int SEED, int TY, bool PRE = false, bool MOD = false,
+          bool CODES = false>
 __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
   using F = FT<T>;
   constexpr int NT = TX * TY;
@@ -207,6 +213,9 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
         const T thf = limited_face<T, LIM>(sp ? tr[q + 1] : tr[q + 2], dr[q + 1],
                                            sp ? dr[q] : dr[q + 2], sp);
         s_fx[it] = PRE ? thf : face_flux(uf, thf);
+        if (CODES && q >= 1 && x0 + q - 1 < nx && y0 + r < ny)
+          p.codes[p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 2] + pk] =
+              (unsigned char)(lin_code<T, LIM>(dr[q + 1], sp ? dr[q] : dr[q + 2]) | (sp ? 8 : 0));
         if (SEED == SEED_APPLY && p.thf != nullptr) {
           if (q >= 1 && x0 + q - 1 < nx && y0 + r < ny)
             p.thf[p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 2] + pk] = thf;
@@ -222,6 +231,10 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
             sp ? s_th[(r + 1) * SW + c + 2] : s_th[(r + 2) * SW + c + 2], s_dy[(r + 1) * TX + c],
             sp ? s_dy[r * TX + c] : s_dy[(r + 2) * TX + c], sp);
         s_fy[it] = PRE ? thf : face_flux(uf, thf);
+        if (CODES && r >= 1 && x0 + c < nx && y0 + r - 1 < ny)
+          p.codes[p.uy_off + s_wx[c + 2] + (long long)nx * s_wy[r + 1] + pk] = (unsigned char)(
+              lin_code<T, LIM>(s_dy[(r + 1) * TX + c], sp ? s_dy[r * TX + c] : s_dy[(r + 2) * TX + c]) |
+              (sp ? 8 : 0));
         if (SEED == SEED_APPLY && p.thf != nullptr) {
           if (r >= 1 && x0 + c < nx && y0 + r - 1 < ny)
             p.thf[p.uy_off + s_wx[c + 2] + (long long)nx * s_wy[r + 1] + pk] = thf;
@@ -233,6 +246,9 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
       const bool sp = upwind_positive(sign_toggled(cur.uz, p.flip));
       const T thf = limited_face<T, LIM>(sp ? th0 : thp1, dz_0, sp ? dz_m1 : dz_p1, sp);
       fz = PRE ? thf : face_flux(cur.uz, thf);
+      if (CODES && valid)
+        p.codes[p.uz_off + col + pk] =
+            (unsigned char)(lin_code<T, LIM>(dz_0, sp ? dz_m1 : dz_p1) | (sp ? 8 : 0));
       if (SEED == SEED_APPLY && p.thf != nullptr && valid) p.thf[p.uz_off + col + pk] = thf;
     }
     __syncthreads();

@@ -35,30 +35,35 @@ namespace {
 #endif
 constexpr int STY = FL_STRUCT_TY;
 
-template <class T, int LIM, int SEED, int TY, bool PRE, bool MOD>
-__global__ void __launch_bounds__(TX *TY, 32 / TY) k_struct_stage(const SParams<T> p) {
-  stage_tile<T, LIM, SEED, TY, PRE, MOD>(p, blockIdx.x);
+// (the code-writing variant, run only in the adjoint's recomputation, gets
+// more registers per thread instead of spilling)
+template <class T, int LIM, int SEED, int TY, bool PRE, bool MOD, bool CODES>
+__global__ void __launch_bounds__(TX *TY, CODES ? 3 : 32 / TY) k_struct_stage(const SParams<T> p) {
+  stage_tile<T, LIM, SEED, TY, PRE, MOD, CODES>(p, blockIdx.x);
 }
 
-template <class T, int LIM, int SEED, bool PRE, bool MOD>
+template <class T, int LIM, int SEED, bool PRE, bool MOD, bool CODES>
 cudaError_t launch_stage(const SParams<T> &p0, int tiles_z, cudaStream_t st) {
   constexpr int TY = STY;
   SParams<T> p = p0;
   const dim3 block(TX, TY);
   const long long grid = (long long)p.tiles_x * p.tiles_y * tiles_z;
-  k_struct_stage<T, LIM, SEED, TY, PRE, MOD><<<(unsigned)grid, block, 0, st>>>(p);
+  k_struct_stage<T, LIM, SEED, TY, PRE, MOD, CODES><<<(unsigned)grid, block, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-template <class T, int SEED, bool PRE, bool MOD = false>
+template <class T, int SEED, bool PRE, bool MOD = false, bool CODES = false>
 cudaError_t dispatch_lim(int lim, const SParams<T> &p, int tz, cudaStream_t st) {
   switch (lim) {
-    case LIM_UPWIND: return launch_stage<T, LIM_UPWIND, SEED, PRE, MOD>(p, tz, st);
-    case LIM_CENTRAL: return launch_stage<T, LIM_CENTRAL, SEED, PRE, MOD>(p, tz, st);
-    case LIM_MINMOD: return launch_stage<T, LIM_MINMOD, SEED, PRE, MOD>(p, tz, st);
-    case LIM_VANLEER: return launch_stage<T, LIM_VANLEER, SEED, PRE, MOD>(p, tz, st);
-    case LIM_SUPERBEE: return launch_stage<T, LIM_SUPERBEE, SEED, PRE, MOD>(p, tz, st);
-    case LIM_SMART: return launch_stage<T, LIM_SMART, SEED, PRE, MOD>(p, tz, st);
+    case LIM_UPWIND: return launch_stage<T, LIM_UPWIND, SEED, PRE, MOD, CODES>(p, tz, st);
+    case LIM_CENTRAL: return launch_stage<T, LIM_CENTRAL, SEED, PRE, MOD, CODES>(p, tz, st);
+    case LIM_MINMOD: return launch_stage<T, LIM_MINMOD, SEED, PRE, MOD, CODES>(p, tz, st);
+    case LIM_VANLEER:
+      // van Leer's adjoint is linearised from values, not branch codes
+      if constexpr (CODES) return cudaErrorInvalidValue;
+      else return launch_stage<T, LIM_VANLEER, SEED, PRE, MOD, false>(p, tz, st);
+    case LIM_SUPERBEE: return launch_stage<T, LIM_SUPERBEE, SEED, PRE, MOD, CODES>(p, tz, st);
+    case LIM_SMART: return launch_stage<T, LIM_SMART, SEED, PRE, MOD, CODES>(p, tz, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -108,6 +113,7 @@ cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStrea
   const double sc = (s.seed == SEED_APPLY) ? 1.0 : s.b * s.dt * (pre ? 1.0 : g);
   p.g = (T)g;
   p.flip = (g < 0) ? (sizeof(T) == 8 ? 0x8000000000000000ull : 0x80000000ull) : 0ull;
+  p.codes = static_cast<unsigned char *>(s.codes);
   p.cx = (T)(sc / m->hx);
   p.cy = (T)(sc / m->hy);
   p.cz = (T)(sc / m->hz);
@@ -120,12 +126,16 @@ cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStrea
   const long long cols = (long long)p.tiles_x * p.tiles_y;
   const int resident =
       resident_ctas(reinterpret_cast<const void *>(&k_struct_stage<T, LIM_SUPERBEE, SEED_PLAIN, STY,
-                                                                   false, false>),
+                                                                   false, false, false>),
                     TX * STY, 0);
   const int zchunk = pick_zchunk(cols, m->nz, resident, 2);
   p.zchunk = zchunk;
   const int tz = (m->nz + zchunk - 1) / zchunk;
   if constexpr (sizeof(T) == 8) {
+    if (pre && !mod && s.codes != nullptr) {
+      if (s.seed == SEED_PLAIN) return dispatch_lim<T, SEED_PLAIN, true, false, true>(lim, p, tz, st);
+      return dispatch_lim<T, SEED_COMBINE, true, false, true>(lim, p, tz, st);
+    }
     if (pre && mod) {
       if (s.seed == SEED_PLAIN) return dispatch_lim<T, SEED_PLAIN, true, true>(lim, p, tz, st);
       return dispatch_lim<T, SEED_COMBINE, true, true>(lim, p, tz, st);
