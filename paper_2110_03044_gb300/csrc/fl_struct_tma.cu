@@ -47,7 +47,10 @@ constexpr int TX = 128, VX = 4, LANES = TX / VX, TY = 8;
 #ifndef FL_TMA_MINB
 #define FL_TMA_MINB 2
 #endif
-constexpr int RING = FL_TMA_RING, MINB = FL_TMA_MINB;
+#ifndef FL_TMA_UNROLL
+#define FL_TMA_UNROLL 1
+#endif
+constexpr int RING = FL_TMA_RING, MINB = FL_TMA_MINB, UNROLL = FL_TMA_UNROLL;
 // slot layout (bytes); every TMA destination is 128-byte aligned
 constexpr int OFF_TH = 0;       // [8][128] theta
 constexpr int OFF_XL = 4096;    // [8][4]   theta x0-4 .. x0-1
@@ -286,6 +289,8 @@ __global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
   }
   const int umoff = (ty > 0) ? OFF_UY + rowb - TX * 4 : OFF_UYH + lane * VX * 4;
   int knext = wrap_up(z0 + 4, nz);  // plane of the next z-window load
+  // unrolled so that the z-window shifts become register renaming
+#pragma unroll UNROLL
   for (int q = 0; q < L; ++q) {
     const int k = z0 + q;
     const int slot = q % RING;

@@ -35,10 +35,15 @@ namespace {
 #endif
 constexpr int STY = FL_STRUCT_TY;
 
-// (the code-writing variant, run only in the adjoint's recomputation, gets
-// more registers per thread instead of spilling)
+// CTAs per SM of the code-writing variant (run only in the adjoint's
+// recomputation): 4 with a few spilled registers measured faster than 3
+// without spills (128^3 superbee reverse sweep 121 ms against 133 ms)
+#ifndef FL_CODES_MINB
+#define FL_CODES_MINB 4
+#endif
 template <class T, int LIM, int SEED, int TY, bool PRE, bool MOD, bool CODES>
-__global__ void __launch_bounds__(TX *TY, CODES ? 3 : 32 / TY) k_struct_stage(const SParams<T> p) {
+__global__ void __launch_bounds__(TX *TY, CODES ? FL_CODES_MINB : 32 / TY)
+    k_struct_stage(const SParams<T> p) {
   stage_tile<T, LIM, SEED, TY, PRE, MOD, CODES>(p, blockIdx.x);
 }
 
