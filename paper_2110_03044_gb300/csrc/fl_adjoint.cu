@@ -25,6 +25,7 @@
 #include "fl_face.cuh"
 #include "fl_internal.h"
 #include "fl_kernels.h"
+#include "fl_unstructured.h"
 
 namespace fl {
 
@@ -722,6 +723,11 @@ cudaError_t struct_adjoint(const fl_mesh *m, int lim, fl_dtype dt, const AdjArgs
   return dt == FL_F64 ? run_adj_t<double>(m, lim, s, st) : run_adj_t<float>(m, lim, s, st);
 }
 
+// one stage adjoint on either kind of mesh
+cudaError_t adjoint_any(const fl_mesh *m, int lim, fl_dtype dt, const AdjArgs &s, cudaStream_t st) {
+  return m->kind == 1 ? unstruct_adjoint(m, lim, dt, s, st) : struct_adjoint(m, lim, dt, s, st);
+}
+
 // ------------------------------------------------------------- host side
 size_t adjoint_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps, int64_t every) {
   const size_t one = align256((size_t)m->C * dsize(dt));
@@ -758,15 +764,15 @@ fl_status fl_conv_limited_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt,
   FL_TRY(check_buffer(lambda_theta, m->C * es, "lambda_theta"));
   if (lambda_theta == lambda_rhs || lambda_theta == theta_c)
     return fail(FL_EINVAL, "lambda_theta must not alias the inputs");
-  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "adjoint of face-based meshes is not available");
   if (m->C == 0) return FL_OK;
+  if (m->kind == 1) FL_TRY(unstruct_adjoint_prepare(m));
   AdjArgs a;
   a.x = theta_c;
   a.mu = lambda_rhs;
   a.out = lambda_theta;
   a.u = u_f;
   a.bare = 1;
-  cudaError_t e = struct_adjoint(m, lim, dt, a, as_stream(stream));
+  cudaError_t e = adjoint_any(m, lim, dt, a, as_stream(stream));
   if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel");
   return FL_OK;
 }
@@ -809,14 +815,18 @@ struct Sweep {
   // branch codes of stage i = S n + s of the segment (FP64 pre-scaled
   // stages of the piecewise-linear limiters: the adjoint reads them instead
   // of recomputing the forward stage's differences)
-  bool use_codes() const { return dt == FL_F64 && cu_dt() && lim != LIM_VANLEER; }
+  bool use_codes() const {
+    return m->kind == 0 && dt == FL_F64 && cu_dt() && lim != LIM_VANLEER;
+  }
   unsigned char *codes(int64_t i) const {
     return reinterpret_cast<unsigned char *>(base + one * (nck + S * every + 1 + 3) +
                                              align256((size_t)m->F * dsize(dt))) +
            (size_t)m->F * i;
   }
   cudaError_t prescale() const {
-    return struct_scale_faces(m, dt, u, cu(), cu_dt() ? dtime : 1.0, st);
+    // structured: (fac / h_axis) u_f; face-based: fac A_f u_f
+    return m->kind == 1 ? unstruct_scale_area(m, dt, u, cu(), cu_dt() ? dtime : 1.0, st)
+                        : struct_scale_faces(m, dt, u, cu(), cu_dt() ? dtime : 1.0, st);
   }
   cudaError_t stage(const void *x, const void *thn, void *y, int seed, double a, double b,
                     void *code_out = nullptr) const {
@@ -824,7 +834,7 @@ struct Sweep {
     s.x = x; s.thn = thn; s.y = y; s.u = u; s.dt = dtime; s.seed = seed; s.a = a; s.b = b;
     if (cu_dt()) s.w = cu();
     s.codes = code_out;
-    return struct_stage(m, lim, dt, s, st);
+    return m->kind == 1 ? unstruct_stage(m, lim, dt, s, st) : struct_stage(m, lim, dt, s, st);
   }
   // one forward step from slot(S n) storing its stage inputs (and, when
   // `codes_on`, their branch codes); the result lands in slot(S (n + 1))
@@ -849,7 +859,7 @@ fl_status sweep_setup(Sweep &w, const fl_mesh *m, int lim, fl_dtype dt, int rk, 
   if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
   if (nsteps < 0 || every < 1) return fail(FL_EINVAL, "nsteps >= 0 and checkpoint_every >= 1");
   if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
-  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "adjoint of face-based meshes is not available");
+  if (m->kind == 1) FL_TRY(unstruct_adjoint_prepare(m));
   const size_t es = dsize(dt);
   FL_TRY(check_buffer(u_f, m->F * es, "u_f"));
   const size_t need = adjoint_ws_bytes(m, dt, rk, nsteps, every);
@@ -911,23 +921,23 @@ cudaError_t sweep_reverse(const Sweep &w, const void *lambda_T, void *lambda_0) 
       if (w.S == 1) {
         // lam' = lam + dt R'(x)^T lam
         a.x = w.slot(n); a.mu = lam; a.out = la; a.b = 1.0; a.codes = cd(n);
-        e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
+        e = adjoint_any(w.m, w.lim, w.dt, a, w.st);
         void *t = lam;
         lam = la;
         la = t;
       } else {
         // stage 3: la = 2/3 (lam + dt R'(x2)^T lam)
         a.x = w.slot(3 * n + 2); a.mu = lam; a.out = la; a.b = 2.0 / 3.0; a.codes = cd(3 * n + 2);
-        e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
+        e = adjoint_any(w.m, w.lim, w.dt, a, w.st);
         if (e != cudaSuccess) break;
         // stage 2: lbb = 1/4 (la + dt R'(x1)^T la)
         a.x = w.slot(3 * n + 1); a.mu = la; a.out = lbb; a.b = 0.25; a.codes = cd(3 * n + 1);
-        e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
+        e = adjoint_any(w.m, w.lim, w.dt, a, w.st);
         if (e != cudaSuccess) break;
         // stage 1: lam = 1/3 lam + 3/4 la + (lbb + dt R'(x0)^T lbb)
         a.x = w.slot(3 * n); a.mu = lbb; a.out = lam; a.b = 1.0; a.codes = cd(3 * n);
         a.v1 = lam; a.e1 = 1.0 / 3.0; a.v2 = la; a.e2 = 0.75;
-        e = struct_adjoint(w.m, w.lim, w.dt, a, w.st);
+        e = adjoint_any(w.m, w.lim, w.dt, a, w.st);
       }
     }
   }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -79,6 +80,15 @@ struct UnstructDev {
   int32_t *gen_cell = nullptr;   // [n_faces][2][kg]
   double *gen_coef = nullptr;    // [n_faces][2][kg]
   float *gen_coef_f = nullptr;
+  // adjoint gather lists, built on the first adjoint call: cell -> its
+  // faces, and cell -> the (face, side | k << 1) upstream-stencil entries
+  // that name it (hexahedra: k = 0, the single upstream cell)
+  bool adj_ready = false;
+  int32_t *adj_cf_ptr = nullptr;   // [n_cells + 1]
+  int32_t *adj_cf = nullptr;       // [2 n_faces]
+  int32_t *adj_inv_ptr = nullptr;  // [n_cells + 1]
+  int32_t *adj_inv_f = nullptr;
+  uint8_t *adj_inv_sk = nullptr;
 };
 
 }  // namespace fl
@@ -98,4 +108,5 @@ struct fl_mesh {
   std::vector<uint8_t> face_flip;
   bool renumbered = false;
   fl::UnstructDev u;
+  std::mutex adj_mu;  // guards the lazy build of the adjoint lists
 };

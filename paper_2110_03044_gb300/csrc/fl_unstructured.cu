@@ -198,6 +198,134 @@ __global__ void k_unstruct_selection(const T *u, const int4 *c4, int4 *sel, long
   }
 }
 
+// ------------------------------------------------------------------ adjoint
+// Stage adjoint on face-based meshes, as a gather (no atomics, the same
+// result on every run).  The forward face value, linearised on the branch
+// its evaluation takes (limited_face_lin), is
+//   theta_f ~ theta_C + alpha (theta_D - theta_C) + s beta b,
+// with b = sigma (theta_C - theta_U) s (hexahedra) or
+// b = sum_k coef_k (theta_k - theta_C) (general polyhedra).  With
+// h_f = mu_c1 / V_c1 - mu_c0 / V_c0 (the derivative of sum_c mu_c R_c with
+// respect to the flux u_f A_f theta_f) and G = h_f u_f A_f, face f hands
+//   C: G (1 - alpha + sigma beta)  or  G (1 - alpha - s beta sum_k coef_k),
+//   D: G alpha,
+//   U: -G sigma beta               or  stencil cell k: G s beta coef_k.
+// A cell sums what its own faces hand it (as C or D) and what the faces
+// whose upstream stencil names it hand it (the lists built by
+// unstruct_adjoint_prepare), evaluating each face where it needs it.
+template <class T>
+struct UAParams {
+  const T *x, *mu, *v1, *v2;
+  T *out;
+  const T *u;        // u_f, or w_f = (dt) A_f u_f when PRE
+  const T *area, *inv_vol;
+  const int4 *c4;
+  const int32_t *gen_cell;
+  const T *gen_coef;
+  int kg;
+  const int32_t *cf_ptr, *cf, *inv_ptr, *inv_f;
+  const uint8_t *inv_sk;
+  T e1, e2, b, bdt;
+  int bare;
+  long long C;
+};
+
+template <class T>
+struct ULin {
+  T G, al, be, sumc;  // sumc: sigma (hexahedra) or sum_k coef_k (general)
+  bool sp;
+};
+
+template <class T, int LIM, bool GEN, bool PRE>
+__device__ __forceinline__ ULin<T> u_lin(const UAParams<T> &p, int f) {
+  using F = FT<T>;
+  ULin<T> r;
+  const int4 cc = p.c4[f];
+  const T uf = p.u[f];
+  r.sp = upwind_positive(uf);
+  const T t0 = p.x[cc.x], t1 = p.x[cc.y];
+  const T tC = r.sp ? t0 : t1;
+  const T a = F::sub(t1, t0);
+  T b;
+  if (GEN) {
+    const size_t base = ((size_t)f * 2 + (r.sp ? 0 : 1)) * (size_t)p.kg;
+    b = T(0);
+    r.sumc = T(0);
+    for (int k = 0; k < p.kg; ++k) {
+      b = F::fma(p.gen_coef[base + k], F::sub(p.x[p.gen_cell[base + k]], tC), b);
+      r.sumc = F::add(r.sumc, p.gen_coef[base + k]);
+    }
+  } else {
+    const unsigned up = r.sp ? (unsigned)cc.z : (unsigned)cc.w;
+    const bool sneg = (up & SIGMA_BIT) != 0;
+    b = flip_sign(F::sub(tC, p.x[up & ~SIGMA_BIT]), (!r.sp) != sneg);
+    r.sumc = sneg ? T(-1) : T(1);
+  }
+  T c1;
+  limited_face_lin<T, LIM>(a, b, r.al, r.be, c1);
+  const T h = F::sub(F::mul(p.mu[cc.y], p.inv_vol[cc.y]), F::mul(p.mu[cc.x], p.inv_vol[cc.x]));
+  r.G = F::mul(h, PRE ? uf : F::mul(uf, p.area[f]));
+  return r;
+}
+
+template <class T, int LIM, bool GEN, bool PRE>
+__global__ void __launch_bounds__(256) k_unstruct_adjoint(const UAParams<T> p) {
+  using F = FT<T>;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < p.C;
+       c += (long long)gridDim.x * blockDim.x) {
+    T acc = T(0);
+    for (int q = p.cf_ptr[c]; q < p.cf_ptr[c + 1]; ++q) {
+      const int f = p.cf[q];
+      const ULin<T> L = u_lin<T, LIM, GEN, PRE>(p, f);
+      const int4 cc = p.c4[f];
+      const bool isC = L.sp ? (cc.x == c) : (cc.y == c);
+      if (isC) {
+        // 1 - alpha + sigma beta (hexahedra); 1 - alpha - s beta sum coef
+        const T up = GEN ? F::mul(L.sp ? -L.be : L.be, L.sumc) : F::mul(L.sumc, L.be);
+        acc = F::fma(L.G, F::add(F::sub(T(1), L.al), up), acc);
+      } else {
+        acc = F::fma(L.G, L.al, acc);
+      }
+    }
+    for (int q = p.inv_ptr[c]; q < p.inv_ptr[c + 1]; ++q) {
+      const int f = p.inv_f[q];
+      const int sk = p.inv_sk[q];
+      const bool side_pos = (sk & 1) == 0;  // side 0: C = c0, the s > 0 side
+      if (upwind_positive(p.u[f]) != side_pos) continue;
+      const ULin<T> L = u_lin<T, LIM, GEN, PRE>(p, f);
+      if (GEN) {
+        const T coef = p.gen_coef[((size_t)f * 2 + (sk & 1)) * (size_t)p.kg + (sk >> 1)];
+        acc = F::fma(L.G, F::mul(L.sp ? L.be : -L.be, coef), acc);
+      } else {
+        acc = F::fma(L.G, F::mul(-L.sumc, L.be), acc);
+      }
+    }
+    T o;
+    if (p.bare) {
+      o = acc;
+    } else {
+      o = F::fma(p.bdt, acc, F::mul(p.b, p.mu[c]));
+      if (p.v1) o = F::fma(p.e1, p.v1[c], o);
+      if (p.v2) o = F::fma(p.e2, p.v2[c], o);
+    }
+    p.out[c] = o;
+  }
+}
+
+// w_f = fac A_f u_f for the adjoint (fac = dt, or 1), any precision; a
+// product that underflows keeps the sign of u_f
+template <class T>
+__global__ void k_scale_area_t(const T *u, const T *area, T *w, long long nf, T fac) {
+  using F = FT<T>;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
+       f += (long long)gridDim.x * blockDim.x) {
+    const T uf = u[f];
+    T v = F::mul(F::mul(uf, area[f]), fac);
+    if (upwind_positive(uf) && !upwind_positive(v)) v = F::val(1);
+    w[f] = v;
+  }
+}
+
 template <class T, int SEED, bool PRE, bool GEN>
 cudaError_t launch_lim(int lim, const fl_mesh *m, const UParams<T> &p, cudaStream_t st) {
   const int nb = m->u.n_blocks;
@@ -846,11 +974,162 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   return FL_OK;
 }
 
+// The gather lists of the adjoint, built once per mesh from the device
+// records (face cells, upstream cells, general stencil).
+fl_status unstruct_adjoint_prepare(const fl_mesh *mc) {
+  fl_mesh *m = const_cast<fl_mesh *>(mc);
+  std::lock_guard<std::mutex> lock(m->adj_mu);
+  UnstructDev &u = m->u;
+  if (u.adj_ready) return FL_OK;
+  const int64_t C = m->C, F = m->F;
+  std::vector<int4> c4(F);
+  if (F > 0 && cudaMemcpy(c4.data(), u.face_c4, F * sizeof(int4), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(FL_ECUDA, "face record download failed");
+  std::vector<int32_t> gcell;
+  std::vector<double> gcoef;
+  const int kg = u.kg;
+  if (kg > 0) {
+    gcell.resize((size_t)F * 2 * kg);
+    gcoef.resize((size_t)F * 2 * kg);
+    if (cudaMemcpy(gcell.data(), u.gen_cell, gcell.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(gcoef.data(), u.gen_coef, gcoef.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(FL_ECUDA, "stencil download failed");
+  }
+  // cell -> faces
+  std::vector<int32_t> cf_ptr(C + 1, 0), cf(2 * F);
+  for (int64_t f = 0; f < F; ++f) {
+    cf_ptr[c4[f].x + 1]++;
+    cf_ptr[c4[f].y + 1]++;
+  }
+  for (int64_t c = 0; c < C; ++c) cf_ptr[c + 1] += cf_ptr[c];
+  {
+    std::vector<int32_t> fill(cf_ptr.begin(), cf_ptr.end() - 1);
+    for (int64_t f = 0; f < F; ++f) {
+      cf[fill[c4[f].x]++] = (int32_t)f;
+      cf[fill[c4[f].y]++] = (int32_t)f;
+    }
+  }
+  // cell -> (face, side | k << 1) entries naming it upstream
+  std::vector<int32_t> inv_ptr(C + 1, 0);
+  auto for_entries = [&](auto fn) {
+    for (int64_t f = 0; f < F; ++f)
+      for (int side = 0; side < 2; ++side) {
+        if (kg > 0) {
+          for (int k = 0; k < kg; ++k) {
+            const size_t i = ((size_t)f * 2 + side) * kg + k;
+            if (gcoef[i] != 0.0) fn(gcell[i], f, side | (k << 1));
+          }
+        } else {
+          const unsigned up = (unsigned)(side == 0 ? c4[f].z : c4[f].w);
+          if (up != 0xFFFFFFFFu) fn((int32_t)(up & ~SIGMA_BIT), f, side);
+        }
+      }
+  };
+  for_entries([&](int32_t c, int64_t, int) { inv_ptr[c + 1]++; });
+  for (int64_t c = 0; c < C; ++c) inv_ptr[c + 1] += inv_ptr[c];
+  std::vector<int32_t> inv_f(inv_ptr[C]);
+  std::vector<uint8_t> inv_sk(inv_ptr[C]);
+  {
+    std::vector<int32_t> fill(inv_ptr.begin(), inv_ptr.end() - 1);
+    for_entries([&](int32_t c, int64_t f, int sk) {
+      inv_f[fill[c]] = (int32_t)f;
+      inv_sk[fill[c]++] = (uint8_t)sk;
+    });
+  }
+  fl_status st = upload(cf_ptr, &u.adj_cf_ptr);
+  if (st == FL_OK) st = upload(cf, &u.adj_cf);
+  if (st == FL_OK) st = upload(inv_ptr, &u.adj_inv_ptr);
+  if (st == FL_OK && !inv_f.empty()) st = upload(inv_f, &u.adj_inv_f);
+  if (st == FL_OK && !inv_sk.empty()) st = upload(inv_sk, &u.adj_inv_sk);
+  if (st == FL_OK) u.adj_ready = true;
+  return st;
+}
+
+namespace {
+template <class T, int LIM>
+cudaError_t launch_uadj(const fl_mesh *m, const UAParams<T> &p, bool pre, cudaStream_t st) {
+  long long blocks = (m->C + 255) / 256;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  const unsigned g = (unsigned)std::max<long long>(blocks, 1);
+  const bool gen = m->u.kg > 0;
+  if (gen && pre) k_unstruct_adjoint<T, LIM, true, true><<<g, 256, 0, st>>>(p);
+  else if (gen) k_unstruct_adjoint<T, LIM, true, false><<<g, 256, 0, st>>>(p);
+  else if (pre) k_unstruct_adjoint<T, LIM, false, true><<<g, 256, 0, st>>>(p);
+  else k_unstruct_adjoint<T, LIM, false, false><<<g, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t run_uadj(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t st) {
+  UAParams<T> p;
+  p.x = static_cast<const T *>(s.x);
+  p.mu = static_cast<const T *>(s.mu);
+  p.v1 = static_cast<const T *>(s.v1);
+  p.v2 = static_cast<const T *>(s.v2);
+  p.out = static_cast<T *>(s.out);
+  const bool pre = s.cu != nullptr;
+  p.u = static_cast<const T *>(pre ? s.cu : s.u);
+  if (sizeof(T) == 8) {
+    p.area = reinterpret_cast<const T *>(m->u.area);
+    p.inv_vol = reinterpret_cast<const T *>(m->u.inv_vol);
+    p.gen_coef = reinterpret_cast<const T *>(m->u.gen_coef);
+  } else {
+    p.area = reinterpret_cast<const T *>(m->u.area_f);
+    p.inv_vol = reinterpret_cast<const T *>(m->u.inv_vol_f);
+    p.gen_coef = reinterpret_cast<const T *>(m->u.gen_coef_f);
+  }
+  p.c4 = m->u.face_c4;
+  p.gen_cell = m->u.gen_cell;
+  p.kg = m->u.kg;
+  p.cf_ptr = m->u.adj_cf_ptr;
+  p.cf = m->u.adj_cf;
+  p.inv_ptr = m->u.adj_inv_ptr;
+  p.inv_f = m->u.adj_inv_f;
+  p.inv_sk = m->u.adj_inv_sk;
+  p.e1 = (T)s.e1;
+  p.e2 = (T)s.e2;
+  p.b = (T)s.b;
+  p.bdt = (T)(s.cu_dt ? s.b : s.b * s.dt);
+  p.bare = s.bare;
+  p.C = m->C;
+  switch (lim) {
+    case LIM_UPWIND: return launch_uadj<T, LIM_UPWIND>(m, p, pre, st);
+    case LIM_CENTRAL: return launch_uadj<T, LIM_CENTRAL>(m, p, pre, st);
+    case LIM_MINMOD: return launch_uadj<T, LIM_MINMOD>(m, p, pre, st);
+    case LIM_VANLEER: return launch_uadj<T, LIM_VANLEER>(m, p, pre, st);
+    case LIM_SUPERBEE: return launch_uadj<T, LIM_SUPERBEE>(m, p, pre, st);
+    case LIM_SMART: return launch_uadj<T, LIM_SMART>(m, p, pre, st);
+  }
+  return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t unstruct_adjoint(const fl_mesh *m, int lim, fl_dtype dt, const AdjArgs &s,
+                             cudaStream_t st) {
+  if (m->C == 0) return cudaSuccess;
+  return dt == FL_F64 ? run_uadj<double>(m, lim, s, st) : run_uadj<float>(m, lim, s, st);
+}
+
+cudaError_t unstruct_scale_area(const fl_mesh *m, fl_dtype dt, const void *u, void *w, double fac,
+                                cudaStream_t st) {
+  if (m->F == 0) return cudaSuccess;
+  long long blocks = (m->F + 255) / 256;
+  if (blocks > 152LL * 32) blocks = 152LL * 32;
+  if (dt == FL_F64)
+    k_scale_area_t<double><<<(unsigned)blocks, 256, 0, st>>>(
+        static_cast<const double *>(u), m->u.area, static_cast<double *>(w), m->F, fac);
+  else
+    k_scale_area_t<float><<<(unsigned)blocks, 256, 0, st>>>(
+        static_cast<const float *>(u), m->u.area_f, static_cast<float *>(w), m->F, (float)fac);
+  return cudaGetLastError();
+}
+
 void unstruct_free(fl_mesh *m) {
   UnstructDev &u = m->u;
-  void *ptrs[] = {u.blk_cell, u.blk_entry, u.ent_face, u.ent_cells, u.cell_slots, u.face_c4,
-                  u.area, u.vol, u.inv_vol, u.area_f, u.inv_vol_f, u.gen_cell, u.gen_coef,
-                  u.gen_coef_f};
+  void *ptrs[] = {u.blk_cell,   u.blk_entry,  u.ent_face,    u.ent_cells, u.cell_slots,
+                  u.face_c4,    u.area,       u.vol,         u.inv_vol,   u.area_f,
+                  u.inv_vol_f,  u.gen_cell,   u.gen_coef,    u.gen_coef_f, u.adj_cf_ptr,
+                  u.adj_cf,     u.adj_inv_ptr, u.adj_inv_f,  u.adj_inv_sk};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   u = UnstructDev();

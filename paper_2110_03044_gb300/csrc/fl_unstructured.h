@@ -19,6 +19,14 @@ fl_status unstruct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double d
 cudaError_t unstruct_selection(const fl_mesh *m, fl_dtype dt, const void *u, int32_t *sel,
                                cudaStream_t st);
 const double *unstruct_volumes(const fl_mesh *m);
+struct AdjArgs;
+// adjoint of one stage on a face-based mesh (fl_kernels.h's AdjArgs)
+fl_status unstruct_adjoint_prepare(const fl_mesh *m);
+cudaError_t unstruct_adjoint(const fl_mesh *m, int lim, fl_dtype dt, const AdjArgs &s,
+                             cudaStream_t st);
+// w_f = fac A_f u_f (internal face order)
+cudaError_t unstruct_scale_area(const fl_mesh *m, fl_dtype dt, const void *u, void *w, double fac,
+                                cudaStream_t st);
 struct StageArgs;
 cudaError_t unstruct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs &s,
                            cudaStream_t st);
