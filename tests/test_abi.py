@@ -31,6 +31,10 @@ def test_host_side_argument_errors_without_gpu(fl):
     with pytest.raises(fl.FLError) as e:
         fl.fl_mesh_create_structured(0, 4, 4, 1.0, 1.0, 1.0)
     assert e.value.status == fl.FL_EINVAL
+    # 2^31 cells is one past the largest structured mesh
+    with pytest.raises(fl.FLError) as e:
+        fl.fl_mesh_create_structured(1024, 1024, 2048, 1.0, 1.0, 1.0)
+    assert e.value.status == fl.FL_EUNSUPPORTED
     assert fl.fl_reduce_workspace_size() > 0
 
 
