@@ -67,13 +67,13 @@ def stage_bytes_per_cell(es, stage):
 
 # FP64 operations per cell of one stage in the kernel's formulation: per
 # face one difference and the limited face value (one fma for minmod /
-# superbee / central, three for SMART, six for van Leer: pq, p+q, the three
+# superbee / central, two for SMART, six for van Leer: pq, p+q, the three
 # operations of the Newton quotient and the fma);
 # per cell six fmas w theta_f (the flux product folded into the update with
 # the pre-scaled velocity w = dt (A/V) u) and two more for the RK blend of
 # stages 2-3.  Superbee: 12 + 14 + 14 = 40 per SSP-RK3 step.
 def stage_fp64_ops_per_cell(lim, stage):
-    per_face = {"upwind": 1, "central": 2, "minmod": 2, "superbee": 2, "smart": 4,
+    per_face = {"upwind": 1, "central": 2, "minmod": 2, "superbee": 2, "smart": 3,
                 "vanleer": 7}[lim]
     return 3 * per_face + 6 + (2 if stage > 0 else 0)
 
