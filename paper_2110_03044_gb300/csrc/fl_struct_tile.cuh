@@ -33,6 +33,12 @@ struct SParams {
 
 enum { SEED_PLAIN = 0, SEED_COMBINE = 1, SEED_APPLY = 2 };
 
+// Keeps a value as computed: the compiler may no longer recompute it from
+// its operands at a later use.  Under the register cap it otherwise
+// rematerialised the z-window differences, spending FP64 pipe slots.
+__device__ __forceinline__ void keep(double &x) { asm("" : "+d"(x)); }
+__device__ __forceinline__ void keep(float &x) { asm("" : "+f"(x)); }
+
 __device__ __forceinline__ int wrap(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
@@ -154,6 +160,8 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
     const T d_m2 = F::sub(tm1, tm2);
     dz_m1 = F::sub(th0, tm1);
     dz_0 = F::sub(thp1, th0);
+    keep(dz_m1);
+    keep(dz_0);
     const T uz = p.u[p.uz_off + col + p.plane * wrap(z0 - 1, nz)];
     const bool sp = upwind_positive(sign_toggled(uz, p.flip));
     const T thf = limited_face<T, LIM>(sp ? tm1 : th0, dz_m1, sp ? d_m2 : dz_0, sp);
@@ -200,7 +208,10 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
       }
     }
     T dz_p1 = T(0);
-    if (need_z) dz_p1 = F::sub(thp2, thp1);
+    if (need_z) {
+      dz_p1 = F::sub(thp2, thp1);
+      keep(dz_p1);
+    }
     __syncthreads();
     // ----------------------------------------------- phase B: fluxes
     if (need_x) {

@@ -72,10 +72,13 @@ struct UParams {
   int kg;
 };
 
+// v with its sign bit toggled when neg, on the integer pipe (opaque bits:
+// otherwise the compiler may evaluate a flipped difference as both
+// subtractions and a select, one FP64 add more per face entry)
 template <class T>
 __device__ __forceinline__ T flip_sign(T v, bool neg) {
   using F = FT<T>;
-  return F::val(F::bits(v) ^ (neg ? F::SIGN : typename F::U(0)));
+  return F::val(F::opaque_bits(v) ^ (neg ? F::SIGN : typename F::U(0)));
 }
 
 // PRE: p.u holds w_f = dt A_f u_f (pre-scaled once per call, same signs);
