@@ -1,0 +1,65 @@
+// Test probe (not part of the library): runs two FP64 building blocks of
+// the stage kernels, FT<double>::quot (the van Leer quotient by
+// Newton-Raphson) and smart_piece (SMART's exact integer piece test), on
+// arrays, beside CUDA's IEEE division __ddiv_rn for the quotient.
+#include <cuda_runtime.h>
+
+#include "fl_face.cuh"
+
+namespace {
+
+__global__ void k_quot(const double *n, const double *s, double *q, double *ref, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  q[i] = fl::FT<double>::quot(n[i], s[i], true);
+  ref[i] = __ddiv_rn(n[i], s[i]);
+}
+
+__global__ void k_smart(const double *p, const double *q, int *piece, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  using F = fl::FT<double>;
+  piece[i] = fl::smart_piece<double>(F::bits(p[i]), F::bits(q[i]), true);
+}
+
+template <class T>
+int to_device(const T *h, T **d, int count) {
+  if (cudaMalloc(d, sizeof(T) * (size_t)count) != cudaSuccess) return 1;
+  if (h && cudaMemcpy(*d, h, sizeof(T) * (size_t)count, cudaMemcpyHostToDevice) != cudaSuccess)
+    return 1;
+  return 0;
+}
+
+}  // namespace
+
+// n, s: inputs; q: quot(n, s); ref: __ddiv_rn(n, s).  Host arrays of count.
+extern "C" int probe_quot(const double *n, const double *s, double *q, double *ref, int count) {
+  double *dn = nullptr, *ds = nullptr, *dq = nullptr, *dr = nullptr;
+  int rc = to_device(n, &dn, count) | to_device(s, &ds, count) |
+           to_device<double>(nullptr, &dq, count) | to_device<double>(nullptr, &dr, count);
+  if (rc == 0) {
+    k_quot<<<(count + 255) / 256, 256>>>(dn, ds, dq, dr, count);
+    rc = cudaMemcpy(q, dq, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess;
+    rc |= cudaMemcpy(ref, dr, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess;
+  }
+  cudaFree(dn);
+  cudaFree(ds);
+  cudaFree(dq);
+  cudaFree(dr);
+  return rc;
+}
+
+// p, q > 0: inputs; piece: smart_piece(p, q).  Host arrays of count.
+extern "C" int probe_smart(const double *p, const double *q, int *piece, int count) {
+  double *dp = nullptr, *dq = nullptr;
+  int *dk = nullptr;
+  int rc = to_device(p, &dp, count) | to_device(q, &dq, count) | to_device<int>(nullptr, &dk, count);
+  if (rc == 0) {
+    k_smart<<<(count + 255) / 256, 256>>>(dp, dq, dk, count);
+    rc = cudaMemcpy(piece, dk, sizeof(int) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess;
+  }
+  cudaFree(dp);
+  cudaFree(dq);
+  cudaFree(dk);
+  return rc;
+}

@@ -1,0 +1,128 @@
+"""Two FP64 building blocks of the stage kernels, run on the device through a
+small probe compiled against the library's own header (fl_face.cuh):
+
+* the van Leer quotient p q / (p + q), computed by Newton-Raphson division
+  from an FP32 seed instead of an IEEE division: against CUDA's __ddiv_rn,
+  relative error below 2^-47 where the fast path runs, and identical to it
+  where the exponent of the divisor sends it to the IEEE division;
+* SMART's piece test on the integer pipe (r >= 5, r <= 1/5 for r = p / q):
+  against the exact decision in rational arithmetic, including ties, inputs
+  one ulp either side of the boundaries, and subnormal operands."""
+import ctypes
+import os
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2110_03044_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def probe(tmp_path_factory):
+    from paper_2110_03044_gb300._build_lib import ARCH, _nvcc
+    out = str(tmp_path_factory.mktemp("probe") / "face_arith_probe.so")
+    cmd = [_nvcc()] + ARCH + ["-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+                              "-I" + CSRC, os.path.join(HERE, "cuda", "face_arith_probe.cu"),
+                              "-o", out]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr[-3000:]
+    lib = ctypes.CDLL(out)
+    P = ctypes.c_void_p
+    lib.probe_quot.argtypes = [P, P, P, P, ctypes.c_int]
+    lib.probe_smart.argtypes = [P, P, P, ctypes.c_int]
+    return lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _quot(probe, n, s):
+    n = np.ascontiguousarray(n, np.float64)
+    s = np.ascontiguousarray(s, np.float64)
+    q = np.empty_like(n)
+    ref = np.empty_like(n)
+    assert probe.probe_quot(_ptr(n), _ptr(s), _ptr(q), _ptr(ref), len(n)) == 0
+    return q, ref
+
+
+def _exponent_field(x):
+    return (np.asarray(x, np.float64).view(np.uint64) >> np.uint64(52)) & np.uint64(0x7FF)
+
+
+def test_van_leer_quotient_against_ieee_division(probe):
+    rng = np.random.default_rng(3)
+    k = 200000
+    p = rng.uniform(0.5, 1.0, k) * 10.0 ** rng.integers(-150, 150, k)
+    q = rng.uniform(0.5, 1.0, k) * 10.0 ** rng.integers(-150, 150, k)
+    # the limiter's own operands: n = p q, s = p + q
+    n, s = p * q, p + q
+    got, ref = _quot(probe, n, s)
+    E = _exponent_field(s)
+    fast = (E >= 2) & (E <= 2044) & np.isfinite(n)
+    assert fast.all()
+    normal = fast & (np.abs(ref) >= np.finfo(np.float64).tiny)
+    rel = np.abs(got[normal] - ref[normal]) / np.abs(ref[normal])
+    assert rel.max() <= 2.0 ** -47, rel.max()
+    # tiny quotients round at subnormal spacing: within 4 of its units
+    sub = fast & ~normal
+    assert np.all(np.abs(got[sub] - ref[sub]) <= 4 * 2.0 ** -1074 + 2.0 ** -47 * np.abs(ref[sub]))
+
+
+def test_van_leer_quotient_range_edges_take_ieee_division(probe):
+    tiny = np.finfo(np.float64).tiny
+    big = np.finfo(np.float64).max
+    s = np.array([tiny / 8, tiny, 1.5 * tiny, 2 * tiny, 3.99 * tiny,  # E = 0, 1, 1, 2, 2
+                  2.0 ** 1021, 1.9 * 2.0 ** 1021, 2.0 ** 1022, big, np.inf, 5.0])
+    n = np.array([1e-320, 3e-310, 1.0, 2.5e-300, 7.0, 1e300, 2.0, 1.5e307, big, 1.0, np.inf])
+    got, ref = _quot(probe, n, s)
+    E = _exponent_field(s)
+    slow = (E < 2) | (E > 2044) | ~np.isfinite(n)
+    assert slow.sum() >= 6
+    np.testing.assert_array_equal(got[slow], ref[slow])
+    rel = np.abs(got[~slow] - ref[~slow]) / np.abs(ref[~slow])
+    assert rel.max() <= 2.0 ** -47
+
+
+def _exact_piece(p, q):
+    fp, fq = Fraction(float(p)), Fraction(float(q))
+    if fp >= 5 * fq:
+        return 1
+    if fq >= 5 * fp:
+        return 2
+    return 3
+
+
+def test_smart_piece_is_the_exact_decision(probe):
+    rng = np.random.default_rng(5)
+    p = [rng.uniform(0.5, 1.0, 4000) * 10.0 ** rng.integers(-300, 300, 4000)]
+    q = [p[0] * 10.0 ** rng.uniform(-2, 2, 4000)]
+    # one to four ulps either side of q = 5p and p = 5q, and the ties
+    base = rng.uniform(1.0, 2.0, 500) * 2.0 ** rng.integers(-1000, 1000, 500)
+    for step in range(-4, 5):
+        five = base * 5.0
+        for _ in range(abs(step)):
+            five = np.nextafter(five, np.inf if step > 0 else -np.inf)
+        p += [base, five]
+        q += [five, base]
+    ties = 2.0 ** rng.integers(-1000, 1000, 200).astype(np.float64)
+    p += [ties, 5 * ties]
+    q += [5 * ties, ties]
+    # subnormal operands (and normal ones beside them)
+    sub = rng.integers(1, 2 ** 40, 600).astype(np.float64) * 2.0 ** -1074
+    p += [sub[:300], sub[300:] * 5, np.full(100, 2.0 ** -1020)]
+    q += [sub[300:], sub[:300], sub[:100]]
+    p = np.concatenate(p)
+    q = np.concatenate(q)
+    assert np.all(p > 0) and np.all(q > 0) and np.all(np.isfinite(p)) and np.all(np.isfinite(q))
+    piece = np.empty(len(p), np.int32)
+    assert probe.probe_smart(_ptr(p), _ptr(q), _ptr(piece), len(p)) == 0
+    want = np.array([_exact_piece(a, b) for a, b in zip(p, q)], np.int32)
+    bad = np.nonzero(piece != want)[0]
+    assert bad.size == 0, [(p[i], q[i], piece[i], want[i]) for i in bad[:5]]
+    assert {1, 2, 3} <= set(want.tolist())
