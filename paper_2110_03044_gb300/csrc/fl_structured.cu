@@ -42,8 +42,11 @@ constexpr int STY = FL_STRUCT_TY;
 #ifndef FL_CODES_MINB
 #define FL_CODES_MINB 4
 #endif
+#ifndef FL_STRUCT_MINB
+#define FL_STRUCT_MINB (32 / STY)
+#endif
 template <class T, int LIM, int SEED, int TY, bool PRE, bool MOD, bool CODES>
-__global__ void __launch_bounds__(TX *TY, CODES ? FL_CODES_MINB : 32 / TY)
+__global__ void __launch_bounds__(TX *TY, CODES ? FL_CODES_MINB : FL_STRUCT_MINB)
     k_struct_stage(const SParams<T> p) {
   stage_tile<T, LIM, SEED, TY, PRE, MOD, CODES>(p, blockIdx.x);
 }
