@@ -13,7 +13,7 @@
 //     the neighbouring warps through L1), one plane ahead with the face
 //     velocities;
 //   * the z neighbours live in registers, loaded one plane ahead;
-//   * each face value uses FP32 min/max (limited_face_native) and the
+//   * each face flux uses FP32 min/max (native_flux) and the
 //     accumulation order of the TMA kernel (fl_struct_tma.cu: x, y, z; the
 //     + face before the - face), so both kernels give the same bits.
 // Each x face is evaluated once per warp (the -x face of a cell arrives by
@@ -38,7 +38,7 @@ template <int LIM>
 __device__ __forceinline__ float reg_flux(float u, float thC_pos, float thC_neg, float a,
                                           float b_pos, float b_neg, unsigned flip) {
   const bool sp = __uint_as_float(__float_as_uint(u) ^ flip) > 0.0f;
-  return __fmul_rn(u, limited_face_native<LIM>(sp ? thC_pos : thC_neg, a, sp ? b_pos : b_neg, sp));
+  return native_flux<LIM>(u, sp ? thC_pos : thC_neg, a, sp ? b_pos : b_neg, flip);
 }
 
 template <int LIM, int SEED>

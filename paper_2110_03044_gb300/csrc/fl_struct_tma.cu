@@ -25,7 +25,7 @@
 //     row is the -y face of the next, computed by another warp from the same
 //     values with the same code, so both sides see bit-identical fluxes) and
 //     the +z face; the -z face is the previous plane's, kept in a register;
-//   * the limiter runs on FP32 min/max (limited_face_native).
+//   * the limiter runs on FP32 min/max (native_flux).
 // Every mbarrier wait is bounded: on expiry the warp records FL_ETIMEOUT in
 // the mesh status word and stops; the producer stops issuing and waits
 // (bounded again) for the copies it has in flight before it returns.
@@ -140,7 +140,7 @@ template <int LIM>
 __device__ __forceinline__ float flux(float u, float thC_pos, float thC_neg, float a, float b_pos,
                                       float b_neg) {
   const bool sp = u > 0.0f;
-  return __fmul_rn(u, limited_face_native<LIM>(sp ? thC_pos : thC_neg, a, sp ? b_pos : b_neg, sp));
+  return native_flux<LIM>(u, sp ? thC_pos : thC_neg, a, sp ? b_pos : b_neg);
 }
 
 __device__ __forceinline__ float4 ld4(const unsigned char *base, int off_bytes) {

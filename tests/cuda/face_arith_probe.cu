@@ -1,7 +1,7 @@
-// Test probe (not part of the library): runs two FP64 building blocks of
-// the stage kernels, FT<double>::quot (the van Leer quotient by
-// Newton-Raphson) and smart_piece (SMART's exact integer piece test), on
-// arrays, beside CUDA's IEEE division __ddiv_rn for the quotient.
+// Test probe (not part of the library): runs building blocks of the stage
+// kernels on arrays -- FT<double>::quot and FT<float>::quot (the van Leer
+// quotient by Newton-Raphson) beside CUDA's IEEE divisions __ddiv_rn and
+// __fdiv_rn, and smart_piece (SMART's exact integer piece test).
 #include <cuda_runtime.h>
 
 #include "fl_face.cuh"
@@ -13,6 +13,13 @@ __global__ void k_quot(const double *n, const double *s, double *q, double *ref,
   if (i >= count) return;
   q[i] = fl::FT<double>::quot(n[i], s[i], true);
   ref[i] = __ddiv_rn(n[i], s[i]);
+}
+
+__global__ void k_quot32(const float *n, const float *s, float *q, float *ref, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  q[i] = fl::FT<float>::quot(n[i], s[i], true);
+  ref[i] = __fdiv_rn(n[i], s[i]);
 }
 
 __global__ void k_smart(const double *p, const double *q, int *piece, int count) {
@@ -41,6 +48,23 @@ extern "C" int probe_quot(const double *n, const double *s, double *q, double *r
     k_quot<<<(count + 255) / 256, 256>>>(dn, ds, dq, dr, count);
     rc = cudaMemcpy(q, dq, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess;
     rc |= cudaMemcpy(ref, dr, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess;
+  }
+  cudaFree(dn);
+  cudaFree(ds);
+  cudaFree(dq);
+  cudaFree(dr);
+  return rc;
+}
+
+// The same for FT<float>::quot against __fdiv_rn.
+extern "C" int probe_quot32(const float *n, const float *s, float *q, float *ref, int count) {
+  float *dn = nullptr, *ds = nullptr, *dq = nullptr, *dr = nullptr;
+  int rc = to_device(n, &dn, count) | to_device(s, &ds, count) |
+           to_device<float>(nullptr, &dq, count) | to_device<float>(nullptr, &dr, count);
+  if (rc == 0) {
+    k_quot32<<<(count + 255) / 256, 256>>>(dn, ds, dq, dr, count);
+    rc = cudaMemcpy(q, dq, sizeof(float) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess;
+    rc |= cudaMemcpy(ref, dr, sizeof(float) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess;
   }
   cudaFree(dn);
   cudaFree(ds);

@@ -1,10 +1,11 @@
-"""Two FP64 building blocks of the stage kernels, run on the device through a
+"""Building blocks of the stage kernels, run on the device through a
 small probe compiled against the library's own header (fl_face.cuh):
 
 * the van Leer quotient p q / (p + q), computed by Newton-Raphson division
-  from an FP32 seed instead of an IEEE division: against CUDA's __ddiv_rn,
-  relative error below 2^-47 where the fast path runs, and identical to it
-  where the exponent of the divisor sends it to the IEEE division;
+  instead of an IEEE division: in FP64 (from an FP32 seed) against CUDA's
+  __ddiv_rn, relative error below 2^-47; in FP32 against __fdiv_rn, below
+  2^-22; and identical to the IEEE quotient where the divisor's range sends
+  it to the IEEE division;
 * SMART's piece test on the integer pipe (r >= 5, r <= 1/5 for r = p / q):
   against the exact decision in rational arithmetic, including ties, inputs
   one ulp either side of the boundaries, and subnormal operands."""
@@ -34,6 +35,7 @@ def probe(tmp_path_factory):
     lib = ctypes.CDLL(out)
     P = ctypes.c_void_p
     lib.probe_quot.argtypes = [P, P, P, P, ctypes.c_int]
+    lib.probe_quot32.argtypes = [P, P, P, P, ctypes.c_int]
     lib.probe_smart.argtypes = [P, P, P, ctypes.c_int]
     return lib
 
@@ -87,6 +89,32 @@ def test_van_leer_quotient_range_edges_take_ieee_division(probe):
     np.testing.assert_array_equal(got[slow], ref[slow])
     rel = np.abs(got[~slow] - ref[~slow]) / np.abs(ref[~slow])
     assert rel.max() <= 2.0 ** -47
+
+
+def test_van_leer_quotient_fp32_against_ieee_division(probe):
+    rng = np.random.default_rng(4)
+    k = 200000
+    p = (rng.uniform(0.5, 1.0, k) * 10.0 ** rng.integers(-18, 18, k)).astype(np.float32)
+    q = (rng.uniform(0.5, 1.0, k) * 10.0 ** rng.integers(-18, 18, k)).astype(np.float32)
+    # the range edges: sums below 2^-125 or above 2^62 take the IEEE division
+    edge_p = np.array([2.0 ** -127, 2.0 ** -126, 1e-38, 2.0 ** 61, 2.0 ** 62, 1e20, 3e38],
+                      np.float32)
+    edge_q = np.array([2.0 ** -128, 2.0 ** -127, 1e-38, 2.0 ** 61, 1.0, 1e19, 1e30], np.float32)
+    p = np.concatenate([p, edge_p])
+    q = np.concatenate([q, edge_q])
+    with np.errstate(over="ignore", under="ignore"):
+        n, s = p * q, p + q
+    got = np.empty_like(n)
+    ref = np.empty_like(n)
+    assert probe.probe_quot32(_ptr(n), _ptr(s), _ptr(got), _ptr(ref), len(n)) == 0
+    slow = ~((s >= np.float32(2.0 ** -125)) & (s <= np.float32(2.0 ** 62)))
+    assert slow.sum() >= 5
+    np.testing.assert_array_equal(got[slow], ref[slow])
+    normal = ~slow & (np.abs(ref) >= np.finfo(np.float32).tiny)
+    rel = np.abs(got[normal].astype(np.float64) - ref[normal]) / np.abs(ref[normal])
+    assert rel.max() <= 2.0 ** -22, rel.max()
+    sub = ~slow & ~normal
+    assert np.all(np.abs(got[sub] - ref[sub]) <= 4 * 2.0 ** -149)
 
 
 def _exact_piece(p, q):
