@@ -45,7 +45,7 @@ FP64_OPS_PEAK = 2 * 152 * 2.070e9
 NCU_TRAFFIC = {
     ("f64", "superbee", 256): (808.8e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
                                "algorithmic 805.3e6 (48 B x 16.8M cells)"),
-    ("f32", "superbee", 256): (330.5e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
+    ("f32", "superbee", 256): (330.9e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
                                "algorithmic 335.5e6 (20 B x 16.8M cells)"),
 }
 
