@@ -105,11 +105,17 @@ fl_status fl_mesh_create_structured(int nx, int ny, int nz, double hx, double hy
  *   face_normals double [n_faces][3], unit normal pointing c0 -> c1
  *   face_areas   double [n_faces] > 0
  *   cell_volumes double [n_cells] > 0
- * Supported meshes: every cell has an opposite face for each of its faces
- * (n_f . n_j = -+1 for exactly one other face j of the cell and 0 for the
- * rest), i.e. hexahedral meshes in any numbering and orientation; other
- * meshes return FL_EUNSUPPORTED.  Faces listed twice, c0 == c1, out-of-range
- * cells and non-unit normals return FL_EINVAL.
+ * Supported meshes: cells of at most 8 faces.  The upstream difference of
+ * a face f with upwind cell C is
+ *   - theta_C - theta_U across the face of C opposite f, where every face
+ *     of C has exactly one other face j with n_f . n_j = -+1 and the rest
+ *     are orthogonal (hexahedra in any numbering and orientation);
+ *   - otherwise (tetrahedra, prisms, mixed meshes) the weighted sum of eq.
+ *     (Delta_Upwind), s sum_j (n_f . n_j)(theta_{j,c1} - theta_{j,c0}) over
+ *     the other faces j of C, without distance weights (Section 6).
+ * Cells with more than 8 faces, and sizes of 2^31 - 1 or more, return
+ * FL_EUNSUPPORTED.  Faces listed twice, c0 == c1, out-of-range cells,
+ * non-unit normals and non-positive areas or volumes return FL_EINVAL.
  * With FL_RENUMBER the library reorders cells and faces into compact blocks
  * for locality; fields passed to compute calls are then in the INTERNAL
  * order given by fl_mesh_permutation.  Without it the user order is used.

@@ -178,6 +178,33 @@ def test_config_1d_resident(fl):
     m.close()
 
 
+# the largest 1D line the resident one-CTA kernel holds in shared memory
+# (five arrays in 200 KiB: 5120 FP64 or 10240 FP32 cells) and one cell more,
+# which takes the tiled kernel instead
+@pytest.mark.parametrize("rk", [1, 3])
+@pytest.mark.parametrize("lim", ["vanleer", "superbee", "smart"])
+@pytest.mark.parametrize("dtype,n", [(torch.float64, 5120), (torch.float64, 5121),
+                                     (torch.float32, 10240), (torch.float32, 10241)])
+def test_line_resident_size_limit(fl, dtype, n, lim, rk):
+    mesh, th, u = _mesh_inputs((n, 1, 1), seed=11)
+    u = u * 0.3
+    dt = 0.4 * mesh.h[0] / np.max(np.abs(u))
+    if dtype == torch.float32:
+        th = th.astype(np.float32).astype(np.float64)
+        u = u.astype(np.float32).astype(np.float64)
+    m = fl.Mesh.structured(n, 1, 1, *mesh.h)
+    ud = _dev(u, dtype)
+    cur = th
+    for _ in range(3):
+        ref = oracle.step(mesh, lim, rk, dt, 1, u, cur)
+        g = _dev(cur, dtype)
+        fl.step_rk(m, lim, g, ud, dt, 1, rk_order=rk)
+        got = g.cpu().double().numpy()
+        assert _rel(got, ref) <= TOL[dtype]
+        cur = ref if dtype == torch.float64 else got
+    m.close()
+
+
 def _raw_device_alloc(nbytes):
     """cudaMalloc of exactly nbytes through the CUDA runtime (the caching
     allocator would place a small tensor inside a larger allocation)."""
