@@ -339,8 +339,7 @@ fl_status step_rk_impl(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, do
                                            : nullptr;
     return unstruct_step(m, lim, dt, rk, dtime, nsteps, theta, u_f, ws, st, gfac, W);
   }
-  if (gfac == nullptr && m->ny == 1 && m->nz == 1 &&
-      (size_t)m->nx <= line_resident_max_cells(dt)) {
+  if (gfac == nullptr && line_resident_takes(m, dt)) {
     cudaError_t e = line_resident(m, lim, dt, theta, u_f, nsteps, rk, dtime, st);
     if (e != cudaSuccess) return cuda_fail(e, "1D resident kernel");
     return FL_OK;

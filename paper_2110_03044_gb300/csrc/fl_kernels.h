@@ -40,6 +40,10 @@ cudaError_t struct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double d
                         int64_t nsteps, void *theta, const void *u, void *A, void *B, void *W,
                         cudaStream_t st, const double *gfac = nullptr);
 size_t line_resident_max_cells(fl_dtype dt);
+// whether the one-CTA resident kernel runs a structured mesh's steps: a
+// periodic line of 2 .. line_resident_max_cells cells (a 1 x 1 x 1 mesh has
+// no faces and takes the tiled kernel, which reads no velocity there)
+bool line_resident_takes(const fl_mesh *m, fl_dtype dt);
 cudaError_t line_resident(const fl_mesh *m, int lim, fl_dtype dt, void *theta, const void *u,
                           int64_t nsteps, int rk, double dtime, cudaStream_t st);
 cudaError_t struct_selection(const fl_mesh *m, fl_dtype dt, const void *u, int32_t *sel,

@@ -96,7 +96,7 @@ extern "C" fl_status fl_step_rk_noalloc(const fl_mesh *m, fl_limiter lim, fl_dty
   if ((st = scratch_address(m->device, &ws)) != FL_OK) return st;
   cudaStream_t s = as_stream(stream);
   if (m->kind == 1) return unstruct_step(m, lim, dt, rk, dtime, nsteps, theta, u_f, ws, s);
-  if (m->ny == 1 && m->nz == 1 && (size_t)m->nx <= line_resident_max_cells(dt)) {
+  if (line_resident_takes(m, dt)) {
     cudaError_t e = line_resident(m, lim, dt, theta, u_f, nsteps, rk, dtime, s);
     if (e != cudaSuccess) return cuda_fail(e, "1D resident kernel");
     return FL_OK;

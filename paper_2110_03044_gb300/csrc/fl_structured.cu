@@ -343,7 +343,7 @@ cudaError_t struct_scale_faces(const fl_mesh *m, fl_dtype dt, const void *u, voi
 bool struct_step_prescales(const fl_mesh *m, fl_dtype dt) {
   if (dt != FL_F64) return false;
   if (m->kind == 1) return true;  // face-based meshes: w_f = dt A_f u_f
-  return !(m->ny == 1 && m->nz == 1 && (size_t)m->nx <= line_resident_max_cells(dt));
+  return !line_resident_takes(m, dt);
 }
 
 cudaError_t struct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
@@ -406,8 +406,14 @@ size_t line_resident_max_cells(fl_dtype dt) {
   return (200u * 1024u) / (5u * dsize(dt));
 }
 
+bool line_resident_takes(const fl_mesh *m, fl_dtype dt) {
+  return m->kind == 0 && m->nx > 1 && m->ny == 1 && m->nz == 1 &&
+         (size_t)m->nx <= line_resident_max_cells(dt);
+}
+
 cudaError_t line_resident(const fl_mesh *m, int lim, fl_dtype dt, void *theta, const void *u,
                           int64_t nsteps, int rk, double dtime, cudaStream_t st) {
+  if (!line_resident_takes(m, dt)) return cudaErrorInvalidValue;
   const double c = dtime / m->hx;
   return dt == FL_F64 ? run_line_t<double>(lim, theta, u, m->nx, nsteps, rk, c, st)
                       : run_line_t<float>(lim, theta, u, m->nx, nsteps, rk, c, st);
