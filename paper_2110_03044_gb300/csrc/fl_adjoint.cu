@@ -80,40 +80,82 @@ __device__ __forceinline__ int wrapi(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// Branch constants (alpha, beta, 1 - alpha + beta) of the piecewise-linear
+// limiters for branch codes 1..4, as the top 16 bits of their IEEE patterns
+// (every constant is a short binary fraction, so the remaining bits are
+// zero), four to a 64-bit word.  Decoding is a shift and a mask on the
+// integer pipe: a switch on the code compiled to per-lane indexed constant
+// loads, which serialise whenever the lanes of a warp hold different codes.
+// Code 0 (correction off) is alpha = beta = 0, 1 - alpha + beta = 1.
+//   minmod   1: beta 1/2      2: alpha 1/2
+//   superbee 1: beta 1   2: alpha 1/2   3: beta 1/2   4: alpha 1
+//   SMART    1: alpha 2  2: beta 1      3: alpha 1/8, beta 3/8
+//   central  1: alpha 1/2
+template <class T, int LIM>
+struct CoefTab {
+  static constexpr unsigned long long AL = 0, BE = 0, C1 = 0;
+};
+template <int LIM>
+struct CoefTab<float, LIM> {
+  static constexpr unsigned long long AL =
+      LIM == LIM_CENTRAL ? 0x3f00ull
+      : LIM == LIM_MINMOD ? 0x3f000000ull
+      : LIM == LIM_SUPERBEE ? 0x3f8000003f000000ull
+      : LIM == LIM_SMART ? 0x00003e0000004000ull : 0ull;
+  static constexpr unsigned long long BE =
+      LIM == LIM_MINMOD ? 0x3f00ull
+      : LIM == LIM_SUPERBEE ? 0x00003f0000003f80ull
+      : LIM == LIM_SMART ? 0x00003ec03f800000ull : 0ull;
+  static constexpr unsigned long long C1 =
+      LIM == LIM_CENTRAL ? 0x3f00ull
+      : LIM == LIM_MINMOD ? 0x3f003fc0ull
+      : LIM == LIM_SUPERBEE ? 0x00003fc03f004000ull
+      : LIM == LIM_SMART ? 0x00003fa04000bf80ull : 0ull;
+  static constexpr unsigned ONE = 0x3f80u;
+  __device__ __forceinline__ static unsigned bits(unsigned h) { return h << 16; }
+};
+template <int LIM>
+struct CoefTab<double, LIM> {
+  static constexpr unsigned long long AL =
+      LIM == LIM_CENTRAL ? 0x3fe0ull
+      : LIM == LIM_MINMOD ? 0x3fe00000ull
+      : LIM == LIM_SUPERBEE ? 0x3ff000003fe00000ull
+      : LIM == LIM_SMART ? 0x00003fc000004000ull : 0ull;
+  static constexpr unsigned long long BE =
+      LIM == LIM_MINMOD ? 0x3fe0ull
+      : LIM == LIM_SUPERBEE ? 0x00003fe000003ff0ull
+      : LIM == LIM_SMART ? 0x00003fd83ff00000ull : 0ull;
+  static constexpr unsigned long long C1 =
+      LIM == LIM_CENTRAL ? 0x3fe0ull
+      : LIM == LIM_MINMOD ? 0x3fe03ff8ull
+      : LIM == LIM_SUPERBEE ? 0x00003ff83fe04000ull
+      : LIM == LIM_SMART ? 0x00003ff44000bff0ull : 0ull;
+  static constexpr unsigned ONE = 0x3ff0u;
+  __device__ __forceinline__ static unsigned long long bits(unsigned h) {
+    return (unsigned long long)h << 48;
+  }
+};
+
 // Per-face adjoint data: the weight g and the branch coefficients.  For the
 // piecewise-linear limiters the coefficients are constants of the branch, so
 // only a small branch code is kept (fewer registers for the z faces and less
 // shared memory); van Leer keeps its computed alpha, beta, 1 - alpha + beta.
 template <class T, int LIM>
 struct FaceAdj {
+  using Tab = CoefTab<T, LIM>;
+  using U = typename FT<T>::U;
   T g;
   int code;  // bits 0-2: branch, bit 3: s > 0
   __device__ __forceinline__ bool sp() const { return (code & 8) != 0; }
-  // (alpha, beta, 1 - alpha + beta) of each branch; branch 0 = inactive
-  __device__ __forceinline__ T al() const {
+  // IEEE bit patterns of the branch's alpha, beta, 1 - alpha + beta
+  __device__ __forceinline__ U pick(unsigned long long tab, unsigned off) const {
     const int b = code & 7;
-    if (LIM == LIM_CENTRAL) return b ? T(0.5) : T(0);
-    if (LIM == LIM_MINMOD) return b == 2 ? T(0.5) : T(0);
-    if (LIM == LIM_SUPERBEE) return b == 2 ? T(0.5) : (b == 4 ? T(1) : T(0));
-    if (LIM == LIM_SMART) return b == 1 ? T(2) : (b == 3 ? T(0.125) : T(0));
-    return T(0);
+    const unsigned h = b ? (unsigned)(tab >> (16 * (b - 1))) & 0xFFFFu : off;
+    return Tab::bits(h);
   }
-  __device__ __forceinline__ T be() const {
-    const int b = code & 7;
-    if (LIM == LIM_MINMOD) return b == 1 ? T(0.5) : T(0);
-    if (LIM == LIM_SUPERBEE) return b == 1 ? T(1) : (b == 3 ? T(0.5) : T(0));
-    if (LIM == LIM_SMART) return b == 2 ? T(1) : (b == 3 ? T(0.375) : T(0));
-    return T(0);
-  }
-  __device__ __forceinline__ T c1() const {
-    const int b = code & 7;
-    if (LIM == LIM_CENTRAL) return b ? T(0.5) : T(1);
-    if (LIM == LIM_MINMOD) return b == 1 ? T(1.5) : (b == 2 ? T(0.5) : T(1));
-    if (LIM == LIM_SUPERBEE)
-      return b == 1 ? T(2) : (b == 2 ? T(0.5) : (b == 3 ? T(1.5) : (b == 4 ? T(0) : T(1))));
-    if (LIM == LIM_SMART) return b == 1 ? T(-1) : (b == 2 ? T(2) : (b == 3 ? T(1.25) : T(1)));
-    return T(1);
-  }
+  __device__ __forceinline__ U al() const { return pick(Tab::AL, 0u); }
+  __device__ __forceinline__ U be() const { return pick(Tab::BE, 0u); }
+  __device__ __forceinline__ U c1() const { return pick(Tab::C1, Tab::ONE); }
 };
 
 template <class T>
@@ -190,10 +232,30 @@ template <class T, int LIM>
 __device__ __forceinline__ T gather4(T acc, const FaceAdj<T, LIM> &fm2, const FaceAdj<T, LIM> &fm1,
                                      const FaceAdj<T, LIM> &f0, const FaceAdj<T, LIM> &fp1) {
   using F = FT<T>;
-  acc = F::fma(f0.sp() ? f0.c1() : f0.al(), f0.g, acc);     // face i   (cell i is m)
-  acc = F::fma(fm1.sp() ? fm1.al() : fm1.c1(), fm1.g, acc);  // face i-1 (cell i is m+1)
-  if (fp1.sp()) acc = F::fma(-fp1.be(), fp1.g, acc);         // face i+1, s > 0: cell i is m-1
-  if (!fm2.sp()) acc = F::fma(-fm2.be(), fm2.g, acc);        // face i-2, s < 0: cell i is m+2
+  if constexpr (LIM == LIM_VANLEER) {
+    acc = F::fma(f0.sp() ? f0.c1() : f0.al(), f0.g, acc);     // face i   (cell i is m)
+    acc = F::fma(fm1.sp() ? fm1.al() : fm1.c1(), fm1.g, acc);  // face i-1 (cell i is m+1)
+    if (fp1.sp()) acc = F::fma(-fp1.be(), fp1.g, acc);         // face i+1, s > 0: cell i is m-1
+    if (!fm2.sp()) acc = F::fma(-fm2.be(), fm2.g, acc);        // face i-2, s < 0: cell i is m+2
+  } else {
+    // branch-free, with every coefficient (its sign, and 0 for a face that
+    // does not reach cell i) formed on the integer pipe: on plain values the
+    // compiler selected and negated them with FP64 operations.  (A
+    // warp-uniform vote to skip the fma of a face no lane needs was
+    // if-converted into an fma and a select: no FP64 saved.)
+    using U = typename F::U;
+    U c[4];
+    c[0] = f0.sp() ? f0.c1() : f0.al();
+    c[1] = fm1.sp() ? fm1.al() : fm1.c1();
+    c[2] = fp1.sp() ? fp1.be() ^ F::SIGN : U(0);
+    c[3] = fm2.sp() ? U(0) : fm2.be() ^ F::SIGN;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = F::opaque(c[k]);
+    acc = F::fma(F::val(c[0]), f0.g, acc);
+    acc = F::fma(F::val(c[1]), fm1.g, acc);
+    acc = F::fma(F::val(c[2]), fp1.g, acc);
+    acc = F::fma(F::val(c[3]), fm2.g, acc);
+  }
   return acc;
 }
 
