@@ -79,9 +79,14 @@ def stage_fp64_ops_per_cell(lim, stage):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi samples of SM clock and throttle reasons, every 100 ms.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Each sample carries nvidia-smi's own timestamp, so the summary keeps the
+    samples taken inside the timed region (mark() brackets it with the wall
+    clock); entering waits for the first sample, so that the sampler is
+    running before the region starts."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -89,6 +94,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.window = None
 
     def __enter__(self):
         try:
@@ -98,6 +104,9 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 10 and self.proc.poll() is None:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -106,8 +115,13 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def mark(self, t0, t1):
+        """The timed region's wall-clock bounds (time.time())."""
+        self.window = (t0, t1)
+
     def __exit__(self, *a):
         if self.proc is not None:
+            time.sleep(0.15)  # the sample that closes the region
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -115,24 +129,33 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        import datetime
+        rows = []
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
+        inside = rows
+        if self.window is not None:
+            # a sample stands for the 100 ms before it
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 < r[0] <= t1 + 0.1]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                    "samples": 0}
+        reasons = set()
+        for r in inside:
             for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
-                                "sw_power_cap"], f[5:9]):
+                                "sw_power_cap"], r[3]):
                 if v.lower() == "active":
                     reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median([r[1] for r in inside]), "sm_max_mhz": inside[-1][2],
+                "reasons": sorted(reasons), "samples": len(inside)}
 
 
 def dist_env():
@@ -180,8 +203,7 @@ def run_ours(args):
         fl.fl_step_rk(mesh.handle, lim, dt64, 3, wl.dt, nsteps, th, u, ws_t, ws_bytes, stream)
 
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # clocks are sampled from the start of the warm-up to the end of the
-    # timed region (nvidia-smi samples every 100 ms)
+    # clocks: the nvidia-smi samples taken inside the timed region
     with ClockSampler(local) as clk:
         for _ in range(args.warmup):
             step(1)
@@ -189,13 +211,14 @@ def run_ours(args):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        w0 = time.time()
         ev0.record(stream)
         step(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
+        clk.mark(w0, time.time())
         if dist:
             dist.barrier()
-        time.sleep(0.25)
     stages = 3 * args.steps
     # units of all ranks / the slowest rank's time (replicas: no exchange)
     value, ms = whole_job_rate(F * stages, ev0.elapsed_time(ev1), device="cuda")
@@ -603,12 +626,13 @@ def run_config_deformation(args):
     e0, e1 = _events()
     torch.cuda.synchronize()
     with ClockSampler(0) as clk:
+        w0 = time.time()
         e0.record()
         fl.fl_step_rk_modulated(m.handle, "superbee", torch.float64, 1, wl.dt, wl.nsteps, th, u, g,
                                 ws, nb)
         e1.record()
         torch.cuda.synchronize()
-        time.sleep(0.25)
+        clk.mark(w0, time.time())
     ms = e0.elapsed_time(e1)
     out = th.cpu().numpy()
     F = m.n_faces
@@ -801,7 +825,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
