@@ -85,7 +85,9 @@ __device__ __forceinline__ T flip_sign(T v, bool neg) {
 // phase 1 keeps theta_f and w_f of every face, and phase 2 adds w theta_f of
 // each of the cell's faces with one fma -- the two flux products per face
 // disappear.  The block's shared memory then holds both arrays.
-template <class T, int LIM, int SEED, bool PRE, bool GEN>
+// MOD (with PRE): the stage's velocity factor g is not 1 and scales the cell
+// update; without it the factor is 1 and its multiply is skipped.
+template <class T, int LIM, int SEED, bool PRE, bool GEN, bool MOD = false>
 __global__ void __launch_bounds__(UTHREADS) k_unstruct_stage(const UParams<T> p) {
   using F = FT<T>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(UTHREADS) k_unstruct_stage(const UParams<T> p)
           acc = F::fma(flip_sign(s_w[k], (s16 & 0x8000u) != 0), s_phi[k], acc);
         }
       }
-      const T coef = F::mul(p.g, p.inv_vol[c]);
+      const T coef = MOD ? F::mul(p.g, p.inv_vol[c]) : p.inv_vol[c];
       T out = F::fma(-coef, acc, p.x[c]);
       if (SEED == 1) out = F::fma(p.b, out, F::mul(p.a, p.thn[c]));
       p.y[c] = out;
@@ -329,14 +331,14 @@ __global__ void k_scale_area_t(const T *u, const T *area, T *w, long long nf, T 
   }
 }
 
-template <class T, int SEED, bool PRE, bool GEN>
+template <class T, int SEED, bool PRE, bool GEN, bool MOD = false>
 cudaError_t launch_lim(int lim, const fl_mesh *m, const UParams<T> &p, cudaStream_t st) {
   const int nb = m->u.n_blocks;
   const size_t smem = (size_t)m->u.max_block_entries * sizeof(T) * (PRE ? 2 : 1);
   if (nb == 0) return cudaSuccess;
 #define FL_U_CASE(L)                                                                           \
   case L: {                                                                                    \
-    auto k = k_unstruct_stage<T, L, SEED, PRE, GEN>;                                           \
+    auto k = k_unstruct_stage<T, L, SEED, PRE, GEN, MOD>;                                      \
     if (smem > 48 * 1024) {                                                                    \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                            (int)smem);                                         \
@@ -361,6 +363,10 @@ template <class T, bool GEN>
 cudaError_t dispatch_seed(int lim, const fl_mesh *m, const UParams<T> &p, int seed, bool pre,
                           cudaStream_t st) {
   if constexpr (sizeof(T) == 8) {
+    if (pre && p.g != T(1)) {
+      if (seed == 0) return launch_lim<T, 0, true, GEN, true>(lim, m, p, st);
+      return launch_lim<T, 1, true, GEN, true>(lim, m, p, st);
+    }
     if (pre) {
       if (seed == 0) return launch_lim<T, 0, true, GEN>(lim, m, p, st);
       return launch_lim<T, 1, true, GEN>(lim, m, p, st);
