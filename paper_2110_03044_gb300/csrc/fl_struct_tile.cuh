@@ -67,6 +67,11 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
   constexpr int NT = TX * TY;
   constexpr int SW = TX + 4;  // s_th row pitch
   constexpr int NUB = PRE ? 2 : 1;
+  // FP32 stage updates keep each face's flux u theta_f, taken on the native
+  // FP32 min/max with its sign on the FMA pipe (native_flux): the FP32 ALU
+  // pipe, not the FP64 one, bounds them, and the integer-domain limiter made
+  // for FP64 costs it more instructions
+  constexpr bool NATIVE = sizeof(T) == 4 && !PRE && SEED != SEED_APPLY && !CODES;
   __shared__ T s_th[(TY + 4) * SW];
   __shared__ T s_dx[TY * (TX + 3)];
   __shared__ T s_dy[(TY + 3) * TX];
@@ -164,8 +169,13 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
     keep(dz_0);
     const T uz = p.u[p.uz_off + col + p.plane * wrap(z0 - 1, nz)];
     const bool sp = upwind_positive(sign_toggled(uz, p.flip));
-    const T thf = limited_face<T, LIM>(sp ? tm1 : th0, dz_m1, sp ? d_m2 : dz_0, sp);
-    fz_prev = PRE ? thf : face_flux(uz, thf);
+    // (the same value the previous z chunk computes for this face)
+    if constexpr (NATIVE) {
+      fz_prev = native_flux<LIM>(uz, sp ? tm1 : th0, dz_m1, sp ? d_m2 : dz_0, (unsigned)p.flip);
+    } else {
+      const T thf = limited_face<T, LIM>(sp ? tm1 : th0, dz_m1, sp ? d_m2 : dz_0, sp);
+      fz_prev = PRE ? thf : face_flux(uz, thf);
+    }
     wz_prev = uz;
   } else {
     th0 = p.x[col];
@@ -221,6 +231,11 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
         const bool sp = upwind_positive(sign_toggled(uf, p.flip));
         const T *dr = &s_dx[r * (TX + 3)];
         const T *tr = &s_th[(r + 2) * SW];
+        if constexpr (NATIVE) {
+          s_fx[it] = native_flux<LIM>(uf, sp ? tr[q + 1] : tr[q + 2], dr[q + 1],
+                                      sp ? dr[q] : dr[q + 2], (unsigned)p.flip);
+          continue;
+        }
         const T thf = limited_face<T, LIM>(sp ? tr[q + 1] : tr[q + 2], dr[q + 1],
                                            sp ? dr[q] : dr[q + 2], sp);
         s_fx[it] = PRE ? thf : face_flux(uf, thf);
@@ -238,6 +253,13 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
         const int r = it / TX, c = it - r * TX;  // face m = y0-1+r
         const T uf = s_uy[it];
         const bool sp = upwind_positive(sign_toggled(uf, p.flip));
+        if constexpr (NATIVE) {
+          s_fy[it] = native_flux<LIM>(
+              uf, sp ? s_th[(r + 1) * SW + c + 2] : s_th[(r + 2) * SW + c + 2],
+              s_dy[(r + 1) * TX + c], sp ? s_dy[r * TX + c] : s_dy[(r + 2) * TX + c],
+              (unsigned)p.flip);
+          continue;
+        }
         const T thf = limited_face<T, LIM>(
             sp ? s_th[(r + 1) * SW + c + 2] : s_th[(r + 2) * SW + c + 2], s_dy[(r + 1) * TX + c],
             sp ? s_dy[r * TX + c] : s_dy[(r + 2) * TX + c], sp);
@@ -255,8 +277,14 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
     T fz = T(0);
     if (need_z) {
       const bool sp = upwind_positive(sign_toggled(cur.uz, p.flip));
-      const T thf = limited_face<T, LIM>(sp ? th0 : thp1, dz_0, sp ? dz_m1 : dz_p1, sp);
-      fz = PRE ? thf : face_flux(cur.uz, thf);
+      T thf = T(0);
+      if constexpr (NATIVE) {
+        fz = native_flux<LIM>(cur.uz, sp ? th0 : thp1, dz_0, sp ? dz_m1 : dz_p1,
+                              (unsigned)p.flip);
+      } else {
+        thf = limited_face<T, LIM>(sp ? th0 : thp1, dz_0, sp ? dz_m1 : dz_p1, sp);
+        fz = PRE ? thf : face_flux(cur.uz, thf);
+      }
       if (CODES && valid)
         p.codes[p.uz_off + col + pk] =
             (unsigned char)(lin_code<T, LIM>(dz_0, sp ? dz_m1 : dz_p1) | (sp ? 8 : 0));
