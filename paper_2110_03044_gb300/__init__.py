@@ -140,6 +140,21 @@ def _ptr(x):
     raise TypeError("expected a CUDA tensor or an integer device pointer, got %r" % type(x))
 
 
+def _fptr(x, code):
+    """Device pointer of a field buffer whose elements have the call's type
+    (FL_F32 / FL_F64): a tensor of another dtype, or a CPU tensor, is
+    refused here (the library checks sizes against allocations, which a
+    wrong element type inside a larger cached block would pass)."""
+    if hasattr(x, "dtype") and hasattr(x, "is_cuda"):
+        import torch
+        want = torch.float64 if code == FL_F64 else torch.float32
+        if x.dtype != want:
+            raise TypeError("field tensor has dtype %s, the call's dtype is %s" % (x.dtype, want))
+        if not x.is_cuda:
+            raise ValueError("field tensors must be CUDA tensors")
+    return _ptr(x)
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -216,13 +231,14 @@ def fl_mesh_destroy(mesh):
 
 
 def fl_conv_limited_apply(mesh, limiter, dtype, theta_c, u_f, rhs_c, theta_f=None, stream=None):
-    _check(lib().fl_conv_limited_apply(mesh, _lim(limiter), dtype_code(dtype), _ptr(theta_c),
-                                       _ptr(u_f), _ptr(rhs_c), _ptr(theta_f), _stream(stream)))
+    c = dtype_code(dtype)
+    _check(lib().fl_conv_limited_apply(mesh, _lim(limiter), c, _fptr(theta_c, c), _fptr(u_f, c),
+                                       _fptr(rhs_c, c), _fptr(theta_f, c), _stream(stream)))
 
 
 def fl_face_selection(mesh, dtype, u_f, sel, stream=None):
-    _check(lib().fl_face_selection(mesh, dtype_code(dtype), _ptr(u_f), _ptr(sel),
-                                   _stream(stream)))
+    c = dtype_code(dtype)
+    _check(lib().fl_face_selection(mesh, c, _fptr(u_f, c), _ptr(sel), _stream(stream)))
 
 
 def fl_workspace_size(mesh, dtype, rk_order):
@@ -233,8 +249,9 @@ def fl_workspace_size(mesh, dtype, rk_order):
 
 def fl_step_rk(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, workspace,
                workspace_bytes, stream=None):
-    _check(lib().fl_step_rk(mesh, _lim(limiter), dtype_code(dtype), int(rk_order), float(dt),
-                            int(nsteps), _ptr(theta), _ptr(u_f), _ptr(workspace),
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk(mesh, _lim(limiter), c, int(rk_order), float(dt), int(nsteps),
+                            _fptr(theta, c), _fptr(u_f, c), _ptr(workspace),
                             int(workspace_bytes), _stream(stream)))
 
 
@@ -247,8 +264,9 @@ def fl_step_rk_modulated(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f,
     gg = np.ascontiguousarray(np.asarray(g, dtype=np.float64).ravel())
     if gg.size < int(nsteps) * S:
         raise ValueError("need nsteps * stages velocity factors")
-    _check(lib().fl_step_rk_modulated(mesh, _lim(limiter), dtype_code(dtype), int(rk_order),
-                                      float(dt), int(nsteps), _ptr(theta), _ptr(u_f),
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_modulated(mesh, _lim(limiter), c, int(rk_order),
+                                      float(dt), int(nsteps), _fptr(theta, c), _fptr(u_f, c),
                                       gg.ctypes.data_as(ctypes.c_void_p), _ptr(workspace),
                                       int(workspace_bytes), _stream(stream)))
 
@@ -256,16 +274,18 @@ def fl_step_rk_modulated(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f,
 def fl_step_rk_noalloc(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, stream=None):
     """fl_step_rk for callers that cannot allocate device memory: the stage
     buffers come from the library's built-in scratch area (see fl.h)."""
-    _check(lib().fl_step_rk_noalloc(mesh, _lim(limiter), dtype_code(dtype), int(rk_order),
-                                    float(dt), int(nsteps), _ptr(theta), _ptr(u_f),
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_noalloc(mesh, _lim(limiter), c, int(rk_order), float(dt),
+                                    int(nsteps), _fptr(theta, c), _fptr(u_f, c),
                                     _stream(stream)))
 
 
 def fl_conv_limited_adjoint(mesh, limiter, dtype, theta_c, u_f, lambda_rhs, lambda_theta,
                             stream=None):
-    _check(lib().fl_conv_limited_adjoint(mesh, _lim(limiter), dtype_code(dtype), _ptr(theta_c),
-                                         _ptr(u_f), _ptr(lambda_rhs), _ptr(lambda_theta),
-                                         _stream(stream)))
+    c = dtype_code(dtype)
+    _check(lib().fl_conv_limited_adjoint(mesh, _lim(limiter), c, _fptr(theta_c, c),
+                                         _fptr(u_f, c), _fptr(lambda_rhs, c),
+                                         _fptr(lambda_theta, c), _stream(stream)))
 
 
 def fl_adjoint_workspace_size(mesh, dtype, rk_order, nsteps, checkpoint_every):
@@ -277,26 +297,29 @@ def fl_adjoint_workspace_size(mesh, dtype, rk_order, nsteps, checkpoint_every):
 
 def fl_step_rk_adjoint(mesh, limiter, dtype, rk_order, dt, nsteps, checkpoint_every, theta0, u_f,
                        lambda_T, lambda_0, workspace, workspace_bytes, stream=None):
-    _check(lib().fl_step_rk_adjoint(mesh, _lim(limiter), dtype_code(dtype), int(rk_order),
-                                    float(dt), int(nsteps), int(checkpoint_every), _ptr(theta0),
-                                    _ptr(u_f), _ptr(lambda_T), _ptr(lambda_0), _ptr(workspace),
-                                    int(workspace_bytes), _stream(stream)))
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_adjoint(mesh, _lim(limiter), c, int(rk_order), float(dt),
+                                    int(nsteps), int(checkpoint_every), _fptr(theta0, c),
+                                    _fptr(u_f, c), _fptr(lambda_T, c), _fptr(lambda_0, c),
+                                    _ptr(workspace), int(workspace_bytes), _stream(stream)))
 
 
 def fl_step_rk_checkpointed(mesh, limiter, dtype, rk_order, dt, nsteps, checkpoint_every,
                             theta, u_f, workspace, workspace_bytes, stream=None):
-    _check(lib().fl_step_rk_checkpointed(mesh, _lim(limiter), dtype_code(dtype), int(rk_order),
-                                         float(dt), int(nsteps), int(checkpoint_every),
-                                         _ptr(theta), _ptr(u_f), _ptr(workspace),
-                                         int(workspace_bytes), _stream(stream)))
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_checkpointed(mesh, _lim(limiter), c, int(rk_order), float(dt),
+                                         int(nsteps), int(checkpoint_every), _fptr(theta, c),
+                                         _fptr(u_f, c), _ptr(workspace), int(workspace_bytes),
+                                         _stream(stream)))
 
 
 def fl_step_rk_adjoint_from_checkpoints(mesh, limiter, dtype, rk_order, dt, nsteps,
                                         checkpoint_every, u_f, lambda_T, lambda_0, workspace,
                                         workspace_bytes, stream=None):
+    c = dtype_code(dtype)
     _check(lib().fl_step_rk_adjoint_from_checkpoints(
-        mesh, _lim(limiter), dtype_code(dtype), int(rk_order), float(dt), int(nsteps),
-        int(checkpoint_every), _ptr(u_f), _ptr(lambda_T), _ptr(lambda_0), _ptr(workspace),
+        mesh, _lim(limiter), c, int(rk_order), float(dt), int(nsteps), int(checkpoint_every),
+        _fptr(u_f, c), _fptr(lambda_T, c), _fptr(lambda_0, c), _ptr(workspace),
         int(workspace_bytes), _stream(stream)))
 
 
@@ -318,9 +341,10 @@ def fl_batch_step_rk(batch, limiter, dtype, rk_order, dts, nsteps, thetas, u_fs,
                      workspace_bytes, stream=None):
     n = len(thetas)
     dt_arr = (ctypes.c_double * n)(*[float(d) for d in dts])
-    th_arr = (ctypes.c_void_p * n)(*[_ptr(t) for t in thetas])
-    u_arr = (ctypes.c_void_p * n)(*[_ptr(u) for u in u_fs])
-    _check(lib().fl_batch_step_rk(batch, _lim(limiter), dtype_code(dtype), int(rk_order), dt_arr,
+    c = dtype_code(dtype)
+    th_arr = (ctypes.c_void_p * n)(*[_fptr(t, c) for t in thetas])
+    u_arr = (ctypes.c_void_p * n)(*[_fptr(u, c) for u in u_fs])
+    _check(lib().fl_batch_step_rk(batch, _lim(limiter), c, int(rk_order), dt_arr,
                                   int(nsteps), th_arr, u_arr, _ptr(workspace),
                                   int(workspace_bytes), _stream(stream)))
 
@@ -366,14 +390,16 @@ def fl_alg_workspace_size(alg):
 
 def fl_alg_face_values(alg, limiter, theta, u_f, theta_f, workspace, workspace_bytes,
                        stream=None):
-    _check(lib().fl_alg_face_values(alg, _lim(limiter), _ptr(theta), _ptr(u_f), _ptr(theta_f),
+    _check(lib().fl_alg_face_values(alg, _lim(limiter), _fptr(theta, FL_F64),
+                                    _fptr(u_f, FL_F64), _fptr(theta_f, FL_F64),
                                     _ptr(workspace), int(workspace_bytes), _stream(stream)))
 
 
 def fl_alg_step_euler(alg, limiter, dt, nsteps, theta, u_f, workspace, workspace_bytes,
                       stream=None):
-    _check(lib().fl_alg_step_euler(alg, _lim(limiter), float(dt), int(nsteps), _ptr(theta),
-                                   _ptr(u_f), _ptr(workspace), int(workspace_bytes),
+    _check(lib().fl_alg_step_euler(alg, _lim(limiter), float(dt), int(nsteps),
+                                   _fptr(theta, FL_F64), _fptr(u_f, FL_F64), _ptr(workspace),
+                                   int(workspace_bytes),
                                    _stream(stream)))
 
 
@@ -383,14 +409,16 @@ def fl_reduce_workspace_size():
 
 def fl_reduce_max_abs(dtype, x, n, workspace, stream=None):
     out = ctypes.c_double()
-    _check(lib().fl_reduce_max_abs(dtype_code(dtype), _ptr(x), int(n), ctypes.byref(out),
+    c = dtype_code(dtype)
+    _check(lib().fl_reduce_max_abs(c, _fptr(x, c), int(n), ctypes.byref(out),
                                    _ptr(workspace), _stream(stream)))
     return out.value
 
 
 def fl_reduce_mass(mesh, dtype, theta, workspace, stream=None):
     out = ctypes.c_double()
-    _check(lib().fl_reduce_mass(mesh, dtype_code(dtype), _ptr(theta), ctypes.byref(out),
+    c = dtype_code(dtype)
+    _check(lib().fl_reduce_mass(mesh, c, _fptr(theta, c), ctypes.byref(out),
                                 _ptr(workspace), _stream(stream)))
     return out.value
 

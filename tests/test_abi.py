@@ -38,6 +38,19 @@ def test_host_side_argument_errors_without_gpu(fl):
     assert fl.fl_reduce_workspace_size() > 0
 
 
+def test_field_tensors_must_match_the_call_dtype(fl):
+    # the binding refuses a field tensor of another element type (a wrong
+    # type inside a larger cached block would pass the library's size check)
+    import torch
+    with pytest.raises(TypeError):
+        fl._fptr(torch.zeros(4, dtype=torch.float32), fl.FL_F64)
+    with pytest.raises(TypeError):
+        fl._fptr(torch.zeros(4, dtype=torch.float64), fl.FL_F32)
+    with pytest.raises(ValueError):
+        fl._fptr(torch.zeros(4, dtype=torch.float64), fl.FL_F64)  # a CPU tensor
+    assert fl._fptr(None, fl.FL_F64) is None and fl._fptr(1234, fl.FL_F32) == 1234
+
+
 def test_no_cpu_fallback_when_library_missing(monkeypatch, fl):
     import paper_2110_03044_gb300 as pkg
     monkeypatch.setattr(pkg, "_lib", None)
