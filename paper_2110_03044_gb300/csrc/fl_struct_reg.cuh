@@ -58,37 +58,43 @@ __device__ __forceinline__ void stage_tile_reg(const SParams<float> &p, int tile
   const int x = x0 + min(lane, last);
   const int y = min(y0 + ty, ny - 1);
   const bool need_x = p.act_x, need_y = p.act_y, need_z = p.act_z;
-  const long long plane = p.plane;
+  // Addressing: one 64-bit base pointer per stream, computed once, plus
+  // 32-bit element offsets (a plane offset plane * k is below n_cells <
+  // 2^31), so that each load costs one wide multiply-add instead of 64-bit
+  // index arithmetic (which had been about 40 % of the tile's instructions)
+  const unsigned plane = (unsigned)p.plane;
   auto wr = [](int v, int n) {
     v %= n;
     return v < 0 ? v + n : v;
   };
-  // column offsets of the cell and of its x and y neighbours
-  const long long col = (long long)x + (long long)nx * y;
-  const long long rowy = (long long)nx * y;
+  const unsigned rowy = (unsigned)nx * (unsigned)y;
+  const unsigned col = (unsigned)x + rowy;
   const int xl1 = wr(x - 1, nx), xl2 = wr(x - 2, nx), xr1 = wr(x + 1, nx), xr2 = wr(x + 2, nx);
-  const long long ym2 = (long long)nx * wr(y - 2, ny), ym1 = (long long)nx * wr(y - 1, ny);
-  const long long yp1 = (long long)nx * wr(y + 1, ny), yp2 = (long long)nx * wr(y + 2, ny);
+  const unsigned ym2 = (unsigned)nx * wr(y - 2, ny) + x, ym1 = (unsigned)nx * wr(y - 1, ny) + x;
+  const unsigned yp1 = (unsigned)nx * wr(y + 1, ny) + x, yp2 = (unsigned)nx * wr(y + 2, ny) + x;
   // which x neighbours come by shuffle (the lane holding them is inside)
   const bool sh_l1 = lane >= 1, sh_l2 = lane >= 2;
   const bool sh_r1 = lane + 1 <= last, sh_r2 = lane + 2 <= last;
-  const float *X = p.x;
+  const float *__restrict__ X = p.x;
+  const float *__restrict__ Ux = p.u + p.ux_off;
+  const float *__restrict__ Uy = p.u + p.uy_off;
+  const float *__restrict__ Uz = p.u + p.uz_off;
   const unsigned fl = (unsigned)p.flip;
   // the plane's loads, issued one plane ahead
   struct Plane {
     float ym2, ym1, yp1, yp2, ux, uy, uym, uz, thn;
   };
-  auto load_plane = [&](long long pk, Plane &q) {
+  auto load_plane = [&](unsigned pk, Plane &q) {
     if (need_y) {
-      q.ym2 = X[ym2 + x + pk];
-      q.ym1 = X[ym1 + x + pk];
-      q.yp1 = X[yp1 + x + pk];
-      q.yp2 = X[yp2 + x + pk];
-      q.uy = p.u[p.uy_off + col + pk];
-      q.uym = p.u[p.uy_off + ym1 + x + pk];
+      q.ym2 = X[ym2 + pk];
+      q.ym1 = X[ym1 + pk];
+      q.yp1 = X[yp1 + pk];
+      q.yp2 = X[yp2 + pk];
+      q.uy = Uy[col + pk];
+      q.uym = Uy[ym1 + pk];
     }
-    if (need_x) q.ux = p.u[p.ux_off + col + pk];
-    if (need_z) q.uz = p.u[p.uz_off + col + pk];
+    if (need_x) q.ux = Ux[col + pk];
+    if (need_z) q.uz = Uz[col + pk];
     if (SEED == SEED_COMBINE) q.thn = p.thn[col + pk];
   };
   Plane cur{}, nxt{};
@@ -101,7 +107,7 @@ __device__ __forceinline__ void stage_tile_reg(const SParams<float> &p, int tile
     thp1 = X[col + plane * wr(z0 + 1, nz)];
     thp2 = X[col + plane * wr(z0 + 2, nz)];
     pf = X[col + plane * wr(z0 + 3, nz)];
-    const float um = p.u[p.uz_off + col + plane * wr(z0 - 1, nz)];
+    const float um = Uz[col + plane * wr(z0 - 1, nz)];
     const float d_m2 = __fsub_rn(tm1, tm2);
     dzm = __fsub_rn(th0, tm1);
     dz0 = __fsub_rn(thp1, th0);
@@ -109,7 +115,7 @@ __device__ __forceinline__ void stage_tile_reg(const SParams<float> &p, int tile
   }
   load_plane(plane * z0, cur);
   for (int k = z0; k < z1; ++k) {
-    const long long pk = plane * k;
+    const unsigned pk = plane * k;
     if (k + 1 < z1) load_plane(pk + plane, nxt);
     float pf_next = 0.f;
     if (need_z && k + 1 < z1) {
@@ -138,7 +144,7 @@ __device__ __forceinline__ void stage_tile_reg(const SParams<float> &p, int tile
       // -x face: the left lane's +x face, lane 0 its own
       float fm = __shfl_up_sync(0xffffffffu, fp, 1);
       if (lane == 0)
-        fm = reg_flux<LIM>(p.u[p.ux_off + rowy + xl1 + pk], tl1, th0, dm1, dm2, d0, fl);
+        fm = reg_flux<LIM>(Ux[rowy + xl1 + pk], tl1, th0, dm1, dm2, d0, fl);
       acc = __fmaf_rn(-p.cx, fp, acc);
       acc = __fmaf_rn(p.cx, fm, acc);
     }

@@ -100,42 +100,51 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
   __syncthreads();
 
   const bool valid = (x0 + tx < nx) && (y0 + ty < ny);
-  const long long col = (long long)s_wx[tx + 2] + (long long)nx * s_wy[ty + 2];
+  // Addressing: one 64-bit base pointer per stream and 32-bit element
+  // offsets (every cell or plane offset is below n_cells < 2^31), so that a
+  // load costs one wide multiply-add rather than 64-bit index arithmetic
+  const unsigned plane = (unsigned)p.plane;
+  const unsigned col = (unsigned)s_wx[tx + 2] + (unsigned)nx * (unsigned)s_wy[ty + 2];
+  const T *__restrict__ Ux = p.u + p.ux_off;
+  const T *__restrict__ Uy = p.u + p.uy_off;
+  const T *__restrict__ Uz = p.u + p.uz_off;
   const bool need_x = p.act_x, need_y = p.act_y, need_z = p.act_z;
 
   // halo cells of s_th: 2 columns left/right of every row, 2 rows above/below
   constexpr int NH = 4 * (TX + TY);
   static_assert(NH <= NT, "halo items exceed threads");
   int h_slot = -1;
-  long long h_off = 0;
+  unsigned h_off = 0;
   if (tid < 4 * TY) {  // x halo
     const int r = tid >> 2, k4 = tid & 3;
     const int c = (k4 < 2) ? k4 : (TX + k4);  // 0,1,TX+2,TX+3
     h_slot = (r + 2) * SW + c;
-    h_off = (long long)s_wx[c] + (long long)nx * s_wy[r + 2];
+    h_off = (unsigned)s_wx[c] + (unsigned)nx * (unsigned)s_wy[r + 2];
   } else if (tid < NH) {  // y halo
     const int t = tid - 4 * TY;
     const int k4 = t / TX, c = t % TX;
     const int r = (k4 < 2) ? k4 : (TY + k4);  // 0,1,TY+2,TY+3
     h_slot = r * SW + c + 2;
-    h_off = (long long)s_wx[c + 2] + (long long)nx * s_wy[r];
+    h_off = (unsigned)s_wx[c + 2] + (unsigned)nx * (unsigned)s_wy[r];
   }
   // halo faces: the -x face of every row (x0-1) and the -y face of every
   // column (y0-1); each thread owns the +x, +y and +z faces of its cell
   int hu_slot = -1;
-  long long hu_off = 0;
+  unsigned hu_off = 0;
+  const T *hu_base = Ux;
   bool hu_is_x = false;
   if (tid < TY) {
     if (need_x) {
       hu_slot = tid * (TX + 1);
-      hu_off = p.ux_off + s_wx[1] + (long long)nx * s_wy[tid + 2];
+      hu_off = (unsigned)s_wx[1] + (unsigned)nx * (unsigned)s_wy[tid + 2];
       hu_is_x = true;
     }
   } else if (tid < TY + TX) {
     if (need_y) {
       const int c = tid - TY;
       hu_slot = c;
-      hu_off = p.uy_off + s_wx[c + 2] + (long long)nx * s_wy[1];
+      hu_base = Uy;
+      hu_off = (unsigned)s_wx[c + 2] + (unsigned)nx * (unsigned)s_wy[1];
     }
   }
 
@@ -144,30 +153,30 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
     T ux, uy, uz, thn, h, hu;
   };
   auto load_plane = [&](int k, Plane &q) {
-    const long long pk = p.plane * k;
-    if (need_x) q.ux = p.u[p.ux_off + col + pk];
-    if (need_y) q.uy = p.u[p.uy_off + col + pk];
-    if (need_z) q.uz = p.u[p.uz_off + col + pk];
+    const unsigned pk = plane * (unsigned)k;
+    if (need_x) q.ux = Ux[col + pk];
+    if (need_y) q.uy = Uy[col + pk];
+    if (need_z) q.uz = Uz[col + pk];
     if (SEED == SEED_COMBINE) q.thn = p.thn[col + pk];
     if (h_slot >= 0) q.h = p.x[h_off + pk];
-    if (hu_slot >= 0) q.hu = p.u[hu_off + pk];
+    if (hu_slot >= 0) q.hu = hu_base[hu_off + pk];
   };
   Plane cur{}, nxt{};
 
   // ---- z prologue: columns k-2 .. k+1 around z0, and the flux of face z0-1/2
   T th0, thp1, thp2 = T(0), dz_m1 = T(0), dz_0 = T(0), fz_prev = T(0), wz_prev = T(0);
   if (need_z) {
-    const T tm2 = p.x[col + p.plane * wrap(z0 - 2, nz)];
-    const T tm1 = p.x[col + p.plane * wrap(z0 - 1, nz)];
-    th0 = p.x[col + p.plane * z0];
-    thp1 = p.x[col + p.plane * wrap(z0 + 1, nz)];
-    thp2 = p.x[col + p.plane * wrap(z0 + 2, nz)];
+    const T tm2 = p.x[col + plane * (unsigned)wrap(z0 - 2, nz)];
+    const T tm1 = p.x[col + plane * (unsigned)wrap(z0 - 1, nz)];
+    th0 = p.x[col + plane * (unsigned)z0];
+    thp1 = p.x[col + plane * (unsigned)wrap(z0 + 1, nz)];
+    thp2 = p.x[col + plane * (unsigned)wrap(z0 + 2, nz)];
     const T d_m2 = F::sub(tm1, tm2);
     dz_m1 = F::sub(th0, tm1);
     dz_0 = F::sub(thp1, th0);
     keep(dz_m1);
     keep(dz_0);
-    const T uz = p.u[p.uz_off + col + p.plane * wrap(z0 - 1, nz)];
+    const T uz = Uz[col + plane * (unsigned)wrap(z0 - 1, nz)];
     const bool sp = upwind_positive(sign_toggled(uz, p.flip));
     // (the same value the previous z chunk computes for this face)
     if constexpr (NATIVE) {
@@ -184,7 +193,7 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
   load_plane(z0, cur);
 
   for (int k = z0; k < z1; ++k) {
-    const long long pk = p.plane * k;
+    const unsigned pk = plane * (unsigned)k;
     T *s_ux = s_uxb[PRE ? (k & 1) : 0];
     T *s_uy = s_uyb[PRE ? (k & 1) : 0];
     // -------------------------------------------- fill plane k
@@ -200,7 +209,7 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
     T tp3 = T(0);
     if (k + 1 < z1) {
       load_plane(k + 1, nxt);
-      if (need_z) tp3 = p.x[col + p.plane * wrap(k + 3, nz)];
+      if (need_z) tp3 = p.x[col + plane * (unsigned)wrap(k + 3, nz)];
     }
     __syncthreads();
     // ------------------------------------------- phase A: differences
@@ -240,11 +249,11 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
                                            sp ? dr[q] : dr[q + 2], sp);
         s_fx[it] = PRE ? thf : face_flux(uf, thf);
         if (CODES && q >= 1 && x0 + q - 1 < nx && y0 + r < ny)
-          p.codes[p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 2] + pk] =
+          p.codes[p.ux_off + (s_wx[q + 1] + (unsigned)nx * (unsigned)s_wy[r + 2] + pk)] =
               (unsigned char)(lin_code<T, LIM>(dr[q + 1], sp ? dr[q] : dr[q + 2]) | (sp ? 8 : 0));
         if (SEED == SEED_APPLY && p.thf != nullptr) {
           if (q >= 1 && x0 + q - 1 < nx && y0 + r < ny)
-            p.thf[p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 2] + pk] = thf;
+            p.thf[p.ux_off + (s_wx[q + 1] + (unsigned)nx * (unsigned)s_wy[r + 2] + pk)] = thf;
         }
       }
     }
@@ -265,12 +274,12 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
             sp ? s_dy[r * TX + c] : s_dy[(r + 2) * TX + c], sp);
         s_fy[it] = PRE ? thf : face_flux(uf, thf);
         if (CODES && r >= 1 && x0 + c < nx && y0 + r - 1 < ny)
-          p.codes[p.uy_off + s_wx[c + 2] + (long long)nx * s_wy[r + 1] + pk] = (unsigned char)(
+          p.codes[p.uy_off + (s_wx[c + 2] + (unsigned)nx * (unsigned)s_wy[r + 1] + pk)] = (unsigned char)(
               lin_code<T, LIM>(s_dy[(r + 1) * TX + c], sp ? s_dy[r * TX + c] : s_dy[(r + 2) * TX + c]) |
               (sp ? 8 : 0));
         if (SEED == SEED_APPLY && p.thf != nullptr) {
           if (r >= 1 && x0 + c < nx && y0 + r - 1 < ny)
-            p.thf[p.uy_off + s_wx[c + 2] + (long long)nx * s_wy[r + 1] + pk] = thf;
+            p.thf[p.uy_off + (s_wx[c + 2] + (unsigned)nx * (unsigned)s_wy[r + 1] + pk)] = thf;
         }
       }
     }
@@ -286,9 +295,9 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
         fz = PRE ? thf : face_flux(cur.uz, thf);
       }
       if (CODES && valid)
-        p.codes[p.uz_off + col + pk] =
+        p.codes[p.uz_off + (col + pk)] =
             (unsigned char)(lin_code<T, LIM>(dz_0, sp ? dz_m1 : dz_p1) | (sp ? 8 : 0));
-      if (SEED == SEED_APPLY && p.thf != nullptr && valid) p.thf[p.uz_off + col + pk] = thf;
+      if (SEED == SEED_APPLY && p.thf != nullptr && valid) p.thf[p.uz_off + (col + pk)] = thf;
     }
     __syncthreads();
     // ------------------------------------------------ phase C: update
@@ -341,7 +350,7 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
       thp1 = thp2;
       thp2 = tp3;
     } else if (k + 1 < z1) {
-      th0 = p.x[col + p.plane * (k + 1)];
+      th0 = p.x[col + plane * (unsigned)(k + 1)];
     }
   }
 }
