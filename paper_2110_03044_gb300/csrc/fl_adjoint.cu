@@ -537,12 +537,21 @@ __global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParam
   if (tid < TY + 6) s_wy[tid] = wrapi(y0 - 3 + tid, ny);
   __syncthreads();
   const bool valid = (x0 + tx < nx) && (y0 + ty < ny);
-  const long long col = (long long)s_wx[tx + 3] + (long long)nx * s_wy[ty + 3];
+  // addressing: 64-bit base pointers per stream, 32-bit offsets (cell and
+  // plane offsets are below n_cells < 2^31): one wide multiply-add a load
+  const unsigned plane = (unsigned)p.plane;
+  const unsigned col = (unsigned)s_wx[tx + 3] + (unsigned)nx * (unsigned)s_wy[ty + 3];
+  const T *__restrict__ Ux = p.u + p.ux_off;
+  const T *__restrict__ Uy = p.u + p.uy_off;
+  const T *__restrict__ Uz = p.u + p.uz_off;
+  const unsigned char *__restrict__ Cx = p.codes + p.ux_off;
+  const unsigned char *__restrict__ Cy = p.codes + p.uy_off;
+  const unsigned char *__restrict__ Cz = p.codes + p.uz_off;
   const bool need_x = p.act_x, need_y = p.act_y, need_z = p.act_z;
 
   // mu halo (2 wide)
   int mu_slot = -1;
-  long long mu_off = 0;
+  unsigned mu_off = 0;
   {
     constexpr int NMX = 4 * TY, NMT = NMX + 4 * TX;
     static_assert(NMT <= NT, "mu halo exceeds threads");
@@ -550,19 +559,19 @@ __global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParam
       const int r = tid >> 2, k4 = tid & 3;
       const int c = (k4 < 2) ? k4 : (TX + k4);
       mu_slot = (r + 2) * SWM + c;
-      mu_off = (long long)s_wx[c + 1] + (long long)nx * s_wy[r + 3];
+      mu_off = (unsigned)s_wx[c + 1] + (unsigned)nx * (unsigned)s_wy[r + 3];
     } else if (tid < NMT) {
       const int t = tid - NMX;
       const int k4 = t / TX, c = t % TX;
       const int r = (k4 < 2) ? k4 : (TY + k4);
       mu_slot = r * SWM + c + 2;
-      mu_off = (long long)s_wx[c + 3] + (long long)nx * s_wy[r + 1];
+      mu_off = (unsigned)s_wx[c + 3] + (unsigned)nx * (unsigned)s_wy[r + 1];
     }
   }
   // faces of the plane: every thread its own +x and +y face, threads
   // tid < 3 (TX + TY) one halo face each (u by cp.async, codes by registers)
   int hu_slot = -1;
-  long long hu_off = 0;
+  unsigned hu_off = 0;
   bool hu_x = false;
   {
     constexpr int NUX = 3 * TY, NUT = NUX + 3 * TX;
@@ -572,7 +581,7 @@ __global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParam
         const int r = tid / 3, k3 = tid % 3;
         const int q = (k3 < 2) ? k3 : TX + 2;
         hu_slot = r * NXF + q;
-        hu_off = p.ux_off + s_wx[q + 1] + (long long)nx * s_wy[r + 3];
+        hu_off = (unsigned)s_wx[q + 1] + (unsigned)nx * (unsigned)s_wy[r + 3];
         hu_x = true;
       }
     } else if (tid < NUT) {
@@ -581,37 +590,38 @@ __global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParam
         const int k3 = t / TX, c = t % TX;
         const int r = (k3 < 2) ? k3 : TY + 2;
         hu_slot = r * TX + c;
-        hu_off = p.uy_off + s_wx[c + 3] + (long long)nx * s_wy[r + 1];
+        hu_off = (unsigned)s_wx[c + 3] + (unsigned)nx * (unsigned)s_wy[r + 1];
       }
     }
   }
   unsigned cx_n = 0, cy_n = 0, ch_n = 0;
-  auto load_face = [&](long long pk, int buf) {
+  auto load_face = [&](unsigned pk, int buf) {
     if (need_x) {
-      cp_async1(&s_uxb[buf][ty * NXF + tx + 2], p.u + p.ux_off + col + pk);
-      cx_n = p.codes[p.ux_off + col + pk];
+      cp_async1(&s_uxb[buf][ty * NXF + tx + 2], Ux + (col + pk));
+      cx_n = Cx[col + pk];
     }
     if (need_y) {
-      cp_async1(&s_uyb[buf][(ty + 2) * TX + tx], p.u + p.uy_off + col + pk);
-      cy_n = p.codes[p.uy_off + col + pk];
+      cp_async1(&s_uyb[buf][(ty + 2) * TX + tx], Uy + (col + pk));
+      cy_n = Cy[col + pk];
     }
     if (hu_slot >= 0) {
-      cp_async1(hu_x ? &s_uxb[buf][hu_slot] : &s_uyb[buf][hu_slot], p.u + hu_off + pk);
-      ch_n = p.codes[hu_off + pk];
+      cp_async1(hu_x ? &s_uxb[buf][hu_slot] : &s_uyb[buf][hu_slot],
+                (hu_x ? Ux : Uy) + (hu_off + pk));
+      ch_n = (hu_x ? Cx : Cy)[hu_off + pk];
     }
     cp_async_commit();
   };
-  load_face(p.plane * z0, z0 & 1);
+  load_face(plane * (unsigned)z0, z0 & 1);
 
   // ---- z prologue: faces z0-2, z0-1, z0 from the mu column and the codes
   T mu_k, mu_k1 = T(0);
   FaceAdj<T, LIM> zf_m2{}, zf_m1{}, zf_0{};
-  auto MU = [&](int k) { return p.mu[col + p.plane * wrapi(k, nz)]; };
+  auto MU = [&](int k) { return p.mu[col + plane * (unsigned)wrapi(k, nz)]; };
   auto ZF = [&](int k, T m0, T m1) {
-    const long long i = p.uz_off + col + p.plane * wrapi(k, nz);
+    const unsigned i = col + plane * (unsigned)wrapi(k, nz);
     FaceAdj<T, LIM> f;
-    f.g = F::mul(p.u[i], F::sub(m1, m0));
-    f.code = p.codes[i];
+    f.g = F::mul(Uz[i], F::sub(m1, m0));
+    f.code = Cz[i];
     return f;
   };
   if (need_z) {
@@ -626,7 +636,7 @@ __global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParam
   }
 
   for (int k = z0; k < z1; ++k) {
-    const long long pk = p.plane * k;
+    const unsigned pk = plane * (unsigned)k;
     T mu_k2 = T(0);
     if (need_z) mu_k2 = MU(k + 2);
     const T hv_m = (mu_slot >= 0) ? p.mu[mu_off + pk] : T(0);
@@ -644,7 +654,7 @@ __global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParam
       else s_cy[hu_slot] = (unsigned char)ch_n;
     }
     cp_async_wait_all();
-    if (k + 1 < z1) load_face(pk + p.plane, (k + 1) & 1);
+    if (k + 1 < z1) load_face(pk + plane, (k + 1) & 1);
     const T *s_ux = s_uxb[k & 1];
     const T *s_uy = s_uyb[k & 1];
     FaceAdj<T, LIM> zf_1{};
@@ -700,7 +710,7 @@ __global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParam
       mu_k = mu_k1;
       mu_k1 = mu_k2;
     } else if (k + 1 < z1) {
-      mu_k = p.mu[col + p.plane * (k + 1)];
+      mu_k = p.mu[col + plane * (unsigned)(k + 1)];
     }
   }
 }
