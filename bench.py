@@ -43,7 +43,7 @@ FP64_OPS_PEAK = 2 * 152 * 2.070e9
 # FP64 superbee, RK stages 2-3 (65 % of the step's kernel time); FP32
 # superbee TMA kernel, RK stage 1.  Keyed by (dtype, limiter, n).
 NCU_TRAFFIC = {
-    ("f64", "superbee", 256): (808.8e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
+    ("f64", "superbee", 256): (812.2e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
                                "algorithmic 805.3e6 (48 B x 16.8M cells)"),
     ("f32", "superbee", 256): (330.9e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
                                "algorithmic 335.5e6 (20 B x 16.8M cells)"),
