@@ -239,11 +239,12 @@ __global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
   const int last_lane = w / VX - 1;
   const bool valid = lane <= last_lane && ty < h;
   // z window of the thread's four cells by plain 128-bit loads
-  const long long plane = (long long)nx * ny;
+  // 32-bit element offsets from the field base pointers (below n_cells < 2^31)
+  const unsigned plane = (unsigned)nx * (unsigned)ny;
   const int cxv = min(x0 + VX * lane, nx - VX), cyv = min(y0 + ty, ny - 1);
-  const long long col = (long long)cxv + (long long)nx * cyv;
+  const unsigned col = (unsigned)cxv + (unsigned)nx * (unsigned)cyv;
   auto X4 = [&](int k) {  // k in [0, nz)
-    return *reinterpret_cast<const float4 *>(p.x + col + plane * k);
+    return *reinterpret_cast<const float4 *>(p.x + (col + plane * (unsigned)k));
   };
   float th0[4], thp1[4] = {0, 0, 0, 0}, thp2[4] = {0, 0, 0, 0}, dzm[4] = {0, 0, 0, 0},
         dz0[4] = {0, 0, 0, 0}, fzp[4] = {0, 0, 0, 0};
@@ -259,8 +260,8 @@ __global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
     const float4 m2 = X4(wrapv(z0 - 2, nz)), m1 = X4(wrapv(z0 - 1, nz));
     const float4 p1 = X4(wrapv(z0 + 1, nz)), p2 = X4(wrapv(z0 + 2, nz));
     pf = X4(wrapv(z0 + 3, nz));
-    const float4 um = *reinterpret_cast<const float4 *>(p.u + p.uz_off + col +
-                                                         plane * wrapv(z0 - 1, nz));
+    const float4 um = *reinterpret_cast<const float4 *>(
+        p.u + p.uz_off + (col + plane * (unsigned)wrapv(z0 - 1, nz)));
     const float tm2[4] = {m2.x, m2.y, m2.z, m2.w}, tm1[4] = {m1.x, m1.y, m1.z, m1.w};
     const float tp1[4] = {p1.x, p1.y, p1.z, p1.w}, tp2[4] = {p2.x, p2.y, p2.z, p2.w};
     const float uzm[4] = {um.x, um.y, um.z, um.w};
@@ -392,7 +393,8 @@ __global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[slot]);
     if (valid)
-      *reinterpret_cast<float4 *>(p.y + col + plane * k) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      *reinterpret_cast<float4 *>(p.y + (col + plane * (unsigned)k)) =
+          make_float4(acc[0], acc[1], acc[2], acc[3]);
     // ------------------------------------------------------ rotate z
     if (az) {
       const float pv[4] = {pf.x, pf.y, pf.z, pf.w};
