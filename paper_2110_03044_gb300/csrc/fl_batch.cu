@@ -58,8 +58,8 @@ constexpr int BTY = 8;
 constexpr int MAXSTAGES = 3;
 
 // (FP32 boxes run the shared-memory tile here: in this persistent kernel the
-// register tile of fl_struct_reg.cuh measured slower, 1.98 against 1.77 ms
-// for the 64-box SSP-RK3 step, at its lower occupancy)
+// register tile of fl_struct_reg.cuh measured no faster, 1.61 against 1.60 ms
+// for the 64-box SSP-RK3 step, both with 32-bit addressing)
 template <class T, int LIM, int SEED, bool PRE>
 __global__ void __launch_bounds__(TX *BTY, 4)
     k_batch_stage(const SParams<T> *__restrict__ params, const int2 *__restrict__ tiles,
