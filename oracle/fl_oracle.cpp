@@ -17,10 +17,11 @@
 //   * eq. (Delta_Upwind): upstream difference accumulated over the other faces
 //     j of the upstream cell C, each projected on n_f:
 //       d_U = s * sum_{j in dC, j != f} (n_f . n_j) (theta_{j,c1} - theta_{j,c0})
-//     The leading factor s is the sign correction described in the design
-//     notes (the printed forms agree with Sweby's r for one flow direction
-//     only); on hexahedral meshes this is exactly theta_C - theta_U
-//     (Algorithm 3 written without the distance weights, all meshes uniform).
+//     The leading factor s is a sign correction: each printed form of d_U
+//     agrees with Sweby's r for one flow direction only, and the
+//     orientation-invariant sum times s = sign(u_f) agrees for both.  On
+//     hexahedral meshes this is exactly theta_C - theta_U (Algorithm 3
+//     written without the distance weights, all meshes uniform).
 //   * Algorithm 4: theta^{n+1} = theta^n + dt M U(u_f) theta_f, with M read as
 //     minus the divergence: R_c = -(1/V_c) sum_f sigma_cf u_f A_f theta_f,
 //     sigma = +1 when c is c0 of f and -1 when c is c1.
@@ -35,6 +36,16 @@
 //
 // Conventions: face f has cells (c0, c1) and unit normal n_f pointing c0->c1;
 // u_f is the normal velocity along n_f; A_f face area; V_c cell volume.
+//
+// Pins (tests/test_oracle_*.py): every function here is checked against
+// something other than itself -- the paper's printed 2D example, tabulated
+// closed-form limiter values, dense matrix algebra of Algorithm 1 on small
+// meshes, exact upwind shifts and Fourier amplification factors,
+// conservation, the 3D -> 1D collapse, central differences for the
+// tangent-linear model, and the adjoint dot-product identity -- and planted
+// mistakes in a copy of this file must fail those pins.  Parity unpinned:
+// boundedness of SMART (outside Sweby's region) and of 3D unsplit steps,
+// which are reported, not asserted.
 
 #include <cmath>
 #include <cstdint>
