@@ -5,7 +5,7 @@
 // of face f, with upwind cell C, is the n_f-projected sum over the other faces
 // j of C of their differences, orientation-corrected by the velocity sign:
 //   d_U = s sum_{j in dC, j != f} (n_f . n_j) (theta_{j,c1} - theta_{j,c0}).
-// On the supported meshes every face j of C other than the one opposite f has
+// On hexahedral meshes every face j of C other than the one opposite f has
 // n_f . n_j = 0, and the opposite one has n_f . n_j = +-1, so the sum has a
 // single term: d_U = sigma (theta_C - theta_U) with U the cell across the
 // opposite face and sigma = +-1 fixed by the mesh.  mesh creation resolves U
