@@ -18,6 +18,11 @@
 // Stage adjoint (RK stage y = a thn + b (x + dt R(x))):
 //   out = e1 v1 + e2 v2 + b mu + b dt R'(x)^T mu      (v1, v2 pointwise)
 // fl_conv_limited_adjoint is the bare out = R'(x)^T mu.
+//
+// In the reverse sweep of a piecewise-linear limiter the recomputed forward
+// stages store each face's branch code, and k_struct_adjoint_codes reads the
+// codes instead of theta (no theta tile, no differences).  The reverse sweep
+// of a face-based mesh runs the gather kernel of fl_unstructured.cu.
 #include <cuda_runtime.h>
 
 #include <cmath>
