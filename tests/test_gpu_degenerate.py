@@ -1,4 +1,5 @@
-"""Degenerate meshes of the method: meshes without faces.
+"""Degenerate cases of the method: meshes without faces, and zero or negative
+time steps.
 
 A 1 x 1 x 1 structured box and a face-based mesh of isolated cells have no
 faces, so R(theta) = 0 (eq. (M): an empty sum), every step leaves theta
@@ -59,4 +60,51 @@ def test_face_based_mesh_without_faces(fl, dtype, rk, renumber):
     assert _rel(g.cpu().double().numpy()[cp], ref) <= TOL[dtype]
     R = fl.conv_limited_apply(m, "superbee", g, u)
     assert R.cpu().tolist() == [0.0] * n
+    m.close()
+
+
+# dt = 0 and dt < 0: the step is theta + dt R(theta) with the upwind side
+# still taken from u_f (the FP64 path pre-scales w = dt (A/V) u_f only when
+# dt > 0, since a negative factor would flip every upwind test)
+@pytest.mark.parametrize("dt_scale", [0.0, -1.0])
+@pytest.mark.parametrize("rk", [1, 3])
+@pytest.mark.parametrize("case", ["f64 tile", "f32 tma", "f32 register tile", "f64 face-based"])
+def test_zero_and_negative_time_step(fl, case, rk, dt_scale):
+    dtype = torch.float64 if case.startswith("f64") else torch.float32
+    shape = (128, 8, 5) if case == "f32 tma" else (37, 21, 13)
+    h = (0.7 / shape[0], 0.9 / shape[1], 1.1 / shape[2])
+    mesh = W.structured_mesh(*shape, *h)
+    rng = np.random.default_rng(17)
+    th = rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3)
+    u = 0.3 * W.mixed_sign_velocity(mesh.n_faces, 18)
+    if dtype == torch.float32:
+        th = th.astype(np.float32).astype(np.float64)
+        u = u.astype(np.float32).astype(np.float64)
+    dt = dt_scale * 0.1 * min(h) / np.max(np.abs(u))
+    ref = oracle.step(mesh, "superbee", rk, dt, 1, u, th)
+    if case == "f64 face-based":
+        pm, cp, fp, flip = W.permuted_mesh(mesh, seed=3)
+        m = fl.Mesh.from_faces(pm.n_cells, pm.face_cells, pm.normals, pm.areas, pm.volumes,
+                               renumber=True)
+        icp, ifp, _ = m.permutation()
+        # user order of the permuted mesh, then the library's internal order
+        th_u = np.empty_like(th)
+        th_u[cp] = th
+        u_u = np.empty_like(u)
+        u_u[fp] = np.where(flip, -u, u)
+        x = np.empty_like(th_u)
+        x[icp] = th_u
+        uu = np.empty_like(u_u)
+        uu[ifp] = u_u
+        g = torch.tensor(x, dtype=dtype, device="cuda")
+        fl.step_rk(m, "superbee", g, torch.tensor(uu, dtype=dtype, device="cuda"), dt, 1,
+                   rk_order=rk)
+        got = g.cpu().double().numpy()[icp][cp]
+    else:
+        m = fl.Mesh.structured(*shape, *h)
+        g = torch.tensor(th, dtype=dtype, device="cuda")
+        fl.step_rk(m, "superbee", g, torch.tensor(u, dtype=dtype, device="cuda"), dt, 1,
+                   rk_order=rk)
+        got = g.cpu().double().numpy()
+    assert _rel(got, ref) <= TOL[dtype]
     m.close()
