@@ -1013,7 +1013,10 @@ cudaError_t sweep_reverse(const Sweep &w, const void *lambda_T, void *lambda_0) 
         if (e != cudaSuccess) break;
         // stage 1: lam = 1/3 lam + 3/4 la + (lbb + dt R'(x0)^T lbb)
         a.x = w.slot(3 * n); a.mu = lbb; a.out = lam; a.b = 1.0; a.codes = cd(3 * n);
-        a.v1 = lam; a.e1 = 1.0 / 3.0; a.v2 = la; a.e2 = 0.75;
+        // e1: the forward stage 3's weight of thn, as the forward kernels used it
+        a.v1 = lam; a.v2 = la; a.e2 = 0.75;
+        a.e1 = w.dt == FL_F64 ? blend_a<double>(1.0 / 3.0, 2.0 / 3.0)
+                              : (double)blend_a<float>(1.0 / 3.0, 2.0 / 3.0);
         e = adjoint_any(w.m, w.lim, w.dt, a, w.st);
       }
     }

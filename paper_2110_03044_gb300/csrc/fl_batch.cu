@@ -162,7 +162,7 @@ SParams<T> box_params(const fl_mesh *m, int zc, const void *x, const void *thn, 
   p.cx = (T)(sc / m->hx);
   p.cy = (T)(sc / m->hy);
   p.cz = (T)(sc / m->hz);
-  p.a = (T)a;
+  p.a = blend_a<T>(a, bcoef);
   p.b = (T)bcoef;
   p.g = (T)1;
   p.flip = 0;

@@ -46,6 +46,17 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 inline size_t dsize(fl_dtype t) { return t == FL_F64 ? 8 : 4; }
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// The weight a of an RK blend y = a thn + b (x + dt R(x)) as the kernels
+// use it in precision T.  When the weights sum to 1, a = 1 - b is computed
+// in T (exact: b lies in [1/2, 1] or a is 0.75 / 0), so that a + b == 1
+// exactly and the blend moves no mass.  With a = RN(1/3) and b = RN(2/3),
+// SSP-RK3's third stage would scale the total by 1 - 2^-54 in FP64 and by
+// 1 + 2^-25 in FP32 every step.
+template <class T>
+inline T blend_a(double a, double b) {
+  return (a + b == 1.0) ? T(1) - (T)b : (T)a;
+}
+
 // ----------------------------------------------------------- unstructured
 // Device data of a face-based mesh in the library's internal numbering.
 // Cells are grouped in blocks (compact patches of at most UBLOCK cells);

@@ -523,7 +523,7 @@ cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cuda
   p.cx = (float)(sc / m->hx);
   p.cy = (float)(sc / m->hy);
   p.cz = (float)(sc / m->hz);
-  p.a = (float)s.a;
+  p.a = blend_a<float>(s.a, s.b);
   p.b = (float)s.b;
   p.tiles_x = (nx + TX - 1) / TX;
   p.tiles_y = (ny + TY - 1) / TY;

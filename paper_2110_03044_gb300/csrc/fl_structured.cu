@@ -142,7 +142,7 @@ cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStrea
   p.cx = (T)(sc / m->hx);
   p.cy = (T)(sc / m->hy);
   p.cz = (T)(sc / m->hz);
-  p.a = (T)s.a;
+  p.a = blend_a<T>(s.a, s.b);
   p.b = (T)s.b;
   p.tiles_x = (m->nx + TX - 1) / TX;
   p.tiles_y = (m->ny + STY - 1) / STY;
@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(1024) k_line_resident(T *theta, const T *u, in
           acc = F::fma(-c, s_f[i], acc);
           acc = F::fma(c, s_f[im], acc);
         } else {
-          const T a = (st == 1) ? T(0.75) : T(1.0 / 3.0);
+          // (stage 3: 1 - RN(2/3), so that the two weights sum to exactly 1)
+          const T a = (st == 1) ? T(0.75) : T(1) - T(2.0 / 3.0);
           const T b = (st == 1) ? T(0.25) : T(2.0 / 3.0);
           const T cb = (st == 1) ? F::mul(T(0.25), c) : F::mul(T(2.0 / 3.0), c);
           acc = F::fma(a, s_n[i], F::mul(b, s_x[i]));

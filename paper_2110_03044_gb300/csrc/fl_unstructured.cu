@@ -400,7 +400,7 @@ cudaError_t run_ustage(const fl_mesh *m, int lim, const StageArgs &s, cudaStream
     p.area = reinterpret_cast<const T *>(m->u.area_f);
     p.inv_vol = reinterpret_cast<const T *>(m->u.inv_vol_f);
   }
-  p.a = (T)s.a;
+  p.a = blend_a<T>(s.a, s.b);
   p.b = (T)s.b;
   // the flow of this stage is g u_f: fluxes scale by g, and g < 0 flips
   // every face's upwind side (the bare operator has g = 1)
