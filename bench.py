@@ -408,6 +408,56 @@ def run_config_1d(args):
             "dtype": "f64", "config": {"workload": "1d_n1000_vanleer_euler_1000steps"}}
 
 
+def run_config_blocked(args):
+    """256^3 Taylor-Green SSP-RK3 with temporal blocking (one launch per step,
+    each stage's halo recomputed on chip) against the per-stage launches, on
+    the same inputs, for every limiter in FP64 and FP32."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    fl.build()
+    n = args.n
+    wl = build_workload(n, args.limiter)
+    mesh = fl.Mesh.structured(n, n, n, *wl.mesh.h)
+    C, F = mesh.n_cells, mesh.n_faces
+    stream = torch.cuda.current_stream()
+    e0, e1 = _events()
+    rows = {}
+    for vd in ("f32", "f64"):
+        vt = torch.float32 if vd == "f32" else torch.float64
+        es = 4 if vd == "f32" else 8
+        th = torch.tensor(wl.theta0, dtype=vt, device="cuda")
+        u = torch.tensor(wl.u, dtype=vt, device="cuda")
+        ws, nb = fl.workspace_for(mesh, vt, 3)
+        for lim in ("minmod", "vanleer", "superbee", "smart"):
+            res = {}
+            for kind, fn in (("blocked", fl.fl_step_rk_blocked), ("per_stage", fl.fl_step_rk)):
+                for _ in range(args.warmup):
+                    fn(mesh.handle, lim, vt, 3, wl.dt, 1, th, u, ws, nb, stream)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                fn(mesh.handle, lim, vt, 3, wl.dt, args.steps, th, u, ws, nb, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res[kind] = e0.elapsed_time(e1) / args.steps
+            # algorithmic HBM bytes of a blocked step: theta^n, u_f, result
+            rows["%s_%s" % (vd, lim)] = {
+                "blocked_ms_per_step": res["blocked"],
+                "per_stage_ms_per_step": res["per_stage"],
+                "speedup": res["per_stage"] / res["blocked"],
+                "blocked_face_updates_per_s": F * 3 / (res["blocked"] * 1e-3),
+                "blocked_hbm_gbs": (2 * C + F) * es / (res["blocked"] * 1e-3) / 1e9}
+        del th, u, ws
+    main = rows["%s_%s" % (args.dtype, args.limiter)]
+    return {"metric": "limited-convection face-updates/s (temporally blocked SSP-RK3 step)",
+            "value": main["blocked_face_updates_per_s"], "unit": "face-updates/s",
+            "ms_per_step": main["blocked_ms_per_step"], "steps": args.steps,
+            "warmup": args.warmup, "dtype": args.dtype, "gpu_launches": args.steps,
+            "config": {"workload": "taylor_green_%d^3_ssprk3_blocked" % n, "cells": C,
+                       "faces": F, "limiter": args.limiter},
+            "by_variant": rows}
+
+
 def run_config_unstructured(args):
     """256^3 hex mesh in seeded random cell/face order with half of the faces
     reoriented (face-cell incidence as int32 pairs), renumbered by the
@@ -839,7 +889,7 @@ def main():
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")
     ap.add_argument("--config", default="tg256",
                     choices=["tg256", "1d", "unstructured", "batched", "adjoint", "deformation",
-                             "algebraic"])
+                             "algebraic", "blocked"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -850,7 +900,7 @@ def main():
         fn = {"1d": run_config_1d, "unstructured": run_config_unstructured,
               "batched": run_config_batched, "adjoint": run_config_adjoint,
               "deformation": run_config_deformation,
-              "algebraic": run_config_algebraic}[args.config]
+              "algebraic": run_config_algebraic, "blocked": run_config_blocked}[args.config]
         line = fn(args)
         if line is not None:
             print(json.dumps(line))

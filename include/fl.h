@@ -240,6 +240,26 @@ fl_status fl_step_rk_modulated(const fl_mesh *mesh, fl_limiter limiter, fl_dtype
                                size_t workspace_bytes, void *stream);
 
 /*
+ * fl_step_rk with temporal blocking, for structured meshes: one kernel launch
+ * runs all three stages of an SSP-RK3 step (rk_order 3) or three forward-Euler
+ * steps of Algorithm 4 (rk_order 1), so that theta^n and u_f are read from
+ * device memory once per launch instead of once per stage.  The paper
+ * evaluates one operator application at a time; this is the same arithmetic
+ * (Algorithm 1's limited face values, Algorithm 4's update, the SSP-RK3
+ * blends) with each stage's halo recomputed on chip, two cells per stage and
+ * side.  Results agree with fl_step_rk to rounding (the cell sums associate
+ * in the same order; the FP32 flux is the same expression).
+ * Same arguments, ownership and workspace as fl_step_rk (the workspace holds
+ * the other half of a ping-pong pair; the result is copied back into theta
+ * when it lands there).  Euler steps beyond a multiple of three run stage by
+ * stage.  A face-based mesh returns FL_EUNSUPPORTED before any launch.
+ */
+fl_status fl_step_rk_blocked(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                             int rk_order, double dt, int64_t nsteps, void *theta,
+                             const void *u_f, void *workspace, size_t workspace_bytes,
+                             void *stream);
+
+/*
  * fl_step_rk without a workspace argument, for callers that may not allocate
  * device memory at all (plugin hosts that own the whole device memory pool,
  * real-time loops that cannot pay for an allocation's device-wide

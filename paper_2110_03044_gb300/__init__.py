@@ -34,7 +34,7 @@ ABI_SYMBOLS = [
     "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_status", "fl_mesh_destroy",
     "fl_conv_limited_apply",
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_modulated",
-    "fl_step_rk_noalloc",
+    "fl_step_rk_noalloc", "fl_step_rk_blocked",
     "fl_conv_limited_adjoint",
     "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_checkpointed",
     "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
@@ -93,6 +93,7 @@ def lib():
             "fl_step_rk": (I, [P, I, I, I, D, I64, P, P, P, SZ, P]),
             "fl_step_rk_modulated": (I, [P, I, I, I, D, I64, P, P, P, P, SZ, P]),
             "fl_step_rk_noalloc": (I, [P, I, I, I, D, I64, P, P, P]),
+            "fl_step_rk_blocked": (I, [P, I, I, I, D, I64, P, P, P, SZ, P]),
             "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
             "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
             "fl_step_rk_adjoint": (I, [P, I, I, I, D, I64, I64, P, P, P, P, P, SZ, P]),
@@ -253,6 +254,14 @@ def fl_step_rk(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, workspace
     _check(lib().fl_step_rk(mesh, _lim(limiter), c, int(rk_order), float(dt), int(nsteps),
                             _fptr(theta, c), _fptr(u_f, c), _ptr(workspace),
                             int(workspace_bytes), _stream(stream)))
+
+
+def fl_step_rk_blocked(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, workspace,
+                       workspace_bytes, stream=None):
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_blocked(mesh, _lim(limiter), c, int(rk_order), float(dt),
+                                    int(nsteps), _fptr(theta, c), _fptr(u_f, c),
+                                    _ptr(workspace), int(workspace_bytes), _stream(stream)))
 
 
 def fl_step_rk_modulated(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, g, workspace,
@@ -477,6 +486,19 @@ def step_rk(mesh, limiter, theta, u_f, dt, nsteps, rk_order=3, workspace=None, s
         nbytes = workspace.numel() * workspace.element_size()
     fl_step_rk(mesh.handle, limiter, theta.dtype, rk_order, dt, nsteps, theta, u_f, workspace,
                nbytes, stream)
+    return theta
+
+
+def step_rk_blocked(mesh, limiter, theta, u_f, dt, nsteps, rk_order=3, workspace=None,
+                    stream=None):
+    """``step_rk`` with temporal blocking (structured meshes): one launch per
+    SSP-RK3 step, or per three Euler steps."""
+    if workspace is None:
+        workspace, nbytes = workspace_for(mesh, theta.dtype, rk_order, theta.device)
+    else:
+        nbytes = workspace.numel() * workspace.element_size()
+    fl_step_rk_blocked(mesh.handle, limiter, theta.dtype, rk_order, dt, nsteps, theta, u_f,
+                       workspace, nbytes, stream)
     return theta
 
 

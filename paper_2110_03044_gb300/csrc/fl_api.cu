@@ -371,6 +371,29 @@ fl_status fl_step_rk_modulated(const fl_mesh *m, fl_limiter lim, fl_dtype dt, in
   return step_rk_impl(m, lim, dt, rk, dtime, nsteps, theta, u_f, g, ws, ws_bytes, stream);
 }
 
+fl_status fl_step_rk_blocked(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
+                             double dtime, int64_t nsteps, void *theta, const void *u_f,
+                             void *ws, size_t ws_bytes, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(lim, dt));
+  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "temporal blocking needs a structured mesh");
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (nsteps < 0) return fail(FL_EINVAL, "nsteps < 0");
+  if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
+  const size_t es = dsize(dt);
+  FL_TRY(check_buffer(theta, m->C * es, "theta"));
+  FL_TRY(check_buffer(u_f, m->F * es, "u_f"));
+  const size_t need = step_ws_bytes(m, dt, rk);
+  if (ws_bytes < need) return fail(FL_EINVAL, "workspace too small: %zu < %zu", ws_bytes, need);
+  if (((uintptr_t)ws & 255) != 0) return fail(FL_EINVAL, "workspace must be 256-byte aligned");
+  FL_TRY(check_buffer(ws, need, "workspace"));
+  if (nsteps == 0 || m->C == 0) return FL_OK;
+  const cudaError_t e =
+      struct_step_fused(m, lim, dt, rk, dtime, nsteps, theta, u_f, ws, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "temporally blocked step kernel");
+  return FL_OK;
+}
+
 size_t fl_reduce_workspace_size(void) { return reduce_ws_bytes(); }
 
 fl_status fl_reduce_max_abs(fl_dtype dt, const void *x, int64_t n, double *out, void *ws,

@@ -39,6 +39,14 @@ bool struct_step_prescales(const fl_mesh *m, fl_dtype dt);
 cudaError_t struct_step(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
                         int64_t nsteps, void *theta, const void *u, void *A, void *B, void *W,
                         cudaStream_t st, const double *gfac = nullptr);
+// temporally blocked steps (fl_struct_fused.cu): each launch runs one
+// SSP-RK3 step (rk 3) or three Euler steps (rk 1) from theta into Y (|C|
+// values) and the result returns to theta; Euler steps beyond a multiple of
+// three run through struct_step with Y as its stage buffer
+cudaError_t struct_step_fused(const fl_mesh *m, int lim, fl_dtype dt, int rk, double dtime,
+                              int64_t nsteps, void *theta, const void *u, void *Y,
+                              cudaStream_t st);
+size_t struct_fused_smem_bytes(fl_dtype dt);
 size_t line_resident_max_cells(fl_dtype dt);
 // whether the one-CTA resident kernel runs a structured mesh's steps: a
 // periodic line of 2 .. line_resident_max_cells cells (a 1 x 1 x 1 mesh has
