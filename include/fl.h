@@ -247,8 +247,9 @@ fl_status fl_step_rk_modulated(const fl_mesh *mesh, fl_limiter limiter, fl_dtype
  * evaluates one operator application at a time; this is the same arithmetic
  * (Algorithm 1's limited face values, Algorithm 4's update, the SSP-RK3
  * blends) with each stage's halo recomputed on chip, two cells per stage and
- * side.  Results agree with fl_step_rk to rounding (the cell sums associate
- * in the same order; the FP32 flux is the same expression).
+ * side.  Results agree with fl_step_rk to rounding: both meet the same
+ * bounds against the FP64 oracle (FP64 here forms u_f theta_f per face where
+ * fl_step_rk folds dt (A/V) u_f into the cell update).
  * Same arguments, ownership and workspace as fl_step_rk (the workspace holds
  * the other half of a ping-pong pair; the result is copied back into theta
  * when it lands there).  Euler steps beyond a multiple of three run stage by
