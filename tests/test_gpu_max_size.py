@@ -1,7 +1,8 @@
 """The largest structured mesh the library takes (nx ny nz < 2^31 cells, here
 1024 x 1024 x 2047 = 2.15e9 cells with 6.4e9 face entries, so every face
 offset and most cell offsets need 64-bit arithmetic): one SSP-RK3 step
-through each kernel family that serves it, checked cell by cell against the
+through each kernel family that serves it (the temporally blocked step
+included), checked cell by cell against the
 oracle on local patches around sampled cells (the last planes, the periodic
 wrap, tile edges, random cells), plus mass conservation over the whole mesh.
 
@@ -35,11 +36,14 @@ def _samples(dims, rng, n_random=10):
     return fixed + rand
 
 
-# (shape, dtype, kernel that serves it)
+# (shape, dtype, kernel that serves it); the temporally blocked step runs
+# through fl_step_rk_blocked, the others through fl_step_rk
 CASES = [
     ((1024, 1024, 2047), torch.float64, "FP64 shared-memory tile"),
     ((1024, 1024, 2047), torch.float32, "FP32 TMA kernel"),
     ((1030, 1024, 2036), torch.float32, "FP32 register tile"),
+    ((1024, 1024, 2047), torch.float64, "FP64 temporally blocked"),
+    ((1030, 1024, 2036), torch.float32, "FP32 temporally blocked"),
 ]
 
 
@@ -74,7 +78,8 @@ def test_largest_mesh_sampled_and_conserved(fl, shape, dtype, kernel):
     red = torch.empty(fl.fl_reduce_workspace_size(), dtype=torch.uint8, device="cuda")
     m0 = fl.fl_reduce_mass(m.handle, dtype, th, red)
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
-    fl.fl_step_rk(m.handle, "superbee", dtype, 3, dt, 1, th, u, ws, nb)
+    step = fl.fl_step_rk_blocked if "blocked" in kernel else fl.fl_step_rk
+    step(m.handle, "superbee", dtype, 3, dt, 1, th, u, ws, nb)
     torch.cuda.synchronize()
     m1 = fl.fl_reduce_mass(m.handle, dtype, th, red)
     tol = 1e-12 if dtype == torch.float64 else 1e-5
