@@ -815,9 +815,23 @@ def run_config_algebraic(args):
                        "faces": F}}
 
 
+def _cpu_model():
+    """The host CPU's model name (lscpu), for the record."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return None
+    for line in out.splitlines():
+        if line.strip().lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    return None
+
+
 def cpu_baseline(wl, lim, budget_s):
     """The oracle as it stands on the host cores: one SSP-RK3 stage of the
-    same mesh and fields (all cells), repeated while within budget."""
+    same mesh and fields (all cells), repeated while within budget; then one
+    stage on a single thread, for the record."""
     import oracle
     threads = oracle.set_threads(os.cpu_count() or 1)
     om = oracle.OracleMesh(wl.mesh)
@@ -830,11 +844,18 @@ def cpu_baseline(wl, lim, budget_s):
         el = time.perf_counter() - t0
         if el > budget_s or reps >= 10:
             break
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    y = oracle.stage(om, lim, 3, 0, wl.dt, wl.theta0, wl.theta0, wl.u)
+    el1 = time.perf_counter() - t1
+    oracle.set_threads(threads)
     del y
     return {"value": om.F * reps / el, "unit": "face-updates/s", "cores": threads,
             "kind": "oracle",
             "sample": "%d SSP-RK3 stage(s) over the full %d-cell mesh, FP64, OpenMP" % (
-                reps, om.C)}
+                reps, om.C),
+            "single_thread_value": om.F / el1, "nproc": os.cpu_count(),
+            "cpu_model": _cpu_model()}
 
 
 # -------------------------------------------------------------- reference
