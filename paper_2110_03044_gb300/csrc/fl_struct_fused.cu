@@ -32,7 +32,7 @@
 // GB300 that extra arithmetic outweighs the saved HBM traffic (the per-stage
 // kernels are bound by instruction issue in FP32 and by the FP64 pipe), so
 // fl_step_rk keeps the per-stage kernels; 256^3 superbee SSP-RK3 measured
-// 1.08 ms per step here against 0.211 ms (FP32), with 346 MB of DRAM traffic
+// 1.03 ms per step here against 0.211 ms (FP32), with 346 MB of DRAM traffic
 // per step against 993 MB.
 #include <cuda_runtime.h>
 
@@ -117,9 +117,6 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 // all but the most recent group complete
 __device__ __forceinline__ void cp_wait_prev() {
   asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ int wrapn(int v, int n) {
@@ -377,20 +374,6 @@ __global__ void __launch_bounds__(FCfg<T>::NT, FCfg<T>::MINB)
     if (t > 0) {
       if (vl) fetch(z0 + t, t % NRING0);
       cp_commit();
-    }
-    // stage 1's face velocities two planes ahead into L2: one prefetch per
-    // 128-byte line of each row of the theta^n region
-    if (t + 2 < L + 8) {
-      const unsigned zo = zoff(q1 + 2);
-      for (int it = tid; it < N0; it += NT) {
-        const int jr = it / G::W(0), ic = it - jr * G::W(0);
-        const unsigned c = (unsigned)xs[ic] + (unsigned)ys[jr] * nx + zo;
-        if (ic == 0 || xs[ic] == 0 || (c % (128 / sizeof(T))) == 0) {
-          if (p.ax) prefetch_l2(p.ux + c);
-          if (p.ay) prefetch_l2(p.uy + c);
-          if (p.az) prefetch_l2(p.uz + c);
-        }
-      }
     }
     if (p.combine) {
       if (v2) s2.load_thn(p, xs, ys, zoff(q2));
