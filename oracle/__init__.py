@@ -69,6 +69,7 @@ def _load():
         lib.orc_mesh_new.restype = P
         lib.orc_mesh_new.argtypes = [i64, i64, P, P, P, P]
         lib.orc_mesh_free.argtypes = [P]
+        lib.orc_mesh_set_distances.argtypes = [P, P]
         lib.orc_psi.argtypes = [I, P, P, i64]
         lib.orc_psi_branch.argtypes = [I, P, P, P, i64]
         lib.orc_face_values.argtypes = [P, I, P, P, P, P, P, P]
@@ -120,6 +121,12 @@ class OracleMesh:
         self.h = lib.orc_mesh_new(self.C, self.F, _ptr(fc), _ptr(nrm), _ptr(ar), _ptr(vol))
         if not self.h:
             raise ValueError(lib.orc_last_error().decode())
+        # face distances of a non-uniform mesh (Algorithm 3's weights)
+        dist = getattr(mesh, "distances", None)
+        if dist is not None:
+            self._dist = _f64(dist)
+            if lib.orc_mesh_set_distances(self.h, _ptr(self._dist)) != 0:
+                raise ValueError(lib.orc_last_error().decode())
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

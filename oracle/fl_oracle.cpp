@@ -20,8 +20,10 @@
 //     The leading factor s is a sign correction: each printed form of d_U
 //     agrees with Sweby's r for one flow direction only, and the
 //     orientation-invariant sum times s = sign(u_f) agrees for both.  On
-//     hexahedral meshes this is exactly theta_C - theta_U (Algorithm 3
-//     written without the distance weights, all meshes uniform).
+//     hexahedral meshes this is exactly theta_C - theta_U.  Non-uniform
+//     meshes given face distances d_f take Algorithm 3's weights (Algorithm
+//     2's d_i / d_U in 1D): each term is divided by d_j and the sum
+//     multiplied by d_f, so r compares gradients, not differences.
 //   * Algorithm 4: theta^{n+1} = theta^n + dt M U(u_f) theta_f, with M read as
 //     minus the divergence: R_c = -(1/V_c) sum_f sigma_cf u_f A_f theta_f,
 //     sigma = +1 when c is c0 of f and -1 when c is c1.
@@ -68,7 +70,20 @@ struct OMesh {
   std::vector<double> vol;            // cell volumes
   std::vector<int64_t> cf_ptr;        // cell -> faces (CSR), ascending face id
   std::vector<int64_t> cf_idx;
+  std::vector<double> dist;           // face distances d_f (empty: uniform mesh)
 };
+
+// Algorithm 3's distance weighting (and Algorithm 2's d_i / d_U in 1D): the
+// contribution of face j to the upstream gradient is divided by its
+// distance d_j, and r compares that gradient with the face's own,
+// (theta_D - theta_C) / d_f.  So d_U carries the factor d_f / d_j per term.
+// Meshes given without distances (uniform spacing) take no weights.
+inline double dist_term(const OMesh &m, double term, int64_t j) {
+  return m.dist.empty() ? term : term / m.dist[j];
+}
+inline double dist_face(const OMesh &m, double acc, int64_t f) {
+  return m.dist.empty() ? acc : acc * m.dist[f];
+}
 
 // ---------------------------------------------------------------- limiters
 // Closed forms (Sweby's Psi; F(r) = (Psi - 1)/2 in the paper's notation).
@@ -155,13 +170,14 @@ FaceEval eval_face(const OMesh &m, int lim, const double *th, const double *u, i
     const int64_t j = m.cf_idx[q];
     if (j == f) continue;
     const double w = m.nx[f] * m.nx[j] + m.ny[f] * m.ny[j] + m.nz[f] * m.nz[j];
-    acc = acc + w * (th[m.c1[j]] - th[m.c0[j]]);
+    acc = acc + dist_term(m, w * (th[m.c1[j]] - th[m.c0[j]]), j);
     if (w != 0.0) {
       ++n_nonzero;
       U = (m.c0[j] == e.C) ? m.c1[j] : m.c0[j];
     }
   }
   e.U = (n_nonzero == 1) ? U : -1;
+  acc = dist_face(m, acc, f);
   e.dU = (e.s > 0) ? acc : -acc;
   // eq. (rf) and eq. (FL-UP); a zero denominator keeps the upwind value.
   if (e.du == 0.0) {
@@ -211,8 +227,9 @@ double face_tlm(const OMesh &m, const FaceEval &e, const double *dth, int64_t f)
     const int64_t j = m.cf_idx[q];
     if (j == f) continue;
     const double w = m.nx[f] * m.nx[j] + m.ny[f] * m.ny[j] + m.nz[f] * m.nz[j];
-    acc = acc + w * (dth[m.c1[j]] - dth[m.c0[j]]);
+    acc = acc + dist_term(m, w * (dth[m.c1[j]] - dth[m.c0[j]]), j);
   }
+  acc = dist_face(m, acc, f);
   const double ddU = (e.s > 0) ? acc : -acc;
   if (e.du == 0.0) return dth[e.C];
   // theta_f = theta_C + Psi(r) du / 2, r = dU / du
@@ -265,8 +282,10 @@ void rhs_adjoint(const OMesh &m, int lim, const double *th, const double *u, con
       if (j == f) continue;
       const double w = m.nx[f] * m.nx[j] + m.ny[f] * m.ny[j] + m.nz[f] * m.nz[j];
       if (w == 0.0) continue;
-      out[m.c1[j]] += gb * w;
-      out[m.c0[j]] -= gb * w;
+      // d(d_U)/d(theta) of the weighted sum: w d_f / d_j per term
+      const double wj = dist_face(m, dist_term(m, w, j), f);
+      out[m.c1[j]] += gb * wj;
+      out[m.c0[j]] -= gb * wj;
     }
   }
 }
@@ -339,6 +358,20 @@ void *orc_mesh_new(int64_t C, int64_t F, const int32_t *face_cells, const double
     if (m->c1[f] != m->c0[f]) m->cf_idx[fill[m->c1[f]]++] = f;
   }
   return m;
+}
+
+// Face distances d_f (distance between the centres of c0 and c1, > 0) of a
+// non-uniform mesh; NULL removes them (uniform spacing, no weights).
+int orc_mesh_set_distances(void *h, const double *d) {
+  OMesh &m = *static_cast<OMesh *>(h);
+  if (d == nullptr) {
+    m.dist.clear();
+    return 0;
+  }
+  for (int64_t f = 0; f < m.F; ++f)
+    if (!(d[f] > 0.0) || !std::isfinite(d[f])) { set_err("face distances must be > 0"); return 1; }
+  m.dist.assign(d, d + m.F);
+  return 0;
 }
 
 void orc_mesh_free(void *h) { delete static_cast<OMesh *>(h); }

@@ -15,7 +15,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "fl_oracle.cpp")
 PINS = ["tests/test_oracle_limiters.py", "tests/test_oracle_bruteforce.py",
-        "tests/test_oracle_properties.py", "tests/test_oracle_adjoint.py"]
+        "tests/test_oracle_properties.py", "tests/test_oracle_adjoint.py",
+        "tests/test_oracle_distances.py"]
 
 # (name, original text, mutated text)
 MUTANTS = [
@@ -25,8 +26,8 @@ MUTANTS = [
      "for (int64_t q = m.cf_ptr[e.C]; q < m.cf_ptr[e.C + 1]; ++q) {\n    const int64_t j = m.cf_idx[q];\n    if (j == f) continue;\n    const double w",
      "for (int64_t q = m.cf_ptr[e.D]; q < m.cf_ptr[e.D + 1]; ++q) {\n    const int64_t j = m.cf_idx[q];\n    if (j == f) continue;\n    const double w"),
     ("normal_dot_transposed",
-     "const double w = m.nx[f] * m.nx[j] + m.ny[f] * m.ny[j] + m.nz[f] * m.nz[j];\n    acc = acc + w",
-     "const double w = m.nx[f] * m.ny[j] + m.ny[f] * m.nx[j] + m.nz[f] * m.nz[j];\n    acc = acc + w"),
+     "const double w = m.nx[f] * m.nx[j] + m.ny[f] * m.ny[j] + m.nz[f] * m.nz[j];\n    acc = acc + dist_term(m, w",
+     "const double w = m.nx[f] * m.ny[j] + m.ny[f] * m.nx[j] + m.nz[f] * m.nz[j];\n    acc = acc + dist_term(m, w"),
     ("superbee_cap_wrong", "std::fmin(r, 2.0)));", "std::fmin(r, 1.0)));"),
     ("face_value_from_downwind", "e.thf = th[e.C] + 0.5 * e.psi * e.du;",
      "e.thf = th[e.D] + 0.5 * e.psi * e.du;"),
@@ -40,6 +41,10 @@ MUTANTS = [
     ("tlm_alpha_sign", "const double alpha = 0.5 * (e.psi - e.dpsi * e.r);\n  const double beta = 0.5 * e.dpsi;\n  return",
      "const double alpha = 0.5 * (e.psi + e.dpsi * e.r);\n  const double beta = 0.5 * e.dpsi;\n  return"),
     ("adjoint_downwind_to_upwind", "out[e.D] += g * alpha;", "out[e.C] += g * alpha;"),
+    ("distance_weight_inverted", "return m.dist.empty() ? term : term / m.dist[j];",
+     "return m.dist.empty() ? term : term * m.dist[j];"),
+    ("distance_of_face_dropped", "return m.dist.empty() ? acc : acc * m.dist[f];",
+     "return acc;"),
 ]
 
 

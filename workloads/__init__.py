@@ -44,6 +44,8 @@ class Mesh:
     dims: tuple | None = None  # (nx, ny, nz) for structured meshes
     h: tuple | None = None  # (hx, hy, hz)
     extra: dict = field(default_factory=dict)
+    distances: np.ndarray | None = None  # float64 [F]: c0-c1 centre distance
+                                         # (non-uniform meshes; None = uniform)
 
     @property
     def n_faces(self) -> int:
@@ -88,6 +90,63 @@ def structured_mesh(nx: int, ny: int = 1, nz: int = 1, hx: float = 1.0,
         areas = np.zeros(0)
     volumes = np.full(n, hx * hy * hz)
     return Mesh(n, face_cells, normals, areas, volumes, dims=dims, h=hs)
+
+
+def stretched_mesh(wx, wy=(1.0,), wz=(1.0,)) -> Mesh:
+    """Periodic tensor-product box with cell widths ``wx`` [nx], ``wy`` [ny],
+    ``wz`` [nz] along the axes, as explicit face arrays with the face
+    distances of a non-uniform mesh: the face between cells i and i+1 along
+    an axis has distance (w_i + w_{i+1}) / 2 (periodic)."""
+    wx, wy, wz = (np.asarray(w, dtype=np.float64) for w in (wx, wy, wz))
+    nx, ny, nz = len(wx), len(wy), len(wz)
+    dims = (nx, ny, nz)
+    n = nx * ny * nz
+    c = np.arange(n, dtype=np.int64)
+    i = c % nx
+    j = (c // nx) % ny
+    k = c // (nx * ny)
+    ws = (wx[i], wy[j], wz[k])
+    widths = (wx, wy, wz)
+    idx = (i, j, k)
+    fc, nrm, ar, dist = [], [], [], []
+    for a in active_axes(dims):
+        if a == 0:
+            nb = ((i + 1) % nx) + nx * (j + ny * k)
+        elif a == 1:
+            nb = i + nx * (((j + 1) % ny) + ny * k)
+        else:
+            nb = i + nx * (j + ny * ((k + 1) % nz))
+        fc.append(np.stack([c, nb], axis=1))
+        nv = np.zeros((n, 3))
+        nv[:, a] = 1.0
+        nrm.append(nv)
+        others = [ws[b] for b in range(3) if b != a]
+        ar.append(others[0] * others[1])
+        w = widths[a]
+        dist.append(0.5 * (w[idx[a]] + w[(idx[a] + 1) % dims[a]]))
+    if fc:
+        face_cells = np.concatenate(fc).astype(np.int32)
+        normals = np.concatenate(nrm)
+        areas = np.concatenate(ar)
+        distances = np.concatenate(dist)
+    else:
+        face_cells = np.zeros((0, 2), np.int32)
+        normals = np.zeros((0, 3))
+        areas = np.zeros(0)
+        distances = np.zeros(0)
+    volumes = ws[0] * ws[1] * ws[2]
+    return Mesh(n, face_cells, normals, areas, volumes, dims=dims, distances=distances)
+
+
+def stretched_widths(n, length, ratio, seed):
+    """``n`` seeded cell widths summing to ``length`` whose largest / smallest
+    ratio is at most ``ratio`` (a smooth stretching plus seeded jitter)."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(n) / n
+    base = 1.0 + 0.5 * (ratio - 1.0) * (1.0 + np.sin(2.0 * np.pi * x))
+    w = base * rng.uniform(0.9, 1.1, n)
+    w = np.clip(w, 1.0, ratio)
+    return w * (length / w.sum())
 
 
 # --------------------------------------------------------------------------
@@ -220,7 +279,11 @@ def permuted_mesh(mesh: Mesh, seed: int, flip_fraction: float = 0.5):
     new_a[face_perm] = mesh.areas
     new_v = np.empty_like(mesh.volumes)
     new_v[cell_perm] = mesh.volumes
-    out = Mesh(C, new_fc.astype(np.int32), new_n, new_a, new_v)
+    new_d = None
+    if mesh.distances is not None:
+        new_d = np.empty_like(mesh.distances)
+        new_d[face_perm] = mesh.distances
+    out = Mesh(C, new_fc.astype(np.int32), new_n, new_a, new_v, distances=new_d)
     return out, cell_perm, face_perm, flip
 
 
