@@ -458,6 +458,59 @@ def run_config_blocked(args):
             "by_variant": rows}
 
 
+def run_config_stretched(args):
+    """A non-uniform n^3 hexahedral box (cell widths stretched up to 3x along
+    each axis) as a face-based mesh with face distances (Algorithm 3's
+    weights, the general stencil) against the same mesh without them (the
+    hexahedral path); SMART, SSP-RK3, FP64, renumbered.  The face velocities
+    are the 256^3 Taylor-Green values reused on the stretched geometry."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    import workloads as W
+    fl.build()
+    n = args.n
+    wl = W.config_taylor_green(n=n, seed=1, nsteps=50, limiter="smart")
+    widths = [W.stretched_widths(n, 2 * np.pi, 3.0, s) for s in (21, 22, 23)]
+    mesh = W.stretched_mesh(*widths)
+    res = {}
+    for kind, dist in (("weighted", mesh.distances), ("unweighted", None)):
+        t0 = time.perf_counter()
+        m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
+                               mesh.volumes, renumber=True, distances=dist)
+        t_mesh = time.perf_counter() - t0
+        icp, ifp, _ = m.permutation()
+        th_i = np.empty_like(wl.theta0)
+        th_i[icp] = wl.theta0
+        u_i = np.empty_like(wl.u)
+        u_i[ifp] = wl.u
+        th = torch.tensor(th_i, device="cuda")
+        u = torch.tensor(u_i, device="cuda")
+        dt = 0.4 * np.min(np.concatenate(widths)) / np.max(np.abs(wl.u))
+        nb = fl.fl_workspace_size(m.handle, torch.float64, 3)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        for _ in range(args.warmup):
+            fl.fl_step_rk(m.handle, "smart", torch.float64, 3, dt, 1, th, u, ws, nb)
+        e0, e1 = _events()
+        torch.cuda.synchronize()
+        e0.record()
+        fl.fl_step_rk(m.handle, "smart", torch.float64, 3, dt, args.steps, th, u, ws, nb)
+        e1.record()
+        torch.cuda.synchronize()
+        res[kind] = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "mesh_create_s": t_mesh}
+        m.close()
+        del th, u, ws
+    F = mesh.n_faces
+    ms = res["weighted"]["ms_per_step"]
+    return {"metric": "limited-convection face-updates/s (non-uniform face-based mesh, SSP-RK3)",
+            "value": F * 3 / (ms * 1e-3), "unit": "face-updates/s", "ms_per_step": ms,
+            "dtype": "f64", "steps": args.steps, "warmup": args.warmup,
+            "unweighted_ms_per_step": res["unweighted"]["ms_per_step"],
+            "mesh_create_s": {k: v["mesh_create_s"] for k, v in res.items()},
+            "config": {"workload": "stretched_hex%d^3_ratio3_smart_ssprk3" % n,
+                       "cells": mesh.n_cells, "faces": F}}
+
+
 def run_config_unstructured(args):
     """256^3 hex mesh in seeded random cell/face order with half of the faces
     reoriented (face-cell incidence as int32 pairs), renumbered by the
@@ -910,7 +963,7 @@ def main():
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")
     ap.add_argument("--config", default="tg256",
                     choices=["tg256", "1d", "unstructured", "batched", "adjoint", "deformation",
-                             "algebraic", "blocked"])
+                             "algebraic", "blocked", "stretched"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -921,7 +974,8 @@ def main():
         fn = {"1d": run_config_1d, "unstructured": run_config_unstructured,
               "batched": run_config_batched, "adjoint": run_config_adjoint,
               "deformation": run_config_deformation,
-              "algebraic": run_config_algebraic, "blocked": run_config_blocked}[args.config]
+              "algebraic": run_config_algebraic, "blocked": run_config_blocked,
+              "stretched": run_config_stretched}[args.config]
         line = fn(args)
         if line is not None:
             print(json.dumps(line))

@@ -112,7 +112,8 @@ fl_status fl_mesh_create_structured(int nx, int ny, int nz, double hx, double hy
  *     are orthogonal (hexahedra in any numbering and orientation);
  *   - otherwise (tetrahedra, prisms, mixed meshes) the weighted sum of eq.
  *     (Delta_Upwind), s sum_j (n_f . n_j)(theta_{j,c1} - theta_{j,c0}) over
- *     the other faces j of C, without distance weights (Section 6).
+ *     the other faces j of C, without distance weights (uniform spacing;
+ *     fl_mesh_create_weighted adds Algorithm 3's distance weights).
  * Cells with more than 8 faces, and sizes of 2^31 - 1 or more, return
  * FL_EUNSUPPORTED.  Faces listed twice, c0 == c1, out-of-range cells,
  * non-unit normals and non-positive areas or volumes return FL_EINVAL.
@@ -123,6 +124,25 @@ fl_status fl_mesh_create_structured(int nx, int ny, int nz, double hx, double hy
 fl_status fl_mesh_create(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,
                          const double *face_normals, const double *face_areas,
                          const double *cell_volumes, unsigned flags, fl_mesh **out);
+
+/*
+ * fl_mesh_create for a non-uniform mesh: face_distances[f] (HOST, double
+ * [n_faces], > 0, copied) is the distance between the centres of c0 and c1.
+ * The gradient ratio then compares gradients, not differences (Algorithm 3,
+ * and Algorithm 2's (d_i / d_U) on a line): every term of the upstream sum
+ * is divided by the distance d_j of its face and the sum is multiplied by
+ * d_f, i.e.
+ *   d_U = s sum_j (n_f . n_j) (d_f / d_j) (theta_{j,c1} - theta_{j,c0}),
+ * and r = d_U / d_u as before.  Such meshes run the general stencil on any
+ * cell shape (hexahedra included), with the weights in its coefficients.
+ * Same arguments, ownership and errors as fl_mesh_create; a non-positive or
+ * non-finite distance returns FL_EINVAL.  Uniform distances give the
+ * results of fl_mesh_create to rounding.
+ */
+fl_status fl_mesh_create_weighted(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,
+                                  const double *face_normals, const double *face_areas,
+                                  const double *cell_volumes, const double *face_distances,
+                                  unsigned flags, fl_mesh **out);
 
 /*
  * Internal numbering of a mesh created with FL_RENUMBER (host arrays):

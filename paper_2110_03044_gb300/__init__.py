@@ -31,6 +31,7 @@ FL_RENUMBER = 1
 # Exported symbols of include/fl.h (checked by the ABI test).
 ABI_SYMBOLS = [
     "fl_last_error", "fl_version", "fl_mesh_create_structured", "fl_mesh_create",
+    "fl_mesh_create_weighted",
     "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_status", "fl_mesh_destroy",
     "fl_conv_limited_apply",
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_modulated",
@@ -82,6 +83,7 @@ def lib():
             "fl_version": (ctypes.c_char_p, []),
             "fl_mesh_create_structured": (I, [I, I, I, D, D, D, U, PP]),
             "fl_mesh_create": (I, [I64, I64, P, P, P, P, U, PP]),
+            "fl_mesh_create_weighted": (I, [I64, I64, P, P, P, P, P, U, PP]),
             "fl_mesh_permutation": (I, [P, P, P, P]),
             "fl_mesh_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                  ctypes.POINTER(I)]),
@@ -203,6 +205,23 @@ def fl_mesh_create(n_cells, face_cells, face_normals, face_areas, cell_volumes, 
     h = ctypes.c_void_p()
     _check(lib().fl_mesh_create(int(n_cells), int(fc.shape[0]), fc.ctypes.data, nrm.ctypes.data,
                                 ar.ctypes.data, vol.ctypes.data, int(flags), ctypes.byref(h)))
+    return h.value
+
+
+def fl_mesh_create_weighted(n_cells, face_cells, face_normals, face_areas, cell_volumes,
+                            face_distances, flags=0):
+    import numpy as np
+    fc = np.ascontiguousarray(face_cells, dtype=np.int32)
+    nrm = np.ascontiguousarray(face_normals, dtype=np.float64)
+    ar = np.ascontiguousarray(face_areas, dtype=np.float64)
+    vol = np.ascontiguousarray(cell_volumes, dtype=np.float64)
+    dist = np.ascontiguousarray(face_distances, dtype=np.float64)
+    if dist.shape != (fc.shape[0],):
+        raise ValueError("face_distances must hold one value per face")
+    h = ctypes.c_void_p()
+    _check(lib().fl_mesh_create_weighted(int(n_cells), int(fc.shape[0]), fc.ctypes.data,
+                                         nrm.ctypes.data, ar.ctypes.data, vol.ctypes.data,
+                                         dist.ctypes.data, int(flags), ctypes.byref(h)))
     return h.value
 
 
@@ -449,9 +468,15 @@ class Mesh:
 
     @classmethod
     def from_faces(cls, n_cells, face_cells, face_normals, face_areas, cell_volumes,
-                   renumber=False):
+                   renumber=False, distances=None):
+        """Face-based mesh; ``distances`` (one per face) makes it non-uniform
+        (Algorithm 3's distance weights, fl_mesh_create_weighted)."""
+        flags = FL_RENUMBER if renumber else 0
+        if distances is not None:
+            return cls(fl_mesh_create_weighted(n_cells, face_cells, face_normals, face_areas,
+                                               cell_volumes, distances, flags))
         return cls(fl_mesh_create(n_cells, face_cells, face_normals, face_areas, cell_volumes,
-                                  FL_RENUMBER if renumber else 0))
+                                  flags))
 
     def permutation(self):
         return fl_mesh_permutation(self.handle)

@@ -217,7 +217,18 @@ fl_status fl_mesh_create(int64_t n_cells, int64_t n_faces, const int32_t *face_c
   if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
   *out = nullptr;
   return unstruct_create(n_cells, n_faces, face_cells, face_normals, face_areas, cell_volumes,
-                         flags, out);
+                         nullptr, flags, out);
+}
+
+fl_status fl_mesh_create_weighted(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,
+                                  const double *face_normals, const double *face_areas,
+                                  const double *cell_volumes, const double *face_distances,
+                                  unsigned flags, fl_mesh **out) {
+  if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_faces > 0 && face_distances == nullptr) return fail(FL_EINVAL, "NULL input array");
+  return unstruct_create(n_cells, n_faces, face_cells, face_normals, face_areas, cell_volumes,
+                         face_distances, flags, out);
 }
 
 fl_status fl_mesh_permutation(const fl_mesh *m, int32_t *cell_perm, int32_t *face_perm,

@@ -14,9 +14,12 @@
 //
 // Meshes of other polyhedra (tetrahedra, prisms, mixed) have faces without a
 // single opposite face; for them mesh creation stores, per face and flow
-// direction, every other face j of the upwind cell as a pair (the cell
-// across j, coefficient (n_f . n_j) eps_j), eps_j = +1 when C is c0 of j,
-// so that s d_U = sum_j coef_j (theta_j - theta_C), and the kernel sums it.
+// direction, every other face j of the upwind cell with n_f . n_j != 0 as a
+// pair (the cell across j, coefficient (n_f . n_j) eps_j), eps_j = +1 when
+// C is c0 of j, so that s d_U = sum_j coef_j (theta_j - theta_C), and the
+// kernel sums it.  Non-uniform meshes (given face distances) take this
+// stencil on any cell shape, with Algorithm 3's weights d_f / d_j folded
+// into the coefficients; a hexahedral cell then keeps one term per face.
 //
 // Kernel: one CTA per cell block (a compact patch of cells in the internal
 // numbering).  Phase 1 evaluates every face of the block's list once --
@@ -643,8 +646,8 @@ void renumber_cells(const HostMesh &h, std::vector<int32_t> &order, std::vector<
 
 // ----------------------------------------------------------------- create
 fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const double *normals,
-                          const double *areas, const double *volumes, unsigned flags,
-                          fl_mesh **out) {
+                          const double *areas, const double *volumes, const double *distances,
+                          unsigned flags, fl_mesh **out) {
   if (C < 0 || F < 0) return fail(FL_EINVAL, "negative size");
   if (C >= (1LL << 31) - 1 || F >= (1LL << 31) - 1) return fail(FL_EUNSUPPORTED, "sizes must be < 2^31");
   if ((F > 0 && (!face_cells || !normals || !areas)) || (C > 0 && !volumes))
@@ -668,6 +671,8 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
         return err.put(FL_EINVAL, "face %lld: normal is not unit", f);
       if (!(areas[f] > 0) || !std::isfinite(areas[f]))
         return err.put(FL_EINVAL, "face %lld: bad area", f);
+      if (distances && (!(distances[f] > 0) || !std::isfinite(distances[f])))
+        return err.put(FL_EINVAL, "face %lld: bad distance", f);
       h.c0[f] = a;
       h.c1[f] = b;
     }
@@ -757,14 +762,38 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
     }
   });
   if (err.set.load()) return fail(err.st, "%s", err.msg);
+  // Face distances (non-uniform spacing, Algorithm 3) weight every term of
+  // the upstream stencil by d_f / d_j; they take the general stencil, whose
+  // coefficients carry the weights, on any cell shape.
+  if (distances && F > 0) general.store(true);
   // ---- general polyhedra: the weighted upstream stencil of every face and
-  // side (the oracle's definition: all other faces j of C, weight n_f . n_j)
+  // side (the oracle's definition: all other faces j of C, weight n_f . n_j,
+  // times d_f / d_j when distances are given).  Only the terms with a
+  // nonzero weight are stored, in the cell's face order: a face orthogonal to
+  // f adds nothing, so a hexahedral cell keeps one term (its opposite face)
+  // and a prism's quadrilateral faces drop their orthogonal neighbours.
   int kg = 0;
   std::vector<int32_t> gcell;
   std::vector<double> gcoef;
   if (general.load()) {
-    for (int64_t c = 0; c < C; ++c) kg = std::max<int>(kg, (int)(h.cf_ptr[c + 1] - h.cf_ptr[c]) - 1);
-    kg = std::max(kg, 1);
+    std::atomic<int> kmax(1);
+    parallel_for(F, [&](int64_t lo, int64_t hi) {
+      int local = 1;
+      for (int64_t f = lo; f < hi; ++f)
+        for (int side = 0; side < 2; ++side) {
+          const int32_t Cc = side == 0 ? h.c0[f] : h.c1[f];
+          int nz = 0;
+          for (int64_t q = h.cf_ptr[Cc]; q < h.cf_ptr[Cc + 1]; ++q) {
+            const int32_t j = h.cf_idx[q];
+            if (j != f && dot3(&h.n[3 * f], &h.n[3 * (int64_t)j]) != 0.0) ++nz;
+          }
+          local = std::max(local, nz);
+        }
+      int cur = kmax.load();
+      while (local > cur && !kmax.compare_exchange_weak(cur, local)) {
+      }
+    });
+    kg = kmax.load();
     gcell.assign((size_t)F * 2 * kg, 0);
     gcoef.assign((size_t)F * 2 * kg, 0.0);
     parallel_for(F, [&](int64_t lo, int64_t hi) {
@@ -772,24 +801,23 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
         for (int side = 0; side < 2; ++side) {
           const int32_t Cc = side == 0 ? h.c0[f] : h.c1[f];
           const size_t base = ((size_t)f * 2 + side) * kg;
-          int k = 0, nonzero = 0;
+          int k = 0;
           int32_t U = -1;
           for (int64_t q = h.cf_ptr[Cc]; q < h.cf_ptr[Cc + 1]; ++q) {
             const int32_t j = h.cf_idx[q];
             if (j == f) continue;
             const double w = dot3(&h.n[3 * f], &h.n[3 * (int64_t)j]);
+            if (w == 0.0) continue;
             const bool c_is_c0 = (h.c0[j] == Cc);
             const int32_t other = c_is_c0 ? h.c1[j] : h.c0[j];
             gcell[base + k] = other;
-            gcoef[base + k] = c_is_c0 ? w : -w;
+            const double wd = distances ? w * (distances[f] / distances[j]) : w;
+            gcoef[base + k] = c_is_c0 ? wd : -wd;
             ++k;
-            if (w != 0.0) {
-              ++nonzero;
-              U = other;
-            }
+            U = other;
           }
+          h.up[side][f] = (k == 1) ? U : -1;
           for (; k < kg; ++k) gcell[base + k] = Cc;  // coef 0: no contribution
-          h.up[side][f] = (nonzero == 1) ? U : -1;
           h.sig[side][f] = 1;
         }
     });
