@@ -511,6 +511,62 @@ def run_config_stretched(args):
                        "cells": mesh.n_cells, "faces": F}}
 
 
+def run_config_polyhedra(args):
+    """General polyhedra on the fused face-based kernel: a periodic box of
+    64^3 cubes split into 6 Kuhn tetrahedra each, and one of 80^3 cubes split
+    into 2 triangular prisms each (renumbered); seeded mixed-sign face
+    velocities and the sine-plus-cube scalar; SMART, SSP-RK3, FP64 and FP32."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    import workloads as W
+    fl.build()
+    rows = {}
+    for name, make in (("tet64", lambda: W.tet_mesh(64)), ("prism80", lambda: W.prism_mesh(80))):
+        mesh = make()
+        t0 = time.perf_counter()
+        m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
+                               mesh.volumes, renumber=True)
+        t_mesh = time.perf_counter() - t0
+        icp, ifp, _ = m.permutation()
+        rng = np.random.default_rng(1)
+        th0 = rng.uniform(0, 1, mesh.n_cells)
+        u0 = W.mixed_sign_velocity(mesh.n_faces, 2)
+        th_i = np.empty_like(th0)
+        th_i[icp] = th0
+        u_i = np.empty_like(u0)
+        u_i[ifp] = u0
+        dt = 0.05 * np.min(mesh.volumes) / np.max(mesh.areas) / np.max(np.abs(u0))
+        for vd, vt in (("f64", torch.float64), ("f32", torch.float32)):
+            th = torch.tensor(th_i, dtype=vt, device="cuda")
+            u = torch.tensor(u_i, dtype=vt, device="cuda")
+            nb = fl.fl_workspace_size(m.handle, vt, 3)
+            ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            for _ in range(args.warmup):
+                fl.fl_step_rk(m.handle, "smart", vt, 3, dt, 1, th, u, ws, nb)
+            e0, e1 = _events()
+            torch.cuda.synchronize()
+            e0.record()
+            fl.fl_step_rk(m.handle, "smart", vt, 3, dt, args.steps, th, u, ws, nb)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            rows["%s_%s" % (name, vd)] = {"ms_per_step": ms, "cells": mesh.n_cells,
+                                          "faces": mesh.n_faces,
+                                          "face_updates_per_s": mesh.n_faces * 3 / (ms * 1e-3),
+                                          "mesh_create_s": t_mesh}
+            del th, u, ws
+        m.close()
+    main = rows["tet64_f64"]
+    return {"metric": "limited-convection face-updates/s (tetrahedra, SSP-RK3)",
+            "value": main["face_updates_per_s"], "unit": "face-updates/s",
+            "ms_per_step": main["ms_per_step"], "dtype": "f64", "steps": args.steps,
+            "warmup": args.warmup,
+            "config": {"workload": "kuhn_tet_64^3x6_smart_ssprk3", "cells": main["cells"],
+                       "faces": main["faces"]},
+            "by_mesh": rows}
+
+
 def run_config_unstructured(args):
     """256^3 hex mesh in seeded random cell/face order with half of the faces
     reoriented (face-cell incidence as int32 pairs), renumbered by the
@@ -963,7 +1019,7 @@ def main():
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")
     ap.add_argument("--config", default="tg256",
                     choices=["tg256", "1d", "unstructured", "batched", "adjoint", "deformation",
-                             "algebraic", "blocked", "stretched"])
+                             "algebraic", "blocked", "stretched", "polyhedra"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -975,7 +1031,8 @@ def main():
               "batched": run_config_batched, "adjoint": run_config_adjoint,
               "deformation": run_config_deformation,
               "algebraic": run_config_algebraic, "blocked": run_config_blocked,
-              "stretched": run_config_stretched}[args.config]
+              "stretched": run_config_stretched,
+              "polyhedra": run_config_polyhedra}[args.config]
         line = fn(args)
         if line is not None:
             print(json.dumps(line))
