@@ -17,6 +17,7 @@
 //     are evaluated by both neighbouring CTAs (same inputs, same code, so the
 //     two results are bit-identical and the scheme stays conservative);
 //   * theta_f and the fluxes never leave the chip.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "fl_face.cuh"
@@ -242,9 +243,135 @@ __global__ void __launch_bounds__(1024) k_line_resident(T *theta, const T *u, in
   for (int i = threadIdx.x; i < n; i += nt) theta[i] = s_x[i];
 }
 
+// The same rollout spread over a thread-block cluster of LNC CTAs (one SM
+// each): GB300's FP64 rate per SM is low (about 1.6 operations per clock),
+// so a single CTA is bound by its one SM's FP64 pipe.  CTA r of the cluster
+// owns the cells [n r / LNC, n (r+1) / LNC) (at least 2 when n >= 2 LNC) and
+// reads the two cells on each side it needs from its neighbours' shared
+// memory (distributed shared memory, cluster-mapped addresses).  Stage
+// values alternate between two buffers, so one cluster barrier per stage
+// orders every neighbour read after the writes it needs and before the
+// writes that reuse the buffer.  The per-face and per-cell arithmetic is
+// that of k_line_resident, operation for operation, so both give the same
+// bits.  Buffers use one stride for all CTAs (LM = ceil(n / LNC) + 4
+// entries) so that a neighbour's buffer sits at the same offset.
+constexpr int LNC = 8;
+
+template <class T, int LIM>
+__global__ void __cluster_dims__(LNC, 1, 1) __launch_bounds__(1024)
+    k_line_cluster(T *theta, const T *u, int n, int64_t nsteps, int rk, T c, int LM) {
+  namespace cg = cooperative_groups;
+  using F = FT<T>;
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  const int lo = (int)(((long long)n * r) / LNC);
+  const int hi = (int)(((long long)n * (r + 1)) / LNC);
+  const int m = hi - lo;  // cells of this CTA; local index j <-> cell lo + j - 2
+  const int rl = (r + LNC - 1) % LNC, rr = (r + 1) % LNC;
+  const int ml = (int)(((long long)n * (rl + 1)) / LNC) - (int)(((long long)n * rl) / LNC);
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *buf0 = reinterpret_cast<T *>(smem);  // stage values, two buffers of LM
+  T *buf1 = buf0 + LM;
+  T *s_n = buf1 + LM;   // theta^n at j
+  T *s_d = s_n + LM;    // Delta of local face j (between j and j + 1)
+  T *s_f = s_d + LM;    // flux of local face j
+  T *s_u = s_f + LM;    // u of local face j
+  const int nt = blockDim.x, tid = threadIdx.x;
+  // own cells, and the velocities of local faces 1 .. m + 1 (faces of the
+  // cells lo - 1 .. hi - 1, the face of cell i lying between i and i + 1)
+  for (int j = tid; j < m; j += nt) buf0[j + 2] = theta[lo + j];
+  for (int j = tid; j <= m; j += nt) {
+    const int cell = (lo + j - 1 + n) % n;
+    s_u[j + 1] = u[cell];
+  }
+  const int ns = (rk == 3) ? 3 : 1;
+  T *cur = buf0, *nxt = buf1;
+  for (int64_t step = 0; step < nsteps; ++step) {
+    for (int st = 0; st < ns; ++st) {
+      // every CTA's cur is complete; nobody writes it again before the next barrier
+      cl.sync();
+      if (ns == 3 && st == 0)
+        for (int j = 2 + tid; j < m + 2; j += nt) s_n[j] = cur[j];
+      if (tid < 4) {
+        if (tid < 2) {
+          const T *src = cl.map_shared_rank(cur, (unsigned)rl);
+          cur[tid] = src[ml + tid];  // the left neighbour's last two cells
+        } else {
+          const T *src = cl.map_shared_rank(cur, (unsigned)rr);
+          cur[m + tid] = src[tid];   // the right neighbour's first two cells
+        }
+      }
+      __syncthreads();
+      for (int j = tid; j < m + 3; j += nt) s_d[j] = F::sub(cur[j + 1], cur[j]);
+      __syncthreads();
+      for (int j = 1 + tid; j <= m + 1; j += nt) {
+        const T uf = s_u[j];
+        const bool sp = upwind_positive(uf);
+        const T thf = limited_face<T, LIM>(sp ? cur[j] : cur[j + 1], s_d[j],
+                                           sp ? s_d[j - 1] : s_d[j + 1], sp);
+        s_f[j] = face_flux(uf, thf);
+      }
+      __syncthreads();
+      for (int j = 2 + tid; j < m + 2; j += nt) {
+        T acc;
+        if (ns == 1 || st == 0) {
+          acc = cur[j];
+          acc = F::fma(-c, s_f[j], acc);
+          acc = F::fma(c, s_f[j - 1], acc);
+        } else {
+          const T a = (st == 1) ? T(0.75) : T(1) - T(2.0 / 3.0);
+          const T b = (st == 1) ? T(0.25) : T(2.0 / 3.0);
+          const T cb = (st == 1) ? F::mul(T(0.25), c) : F::mul(T(2.0 / 3.0), c);
+          acc = F::fma(a, s_n[j], F::mul(b, cur[j]));
+          acc = F::fma(-cb, s_f[j], acc);
+          acc = F::fma(cb, s_f[j - 1], acc);
+        }
+        nxt[j] = acc;
+      }
+      T *t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < m; j += nt) theta[lo + j] = cur[j + 2];
+  // no CTA leaves while a neighbour may still read its shared memory
+  cl.sync();
+}
+
+template <class T>
+cudaError_t run_line_cluster_t(int lim, void *theta, const void *u, int n, int64_t nsteps,
+                               int rk, double c, cudaStream_t st) {
+  const int LM = (n + LNC - 1) / LNC + 4;
+  const size_t smem = 6 * sizeof(T) * (size_t)LM;
+  const int threads = LM >= 1024 ? 1024 : ((LM + 31) / 32) * 32;
+  T *th = static_cast<T *>(theta);
+  const T *uu = static_cast<const T *>(u);
+#define FL_LINE_CASE(L)                                                                        \
+  case L: {                                                                                    \
+    auto k = k_line_cluster<T, L>;                                                             \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                         (int)smem);                                           \
+    if (e != cudaSuccess) return e;                                                            \
+    k<<<LNC, threads, smem, st>>>(th, uu, n, nsteps, rk, (T)c, LM);                            \
+    return cudaGetLastError();                                                                 \
+  }
+  switch (lim) {
+    FL_LINE_CASE(LIM_UPWIND)
+    FL_LINE_CASE(LIM_CENTRAL)
+    FL_LINE_CASE(LIM_MINMOD)
+    FL_LINE_CASE(LIM_VANLEER)
+    FL_LINE_CASE(LIM_SUPERBEE)
+    FL_LINE_CASE(LIM_SMART)
+  }
+#undef FL_LINE_CASE
+  return cudaErrorInvalidValue;
+}
+
 template <class T>
 cudaError_t run_line_t(int lim, void *theta, const void *u, int n, int64_t nsteps, int rk, double c,
                        cudaStream_t st) {
+  if (n >= 2 * LNC) return run_line_cluster_t<T>(lim, theta, u, n, nsteps, rk, c, st);
   const size_t smem = 5 * sizeof(T) * (size_t)n;
   const int threads = n >= 1024 ? 1024 : ((n + 31) / 32) * 32;
   T *th = static_cast<T *>(theta);

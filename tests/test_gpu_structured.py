@@ -205,6 +205,43 @@ def test_line_resident_size_limit(fl, dtype, n, lim, rk):
     m.close()
 
 
+# Lines of 16 cells or more run on a cluster of 8 CTAs: each owns a run of
+# cells and reads the two cells on each side from its neighbours' shared
+# memory; 15 cells take the one-CTA kernel.  Several steps in one launch
+# against the oracle, then the mass over 200 steps: a halo exchange that gave
+# the two sides of a run boundary different values would break the
+# telescoping of the fluxes.
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("rk", [1, 3])
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "superbee", "smart"])
+@pytest.mark.parametrize("n", [15, 16, 17, 23, 100, 1000, 5120])
+def test_line_cluster_multi_step(fl, n, lim, rk, dtype):
+    mesh, th, u = _mesh_inputs((n, 1, 1), seed=13)
+    u = u * 0.3
+    dt = 0.4 * mesh.h[0] / np.max(np.abs(u))
+    if dtype == torch.float32:
+        th = th.astype(np.float32).astype(np.float64)
+        u = u.astype(np.float32).astype(np.float64)
+    m = fl.Mesh.structured(n, 1, 1, *mesh.h)
+    ud = _dev(u, dtype)
+    ref = oracle.step(mesh, lim, rk, dt, 5, u, th)
+    g = _dev(th, dtype)
+    fl.step_rk(m, lim, g, ud, dt, 5, rk_order=rk)
+    assert _rel(g.cpu().double().numpy(), ref) <= 5 * TOL[dtype]
+    # mass over 200 steps of a uniform flow (right for Euler, left for
+    # SSP-RK3): in 1D a varying face velocity compresses the profile without
+    # bound, and the rounding of the growing values would swamp the check
+    uc = np.full(n, 0.3 if rk == 1 else -0.3)
+    g = _dev(th, dtype)
+    fl.step_rk(m, lim, g, _dev(uc, dtype), 0.4 * mesh.h[0] / 0.3, 200, rk_order=rk)
+    got = g.cpu().double().numpy()
+    assert np.all(np.isfinite(got))
+    m0 = math.fsum((th * mesh.volumes).tolist())
+    m1 = math.fsum((got * mesh.volumes).tolist())
+    assert abs(m1 - m0) <= (1e-13 if dtype == torch.float64 else 1e-5) * abs(m0)
+    m.close()
+
+
 def _raw_device_alloc(nbytes):
     """cudaMalloc of exactly nbytes through the CUDA runtime (the caching
     allocator would place a small tensor inside a larger allocation)."""
