@@ -83,3 +83,22 @@ def test_rejects_cells_with_too_many_faces(fl):
     with pytest.raises(fl.FLError) as e:
         _create(fl, m, fc=fc, nrm=nrm, ar=ar)
     assert e.value.status in (fl.FL_EINVAL, fl.FL_EUNSUPPORTED)
+
+
+@pytest.mark.parametrize("bad", [0.0, -1.0, float("nan"), float("inf")])
+def test_rejects_bad_face_distance(fl, bad):
+    m = W.stretched_mesh(W.stretched_widths(8, 1.0, 2.0, 1), W.stretched_widths(5, 1.0, 2.0, 2))
+    d = m.distances.copy()
+    d[4] = bad
+    with pytest.raises(fl.FLError) as e:
+        fl.fl_mesh_create_weighted(m.n_cells, m.face_cells, m.normals, m.areas, m.volumes, d,
+                                   fl.FL_RENUMBER)
+    assert e.value.status == fl.FL_EINVAL
+    assert "distance" in str(e.value)
+
+
+def test_rejects_missing_face_distances(fl):
+    m = _box()
+    with pytest.raises(ValueError):
+        fl.fl_mesh_create_weighted(m.n_cells, m.face_cells, m.normals, m.areas, m.volumes,
+                                   np.ones(m.n_faces - 1))
