@@ -33,9 +33,14 @@ sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
-# FP64 pipe: 2 lane-operations per clock per SM (1.25 TFLOP/s dense nominal,
-# an FMA counting two) x 152 SMs x 2070 MHz maximum SM clock
-FP64_OPS_PEAK = 2 * 152 * 2.070e9
+
+# The FP64 stage kernel is bound by the FP64 pipe, not by HBM: the busy
+# fraction of that pipe in one ncu capture of the current kernel (the
+# profile summary named beside it), reported next to the HBM roofline.
+NCU_FP64_PIPE = {
+    ("f64", "superbee", 256): (0.850, "sm__pipe_fp64_cycles_active, RK stage 2 launch, "
+                               "profiles/k_struct_stage_f64_superbee_tg256.md"),
+}
 
 
 # DRAM bytes (read + write) per launch of the dominant stage kernel at 256^3,
@@ -224,26 +229,30 @@ def run_ours(args):
     value, ms = whole_job_rate(F * stages, ev0.elapsed_time(ev1), device="cuda")
     launch_ms = ms / stages
 
-    # ---- roofline of the stage kernel (all launches in the region are it)
+    # ---- roofline of the stage kernel (all launches in the region are it):
+    # algorithmic bytes of a step (3 stage launches) / the step's time, i.e.
+    # the stage launches' average, against the measured copy bandwidth
     hbm_peak, peak_kind = peaks()
     traffic, traffic_note = args.traffic, None
     if traffic is None and (args.dtype, lim, n) in NCU_TRAFFIC:
         traffic, traffic_note = NCU_TRAFFIC[(args.dtype, lim, n)]
     bytes_step = sum(stage_bytes_per_cell(es, s) for s in range(3)) * C
     gbs = bytes_step * args.steps / (ms * 1e-3) / 1e9
-    ops_step = sum(stage_fp64_ops_per_cell(lim, s) for s in range(3)) * C
-    roof_hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
-                "traffic_kernel": traffic_note,
-                "peak_kind": peak_kind + " copy bandwidth"}
+    roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
+            "traffic_kernel": traffic_note,
+            "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS hbm_gbs)"
+                         if peak_kind == "measured" else "fallback copy bandwidth",
+            "bytes_per_cell_step": bytes_step // C}
+    fp64 = None
     if args.dtype == "f64":
-        ach = ops_step * args.steps / (ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_OPS_PEAK / 1e12, 4),
-                "unit": "T FP64 ops/s", "frac": round(ach * 1e12 / FP64_OPS_PEAK, 4),
-                "traffic": traffic, "traffic_kernel": traffic_note,
-                "peak_kind": "FP64 pipe, 2 ops/clk/SM x 152 SMs x 2070 MHz (nominal)"}
-    else:
-        roof = roof_hbm
+        ops_step = sum(stage_fp64_ops_per_cell(lim, s) for s in range(3)) * C
+        pipe = NCU_FP64_PIPE.get((args.dtype, lim, n))
+        fp64 = {"bound": "fp64 pipe",
+                "fp64_ops_per_cell_step": ops_step // C,
+                "achieved_fp64_ops_per_s": ops_step * args.steps / (ms * 1e-3),
+                "pipe_busy_ncu": pipe[0] if pipe else None,
+                "pipe_busy_source": pipe[1] if pipe else None}
 
     # ---- end to end through the C ABI: every step copies its inputs (theta
     # and u_f) in from pinned host memory and its result (theta) back out.
@@ -337,6 +346,13 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(wl, lim, args.cpu_budget)
 
+    # the other configurations' headline numbers, on the same GPU (one rank)
+    configs = None
+    if ws_ == 1 and not args.no_configs:
+        del th, u, ws_t
+        torch.cuda.empty_cache()
+        configs = run_default_configs(args)
+
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -361,7 +377,7 @@ def run_ours(args):
                          % (C * es // 2**20, F * es // 2**20),
                    "parallelism": "replicas" if ws_ > 1 else "single"},
         "roofline": roof,
-        "roofline_hbm": roof_hbm,
+        "fp64_pipe": fp64,
         "stage_launch_ms": launch_ms,
         # the stage launches plus, in FP64, the one velocity pre-scaling
         # launch of the fl_step_rk call
@@ -370,8 +386,31 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "variants": variants,
+        "configs": configs,
     }
     print(json.dumps(line))
+
+
+def run_default_configs(args):
+    """Configurations 0, 2, 3 and 4 of the benchmark set, each in its own
+    runner: the 1D rollout, the 256^3 face-based (unstructured storage) SMART
+    step with its HBM fraction, batched against separate launches in FP64 and
+    FP32, and the adjoint's reverse sweep against the forward rollout."""
+    import argparse as ap
+    import torch
+    out = {}
+    sub = ap.Namespace(**vars(args))
+    sub.n = 256
+    sub.no_cpu = True
+    for name, fn in (("1d", run_config_1d), ("unstructured", run_config_unstructured),
+                     ("batched", run_config_batched), ("adjoint", run_config_adjoint)):
+        try:
+            out[name] = fn(sub)
+        except Exception as e:  # a failing runner must not hide the headline line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 def _events():
@@ -479,13 +518,8 @@ def run_config_stretched(args):
         m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
                                mesh.volumes, renumber=True, distances=dist)
         t_mesh = time.perf_counter() - t0
-        icp, ifp, _ = m.permutation()
-        th_i = np.empty_like(wl.theta0)
-        th_i[icp] = wl.theta0
-        u_i = np.empty_like(wl.u)
-        u_i[ifp] = wl.u
-        th = torch.tensor(th_i, device="cuda")
-        u = torch.tensor(u_i, device="cuda")
+        th = m.to_internal(torch.tensor(wl.theta0, device="cuda"), "cell")
+        u = m.to_internal(torch.tensor(wl.u, device="cuda"), "face")
         dt = 0.4 * np.min(np.concatenate(widths)) / np.max(np.abs(wl.u))
         nb = fl.fl_workspace_size(m.handle, torch.float64, 3)
         ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
@@ -528,18 +562,13 @@ def run_config_polyhedra(args):
         m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
                                mesh.volumes, renumber=True)
         t_mesh = time.perf_counter() - t0
-        icp, ifp, _ = m.permutation()
         rng = np.random.default_rng(1)
         th0 = rng.uniform(0, 1, mesh.n_cells)
         u0 = W.mixed_sign_velocity(mesh.n_faces, 2)
-        th_i = np.empty_like(th0)
-        th_i[icp] = th0
-        u_i = np.empty_like(u0)
-        u_i[ifp] = u0
         dt = 0.05 * np.min(mesh.volumes) / np.max(mesh.areas) / np.max(np.abs(u0))
         for vd, vt in (("f64", torch.float64), ("f32", torch.float32)):
-            th = torch.tensor(th_i, dtype=vt, device="cuda")
-            u = torch.tensor(u_i, dtype=vt, device="cuda")
+            th = m.to_internal(torch.tensor(th0, dtype=vt, device="cuda"), "cell")
+            u = m.to_internal(torch.tensor(u0, dtype=vt, device="cuda"), "face")
             nb = fl.fl_workspace_size(m.handle, vt, 3)
             ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
             for _ in range(args.warmup):
@@ -585,13 +614,9 @@ def run_config_unstructured(args):
     m = fl.Mesh.from_faces(pm.n_cells, pm.face_cells, pm.normals, pm.areas, pm.volumes,
                            renumber=True)
     t_mesh = time.perf_counter() - t0
-    icp, ifp, _ = m.permutation()
-    th_i = np.empty_like(thp)
-    th_i[icp] = thp
-    u_i = np.empty_like(up)
-    u_i[ifp] = up
-    th = torch.tensor(th_i, device="cuda")
-    u = torch.tensor(u_i, device="cuda")
+    # the fields cross into the library's numbering once, by its own kernels
+    th = m.to_internal(torch.tensor(thp, device="cuda"), "cell")
+    u = m.to_internal(torch.tensor(up, device="cuda"), "face")
     nb = fl.fl_workspace_size(m.handle, torch.float64, 3)
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
@@ -604,8 +629,18 @@ def run_config_unstructured(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     C, F = pm.n_cells, pm.n_faces
+    # SURVEY-style algorithmic bytes of the face-based step: per stage theta
+    # in/out, u_f, the face records (c0, c1, up0, up1) and the cell -> 6 faces
+    # lists, plus theta^n in stages 2-3 (352 B per cell and SSP-RK3 step)
+    hbm_peak, peak_kind = peaks()
+    bpc = 352
+    gbs = bpc * C / (ms * 1e-3) / 1e9
+    m.close()
     return {"metric": "limited-convection face-updates/s (unstructured storage, SSP-RK3)",
             "value": F * 3 / (ms * 1e-3), "unit": "face-updates/s", "ms_per_step": ms,
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
+                         "unit": "GB/s", "frac": round(gbs / hbm_peak, 4), "traffic": None,
+                         "bytes_per_cell_step": bpc},
             "dtype": "f64", "mesh_create_s": t_mesh,
             "config": {"workload": "hex%d^3_permuted_flipped_smart_ssprk3" % n, "cells": C,
                        "faces": F}}
@@ -798,6 +833,9 @@ def run_config_deformation(args):
     m0 = float(wl.theta0.sum())
     ops = stage_fp64_ops_per_cell("superbee", 0) + 1  # + the velocity factor
     ach = ops * m.n_cells * wl.nsteps / (ms * 1e-3) / 1e12
+    # an Euler stage moves theta in, u_f (3 faces) and theta out: 40 B per cell
+    hbm_peak, _ = peaks()
+    gbs = 40.0 * m.n_cells * wl.nsteps / (ms * 1e-3) / 1e9
     cpu = None
     if not args.no_cpu:
         import oracle
@@ -814,9 +852,10 @@ def run_config_deformation(args):
     return {"metric": "deformation benchmark face-updates/s (Section 4.1, superbee, Euler)",
             "value": F * wl.nsteps / (ms * 1e-3), "unit": "face-updates/s",
             "ms_per_step": ms / wl.nsteps, "rollout_ms": ms, "steps": wl.nsteps, "dtype": "f64",
-            "roofline": {"bound": "alu", "achieved": round(ach, 4),
-                         "peak": round(FP64_OPS_PEAK / 1e12, 4), "unit": "T FP64 ops/s",
-                         "frac": round(ach * 1e12 / FP64_OPS_PEAK, 4), "traffic": None},
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
+                         "unit": "GB/s", "frac": round(gbs / hbm_peak, 4), "traffic": None,
+                         "bytes_per_cell_step": 40},
+            "achieved_fp64_ops_per_s": ach * 1e12,
             "checks": {"mass_rel_drift": abs(float(out.sum()) - m0) / m0,
                        "min": float(out.min()), "max": float(out.max()),
                        "l1_theta_T_vs_sphere": float(np.sum(np.abs(out - wl.theta0)) / n ** 3)},
@@ -938,37 +977,40 @@ def _cpu_model():
 
 
 def cpu_baseline(wl, lim, budget_s):
-    """The oracle as it stands on the host cores: one SSP-RK3 stage of the
-    same mesh and fields (all cells), repeated while within budget; then one
-    stage on a single thread, for the record."""
+    """The oracle as it stands on the host cores: whole SSP-RK3 steps of the
+    same mesh and fields (all cells, three stages each), repeated while within
+    budget; then one step on a single thread, for the record."""
     import oracle
     threads = oracle.set_threads(os.cpu_count() or 1)
     om = oracle.OracleMesh(wl.mesh)
     t0 = time.perf_counter()
     reps = 0
-    y = None
+    y = wl.theta0
     while True:
-        y = oracle.stage(om, lim, 3, 0, wl.dt, wl.theta0, wl.theta0, wl.u)
+        y = oracle.step(om, lim, 3, wl.dt, 1, wl.u, y)
         reps += 1
         el = time.perf_counter() - t0
         if el > budget_s or reps >= 10:
             break
     oracle.set_threads(1)
     t1 = time.perf_counter()
-    y = oracle.stage(om, lim, 3, 0, wl.dt, wl.theta0, wl.theta0, wl.u)
+    oracle.step(om, lim, 3, wl.dt, 1, wl.u, wl.theta0)
     el1 = time.perf_counter() - t1
     oracle.set_threads(threads)
     del y
-    return {"value": om.F * reps / el, "unit": "face-updates/s", "cores": threads,
+    return {"value": om.F * 3 * reps / el, "unit": "face-updates/s", "cores": threads,
             "kind": "oracle",
-            "sample": "%d SSP-RK3 stage(s) over the full %d-cell mesh, FP64, OpenMP" % (
-                reps, om.C),
-            "single_thread_value": om.F / el1, "nproc": os.cpu_count(),
+            "sample": "%d SSP-RK3 step(s) (3 stages each) over the full %d-cell mesh, FP64, "
+                      "OpenMP" % (reps, om.C),
+            "single_thread_value": om.F * 3 / el1, "nproc": os.cpu_count(),
             "cpu_model": _cpu_model()}
 
 
 # -------------------------------------------------------------- reference
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on all host cores,
+    timing whole SSP-RK3 steps (three stages each) of the same 256^3 workload
+    and reporting the same metric (face-updates/s = |F| x 3 x steps / time)."""
     ws_, rank, _ = dist_env()
     if rank != 0:
         return
@@ -977,14 +1019,17 @@ def run_reference(args):
     wl = build_workload(args.n, args.limiter)
     threads = oracle.set_threads(os.cpu_count() or 1)
     om = oracle.OracleMesh(wl.mesh)
+    y = wl.theta0
     for _ in range(args.warmup):
-        oracle.stage(om, args.limiter, 3, 0, wl.dt, wl.theta0, wl.theta0, wl.u)
+        y = oracle.step(om, args.limiter, 3, wl.dt, 1, wl.u, y)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.stage(om, args.limiter, 3, 0, wl.dt, wl.theta0, wl.theta0, wl.u)
+        y = oracle.step(om, args.limiter, 3, wl.dt, 1, wl.u, y)
     el = time.perf_counter() - t0
-    value = om.F * args.steps / el
-    sample = "each step: one SSP-RK3 stage of the full %d-cell mesh, FP64" % om.C
+    value = om.F * 3 * args.steps / el
+    sample = ("each step: one whole SSP-RK3 step (3 stages) of the full %d-cell mesh, FP64"
+              % om.C)
+    es = 8
     line = {
         "impl": "reference",
         "metric": "limited-convection face-updates/s (fused SSP-RK3 step)",
@@ -993,7 +1038,10 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Taylor-Green velocity and sine+cube scalar)",
         "config": {"workload": "taylor_green_%d^3_ssprk3_cfl0.4" % args.n,
-                   "limiter": args.limiter},
+                   "limiter": args.limiter, "cells": om.C, "faces": om.F, "rk_order": 3,
+                   "l2": "inputs larger than L2 (theta %d MB + u_f %d MB), no flush"
+                         % (om.C * es // 2**20, om.F * es // 2**20),
+                   "parallelism": "single"},
         "cpu_baseline": {"value": value, "unit": "face-updates/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "face-updates/s", "h2d_bytes_per_step": 0,
@@ -1014,6 +1062,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations' numbers in the default line")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")

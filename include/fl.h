@@ -36,6 +36,11 @@
  *     returned synchronously before anything is enqueued.
  *   - Every call returns fl_status; fl_last_error() gives a thread-local
  *     message for the last failure on the calling thread.
+ *   - Device-side errors (a bounded wait inside a kernel that gave up) are
+ *     latched in a status word owned by the mesh, in mapped host memory.
+ *     The next call on that mesh that finds one set returns it (and clears
+ *     it) before running anything; fl_mesh_status synchronises a stream
+ *     first and then does the same.
  *   - No compute call allocates device memory; scratch comes from the caller
  *     (fl_workspace_size / fl_adjoint_workspace_size).
  */
@@ -57,7 +62,7 @@ typedef enum {
   FL_EUNSUPPORTED = 4,  /* valid input the library does not handle */
   FL_ENONFINITE = 5,    /* a reduction met NaN or Inf */
   FL_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
-  FL_EINDEX = 7         /* a device-side index check failed (checked builds) */
+  FL_EINDEX = 7         /* a cell index in the connectivity is outside [0, n_cells) */
 } fl_status;
 
 /* Limiter functions Psi(r) (Sweby's form; the paper's F(r) = (Psi - 1)/2). */
@@ -115,11 +120,15 @@ fl_status fl_mesh_create_structured(int nx, int ny, int nz, double hx, double hy
  *     the other faces j of C, without distance weights (uniform spacing;
  *     fl_mesh_create_weighted adds Algorithm 3's distance weights).
  * Cells with more than 8 faces, and sizes of 2^31 - 1 or more, return
- * FL_EUNSUPPORTED.  Faces listed twice, c0 == c1, out-of-range cells,
- * non-unit normals and non-positive areas or volumes return FL_EINVAL.
+ * FL_EUNSUPPORTED.  A cell index outside [0, n_cells) returns FL_EINDEX.
+ * Faces listed twice, c0 == c1, non-unit normals and non-positive areas or
+ * volumes return FL_EINVAL.
  * With FL_RENUMBER the library reorders cells and faces into compact blocks
- * for locality; fields passed to compute calls are then in the INTERNAL
- * order given by fl_mesh_permutation.  Without it the user order is used.
+ * for locality.  Compute calls then take and return fields in that INTERNAL
+ * order (so that a step pays nothing for the user's numbering); callers
+ * holding fields in their own (user) order convert them once, before and
+ * after a rollout, with fl_mesh_to_internal / fl_mesh_to_user.  Without
+ * FL_RENUMBER the two orders coincide.
  */
 fl_status fl_mesh_create(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,
                          const double *face_normals, const double *face_areas,
@@ -159,10 +168,32 @@ fl_status fl_mesh_info(const fl_mesh *mesh, int64_t *n_cells, int64_t *n_faces, 
 
 /*
  * Device-side status of the kernels run on this mesh: synchronises the
- * stream, returns FL_ETIMEOUT (a bounded wait inside a kernel gave up) or
- * FL_EINDEX if one was recorded since the last call, and clears it.
+ * stream, then returns FL_ETIMEOUT (a bounded wait inside a kernel gave up)
+ * if a kernel recorded it since it was last returned, and clears it.  Any
+ * other call on the mesh returns a recorded error the same way, without
+ * synchronising (so it sees only kernels that have finished).
  */
 fl_status fl_mesh_status(const fl_mesh *mesh, void *stream);
+
+/*
+ * Field order conversion for meshes created with FL_RENUMBER (Section 2's
+ * incidence E_{C->F} relabelled: the renumbering is a permutation P_c of the
+ * cells and P_f of the faces, and E' = P_f E P_c^T is the same operator).
+ *   kind FL_FIELD_CELL: a [n_cells] cell field (theta, rhs, lambda);
+ *   kind FL_FIELD_FACE: a [n_faces] face field (u_f, theta_f).
+ * fl_mesh_to_internal: dst[internal index] = src[user index];
+ * fl_mesh_to_user:     dst[user index] = src[internal index];
+ * with the permutation of fl_mesh_permutation (the renumbering keeps every
+ * face's orientation, so no value changes sign).  src and dst: device
+ * buffers of dtype elements, distinct (no aliasing: one gather or scatter
+ * kernel writes dst while it reads src).  Meshes without renumbering (and
+ * structured meshes) copy src to dst.  Asynchronous on `stream`.
+ */
+typedef enum { FL_FIELD_CELL = 0, FL_FIELD_FACE = 1 } fl_field_kind;
+fl_status fl_mesh_to_internal(const fl_mesh *mesh, fl_field_kind kind, fl_dtype dtype,
+                              const void *src, void *dst, void *stream);
+fl_status fl_mesh_to_user(const fl_mesh *mesh, fl_field_kind kind, fl_dtype dtype,
+                          const void *src, void *dst, void *stream);
 
 fl_status fl_mesh_destroy(fl_mesh *mesh);
 
@@ -202,9 +233,9 @@ typedef struct fl_alg fl_alg;
  * precomputed operators after eq. SimplifiedDeltaUpstream, stored with the
  * sign that gives d_U = (Q T - S) theta for both flow directions), Pi
  * (eq. sCF) and M = V^-1 E^T diag(A) (|C| x |F|).  Rows keep every
- * structural entry (zero coefficients included).  Returns FL_EINVAL for
- * out-of-range cells, self-loops, non-positive areas or volumes;
- * FL_ENOMEM when device memory runs out.  The handle owns its device
+ * structural entry (zero coefficients included).  Returns FL_EINDEX for
+ * out-of-range cells, FL_EINVAL for self-loops, non-positive areas or
+ * volumes; FL_ENOMEM when device memory runs out.  The handle owns its device
  * memory until fl_alg_destroy.
  */
 fl_status fl_alg_create(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,
@@ -297,7 +328,9 @@ fl_status fl_step_rk_blocked(const fl_mesh *mesh, fl_limiter limiter, fl_dtype d
  * runs.  (fl_step_rk's FP64 workspace also holds a pre-scaled copy of u_f;
  * this entry point runs the same stages without it.)
  * The first call on each device looks up the area's device address, so make
- * it before any stream capture.  All calls share the area: calls whose GPU
+ * it before any stream capture.  The address is remembered with the identity
+ * of the CUDA context it was taken in; after a device reset (a new context)
+ * the next call looks it up again.  All calls share the area: calls whose GPU
  * work overlaps in time race and must be ordered by the caller.  The call
  * allocates nothing (no cudaMalloc, no library allocator).
  */
@@ -369,7 +402,11 @@ fl_status fl_batch_workspace_size(const fl_batch *batch, fl_dtype dtype, int rk_
 /*
  * nsteps steps of every instance.  theta, u_f: host arrays of n device
  * pointers; dt: host array of n step sizes.  Tiles of all instances form
- * one work list; every stage is one launch over it.
+ * one work list; every stage is one launch over it.  The batch owns one
+ * parameter table and one set of work counters, so calls on one batch run in
+ * call order: a call's stream first waits for the previous call's launches
+ * (an event recorded on that call's stream), whichever stream that was.
+ * Calls on one batch from several host threads at once are not supported.
  */
 fl_status fl_batch_step_rk(fl_batch *batch, fl_limiter limiter, fl_dtype dtype, int rk_order,
                            const double *dt, int64_t nsteps, void *const *theta,

@@ -27,12 +27,14 @@ STATUS_NAMES = ["FL_OK", "FL_EINVAL", "FL_ENOMEM", "FL_ECUDA", "FL_EUNSUPPORTED"
 LIMITERS = {"upwind": 0, "central": 1, "minmod": 2, "vanleer": 3, "superbee": 4, "smart": 5}
 FL_F32, FL_F64 = 0, 1
 FL_RENUMBER = 1
+FL_FIELD_CELL, FL_FIELD_FACE = 0, 1
 
 # Exported symbols of include/fl.h (checked by the ABI test).
 ABI_SYMBOLS = [
     "fl_last_error", "fl_version", "fl_mesh_create_structured", "fl_mesh_create",
     "fl_mesh_create_weighted",
     "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_status", "fl_mesh_destroy",
+    "fl_mesh_to_internal", "fl_mesh_to_user",
     "fl_conv_limited_apply",
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_modulated",
     "fl_step_rk_noalloc", "fl_step_rk_blocked",
@@ -89,6 +91,8 @@ def lib():
                                  ctypes.POINTER(I)]),
             "fl_mesh_status": (I, [P, P]),
             "fl_mesh_destroy": (I, [P]),
+            "fl_mesh_to_internal": (I, [P, I, I, P, P, P]),
+            "fl_mesh_to_user": (I, [P, I, I, P, P, P]),
             "fl_conv_limited_apply": (I, [P, I, I, P, P, P, P, P]),
             "fl_face_selection": (I, [P, I, P, P, P]),
             "fl_workspace_size": (I, [P, I, I, ctypes.POINTER(SZ)]),
@@ -248,6 +252,28 @@ def fl_mesh_status(mesh, stream=None):
 
 def fl_mesh_destroy(mesh):
     _check(lib().fl_mesh_destroy(mesh))
+
+
+def _kind(kind):
+    if kind in ("cell", FL_FIELD_CELL):
+        return FL_FIELD_CELL
+    if kind in ("face", FL_FIELD_FACE):
+        return FL_FIELD_FACE
+    raise ValueError("field kind must be 'cell' or 'face', got %r" % (kind,))
+
+
+def fl_mesh_to_internal(mesh, kind, dtype, src, dst, stream=None):
+    """dst (internal order) <- src (user order) for a cell or face field."""
+    c = dtype_code(dtype)
+    _check(lib().fl_mesh_to_internal(mesh, _kind(kind), c, _fptr(src, c), _fptr(dst, c),
+                                     _stream(stream)))
+
+
+def fl_mesh_to_user(mesh, kind, dtype, src, dst, stream=None):
+    """dst (user order) <- src (internal order) for a cell or face field."""
+    c = dtype_code(dtype)
+    _check(lib().fl_mesh_to_user(mesh, _kind(kind), c, _fptr(src, c), _fptr(dst, c),
+                                 _stream(stream)))
 
 
 def fl_conv_limited_apply(mesh, limiter, dtype, theta_c, u_f, rhs_c, theta_f=None, stream=None):
@@ -480,6 +506,23 @@ class Mesh:
 
     def permutation(self):
         return fl_mesh_permutation(self.handle)
+
+    def to_internal(self, field, kind="cell", stream=None):
+        """A new CUDA tensor holding ``field`` (user order) in the library's
+        internal order (fl_mesh_to_internal; a copy for meshes that were not
+        renumbered)."""
+        import torch
+        out = torch.empty_like(field)
+        fl_mesh_to_internal(self.handle, kind, field.dtype, field, out, stream)
+        return out
+
+    def to_user(self, field, kind="cell", stream=None):
+        """A new CUDA tensor holding ``field`` (internal order) in user order
+        (fl_mesh_to_user)."""
+        import torch
+        out = torch.empty_like(field)
+        fl_mesh_to_user(self.handle, kind, field.dtype, field, out, stream)
+        return out
 
     def close(self):
         if self.handle:

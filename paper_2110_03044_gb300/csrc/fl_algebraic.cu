@@ -313,7 +313,7 @@ fl_status fl_alg_create(int64_t n_cells, int64_t n_faces, const int32_t *face_ce
   const int64_t C = n_cells, F = n_faces;
   for (int64_t f = 0; f < F; ++f) {
     const int32_t a = face_cells[2 * f], b = face_cells[2 * f + 1];
-    if (a < 0 || b < 0 || a >= C || b >= C) return fail(FL_EINVAL, "face %lld: cell out of range", (long long)f);
+    if (a < 0 || b < 0 || a >= C || b >= C) return fail(FL_EINDEX, "face %lld: cell out of range", (long long)f);
     if (a == b) return fail(FL_EINVAL, "face %lld joins cell %d to itself", (long long)f, a);
     if (!(areas[f] > 0) || !std::isfinite(areas[f])) return fail(FL_EINVAL, "face %lld: bad area", (long long)f);
   }

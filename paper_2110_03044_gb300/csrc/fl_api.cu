@@ -62,6 +62,42 @@ addr_range_fn get_addr_range() {
   return fn;
 }
 
+typedef CUresult (*ctx_id_fn)(CUcontext, unsigned long long *);
+
+bool current_context_id(unsigned long long *id) {
+  static ctx_id_fn fn = []() -> ctx_id_fn {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<ctx_id_fn>(f);
+  }();
+  if (fn == nullptr) return false;
+  return fn(nullptr, id) == CUDA_SUCCESS;
+}
+
+cudaError_t set_smem_limit(const void *kernel, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, unsigned long long>, int> done;
+  unsigned long long ctx = 0;
+  if (!current_context_id(&ctx)) {
+    // no context yet: bind the current device's primary context, then ask again
+    cudaFree(nullptr);
+    if (!current_context_id(&ctx))
+      return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(kernel, ctx);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[key] = bytes;
+  return e;
+}
+
 fl_status check_buffer(const void *p, size_t bytes, const char *name) {
   if (bytes == 0) return FL_OK;
   if (p == nullptr) return fail(FL_EINVAL, "%s is NULL", name);
@@ -85,12 +121,56 @@ fl_status check_buffer(const void *p, size_t bytes, const char *name) {
   return FL_OK;
 }
 
+fl_status status_alloc(fl_mesh *m) {
+  void *h = nullptr, *d = nullptr;
+  if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+    return fail(FL_ENOMEM, "status word allocation failed");
+  *static_cast<volatile int *>(h) = 0;
+  if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+    cudaFreeHost(h);
+    return fail(FL_ECUDA, "status word mapping failed");
+  }
+  m->status_host = static_cast<int *>(h);
+  m->status = static_cast<int *>(d);
+  return FL_OK;
+}
+
+void status_free(fl_mesh *m) {
+  if (m->status_host) cudaFreeHost(m->status_host);
+  m->status_host = nullptr;
+  m->status = nullptr;
+}
+
+namespace {
+const char *status_name(int s) {
+  switch (s) {
+    case FL_ETIMEOUT: return "FL_ETIMEOUT (a bounded wait inside a kernel gave up)";
+    case FL_EINDEX: return "FL_EINDEX";
+    default: return "an error";
+  }
+}
+}  // namespace
+
+// The mesh is usable from the calling thread: it lives on the current device
+// and no kernel of an earlier call on it has recorded a device-side error.
+// A recorded error is returned once (and cleared) by the first call that
+// sees it; that call runs nothing.  A kernel still running when the call
+// starts may record its error later: the next call, or fl_mesh_status
+// (which synchronises first), reports it.
 fl_status check_mesh(const fl_mesh *m) {
   if (m == nullptr) return fail(FL_EINVAL, "mesh is NULL");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return fail(FL_ECUDA, "cudaGetDevice failed");
   if (dev != m->device)
     return fail(FL_EINVAL, "mesh was created on device %d but device %d is current", m->device, dev);
+  if (m->status_host != nullptr) {
+    const int h = __atomic_exchange_n(m->status_host, 0, __ATOMIC_ACQ_REL);
+    if (h != 0)
+      return fail((fl_status)h,
+                  "a kernel launched by an earlier call on this mesh recorded %s; this call "
+                  "ran nothing",
+                  status_name(h));
+  }
   return FL_OK;
 }
 
@@ -201,11 +281,9 @@ fl_status fl_mesh_create_structured(int nx, int ny, int nz, double hx, double hy
     na += m->act[a];
   }
   m->F = (int64_t)na * C;
-  if (cudaMalloc(&m->status, sizeof(int)) != cudaSuccess ||
-      cudaMemset(m->status, 0, sizeof(int)) != cudaSuccess) {
-    if (m->status) cudaFree(m->status);
+  if (const fl_status st = status_alloc(m); st != FL_OK) {
     delete m;
-    return fail(FL_ENOMEM, "status word allocation failed");
+    return st;
   }
   *out = m;
   return FL_OK;
@@ -252,22 +330,15 @@ fl_status fl_mesh_info(const fl_mesh *m, int64_t *n_cells, int64_t *n_faces, int
 }
 
 fl_status fl_mesh_status(const fl_mesh *m, void *stream) {
-  FL_TRY(check_mesh(m));
-  if (m->status == nullptr) return FL_OK;
-  int h = 0;
-  cudaStream_t st = as_stream(stream);
-  cudaError_t e = cudaMemcpyAsync(&h, m->status, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess && h != 0) e = cudaMemsetAsync(m->status, 0, sizeof(int), st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "status read");
-  if (h != 0) return fail((fl_status)h, "a kernel on this mesh reported status %d", h);
-  return FL_OK;
+  if (m == nullptr) return fail(FL_EINVAL, "mesh is NULL");
+  const cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronisation");
+  return check_mesh(m);
 }
 
 fl_status fl_mesh_destroy(fl_mesh *m) {
   if (m == nullptr) return FL_OK;
-  if (m->status) cudaFree(m->status);
+  status_free(m);
   if (m->kind == 1) unstruct_free(m);
   delete m;
   return FL_OK;

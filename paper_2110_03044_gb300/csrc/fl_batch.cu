@@ -42,6 +42,10 @@ struct fl_batch {
   void *h_params = nullptr;  // pinned staging
   size_t params_bytes = 0;
   cudaEvent_t params_done = nullptr;
+  // recorded on the caller's stream after every call's last launch; the next
+  // call's stream waits on it before touching the parameter table and the
+  // work counters, so calls on different streams run one after the other
+  cudaEvent_t last_call = nullptr;
   unsigned *d_counters = nullptr;  // one work counter per stage
   // tile lists per z chunk
   std::map<int, std::pair<int2 *, int>> tiles;
@@ -280,24 +284,26 @@ fl_status tune(fl_batch *b, fl_dtype dt, int lim, int rk, const double *dtv, voi
   const int cand[] = {8, 16, 32, 64};
   float best_ms = 1e30f;
   *best = 16;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(FL_ECUDA, "autotune event creation failed");
+  }
+  fl_status s = FL_OK;
   for (int zc : cand) {
     int2 *tiles;
     int nt;
-    fl_status s = get_tiles(b, zc, &tiles, &nt);
-    if (s != FL_OK) return s;
-    if ((s = upload_params(b, dt, rk, zc, dtv, theta, u, ws, pre, st)) != FL_OK) return s;
+    if ((s = get_tiles(b, zc, &tiles, &nt)) != FL_OK) break;
+    if ((s = upload_params(b, dt, rk, zc, dtv, theta, u, ws, pre, st)) != FL_OK) break;
     cudaError_t e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);  // warm-up
-    cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r)
       e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);
-    cudaEventRecord(e1, st);
-    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return cuda_fail(e != cudaSuccess ? e : cudaGetLastError(), "autotune launch");
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "autotune launch");
+      break;
     }
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -308,7 +314,7 @@ fl_status tune(fl_batch *b, fl_dtype dt, int lim, int rk, const double *dtv, voi
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return FL_OK;
+  return s;
 }
 
 }  // namespace
@@ -343,6 +349,7 @@ fl_status fl_batch_create(int n, const fl_mesh *const *meshes, fl_batch **out) {
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_params, b->params_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, MAXSTAGES * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->params_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->last_call, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     fl_batch_destroy(b);
     return fail(FL_ENOMEM, "batch allocation failed");
@@ -384,6 +391,10 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
   if ((s = check_buffer(ws, need, "workspace")) != FL_OK) return s;
   if (nsteps == 0) return FL_OK;
   cudaStream_t st = as_stream(stream);
+  // the previous call's launches (perhaps on another stream) read the
+  // parameter table and the work counters this call rewrites: wait for them
+  if (cudaStreamWaitEvent(st, b->last_call, 0) != cudaSuccess)
+    return fail(FL_ECUDA, "ordering after the previous batched call failed");
   // pre-scaled velocities (FP64) when every dt is positive (keeps signs)
   bool pre = batch_prescales(dt);
   for (int i = 0; i < b->n && pre; ++i) pre = dtv[i] > 0;
@@ -446,6 +457,7 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
       }
     }
   }
+  if (e == cudaSuccess) e = cudaEventRecord(b->last_call, st);
   if (e != cudaSuccess) return cuda_fail(e, "batched step");
   return FL_OK;
 }
@@ -458,6 +470,7 @@ fl_status fl_batch_destroy(fl_batch *b) {
   if (b->h_params) cudaFreeHost(b->h_params);
   if (b->d_counters) cudaFree(b->d_counters);
   if (b->params_done) cudaEventDestroy(b->params_done);
+  if (b->last_call) cudaEventDestroy(b->last_call);
   delete b;
   return FL_OK;
 }

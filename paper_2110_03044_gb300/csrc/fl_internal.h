@@ -42,6 +42,31 @@ int resident_ctas(const void *kernel, int threads, size_t smem);
 // planes it loads before its first output plane) once.
 int pick_zchunk(long long cols, int nz, long long resident, int prologue);
 
+// Identity of the CUDA context current on the calling thread (the driver's
+// cuCtxGetId); false when there is none or the driver lacks the call.  A
+// device reset or a new primary context gives a new identity, so per-context
+// state (function attributes, symbol addresses) is cached under it.
+bool current_context_id(unsigned long long *id);
+
+// Raise `kernel`'s dynamic shared-memory limit to `bytes` in the current
+// context.  The attribute belongs to the context, so the call is made once
+// per (kernel, context) and remembered under a lock: a process driving
+// several GPUs, or one whose device was reset, sets it in every context.
+cudaError_t set_smem_limit(const void *kernel, int bytes);
+
+// The mesh status word (fl_mesh::status) lives in mapped, page-locked host
+// memory: a kernel records a device-side error there with a plain store,
+// and the next call on the mesh reads it on the host without synchronising.
+fl_status status_alloc(fl_mesh *m);
+void status_free(fl_mesh *m);
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void record_status(int *status, int code) {
+  *reinterpret_cast<volatile int *>(status) = code;
+  __threadfence_system();
+}
+#endif
+
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 inline size_t dsize(fl_dtype t) { return t == FL_F64 ? 8 : 4; }
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -100,6 +125,10 @@ struct UnstructDev {
   int32_t *adj_inv_ptr = nullptr;  // [n_cells + 1]
   int32_t *adj_inv_f = nullptr;
   uint8_t *adj_inv_sk = nullptr;
+  // renumbered meshes: internal index of every user cell / user face, for
+  // the field order conversions (fl_mesh_to_internal / fl_mesh_to_user)
+  int32_t *perm_cell = nullptr;  // [n_cells]
+  int32_t *perm_face = nullptr;  // [n_faces]
 };
 
 }  // namespace fl
@@ -107,7 +136,10 @@ struct UnstructDev {
 struct fl_mesh {
   int kind = 0;  // 0 structured, 1 unstructured
   int device = 0;
-  int *status = nullptr;  // device status word (bounded waits record timeouts here)
+  // status word: device address for the kernels (bounded waits record
+  // timeouts there) and host address of the same mapped host memory
+  int *status = nullptr;
+  int *status_host = nullptr;
   int64_t C = 0, F = 0;
   // structured
   int nx = 1, ny = 1, nz = 1;

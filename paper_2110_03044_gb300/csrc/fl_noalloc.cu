@@ -14,8 +14,12 @@
 // every GPU that loads the library holds it until the process exits.  Host
 // code cannot use the array's name as a device address, so the first call on
 // each device (with that device current) asks the runtime for the address
-// with cudaGetSymbolAddress and remembers it.  That first call should
-// therefore come before any stream capture.
+// with cudaGetSymbolAddress and remembers it, together with the identity of
+// the CUDA context it belongs to.  That first call should therefore come
+// before any stream capture.  If the context changes (cudaDeviceReset, or a
+// primary context released and created again), the module is loaded anew at
+// another address: the next call sees the new context identity and looks the
+// address up again instead of handing the kernels a stale pointer.
 //
 // All calls share the one area and it keeps whatever the last call left in
 // it.  Nothing in it has to start at zero: every element a stage reads was
@@ -46,18 +50,24 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[FL_NOALLOC_SCRA
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void *g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};  // context the address belongs to
 
-// Device address of the scratch area on the current device (set-up on the
-// first call per device).
+// Device address of the scratch area on the current device: looked up on the
+// first call per device, and again whenever the current context is not the
+// one the cached address was taken in.
 fl_status scratch_address(int device, void **out) {
   if (device < 0 || device >= kMaxDevices)
     return fl::fail(FL_EUNSUPPORTED, "device ordinal %d out of range", device);
+  unsigned long long ctx = 0;
+  if (!fl::current_context_id(&ctx))
+    return fl::fail(FL_ECUDA, "no CUDA context is current for device %d", device);
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_scratch_addr[device] == nullptr) {
+  if (g_scratch_addr[device] == nullptr || g_scratch_ctx[device] != ctx) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return fl::cuda_fail(e, "cudaGetSymbolAddress(scratch area)");
     g_scratch_addr[device] = p;
+    g_scratch_ctx[device] = ctx;
   }
   *out = g_scratch_addr[device];
   return FL_OK;

@@ -435,13 +435,8 @@ __global__ void __launch_bounds__(FCfg<T>::NT, FCfg<T>::MINB)
 template <class T, int LIM>
 cudaError_t launch_fused(const FParams<T> &p, unsigned grid, cudaStream_t st) {
   auto k = k_struct_rk3_fused<T, LIM>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Geo<T>::BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  const cudaError_t e = set_smem_limit(reinterpret_cast<const void *>(k), (int)Geo<T>::BYTES);
+  if (e != cudaSuccess) return e;
   k<<<grid, Geo<T>::NT, Geo<T>::BYTES, st>>>(p);
   return cudaGetLastError();
 }
@@ -495,14 +490,9 @@ cudaError_t fused_launch_t(const fl_mesh *m, int lim, int rk, double dtime, cons
   p.tiles_x = (m->nx + G::BX - 1) / G::BX;
   p.tiles_y = (m->ny + G::BY - 1) / G::BY;
   const long long cols = (long long)p.tiles_x * p.tiles_y;
-  static bool attr_q = false;
-  if (!attr_q) {
-    if (cudaFuncSetAttribute(k_struct_rk3_fused<T, LIM_SUPERBEE>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)G::BYTES) != cudaSuccess)
-      return cudaErrorNotSupported;
-    attr_q = true;
-  }
+  if (set_smem_limit(reinterpret_cast<const void *>(&k_struct_rk3_fused<T, LIM_SUPERBEE>),
+                     (int)G::BYTES) != cudaSuccess)
+    return cudaErrorNotSupported;
   const int resident = resident_ctas(
       reinterpret_cast<const void *>(&k_struct_rk3_fused<T, LIM_SUPERBEE>), G::NT, G::BYTES);
   p.zchunk = pick_zchunk(cols, m->nz, resident, PRO);

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
     for (int q = 0; q < L; ++q) {
       const int slot = q % RING;
       if (q >= RING && !mbar_wait(&empty[slot], parity(q - RING))) {
-        atomicExch(p.status, (int)FL_ETIMEOUT);
+        record_status(p.status, (int)FL_ETIMEOUT);
         break;
       }
       unsigned char *s = smem + slot * SLOT;
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
     }
     // before the CTA may end: the last copy issued into each slot has landed
     for (int q = max(0, issued - RING); q < issued; ++q)
-      if (!mbar_wait(&full[q % RING], parity(q))) atomicExch(p.status, (int)FL_ETIMEOUT);
+      if (!mbar_wait(&full[q % RING], parity(q))) record_status(p.status, (int)FL_ETIMEOUT);
     return;
   }
 
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
     {
       const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], parity(q)));
       if (!ok) {
-        if (lane == 0) atomicExch(p.status, (int)FL_ETIMEOUT);
+        if (lane == 0) record_status(p.status, (int)FL_ETIMEOUT);
         return;
       }
     }
@@ -451,12 +451,8 @@ template <int LIM, int SEED>
 cudaError_t launch(const TParams &p, const CUtensorMap *maps, unsigned grid, cudaStream_t st) {
   auto k = k_struct_stage_tma<LIM, SEED>;
   const int smem = RING * SLOT;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  const cudaError_t e = set_smem_limit(reinterpret_cast<const void *>(k), smem);
+  if (e != cudaSuccess) return e;
   k<<<grid, dim3(LANES, TY + 1), smem, st>>>(p, maps[0], maps[1], maps[2], maps[3], maps[4], maps[5],
                                          maps[6], maps[7]);
   return cudaGetLastError();
@@ -530,14 +526,9 @@ cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cuda
   const long long cols = (long long)p.tiles_x * p.tiles_y;
   // whole waves of co-resident CTAs (the occupancy query needs the kernel's
   // dynamic shared-memory limit raised first)
-  static bool attr_q = false;
-  if (!attr_q) {
-    if (cudaFuncSetAttribute(k_struct_stage_tma<LIM_SUPERBEE, 1>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             RING * SLOT) != cudaSuccess)
-      return cudaErrorNotSupported;
-    attr_q = true;
-  }
+  if (set_smem_limit(reinterpret_cast<const void *>(&k_struct_stage_tma<LIM_SUPERBEE, 1>),
+                     RING * SLOT) != cudaSuccess)
+    return cudaErrorNotSupported;
   const int resident = resident_ctas(reinterpret_cast<const void *>(&k_struct_stage_tma<LIM_SUPERBEE, 1>),
                                      LANES * (TY + 1), RING * SLOT);
   const int zchunk = pick_zchunk(cols, nz, resident, 3);

@@ -664,7 +664,7 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
     for (int64_t f = lo; f < hi && !err.set.load(); ++f) {
       const int32_t a = face_cells[2 * f], b = face_cells[2 * f + 1];
       if (a < 0 || b < 0 || a >= C || b >= C)
-        return err.put(FL_EINVAL, "face %lld: cell index out of range", f);
+        return err.put(FL_EINDEX, "face %lld: cell index out of range", f);
       if (a == b) return err.put(FL_EINVAL, "face %lld: c0 == c1", f);
       const double *nf = &normals[3 * f];
       if (!(std::fabs(dot3(nf, nf) - 1.0) < 1e-9))
@@ -956,11 +956,9 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   m->kind = 1;
   m->C = C;
   m->F = F;
-  if (cudaMalloc(&m->status, sizeof(int)) != cudaSuccess ||
-      cudaMemset(m->status, 0, sizeof(int)) != cudaSuccess) {
-    if (m->status) cudaFree(m->status);
+  if (const fl_status sst = status_alloc(m); sst != FL_OK) {
     delete m;
-    return fail(FL_ENOMEM, "status word allocation failed");
+    return sst;
   }
   m->renumbered = renum;
   m->cell_perm = cell_new;
@@ -983,6 +981,8 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   if (st == FL_OK) st = upload(ivol_i, &u.inv_vol);
   if (st == FL_OK) st = upload(area_f, &u.area_f);
   if (st == FL_OK) st = upload(ivol_f, &u.inv_vol_f);
+  if (st == FL_OK && renum) st = upload(m->cell_perm, &u.perm_cell);
+  if (st == FL_OK && renum) st = upload(m->face_perm, &u.perm_face);
   if (st == FL_OK && kg > 0) {
     // the stencil in internal numbering: rows by internal face, cells renamed
     std::vector<int32_t> gc((size_t)F * 2 * kg);
@@ -1004,6 +1004,7 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   }
   if (st != FL_OK) {
     unstruct_free(m);
+    status_free(m);
     delete m;
     return st;
   }
@@ -1166,7 +1167,8 @@ void unstruct_free(fl_mesh *m) {
   void *ptrs[] = {u.blk_cell,   u.blk_entry,  u.ent_face,    u.ent_cells, u.cell_slots,
                   u.face_c4,    u.area,       u.vol,         u.inv_vol,   u.area_f,
                   u.inv_vol_f,  u.gen_cell,   u.gen_coef,    u.gen_coef_f, u.adj_cf_ptr,
-                  u.adj_cf,     u.adj_inv_ptr, u.adj_inv_f,  u.adj_inv_sk};
+                  u.adj_cf,     u.adj_inv_ptr, u.adj_inv_f,  u.adj_inv_sk, u.perm_cell,
+                  u.perm_face};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   u = UnstructDev();

@@ -26,6 +26,10 @@ def test_reference_arm_json_line():
     assert line["metric"] == "limited-convection face-updates/s (fused SSP-RK3 step)"
     assert line["unit"] == "face-updates/s" and line["higher_is_better"] is True
     assert line["value"] > 0 and line["steps"] == 2 and line["warmup"] == 1
+    # the same workload keys as the GPU arm's line, and whole SSP-RK3 steps
+    cfg = line["config"]
+    assert cfg["cells"] == 12 ** 3 and cfg["faces"] == 3 * 12 ** 3 and cfg["rk_order"] == 3
+    assert "whole SSP-RK3 step" in line["cpu_baseline"]["sample"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     e2e = line["e2e"]

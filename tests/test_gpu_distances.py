@@ -24,8 +24,7 @@ class DevW(Dev):
     def __init__(self, fl, mesh, renumber=True):
         self.m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
                                     mesh.volumes, renumber=renumber, distances=mesh.distances)
-        self.cp, self.fp, self.flip = self.m.permutation()
-        assert not self.flip.any()
+        self._maps()
 
 
 def _mesh(name):

@@ -2,8 +2,9 @@
 
 Meshes are hexahedral boxes written out face by face, relabelled with seeded
 random permutations and with a seeded half of the faces reoriented (c0 <-> c1,
-normal and u_f negated).  The library renumbers them for locality; fields
-cross the boundary in its internal numbering (fl_mesh_permutation)."""
+normal and u_f negated).  The library renumbers them for locality; the tests
+hold every field in the user's numbering and convert it with the library's
+own calls (fl_mesh_to_internal / fl_mesh_to_user)."""
 import math
 
 import numpy as np
@@ -32,29 +33,31 @@ def _perm_case(shape, seed=2, h=None):
 
 
 class Dev:
-    """Library mesh + numbering maps between user and internal order."""
+    """Library mesh; fields cross to and from its internal numbering through
+    the library's own conversion calls (fl_mesh_to_internal / _to_user)."""
 
     def __init__(self, fl, mesh, renumber=True):
         self.m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
                                     mesh.volumes, renumber=renumber)
-        self.cp, self.fp, self.flip = self.m.permutation()
-        assert not self.flip.any()
+        self._maps()
+
+    def _maps(self):
+        # the published numbering, used only to translate the cell ids that
+        # the selection dump reports (an index output, not a field)
+        self.cp, self.fp, flip = self.m.permutation()
+        assert not flip.any()
 
     def cells_in(self, x, dtype):
-        out = np.empty_like(x)
-        out[self.cp] = x
-        return torch.tensor(out, dtype=dtype, device="cuda")
+        return self.m.to_internal(torch.tensor(x, dtype=dtype, device="cuda"), "cell")
 
     def faces_in(self, x, dtype):
-        out = np.empty_like(x)
-        out[self.fp] = x
-        return torch.tensor(out, dtype=dtype, device="cuda")
+        return self.m.to_internal(torch.tensor(x, dtype=dtype, device="cuda"), "face")
 
     def cells_out(self, t):
-        return t.cpu().double().numpy()[self.cp]
+        return self.m.to_user(t, "cell").cpu().double().numpy()
 
     def faces_out(self, t):
-        return t.cpu().double().numpy()[self.fp]
+        return self.m.to_user(t, "face").cpu().double().numpy()
 
 
 @pytest.mark.parametrize("renumber", [True, False])

@@ -18,13 +18,25 @@ def _create(fl, m, fc=None, nrm=None, ar=None, vol=None, n_cells=None):
                              m.volumes if vol is None else vol, fl.FL_RENUMBER)
 
 
-def test_rejects_out_of_range_cells(fl):
+@pytest.mark.parametrize("bad", ["n_cells", -1])
+def test_rejects_out_of_range_cells(fl, bad):
+    # an index outside [0, n_cells) in the connectivity is FL_EINDEX
     m = _box()
     fc = m.face_cells.copy()
-    fc[5, 1] = m.n_cells
+    fc[5, 1] = m.n_cells if bad == "n_cells" else bad
     with pytest.raises(fl.FLError) as e:
         _create(fl, m, fc=fc)
-    assert e.value.status == fl.FL_EINVAL
+    assert e.value.status == fl.FL_EINDEX
+    assert "out of range" in str(e.value)
+
+
+def test_algebraic_chain_rejects_out_of_range_cells(fl):
+    m = _box()
+    fc = m.face_cells.copy()
+    fc[7, 0] = m.n_cells + 3
+    with pytest.raises(fl.FLError) as e:
+        fl.fl_alg_create(m.n_cells, fc, m.normals, m.areas, m.volumes)
+    assert e.value.status == fl.FL_EINDEX
 
 
 def test_rejects_degenerate_face(fl):
