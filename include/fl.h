@@ -279,6 +279,37 @@ fl_status fl_step_rk(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype, in
                      size_t workspace_bytes, void *stream);
 
 /*
+ * One RK stage of fl_step_rk, for callers that sequence the stages
+ * themselves (a domain decomposition that exchanges halo cells between
+ * stages):
+ *   y = a theta_n + b (x + dt R(x))
+ * with (a, b) = (0, 1) for stage 0 (forward Euler, Algorithm 4; theta_n is
+ * then unused and may be NULL) and, for rk_order 3 (SSP-RK3), (3/4, 1/4) for
+ * stage 1 and (1/3, 2/3) for stage 2 (the weights sum to exactly 1 in the
+ * working precision).  All buffers are device, dtype elements: theta_n, x, y
+ * [n_cells], u_f, w_f [n_faces].  y must not overlap x (a stage reads the
+ * neighbours of x while it writes y); y may be theta_n.  w_f: NULL, or in
+ * FP64 the pre-scaled velocity of fl_velocity_prescale for the same dt,
+ * with which the stage runs the arithmetic of fl_step_rk (the flux product
+ * folded into the cell update) and gives its bits; without it FP64 forms
+ * u_f theta_f per face.  FP32 ignores w_f.  One kernel launch; no workspace.
+ */
+fl_status fl_step_rk_stage(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype, int rk_order,
+                           int stage, double dt, const void *theta_n, const void *x, void *y,
+                           const void *u_f, const void *w_f, void *stream);
+
+/*
+ * w_f = dt (A_f / V) u_f per face (Algorithm 4's M U with the step size:
+ * structured meshes take A/V = 1/h of the face's axis, face-based meshes
+ * w_f = dt A_f u_f with 1/V applied per cell), the velocity fl_step_rk_stage
+ * takes as w_f.  A product that underflows keeps the sign of u_f, so the
+ * upwind side of every face is unchanged.  dt must be finite and > 0.
+ * u_f, w_f: device, [n_faces] dtype elements.
+ */
+fl_status fl_velocity_prescale(const fl_mesh *mesh, fl_dtype dtype, double dt, const void *u_f,
+                               void *w_f, void *stream);
+
+/*
  * fl_step_rk for a time-modulated flow: stage s of step n advects with the
  * face velocity g[n * S + s] * u_f (S = 1 for Euler, 3 for SSP-RK3), the
  * form of the reversing deformation flow of Section 4.1 (eq. rhodonea),

@@ -37,7 +37,7 @@ ABI_SYMBOLS = [
     "fl_mesh_to_internal", "fl_mesh_to_user",
     "fl_conv_limited_apply",
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_modulated",
-    "fl_step_rk_noalloc", "fl_step_rk_blocked",
+    "fl_step_rk_noalloc", "fl_step_rk_blocked", "fl_step_rk_stage", "fl_velocity_prescale",
     "fl_conv_limited_adjoint",
     "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_checkpointed",
     "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
@@ -100,6 +100,8 @@ def lib():
             "fl_step_rk_modulated": (I, [P, I, I, I, D, I64, P, P, P, P, SZ, P]),
             "fl_step_rk_noalloc": (I, [P, I, I, I, D, I64, P, P, P]),
             "fl_step_rk_blocked": (I, [P, I, I, I, D, I64, P, P, P, SZ, P]),
+            "fl_step_rk_stage": (I, [P, I, I, I, I, D, P, P, P, P, P, P]),
+            "fl_velocity_prescale": (I, [P, I, D, P, P, P]),
             "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
             "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
             "fl_step_rk_adjoint": (I, [P, I, I, I, D, I64, I64, P, P, P, P, P, SZ, P]),
@@ -299,6 +301,22 @@ def fl_step_rk(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, workspace
     _check(lib().fl_step_rk(mesh, _lim(limiter), c, int(rk_order), float(dt), int(nsteps),
                             _fptr(theta, c), _fptr(u_f, c), _ptr(workspace),
                             int(workspace_bytes), _stream(stream)))
+
+
+def fl_step_rk_stage(mesh, limiter, dtype, rk_order, stage, dt, theta_n, x, y, u_f, w_f=None,
+                     stream=None):
+    """One RK stage y = a theta_n + b (x + dt R(x)) (see fl.h)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_stage(mesh, _lim(limiter), c, int(rk_order), int(stage), float(dt),
+                                  _fptr(theta_n, c), _fptr(x, c), _fptr(y, c), _fptr(u_f, c),
+                                  _fptr(w_f, c), _stream(stream)))
+
+
+def fl_velocity_prescale(mesh, dtype, dt, u_f, w_f, stream=None):
+    """w_f = dt (A/V) u_f, the velocity fl_step_rk_stage takes in FP64."""
+    c = dtype_code(dtype)
+    _check(lib().fl_velocity_prescale(mesh, c, float(dt), _fptr(u_f, c), _fptr(w_f, c),
+                                      _stream(stream)))
 
 
 def fl_step_rk_blocked(mesh, limiter, dtype, rk_order, dt, nsteps, theta, u_f, workspace,

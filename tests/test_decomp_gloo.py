@@ -1,0 +1,148 @@
+"""The z-slab domain decomposition and its per-stage halo exchange, on the
+host: world_size 1, 2 and 3 gloo groups, with the oracle's stage as the
+per-rank computation (the GPU runs the library's stage kernel instead; see
+test_gpu_decomp.py).
+
+* The slabs cover the planes once, each owning at least the halo depth.
+* A decomposed SSP-RK3 / Euler rollout gives, on every owned plane, the
+  bits of the one-rank decomposed run (the exchange delivers exactly the
+  planes each stage reads) and the whole-mesh oracle to rounding (the cell
+  sums of the wrapped plane 0 run in another face order there).
+* Mass is conserved across the cuts to round-off."""
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+import oracle
+import workloads as W
+from paper_2110_03044_gb300.decomp import HALO, LocalTransport, Slab, TorchTransport, step_rk
+
+
+@pytest.mark.parametrize("nz,world", [(24, 1), (24, 2), (25, 3), (9, 4), (4, 2)])
+def test_slabs_cover_every_plane_once(nz, world):
+    dims = (5, 3, nz)
+    owned = []
+    for r in range(world):
+        s = Slab(dims, r, world)
+        assert s.nz_local >= HALO
+        assert s.local_dims == (5, 3, s.nz_local + 2 * HALO)
+        assert s.down == (r - 1) % world and s.up == (r + 1) % world
+        gp = s.global_planes()
+        assert gp[HALO:HALO + s.nz_local] == list(range(s.lo, s.hi))
+        assert gp[:HALO] == [(s.lo - HALO + k) % nz for k in range(HALO)]
+        owned += list(range(s.lo, s.hi))
+    assert owned == list(range(nz))
+
+
+def test_slab_refuses_too_thin_slabs():
+    with pytest.raises(ValueError):
+        Slab((4, 4, 5), 0, 3)  # 5 planes over 3 ranks: a slab of 1 < halo
+    with pytest.raises(ValueError):
+        Slab((4, 4, 1), 0, 1)
+
+
+def test_local_fields_cut_from_global():
+    dims = (4, 3, 10)
+    s = Slab(dims, 1, 2)
+    g = torch.arange(4 * 3 * 10, dtype=torch.float64)
+    loc = s.local_cells(g)
+    P = 12
+    assert torch.equal(s.owned(loc), g[5 * P:10 * P])
+    assert torch.equal(loc[:P], g[3 * P:4 * P])          # ghost plane 3
+    assert torch.equal(loc[-P:], g[1 * P:2 * P])         # ghost plane 11 -> 1
+    u = torch.arange(3 * 120, dtype=torch.float64)
+    lu = s.local_faces(u, 3)
+    assert lu.numel() == 3 * loc.numel()
+    assert torch.equal(lu[loc.numel():loc.numel() + P], u[120 + 3 * P:120 + 4 * P])
+
+
+def _case():
+    dims = (9, 7, 12)
+    h = (0.7 / 9, 0.9 / 7, 1.1 / 12)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(3)
+    th = rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3)
+    u = 0.3 * W.mixed_sign_velocity(mesh.n_faces, 4)
+    dt = 0.3 * min(h) / np.max(np.abs(u)) / 3
+    return dims, h, mesh, th, u, dt
+
+
+def _oracle_stage(slab, h, lim, rk, dt, u_local):
+    lm = oracle.OracleMesh(W.structured_mesh(*slab.local_dims, *h))
+    uu = u_local.numpy()
+
+    def stage(s, thn, x, y):
+        xn = x.numpy()
+        t = xn if thn is None else thn.numpy()
+        y.copy_(torch.from_numpy(oracle.stage(lm, lim, rk, s, dt, t, xn, uu)))
+
+    return stage
+
+
+def _run_rank(rank, world, lim, rk, nsteps, transport):
+    dims, h, mesh, th, u, dt = _case()
+    slab = Slab(dims, rank, world)
+    tl = slab.local_cells(torch.from_numpy(th)).clone()
+    ul = slab.local_faces(torch.from_numpy(u), 3)
+    a = torch.empty_like(tl)
+    b = torch.empty_like(tl)
+    step_rk(slab, transport, _oracle_stage(slab, h, lim, rk, dt, ul), rk, nsteps, tl, a, b)
+    return slab.lo, slab.hi, slab.owned(tl).numpy().copy()
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, lim, rk, nsteps, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank,) + _run_rank(rank, world, lim, rk, nsteps, TorchTransport()))
+    finally:
+        dist.destroy_process_group()
+
+
+def _gloo_run(world, lim, rk, nsteps):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, lim, rk, nsteps, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    return sorted(out)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1), ("smart", 3)])
+def test_gloo_decomposed_rollout_equals_one_rank(world, lim, rk):
+    dims, h, mesh, th, u, dt = _case()
+    nsteps = 3
+    P = dims[0] * dims[1]
+    # the one-rank decomposed run (its halo comes from itself)
+    lo, hi, one = _run_rank(0, 1, lim, rk, nsteps, LocalTransport())
+    assert (lo, hi) == (0, dims[2])
+    got = np.empty(mesh.n_cells)
+    for _, lo, hi, part in _gloo_run(world, lim, rk, nsteps):
+        got[lo * P:hi * P] = part
+    assert np.array_equal(got, one)  # bit for bit
+    ref = oracle.step(mesh, lim, rk, dt, nsteps, u, th)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    m0 = math.fsum((th * mesh.volumes).tolist())
+    assert abs(math.fsum((got * mesh.volumes).tolist()) - m0) <= 1e-13 * abs(m0)

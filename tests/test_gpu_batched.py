@@ -9,7 +9,6 @@ import torch
 
 import oracle
 import workloads as W
-from tests.patch import patch
 
 pytestmark = pytest.mark.gpu
 
@@ -69,11 +68,11 @@ def test_batch_matches_single_mesh_path(fl, lim, rk, nsteps, dtype):
         m.close()
 
 
-def test_batched_config_full_size(fl):
-    """64 boxes with seeded sizes in [32, 128]^3 (about 34M cells), each with
-    its own curl-of-Fourier-potential velocity and scalar, van Leer, SSP-RK3:
-    one batched step equals 64 single-mesh steps bit for bit; two boxes are
-    spot-checked against the oracle on 13^3 patches; every box conserves."""
+def test_batched_config_equals_single_mesh_path(fl):
+    """64 boxes with seeded sizes in [32, 128]^3 (about 34M cells): one batched
+    FP64 step equals 64 single-mesh steps bit for bit (the same tile code on
+    the same inputs).  Every cell of every box is checked against the oracle
+    in test_gpu_full_size.py."""
     dims = W.batched_box_dims()
     boxes = [W.random_box(d, 1000 + i) for i, d in enumerate(dims)]
     meshes = [fl.Mesh.structured(*d, *b[0].h) for d, b in zip(dims, boxes)]
@@ -90,17 +89,6 @@ def test_batched_config_full_size(fl):
     torch.cuda.synchronize()
     for a, b in zip(th, ref):
         assert torch.equal(a, b)
-    rng = np.random.default_rng(3)
-    for i in (int(rng.integers(0, 64)), int(np.argmax([np.prod(d) for d in dims]))):
-        mesh, th0, u, dt = boxes[i]
-        got = th[i].cpu().numpy()
-        m0 = float(np.sum(th0 * mesh.volumes))
-        assert abs(float(np.sum(got * mesh.volumes)) - m0) <= 1e-12 * max(abs(m0), 1.0) * 10
-        for _ in range(4):
-            c = [int(rng.integers(0, d)) for d in dims[i]]
-            pm, cells, fidx, centre = patch(dims[i], mesh.h, c, 6)
-            r = oracle.step(pm, "vanleer", 3, dt, 1, u[fidx], th0[cells])
-            assert abs(got[cells[centre]] - r[centre]) <= 1e-12 * np.max(np.abs(th0))
     fl.fl_batch_destroy(batch)
     for m in meshes:
         m.close()

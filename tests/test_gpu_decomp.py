@@ -1,0 +1,131 @@
+"""The z-slab decomposition on the GPU: W ranks emulated in one process on one
+GPU, each a host thread with its own local mesh, running the library's stage
+kernel (fl_step_rk_stage) through the same step_rk loop the multi-GPU run
+uses.  The exchange copies ghost planes between the ranks' device buffers
+after a host barrier; every launch and copy goes to the one default stream,
+in order, so no kernel waits on another.
+
+The owned planes of the decomposed rollout must equal fl_step_rk on the
+whole mesh bit for bit: FP64 (with the pre-scaled velocity, the arithmetic of
+fl_step_rk), FP32 on the register tile and on the TMA kernel, Euler and
+SSP-RK3."""
+import threading
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from paper_2110_03044_gb300.decomp import Slab, SlabRollout
+
+pytestmark = pytest.mark.gpu
+
+
+class ThreadGroupTransport:
+    """Exchange among W host threads sharing one GPU: the ghost planes of each
+    rank are copied from its neighbours' owned planes between two barriers."""
+
+    def __init__(self, world):
+        self.world = world
+        self.fields = [None] * world
+        self.bar = threading.Barrier(world)
+
+    def exchange(self, slab, x):
+        P, h, n = slab.plane, slab.halo, slab.nz_local
+        self.fields[slab.rank] = (slab, x)
+        self.bar.wait()  # every rank's stage input is enqueued and registered
+        sd, xd = self.fields[slab.down]
+        su, xu = self.fields[slab.up]
+        x[0:h * P].copy_(xd[sd.nz_local * P:(sd.nz_local + h) * P])
+        x[(h + n) * P:(2 * h + n) * P].copy_(xu[h * P:2 * h * P])
+        self.bar.wait()  # every copy is enqueued before any rank's next stage
+
+
+def _decomposed(fl, world, dims, h, th, u, lim, dtype, rk, dt, nsteps):
+    out = [None] * world
+    err = []
+    tr = ThreadGroupTransport(world)
+    ug = torch.tensor(u, device="cuda")
+
+    def rank(r):
+        try:
+            torch.cuda.set_device(0)
+            slab = Slab(dims, r, world)
+            ro = SlabRollout(slab, h, ug, lim, dtype, dt, transport=tr)
+            tl = ro.local_field(torch.tensor(th, device="cuda"))
+            ro.step(tl, rk, nsteps)
+            torch.cuda.synchronize()
+            out[r] = (slab.lo, slab.hi, slab.owned(tl).cpu())
+            ro.close()
+        except BaseException as e:  # noqa: BLE001 -- reported below
+            err.append(e)
+            tr.bar.abort()
+
+    ts = [threading.Thread(target=rank, args=(r,)) for r in range(world)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if err:
+        raise err[0]
+    P = dims[0] * dims[1]
+    got = torch.empty(P * dims[2], dtype=dtype)
+    for lo, hi, part in out:
+        got[lo * P:hi * P] = part
+    return got
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4])
+@pytest.mark.parametrize("dims,dtype", [((40, 12, 24), torch.float64),
+                                        ((40, 12, 24), torch.float32),
+                                        ((128, 8, 20), torch.float32)])
+@pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1), ("smart", 3)])
+def test_decomposed_rollout_equals_whole_mesh_bitwise(fl, world, dims, dtype, lim, rk):
+    h = tuple(0.7 / d for d in dims)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(5)
+    th = rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3)
+    u = 0.3 * W.mixed_sign_velocity(mesh.n_faces, 6)
+    dt = 0.3 * min(h) / np.max(np.abs(u)) / 3
+    nsteps = 3
+    got = _decomposed(fl, world, dims, h, th, u, lim, dtype, rk, dt, nsteps)
+    m = fl.Mesh.structured(*dims, *h)
+    ref = torch.tensor(th, dtype=dtype, device="cuda")
+    fl.step_rk(m, lim, ref, torch.tensor(u, dtype=dtype, device="cuda"), dt, nsteps,
+               rk_order=rk)
+    m.close()
+    assert torch.equal(got, ref.cpu())
+
+
+def test_stage_entry_point_composes_to_step_rk(fl):
+    # three fl_step_rk_stage calls (FP64, pre-scaled velocity) give the bits
+    # of one fl_step_rk SSP-RK3 step; without w_f the FP64 stage forms the
+    # flux per face and agrees to rounding
+    dims = (33, 10, 7)
+    h = (0.1, 0.2, 0.3)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(8)
+    th0 = torch.tensor(rng.uniform(-1, 1, mesh.n_cells), device="cuda")
+    u = torch.tensor(0.3 * W.mixed_sign_velocity(mesh.n_faces, 9), device="cuda")
+    dt = 0.05
+    m = fl.Mesh.structured(*dims, *h)
+    ref = th0.clone()
+    fl.step_rk(m, "smart", ref, u, dt, 1, rk_order=3)
+    for w in (torch.empty_like(u), None):
+        if w is not None:
+            fl.fl_velocity_prescale(m.handle, torch.float64, dt, u, w)
+        th = th0.clone()
+        a, b = torch.empty_like(th), torch.empty_like(th)
+        fl.fl_step_rk_stage(m.handle, "smart", torch.float64, 3, 0, dt, None, th, a, u, w)
+        fl.fl_step_rk_stage(m.handle, "smart", torch.float64, 3, 1, dt, th, a, b, u, w)
+        fl.fl_step_rk_stage(m.handle, "smart", torch.float64, 3, 2, dt, th, b, th, u, w)
+        if w is not None:
+            assert torch.equal(th, ref)
+        else:
+            assert float((th - ref).abs().max() / ref.abs().max()) <= 1e-14
+    with pytest.raises(fl.FLError) as e:  # y must not overlap x
+        fl.fl_step_rk_stage(m.handle, "smart", torch.float64, 3, 0, dt, None, th, th, u, None)
+    assert e.value.status == fl.FL_EINVAL
+    with pytest.raises(fl.FLError):  # no stage 1 in forward Euler
+        fl.fl_step_rk_stage(m.handle, "smart", torch.float64, 1, 1, dt, th, a, b, u, None)
+    m.close()

@@ -1,0 +1,246 @@
+"""The method's degenerate inputs through every kernel family, against the
+oracle.
+
+The scalar is drawn from a small set of values (workloads.quantized_field):
+neighbours are often equal, so d_u == 0 (reading: theta_f = theta_C) and
+d_U == 0 (r = 0) occur everywhere; differences in ratios 1/5, 1/2, 1, 2 and
+5 put r exactly on the limiters' kinks (minmod at 1, superbee at 1/2, 1, 2,
+SMART at 1/5 and 5), where the strict ordered tests break the tie; and
+subnormal neighbours of 0 give a subnormal d_u, so that r overflows to
++-inf.  Face velocities include +0 and -0, which select the -1 side.
+
+Covered: the FP64 structured stage tile, the FP32 TMA kernel and the FP32
+register tile, the 1D line kernels (one CTA and a cluster), the face-based
+kernels on permuted and reoriented hexahedra and on tetrahedra, the batched
+persistent kernel, and the adjoints (the structured stage adjoint that reads
+stored branch codes, and the face-based adjoint), where a tie decides the
+branch of the derivative.  Tolerances are the parity bar: 1e-12 relative
+in FP64 and 1e-5 in FP32 per step; the selection is bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+LIMS = ["upwind", "central", "minmod", "vanleer", "superbee", "smart"]
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+DT_NAME = {torch.float64: "f64", torch.float32: "f32"}
+
+# FP64 shapes take the stage tile (or the line kernels); in FP32 (132, 9, 7)
+# takes the TMA kernel and (37, 21, 13) / (40, 9, 1) the register tile
+STRUCT_SHAPES = [(37, 21, 13), (132, 9, 7), (40, 9, 1), (100, 1, 1), (12, 1, 1)]
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _cast(x, dtype):
+    return x.astype(np.float32).astype(np.float64) if dtype == torch.float32 else x
+
+
+def _dev(x, dtype):
+    return torch.tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+def _struct_case(shape, dtype, seed):
+    h = (0.7 / shape[0], 0.9 / shape[1], 1.1 / shape[2])
+    mesh = W.structured_mesh(*shape, *h)
+    th = W.quantized_field(mesh.n_cells, seed, DT_NAME[dtype])
+    u = _cast(W.edge_velocity(mesh.n_faces, seed + 1), dtype)
+    return mesh, th, u
+
+
+def _dt(mesh, u):
+    return 0.3 * min(mesh.h) / max(np.max(np.abs(u)), 1e-300) / 3
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lim", LIMS)
+@pytest.mark.parametrize("shape", STRUCT_SHAPES)
+def test_structured_apply_edge_cases(fl, shape, lim, dtype):
+    mesh, th, u = _struct_case(shape, dtype, 21)
+    m = fl.Mesh.structured(*shape, *mesh.h)
+    R, thf = fl.conv_limited_apply(m, lim, _dev(th, dtype), _dev(u, dtype), want_theta_f=True)
+    ref = oracle.face_values(mesh, lim, th, u)
+    assert _rel(thf.cpu().double().numpy(), ref["theta_f"]) <= TOL[dtype]
+    scale = np.max(np.abs(u)) * np.max(np.abs(th)) / min(mesh.h)
+    assert np.max(np.abs(R.cpu().double().numpy() - oracle.rhs(mesh, lim, th, u))) <= \
+        4 * TOL[dtype] * scale
+    sel = fl.face_selection(m, _dev(u, dtype)).cpu().numpy()
+    assert np.array_equal(sel[:, 0], ref["s"]) and np.array_equal(sel[:, 1], ref["C"])
+    m.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("rk", [1, 3])
+@pytest.mark.parametrize("lim", LIMS)
+@pytest.mark.parametrize("shape", STRUCT_SHAPES)
+def test_structured_step_edge_cases(fl, shape, lim, rk, dtype):
+    mesh, th, u = _struct_case(shape, dtype, 23)
+    dt = _dt(mesh, u)
+    m = fl.Mesh.structured(*shape, *mesh.h)
+    g = _dev(th, dtype)
+    fl.step_rk(m, lim, g, _dev(u, dtype), dt, 1, rk_order=rk)
+    ref = oracle.step(mesh, lim, rk, dt, 1, u, th)
+    assert _rel(g.cpu().double().numpy(), ref) <= TOL[dtype]
+    m.close()
+
+
+def _face_mesh(name):
+    if name == "hex_permuted":
+        base = W.structured_mesh(11, 7, 6, 0.7 / 11, 0.9 / 7, 1.1 / 6)
+        return W.permuted_mesh(base, seed=5)[0]
+    return W.tet_mesh(4)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lim", LIMS)
+@pytest.mark.parametrize("name", ["hex_permuted", "tet"])
+def test_face_based_edge_cases(fl, name, lim, dtype):
+    mesh = _face_mesh(name)
+    th = W.quantized_field(mesh.n_cells, 31, DT_NAME[dtype])
+    u = _cast(W.edge_velocity(mesh.n_faces, 32), dtype)
+    m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
+                           mesh.volumes, renumber=True)
+    thi = m.to_internal(_dev(th, dtype), "cell")
+    ui = m.to_internal(_dev(u, dtype), "face")
+    R = torch.empty_like(thi)
+    thf = torch.empty(mesh.n_faces, dtype=dtype, device="cuda")
+    fl.fl_conv_limited_apply(m.handle, lim, dtype, thi, ui, R, thf)
+    ref = oracle.face_values(mesh, lim, th, u)
+    assert _rel(m.to_user(thf, "face").cpu().double().numpy(), ref["theta_f"]) <= TOL[dtype]
+    scale = np.max(np.abs(u)) * np.max(np.abs(th)) * np.max(mesh.areas) / np.min(mesh.volumes)
+    assert np.max(np.abs(m.to_user(R, "cell").cpu().double().numpy() -
+                         oracle.rhs(mesh, lim, th, u))) <= 8 * TOL[dtype] * scale
+    dt = 0.05 * np.min(mesh.volumes) / np.max(mesh.areas) / np.max(np.abs(u))
+    for rk in (1, 3):
+        g = thi.clone()
+        ws = torch.empty(fl.fl_workspace_size(m.handle, dtype, rk), dtype=torch.uint8,
+                         device="cuda")
+        fl.fl_step_rk(m.handle, lim, dtype, rk, dt, 1, g, ui, ws, ws.numel())
+        got = m.to_user(g, "cell").cpu().double().numpy()
+        assert _rel(got, oracle.step(mesh, lim, rk, dt, 1, u, th)) <= TOL[dtype]
+    m.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "superbee", "smart"])
+def test_batched_edge_cases(fl, lim, dtype):
+    shapes = [(33, 17, 9), (40, 12, 5), (8, 8, 8), (21, 14, 1)]
+    boxes = [_struct_case(sh, dtype, 40 + i) for i, sh in enumerate(shapes)]
+    meshes = [fl.Mesh.structured(*b[0].dims, *b[0].h) for b in boxes]
+    batch = fl.fl_batch_create([mm.handle for mm in meshes])
+    th = [_dev(b[1], dtype) for b in boxes]
+    us = [_dev(b[2], dtype) for b in boxes]
+    dts = [_dt(b[0], b[2]) for b in boxes]
+    nb = fl.fl_batch_workspace_size(batch, dtype, 3)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    fl.fl_batch_step_rk(batch, lim, dtype, 3, dts, 1, th, us, ws, nb)
+    for (mesh, t0, u), g, dt in zip(boxes, th, dts):
+        ref = oracle.step(mesh, lim, 3, dt, 1, u, t0)
+        assert _rel(g.cpu().double().numpy(), ref) <= TOL[dtype]
+    fl.fl_batch_destroy(batch)
+    for mm in meshes:
+        mm.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lim", LIMS)
+@pytest.mark.parametrize("shape", [(37, 21, 13), (40, 9, 1), (100, 1, 1)])
+def test_structured_operator_adjoint_edge_cases(fl, shape, lim, dtype):
+    mesh, th, u = _struct_case(shape, dtype, 51)
+    mu = _cast(np.random.default_rng(52).normal(size=mesh.n_cells), dtype)
+    m = fl.Mesh.structured(*shape, *mesh.h)
+    out = torch.empty(mesh.n_cells, dtype=dtype, device="cuda")
+    fl.fl_conv_limited_adjoint(m.handle, lim, dtype, _dev(th, dtype), _dev(u, dtype),
+                               _dev(mu, dtype), out)
+    ref = oracle.rhs_adjoint(mesh, lim, th, u, mu)
+    scale = np.max(np.abs(u)) * np.max(np.abs(mu)) / min(mesh.h)
+    assert np.max(np.abs(out.cpu().double().numpy() - ref)) <= 8 * TOL[dtype] * scale
+    m.close()
+
+
+@pytest.mark.parametrize("rk", [1, 3])
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "superbee", "smart"])
+def test_structured_gradient_edge_cases(fl, lim, rk):
+    # the reverse sweep recomputes the forward stages, storing the branch code
+    # of every face (piecewise-linear limiters), and the stage adjoint reads
+    # them: at a tie the code decides which one-sided derivative is taken
+    shape = (24, 13, 9)
+    mesh, th, u = _struct_case(shape, torch.float64, 61)
+    dt = _dt(mesh, u)
+    nsteps, every = 3, 2
+    tgt = np.random.default_rng(62).normal(size=mesh.n_cells)
+    _, g_ref = oracle.gradient(mesh, lim, rk, dt, nsteps, u, th, tgt)
+    thT = oracle.step(mesh, lim, rk, dt, nsteps, u, th)
+    m = fl.Mesh.structured(*shape, *mesh.h)
+    nb = fl.fl_adjoint_workspace_size(m.handle, torch.float64, rk, nsteps, every)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    g = torch.empty(mesh.n_cells, dtype=torch.float64, device="cuda")
+    fl.fl_step_rk_adjoint(m.handle, lim, torch.float64, rk, dt, nsteps, every, _dev(th, g.dtype),
+                          _dev(u, g.dtype), _dev(thT - tgt, g.dtype), g, ws, nb)
+    assert np.max(np.abs(g.cpu().numpy() - g_ref)) <= 1e-11 * np.max(np.abs(g_ref))
+    m.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lim", LIMS)
+@pytest.mark.parametrize("name", ["hex_permuted", "tet"])
+def test_face_based_adjoint_edge_cases(fl, name, lim, dtype):
+    mesh = _face_mesh(name)
+    th = W.quantized_field(mesh.n_cells, 71, DT_NAME[dtype])
+    u = _cast(W.edge_velocity(mesh.n_faces, 72), dtype)
+    mu = _cast(np.random.default_rng(73).normal(size=mesh.n_cells), dtype)
+    m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
+                           mesh.volumes, renumber=True)
+    out = torch.empty(mesh.n_cells, dtype=dtype, device="cuda")
+    fl.fl_conv_limited_adjoint(m.handle, lim, dtype, m.to_internal(_dev(th, dtype), "cell"),
+                               m.to_internal(_dev(u, dtype), "face"),
+                               m.to_internal(_dev(mu, dtype), "cell"), out)
+    ref = oracle.rhs_adjoint(mesh, lim, th, u, mu)
+    scale = np.max(np.abs(u)) * np.max(np.abs(mu)) * np.max(mesh.areas) / np.min(mesh.volumes)
+    got = m.to_user(out, "cell").cpu().double().numpy()
+    assert np.max(np.abs(got - ref)) <= 8 * TOL[dtype] * scale
+    m.close()
+
+
+@pytest.mark.parametrize("lim", ["minmod", "superbee", "smart"])
+def test_face_based_gradient_edge_cases(fl, lim):
+    mesh = _face_mesh("hex_permuted")
+    th = W.quantized_field(mesh.n_cells, 81)
+    u = W.edge_velocity(mesh.n_faces, 82)
+    dt = 0.05 * np.min(mesh.volumes) / np.max(mesh.areas) / np.max(np.abs(u))
+    nsteps, every = 3, 2
+    tgt = np.random.default_rng(83).normal(size=mesh.n_cells)
+    _, g_ref = oracle.gradient(mesh, lim, 3, dt, nsteps, u, th, tgt)
+    thT = oracle.step(mesh, lim, 3, dt, nsteps, u, th)
+    m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
+                           mesh.volumes, renumber=True)
+    f64 = torch.float64
+    nb = fl.fl_adjoint_workspace_size(m.handle, f64, 3, nsteps, every)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    g = torch.empty(mesh.n_cells, dtype=f64, device="cuda")
+    fl.fl_step_rk_adjoint(m.handle, lim, f64, 3, dt, nsteps, every,
+                          m.to_internal(_dev(th, f64), "cell"),
+                          m.to_internal(_dev(u, f64), "face"),
+                          m.to_internal(_dev(thT - tgt, f64), "cell"), g, ws, nb)
+    got = m.to_user(g, "cell").cpu().numpy()
+    assert np.max(np.abs(got - g_ref)) <= 1e-11 * np.max(np.abs(g_ref))
+    m.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "superbee", "smart"])
+def test_blocked_step_edge_cases(fl, lim, dtype):
+    shape = (37, 21, 13)
+    mesh, th, u = _struct_case(shape, dtype, 91)
+    dt = _dt(mesh, u)
+    m = fl.Mesh.structured(*shape, *mesh.h)
+    g = _dev(th, dtype)
+    fl.step_rk_blocked(m, lim, g, _dev(u, dtype), dt, 1, rk_order=3)
+    assert _rel(g.cpu().double().numpy(), oracle.step(mesh, lim, 3, dt, 1, u, th)) <= TOL[dtype]
+    m.close()

@@ -13,7 +13,6 @@ import torch
 
 import oracle
 import workloads as W
-from tests.patch import patch
 
 pytestmark = pytest.mark.gpu
 
@@ -141,34 +140,3 @@ def test_equals_structured_path(fl):
     assert _rel(un, gs.cpu().numpy()) <= 1e-13
     d.m.close()
     ms.close()
-
-
-def test_full_size_256_permuted_sampled(fl):
-    """Configuration 2 at full size: 256^3 hex mesh, seeded permutations,
-    half the faces reoriented, SMART, one SSP-RK3 step in the benchmark's
-    launch configuration; 16 sampled cells against the oracle on 13^3
-    patches of the unpermuted mesh, and conservation."""
-    n = 256
-    wl = W.config_taylor_green(n=n, seed=1, nsteps=1, limiter="smart")
-    pm, cp, fp, flip = W.permuted_mesh(wl.mesh, seed=2)
-    up = W.permute_face_field(wl.u, fp, flip)
-    thp = W.permute_cell_field(wl.theta0, cp)
-    d = Dev(fl, pm)
-    g = d.cells_in(thp, torch.float64)
-    ws = torch.empty(fl.fl_workspace_size(d.m.handle, torch.float64, 3), dtype=torch.uint8,
-                     device="cuda")
-    rws = torch.empty(fl.fl_reduce_workspace_size(), dtype=torch.uint8, device="cuda")
-    m0 = fl.fl_reduce_mass(d.m.handle, torch.float64, g, rws)
-    fl.fl_step_rk(d.m.handle, "smart", torch.float64, 3, wl.dt, 1, g,
-                  d.faces_in(up, torch.float64), ws, ws.numel())
-    m1 = fl.fl_reduce_mass(d.m.handle, torch.float64, g, rws)
-    assert abs(m1 - m0) <= 1e-12 * abs(m0)
-    got = d.cells_out(g)[cp]  # structured numbering
-    rng = np.random.default_rng(9)
-    scale = np.max(np.abs(wl.theta0))
-    for _ in range(16):
-        c = rng.integers(0, n, 3)
-        pmesh, cells, fidx, centre = patch((n, n, n), wl.mesh.h, c, 6)
-        ref = oracle.step(pmesh, "smart", 3, wl.dt, 1, wl.u[fidx], wl.theta0[cells])
-        assert abs(got[cells[centre]] - ref[centre]) <= 1e-12 * scale
-    d.m.close()

@@ -552,6 +552,41 @@ def random_field(n, seed, scale=1.0):
     return np.random.default_rng(seed).normal(0.0, scale, n)
 
 
+# Values whose pairwise differences give the gradient ratio's exact edge
+# cases: equal neighbours (d_u = 0, d_U = 0), ratios exactly on the limiters'
+# kinks (1/5, 1/2, 1, 2, 5 and their negatives: e.g. 0, 1, 6 gives 1/5 and
+# 0, 5, 6 gives 5), signed zeros, and subnormal neighbours of 0 whose
+# difference makes r overflow to +-inf.
+QUANTIZED_VALUES = (0.0, -0.0, 0.5, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0, -1.0, -0.5)
+
+
+def quantized_field(n, seed, dtype="f64", repeat=0.4):
+    """Cell values drawn from QUANTIZED_VALUES plus +-1 and +2 smallest
+    subnormals of the dtype; a fraction ``repeat`` of the cells copies the
+    value of the cell before it (plateaus), so equal neighbours are common
+    along every axis."""
+    tiny = float(np.finfo(np.float64 if dtype == "f64" else np.float32).smallest_subnormal)
+    vals = np.array(QUANTIZED_VALUES + (tiny, 2.0 * tiny, -tiny))
+    rng = np.random.default_rng(seed)
+    th = vals[rng.integers(0, len(vals), n)]
+    rep = rng.random(n) < repeat
+    for i in np.flatnonzero(rep):
+        if i > 0:
+            th[i] = th[i - 1]
+    return th
+
+
+def edge_velocity(n_faces, seed, scale=0.3):
+    """Face velocities of both signs with exact +0 and -0 entries (both select
+    the -1 side) among random magnitudes."""
+    rng = np.random.default_rng(seed)
+    u = scale * rng.uniform(-1.0, 1.0, n_faces)
+    r = rng.random(n_faces)
+    u[r < 0.08] = 0.0
+    u[(r >= 0.08) & (r < 0.12)] = -0.0
+    return u
+
+
 def mixed_sign_velocity(n_faces, seed, zero_fraction=0.1):
     """Random face velocities with both signs and some exact zeros (and one
     negative zero) for upwind-selection tests."""
