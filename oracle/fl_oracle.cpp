@@ -133,6 +133,9 @@ double psi_branch(int lim, double r, double *dpsi) {
       *dpsi = 0.0; return 2.0;
     case L_SMART:
       if (r <= 0.0) { *dpsi = 0.0; return 0.0; }
+      // r = +inf (a subnormal d_u) lies on the cap; the test below would
+      // compare inf <= inf
+      if (std::isinf(r)) { *dpsi = 0.0; return 4.0; }
       if (2.0 * r <= 0.25 + 0.75 * r) { *dpsi = 2.0; return 2.0 * r; }
       if (0.25 + 0.75 * r <= 4.0) { *dpsi = 0.75; return 0.25 + 0.75 * r; }
       *dpsi = 0.0; return 4.0;
@@ -180,9 +183,13 @@ FaceEval eval_face(const OMesh &m, int lim, const double *th, const double *u, i
   acc = dist_face(m, acc, f);
   e.dU = (e.s > 0) ? acc : -acc;
   // eq. (rf) and eq. (FL-UP); a zero denominator keeps the upwind value.
+  // Psi there is 0 (the upwind side of the kink at d_u = 0), except for the
+  // central reconstruction, whose Psi = 1 does not depend on r: its face
+  // value theta_C + d_u / 2 is linear through d_u = 0 (eq. FL-CD with F = 0),
+  // and the tangent-linear model takes that slope.
   if (e.du == 0.0) {
     e.r = std::nan("");
-    e.psi = 0.0;
+    e.psi = (lim == L_CENTRAL) ? 1.0 : 0.0;
     e.dpsi = 0.0;
     e.thf = th[e.C];
   } else {
@@ -219,6 +226,16 @@ void rhs(const OMesh &m, int lim, const double *th, const double *u, double *R,
   }
 }
 
+// Coefficient of d(d_u) in the tangent-linear face value, (Psi - Psi' r)/2.
+// On a branch where Psi is constant (Psi' = 0) theta_f = theta_C + Psi d_u/2
+// is linear in d_u with slope Psi/2 for every r, r = +-inf included (a
+// subnormal d_u beside a normal d_U overflows r): the product Psi' r is zero
+// there, not 0 * inf.
+inline double tlm_alpha(const FaceEval &e) {
+  const double pr = (e.dpsi != 0.0) ? e.dpsi * e.r : 0.0;
+  return 0.5 * (e.psi - pr);
+}
+
 // Tangent-linear of theta_f: returns d theta_f for input perturbation dth.
 double face_tlm(const OMesh &m, const FaceEval &e, const double *dth, int64_t f) {
   const double ddu = dth[e.D] - dth[e.C];
@@ -231,10 +248,10 @@ double face_tlm(const OMesh &m, const FaceEval &e, const double *dth, int64_t f)
   }
   acc = dist_face(m, acc, f);
   const double ddU = (e.s > 0) ? acc : -acc;
-  if (e.du == 0.0) return dth[e.C];
+  if (e.du == 0.0) return dth[e.C] + 0.5 * e.psi * ddu;
   // theta_f = theta_C + Psi(r) du / 2, r = dU / du
   //   d theta_f = d theta_C + (Psi - Psi' r)/2 d du + Psi'/2 d dU
-  const double alpha = 0.5 * (e.psi - e.dpsi * e.r);
+  const double alpha = tlm_alpha(e);
   const double beta = 0.5 * e.dpsi;
   return dth[e.C] + alpha * ddu + beta * ddU;
 }
@@ -269,10 +286,11 @@ void rhs_adjoint(const OMesh &m, int lim, const double *th, const double *u, con
     // R_c0 gets -phi/V_c0, R_c1 gets +phi/V_c1
     const double g = u[f] * m.area[f] * (mu[m.c1[f]] / m.vol[m.c1[f]] - mu[m.c0[f]] / m.vol[m.c0[f]]);
     if (e.du == 0.0) {
-      out[e.C] += g;
+      out[e.C] += g * (1.0 - 0.5 * e.psi);
+      out[e.D] += g * (0.5 * e.psi);
       continue;
     }
-    const double alpha = 0.5 * (e.psi - e.dpsi * e.r);
+    const double alpha = tlm_alpha(e);
     const double beta = 0.5 * e.dpsi;
     out[e.C] += g * (1.0 - alpha);
     out[e.D] += g * alpha;

@@ -29,6 +29,22 @@ __global__ void k_smart(const double *p, const double *q, int *piece, int count)
   piece[i] = fl::smart_piece<double>(F::bits(p[i]), F::bits(q[i]), true);
 }
 
+// van Leer's paired-FP32 quotient and SMART's integer middle piece, as the
+// bit patterns the limiter uses (inputs p, q > 0 as doubles)
+__global__ void k_vl_ff(const double *p, const double *q, unsigned long long *g, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  using F = fl::FT<double>;
+  g[i] = F::vl_quot(F::bits(p[i]), F::bits(q[i]));
+}
+
+__global__ void k_smart_mid(const double *p, const double *q, unsigned long long *g, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  using F = fl::FT<double>;
+  g[i] = F::smart_mid(F::bits(p[i]), F::bits(q[i]));
+}
+
 template <class T>
 int to_device(const T *h, T **d, int count) {
   if (cudaMalloc(d, sizeof(T) * (size_t)count) != cudaSuccess) return 1;
@@ -85,5 +101,27 @@ extern "C" int probe_smart(const double *p, const double *q, int *piece, int cou
   cudaFree(dp);
   cudaFree(dq);
   cudaFree(dk);
+  return rc;
+}
+
+// g: the bits of FT<double>::vl_quot (mode 0) or FT<double>::smart_mid
+// (mode 1) for each (p, q).  Host arrays of count.
+extern "C" int probe_limiter_term(const double *p, const double *q, unsigned long long *g,
+                                  int count, int mode) {
+  double *dp = nullptr, *dq = nullptr;
+  unsigned long long *dg = nullptr;
+  int rc = to_device(p, &dp, count) | to_device(q, &dq, count) |
+           to_device<unsigned long long>(nullptr, &dg, count);
+  if (rc == 0) {
+    if (mode == 0)
+      k_vl_ff<<<(count + 255) / 256, 256>>>(dp, dq, dg, count);
+    else
+      k_smart_mid<<<(count + 255) / 256, 256>>>(dp, dq, dg, count);
+    rc = cudaMemcpy(g, dg, sizeof(unsigned long long) * (size_t)count, cudaMemcpyDeviceToHost) !=
+         cudaSuccess;
+  }
+  cudaFree(dp);
+  cudaFree(dq);
+  cudaFree(dg);
   return rc;
 }

@@ -8,7 +8,11 @@ small probe compiled against the library's own header (fl_face.cuh):
   it to the IEEE division;
 * SMART's piece test on the integer pipe (r >= 5, r <= 1/5 for r = p / q):
   against the exact decision in rational arithmetic, including ties, inputs
-  one ulp either side of the boundaries, and subnormal operands."""
+  one ulp either side of the boundaries, and subnormal operands;
+* the FP64 limiter terms formed off the FP64 pipe: van Leer's p q / (p + q)
+  in paired FP32 against the exact rational quotient (relative error below
+  2^-45), and SMART's middle piece (q + 3p) / 8 in 64-bit integers, which
+  must be the correctly rounded value."""
 import ctypes
 import os
 import subprocess
@@ -37,6 +41,7 @@ def probe(tmp_path_factory):
     lib.probe_quot.argtypes = [P, P, P, P, ctypes.c_int]
     lib.probe_quot32.argtypes = [P, P, P, P, ctypes.c_int]
     lib.probe_smart.argtypes = [P, P, P, ctypes.c_int]
+    lib.probe_limiter_term.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int]
     return lib
 
 
@@ -154,3 +159,47 @@ def test_smart_piece_is_the_exact_decision(probe):
     bad = np.nonzero(piece != want)[0]
     assert bad.size == 0, [(p[i], q[i], piece[i], want[i]) for i in bad[:5]]
     assert {1, 2, 3} <= set(want.tolist())
+
+
+def _term(probe, p, q, mode):
+    p = np.ascontiguousarray(p, np.float64)
+    q = np.ascontiguousarray(q, np.float64)
+    g = np.empty(len(p), np.uint64)
+    assert probe.probe_limiter_term(_ptr(p), _ptr(q), _ptr(g), len(p), mode) == 0
+    return g.view(np.float64)
+
+
+def test_van_leer_paired_fp32_quotient_against_exact(probe):
+    rng = np.random.default_rng(7)
+    k = 30000
+    p = rng.uniform(1.0, 2.0, k) * 2.0 ** rng.integers(-1000, 1000, k)
+    # the other operand within 2^-70 .. 2^70 of p (all exponent gaps, including
+    # the d >= 60 shortcut), equal to p, or one ulp from it
+    q = p * 2.0 ** rng.uniform(-70, 70, k)
+    q[:500] = p[:500]
+    q[500:1000] = np.nextafter(p[500:1000], np.inf)
+    ok = (q > 2.0 ** -1018) & (q < 2.0 ** 1020)
+    p, q = p[ok], q[ok]
+    g = _term(probe, p, q, 0)
+    worst = 0.0
+    for a, b, x in zip(p, q, g):
+        fa, fb = Fraction(float(a)), Fraction(float(b))
+        exact = fa * fb / (fa + fb)
+        worst = max(worst, float(abs(Fraction(float(x)) - exact) / exact))
+    assert worst <= 2.0 ** -45, worst
+
+
+def test_smart_middle_piece_is_correctly_rounded(probe):
+    rng = np.random.default_rng(8)
+    k = 30000
+    q = rng.uniform(1.0, 2.0, k) * 2.0 ** rng.integers(-1000, 1000, k)
+    p = q * rng.uniform(0.2, 5.0, k)
+    # exact ties of the rounding: q + 3p one bit beyond 53 significant bits
+    t = 2.0 ** rng.integers(-900, 900, 300).astype(np.float64)
+    p = np.concatenate([p, t, t * (1 + 2.0 ** -52)])
+    q = np.concatenate([q, t * (1 + 2.0 ** -51), t])
+    g = _term(probe, p, q, 1)
+    want = np.array([float((Fraction(float(b)) + 3 * Fraction(float(a))) / 8)
+                     for a, b in zip(p, q)])
+    bad = np.nonzero(g != want)[0]
+    assert bad.size == 0, [(p[i], q[i], g[i], want[i]) for i in bad[:5]]

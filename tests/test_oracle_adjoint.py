@@ -74,3 +74,44 @@ def test_gradient_matches_tlm_and_fd(rk, lim):
                                        wl.theta0 - eps * v) - tgt) ** 2)
         fd = (Jp - Jm) / (2 * eps)
         assert abs(fd - dJ_adj) <= 1e-6 * abs(dJ_adj) + 1e-9
+
+
+@pytest.mark.parametrize("rk", [1, 3])
+def test_central_tlm_is_the_linear_map_through_flat_faces(rk):
+    # Psi = 1 for every r: the central scheme is linear in theta, d_u == 0
+    # faces included (their guarded value theta_C equals theta_C + d_u / 2),
+    # so its tangent-linear model applied to v is the forward step of v
+    # itself -- on a field full of plateaus (many faces with d_u == 0)
+    wl = _setup(n=7, lim="central")
+    th = W.quantized_field(wl.mesh.n_cells, 5)
+    v = np.random.default_rng(6).normal(size=wl.mesh.n_cells)
+    _, dth = oracle.step_tlm(wl.mesh, "central", rk, wl.dt, 2, wl.u, th, v)
+    lin = oracle.step(wl.mesh, "central", rk, wl.dt, 2, wl.u, v)
+    assert np.max(np.abs(dth - lin)) <= 1e-13 * np.max(np.abs(lin))
+
+
+@pytest.mark.parametrize("lim", ["minmod", "superbee", "smart", "vanleer", "upwind", "central"])
+def test_tlm_at_an_overflowing_ratio_is_its_finite_limit(lim):
+    # a subnormal d_u beside a normal d_U makes r = d_U / d_u overflow to inf;
+    # the face sits on the limiter's flat cap, where theta_f = theta_C +
+    # Psi_cap d_u / 2: the derivative is that of the same branch at a tiny
+    # normal d_u (r finite), and the adjoint stays the TLM's transpose
+    n = 12
+    mesh = W.structured_mesh(n, 1, 1, 1.0 / n, 1.0, 1.0)
+    u = np.full(n, 0.7)
+    th = np.linspace(-1.0, 1.0, n)
+    th[3], th[4], th[5] = -1.0, 0.0, 5e-324   # face 4|5: d_u subnormal, d_U = 1
+    th_n = th.copy()
+    th_n[5] = 1e-300                            # same branch, r = 1e300
+    v = np.random.default_rng(9).normal(size=n)
+    _, d_inf = oracle.step_tlm(mesh, lim, 1, 0.01, 1, u, th, v)
+    _, d_fin = oracle.step_tlm(mesh, lim, 1, 0.01, 1, u, th_n, v)
+    assert np.all(np.isfinite(d_inf))
+    assert np.max(np.abs(d_inf - d_fin)) <= 1e-14 * np.max(np.abs(d_fin))
+    w = np.random.default_rng(10).normal(size=n)
+    om = oracle.OracleMesh(mesh)
+    _, d1 = oracle.step_tlm(om, lim, 1, 1.0, 1, u, th, v)
+    JTw = oracle.rhs_adjoint(om, lim, th, u, w)
+    assert np.all(np.isfinite(JTw))
+    assert abs(np.dot(d1 - v, w) - np.dot(v, JTw)) <= 1e-13 * np.linalg.norm(d1 - v) * \
+        np.linalg.norm(w)

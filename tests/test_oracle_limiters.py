@@ -72,3 +72,14 @@ def test_infinite_ratio_limits():
     assert list(oracle.psi("vanleer", inf)) == [2.0, 0.0]
     assert list(oracle.psi("superbee", inf)) == [2.0, 0.0]
     assert list(oracle.psi("smart", inf)) == [4.0, 0.0]
+
+
+@pytest.mark.parametrize("lim", ["upwind", "central", "minmod", "vanleer", "superbee", "smart"])
+def test_branch_form_at_infinite_ratio(lim):
+    # r = +-inf lies on the flat end pieces: the branch form gives the closed
+    # form's limit with a zero derivative (no 0 * inf in the tangent-linear
+    # model's Psi - Psi' r)
+    inf = np.array([np.inf, -np.inf])
+    p, d = oracle.psi_branch(lim, inf)
+    np.testing.assert_array_equal(p, oracle.psi(lim, inf))
+    np.testing.assert_array_equal(d, [0.0, 0.0])

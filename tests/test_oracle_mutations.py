@@ -38,8 +38,12 @@ MUTANTS = [
     ("rk3_coefficient", "const double RK3_A[3] = {0.0, 0.75, 1.0 / 3.0};",
      "const double RK3_A[3] = {0.0, 0.25, 1.0 / 3.0};"),
     ("smart_middle_branch", "0.25 + 0.75 * r), 4.0));", "0.25 + 0.5 * r), 4.0));"),
-    ("tlm_alpha_sign", "const double alpha = 0.5 * (e.psi - e.dpsi * e.r);\n  const double beta = 0.5 * e.dpsi;\n  return",
-     "const double alpha = 0.5 * (e.psi + e.dpsi * e.r);\n  const double beta = 0.5 * e.dpsi;\n  return"),
+    ("tlm_alpha_sign", "return 0.5 * (e.psi - pr);", "return 0.5 * (e.psi + pr);"),
+    ("tlm_infinite_ratio_product", "const double pr = (e.dpsi != 0.0) ? e.dpsi * e.r : 0.0;",
+     "const double pr = e.dpsi * e.r;"),
+    ("smart_branch_at_infinite_ratio", "if (std::isinf(r)) { *dpsi = 0.0; return 4.0; }", ""),
+    ("central_slope_dropped_on_flat_faces", "e.psi = (lim == L_CENTRAL) ? 1.0 : 0.0;",
+     "e.psi = 0.0;"),
     ("adjoint_downwind_to_upwind", "out[e.D] += g * alpha;", "out[e.C] += g * alpha;"),
     ("distance_weight_inverted", "return m.dist.empty() ? term : term / m.dist[j];",
      "return m.dist.empty() ? term : term * m.dist[j];"),
