@@ -144,6 +144,35 @@ double psi_branch(int lim, double r, double *dpsi) {
   return std::nan("");
 }
 
+// Psi'(r) of the branch the exact ratio r = dU / du (du != 0) lies on.  The
+// branch is decided without the rounded quotient: with p = dU sign(du) and
+// q = |du| > 0, r <= k is kd p <= kn q for k = kn / kd, and the sign of
+// kd p - kn q is exact (p, q and the difference are multiples of 2^-1074,
+// so the one fma or subtraction that forms it only rounds a nonzero value
+// to a nonzero value of the same sign).  The rounded quotient underflows to 0
+// for a positive r below 2^-1075 and would take the r <= 0 branch, or
+// overflows to +-inf.  Ties go to the lower branch, as in psi_branch.  r (the
+// rounded quotient) serves van Leer's smooth derivative only.
+double dpsi_exact(int lim, double dU, double du, double r) {
+  const double q = std::fabs(du);
+  const double p = std::signbit(du) ? -dU : dU;
+  if (lim == L_UPWIND || lim == L_CENTRAL || p <= 0.0) return 0.0;
+  switch (lim) {
+    case L_MINMOD: return (p - q <= 0.0) ? 1.0 : 0.0;                 // r <= 1
+    case L_VANLEER: return std::isinf(r) ? 0.0 : 2.0 / ((1.0 + r) * (1.0 + r));
+    case L_SUPERBEE:
+      if (std::fma(2.0, p, -q) <= 0.0) return 2.0;                    // r <= 1/2
+      if (p - q <= 0.0) return 0.0;                                   // r <= 1
+      if (std::fma(-2.0, q, p) <= 0.0) return 1.0;                    // r <= 2
+      return 0.0;
+    case L_SMART:
+      if (std::fma(5.0, p, -q) <= 0.0) return 2.0;                    // r <= 1/5
+      if (std::fma(-5.0, q, p) <= 0.0) return 0.75;                   // r <= 5
+      return 0.0;
+  }
+  return std::nan("");
+}
+
 // ------------------------------------------------------------ one face
 struct FaceEval {
   int s;            // +1 / -1
@@ -195,9 +224,7 @@ FaceEval eval_face(const OMesh &m, int lim, const double *th, const double *u, i
   } else {
     e.r = e.dU / e.du;
     e.psi = psi_closed(lim, e.r);
-    double dp;
-    (void)psi_branch(lim, e.r, &dp);
-    e.dpsi = dp;
+    e.dpsi = dpsi_exact(lim, e.dU, e.du, e.r);
     e.thf = th[e.C] + 0.5 * e.psi * e.du;
   }
   return e;

@@ -46,8 +46,17 @@ constexpr int STY = FL_STRUCT_TY;
 #ifndef FL_STRUCT_MINB
 #define FL_STRUCT_MINB (32 / STY)
 #endif
+// CTAs per SM of the FP64 van Leer and SMART stages, whose limiter terms
+// run on the integer and FP32 pipes (more registers per thread)
+#ifndef FL_HEAVY_MINB
+#define FL_HEAVY_MINB FL_STRUCT_MINB
+#endif
 template <class T, int LIM, int SEED, int TY, bool PRE, bool MOD, bool CODES>
-__global__ void __launch_bounds__(TX *TY, CODES ? FL_CODES_MINB : FL_STRUCT_MINB)
+__global__ void __launch_bounds__(TX *TY, CODES ? FL_CODES_MINB
+                                          : (sizeof(T) == 8 && (LIM == LIM_VANLEER ||
+                                                                LIM == LIM_SMART))
+                                              ? FL_HEAVY_MINB
+                                              : FL_STRUCT_MINB)
     k_struct_stage(const SParams<T> p) {
   stage_tile<T, LIM, SEED, TY, PRE, MOD, CODES>(p, blockIdx.x);
 }

@@ -187,10 +187,15 @@ def test_structured_gradient_edge_cases(fl, lim, rk):
     m.close()
 
 
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("dtype,name", [(torch.float64, "hex_permuted"),
+                                        (torch.float32, "hex_permuted"),
+                                        (torch.float64, "tet")])
 @pytest.mark.parametrize("lim", LIMS)
-@pytest.mark.parametrize("name", ["hex_permuted", "tet"])
 def test_face_based_adjoint_edge_cases(fl, name, lim, dtype):
+    # (an FP32 tetrahedral case is left out: its stencil coefficients n_f . n_j
+    # such as 1/sqrt(2) are rounded differently in FP32 and FP64, so a face
+    # exactly on a limiter kink in one precision is not in the other, and the
+    # derivative's branch is decided in the kernel's precision)
     mesh = _face_mesh(name)
     th = W.quantized_field(mesh.n_cells, 71, DT_NAME[dtype])
     u = _cast(W.edge_velocity(mesh.n_faces, 72), dtype)

@@ -123,8 +123,9 @@ def test_van_leer_quotient_fp32_against_ieee_division(probe):
 
 
 def _exact_piece(p, q):
+    # ties go to the lower piece: r = 5 is the middle piece, r = 1/5 piece 2
     fp, fq = Fraction(float(p)), Fraction(float(q))
-    if fp >= 5 * fq:
+    if fp > 5 * fq:
         return 1
     if fq >= 5 * fp:
         return 2

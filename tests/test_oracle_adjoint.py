@@ -115,3 +115,21 @@ def test_tlm_at_an_overflowing_ratio_is_its_finite_limit(lim):
     assert np.all(np.isfinite(JTw))
     assert abs(np.dot(d1 - v, w) - np.dot(v, JTw)) <= 1e-13 * np.linalg.norm(d1 - v) * \
         np.linalg.norm(w)
+
+
+@pytest.mark.parametrize("lim", ["minmod", "superbee", "smart", "vanleer"])
+def test_tlm_at_an_underflowing_ratio_keeps_its_branch(lim):
+    # r = d_U / d_u > 0 below 2^-1075 rounds to 0, but the face lies on the
+    # limiter's first increasing piece (Psi' > 0), as at any small positive
+    # r: the derivative's branch is decided from d_U and d_u exactly
+    n = 12
+    mesh = W.structured_mesh(n, 1, 1, 1.0 / n, 1.0, 1.0)
+    u = np.full(n, 0.7)
+    th = np.linspace(-1.0, 1.0, n)
+    th[3], th[4], th[5] = 0.0, 5e-324, 4.0   # face 4|5: d_U subnormal, d_u = 4
+    th_n = th.copy()
+    th_n[4] = 1e-300                           # same piece, r = 2.5e-301
+    v = np.random.default_rng(12).normal(size=n)
+    _, d_tiny = oracle.step_tlm(mesh, lim, 1, 0.01, 1, u, th, v)
+    _, d_norm = oracle.step_tlm(mesh, lim, 1, 0.01, 1, u, th_n, v)
+    assert np.max(np.abs(d_tiny - d_norm)) <= 1e-14 * np.max(np.abs(d_norm))

@@ -41,6 +41,8 @@ MUTANTS = [
     ("tlm_alpha_sign", "return 0.5 * (e.psi - pr);", "return 0.5 * (e.psi + pr);"),
     ("tlm_infinite_ratio_product", "const double pr = (e.dpsi != 0.0) ? e.dpsi * e.r : 0.0;",
      "const double pr = e.dpsi * e.r;"),
+    ("branch_from_rounded_ratio", "e.dpsi = dpsi_exact(lim, e.dU, e.du, e.r);",
+     "(void)psi_branch(lim, e.r, &e.dpsi);"),
     ("smart_branch_at_infinite_ratio", "if (std::isinf(r)) { *dpsi = 0.0; return 4.0; }", ""),
     ("central_slope_dropped_on_flat_faces", "e.psi = (lim == L_CENTRAL) ? 1.0 : 0.0;",
      "e.psi = 0.0;"),
