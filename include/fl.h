@@ -380,6 +380,34 @@ fl_status fl_conv_limited_adjoint(const fl_mesh *mesh, fl_limiter limiter, fl_dt
                                   const void *theta_c, const void *u_f, const void *lambda_rhs,
                                   void *lambda_theta, void *stream);
 
+/*
+ * Reverse mode of one RK stage of fl_step_rk_stage, for callers that run the
+ * reverse sweep themselves (a domain decomposition that exchanges the
+ * adjoint's halo between stages).  Stage s maps
+ *   y_s = a_s theta_n + b_s (x_s + dt R(x_s))
+ * ((a_s, b_s) as in fl_step_rk_stage).  Given mu = dJ/dy_s it writes
+ *   stage s > 0:  out = b_s (mu + dt R'(x_s)^T mu)              (= dJ/dx_s)
+ *   stage 0:      out = mu + dt R'(theta_n)^T mu                 (Euler), or
+ *                 out = mu + dt R'(theta_n)^T mu + a_1 lam_a + a_2 lam_b
+ *                 (SSP-RK3: theta_n's other uses, in the blends of stages 1
+ *                 and 2, with lam_a = dJ/dy_1 and lam_b = dJ/dy_2)
+ * so that one SSP-RK3 step back from lambda = dJ/dtheta^{n+1} is
+ *   m2 = stage 2 (x_2, lambda);  m1 = stage 1 (x_1, m2);
+ *   dJ/dtheta^n = stage 0 (theta^n, m1, lam_a = m2, lam_b = lambda).
+ * The limiter derivative is taken on the branch its forward evaluation at
+ * x_s takes (strict ordered tests, ties to the lower branch).  All buffers
+ * device, dtype elements: x, mu, lam_a, lam_b, out [n_cells]; u_f, w_f
+ * [n_faces].  lam_a, lam_b are read only in stage 0 of SSP-RK3 (else they
+ * may be NULL).  out must not overlap x or mu; it may be lam_a or lam_b.
+ * w_f: NULL, or the pre-scaled velocity of fl_velocity_prescale for the same
+ * dt.  Reads mu within two cells and x within three cells of each output.
+ * The paper has no adjoint; this is defined by the forward steps above.
+ */
+fl_status fl_step_rk_stage_adjoint(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                                   int rk_order, int stage, double dt, const void *x,
+                                   const void *mu, const void *lam_a, const void *lam_b,
+                                   void *out, const void *u_f, const void *w_f, void *stream);
+
 /* Bytes of device workspace fl_step_rk_adjoint needs. */
 fl_status fl_adjoint_workspace_size(const fl_mesh *mesh, fl_dtype dtype, int rk_order,
                                     int64_t nsteps, int64_t checkpoint_every, size_t *bytes);

@@ -39,7 +39,7 @@ ABI_SYMBOLS = [
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_modulated",
     "fl_step_rk_noalloc", "fl_step_rk_blocked", "fl_step_rk_stage", "fl_velocity_prescale",
     "fl_conv_limited_adjoint",
-    "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_checkpointed",
+    "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_stage_adjoint", "fl_step_rk_checkpointed",
     "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
     "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_destroy",
     "fl_alg_create", "fl_alg_destroy", "fl_alg_info", "fl_alg_workspace_size",
@@ -104,6 +104,7 @@ def lib():
             "fl_velocity_prescale": (I, [P, I, D, P, P, P]),
             "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
             "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
+            "fl_step_rk_stage_adjoint": (I, [P, I, I, I, I, D, P, P, P, P, P, P, P, P]),
             "fl_step_rk_adjoint": (I, [P, I, I, I, D, I64, I64, P, P, P, P, P, SZ, P]),
             "fl_step_rk_checkpointed": (I, [P, I, I, I, D, I64, I64, P, P, P, SZ, P]),
             "fl_step_rk_adjoint_from_checkpoints": (I, [P, I, I, I, D, I64, I64, P, P, P, P,
@@ -358,6 +359,17 @@ def fl_conv_limited_adjoint(mesh, limiter, dtype, theta_c, u_f, lambda_rhs, lamb
     _check(lib().fl_conv_limited_adjoint(mesh, _lim(limiter), c, _fptr(theta_c, c),
                                          _fptr(u_f, c), _fptr(lambda_rhs, c),
                                          _fptr(lambda_theta, c), _stream(stream)))
+
+
+def fl_step_rk_stage_adjoint(mesh, limiter, dtype, rk_order, stage, dt, x, mu, lam_a, lam_b,
+                             out, u_f, w_f=None, stream=None):
+    """Reverse mode of one RK stage (see fl.h): dJ/dx_s, or for stage 0 of
+    SSP-RK3 dJ/dtheta_n with theta_n's later uses (lam_a, lam_b)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_stage_adjoint(mesh, _lim(limiter), c, int(rk_order), int(stage),
+                                          float(dt), _fptr(x, c), _fptr(mu, c), _fptr(lam_a, c),
+                                          _fptr(lam_b, c), _fptr(out, c), _fptr(u_f, c),
+                                          _fptr(w_f, c), _stream(stream)))
 
 
 def fl_adjoint_workspace_size(mesh, dtype, rk_order, nsteps, checkpoint_every):

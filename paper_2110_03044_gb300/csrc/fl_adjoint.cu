@@ -854,6 +854,64 @@ fl_status fl_conv_limited_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt,
   return FL_OK;
 }
 
+fl_status fl_step_rk_stage_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
+                                   int stage, double dtime, const void *x, const void *mu,
+                                   const void *lam_a, const void *lam_b, void *out,
+                                   const void *u_f, const void *w_f, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(lim, dt));
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (stage < 0 || stage >= (rk == 3 ? 3 : 1))
+    return fail(FL_EINVAL, "stage %d does not exist for rk_order %d", stage, rk);
+  if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
+  const size_t es = dsize(dt), cb = (size_t)m->C * es;
+  FL_TRY(check_buffer(x, cb, "x"));
+  FL_TRY(check_buffer(mu, cb, "mu"));
+  FL_TRY(check_buffer(out, cb, "out"));
+  FL_TRY(check_buffer(u_f, (size_t)m->F * es, "u_f"));
+  const bool blend = rk == 3 && stage == 0;
+  if (blend) {
+    FL_TRY(check_buffer(lam_a, cb, "lam_a"));
+    FL_TRY(check_buffer(lam_b, cb, "lam_b"));
+  }
+  if (w_f != nullptr) {
+    if (!(dtime > 0)) return fail(FL_EINVAL, "a pre-scaled velocity needs dt > 0");
+    FL_TRY(check_buffer(w_f, (size_t)m->F * es, "w_f"));
+  }
+  if (m->C > 0) {
+    const char *ob = static_cast<const char *>(out);
+    for (const void *in : {x, mu}) {
+      const char *ib = static_cast<const char *>(in);
+      if (ob < ib + cb && ib < ob + cb)
+        return fail(FL_EINVAL, "out overlaps x or mu (the stage reads their neighbours)");
+    }
+  }
+  if (m->C == 0) return FL_OK;
+  if (m->kind == 1) FL_TRY(unstruct_adjoint_prepare(m));
+  AdjArgs a;
+  a.x = x;
+  a.mu = mu;
+  a.out = out;
+  a.u = u_f;
+  a.cu = w_f;
+  a.cu_dt = w_f != nullptr;
+  a.dt = dtime;
+  a.b = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+  if (blend) {
+    // theta^n's weights in the later stages' blends: 1/3 in stage 2 (as the
+    // forward kernels use it: 1 - RN(2/3) in the working precision) and 3/4
+    // in stage 1
+    a.v1 = lam_b;
+    a.e1 = dt == FL_F64 ? blend_a<double>(1.0 / 3.0, 2.0 / 3.0)
+                        : (double)blend_a<float>(1.0 / 3.0, 2.0 / 3.0);
+    a.v2 = lam_a;
+    a.e2 = 0.75;
+  }
+  const cudaError_t e = adjoint_any(m, lim, dt, a, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stage adjoint kernel");
+  return FL_OK;
+}
+
 fl_status fl_adjoint_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps,
                                     int64_t every, size_t *bytes) {
   if (m == nullptr || bytes == nullptr) return fail(FL_EINVAL, "NULL argument");

@@ -32,6 +32,10 @@ receives from below first on every rank, with tags, so that with two ranks
 (where the rank below is also the rank above) the messages pair correctly.
 A rank whose neighbours are itself (one rank) copies its own planes.
 
+The adjoint (gradient_rk) exchanges the adjoint field the same way before
+every adjoint stage; it reads the stage states three planes deep, so a slab
+for the reverse sweep keeps HALO_ADJOINT = 3 ghost planes.
+
 Overlap: at 256^2 planes a halo is 2 x 65536 values per side (1 MiB in
 FP64), against a stage of 16.8 M cells; the exchange is issued before the
 stage and waited for, without splitting the stage into interior and rim.
@@ -150,6 +154,12 @@ class TorchTransport:
 
 
 StageFn = Callable[[int, Optional[object], object, object], None]
+StageAdjointFn = Callable[[int, object, object, Optional[object], Optional[object], object], None]
+
+# The adjoint stage reads mu within two planes and the stage state x within
+# three (the four faces of an axis around a cell, each with its upstream
+# cell): a decomposed reverse sweep keeps three ghost planes.
+HALO_ADJOINT = 3
 
 
 def step_rk(slab: Slab, transport, stage: StageFn, rk_order: int, nsteps: int, theta, a, b=None):
@@ -178,6 +188,72 @@ def step_rk(slab: Slab, transport, stage: StageFn, rk_order: int, nsteps: int, t
         transport.exchange(slab, b)
         stage(2, theta, b, theta)  # y may be theta_n, never x
     return theta
+
+
+def gradient_rk(slab: Slab, transport, stage: StageFn, stage_adjoint: StageAdjointFn,
+                rk_order: int, nsteps: int, every: int, theta0, lam_T, new):
+    """Reverse-mode sweep of a decomposed rollout: dJ/dtheta_0 from
+    lam_T = dJ/dtheta_T, with checkpoints every ``every`` steps and each
+    segment recomputed (its stage inputs stored with their exchanged ghost
+    planes) before its adjoint stages run in reverse; the adjoint's halo is
+    exchanged before every adjoint stage, the same exchange as the forward
+    stages'.  ``stage_adjoint(s, x, mu, lam_a, lam_b, out)`` is the
+    library's fl_step_rk_stage_adjoint on the local mesh; ``new()`` gives a
+    fresh local field.  The slab needs ``halo >= HALO_ADJOINT``.  Returns the
+    local dJ/dtheta_0 (owned planes valid)."""
+    if slab.halo < HALO_ADJOINT:
+        raise ValueError("the reverse sweep needs a halo of %d planes" % HALO_ADJOINT)
+    if rk_order not in (1, 3):
+        raise ValueError("rk_order must be 1 or 3")
+
+    def fwd_step(th, keep):
+        """one step in place on th, appending its exchanged stage inputs"""
+        transport.exchange(slab, th)
+        keep.append(th.clone())
+        if rk_order == 1:
+            y = new()
+            stage(0, None, th, y)
+            th.copy_(y)
+            return
+        a, b = new(), new()
+        stage(0, None, th, a)
+        transport.exchange(slab, a)
+        keep.append(a.clone())
+        stage(1, th, a, b)
+        transport.exchange(slab, b)
+        keep.append(b.clone())
+        stage(2, th, b, th)
+
+    # forward, storing a checkpoint every `every` steps
+    checkpoints = []
+    th = theta0.clone()
+    for n in range(nsteps):
+        if n % every == 0:
+            checkpoints.append(th.clone())
+        fwd_step(th, [])
+    lam = lam_T.clone()
+    for c in range(len(checkpoints) - 1, -1, -1):
+        seg = min(every, nsteps - c * every)
+        th = checkpoints[c].clone()
+        states = []
+        for _ in range(seg):
+            fwd_step(th, states)
+        for n in range(seg - 1, -1, -1):
+            transport.exchange(slab, lam)
+            if rk_order == 1:
+                out = new()
+                stage_adjoint(0, states[n], lam, None, None, out)
+                lam = out
+                continue
+            x0, x1, x2 = states[3 * n], states[3 * n + 1], states[3 * n + 2]
+            m2, m1, out = new(), new(), new()
+            stage_adjoint(2, x2, lam, None, None, m2)
+            transport.exchange(slab, m2)
+            stage_adjoint(1, x1, m2, None, None, m1)
+            transport.exchange(slab, m1)
+            stage_adjoint(0, x0, m1, m2, lam, out)
+            lam = out
+    return lam
 
 
 class SlabRollout:
@@ -215,6 +291,24 @@ class SlabRollout:
                         y, self.u, self.w)
 
         return step_rk(self.slab, self.transport, stage, rk_order, nsteps, theta_local, a, b)
+
+    def gradient(self, theta_local, lam_T_local, rk_order, nsteps, every):
+        """dJ/dtheta_0 on this rank's slab (see gradient_rk); the slab needs
+        a halo of HALO_ADJOINT planes."""
+        import torch
+
+        from . import fl_step_rk_stage_adjoint
+
+        def stage(s, thn, x, y):
+            self._stage(self.mesh.handle, self.limiter, self.dtype, rk_order, s, self.dt, thn, x,
+                        y, self.u, self.w)
+
+        def stage_adjoint(s, x, mu, lam_a, lam_b, out):
+            fl_step_rk_stage_adjoint(self.mesh.handle, self.limiter, self.dtype, rk_order, s,
+                                     self.dt, x, mu, lam_a, lam_b, out, self.u, self.w)
+
+        return gradient_rk(self.slab, self.transport, stage, stage_adjoint, rk_order, nsteps,
+                           every, theta_local, lam_T_local, lambda: torch.empty_like(theta_local))
 
     def close(self):
         self.mesh.close()

@@ -8,7 +8,11 @@ test_gpu_decomp.py).
   bits of the one-rank decomposed run (the exchange delivers exactly the
   planes each stage reads) and the whole-mesh oracle to rounding (the cell
   sums of the wrapped plane 0 run in another face order there).
-* Mass is conserved across the cuts to round-off."""
+* Mass is conserved across the cuts to round-off.
+* The decomposed reverse sweep (checkpoints, recomputed segments, the
+  adjoint's halo exchanged before every adjoint stage, three ghost planes)
+  gives the one-rank sweep's gradient bit for bit and the oracle's reference
+  gradient to 1e-12."""
 import math
 import os
 import socket
@@ -146,3 +150,72 @@ def test_gloo_decomposed_rollout_equals_one_rank(world, lim, rk):
     assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
     m0 = math.fsum((th * mesh.volumes).tolist())
     assert abs(math.fsum((got * mesh.volumes).tolist()) - m0) <= 1e-13 * abs(m0)
+
+
+# ------------------------------------------------ the decomposed reverse sweep
+def _oracle_stage_adjoint(slab, h, lim, rk, dt, u_local):
+    lm = oracle.OracleMesh(W.structured_mesh(*slab.local_dims, *h))
+    uu = u_local.numpy()
+    b = {0: 1.0, 1: 0.25, 2: 2.0 / 3.0}
+
+    def stage_adjoint(s, x, mu, lam_a, lam_b, out):
+        m = mu.numpy()
+        y = b[s if rk == 3 else 0] * (m + dt * oracle.rhs_adjoint(lm, lim, x.numpy(), uu, m))
+        if rk == 3 and s == 0:
+            y = y + 0.75 * lam_a.numpy() + (1.0 / 3.0) * lam_b.numpy()
+        out.copy_(torch.from_numpy(y))
+
+    return stage_adjoint
+
+
+def _grad_rank(rank, world, lim, rk, nsteps, every, transport):
+    from paper_2110_03044_gb300.decomp import HALO_ADJOINT, gradient_rk
+    dims, h, mesh, th, u, dt = _case()
+    tgt = np.random.default_rng(7).normal(size=mesh.n_cells)
+    thT = oracle.step(mesh, lim, rk, dt, nsteps, u, th)
+    slab = Slab(dims, rank, world, halo=HALO_ADJOINT)
+    tl = slab.local_cells(torch.from_numpy(th)).clone()
+    lam = slab.local_cells(torch.from_numpy(thT - tgt)).clone()
+    ul = slab.local_faces(torch.from_numpy(u), 3)
+    g = gradient_rk(slab, transport, _oracle_stage(slab, h, lim, rk, dt, ul),
+                    _oracle_stage_adjoint(slab, h, lim, rk, dt, ul), rk, nsteps, every, tl, lam,
+                    lambda: torch.empty_like(tl))
+    return slab.lo, slab.hi, slab.owned(g).numpy().copy()
+
+
+def _grad_worker(rank, world, port, lim, rk, nsteps, every, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank,) + _grad_rank(rank, world, lim, rk, nsteps, every, TorchTransport()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1)])
+def test_gloo_decomposed_gradient_equals_one_rank(world, lim, rk):
+    dims, h, mesh, th, u, dt = _case()
+    nsteps, every = 3, 2
+    P = dims[0] * dims[1]
+    _, _, one = _grad_rank(0, 1, lim, rk, nsteps, every, LocalTransport())
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_grad_worker, args=(r, world, port, lim, rk, nsteps, every, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = np.empty(mesh.n_cells)
+    for _, lo, hi, part in out:
+        got[lo * P:hi * P] = part
+    assert np.array_equal(got, one)  # bit for bit
+    tgt = np.random.default_rng(7).normal(size=mesh.n_cells)
+    _, g_ref = oracle.gradient(mesh, lim, rk, dt, nsteps, u, th, tgt)
+    assert np.max(np.abs(got - g_ref)) <= 1e-12 * np.max(np.abs(g_ref))

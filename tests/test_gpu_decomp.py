@@ -8,7 +8,10 @@ in order, so no kernel waits on another.
 The owned planes of the decomposed rollout must equal fl_step_rk on the
 whole mesh bit for bit: FP64 (with the pre-scaled velocity, the arithmetic of
 fl_step_rk), FP32 on the register tile and on the TMA kernel, Euler and
-SSP-RK3."""
+SSP-RK3.  The decomposed reverse sweep (fl_step_rk_stage_adjoint, three ghost
+planes, the adjoint's halo exchanged before every adjoint stage) must give the
+one-slab sweep's gradient bit for bit, and fl_step_rk_adjoint's and the
+oracle's gradient to rounding."""
 import threading
 
 import numpy as np
@@ -128,4 +131,108 @@ def test_stage_entry_point_composes_to_step_rk(fl):
     assert e.value.status == fl.FL_EINVAL
     with pytest.raises(fl.FLError):  # no stage 1 in forward Euler
         fl.fl_step_rk_stage(m.handle, "smart", torch.float64, 1, 1, dt, th, a, b, u, None)
+    m.close()
+
+
+def _decomposed_gradient(fl, world, dims, h, th, u, lam_T, lim, rk, dt, nsteps, every):
+    from paper_2110_03044_gb300.decomp import HALO_ADJOINT
+    out = [None] * world
+    err = []
+    tr = ThreadGroupTransport(world)
+    ug = torch.tensor(u, device="cuda")
+
+    def rank(r):
+        try:
+            torch.cuda.set_device(0)
+            slab = Slab(dims, r, world, halo=HALO_ADJOINT)
+            ro = SlabRollout(slab, h, ug, lim, torch.float64, dt, transport=tr)
+            tl = ro.local_field(torch.tensor(th, device="cuda"))
+            ll = ro.local_field(torch.tensor(lam_T, device="cuda"))
+            g = ro.gradient(tl, ll, rk, nsteps, every)
+            torch.cuda.synchronize()
+            out[r] = (slab.lo, slab.hi, slab.owned(g).cpu())
+            ro.close()
+        except BaseException as e:  # noqa: BLE001 -- reported below
+            err.append(e)
+            tr.bar.abort()
+
+    ts = [threading.Thread(target=rank, args=(r,)) for r in range(world)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if err:
+        raise err[0]
+    P = dims[0] * dims[1]
+    got = torch.empty(P * dims[2], dtype=torch.float64)
+    for lo, hi, part in out:
+        got[lo * P:hi * P] = part
+    return got.numpy()
+
+
+@pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 3), ("smart", 1)])
+def test_decomposed_gradient_matches_whole_mesh_and_oracle(fl, lim, rk):
+    # the reverse sweep on 3 slabs (three ghost planes, the adjoint's halo
+    # exchanged before every adjoint stage): bit for bit the one-slab sweep,
+    # and fl_step_rk_adjoint on the whole mesh and the oracle's gradient to
+    # rounding
+    import oracle
+    dims = (24, 10, 18)
+    h = tuple(0.7 / d for d in dims)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(15)
+    th = rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3)
+    u = 0.3 * W.mixed_sign_velocity(mesh.n_faces, 16)
+    dt = 0.3 * min(h) / np.max(np.abs(u)) / 3
+    nsteps, every = 4, 3
+    tgt = rng.normal(size=mesh.n_cells)
+    thT = oracle.step(mesh, lim, rk, dt, nsteps, u, th)
+    got = _decomposed_gradient(fl, 3, dims, h, th, u, thT - tgt, lim, rk, dt, nsteps, every)
+    one = _decomposed_gradient(fl, 1, dims, h, th, u, thT - tgt, lim, rk, dt, nsteps, every)
+    assert np.array_equal(got, one)
+    m = fl.Mesh.structured(*dims, *h)
+    nb = fl.fl_adjoint_workspace_size(m.handle, torch.float64, rk, nsteps, every)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    g = torch.empty(mesh.n_cells, dtype=torch.float64, device="cuda")
+    fl.fl_step_rk_adjoint(m.handle, lim, torch.float64, rk, dt, nsteps, every,
+                          torch.tensor(th, device="cuda"), torch.tensor(u, device="cuda"),
+                          torch.tensor(thT - tgt, device="cuda"), g, ws, nb)
+    m.close()
+    whole = g.cpu().numpy()
+    scale = np.max(np.abs(whole))
+    assert np.max(np.abs(got - whole)) <= 1e-12 * scale
+    _, g_ref = oracle.gradient(mesh, lim, rk, dt, nsteps, u, th, tgt)
+    assert np.max(np.abs(got - g_ref)) <= 1e-11 * np.max(np.abs(g_ref))
+
+
+def test_stage_adjoint_composes_to_the_step_adjoint(fl):
+    # one SSP-RK3 step back through fl_step_rk_stage_adjoint equals
+    # fl_step_rk_adjoint over one step (stage states from fl_step_rk_stage)
+    dims = (33, 10, 7)
+    h = (0.1, 0.2, 0.3)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(18)
+    th0 = torch.tensor(rng.uniform(-1, 1, mesh.n_cells), device="cuda")
+    u = torch.tensor(0.3 * W.mixed_sign_velocity(mesh.n_faces, 19), device="cuda")
+    lam = torch.tensor(rng.normal(size=mesh.n_cells), device="cuda")
+    dt = 0.05
+    m = fl.Mesh.structured(*dims, *h)
+    w = torch.empty_like(u)
+    fl.fl_velocity_prescale(m.handle, torch.float64, dt, u, w)
+    x1, x2, y = torch.empty_like(th0), torch.empty_like(th0), torch.empty_like(th0)
+    f64 = torch.float64
+    fl.fl_step_rk_stage(m.handle, "superbee", f64, 3, 0, dt, None, th0, x1, u, w)
+    fl.fl_step_rk_stage(m.handle, "superbee", f64, 3, 1, dt, th0, x1, x2, u, w)
+    m2, m1, out = torch.empty_like(th0), torch.empty_like(th0), torch.empty_like(th0)
+    fl.fl_step_rk_stage_adjoint(m.handle, "superbee", f64, 3, 2, dt, x2, lam, None, None, m2, u, w)
+    fl.fl_step_rk_stage_adjoint(m.handle, "superbee", f64, 3, 1, dt, x1, m2, None, None, m1, u, w)
+    fl.fl_step_rk_stage_adjoint(m.handle, "superbee", f64, 3, 0, dt, th0, m1, m2, lam, out, u, w)
+    nb = fl.fl_adjoint_workspace_size(m.handle, f64, 3, 1, 1)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    ref = torch.empty_like(th0)
+    fl.fl_step_rk_adjoint(m.handle, "superbee", f64, 3, dt, 1, 1, th0, u, lam, ref, ws, nb)
+    assert float((out - ref).abs().max() / ref.abs().max()) <= 1e-14
+    with pytest.raises(fl.FLError):  # out must not overlap mu
+        fl.fl_step_rk_stage_adjoint(m.handle, "superbee", f64, 3, 1, dt, x1, m2, None, None, m2,
+                                    u, w)
     m.close()
