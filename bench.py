@@ -38,8 +38,12 @@ FALLBACK_HBM = 6800.0
 # fraction of that pipe in one ncu capture of the current kernel (the
 # profile summary named beside it), reported next to the HBM roofline.
 NCU_FP64_PIPE = {
-    ("f64", "superbee", 256): (0.850, "sm__pipe_fp64_cycles_active, RK stage 2 launch, "
+    ("f64", "superbee", 256): (0.843, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
                                "profiles/k_struct_stage_f64_superbee_tg256.md"),
+    ("f64", "vanleer", 256): (0.629, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
+                              "profiles/k_struct_stage_f64_vanleer_smart_tg256.md"),
+    ("f64", "smart", 256): (0.821, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
+                            "profiles/k_struct_stage_f64_vanleer_smart_tg256.md"),
 }
 
 
@@ -48,8 +52,15 @@ NCU_FP64_PIPE = {
 # FP64 superbee, RK stages 2-3 (65 % of the step's kernel time); FP32
 # superbee TMA kernel, RK stage 1.  Keyed by (dtype, limiter, n).
 NCU_TRAFFIC = {
-    ("f64", "superbee", 256): (812.2e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
-                               "algorithmic 805.3e6 (48 B x 16.8M cells)"),
+    ("f64", "superbee", 256): (808.3e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
+                               "algorithmic 805.3e6 (48 B x 16.8M cells), "
+                               "profiles/k_struct_stage_f64_superbee_tg256.md"),
+    ("f64", "vanleer", 256): (833.4e6, "k_struct_stage<double, VANLEER, COMBINE, PRE>, "
+                              "algorithmic 805.3e6, "
+                              "profiles/k_struct_stage_f64_vanleer_smart_tg256.md"),
+    ("f64", "smart", 256): (830.2e6, "k_struct_stage<double, SMART, COMBINE, PRE>, "
+                            "algorithmic 805.3e6, "
+                            "profiles/k_struct_stage_f64_vanleer_smart_tg256.md"),
     ("f32", "superbee", 256): (330.9e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
                                "algorithmic 335.5e6 (20 B x 16.8M cells)"),
 }
@@ -72,14 +83,15 @@ def stage_bytes_per_cell(es, stage):
 
 # FP64 operations per cell of one stage in the kernel's formulation: per
 # face one difference and the limited face value (one fma for minmod /
-# superbee / central, two for SMART, six for van Leer: pq, p+q, the three
-# operations of the Newton quotient and the fma);
+# superbee / central / van Leer, two for SMART);
 # per cell six fmas w theta_f (the flux product folded into the update with
 # the pre-scaled velocity w = dt (A/V) u) and two more for the RK blend of
 # stages 2-3.  Superbee: 12 + 14 + 14 = 40 per SSP-RK3 step.
 def stage_fp64_ops_per_cell(lim, stage):
+    # (van Leer's quotient runs in paired FP32 off the FP64 pipe: Delta and
+    # one fma per face, as for superbee)
     per_face = {"upwind": 1, "central": 2, "minmod": 2, "superbee": 2, "smart": 3,
-                "vanleer": 7}[lim]
+                "vanleer": 2}[lim]
     return 3 * per_face + 6 + (2 if stage > 0 else 0)
 
 
