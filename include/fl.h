@@ -460,8 +460,9 @@ fl_status fl_batch_workspace_size(const fl_batch *batch, fl_dtype dtype, int rk_
 
 /*
  * nsteps steps of every instance.  theta, u_f: host arrays of n device
- * pointers; dt: host array of n step sizes.  Tiles of all instances form
- * one work list; every stage is one launch over it.  The batch owns one
+ * pointers; dt: host array of n step sizes.  The work items of all
+ * instances (see fl_batch_tiling) form one list; every stage is one
+ * persistent launch over it, replayed from a captured CUDA graph.  The batch owns one
  * parameter table and one set of work counters, so calls on one batch run in
  * call order: a call's stream first waits for the previous call's launches
  * (an event recorded on that call's stream), whichever stream that was.
@@ -471,6 +472,25 @@ fl_status fl_batch_step_rk(fl_batch *batch, fl_limiter limiter, fl_dtype dtype, 
                            const double *dt, int64_t nsteps, void *const *theta,
                            const void *const *u_f, void *workspace, size_t workspace_bytes,
                            void *stream);
+
+/*
+ * The work decomposition of a batch's persistent launch for (limiter, dtype,
+ * rk_order): as the autotuner picked it on the first fl_batch_step_rk call
+ * with these arguments (timing a few stage launches of each candidate), or
+ * as fl_batch_set_tiling fixed it.
+ *   kind 0: rectangles of 32 x 8 cells, one cell per thread (FP64 and FP32);
+ *   kind 1: runs of 32 x cells_per_thread x warps consecutive cells of a
+ *           plane in the flat order c = i + nx j (FP32 only);
+ *   z_chunk: planes per work item.
+ * fl_batch_tiling returns FL_EINVAL until a decomposition exists; any
+ * output pointer may be NULL.  fl_batch_set_tiling validates the choice
+ * (kind 0: cells_per_thread 1, warps 8; kind 1: FP32, cells_per_thread 1, 2
+ * or 4, warps 1 .. 8; z_chunk 1 .. 255) and skips the autotuner.
+ */
+fl_status fl_batch_tiling(const fl_batch *batch, fl_limiter limiter, fl_dtype dtype, int rk_order,
+                          int *kind, int *cells_per_thread, int *warps, int *z_chunk);
+fl_status fl_batch_set_tiling(fl_batch *batch, fl_limiter limiter, fl_dtype dtype, int rk_order,
+                              int kind, int cells_per_thread, int warps, int z_chunk);
 
 fl_status fl_batch_destroy(fl_batch *batch);
 

@@ -41,7 +41,8 @@ ABI_SYMBOLS = [
     "fl_conv_limited_adjoint",
     "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_stage_adjoint", "fl_step_rk_checkpointed",
     "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
-    "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_destroy",
+    "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_tiling", "fl_batch_set_tiling",
+    "fl_batch_destroy",
     "fl_alg_create", "fl_alg_destroy", "fl_alg_info", "fl_alg_workspace_size",
     "fl_alg_face_values", "fl_alg_step_euler",
     "fl_reduce_workspace_size", "fl_reduce_max_abs", "fl_reduce_mass",
@@ -112,6 +113,9 @@ def lib():
             "fl_batch_create": (I, [I, PP, PP]),
             "fl_batch_workspace_size": (I, [P, I, I, ctypes.POINTER(SZ)]),
             "fl_batch_step_rk": (I, [P, I, I, I, ctypes.POINTER(D), I64, PP, PP, P, SZ, P]),
+            "fl_batch_tiling": (I, [P, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                    ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "fl_batch_set_tiling": (I, [P, I, I, I, I, I, I, I]),
             "fl_batch_destroy": (I, [P]),
             "fl_alg_create": (I, [I64, I64, P, P, P, P, ctypes.POINTER(P)]),
             "fl_alg_destroy": (I, [P]),
@@ -431,6 +435,19 @@ def fl_batch_step_rk(batch, limiter, dtype, rk_order, dts, nsteps, thetas, u_fs,
     _check(lib().fl_batch_step_rk(batch, _lim(limiter), c, int(rk_order), dt_arr,
                                   int(nsteps), th_arr, u_arr, _ptr(workspace),
                                   int(workspace_bytes), _stream(stream)))
+
+
+def fl_batch_tiling(batch, limiter, dtype, rk_order):
+    """(kind, cells_per_thread, warps, z_chunk) of the batch's decomposition."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().fl_batch_tiling(batch, _lim(limiter), dtype_code(dtype), int(rk_order),
+                                 *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def fl_batch_set_tiling(batch, limiter, dtype, rk_order, kind, cells_per_thread, warps, z_chunk):
+    _check(lib().fl_batch_set_tiling(batch, _lim(limiter), dtype_code(dtype), int(rk_order),
+                                     int(kind), int(cells_per_thread), int(warps), int(z_chunk)))
 
 
 def fl_batch_destroy(batch):

@@ -11,10 +11,15 @@
 // graph per (limiter, dtype, RK order, z chunk) serves every call; a call
 // only refreshes the parameter table (one host-to-device copy) and replays.
 //
-// The z chunk (cells per tile along z) is picked by a small autotuner on the
-// first call for a (limiter, dtype, RK order): each candidate times a few
-// stage-1 launches (which write only workspace, never the caller's fields)
-// and the fastest is kept.
+// The work decomposition is picked by an autotuner on the first call for a
+// (limiter, dtype, RK order): each candidate times a few stage-1 launches
+// (which write only workspace, never the caller's fields) and the fastest is
+// kept.  Candidates:
+//   * 32 x 8 rectangles (the single-mesh stage tile, shared memory, one cell
+//     per thread) with a z chunk of 8, 16, 32 or 64 planes (FP64 and FP32);
+//   * FP32 only: runs of the flat plane (fl_struct_flat.cuh, registers and
+//     warp shuffles, no barriers) with 1, 2 or 4 cells per thread, 4 or 8
+//     warps per CTA and a z chunk of 16, 32 or 64 planes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +30,7 @@
 
 #include "fl_internal.h"
 #include "fl_kernels.h"
+#include "fl_struct_flat.cuh"
 #include "fl_struct_tile.cuh"
 
 namespace fl {
@@ -49,9 +55,9 @@ struct fl_batch {
   unsigned *d_counters = nullptr;  // one work counter per stage
   // tile lists per z chunk
   std::map<int, std::pair<int2 *, int>> tiles;
-  // tuned z chunk per (lim, dtype, rk)
+  // tuned work decomposition (an encoded fl::Cfg) per (lim, dtype, rk)
   std::map<std::tuple<int, int, int>, int> tuned;
-  // graph cache per (lim, dtype, rk, zchunk)
+  // graph cache per (lim, dtype, rk, decomposition)
   std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
 };
 
@@ -81,6 +87,51 @@ __global__ void __launch_bounds__(TX *BTY, 4)
   }
 }
 
+// FP32: items are (box, run + runs-per-plane x z chunk) of the flat tile
+template <int LIM, int SEED, int CX>
+__global__ void __launch_bounds__(256)
+    k_batch_flat(const SParams<float> *__restrict__ params, const int2 *__restrict__ items,
+                 int n_items, unsigned *counter) {
+  __shared__ int s_next;
+  for (;;) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_next = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int t = s_next;
+    __syncthreads();
+    if (t >= n_items) break;
+    const int2 bt = items[t];
+    const SParams<float> p = params[bt.x];
+    stage_flat<LIM, SEED, CX>(p, bt.y % p.tiles_x, bt.y / p.tiles_x);
+  }
+}
+
+// A work decomposition: kind 0 = 32 x 8 rectangles (z chunk zc), kind 1 =
+// flat runs of 32 cx w cells (FP32), packed into one int for the maps.
+struct Cfg {
+  int kind, cx, w, zc;
+};
+int encode(const Cfg &c) { return c.zc | (c.kind << 8) | (c.cx << 12) | (c.w << 16); }
+Cfg decode(int v) { return Cfg{(v >> 8) & 0xF, (v >> 12) & 0xF, (v >> 16) & 0xFF, v & 0xFF}; }
+
+template <int SEED>
+void *flat_kernel(int lim, int cx) {
+#define FL_FLAT(L)                                                        \
+  case L:                                                                 \
+    return cx == 1 ? (void *)k_batch_flat<L, SEED, 1>                     \
+                   : cx == 2 ? (void *)k_batch_flat<L, SEED, 2>           \
+                             : (void *)k_batch_flat<L, SEED, 4>;
+  switch (lim) {
+    FL_FLAT(LIM_UPWIND)
+    FL_FLAT(LIM_CENTRAL)
+    FL_FLAT(LIM_MINMOD)
+    FL_FLAT(LIM_VANLEER)
+    FL_FLAT(LIM_SUPERBEE)
+    FL_FLAT(LIM_SMART)
+  }
+#undef FL_FLAT
+  return nullptr;
+}
+
 template <class T, int SEED, bool PRE>
 void *kernel_ptr(int lim) {
   switch (lim) {
@@ -96,7 +147,11 @@ void *kernel_ptr(int lim) {
 
 // pre: FP64 boxes fold the flux product into the cell update with the
 // pre-scaled velocity w = dt (A/V) u of every box (as fl_step_rk does)
-void *batch_kernel(fl_dtype dt, int lim, int seed, bool pre) {
+void *batch_kernel(fl_dtype dt, int lim, int seed, bool pre, int cfg) {
+  const Cfg c = decode(cfg);
+  if (dt == FL_F32 && c.kind == 1)
+    return seed == SEED_PLAIN ? flat_kernel<SEED_PLAIN>(lim, c.cx)
+                              : flat_kernel<SEED_COMBINE>(lim, c.cx);
   if (dt == FL_F64) {
     if (pre)
       return seed == SEED_PLAIN ? kernel_ptr<double, SEED_PLAIN, true>(lim)
@@ -110,23 +165,33 @@ void *batch_kernel(fl_dtype dt, int lim, int seed, bool pre) {
 
 bool batch_prescales(fl_dtype dt) { return dt == FL_F64; }
 
-int tiles_x_of(const fl_mesh *m) { return (m->nx + TX - 1) / TX; }
-int tiles_y_of(const fl_mesh *m) { return (m->ny + BTY - 1) / BTY; }
+// work items of a box: rectangles (kind 0) or flat runs (kind 1) per plane
+int tiles_x_of(const fl_mesh *m, const Cfg &c) {
+  if (c.kind == 1) {
+    const long long run = 32LL * c.cx * c.w;
+    return (int)(((long long)m->nx * m->ny + run - 1) / run);
+  }
+  return (m->nx + TX - 1) / TX;
+}
+int tiles_y_of(const fl_mesh *m, const Cfg &c) {
+  return c.kind == 1 ? 1 : (m->ny + BTY - 1) / BTY;
+}
 int zchunk_of(const fl_mesh *m, int zc) { return std::min(zc, m->nz); }
 
-// (box, tile) list for a z chunk; tiles of one box are contiguous
-fl_status get_tiles(fl_batch *b, int zc, int2 **d, int *n) {
-  auto it = b->tiles.find(zc);
+// (box, item) list of a decomposition; items of one box are contiguous
+fl_status get_tiles(fl_batch *b, int cfg, int2 **d, int *n) {
+  auto it = b->tiles.find(cfg);
   if (it != b->tiles.end()) {
     *d = it->second.first;
     *n = it->second.second;
     return FL_OK;
   }
+  const Cfg c = decode(cfg);
   std::vector<int2> h;
   for (int i = 0; i < b->n; ++i) {
     const fl_mesh *m = b->meshes[i];
-    const int z = zchunk_of(m, zc);
-    const long long nt = (long long)tiles_x_of(m) * tiles_y_of(m) * ((m->nz + z - 1) / z);
+    const int z = zchunk_of(m, c.zc);
+    const long long nt = (long long)tiles_x_of(m, c) * tiles_y_of(m, c) * ((m->nz + z - 1) / z);
     for (long long t = 0; t < nt; ++t) h.push_back(make_int2(i, (int)t));
   }
   if (h.size() >= (1u << 31)) return fail(FL_EUNSUPPORTED, "too many tiles");
@@ -137,15 +202,16 @@ fl_status get_tiles(fl_batch *b, int zc, int2 **d, int *n) {
     cudaFree(dp);
     return fail(FL_ECUDA, "tile list upload failed");
   }
-  b->tiles[zc] = {dp, (int)h.size()};
+  b->tiles[cfg] = {dp, (int)h.size()};
   *d = dp;
   *n = (int)h.size();
   return FL_OK;
 }
 
 template <class T>
-SParams<T> box_params(const fl_mesh *m, int zc, const void *x, const void *thn, void *y,
+SParams<T> box_params(const fl_mesh *m, int cfg, const void *x, const void *thn, void *y,
                       const void *u, double dtime, int seed, double a, double bcoef) {
+  const Cfg c = decode(cfg);
   SParams<T> p;
   p.x = static_cast<const T *>(x);
   p.thn = static_cast<const T *>(thn);
@@ -171,9 +237,9 @@ SParams<T> box_params(const fl_mesh *m, int zc, const void *x, const void *thn, 
   p.g = (T)1;
   p.flip = 0;
   p.codes = nullptr;
-  p.tiles_x = tiles_x_of(m);
-  p.tiles_y = tiles_y_of(m);
-  p.zchunk = zchunk_of(m, zc);
+  p.tiles_x = tiles_x_of(m, c);
+  p.tiles_y = tiles_y_of(m, c);
+  p.zchunk = zchunk_of(m, c.zc);
   return p;
 }
 
@@ -189,7 +255,7 @@ size_t box_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk) {
 // Fill the staging table: stage s of box i at index s * n + i.  With pre,
 // every stage reads the box's w_f (left in its workspace by prescale_boxes).
 template <class T>
-void fill_params(fl_batch *b, int rk, int zc, const double *dtv, void *const *theta,
+void fill_params(fl_batch *b, int rk, int cfg, const double *dtv, void *const *theta,
                  const void *const *u, char *ws, size_t es, bool pre) {
   SParams<T> *h = static_cast<SParams<T> *>(b->h_params);
   size_t off = 0;
@@ -201,13 +267,13 @@ void fill_params(fl_batch *b, int rk, int zc, const double *dtv, void *const *th
     const void *uw = pre ? static_cast<const void *>(ws + off + (rk == 3 ? 2 : 1) * one) : u[i];
     off += box_ws_bytes(m, es == 8 ? FL_F64 : FL_F32, rk);
     if (rk == 3) {
-      h[0 * b->n + i] = box_params<T>(m, zc, theta[i], theta[i], A, uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
-      h[1 * b->n + i] = box_params<T>(m, zc, A, theta[i], B, uw, dtv[i], SEED_COMBINE, 0.75, 0.25);
+      h[0 * b->n + i] = box_params<T>(m, cfg, theta[i], theta[i], A, uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
+      h[1 * b->n + i] = box_params<T>(m, cfg, A, theta[i], B, uw, dtv[i], SEED_COMBINE, 0.75, 0.25);
       h[2 * b->n + i] =
-          box_params<T>(m, zc, B, theta[i], theta[i], uw, dtv[i], SEED_COMBINE, 1.0 / 3.0, 2.0 / 3.0);
+          box_params<T>(m, cfg, B, theta[i], theta[i], uw, dtv[i], SEED_COMBINE, 1.0 / 3.0, 2.0 / 3.0);
     } else {  // Euler: even step theta -> A, odd step A -> theta
-      h[0 * b->n + i] = box_params<T>(m, zc, theta[i], theta[i], A, uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
-      h[1 * b->n + i] = box_params<T>(m, zc, A, A, theta[i], uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
+      h[0 * b->n + i] = box_params<T>(m, cfg, theta[i], theta[i], A, uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
+      h[1 * b->n + i] = box_params<T>(m, cfg, A, A, theta[i], uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
     }
   }
 }
@@ -232,73 +298,86 @@ cudaError_t prescale_boxes(fl_batch *b, fl_dtype dt, int rk, const double *dtv,
   return e;
 }
 
-int persistent_grid(fl_dtype dt, int lim, int seed, bool pre) {
-  return resident_ctas(batch_kernel(dt, lim, seed, pre), TX * BTY, 0);
+dim3 block_of(int cfg) {
+  const Cfg c = decode(cfg);
+  return c.kind == 1 ? dim3(32, c.w) : dim3(TX, BTY);
+}
+
+int persistent_grid(fl_dtype dt, int lim, int seed, bool pre, int cfg) {
+  const dim3 b = block_of(cfg);
+  return resident_ctas(batch_kernel(dt, lim, seed, pre, cfg), (int)(b.x * b.y), 0);
 }
 
 // Enqueue one launch of stage s (seed) on st.
-cudaError_t enqueue_stage(fl_batch *b, fl_dtype dt, int lim, int s, int seed, bool pre,
+cudaError_t enqueue_stage(fl_batch *b, fl_dtype dt, int lim, int s, int seed, bool pre, int cfg,
                           int2 *tiles, int nt, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b->d_counters + s, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const char *params = static_cast<const char *>(b->d_params) + (size_t)s * b->n * param_size(dt);
   unsigned *ctr = b->d_counters + s;
   void *args[] = {(void *)&params, (void *)&tiles, (void *)&nt, (void *)&ctr};
-  return cudaLaunchKernel(batch_kernel(dt, lim, seed, pre),
-                          dim3(persistent_grid(dt, lim, seed, pre)), dim3(TX, BTY), args, 0, st);
+  return cudaLaunchKernel(batch_kernel(dt, lim, seed, pre, cfg),
+                          dim3(persistent_grid(dt, lim, seed, pre, cfg)), block_of(cfg), args, 0,
+                          st);
 }
 
 // Stage launches of one step (RK3: 3 stages; Euler: 2 steps, even and odd).
-cudaError_t enqueue_step(fl_batch *b, fl_dtype dt, int lim, int rk, bool pre, int2 *tiles, int nt,
-                         cudaStream_t st) {
+cudaError_t enqueue_step(fl_batch *b, fl_dtype dt, int lim, int rk, bool pre, int cfg,
+                         int2 *tiles, int nt, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (rk == 3) {
-    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);
-    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_COMBINE, pre, tiles, nt, st);
-    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 2, SEED_COMBINE, pre, tiles, nt, st);
+    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, cfg, tiles, nt, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_COMBINE, pre, cfg, tiles, nt, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 2, SEED_COMBINE, pre, cfg, tiles, nt, st);
   } else {
-    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);
-    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_PLAIN, pre, tiles, nt, st);
+    e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, cfg, tiles, nt, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 1, SEED_PLAIN, pre, cfg, tiles, nt, st);
   }
   return e;
 }
 
-fl_status upload_params(fl_batch *b, fl_dtype dt, int rk, int zc, const double *dtv,
+fl_status upload_params(fl_batch *b, fl_dtype dt, int rk, int cfg, const double *dtv,
                         void *const *theta, const void *const *u, void *ws, bool pre,
                         cudaStream_t st) {
   // the staging buffer may still feed the previous call's copy
   if (cudaEventSynchronize(b->params_done) != cudaSuccess) return fail(FL_ECUDA, "event sync");
   if (dt == FL_F64)
-    fill_params<double>(b, rk, zc, dtv, theta, u, static_cast<char *>(ws), 8, pre);
+    fill_params<double>(b, rk, cfg, dtv, theta, u, static_cast<char *>(ws), 8, pre);
   else
-    fill_params<float>(b, rk, zc, dtv, theta, u, static_cast<char *>(ws), 4, pre);
+    fill_params<float>(b, rk, cfg, dtv, theta, u, static_cast<char *>(ws), 4, pre);
   const size_t bytes = (size_t)MAXSTAGES * b->n * param_size(dt);
   cudaError_t e = cudaMemcpyAsync(b->d_params, b->h_params, bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(b->params_done, st);
   return e == cudaSuccess ? FL_OK : cuda_fail(e, "parameter upload");
 }
 
-// Autotune the z chunk with timed stage-1 launches (write workspace only).
+// Autotune the work decomposition with timed stage-1 launches (they write
+// workspace only): the candidates of the file header, fastest kept.
 fl_status tune(fl_batch *b, fl_dtype dt, int lim, int rk, const double *dtv, void *const *theta,
                const void *const *u, void *ws, bool pre, cudaStream_t st, int *best) {
-  const int cand[] = {8, 16, 32, 64};
+  std::vector<int> cand;
+  for (int zc : {8, 16, 32, 64}) cand.push_back(encode(Cfg{0, 0, BTY, zc}));
+  if (dt == FL_F32)
+    for (int cx : {1, 2, 4})
+      for (int w : {4, 8})
+        for (int zc : {16, 32, 64}) cand.push_back(encode(Cfg{1, cx, w, zc}));
   float best_ms = 1e30f;
-  *best = 16;
+  *best = cand[0];
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
     return fail(FL_ECUDA, "autotune event creation failed");
   }
   fl_status s = FL_OK;
-  for (int zc : cand) {
+  for (int cfg : cand) {
     int2 *tiles;
     int nt;
-    if ((s = get_tiles(b, zc, &tiles, &nt)) != FL_OK) break;
-    if ((s = upload_params(b, dt, rk, zc, dtv, theta, u, ws, pre, st)) != FL_OK) break;
-    cudaError_t e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);  // warm-up
+    if ((s = get_tiles(b, cfg, &tiles, &nt)) != FL_OK) break;
+    if ((s = upload_params(b, dt, rk, cfg, dtv, theta, u, ws, pre, st)) != FL_OK) break;
+    cudaError_t e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, cfg, tiles, nt, st);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-      e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);
+      e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, cfg, tiles, nt, st);
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) {
@@ -309,7 +388,7 @@ fl_status tune(fl_batch *b, fl_dtype dt, int lim, int rk, const double *dtv, voi
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) {
       best_ms = ms;
-      *best = zc;
+      *best = cfg;
     }
   }
   cudaEventDestroy(e0);
@@ -402,22 +481,22 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
     const cudaError_t e = prescale_boxes(b, dt, rk, dtv, u_f, static_cast<char *>(ws), st);
     if (e != cudaSuccess) return cuda_fail(e, "velocity pre-scaling");
   }
-  // z chunk: tuned once per (limiter, dtype, rk, pre)
+  // work decomposition: tuned once per (limiter, dtype, rk, pre)
   const auto tkey = std::make_tuple((int)lim, (int)dt * 2 + (pre ? 1 : 0), rk);
-  int zc;
+  int cfg;
   auto tit = b->tuned.find(tkey);
   if (tit == b->tuned.end()) {
-    if ((s = tune(b, dt, lim, rk, dtv, theta, u_f, ws, pre, st, &zc)) != FL_OK) return s;
-    b->tuned[tkey] = zc;
+    if ((s = tune(b, dt, lim, rk, dtv, theta, u_f, ws, pre, st, &cfg)) != FL_OK) return s;
+    b->tuned[tkey] = cfg;
   } else {
-    zc = tit->second;
+    cfg = tit->second;
   }
   int2 *tiles;
   int nt;
-  if ((s = get_tiles(b, zc, &tiles, &nt)) != FL_OK) return s;
-  if ((s = upload_params(b, dt, rk, zc, dtv, theta, u_f, ws, pre, st)) != FL_OK) return s;
-  // one graph per (limiter, dtype + pre, rk, z chunk): a step's stage launches
-  const auto gkey = std::make_tuple((int)lim, (int)dt * 2 + (pre ? 1 : 0), rk, zc);
+  if ((s = get_tiles(b, cfg, &tiles, &nt)) != FL_OK) return s;
+  if ((s = upload_params(b, dt, rk, cfg, dtv, theta, u_f, ws, pre, st)) != FL_OK) return s;
+  // one graph per (limiter, dtype + pre, rk, decomposition): a step's stage launches
+  const auto gkey = std::make_tuple((int)lim, (int)dt * 2 + (pre ? 1 : 0), rk, cfg);
   cudaGraphExec_t exec = nullptr;
   auto git = b->graphs.find(gkey);
   if (git != b->graphs.end()) {
@@ -429,7 +508,7 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = enqueue_step(b, dt, lim, rk, pre, tiles, nt, cap);
+      cudaError_t e2 = enqueue_step(b, dt, lim, rk, pre, cfg, tiles, nt, cap);
       e = cudaStreamEndCapture(cap, &g);
       if (e2 != cudaSuccess) e = e2;
     }
@@ -447,7 +526,7 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
     // even stage alone and copies A back
     for (int64_t n = 0; n + 1 < nsteps && e == cudaSuccess; n += 2) e = cudaGraphLaunch(exec, st);
     if (e == cudaSuccess && (nsteps & 1)) {
-      e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, tiles, nt, st);
+      e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, cfg, tiles, nt, st);
       size_t off = 0;
       for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         const fl_mesh *m = b->meshes[i];
@@ -459,6 +538,49 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
   }
   if (e == cudaSuccess) e = cudaEventRecord(b->last_call, st);
   if (e != cudaSuccess) return cuda_fail(e, "batched step");
+  return FL_OK;
+}
+
+fl_status fl_batch_tiling(const fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, int *kind,
+                          int *cells_per_thread, int *warps, int *z_chunk) {
+  if (b == nullptr) return fail(FL_EINVAL, "batch is NULL");
+  fl_status s = check_enums(lim, dt);
+  if (s != FL_OK) return s;
+  for (int pre : {batch_prescales(dt) ? 1 : 0, batch_prescales(dt) ? 0 : 1}) {
+    auto it = b->tuned.find(std::make_tuple((int)lim, (int)dt * 2 + pre, rk));
+    if (it == b->tuned.end()) continue;
+    const Cfg c = decode(it->second);
+    if (kind) *kind = c.kind;
+    if (cells_per_thread) *cells_per_thread = c.kind == 1 ? c.cx : 1;
+    if (warps) *warps = c.w;
+    if (z_chunk) *z_chunk = c.zc;
+    return FL_OK;
+  }
+  return fail(FL_EINVAL, "no decomposition chosen yet for this limiter, dtype and rk_order");
+}
+
+fl_status fl_batch_set_tiling(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, int kind,
+                              int cells_per_thread, int warps, int z_chunk) {
+  if (b == nullptr) return fail(FL_EINVAL, "batch is NULL");
+  fl_status s = check_enums(lim, dt);
+  if (s != FL_OK) return s;
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (z_chunk < 1 || z_chunk > 255) return fail(FL_EINVAL, "z_chunk must be in 1 .. 255");
+  Cfg c{kind, 0, BTY, z_chunk};
+  if (kind == 0) {
+    if (cells_per_thread != 1 || warps != BTY)
+      return fail(FL_EINVAL, "rectangles take 1 cell per thread and %d warps", BTY);
+  } else if (kind == 1) {
+    if (dt != FL_F32) return fail(FL_EUNSUPPORTED, "flat runs are an FP32 decomposition");
+    if (cells_per_thread != 1 && cells_per_thread != 2 && cells_per_thread != 4)
+      return fail(FL_EINVAL, "cells_per_thread must be 1, 2 or 4");
+    if (warps < 1 || warps > 8) return fail(FL_EINVAL, "warps must be in 1 .. 8");
+    c.cx = cells_per_thread;
+    c.w = warps;
+  } else {
+    return fail(FL_EINVAL, "unknown decomposition kind %d", kind);
+  }
+  for (int pre : {0, 1}) b->tuned[std::make_tuple((int)lim, (int)dt * 2 + pre, rk)] = encode(c);
   return FL_OK;
 }
 

@@ -92,3 +92,74 @@ def test_batched_config_equals_single_mesh_path(fl):
     fl.fl_batch_destroy(batch)
     for m in meshes:
         m.close()
+
+
+# every work decomposition the autotuner may pick, fixed with
+# fl_batch_set_tiling: (kind, cells per thread, warps, z chunk)
+TILINGS32 = [(0, 1, 8, 16), (1, 1, 8, 16), (1, 2, 4, 32), (1, 4, 8, 64), (1, 4, 4, 3),
+             (1, 2, 1, 7)]
+
+
+@pytest.mark.parametrize("tiling", TILINGS32)
+@pytest.mark.parametrize("rk", [1, 3])
+@pytest.mark.parametrize("lim", ["minmod", "vanleer", "superbee", "smart"])
+def test_batch_fp32_every_tiling_matches_oracle(fl, lim, rk, tiling):
+    # the flat-run tile and the rectangles give the bits of the single-mesh
+    # FP32 kernels (the same face flux and cell-sum order), so every box is
+    # checked against the oracle per step and against the single-mesh path
+    boxes = _boxes(seed=2)
+    dtype = torch.float32
+    meshes = [fl.Mesh.structured(*b[0].dims, *b[0].h) for b in boxes]
+    batch = fl.fl_batch_create([m.handle for m in meshes])
+    fl.fl_batch_set_tiling(batch, lim, dtype, rk, *tiling)
+    assert fl.fl_batch_tiling(batch, lim, dtype, rk) == tiling
+    th0 = [b[1].astype(np.float32).astype(np.float64) for b in boxes]
+    us = [b[2].astype(np.float32).astype(np.float64) for b in boxes]
+    th = [torch.tensor(t, dtype=dtype, device="cuda") for t in th0]
+    ud = [torch.tensor(u, dtype=dtype, device="cuda") for u in us]
+    dts = [b[3] for b in boxes]
+    nb = fl.fl_batch_workspace_size(batch, dtype, rk)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    fl.fl_batch_step_rk(batch, lim, dtype, rk, dts, 1, th, ud, ws, nb)
+    for (mesh, _, _, dt), t0, u, g in zip(boxes, th0, us, th):
+        ref = oracle.step(mesh, lim, rk, dt, 1, u, t0)
+        got = g.cpu().double().numpy()
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= TOL[dtype]
+    # and two more steps against the single-mesh path (the same FP32 bits)
+    ref = [t.clone() for t in th]
+    for m, t, u, dt in zip(meshes, ref, ud, dts):
+        fl.step_rk(m, lim, t, u, dt, 2, rk_order=rk)
+    fl.fl_batch_step_rk(batch, lim, dtype, rk, dts, 2, th, ud, ws, nb)
+    for i, (a, b) in enumerate(zip(th, ref)):
+        if boxes[i][0].dims[1] == 1 and boxes[i][0].dims[2] == 1:
+            # 1D lines run the resident line kernel on the single-mesh path
+            assert float((a - b).abs().max() / b.abs().max()) <= 2 * TOL[dtype]
+        else:
+            assert torch.equal(a, b), (i, boxes[i][0].dims)
+    fl.fl_batch_destroy(batch)
+    for m in meshes:
+        m.close()
+
+
+def test_batch_tiling_query_and_validation(fl):
+    boxes = _boxes(seed=3)[:3]
+    meshes = [fl.Mesh.structured(*b[0].dims, *b[0].h) for b in boxes]
+    batch = fl.fl_batch_create([m.handle for m in meshes])
+    with pytest.raises(fl.FLError):  # nothing chosen yet
+        fl.fl_batch_tiling(batch, "superbee", torch.float32, 3)
+    th = [torch.tensor(b[1], dtype=torch.float32, device="cuda") for b in boxes]
+    us = [torch.tensor(b[2], dtype=torch.float32, device="cuda") for b in boxes]
+    nb = fl.fl_batch_workspace_size(batch, torch.float32, 3)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    fl.fl_batch_step_rk(batch, "superbee", torch.float32, 3, [b[3] for b in boxes], 1, th, us,
+                        ws, nb)
+    kind, cx, w, zc = fl.fl_batch_tiling(batch, "superbee", torch.float32, 3)
+    assert kind in (0, 1) and cx in (1, 2, 4) and 1 <= w <= 8 and 1 <= zc <= 255
+    for bad in [(2, 1, 8, 16), (1, 3, 8, 16), (1, 2, 9, 16), (0, 2, 8, 16), (1, 2, 4, 0)]:
+        with pytest.raises(fl.FLError):
+            fl.fl_batch_set_tiling(batch, "superbee", torch.float32, 3, *bad)
+    with pytest.raises(fl.FLError):  # flat runs are FP32 only
+        fl.fl_batch_set_tiling(batch, "superbee", torch.float64, 3, 1, 2, 4, 16)
+    fl.fl_batch_destroy(batch)
+    for m in meshes:
+        m.close()
