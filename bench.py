@@ -726,7 +726,25 @@ def run_config_batched(args):
         out[dname] = {"batched_ms_per_step": ms_b, "separate_ms_per_step": ms_s,
                       "batched_face_updates_per_s": rate_b,
                       "separate_face_updates_per_s": rate_s,
-                      "speedup": ms_s / ms_b}
+                      "speedup": ms_s / ms_b,
+                      "tiling": dict(zip(["kind", "cells_per_thread", "warps", "z_chunk"],
+                                         fl.fl_batch_tiling(batch, "vanleer", dt, 3)))}
+        if getattr(args, "tiling_sweep", False):
+            # every candidate of the autotuner, fixed in turn and timed alike
+            sweep = {}
+            cands = [(0, 1, 8, z) for z in (8, 16, 32, 64)]
+            if dt == torch.float32:
+                cands += [(1, c, w, z) for c in (1, 2, 4) for w in (4, 8) for z in (16, 32, 64)]
+            for t in cands:
+                fl.fl_batch_set_tiling(batch, "vanleer", dt, 3, *t)
+                fl.fl_batch_step_rk(batch, "vanleer", dt, 3, dts, 2, th, us, ws, nb)
+                torch.cuda.synchronize()
+                e0.record()
+                fl.fl_batch_step_rk(batch, "vanleer", dt, 3, dts, args.steps, th, us, ws, nb)
+                e1.record()
+                torch.cuda.synchronize()
+                sweep["%d/%d/%d/%d" % t] = round(e0.elapsed_time(e1) / args.steps, 4)
+            out[dname]["tiling_sweep_ms"] = sweep
         fl.fl_batch_destroy(batch)
         for mm in meshes:
             mm.close()
@@ -817,7 +835,9 @@ def run_config_deformation(args):
     fl.build()
     n = args.n
     t0 = time.perf_counter()
-    wl = W.config_deformation(n)
+    # explicit face arrays only where the oracle's CPU baseline needs them
+    with_cpu = not args.no_cpu and n <= 288
+    wl = W.config_deformation(n, faces=with_cpu)
     t_gen = time.perf_counter() - t0
     g = wl.extra["g"]
     m = fl.Mesh.structured(n, n, n, *wl.mesh.h)
@@ -849,7 +869,7 @@ def run_config_deformation(args):
     hbm_peak, _ = peaks()
     gbs = 40.0 * m.n_cells * wl.nsteps / (ms * 1e-3) / 1e9
     cpu = None
-    if not args.no_cpu:
+    if with_cpu:
         import oracle
         threads = oracle.set_threads(os.cpu_count() or 1)
         om = oracle.OracleMesh(wl.mesh)
@@ -1077,6 +1097,8 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other configurations' numbers in the default line")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--tiling-sweep", action="store_true",
+                    help="--config batched: also time every decomposition the autotuner tries")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")
     ap.add_argument("--config", default="tg256",

@@ -49,6 +49,8 @@ class Mesh:
 
     @property
     def n_faces(self) -> int:
+        if self.face_cells is None:  # a structured box given by dims and h only
+            return int(self.n_cells) * len(active_axes(self.dims))
         return int(self.face_cells.shape[0])
 
 
@@ -90,6 +92,15 @@ def structured_mesh(nx: int, ny: int = 1, nz: int = 1, hx: float = 1.0,
         areas = np.zeros(0)
     volumes = np.full(n, hx * hy * hz)
     return Mesh(n, face_cells, normals, areas, volumes, dims=dims, h=hs)
+
+
+def structured_box(nx: int, ny: int = 1, nz: int = 1, hx: float = 1.0, hy: float = 1.0,
+                   hz: float = 1.0) -> Mesh:
+    """A periodic structured box by its sizes and spacings only, without the
+    explicit face arrays of structured_mesh (which take 40 bytes per face:
+    23 GB at 576^3).  For the GPU library, which needs dims and h alone; the
+    oracle needs structured_mesh."""
+    return Mesh(nx * ny * nz, None, None, None, None, dims=(nx, ny, nz), h=(hx, hy, hz))
 
 
 def stretched_mesh(wx, wy=(1.0,), wz=(1.0,)) -> Mesh:
@@ -312,6 +323,23 @@ def _coords(dims, h):
     return i, j, k, hx, hy, hz
 
 
+def _coords_b(dims, h):
+    """The cell indices i, j, k as broadcastable float arrays of shapes
+    (1, 1, nx), (1, ny, 1), (nz, 1, 1): element-wise expressions of them give
+    the (nz, ny, nx) field of the flat arrays of _coords, value for value, with
+    one full-size array per result instead of one per coordinate."""
+    nx, ny, nz = dims
+    i = np.arange(nx, dtype=np.float64).reshape(1, 1, nx)
+    j = np.arange(ny, dtype=np.float64).reshape(1, ny, 1)
+    k = np.arange(nz, dtype=np.float64).reshape(nz, 1, 1)
+    return i, j, k, h[0], h[1], h[2]
+
+
+def _full(a, dims):
+    nx, ny, nz = dims
+    return np.broadcast_to(a, (nz, ny, nx)).ravel()
+
+
 def curl_face_velocity(dims, h, potential):
     """Face normal velocities ``u_f`` (layout of :func:`structured_mesh`) from the
     discrete curl of a vector potential ``A = potential(axis, x, y, z)``.
@@ -321,7 +349,9 @@ def curl_face_velocity(dims, h, potential):
     the flux through a face is the circulation of A around its four edges
     (Stokes), divided by the face area.
     """
-    i, j, k, hx, hy, hz = _coords(dims, h)
+    # the coordinates broadcast over the (nz, ny, nx) grid (the potentials are
+    # element-wise, so each value is the flat evaluation's, bit for bit)
+    i, j, k, hx, hy, hz = _coords_b(dims, h)
     xc, yc, zc = (i + 0.5) * hx, (j + 0.5) * hy, (k + 0.5) * hz
     xp, yp, zp = (i + 1.0) * hx, (j + 1.0) * hy, (k + 1.0) * hz
     xm, ym, zm = i * hx, j * hy, k * hz
@@ -331,15 +361,15 @@ def curl_face_velocity(dims, h, potential):
     if 0 in axes:  # x-face (x_{i+1/2}, y_j, z_k): dAz/dy - dAy/dz
         circ = (hz * (A(2, xp, yp, zc) - A(2, xp, ym, zc))
                 - hy * (A(1, xp, yc, zp) - A(1, xp, yc, zm)))
-        out.append(circ / (hy * hz))
+        out.append(_full(circ / (hy * hz), dims))
     if 1 in axes:  # y-face (x_i, y_{j+1/2}, z_k): dAx/dz - dAz/dx
         circ = (hx * (A(0, xc, yp, zp) - A(0, xc, yp, zm))
                 - hz * (A(2, xp, yp, zc) - A(2, xm, yp, zc)))
-        out.append(circ / (hx * hz))
+        out.append(_full(circ / (hx * hz), dims))
     if 2 in axes:  # z-face (x_i, y_j, z_{k+1/2}): dAy/dx - dAx/dy
         circ = (hy * (A(1, xp, yc, zp) - A(1, xm, yc, zp))
                 - hx * (A(0, xc, yp, zp) - A(0, xc, ym, zp)))
-        out.append(circ / (hx * hy))
+        out.append(_full(circ / (hx * hy), dims))
     return np.concatenate(out) if out else np.zeros(0)
 
 
@@ -472,10 +502,10 @@ def deformation_potential(n):
 def sphere_indicator(n, centre=(0.35, 0.35, 0.35), radius=0.15):
     """1 in the cells of [0, 1]^3 (n^3) whose centre lies in the sphere, else 0."""
     h = 1.0 / n
-    i, j, k, _, _, _ = _coords((n, n, n), (h, h, h))
+    i, j, k, _, _, _ = _coords_b((n, n, n), (h, h, h))
     x, y, z = (i + 0.5) * h, (j + 0.5) * h, (k + 0.5) * h
     r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2
-    return (r2 <= radius * radius).astype(np.float64)
+    return _full(r2 <= radius * radius, (n, n, n)).astype(np.float64)
 
 
 def max_outflow_rate(dims, h, u):
@@ -504,16 +534,17 @@ def modulation_factors(nsteps, dt, rk, period, t0=0.0):
     return np.cos(math.pi * st / period).ravel()
 
 
-def config_deformation(n=72, courant=0.5, period=3.0, rk=1, limiter="superbee"):
+def config_deformation(n=72, courant=0.5, period=3.0, rk=1, limiter="superbee", faces=True):
     """Section 4.1: a sphere (r = 0.15 at (0.35, 0.35, 0.35)) in [0, 1]^3 on
     n^3 hexahedra, deformed by eq. rhodonea for t in [0, T], T = 3, forward
     Euler (Algorithm 5) with superbee.  The velocity at time t is
     cos(pi t / T) u_f with u_f the discrete curl of deformation_potential;
     dt makes the largest per-cell outflow Courant number `courant` and divides
     T into a whole number of steps (the flow reverses, so theta(T) returns
-    to the sphere up to the scheme's error)."""
+    to the sphere up to the scheme's error).  faces=False leaves out the
+    explicit face arrays (structured_box: for the GPU alone, large n)."""
     h = 1.0 / n
-    mesh = structured_mesh(n, n, n, h, h, h)
+    mesh = structured_mesh(n, n, n, h, h, h) if faces else structured_box(n, n, n, h, h, h)
     u = curl_face_velocity((n, n, n), (h, h, h), deformation_potential(n))
     th = sphere_indicator(n)
     dt = courant / max_outflow_rate((n, n, n), (h, h, h), u)
