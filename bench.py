@@ -61,8 +61,9 @@ NCU_TRAFFIC = {
     ("f64", "smart", 256): (830.2e6, "k_struct_stage<double, SMART, COMBINE, PRE>, "
                             "algorithmic 805.3e6, "
                             "profiles/k_struct_stage_f64_vanleer_smart_tg256.md"),
-    ("f32", "superbee", 256): (330.9e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
-                               "algorithmic 335.5e6 (20 B x 16.8M cells)"),
+    ("f32", "superbee", 256): (330.8e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
+                               "algorithmic 335.5e6 (20 B x 16.8M cells), "
+                               "profiles/k_struct_stage_tma_f32_superbee_tg256.md"),
 }
 
 
