@@ -34,16 +34,18 @@ sys.path.insert(0, ROOT)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
 # The FP64 stage kernel is bound by the FP64 pipe, not by HBM: the busy
 # fraction of that pipe in one ncu capture of the current kernel (the
 # profile summary named beside it), reported next to the HBM roofline.
 NCU_FP64_PIPE = {
-    ("f64", "superbee", 256): (0.843, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
-                               "profiles/k_struct_stage_f64_superbee_tg256.md"),
-    ("f64", "vanleer", 256): (0.629, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
-                              "profiles/k_struct_stage_f64_vanleer_smart_tg256.md"),
-    ("f64", "smart", 256): (0.821, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
-                            "profiles/k_struct_stage_f64_vanleer_smart_tg256.md"),
+    ("f64", "superbee", 256): (0.842, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
+                               "profiles/k_struct_stage_traffic_tg256.md"),
+    ("f64", "vanleer", 256): (0.627, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
+                              "profiles/k_struct_stage_traffic_tg256.md"),
+    ("f64", "smart", 256): (0.818, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
+                            "profiles/k_struct_stage_traffic_tg256.md"),
 }
 
 
@@ -52,18 +54,16 @@ NCU_FP64_PIPE = {
 # FP64 superbee, RK stages 2-3 (65 % of the step's kernel time); FP32
 # superbee TMA kernel, RK stage 1.  Keyed by (dtype, limiter, n).
 NCU_TRAFFIC = {
-    ("f64", "superbee", 256): (808.3e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
+    ("f64", "superbee", 256): (808.4e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
                                "algorithmic 805.3e6 (48 B x 16.8M cells), "
-                               "profiles/k_struct_stage_f64_superbee_tg256.md"),
-    ("f64", "vanleer", 256): (833.4e6, "k_struct_stage<double, VANLEER, COMBINE, PRE>, "
-                              "algorithmic 805.3e6, "
-                              "profiles/k_struct_stage_f64_vanleer_smart_tg256.md"),
+                               "profiles/k_struct_stage_traffic_tg256.md"),
+    ("f64", "vanleer", 256): (832.5e6, "k_struct_stage<double, VANLEER, COMBINE, PRE>, "
+                              "algorithmic 805.3e6, profiles/k_struct_stage_traffic_tg256.md"),
     ("f64", "smart", 256): (830.2e6, "k_struct_stage<double, SMART, COMBINE, PRE>, "
-                            "algorithmic 805.3e6, "
-                            "profiles/k_struct_stage_f64_vanleer_smart_tg256.md"),
-    ("f32", "superbee", 256): (330.8e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
+                            "algorithmic 805.3e6, profiles/k_struct_stage_traffic_tg256.md"),
+    ("f32", "superbee", 256): (330.5e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
                                "algorithmic 335.5e6 (20 B x 16.8M cells), "
-                               "profiles/k_struct_stage_tma_f32_superbee_tg256.md"),
+                               "profiles/k_struct_stage_traffic_tg256.md"),
 }
 
 
@@ -256,7 +256,9 @@ def run_ours(args):
             "traffic_kernel": traffic_note,
             "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS hbm_gbs)"
                          if peak_kind == "measured" else "fallback copy bandwidth",
-            "bytes_per_cell_step": bytes_step // C}
+            "bytes_per_cell_step": bytes_step // C,
+            # the same achieved bandwidth against the nominal 7.9 TB/s of HBM3e
+            "frac_of_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
     fp64 = None
     if args.dtype == "f64":
         ops_step = sum(stage_fp64_ops_per_cell(lim, s) for s in range(3)) * C
@@ -922,6 +924,79 @@ def algebraic_step_bytes(C, F, wT, wM):
     return b
 
 
+def run_config_decomp(args):
+    """256^3 Taylor-Green, superbee, FP64 SSP-RK3 split into z-slabs, one
+    per rank, with the halo exchanged before every stage (torch.distributed
+    point-to-point, NCCL between GPUs; a single rank exchanges with itself):
+    steps with the stage's interior overlapping the exchange, steps that
+    exchange first, and (one rank) fl_step_rk on the whole mesh.  Strong
+    scaling: the 256^3 mesh is fixed and split."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    from paper_2110_03044_gb300.decomp import Slab, SlabRollout, TorchTransport
+    from paper_2110_03044_gb300.replicas import whole_job_rate
+    ws_, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    fl.build()
+    n, lim = args.n, args.limiter
+    wl = build_workload(n, lim)
+    dims = (n, n, n)
+    slab = Slab(dims, rank, ws_)
+    ug = torch.tensor(wl.u, device="cuda")
+    thg = torch.tensor(wl.theta0, device="cuda")
+    F = 3 * n ** 3
+    e0, e1 = _events()
+    out = {}
+    for overlap in (True, False):
+        ro = SlabRollout(slab, wl.mesh.h, ug, lim, torch.float64, wl.dt,
+                         transport=TorchTransport(), overlap=overlap)
+        tl = ro.local_field(thg)
+        ro.step(tl, 3, args.warmup)
+        torch.cuda.synchronize()
+        if ws_ > 1:
+            dist.barrier()
+        e0.record()
+        ro.step(tl, 3, args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        rate, ms = whole_job_rate(F * 3 * args.steps / ws_, e0.elapsed_time(e1), device="cuda")
+        out["overlap" if overlap else "exchange_first"] = {
+            "face_updates_per_s": rate, "ms_per_step": ms / args.steps,
+            "launches_per_stage": 3 if overlap and slab.nz_local > 4 else 1}
+        ro.close()
+    if ws_ == 1:
+        m = fl.Mesh.structured(n, n, n, *wl.mesh.h)
+        ws, nb = fl.workspace_for(m, torch.float64, 3)
+        th = thg.clone()
+        fl.fl_step_rk(m.handle, lim, torch.float64, 3, wl.dt, args.warmup, th, ug, ws, nb)
+        torch.cuda.synchronize()
+        e0.record()
+        fl.fl_step_rk(m.handle, lim, torch.float64, 3, wl.dt, args.steps, th, ug, ws, nb)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["whole_mesh_fl_step_rk"] = {"face_updates_per_s": F * 3 * args.steps / (ms * 1e-3),
+                                        "ms_per_step": ms / args.steps}
+        m.close()
+    if ws_ > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    return {"metric": "decomposed limited-convection face-updates/s (z-slabs, SSP-RK3)",
+            "value": out["overlap"]["face_updates_per_s"], "unit": "face-updates/s",
+            "n_gpus": ws_, "scaling": "strong", "dtype": "f64", "results": out,
+            "config": {"workload": "taylor_green_%d^3_%s_ssprk3_zslabs" % (n, lim),
+                       "halo_planes": slab.halo,
+                       "halo_bytes_per_stage_per_rank": 2 * slab.halo * n * n * 8,
+                       "transport": "nccl p2p" if ws_ > 1 else "local copy (one rank)",
+                       "parallelism": "z-slabs over %d ranks" % ws_}}
+
+
 def run_config_algebraic(args):
     """The paper's stencil-vs-algebraic comparison (Section 3's Table 2 and
     its roofline study) on GB300: one forward-Euler superbee step of the
@@ -1110,7 +1185,7 @@ def main():
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")
     ap.add_argument("--config", default="tg256",
                     choices=["tg256", "1d", "unstructured", "batched", "adjoint", "deformation",
-                             "algebraic", "blocked", "stretched", "polyhedra"])
+                             "algebraic", "blocked", "stretched", "polyhedra", "decomp"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -1123,7 +1198,7 @@ def main():
               "deformation": run_config_deformation,
               "algebraic": run_config_algebraic, "blocked": run_config_blocked,
               "stretched": run_config_stretched,
-              "polyhedra": run_config_polyhedra}[args.config]
+              "polyhedra": run_config_polyhedra, "decomp": run_config_decomp}[args.config]
         line = fn(args)
         if line is not None:
             print(json.dumps(line))

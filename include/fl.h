@@ -299,6 +299,22 @@ fl_status fl_step_rk_stage(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dty
                            const void *u_f, const void *w_f, void *stream);
 
 /*
+ * fl_step_rk_stage over the z planes [z_begin, z_end) of a structured mesh
+ * only: the cells c = i + nx (j + ny k) with z_begin <= k < z_end get the
+ * bits fl_step_rk_stage gives them; y keeps its other planes.  Each updated
+ * plane reads x within two planes of itself (periodic in z), so a z-slab
+ * domain decomposition (Section 4's split runs) can update the planes that
+ * need no ghost plane while the halo exchange is in flight, then the planes
+ * next to its cuts.  Arguments as fl_step_rk_stage.  FL_EUNSUPPORTED on a
+ * face-based mesh; FL_EINVAL unless 0 <= z_begin <= z_end <= nz (an empty
+ * range runs nothing).  One kernel launch.
+ */
+fl_status fl_step_rk_stage_planes(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                                  int rk_order, int stage, double dt, int z_begin, int z_end,
+                                  const void *theta_n, const void *x, void *y, const void *u_f,
+                                  const void *w_f, void *stream);
+
+/*
  * w_f = dt (A_f / V) u_f per face (Algorithm 4's M U with the step size:
  * structured meshes take A/V = 1/h of the face's axis, face-based meshes
  * w_f = dt A_f u_f with 1/V applied per cell), the velocity fl_step_rk_stage
@@ -407,6 +423,20 @@ fl_status fl_step_rk_stage_adjoint(const fl_mesh *mesh, fl_limiter limiter, fl_d
                                    int rk_order, int stage, double dt, const void *x,
                                    const void *mu, const void *lam_a, const void *lam_b,
                                    void *out, const void *u_f, const void *w_f, void *stream);
+
+/*
+ * fl_step_rk_stage_adjoint over the z planes [z_begin, z_end) of a
+ * structured mesh only (out keeps its other planes), the reverse
+ * counterpart of fl_step_rk_stage_planes: an updated plane reads mu within
+ * two planes and x within three planes of itself.  Arguments as
+ * fl_step_rk_stage_adjoint; FL_EUNSUPPORTED on a face-based mesh, FL_EINVAL
+ * unless 0 <= z_begin <= z_end <= nz.  One kernel launch.
+ */
+fl_status fl_step_rk_stage_adjoint_planes(const fl_mesh *mesh, fl_limiter limiter,
+                                          fl_dtype dtype, int rk_order, int stage, double dt,
+                                          int z_begin, int z_end, const void *x, const void *mu,
+                                          const void *lam_a, const void *lam_b, void *out,
+                                          const void *u_f, const void *w_f, void *stream);
 
 /* Bytes of device workspace fl_step_rk_adjoint needs. */
 fl_status fl_adjoint_workspace_size(const fl_mesh *mesh, fl_dtype dtype, int rk_order,

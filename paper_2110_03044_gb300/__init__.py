@@ -37,9 +37,11 @@ ABI_SYMBOLS = [
     "fl_mesh_to_internal", "fl_mesh_to_user",
     "fl_conv_limited_apply",
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_modulated",
-    "fl_step_rk_noalloc", "fl_step_rk_blocked", "fl_step_rk_stage", "fl_velocity_prescale",
+    "fl_step_rk_noalloc", "fl_step_rk_blocked", "fl_step_rk_stage", "fl_step_rk_stage_planes",
+    "fl_velocity_prescale",
     "fl_conv_limited_adjoint",
-    "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_stage_adjoint", "fl_step_rk_checkpointed",
+    "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_stage_adjoint",
+    "fl_step_rk_stage_adjoint_planes", "fl_step_rk_checkpointed",
     "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
     "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_tiling", "fl_batch_set_tiling",
     "fl_batch_destroy",
@@ -102,10 +104,13 @@ def lib():
             "fl_step_rk_noalloc": (I, [P, I, I, I, D, I64, P, P, P]),
             "fl_step_rk_blocked": (I, [P, I, I, I, D, I64, P, P, P, SZ, P]),
             "fl_step_rk_stage": (I, [P, I, I, I, I, D, P, P, P, P, P, P]),
+            "fl_step_rk_stage_planes": (I, [P, I, I, I, I, D, I, I, P, P, P, P, P, P]),
             "fl_velocity_prescale": (I, [P, I, D, P, P, P]),
             "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
             "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
             "fl_step_rk_stage_adjoint": (I, [P, I, I, I, I, D, P, P, P, P, P, P, P, P]),
+            "fl_step_rk_stage_adjoint_planes": (I, [P, I, I, I, I, D, I, I, P, P, P, P, P, P, P,
+                                                    P]),
             "fl_step_rk_adjoint": (I, [P, I, I, I, D, I64, I64, P, P, P, P, P, SZ, P]),
             "fl_step_rk_checkpointed": (I, [P, I, I, I, D, I64, I64, P, P, P, SZ, P]),
             "fl_step_rk_adjoint_from_checkpoints": (I, [P, I, I, I, D, I64, I64, P, P, P, P,
@@ -317,6 +322,17 @@ def fl_step_rk_stage(mesh, limiter, dtype, rk_order, stage, dt, theta_n, x, y, u
                                   _fptr(w_f, c), _stream(stream)))
 
 
+def fl_step_rk_stage_planes(mesh, limiter, dtype, rk_order, stage, dt, z_begin, z_end, theta_n,
+                            x, y, u_f, w_f=None, stream=None):
+    """fl_step_rk_stage over the z planes [z_begin, z_end) of a structured
+    mesh only (see fl.h)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_stage_planes(mesh, _lim(limiter), c, int(rk_order), int(stage),
+                                         float(dt), int(z_begin), int(z_end), _fptr(theta_n, c),
+                                         _fptr(x, c), _fptr(y, c), _fptr(u_f, c), _fptr(w_f, c),
+                                         _stream(stream)))
+
+
 def fl_velocity_prescale(mesh, dtype, dt, u_f, w_f, stream=None):
     """w_f = dt (A/V) u_f, the velocity fl_step_rk_stage takes in FP64."""
     c = dtype_code(dtype)
@@ -374,6 +390,17 @@ def fl_step_rk_stage_adjoint(mesh, limiter, dtype, rk_order, stage, dt, x, mu, l
                                           float(dt), _fptr(x, c), _fptr(mu, c), _fptr(lam_a, c),
                                           _fptr(lam_b, c), _fptr(out, c), _fptr(u_f, c),
                                           _fptr(w_f, c), _stream(stream)))
+
+
+def fl_step_rk_stage_adjoint_planes(mesh, limiter, dtype, rk_order, stage, dt, z_begin, z_end,
+                                    x, mu, lam_a, lam_b, out, u_f, w_f=None, stream=None):
+    """fl_step_rk_stage_adjoint over the z planes [z_begin, z_end) of a
+    structured mesh only (see fl.h)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_stage_adjoint_planes(
+        mesh, _lim(limiter), c, int(rk_order), int(stage), float(dt), int(z_begin), int(z_end),
+        _fptr(x, c), _fptr(mu, c), _fptr(lam_a, c), _fptr(lam_b, c), _fptr(out, c),
+        _fptr(u_f, c), _fptr(w_f, c), _stream(stream)))
 
 
 def fl_adjoint_workspace_size(mesh, dtype, rk_order, nsteps, checkpoint_every):

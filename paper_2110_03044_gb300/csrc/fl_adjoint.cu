@@ -63,6 +63,7 @@ struct AParams {
   const unsigned char *codes;  // branch codes of the forward stage (layout of u), or null
   int bare;      // 1: out = R'^T mu only
   int tiles_x, tiles_y, zchunk;
+  int zlo, zhi;  // the tiles cover planes [zlo, zhi)
 };
 
 // asynchronous global -> shared copy of one element (no register staging)
@@ -292,8 +293,8 @@ __global__ void __launch_bounds__(TX *TY, FL_ADJ_MINB) k_struct_adjoint(const AP
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
   const int x0 = bx * TX, y0 = by * TY;
-  const int z0 = bz * p.zchunk;
-  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int z0 = p.zlo + bz * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.zhi);
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (tid < TX + 6) s_wx[tid] = wrapi(x0 - 3 + tid, nx);
   if (tid < TY + 6) s_wy[tid] = wrapi(y0 - 3 + tid, ny);
@@ -535,8 +536,8 @@ __global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParam
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
   const int x0 = bx * TX, y0 = by * TY;
-  const int z0 = bz * p.zchunk;
-  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int z0 = p.zlo + bz * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.zhi);
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (tid < TX + 6) s_wx[tid] = wrapi(x0 - 3 + tid, nx);
   if (tid < TY + 6) s_wy[tid] = wrapi(y0 - 3 + tid, ny);
@@ -750,13 +751,16 @@ cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t 
   p.codes = static_cast<const unsigned char *>(s.codes);
   p.tiles_x = (m->nx + TX - 1) / TX;
   p.tiles_y = (m->ny + TY - 1) / TY;
+  p.zlo = s.zhi < 0 ? 0 : s.zlo;
+  p.zhi = s.zhi < 0 ? m->nz : s.zhi;
+  const int nzr = p.zhi - p.zlo;
   const long long cols = (long long)p.tiles_x * p.tiles_y;
   if (s.codes != nullptr && s.cu != nullptr && lim != LIM_VANLEER) {
     // the stage's branch codes are stored: no theta, no differences
     const int res = resident_ctas(
         reinterpret_cast<const void *>(&k_struct_adjoint_codes<T, LIM_SUPERBEE>), TX * TY, 0);
-    p.zchunk = pick_zchunk(cols, m->nz, res, 2);
-    const unsigned g = (unsigned)(cols * ((m->nz + p.zchunk - 1) / p.zchunk));
+    p.zchunk = pick_zchunk(cols, nzr, res, 2);
+    const unsigned g = (unsigned)(cols * ((nzr + p.zchunk - 1) / p.zchunk));
     const dim3 blk(TX, TY);
     switch (lim) {
       case LIM_UPWIND: k_struct_adjoint_codes<T, LIM_UPWIND><<<g, blk, 0, st>>>(p); break;
@@ -770,9 +774,9 @@ cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t 
   }
   const int resident = resident_ctas(
       reinterpret_cast<const void *>(&k_struct_adjoint<T, LIM_SUPERBEE, true>), TX * TY, 0);
-  const int zchunk = pick_zchunk(cols, m->nz, resident, 3);
+  const int zchunk = pick_zchunk(cols, nzr, resident, 3);
   p.zchunk = zchunk;
-  const int tz = (m->nz + zchunk - 1) / zchunk;
+  const int tz = (nzr + zchunk - 1) / zchunk;
   const unsigned grid = (unsigned)(cols * tz);
   const dim3 block(TX, TY);
 #define FL_ADJ_CASE(L)                                                     \
@@ -827,6 +831,69 @@ using namespace fl;
     if (s_ != FL_OK) return s_; \
   } while (0)
 
+// One adjoint stage over planes [zlo, zhi) of a structured mesh (zhi < 0:
+// the whole mesh, any kind): the shared body of fl_step_rk_stage_adjoint and
+// fl_step_rk_stage_adjoint_planes.
+static fl_status stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
+                                      int stage, double dtime, int zlo, int zhi, const void *x,
+                                      const void *mu, const void *lam_a, const void *lam_b,
+                                      void *out, const void *u_f, const void *w_f, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(lim, dt));
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (stage < 0 || stage >= (rk == 3 ? 3 : 1))
+    return fail(FL_EINVAL, "stage %d does not exist for rk_order %d", stage, rk);
+  if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
+  const size_t es = dsize(dt), cb = (size_t)m->C * es;
+  FL_TRY(check_buffer(x, cb, "x"));
+  FL_TRY(check_buffer(mu, cb, "mu"));
+  FL_TRY(check_buffer(out, cb, "out"));
+  FL_TRY(check_buffer(u_f, (size_t)m->F * es, "u_f"));
+  const bool blend = rk == 3 && stage == 0;
+  if (blend) {
+    FL_TRY(check_buffer(lam_a, cb, "lam_a"));
+    FL_TRY(check_buffer(lam_b, cb, "lam_b"));
+  }
+  if (w_f != nullptr) {
+    if (!(dtime > 0)) return fail(FL_EINVAL, "a pre-scaled velocity needs dt > 0");
+    FL_TRY(check_buffer(w_f, (size_t)m->F * es, "w_f"));
+  }
+  if (m->C > 0) {
+    const char *ob = static_cast<const char *>(out);
+    for (const void *in : {x, mu}) {
+      const char *ib = static_cast<const char *>(in);
+      if (ob < ib + cb && ib < ob + cb)
+        return fail(FL_EINVAL, "out overlaps x or mu (the stage reads their neighbours)");
+    }
+  }
+  if (m->C == 0 || (zhi >= 0 && zhi == zlo)) return FL_OK;
+  if (m->kind == 1) FL_TRY(unstruct_adjoint_prepare(m));
+  AdjArgs a;
+  a.zlo = zlo;
+  a.zhi = zhi;
+  a.x = x;
+  a.mu = mu;
+  a.out = out;
+  a.u = u_f;
+  a.cu = w_f;
+  a.cu_dt = w_f != nullptr;
+  a.dt = dtime;
+  a.b = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+  if (blend) {
+    // theta^n's weights in the later stages' blends: 1/3 in stage 2 (as the
+    // forward kernels use it: 1 - RN(2/3) in the working precision) and 3/4
+    // in stage 1
+    a.v1 = lam_b;
+    a.e1 = dt == FL_F64 ? blend_a<double>(1.0 / 3.0, 2.0 / 3.0)
+                        : (double)blend_a<float>(1.0 / 3.0, 2.0 / 3.0);
+    a.v2 = lam_a;
+    a.e2 = 0.75;
+  }
+  const cudaError_t e = adjoint_any(m, lim, dt, a, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stage adjoint kernel");
+  return FL_OK;
+}
+
 extern "C" {
 
 fl_status fl_conv_limited_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt,
@@ -858,58 +925,21 @@ fl_status fl_step_rk_stage_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt
                                    int stage, double dtime, const void *x, const void *mu,
                                    const void *lam_a, const void *lam_b, void *out,
                                    const void *u_f, const void *w_f, void *stream) {
+  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, 0, -1, x, mu, lam_a, lam_b, out, u_f,
+                              w_f, stream);
+}
+
+fl_status fl_step_rk_stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
+                                          int stage, double dtime, int z_begin, int z_end,
+                                          const void *x, const void *mu, const void *lam_a,
+                                          const void *lam_b, void *out, const void *u_f,
+                                          const void *w_f, void *stream) {
   FL_TRY(check_mesh(m));
-  FL_TRY(check_enums(lim, dt));
-  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
-  if (stage < 0 || stage >= (rk == 3 ? 3 : 1))
-    return fail(FL_EINVAL, "stage %d does not exist for rk_order %d", stage, rk);
-  if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
-  const size_t es = dsize(dt), cb = (size_t)m->C * es;
-  FL_TRY(check_buffer(x, cb, "x"));
-  FL_TRY(check_buffer(mu, cb, "mu"));
-  FL_TRY(check_buffer(out, cb, "out"));
-  FL_TRY(check_buffer(u_f, (size_t)m->F * es, "u_f"));
-  const bool blend = rk == 3 && stage == 0;
-  if (blend) {
-    FL_TRY(check_buffer(lam_a, cb, "lam_a"));
-    FL_TRY(check_buffer(lam_b, cb, "lam_b"));
-  }
-  if (w_f != nullptr) {
-    if (!(dtime > 0)) return fail(FL_EINVAL, "a pre-scaled velocity needs dt > 0");
-    FL_TRY(check_buffer(w_f, (size_t)m->F * es, "w_f"));
-  }
-  if (m->C > 0) {
-    const char *ob = static_cast<const char *>(out);
-    for (const void *in : {x, mu}) {
-      const char *ib = static_cast<const char *>(in);
-      if (ob < ib + cb && ib < ob + cb)
-        return fail(FL_EINVAL, "out overlaps x or mu (the stage reads their neighbours)");
-    }
-  }
-  if (m->C == 0) return FL_OK;
-  if (m->kind == 1) FL_TRY(unstruct_adjoint_prepare(m));
-  AdjArgs a;
-  a.x = x;
-  a.mu = mu;
-  a.out = out;
-  a.u = u_f;
-  a.cu = w_f;
-  a.cu_dt = w_f != nullptr;
-  a.dt = dtime;
-  a.b = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
-  if (blend) {
-    // theta^n's weights in the later stages' blends: 1/3 in stage 2 (as the
-    // forward kernels use it: 1 - RN(2/3) in the working precision) and 3/4
-    // in stage 1
-    a.v1 = lam_b;
-    a.e1 = dt == FL_F64 ? blend_a<double>(1.0 / 3.0, 2.0 / 3.0)
-                        : (double)blend_a<float>(1.0 / 3.0, 2.0 / 3.0);
-    a.v2 = lam_a;
-    a.e2 = 0.75;
-  }
-  const cudaError_t e = adjoint_any(m, lim, dt, a, as_stream(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "stage adjoint kernel");
-  return FL_OK;
+  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "a plane range needs a structured mesh");
+  if (z_begin < 0 || z_end < z_begin || z_end > m->nz)
+    return fail(FL_EINVAL, "plane range [%d, %d) is not inside [0, %d]", z_begin, z_end, m->nz);
+  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, z_begin, z_end, x, mu, lam_a, lam_b,
+                              out, u_f, w_f, stream);
 }
 
 fl_status fl_adjoint_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps,

@@ -438,6 +438,51 @@ fl_status step_rk_impl(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, do
 
 }  // namespace
 
+// One stage over planes [zlo, zhi) of a structured mesh (zhi < 0: the whole
+// mesh, any kind): the shared body of fl_step_rk_stage and
+// fl_step_rk_stage_planes.
+static fl_status stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
+                              double dtime, int zlo, int zhi, const void *theta_n, const void *x,
+                              void *y, const void *u_f, const void *w_f, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_enums(lim, dt));
+  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
+  if (stage < 0 || stage >= (rk == 3 ? 3 : 1))
+    return fail(FL_EINVAL, "stage %d does not exist for rk_order %d", stage, rk);
+  if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
+  const size_t es = dsize(dt), cb = (size_t)m->C * es;
+  FL_TRY(check_buffer(x, cb, "x"));
+  FL_TRY(check_buffer(y, cb, "y"));
+  if (stage > 0) FL_TRY(check_buffer(theta_n, cb, "theta_n"));
+  FL_TRY(check_buffer(u_f, (size_t)m->F * es, "u_f"));
+  const bool pre = dt == FL_F64 && w_f != nullptr;
+  if (pre) {
+    if (!(dtime > 0)) return fail(FL_EINVAL, "a pre-scaled velocity needs dt > 0");
+    FL_TRY(check_buffer(w_f, (size_t)m->F * es, "w_f"));
+  }
+  const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
+  if (m->C > 0 && xb < yb + cb && yb < xb + cb)
+    return fail(FL_EINVAL, "x and y overlap (a stage reads neighbours of x while writing y)");
+  if (m->C == 0 || (zhi >= 0 && zhi == zlo)) return FL_OK;
+  StageArgs s;
+  s.zlo = zlo;
+  s.zhi = zhi;
+  s.x = x;
+  s.thn = stage == 0 ? x : theta_n;
+  s.y = y;
+  s.u = u_f;
+  s.w = pre ? w_f : nullptr;
+  s.dt = dtime;
+  s.seed = stage == 0 ? 0 : 1;
+  s.a = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+  s.b = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+  const cudaError_t e = (m->kind == 1) ? unstruct_stage(m, lim, dt, s, as_stream(stream))
+                                       : struct_stage(m, lim, dt, s, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stage kernel");
+  return FL_OK;
+}
+
+
 extern "C" {
 
 fl_status fl_step_rk(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, double dtime,
@@ -495,40 +540,19 @@ fl_status fl_velocity_prescale(const fl_mesh *m, fl_dtype dt, double dtime, cons
 fl_status fl_step_rk_stage(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
                            double dtime, const void *theta_n, const void *x, void *y,
                            const void *u_f, const void *w_f, void *stream) {
+  return stage_planes(m, lim, dt, rk, stage, dtime, 0, -1, theta_n, x, y, u_f, w_f, stream);
+}
+
+fl_status fl_step_rk_stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
+                                  double dtime, int z_begin, int z_end, const void *theta_n,
+                                  const void *x, void *y, const void *u_f, const void *w_f,
+                                  void *stream) {
   FL_TRY(check_mesh(m));
-  FL_TRY(check_enums(lim, dt));
-  if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
-  if (stage < 0 || stage >= (rk == 3 ? 3 : 1))
-    return fail(FL_EINVAL, "stage %d does not exist for rk_order %d", stage, rk);
-  if (!std::isfinite(dtime)) return fail(FL_EINVAL, "dt is not finite");
-  const size_t es = dsize(dt), cb = (size_t)m->C * es;
-  FL_TRY(check_buffer(x, cb, "x"));
-  FL_TRY(check_buffer(y, cb, "y"));
-  if (stage > 0) FL_TRY(check_buffer(theta_n, cb, "theta_n"));
-  FL_TRY(check_buffer(u_f, (size_t)m->F * es, "u_f"));
-  const bool pre = dt == FL_F64 && w_f != nullptr;
-  if (pre) {
-    if (!(dtime > 0)) return fail(FL_EINVAL, "a pre-scaled velocity needs dt > 0");
-    FL_TRY(check_buffer(w_f, (size_t)m->F * es, "w_f"));
-  }
-  const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
-  if (m->C > 0 && xb < yb + cb && yb < xb + cb)
-    return fail(FL_EINVAL, "x and y overlap (a stage reads neighbours of x while writing y)");
-  if (m->C == 0) return FL_OK;
-  StageArgs s;
-  s.x = x;
-  s.thn = stage == 0 ? x : theta_n;
-  s.y = y;
-  s.u = u_f;
-  s.w = pre ? w_f : nullptr;
-  s.dt = dtime;
-  s.seed = stage == 0 ? 0 : 1;
-  s.a = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
-  s.b = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
-  const cudaError_t e = (m->kind == 1) ? unstruct_stage(m, lim, dt, s, as_stream(stream))
-                                       : struct_stage(m, lim, dt, s, as_stream(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "stage kernel");
-  return FL_OK;
+  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "a plane range needs a structured mesh");
+  if (z_begin < 0 || z_end < z_begin || z_end > m->nz)
+    return fail(FL_EINVAL, "plane range [%d, %d) is not inside [0, %d]", z_begin, z_end, m->nz);
+  return stage_planes(m, lim, dt, rk, stage, dtime, z_begin, z_end, theta_n, x, y, u_f, w_f,
+                      stream);
 }
 
 size_t fl_reduce_workspace_size(void) { return reduce_ws_bytes(); }

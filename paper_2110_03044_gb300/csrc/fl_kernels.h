@@ -20,6 +20,7 @@ struct StageArgs {
   double g = 1.0;  // velocity factor of the stage: the flow is g u_f
   void *codes = nullptr;  // FP64 pre-scaled stages: branch code per face out (or null)
   int seed = 0;
+  int zlo = 0, zhi = -1;  // structured meshes: update planes [zlo, zhi) only (zhi < 0: all)
 };
 
 cudaError_t struct_stage(const fl_mesh *m, int lim, fl_dtype dt, const StageArgs &s,
@@ -71,6 +72,7 @@ struct AdjArgs {
   const void *codes = nullptr;  // branch codes of the forward stage at x, or null
   double e1 = 0.0, e2 = 0.0, b = 1.0, dt = 0.0;
   int bare = 0;
+  int zlo = 0, zhi = -1;  // structured meshes: update planes [zlo, zhi) only (zhi < 0: all)
 };
 
 cudaError_t struct_adjoint(const fl_mesh *m, int lim, fl_dtype dt, const AdjArgs &s,

@@ -50,8 +50,8 @@ __device__ __forceinline__ void stage_tile_reg(const SParams<float> &p, int tile
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
   const int x0 = bx * TX, y0 = by * (int)blockDim.y;
-  const int z0 = bz * p.zchunk;
-  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int z0 = p.zlo + bz * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, min(p.nz, p.zhi));
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int last = min(TX, nx - x0) - 1;  // last lane inside the mesh
   const bool valid = lane <= last && y0 + ty < ny;

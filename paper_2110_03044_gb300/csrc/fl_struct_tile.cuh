@@ -29,6 +29,9 @@ struct SParams {
   unsigned long long flip;  // sign mask toggled into u before the upwind test (g < 0)
   unsigned char *codes;     // CODES: branch code per face (layout of u), or null
   int tiles_x, tiles_y, zchunk;
+  // the tiles cover planes [zlo, min(zhi, nz)) (a plane range of a
+  // decomposed mesh; the whole mesh by default)
+  int zlo = 0, zhi = 1 << 30;
 };
 
 enum { SEED_PLAIN = 0, SEED_COMBINE = 1, SEED_APPLY = 2 };
@@ -89,8 +92,8 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
   const int x0 = bx * TX, y0 = by * TY;
-  const int z0 = bz * p.zchunk;
-  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int z0 = p.zlo + bz * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, min(p.nz, p.zhi));
   const int nx = p.nx, ny = p.ny, nz = p.nz;
 
   // wrapped coordinates of the tile's columns/rows, halo included:

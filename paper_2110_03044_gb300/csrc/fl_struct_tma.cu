@@ -77,6 +77,7 @@ struct TParams {
   float cx, cy, cz, a, b;
   int tiles_x, tiles_y, zchunk;
   int *status;
+  int zlo, zhi;  // the tiles cover planes [zlo, zhi)
 };
 
 __device__ __forceinline__ uint32_t sa(const void *p) {
@@ -174,8 +175,8 @@ __global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
   const int x0 = bx * TX, y0 = by * TY;
-  const int z0 = bz * p.zchunk;
-  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int z0 = p.zlo + bz * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.zhi);
   const int L = z1 - z0;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int w = min(TX, nx - x0), h = min(TY, ny - y0);  // w is a multiple of 4
@@ -531,10 +532,13 @@ cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cuda
     return cudaErrorNotSupported;
   const int resident = resident_ctas(reinterpret_cast<const void *>(&k_struct_stage_tma<LIM_SUPERBEE, 1>),
                                      LANES * (TY + 1), RING * SLOT);
-  const int zchunk = pick_zchunk(cols, nz, resident, 3);
+  p.zlo = s.zhi < 0 ? 0 : s.zlo;
+  p.zhi = s.zhi < 0 ? nz : s.zhi;
+  const int nzr = p.zhi - p.zlo;
+  const int zchunk = pick_zchunk(cols, nzr, resident, 3);
   p.zchunk = zchunk;
   p.status = m->status;
-  const unsigned grid = (unsigned)(cols * ((nz + zchunk - 1) / zchunk));
+  const unsigned grid = (unsigned)(cols * ((nzr + zchunk - 1) / zchunk));
   return s.seed == 0 ? launch_lim<0>(lim, p, maps, grid, st) : launch_lim<1>(lim, p, maps, grid, st);
 }
 

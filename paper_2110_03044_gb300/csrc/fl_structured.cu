@@ -166,9 +166,12 @@ cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStrea
     kq = reinterpret_cast<const void *>(
         &k_struct_stage<T, LIM_SUPERBEE, SEED_PLAIN, STY, false, false, false>);
   const int resident = resident_ctas(kq, TX * STY, 0);
-  const int zchunk = pick_zchunk(cols, m->nz, resident, 2);
+  p.zlo = s.zhi < 0 ? 0 : s.zlo;
+  p.zhi = s.zhi < 0 ? m->nz : s.zhi;
+  const int nzr = p.zhi - p.zlo;
+  const int zchunk = pick_zchunk(cols, nzr, resident, 2);
   p.zchunk = zchunk;
-  const int tz = (m->nz + zchunk - 1) / zchunk;
+  const int tz = (nzr + zchunk - 1) / zchunk;
   if constexpr (sizeof(T) == 8) {
     if (pre && !mod && s.codes != nullptr) {
       if (s.seed == SEED_PLAIN) return dispatch_lim<T, SEED_PLAIN, true, false, true>(lim, p, tz, st);

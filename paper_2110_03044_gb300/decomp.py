@@ -36,9 +36,18 @@ The adjoint (gradient_rk) exchanges the adjoint field the same way before
 every adjoint stage; it reads the stage states three planes deep, so a slab
 for the reverse sweep keeps HALO_ADJOINT = 3 ghost planes.
 
-Overlap: at 256^2 planes a halo is 2 x 65536 values per side (1 MiB in
-FP64), against a stage of 16.8 M cells; the exchange is issued before the
-stage and waited for, without splitting the stage into interior and rim.
+Overlap (the paper's split runs hide the exchange behind the interior's
+work): a stage updates only the owned planes, through the library's
+plane-range stage (fl_step_rk_stage_planes).  The exchange of its input is
+started first; the owned planes at least two planes away from both cuts (the
+stage's reach) need no ghost plane and run while the halos travel; after the
+wait, the two planes next to each cut run.  With NCCL the messages travel on
+the communicator's own stream while the interior kernel runs on the rank's
+stream, and the wait orders the rim kernels after the messages without
+blocking the host.  The ghost planes of a stage result are never written:
+the next exchange fills them before anything reads them.  A slab of fewer
+than 2 x reach planes has no interior and runs its owned planes after the
+wait.
 """
 from __future__ import annotations
 
@@ -121,6 +130,34 @@ def _cat(parts):
     return np.concatenate(parts)
 
 
+class _Done:
+    """The handle of an exchange that has completed when it was started."""
+
+    def wait(self):
+        return None
+
+
+class _Pending:
+    """The handle of an exchange in flight: its point-to-point requests."""
+
+    def __init__(self, reqs):
+        self.reqs = reqs
+
+    def wait(self):
+        for r in self.reqs:
+            r.wait()
+
+
+def start_exchange(transport, slab: Slab, x):
+    """Start the halo exchange of x and return a handle whose wait() ends it;
+    a transport with no start() exchanges at once."""
+    start = getattr(transport, "start", None)
+    if start is not None:
+        return start(slab, x)
+    transport.exchange(slab, x)
+    return _Done()
+
+
 class LocalTransport:
     """Exchange for a single rank: its neighbours are itself."""
 
@@ -128,6 +165,10 @@ class LocalTransport:
         P, h, n = slab.plane, slab.halo, slab.nz_local
         x[0:h * P].copy_(x[n * P:(n + h) * P])
         x[(h + n) * P:(2 * h + n) * P].copy_(x[h * P:2 * h * P])
+
+    def start(self, slab: Slab, x):
+        self.exchange(slab, x)
+        return _Done()
 
 
 class TorchTransport:
@@ -137,9 +178,14 @@ class TorchTransport:
     UP, DOWN = 11, 12  # tags: planes travelling to the rank above / below
 
     def exchange(self, slab: Slab, x):
+        self.start(slab, x).wait()
+
+    def start(self, slab: Slab, x):
+        """Post the four point-to-point operations of x's halo exchange and
+        return their handle (NCCL: enqueued on the communicator's stream)."""
         import torch.distributed as dist
         if slab.world == 1:
-            return LocalTransport().exchange(slab, x)
+            return LocalTransport().start(slab, x)
         P, h, n = slab.plane, slab.halo, slab.nz_local
         top = x[n * P:(n + h) * P]            # my highest owned planes -> rank above
         bottom = x[h * P:2 * h * P]           # my lowest owned planes -> rank below
@@ -149,80 +195,108 @@ class TorchTransport:
                dist.P2POp(dist.isend, bottom, slab.down, tag=self.DOWN),
                dist.P2POp(dist.irecv, lower_ghost, slab.down, tag=self.UP),
                dist.P2POp(dist.irecv, upper_ghost, slab.up, tag=self.DOWN)]
-        for req in dist.batch_isend_irecv(ops):
-            req.wait()
+        return _Pending(dist.batch_isend_irecv(ops))
 
 
-StageFn = Callable[[int, Optional[object], object, object], None]
-StageAdjointFn = Callable[[int, object, object, Optional[object], Optional[object], object], None]
+StageFn = Callable[[int, Optional[object], object, object, int, int], None]
+StageAdjointFn = Callable[[int, object, object, Optional[object], Optional[object], object, int,
+                           int], None]
 
 # The adjoint stage reads mu within two planes and the stage state x within
 # three (the four faces of an axis around a cell, each with its upstream
 # cell): a decomposed reverse sweep keeps three ghost planes.
 HALO_ADJOINT = 3
 
+# How far a stage reads the field whose halo is exchanged before it: the
+# forward stage reads x, the adjoint stage mu, within two planes.
+REACH = 2
 
-def step_rk(slab: Slab, transport, stage: StageFn, rk_order: int, nsteps: int, theta, a, b=None):
+
+def exchange_and_run(slab: Slab, transport, x, run, overlap=True, reach=REACH):
+    """Exchange x's halo and run ``run(z0, z1)`` over every owned local plane
+    (z0, z1 local plane indices).  With ``overlap`` the planes at least
+    ``reach`` planes from both cuts run while the exchange is in flight and
+    the planes next to the cuts after it ends; without it (or when the slab
+    has no such interior) everything runs after the exchange."""
+    h, n = slab.halo, slab.nz_local
+    if not overlap or n <= 2 * reach:
+        transport.exchange(slab, x)
+        run(h, h + n)
+        return
+    pending = start_exchange(transport, slab, x)
+    run(h + reach, h + n - reach)
+    pending.wait()
+    run(h, h + reach)
+    run(h + n - reach, h + n)
+
+
+def step_rk(slab: Slab, transport, stage: StageFn, rk_order: int, nsteps: int, theta, a, b=None,
+            overlap=True):
     """``nsteps`` steps of Euler (rk_order 1) or SSP-RK3 (3) on the local
     field ``theta`` (owned planes valid on entry and on return), exchanging
-    the halo of every stage input.  ``stage(s, theta_n, x, y)`` runs stage s
-    into y (the library's fl_step_rk_stage on the local mesh); ``a`` and ``b``
-    are local scratch fields of the same size (``b`` for SSP-RK3 only).
-    Returns the local field that holds the result (``theta``)."""
+    the halo of every stage input.  ``stage(s, theta_n, x, y, z0, z1)`` runs
+    stage s into the local planes [z0, z1) of y (the library's
+    fl_step_rk_stage_planes on the local mesh); ``a`` and ``b`` are local
+    scratch fields of the same size (``b`` for SSP-RK3 only).  ``overlap``
+    runs each stage's interior while its input's halo is exchanged.  Returns
+    the local field that holds the result (``theta``)."""
+    def run_stage(s, thn, x, y):
+        exchange_and_run(slab, transport, x, lambda z0, z1: stage(s, thn, x, y, z0, z1), overlap)
+
     if rk_order == 1:
         cur, nxt = theta, a
         for _ in range(nsteps):
-            transport.exchange(slab, cur)
-            stage(0, None, cur, nxt)
+            run_stage(0, None, cur, nxt)
             cur, nxt = nxt, cur
         if cur is not theta:
-            theta.copy_(cur)
+            slab.owned(theta).copy_(slab.owned(cur))
         return theta
     if rk_order != 3:
         raise ValueError("rk_order must be 1 or 3")
     for _ in range(nsteps):
-        transport.exchange(slab, theta)
-        stage(0, None, theta, a)
-        transport.exchange(slab, a)
-        stage(1, theta, a, b)
-        transport.exchange(slab, b)
-        stage(2, theta, b, theta)  # y may be theta_n, never x
+        run_stage(0, None, theta, a)
+        run_stage(1, theta, a, b)
+        run_stage(2, theta, b, theta)  # y may be theta_n, never x
     return theta
 
 
 def gradient_rk(slab: Slab, transport, stage: StageFn, stage_adjoint: StageAdjointFn,
-                rk_order: int, nsteps: int, every: int, theta0, lam_T, new):
+                rk_order: int, nsteps: int, every: int, theta0, lam_T, new, overlap=True):
     """Reverse-mode sweep of a decomposed rollout: dJ/dtheta_0 from
     lam_T = dJ/dtheta_T, with checkpoints every ``every`` steps and each
     segment recomputed (its stage inputs stored with their exchanged ghost
     planes) before its adjoint stages run in reverse; the adjoint's halo is
     exchanged before every adjoint stage, the same exchange as the forward
-    stages'.  ``stage_adjoint(s, x, mu, lam_a, lam_b, out)`` is the
-    library's fl_step_rk_stage_adjoint on the local mesh; ``new()`` gives a
-    fresh local field.  The slab needs ``halo >= HALO_ADJOINT``.  Returns the
-    local dJ/dtheta_0 (owned planes valid)."""
+    stages', and with ``overlap`` the interior of every forward and adjoint
+    stage runs while it travels.  ``stage_adjoint(s, x, mu, lam_a, lam_b,
+    out, z0, z1)`` is the library's fl_step_rk_stage_adjoint_planes on the
+    local mesh; ``new()`` gives a fresh local field.  The slab needs
+    ``halo >= HALO_ADJOINT``.  Returns the local dJ/dtheta_0 (owned planes
+    valid)."""
     if slab.halo < HALO_ADJOINT:
         raise ValueError("the reverse sweep needs a halo of %d planes" % HALO_ADJOINT)
     if rk_order not in (1, 3):
         raise ValueError("rk_order must be 1 or 3")
 
+    def run_stage(s, thn, x, y, keep):
+        exchange_and_run(slab, transport, x, lambda z0, z1: stage(s, thn, x, y, z0, z1), overlap)
+        keep.append(x.clone())  # x with its exchanged ghost planes (a stage never writes x)
+
     def fwd_step(th, keep):
         """one step in place on th, appending its exchanged stage inputs"""
-        transport.exchange(slab, th)
-        keep.append(th.clone())
         if rk_order == 1:
             y = new()
-            stage(0, None, th, y)
-            th.copy_(y)
+            run_stage(0, None, th, y, keep)
+            slab.owned(th).copy_(slab.owned(y))
             return
         a, b = new(), new()
-        stage(0, None, th, a)
-        transport.exchange(slab, a)
-        keep.append(a.clone())
-        stage(1, th, a, b)
-        transport.exchange(slab, b)
-        keep.append(b.clone())
-        stage(2, th, b, th)
+        run_stage(0, None, th, a, keep)
+        run_stage(1, th, a, b, keep)
+        run_stage(2, th, b, th, keep)  # y is theta_n, never x
+
+    def adj(s, x, mu, lam_a, lam_b, out):
+        exchange_and_run(slab, transport, mu,
+                         lambda z0, z1: stage_adjoint(s, x, mu, lam_a, lam_b, out, z0, z1), overlap)
 
     # forward, storing a checkpoint every `every` steps
     checkpoints = []
@@ -239,19 +313,16 @@ def gradient_rk(slab: Slab, transport, stage: StageFn, stage_adjoint: StageAdjoi
         for _ in range(seg):
             fwd_step(th, states)
         for n in range(seg - 1, -1, -1):
-            transport.exchange(slab, lam)
             if rk_order == 1:
                 out = new()
-                stage_adjoint(0, states[n], lam, None, None, out)
+                adj(0, states[n], lam, None, None, out)
                 lam = out
                 continue
             x0, x1, x2 = states[3 * n], states[3 * n + 1], states[3 * n + 2]
             m2, m1, out = new(), new(), new()
-            stage_adjoint(2, x2, lam, None, None, m2)
-            transport.exchange(slab, m2)
-            stage_adjoint(1, x1, m2, None, None, m1)
-            transport.exchange(slab, m1)
-            stage_adjoint(0, x0, m1, m2, lam, out)
+            adj(2, x2, lam, None, None, m2)
+            adj(1, x1, m2, None, None, m1)
+            adj(0, x0, m1, m2, lam, out)
             lam = out
     return lam
 
@@ -259,13 +330,16 @@ def gradient_rk(slab: Slab, transport, stage: StageFn, stage_adjoint: StageAdjoi
 class SlabRollout:
     """A rank's part of a decomposed rollout on the GPU: the local mesh, its
     face velocities (and, in FP64, the pre-scaled velocity fl_step_rk uses),
-    the stage scratch, and the library's stage kernel.  The owned planes of
-    the result equal those of fl_step_rk on the whole mesh, bit for bit."""
+    the stage scratch, and the library's plane-range stage kernels.  The
+    owned planes of the result equal those of fl_step_rk on the whole mesh,
+    bit for bit.  ``overlap`` runs each stage's interior planes while the
+    halo of its input is exchanged."""
 
-    def __init__(self, slab: Slab, h, u_global, limiter, dtype, dt, transport=None):
+    def __init__(self, slab: Slab, h, u_global, limiter, dtype, dt, transport=None,
+                 overlap=True):
         import torch
 
-        from . import Mesh, fl_velocity_prescale, fl_step_rk_stage
+        from . import Mesh, fl_velocity_prescale
         self.slab = slab
         self.mesh = Mesh.structured(*slab.local_dims, *h)
         n_axes = sum(1 for d in slab.dims if d > 1)
@@ -276,39 +350,42 @@ class SlabRollout:
             fl_velocity_prescale(self.mesh.handle, dtype, dt, self.u, self.w)
         self.limiter, self.dtype, self.dt = limiter, dtype, dt
         self.transport = transport or TorchTransport()
-        self._stage = fl_step_rk_stage
+        self.overlap = overlap
 
     def local_field(self, theta_global):
         return self.slab.local_cells(theta_global).to(self.dtype).contiguous()
+
+    def _stage_fn(self, rk_order):
+        from . import fl_step_rk_stage_planes
+
+        def stage(s, thn, x, y, z0, z1):
+            fl_step_rk_stage_planes(self.mesh.handle, self.limiter, self.dtype, rk_order, s,
+                                    self.dt, z0, z1, thn, x, y, self.u, self.w)
+
+        return stage
 
     def step(self, theta_local, rk_order, nsteps):
         import torch
         a = torch.empty_like(theta_local)
         b = torch.empty_like(theta_local) if rk_order == 3 else None
-
-        def stage(s, thn, x, y):
-            self._stage(self.mesh.handle, self.limiter, self.dtype, rk_order, s, self.dt, thn, x,
-                        y, self.u, self.w)
-
-        return step_rk(self.slab, self.transport, stage, rk_order, nsteps, theta_local, a, b)
+        return step_rk(self.slab, self.transport, self._stage_fn(rk_order), rk_order, nsteps,
+                       theta_local, a, b, overlap=self.overlap)
 
     def gradient(self, theta_local, lam_T_local, rk_order, nsteps, every):
         """dJ/dtheta_0 on this rank's slab (see gradient_rk); the slab needs
         a halo of HALO_ADJOINT planes."""
         import torch
 
-        from . import fl_step_rk_stage_adjoint
+        from . import fl_step_rk_stage_adjoint_planes
 
-        def stage(s, thn, x, y):
-            self._stage(self.mesh.handle, self.limiter, self.dtype, rk_order, s, self.dt, thn, x,
-                        y, self.u, self.w)
+        def stage_adjoint(s, x, mu, lam_a, lam_b, out, z0, z1):
+            fl_step_rk_stage_adjoint_planes(self.mesh.handle, self.limiter, self.dtype, rk_order,
+                                            s, self.dt, z0, z1, x, mu, lam_a, lam_b, out, self.u,
+                                            self.w)
 
-        def stage_adjoint(s, x, mu, lam_a, lam_b, out):
-            fl_step_rk_stage_adjoint(self.mesh.handle, self.limiter, self.dtype, rk_order, s,
-                                     self.dt, x, mu, lam_a, lam_b, out, self.u, self.w)
-
-        return gradient_rk(self.slab, self.transport, stage, stage_adjoint, rk_order, nsteps,
-                           every, theta_local, lam_T_local, lambda: torch.empty_like(theta_local))
+        return gradient_rk(self.slab, self.transport, self._stage_fn(rk_order), stage_adjoint,
+                           rk_order, nsteps, every, theta_local, lam_T_local,
+                           lambda: torch.empty_like(theta_local), overlap=self.overlap)
 
     def close(self):
         self.mesh.close()

@@ -4,10 +4,14 @@ per-rank computation (the GPU runs the library's stage kernel instead; see
 test_gpu_decomp.py).
 
 * The slabs cover the planes once, each owning at least the halo depth.
-* A decomposed SSP-RK3 / Euler rollout gives, on every owned plane, the
-  bits of the one-rank decomposed run (the exchange delivers exactly the
-  planes each stage reads) and the whole-mesh oracle to rounding (the cell
-  sums of the wrapped plane 0 run in another face order there).
+* A stage runs every owned plane once and no ghost plane: with overlap, the
+  planes two or more planes from both cuts between starting the exchange and
+  waiting for it, the planes next to the cuts after.
+* A decomposed SSP-RK3 / Euler rollout, with and without overlap, gives on
+  every owned plane the bits of the one-rank decomposed run (the exchange
+  delivers exactly the planes each stage reads; scratch planes no stage
+  writes hold NaN) and the whole-mesh oracle to rounding (the cell sums of
+  the wrapped plane 0 run in another face order there).
 * Mass is conserved across the cuts to round-off.
 * The decomposed reverse sweep (checkpoints, recomputed segments, the
   adjoint's halo exchanged before every adjoint stage, three ghost planes)
@@ -65,6 +69,44 @@ def test_local_fields_cut_from_global():
     assert torch.equal(lu[loc.numel():loc.numel() + P], u[120 + 3 * P:120 + 4 * P])
 
 
+class _Recorder:
+    """A transport that only records the order of its calls."""
+
+    def __init__(self):
+        self.log = []
+
+    def exchange(self, slab, x):
+        self.log.append("exchange")
+
+    def start(self, slab, x):
+        self.log.append("start")
+        log = self.log
+
+        class Pending:
+            def wait(self):
+                log.append("wait")
+
+        return Pending()
+
+
+@pytest.mark.parametrize("nz,world,overlap", [(16, 2, True), (16, 2, False), (8, 2, True),
+                                              (9, 2, True), (5, 1, True), (4, 1, True)])
+def test_exchange_and_run_covers_owned_planes_once(nz, world, overlap):
+    from paper_2110_03044_gb300.decomp import REACH, exchange_and_run
+    slab = Slab((3, 2, nz), 0, world)
+    tr = _Recorder()
+    exchange_and_run(slab, tr, None, lambda z0, z1: tr.log.append((z0, z1)), overlap)
+    h, n = slab.halo, slab.nz_local
+    ranges = [e for e in tr.log if isinstance(e, tuple)]
+    planes = sorted(k for z0, z1 in ranges for k in range(z0, z1))
+    assert planes == list(range(h, h + n))  # every owned plane once, no ghost plane
+    if overlap and n > 2 * REACH:
+        assert tr.log == ["start", (h + REACH, h + n - REACH), "wait", (h, h + REACH),
+                          (h + n - REACH, h + n)]
+    else:
+        assert tr.log == ["exchange", (h, h + n)]
+
+
 def _case():
     dims = (9, 7, 12)
     h = (0.7 / 9, 0.9 / 7, 1.1 / 12)
@@ -77,25 +119,31 @@ def _case():
 
 
 def _oracle_stage(slab, h, lim, rk, dt, u_local):
+    """The oracle's stage on the local mesh, written into local planes
+    [z0, z1) of y only (the other planes of y keep their values)."""
     lm = oracle.OracleMesh(W.structured_mesh(*slab.local_dims, *h))
     uu = u_local.numpy()
+    P = slab.plane
 
-    def stage(s, thn, x, y):
+    def stage(s, thn, x, y, z0, z1):
         xn = x.numpy()
         t = xn if thn is None else thn.numpy()
-        y.copy_(torch.from_numpy(oracle.stage(lm, lim, rk, s, dt, t, xn, uu)))
+        full = oracle.stage(lm, lim, rk, s, dt, t, xn, uu)
+        y[z0 * P:z1 * P] = torch.from_numpy(full[z0 * P:z1 * P])
 
     return stage
 
 
-def _run_rank(rank, world, lim, rk, nsteps, transport):
+def _run_rank(rank, world, lim, rk, nsteps, transport, overlap=True):
     dims, h, mesh, th, u, dt = _case()
     slab = Slab(dims, rank, world)
     tl = slab.local_cells(torch.from_numpy(th)).clone()
     ul = slab.local_faces(torch.from_numpy(u), 3)
-    a = torch.empty_like(tl)
-    b = torch.empty_like(tl)
-    step_rk(slab, transport, _oracle_stage(slab, h, lim, rk, dt, ul), rk, nsteps, tl, a, b)
+    # scratch full of NaN: a plane the stages never write must never be read
+    a = torch.full_like(tl, float("nan"))
+    b = torch.full_like(tl, float("nan"))
+    step_rk(slab, transport, _oracle_stage(slab, h, lim, rk, dt, ul), rk, nsteps, tl, a, b,
+            overlap=overlap)
     return slab.lo, slab.hi, slab.owned(tl).numpy().copy()
 
 
@@ -107,22 +155,22 @@ def _free_port():
     return p
 
 
-def _worker(rank, world, port, lim, rk, nsteps, q):
+def _worker(rank, world, port, lim, rk, nsteps, overlap, q):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        q.put((rank,) + _run_rank(rank, world, lim, rk, nsteps, TorchTransport()))
+        q.put((rank,) + _run_rank(rank, world, lim, rk, nsteps, TorchTransport(), overlap))
     finally:
         dist.destroy_process_group()
 
 
-def _gloo_run(world, lim, rk, nsteps):
+def _gloo_run(world, lim, rk, nsteps, overlap=True):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, lim, rk, nsteps, q))
+    procs = [ctx.Process(target=_worker, args=(r, world, port, lim, rk, nsteps, overlap, q))
              for r in range(world)]
     for p in procs:
         p.start()
@@ -133,17 +181,17 @@ def _gloo_run(world, lim, rk, nsteps):
     return sorted(out)
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world,overlap", [(2, True), (3, True), (2, False)])
 @pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1), ("smart", 3)])
-def test_gloo_decomposed_rollout_equals_one_rank(world, lim, rk):
+def test_gloo_decomposed_rollout_equals_one_rank(world, overlap, lim, rk):
     dims, h, mesh, th, u, dt = _case()
     nsteps = 3
     P = dims[0] * dims[1]
     # the one-rank decomposed run (its halo comes from itself)
-    lo, hi, one = _run_rank(0, 1, lim, rk, nsteps, LocalTransport())
+    lo, hi, one = _run_rank(0, 1, lim, rk, nsteps, LocalTransport(), overlap=False)
     assert (lo, hi) == (0, dims[2])
     got = np.empty(mesh.n_cells)
-    for _, lo, hi, part in _gloo_run(world, lim, rk, nsteps):
+    for _, lo, hi, part in _gloo_run(world, lim, rk, nsteps, overlap):
         got[lo * P:hi * P] = part
     assert np.array_equal(got, one)  # bit for bit
     ref = oracle.step(mesh, lim, rk, dt, nsteps, u, th)
@@ -157,18 +205,19 @@ def _oracle_stage_adjoint(slab, h, lim, rk, dt, u_local):
     lm = oracle.OracleMesh(W.structured_mesh(*slab.local_dims, *h))
     uu = u_local.numpy()
     b = {0: 1.0, 1: 0.25, 2: 2.0 / 3.0}
+    P = slab.plane
 
-    def stage_adjoint(s, x, mu, lam_a, lam_b, out):
+    def stage_adjoint(s, x, mu, lam_a, lam_b, out, z0, z1):
         m = mu.numpy()
         y = b[s if rk == 3 else 0] * (m + dt * oracle.rhs_adjoint(lm, lim, x.numpy(), uu, m))
         if rk == 3 and s == 0:
             y = y + 0.75 * lam_a.numpy() + (1.0 / 3.0) * lam_b.numpy()
-        out.copy_(torch.from_numpy(y))
+        out[z0 * P:z1 * P] = torch.from_numpy(y[z0 * P:z1 * P])
 
     return stage_adjoint
 
 
-def _grad_rank(rank, world, lim, rk, nsteps, every, transport):
+def _grad_rank(rank, world, lim, rk, nsteps, every, transport, overlap=True):
     from paper_2110_03044_gb300.decomp import HALO_ADJOINT, gradient_rk
     dims, h, mesh, th, u, dt = _case()
     tgt = np.random.default_rng(7).normal(size=mesh.n_cells)
@@ -179,7 +228,7 @@ def _grad_rank(rank, world, lim, rk, nsteps, every, transport):
     ul = slab.local_faces(torch.from_numpy(u), 3)
     g = gradient_rk(slab, transport, _oracle_stage(slab, h, lim, rk, dt, ul),
                     _oracle_stage_adjoint(slab, h, lim, rk, dt, ul), rk, nsteps, every, tl, lam,
-                    lambda: torch.empty_like(tl))
+                    lambda: torch.full_like(tl, float("nan")), overlap=overlap)
     return slab.lo, slab.hi, slab.owned(g).numpy().copy()
 
 
@@ -200,7 +249,7 @@ def test_gloo_decomposed_gradient_equals_one_rank(world, lim, rk):
     dims, h, mesh, th, u, dt = _case()
     nsteps, every = 3, 2
     P = dims[0] * dims[1]
-    _, _, one = _grad_rank(0, 1, lim, rk, nsteps, every, LocalTransport())
+    _, _, one = _grad_rank(0, 1, lim, rk, nsteps, every, LocalTransport(), overlap=False)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()

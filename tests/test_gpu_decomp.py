@@ -236,3 +236,114 @@ def test_stage_adjoint_composes_to_the_step_adjoint(fl):
         fl.fl_step_rk_stage_adjoint(m.handle, "superbee", f64, 3, 1, dt, x1, m2, None, None, m2,
                                     u, w)
     m.close()
+
+
+# ------------------------------------------------ plane-range stage kernels
+@pytest.mark.parametrize("dims,dtype,pre", [((40, 12, 23), torch.float64, True),
+                                            ((40, 12, 23), torch.float64, False),
+                                            ((40, 12, 23), torch.float32, False),
+                                            ((128, 8, 21), torch.float32, False)])
+@pytest.mark.parametrize("lim", ["superbee", "vanleer", "smart"])
+def test_stage_planes_compose_to_the_whole_stage(fl, dims, dtype, pre, lim):
+    # the stage over three plane ranges (one of them a single plane, one at
+    # each periodic end) gives the whole stage's bits on every plane it
+    # covers and leaves every other plane of y as it was
+    h = tuple(0.7 / d for d in dims)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(21)
+    P, nz = dims[0] * dims[1], dims[2]
+    th0 = torch.tensor(rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3),
+                       dtype=dtype, device="cuda")
+    thn = torch.tensor(rng.uniform(-1, 1, mesh.n_cells), dtype=dtype, device="cuda")
+    u = torch.tensor(0.3 * W.mixed_sign_velocity(mesh.n_faces, 22), dtype=dtype, device="cuda")
+    dt = 0.3 * min(h) / float(u.abs().max()) / 3
+    m = fl.Mesh.structured(*dims, *h)
+    w = None
+    if pre:
+        w = torch.empty_like(u)
+        fl.fl_velocity_prescale(m.handle, dtype, dt, u, w)
+    for s in range(3):
+        ref = torch.empty_like(th0)
+        fl.fl_step_rk_stage(m.handle, lim, dtype, 3, s, dt, thn, th0, ref, u, w)
+        sentinel = torch.full_like(th0, 7.25)
+        for z0, z1 in [(0, 1), (5, 9), (nz - 3, nz)]:
+            y = sentinel.clone()
+            fl.fl_step_rk_stage_planes(m.handle, lim, dtype, 3, s, dt, z0, z1, thn, th0, y, u, w)
+            torch.cuda.synchronize()
+            assert torch.equal(y[z0 * P:z1 * P], ref[z0 * P:z1 * P])
+            assert torch.equal(y[:z0 * P], sentinel[:z0 * P])
+            assert torch.equal(y[z1 * P:], sentinel[z1 * P:])
+        y = sentinel.clone()
+        for z0, z1 in [(0, 1), (1, 12), (12, 12), (12, nz)]:
+            fl.fl_step_rk_stage_planes(m.handle, lim, dtype, 3, s, dt, z0, z1, thn, th0, y, u, w)
+        assert torch.equal(y, ref)
+    m.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("lim", ["superbee", "vanleer", "smart"])
+def test_stage_adjoint_planes_compose_to_the_whole_stage(fl, dtype, lim):
+    dims = (36, 10, 17)
+    h = tuple(0.7 / d for d in dims)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(23)
+    P, nz = dims[0] * dims[1], dims[2]
+
+    def field():
+        return torch.tensor(rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3),
+                            dtype=dtype, device="cuda")
+
+    x, mu, la, lb = field(), field(), field(), field()
+    u = torch.tensor(0.3 * W.mixed_sign_velocity(mesh.n_faces, 24), dtype=dtype, device="cuda")
+    dt = 0.3 * min(h) / float(u.abs().max()) / 3
+    m = fl.Mesh.structured(*dims, *h)
+    for s in range(3):
+        ref = torch.empty_like(x)
+        fl.fl_step_rk_stage_adjoint(m.handle, lim, dtype, 3, s, dt, x, mu, la, lb, ref, u)
+        out = torch.full_like(x, -3.5)
+        fl.fl_step_rk_stage_adjoint_planes(m.handle, lim, dtype, 3, s, dt, 4, 11, x, mu, la, lb,
+                                           out, u)
+        torch.cuda.synchronize()
+        assert torch.equal(out[4 * P:11 * P], ref[4 * P:11 * P])
+        assert bool((out[:4 * P] == -3.5).all()) and bool((out[11 * P:] == -3.5).all())
+        for z0, z1 in [(0, 4), (11, nz)]:
+            fl.fl_step_rk_stage_adjoint_planes(m.handle, lim, dtype, 3, s, dt, z0, z1, x, mu, la,
+                                               lb, out, u)
+        assert torch.equal(out, ref)
+    m.close()
+
+
+def test_stage_planes_argument_errors(fl):
+    dims = (16, 8, 6)
+    h = (0.1, 0.1, 0.1)
+    m = fl.Mesh.structured(*dims, *h)
+    n = 16 * 8 * 6
+    x = torch.rand(n, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    u = torch.rand(3 * n, dtype=torch.float64, device="cuda")
+    for z0, z1 in [(-1, 2), (3, 2), (0, 7)]:
+        with pytest.raises(fl.FLError) as e:
+            fl.fl_step_rk_stage_planes(m.handle, "superbee", torch.float64, 1, 0, 0.01, z0, z1,
+                                       None, x, y, u)
+        assert e.value.status == fl.FL_EINVAL
+        with pytest.raises(fl.FLError) as e:
+            fl.fl_step_rk_stage_adjoint_planes(m.handle, "superbee", torch.float64, 1, 0, 0.01,
+                                               z0, z1, x, x.clone(), None, None, y, u)
+        assert e.value.status == fl.FL_EINVAL
+    # an empty range runs nothing
+    fl.fl_step_rk_stage_planes(m.handle, "superbee", torch.float64, 1, 0, 0.01, 3, 3, None, x, y,
+                               u)
+    torch.cuda.synchronize()
+    assert bool((y == 0).all())
+    m.close()
+    # a face-based mesh has no planes
+    mesh = W.structured_mesh(4, 4, 4, 0.25, 0.25, 0.25)
+    fm = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas,
+                            mesh.volumes)
+    xf = torch.rand(mesh.n_cells, dtype=torch.float64, device="cuda")
+    uf = torch.rand(mesh.n_faces, dtype=torch.float64, device="cuda")
+    with pytest.raises(fl.FLError) as e:
+        fl.fl_step_rk_stage_planes(fm.handle, "superbee", torch.float64, 1, 0, 0.01, 0, 1, None,
+                                   xf, torch.empty_like(xf), uf)
+    assert e.value.status == fl.FL_EUNSUPPORTED
+    fm.close()
