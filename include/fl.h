@@ -154,6 +154,47 @@ fl_status fl_mesh_create_weighted(int64_t n_cells, int64_t n_faces, const int32_
                                   unsigned flags, fl_mesh **out);
 
 /*
+ * The local mesh of one part of a partitioned face-based mesh (Section 4's
+ * split runs; each process owns the cells of one part and keeps copies of
+ * the cells its stencils reach): cells [0, n_interior) are owned and read
+ * no halo cell, cells [n_interior, n_owned) are owned and read halo cells,
+ * cells [n_owned, n_cells) are halo copies of other parts' cells.  Compute
+ * calls on the mesh update the owned cells only and never write a halo cell.
+ * A stencil of an owned cell reaches two cells deep (the face's other cell,
+ * and the upstream cell behind the upwind one), so the caller gives:
+ *   - every face of every owned cell and of every halo cell adjacent to an
+ *     owned cell, in the relative order of the whole mesh's faces (a cell
+ *     then sums its faces in the whole mesh's order and gets its bits);
+ *   - the cells of those faces (the second halo ring may have cut face
+ *     lists: no stencil of an owned cell is taken at them).
+ * face_distances: NULL, or as in fl_mesh_create_weighted.  Other arguments
+ * and errors as fl_mesh_create (no renumbering: the caller's cell order
+ * keeps its locality); FL_EINVAL unless 0 <= n_interior <= n_owned <=
+ * n_cells.  Multi-stage calls (fl_step_rk ...) on a local mesh run with the
+ * halo as it stands; a decomposed run calls the stage entry points and
+ * refreshes the halo before each.  fl_reduce_mass sums the owned cells.
+ */
+fl_status fl_mesh_create_local(int64_t n_cells, int64_t n_owned, int64_t n_interior,
+                               int64_t n_faces, const int32_t *face_cells,
+                               const double *face_normals, const double *face_areas,
+                               const double *cell_volumes, const double *face_distances,
+                               fl_mesh **out);
+
+/* n_owned and n_interior of a mesh (both n_cells for a whole mesh). */
+fl_status fl_mesh_local_info(const fl_mesh *mesh, int64_t *n_owned, int64_t *n_interior);
+
+/*
+ * Halo gather of a partitioned run: dst[i] = src[index[i]] for i < n, the
+ * values one part sends to a neighbour part (src: a cell field [n_cells] of
+ * the mesh, device; index: int32 [n], device; dst: [n] device, not
+ * overlapping src).  An index outside [0, n_cells) records FL_EINDEX in the
+ * mesh's status word (returned by the next call) and leaves its dst entry
+ * as it was.  One kernel launch.
+ */
+fl_status fl_halo_pack(const fl_mesh *mesh, fl_dtype dtype, const void *src,
+                       const int32_t *index, int64_t n, void *dst, void *stream);
+
+/*
  * Internal numbering of a mesh created with FL_RENUMBER (host arrays):
  * cell_perm[user_cell] = internal cell, face_perm[user_face] = internal face,
  * face_flip[user_face] = 1 if the internal face has the opposite orientation
@@ -315,6 +356,19 @@ fl_status fl_step_rk_stage_planes(const fl_mesh *mesh, fl_limiter limiter, fl_dt
                                   const void *w_f, void *stream);
 
 /*
+ * fl_step_rk_stage over the owned cells [c_begin, c_end) of a local mesh
+ * (fl_mesh_create_local) only; each end is 0, n_interior or n_owned, so a
+ * partitioned run can update its interior cells while the halo exchange is
+ * in flight and the cells next to the halo after it.  Cells outside the
+ * range keep their values in y.  FL_EUNSUPPORTED on a structured mesh;
+ * FL_EINVAL for another range.  One kernel launch.
+ */
+fl_status fl_step_rk_stage_cells(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                                 int rk_order, int stage, double dt, int64_t c_begin,
+                                 int64_t c_end, const void *theta_n, const void *x, void *y,
+                                 const void *u_f, const void *w_f, void *stream);
+
+/*
  * w_f = dt (A_f / V) u_f per face (Algorithm 4's M U with the step size:
  * structured meshes take A/V = 1/h of the face's axis, face-based meshes
  * w_f = dt A_f u_f with 1/V applied per cell), the velocity fl_step_rk_stage
@@ -437,6 +491,18 @@ fl_status fl_step_rk_stage_adjoint_planes(const fl_mesh *mesh, fl_limiter limite
                                           int z_begin, int z_end, const void *x, const void *mu,
                                           const void *lam_a, const void *lam_b, void *out,
                                           const void *u_f, const void *w_f, void *stream);
+
+/*
+ * fl_step_rk_stage_adjoint over the owned cells [c_begin, c_end) of a local
+ * mesh only (each end 0, n_interior or n_owned): an owned cell's output
+ * reads mu and x within two cells of it.  Errors as fl_step_rk_stage_cells.
+ */
+fl_status fl_step_rk_stage_adjoint_cells(const fl_mesh *mesh, fl_limiter limiter,
+                                         fl_dtype dtype, int rk_order, int stage, double dt,
+                                         int64_t c_begin, int64_t c_end, const void *x,
+                                         const void *mu, const void *lam_a, const void *lam_b,
+                                         void *out, const void *u_f, const void *w_f,
+                                         void *stream);
 
 /* Bytes of device workspace fl_step_rk_adjoint needs. */
 fl_status fl_adjoint_workspace_size(const fl_mesh *mesh, fl_dtype dtype, int rk_order,

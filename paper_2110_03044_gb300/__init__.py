@@ -34,14 +34,16 @@ ABI_SYMBOLS = [
     "fl_last_error", "fl_version", "fl_mesh_create_structured", "fl_mesh_create",
     "fl_mesh_create_weighted",
     "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_status", "fl_mesh_destroy",
-    "fl_mesh_to_internal", "fl_mesh_to_user",
+    "fl_mesh_to_internal", "fl_mesh_to_user", "fl_mesh_create_local", "fl_mesh_local_info",
+    "fl_halo_pack",
     "fl_conv_limited_apply",
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_modulated",
     "fl_step_rk_noalloc", "fl_step_rk_blocked", "fl_step_rk_stage", "fl_step_rk_stage_planes",
+    "fl_step_rk_stage_cells",
     "fl_velocity_prescale",
     "fl_conv_limited_adjoint",
     "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_stage_adjoint",
-    "fl_step_rk_stage_adjoint_planes", "fl_step_rk_checkpointed",
+    "fl_step_rk_stage_adjoint_planes", "fl_step_rk_stage_adjoint_cells", "fl_step_rk_checkpointed",
     "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
     "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_tiling", "fl_batch_set_tiling",
     "fl_batch_destroy",
@@ -89,6 +91,9 @@ def lib():
             "fl_mesh_create_structured": (I, [I, I, I, D, D, D, U, PP]),
             "fl_mesh_create": (I, [I64, I64, P, P, P, P, U, PP]),
             "fl_mesh_create_weighted": (I, [I64, I64, P, P, P, P, P, U, PP]),
+            "fl_mesh_create_local": (I, [I64, I64, I64, I64, P, P, P, P, P, PP]),
+            "fl_mesh_local_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+            "fl_halo_pack": (I, [P, I, P, P, I64, P, P]),
             "fl_mesh_permutation": (I, [P, P, P, P]),
             "fl_mesh_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                  ctypes.POINTER(I)]),
@@ -105,12 +110,15 @@ def lib():
             "fl_step_rk_blocked": (I, [P, I, I, I, D, I64, P, P, P, SZ, P]),
             "fl_step_rk_stage": (I, [P, I, I, I, I, D, P, P, P, P, P, P]),
             "fl_step_rk_stage_planes": (I, [P, I, I, I, I, D, I, I, P, P, P, P, P, P]),
+            "fl_step_rk_stage_cells": (I, [P, I, I, I, I, D, I64, I64, P, P, P, P, P, P]),
             "fl_velocity_prescale": (I, [P, I, D, P, P, P]),
             "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
             "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
             "fl_step_rk_stage_adjoint": (I, [P, I, I, I, I, D, P, P, P, P, P, P, P, P]),
             "fl_step_rk_stage_adjoint_planes": (I, [P, I, I, I, I, D, I, I, P, P, P, P, P, P, P,
                                                     P]),
+            "fl_step_rk_stage_adjoint_cells": (I, [P, I, I, I, I, D, I64, I64, P, P, P, P, P, P,
+                                                   P, P]),
             "fl_step_rk_adjoint": (I, [P, I, I, I, D, I64, I64, P, P, P, P, P, SZ, P]),
             "fl_step_rk_checkpointed": (I, [P, I, I, I, D, I64, I64, P, P, P, SZ, P]),
             "fl_step_rk_adjoint_from_checkpoints": (I, [P, I, I, I, D, I64, I64, P, P, P, P,
@@ -224,6 +232,41 @@ def fl_mesh_create(n_cells, face_cells, face_normals, face_areas, cell_volumes, 
     return h.value
 
 
+def fl_mesh_create_local(n_cells, n_owned, n_interior, face_cells, face_normals, face_areas,
+                         cell_volumes, face_distances=None):
+    """The local mesh of one part of a partitioned face-based mesh (see fl.h)."""
+    import numpy as np
+    fc = np.ascontiguousarray(face_cells, dtype=np.int32)
+    nrm = np.ascontiguousarray(face_normals, dtype=np.float64)
+    ar = np.ascontiguousarray(face_areas, dtype=np.float64)
+    vol = np.ascontiguousarray(cell_volumes, dtype=np.float64)
+    dist = None
+    if face_distances is not None:
+        dist = np.ascontiguousarray(face_distances, dtype=np.float64)
+        if dist.shape != (fc.shape[0],):
+            raise ValueError("face_distances must hold one value per face")
+    h = ctypes.c_void_p()
+    _check(lib().fl_mesh_create_local(int(n_cells), int(n_owned), int(n_interior), int(fc.shape[0]),
+                                      fc.ctypes.data, nrm.ctypes.data, ar.ctypes.data,
+                                      vol.ctypes.data, None if dist is None else dist.ctypes.data,
+                                      ctypes.byref(h)))
+    return h.value
+
+
+def fl_mesh_local_info(mesh):
+    """(n_owned, n_interior) of a mesh."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().fl_mesh_local_info(mesh, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def fl_halo_pack(mesh, dtype, src, index, n, dst, stream=None):
+    """dst[i] = src[index[i]] for i < n (device arrays; index int32)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_halo_pack(mesh, c, _fptr(src, c), _ptr(index), int(n), _fptr(dst, c),
+                              _stream(stream)))
+
+
 def fl_mesh_create_weighted(n_cells, face_cells, face_normals, face_areas, cell_volumes,
                             face_distances, flags=0):
     import numpy as np
@@ -333,6 +376,17 @@ def fl_step_rk_stage_planes(mesh, limiter, dtype, rk_order, stage, dt, z_begin, 
                                          _stream(stream)))
 
 
+def fl_step_rk_stage_cells(mesh, limiter, dtype, rk_order, stage, dt, c_begin, c_end, theta_n,
+                           x, y, u_f, w_f=None, stream=None):
+    """fl_step_rk_stage over the owned cells [c_begin, c_end) of a local mesh
+    only (see fl.h)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_stage_cells(mesh, _lim(limiter), c, int(rk_order), int(stage),
+                                        float(dt), int(c_begin), int(c_end), _fptr(theta_n, c),
+                                        _fptr(x, c), _fptr(y, c), _fptr(u_f, c), _fptr(w_f, c),
+                                        _stream(stream)))
+
+
 def fl_velocity_prescale(mesh, dtype, dt, u_f, w_f, stream=None):
     """w_f = dt (A/V) u_f, the velocity fl_step_rk_stage takes in FP64."""
     c = dtype_code(dtype)
@@ -399,6 +453,17 @@ def fl_step_rk_stage_adjoint_planes(mesh, limiter, dtype, rk_order, stage, dt, z
     c = dtype_code(dtype)
     _check(lib().fl_step_rk_stage_adjoint_planes(
         mesh, _lim(limiter), c, int(rk_order), int(stage), float(dt), int(z_begin), int(z_end),
+        _fptr(x, c), _fptr(mu, c), _fptr(lam_a, c), _fptr(lam_b, c), _fptr(out, c),
+        _fptr(u_f, c), _fptr(w_f, c), _stream(stream)))
+
+
+def fl_step_rk_stage_adjoint_cells(mesh, limiter, dtype, rk_order, stage, dt, c_begin, c_end, x,
+                                   mu, lam_a, lam_b, out, u_f, w_f=None, stream=None):
+    """fl_step_rk_stage_adjoint over the owned cells [c_begin, c_end) of a
+    local mesh only (see fl.h)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_stage_adjoint_cells(
+        mesh, _lim(limiter), c, int(rk_order), int(stage), float(dt), int(c_begin), int(c_end),
         _fptr(x, c), _fptr(mu, c), _fptr(lam_a, c), _fptr(lam_b, c), _fptr(out, c),
         _fptr(u_f, c), _fptr(w_f, c), _stream(stream)))
 

@@ -37,6 +37,7 @@ namespace fl {
 fl_status check_buffer(const void *p, size_t bytes, const char *name);
 fl_status check_mesh(const fl_mesh *m);
 fl_status check_enums(int lim, fl_dtype dt);
+fl_status check_cell_range(const fl_mesh *m, int64_t c_begin, int64_t c_end);
 
 namespace {
 
@@ -831,13 +832,15 @@ using namespace fl;
     if (s_ != FL_OK) return s_; \
   } while (0)
 
-// One adjoint stage over planes [zlo, zhi) of a structured mesh (zhi < 0:
-// the whole mesh, any kind): the shared body of fl_step_rk_stage_adjoint and
-// fl_step_rk_stage_adjoint_planes.
+// One adjoint stage over planes [zlo, zhi) of a structured mesh or cells
+// [clo, chi) of a local face-based mesh (a negative end: every plane / owned
+// cell): the shared body of fl_step_rk_stage_adjoint and its _planes and
+// _cells forms.
 static fl_status stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
-                                      int stage, double dtime, int zlo, int zhi, const void *x,
-                                      const void *mu, const void *lam_a, const void *lam_b,
-                                      void *out, const void *u_f, const void *w_f, void *stream) {
+                                      int stage, double dtime, int zlo, int zhi, int64_t clo,
+                                      int64_t chi, const void *x, const void *mu,
+                                      const void *lam_a, const void *lam_b, void *out,
+                                      const void *u_f, const void *w_f, void *stream) {
   FL_TRY(check_mesh(m));
   FL_TRY(check_enums(lim, dt));
   if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
@@ -866,11 +869,13 @@ static fl_status stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_dtype
         return fail(FL_EINVAL, "out overlaps x or mu (the stage reads their neighbours)");
     }
   }
-  if (m->C == 0 || (zhi >= 0 && zhi == zlo)) return FL_OK;
+  if (m->C == 0 || (zhi >= 0 && zhi == zlo) || (chi >= 0 && chi == clo)) return FL_OK;
   if (m->kind == 1) FL_TRY(unstruct_adjoint_prepare(m));
   AdjArgs a;
   a.zlo = zlo;
   a.zhi = zhi;
+  a.clo = clo;
+  a.chi = chi;
   a.x = x;
   a.mu = mu;
   a.out = out;
@@ -925,8 +930,8 @@ fl_status fl_step_rk_stage_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt
                                    int stage, double dtime, const void *x, const void *mu,
                                    const void *lam_a, const void *lam_b, void *out,
                                    const void *u_f, const void *w_f, void *stream) {
-  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, 0, -1, x, mu, lam_a, lam_b, out, u_f,
-                              w_f, stream);
+  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, 0, -1, 0, -1, x, mu, lam_a, lam_b,
+                              out, u_f, w_f, stream);
 }
 
 fl_status fl_step_rk_stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
@@ -938,8 +943,19 @@ fl_status fl_step_rk_stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_d
   if (m->kind != 0) return fail(FL_EUNSUPPORTED, "a plane range needs a structured mesh");
   if (z_begin < 0 || z_end < z_begin || z_end > m->nz)
     return fail(FL_EINVAL, "plane range [%d, %d) is not inside [0, %d]", z_begin, z_end, m->nz);
-  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, z_begin, z_end, x, mu, lam_a, lam_b,
-                              out, u_f, w_f, stream);
+  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, z_begin, z_end, 0, -1, x, mu, lam_a,
+                              lam_b, out, u_f, w_f, stream);
+}
+
+fl_status fl_step_rk_stage_adjoint_cells(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
+                                         int stage, double dtime, int64_t c_begin, int64_t c_end,
+                                         const void *x, const void *mu, const void *lam_a,
+                                         const void *lam_b, void *out, const void *u_f,
+                                         const void *w_f, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_cell_range(m, c_begin, c_end));
+  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, 0, -1, c_begin, c_end, x, mu, lam_a,
+                              lam_b, out, u_f, w_f, stream);
 }
 
 fl_status fl_adjoint_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps,

@@ -174,6 +174,17 @@ fl_status check_mesh(const fl_mesh *m) {
   return FL_OK;
 }
 
+// the cell ranges a stage of a local face-based mesh runs on: block-aligned
+fl_status check_cell_range(const fl_mesh *m, int64_t c_begin, int64_t c_end) {
+  if (m->kind != 1) return fail(FL_EUNSUPPORTED, "a cell range needs a face-based mesh");
+  auto ok = [&](int64_t c) { return c == 0 || c == m->n_interior || c == m->n_owned; };
+  if (!ok(c_begin) || !ok(c_end) || c_end < c_begin)
+    return fail(FL_EINVAL, "cell range [%lld, %lld): each end must be 0, n_interior (%lld) or "
+                           "n_owned (%lld)", (long long)c_begin, (long long)c_end,
+                (long long)m->n_interior, (long long)m->n_owned);
+  return FL_OK;
+}
+
 fl_status check_enums(int lim, fl_dtype dt) {
   if (lim < FL_UPWIND || lim > FL_SMART) return fail(FL_EINVAL, "unknown limiter %d", lim);
   if (dt != FL_F32 && dt != FL_F64) return fail(FL_EINVAL, "unknown dtype %d", (int)dt);
@@ -274,6 +285,7 @@ fl_status fl_mesh_create_structured(int nx, int ny, int nz, double hx, double hy
   m->hy = hy;
   m->hz = hz;
   m->C = C;
+  m->n_owned = m->n_interior = C;
   int na = 0;
   for (int a = 0; a < 3; ++a) {
     m->act[a] = n[a] > 1;
@@ -295,7 +307,20 @@ fl_status fl_mesh_create(int64_t n_cells, int64_t n_faces, const int32_t *face_c
   if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
   *out = nullptr;
   return unstruct_create(n_cells, n_faces, face_cells, face_normals, face_areas, cell_volumes,
-                         nullptr, flags, out);
+                         nullptr, flags, n_cells, n_cells, out);
+}
+
+fl_status fl_mesh_create_local(int64_t n_cells, int64_t n_owned, int64_t n_interior,
+                               int64_t n_faces, const int32_t *face_cells,
+                               const double *face_normals, const double *face_areas,
+                               const double *cell_volumes, const double *face_distances,
+                               fl_mesh **out) {
+  if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_interior < 0 || n_owned < n_interior || n_cells < n_owned)
+    return fail(FL_EINVAL, "need 0 <= n_interior <= n_owned <= n_cells");
+  return unstruct_create(n_cells, n_faces, face_cells, face_normals, face_areas, cell_volumes,
+                         face_distances, 0u, n_owned, n_interior, out);
 }
 
 fl_status fl_mesh_create_weighted(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,
@@ -306,7 +331,7 @@ fl_status fl_mesh_create_weighted(int64_t n_cells, int64_t n_faces, const int32_
   *out = nullptr;
   if (n_faces > 0 && face_distances == nullptr) return fail(FL_EINVAL, "NULL input array");
   return unstruct_create(n_cells, n_faces, face_cells, face_normals, face_areas, cell_volumes,
-                         face_distances, flags, out);
+                         face_distances, flags, n_cells, n_cells, out);
 }
 
 fl_status fl_mesh_permutation(const fl_mesh *m, int32_t *cell_perm, int32_t *face_perm,
@@ -438,12 +463,14 @@ fl_status step_rk_impl(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, do
 
 }  // namespace
 
-// One stage over planes [zlo, zhi) of a structured mesh (zhi < 0: the whole
-// mesh, any kind): the shared body of fl_step_rk_stage and
-// fl_step_rk_stage_planes.
+// One stage over planes [zlo, zhi) of a structured mesh or cells [clo, chi)
+// of a local face-based mesh (a negative end: every plane / owned cell): the
+// shared body of fl_step_rk_stage, fl_step_rk_stage_planes and
+// fl_step_rk_stage_cells.
 static fl_status stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
-                              double dtime, int zlo, int zhi, const void *theta_n, const void *x,
-                              void *y, const void *u_f, const void *w_f, void *stream) {
+                              double dtime, int zlo, int zhi, int64_t clo, int64_t chi,
+                              const void *theta_n, const void *x, void *y, const void *u_f,
+                              const void *w_f, void *stream) {
   FL_TRY(check_mesh(m));
   FL_TRY(check_enums(lim, dt));
   if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
@@ -463,10 +490,12 @@ static fl_status stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int
   const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
   if (m->C > 0 && xb < yb + cb && yb < xb + cb)
     return fail(FL_EINVAL, "x and y overlap (a stage reads neighbours of x while writing y)");
-  if (m->C == 0 || (zhi >= 0 && zhi == zlo)) return FL_OK;
+  if (m->C == 0 || (zhi >= 0 && zhi == zlo) || (chi >= 0 && chi == clo)) return FL_OK;
   StageArgs s;
   s.zlo = zlo;
   s.zhi = zhi;
+  s.clo = clo;
+  s.chi = chi;
   s.x = x;
   s.thn = stage == 0 ? x : theta_n;
   s.y = y;
@@ -540,7 +569,8 @@ fl_status fl_velocity_prescale(const fl_mesh *m, fl_dtype dt, double dtime, cons
 fl_status fl_step_rk_stage(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
                            double dtime, const void *theta_n, const void *x, void *y,
                            const void *u_f, const void *w_f, void *stream) {
-  return stage_planes(m, lim, dt, rk, stage, dtime, 0, -1, theta_n, x, y, u_f, w_f, stream);
+  return stage_planes(m, lim, dt, rk, stage, dtime, 0, -1, 0, -1, theta_n, x, y, u_f, w_f,
+                      stream);
 }
 
 fl_status fl_step_rk_stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
@@ -551,8 +581,26 @@ fl_status fl_step_rk_stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt,
   if (m->kind != 0) return fail(FL_EUNSUPPORTED, "a plane range needs a structured mesh");
   if (z_begin < 0 || z_end < z_begin || z_end > m->nz)
     return fail(FL_EINVAL, "plane range [%d, %d) is not inside [0, %d]", z_begin, z_end, m->nz);
-  return stage_planes(m, lim, dt, rk, stage, dtime, z_begin, z_end, theta_n, x, y, u_f, w_f,
-                      stream);
+  return stage_planes(m, lim, dt, rk, stage, dtime, z_begin, z_end, 0, -1, theta_n, x, y, u_f,
+                      w_f, stream);
+}
+
+fl_status fl_step_rk_stage_cells(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
+                                 double dtime, int64_t c_begin, int64_t c_end,
+                                 const void *theta_n, const void *x, void *y, const void *u_f,
+                                 const void *w_f, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_cell_range(m, c_begin, c_end));
+  return stage_planes(m, lim, dt, rk, stage, dtime, 0, -1, c_begin, c_end, theta_n, x, y, u_f,
+                      w_f, stream);
+}
+
+fl_status fl_mesh_local_info(const fl_mesh *m, int64_t *n_owned, int64_t *n_interior) {
+  if (m == nullptr || n_owned == nullptr || n_interior == nullptr)
+    return fail(FL_EINVAL, "NULL argument");
+  *n_owned = m->n_owned;
+  *n_interior = m->n_interior;
+  return FL_OK;
 }
 
 size_t fl_reduce_workspace_size(void) { return reduce_ws_bytes(); }
@@ -581,7 +629,8 @@ fl_status fl_reduce_mass(const fl_mesh *m, fl_dtype dt, const void *theta, doubl
   int bad = 0;
   const double *vol = (m->kind == 1) ? unstruct_volumes(m) : nullptr;
   const double vc = m->hx * m->hy * m->hz;
-  cudaError_t e = reduce_mass(dt, theta, vol, vc, m->C, ws, as_stream(stream), out, &bad);
+  // the owned cells (all cells but a local mesh's halo)
+  cudaError_t e = reduce_mass(dt, theta, vol, vc, m->n_owned, ws, as_stream(stream), out, &bad);
   if (e != cudaSuccess) return cuda_fail(e, "reduction");
   if (bad) return fail(FL_ENONFINITE, "non-finite value in theta");
   return FL_OK;

@@ -93,6 +93,7 @@ constexpr int UMAXDEG = 8;  // faces per cell (slot table width)
 
 struct UnstructDev {
   int n_blocks = 0;
+  int nb_interior = 0;  // local meshes: blocks [0, nb_interior) hold the interior cells
   int max_block_entries = 0;
   int64_t n_entries = 0;
   int32_t *blk_cell = nullptr;   // [n_blocks + 1] cell range of each block
@@ -141,6 +142,10 @@ struct fl_mesh {
   int *status = nullptr;
   int *status_host = nullptr;
   int64_t C = 0, F = 0;
+  // face-based local meshes of a partition (fl_mesh_create_local): cells
+  // [0, n_interior) and [n_interior, n_owned) are updated, the rest are halo
+  // cells that no kernel writes; other meshes have n_interior = n_owned = C
+  int64_t n_owned = 0, n_interior = 0;
   // structured
   int nx = 1, ny = 1, nz = 1;
   double hx = 1, hy = 1, hz = 1;

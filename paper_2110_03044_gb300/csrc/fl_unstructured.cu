@@ -73,6 +73,7 @@ struct UParams {
   const int32_t *gen_cell;  // GEN: general upstream stencil (see UnstructDev)
   const T *gen_coef;
   int kg;
+  int blk0, nblk;  // the launch covers blocks [blk0, blk0 + nblk)
 };
 
 // v with its sign bit toggled when neg, on the integer pipe (opaque bits:
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(UTHREADS) k_unstruct_stage(const UParams<T> p)
   using F = FT<T>;
   extern __shared__ __align__(16) unsigned char smem[];
   T *s_phi = reinterpret_cast<T *>(smem);
-  const int blk = blockIdx.x;
+  const int blk = p.blk0 + (int)blockIdx.x;
   const int eb = p.blk_entry[blk], ee = p.blk_entry[blk + 1];
   const int cb = p.blk_cell[blk], ce = p.blk_cell[blk + 1];
   // ---- phase 1: every face of the block once
@@ -235,7 +236,7 @@ struct UAParams {
   const uint8_t *inv_sk;
   T e1, e2, b, bdt;
   int bare;
-  long long C;
+  long long c0, C;  // the cells [c0, C) are computed
 };
 
 template <class T>
@@ -279,7 +280,7 @@ __device__ __forceinline__ ULin<T> u_lin(const UAParams<T> &p, int f) {
 template <class T, int LIM, bool GEN, bool PRE>
 __global__ void __launch_bounds__(256) k_unstruct_adjoint(const UAParams<T> p) {
   using F = FT<T>;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < p.C;
+  for (long long c = p.c0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; c < p.C;
        c += (long long)gridDim.x * blockDim.x) {
     T acc = T(0);
     for (int q = p.cf_ptr[c]; q < p.cf_ptr[c + 1]; ++q) {
@@ -336,7 +337,7 @@ __global__ void k_scale_area_t(const T *u, const T *area, T *w, long long nf, T 
 
 template <class T, int SEED, bool PRE, bool GEN, bool MOD = false>
 cudaError_t launch_lim(int lim, const fl_mesh *m, const UParams<T> &p, cudaStream_t st) {
-  const int nb = m->u.n_blocks;
+  const int nb = p.nblk;
   const size_t smem = (size_t)m->u.max_block_entries * sizeof(T) * (PRE ? 2 : 1);
   if (nb == 0) return cudaSuccess;
 #define FL_U_CASE(L)                                                                           \
@@ -415,6 +416,21 @@ cudaError_t run_ustage(const fl_mesh *m, int lim, const StageArgs &s, cudaStream
   p.gen_cell = m->u.gen_cell;
   p.gen_coef = (sizeof(T) == 8) ? reinterpret_cast<const T *>(m->u.gen_coef)
                                 : reinterpret_cast<const T *>(m->u.gen_coef_f);
+  // the blocks of the cell range: every owned cell, the interior, or the rim
+  p.blk0 = 0;
+  p.nblk = m->u.n_blocks;
+  if (s.chi >= 0) {
+    const int64_t lo = s.clo, hi = s.chi;
+    const bool whole = lo == 0 && hi == m->n_owned;
+    if (!whole && lo == 0 && hi == m->n_interior) {
+      p.nblk = m->u.nb_interior;
+    } else if (!whole && lo == m->n_interior && hi == m->n_owned) {
+      p.blk0 = m->u.nb_interior;
+      p.nblk = m->u.n_blocks - m->u.nb_interior;
+    } else if (!whole) {
+      return cudaErrorInvalidValue;  // checked by the entry point
+    }
+  }
   if (m->u.kg > 0) return dispatch_seed<T, true>(lim, m, p, s.seed, pre, st);
   return dispatch_seed<T, false>(lim, m, p, s.seed, pre, st);
 }
@@ -647,8 +663,10 @@ void renumber_cells(const HostMesh &h, std::vector<int32_t> &order, std::vector<
 // ----------------------------------------------------------------- create
 fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const double *normals,
                           const double *areas, const double *volumes, const double *distances,
-                          unsigned flags, fl_mesh **out) {
+                          unsigned flags, int64_t n_owned, int64_t n_interior, fl_mesh **out) {
   if (C < 0 || F < 0) return fail(FL_EINVAL, "negative size");
+  // a local mesh of a partition updates cells [0, n_owned) only
+  const bool local = n_owned < C || n_interior < n_owned;
   if (C >= (1LL << 31) - 1 || F >= (1LL << 31) - 1) return fail(FL_EUNSUPPORTED, "sizes must be < 2^31");
   if ((F > 0 && (!face_cells || !normals || !areas)) || (C > 0 && !volumes))
     return fail(FL_EINVAL, "NULL input array");
@@ -703,6 +721,23 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
       h.cf_idx[fill[h.c1[f]]++] = (int32_t)f;
     }
   }
+  // The cells whose upstream stencil is resolved: every cell of a whole
+  // mesh; in a local mesh the owned cells and the halo cells next to them
+  // (the upwind cell of a face of an owned cell is one of these, and the
+  // caller gives them all their faces).  The outer halo cells only supply
+  // values: their face lists may be cut, and no face evaluated for an owned
+  // cell has one of them upwind.
+  std::vector<uint8_t> resolve(C, local ? 0 : 1);
+  if (local) {
+    for (int64_t c = 0; c < n_owned; ++c) {
+      resolve[c] = 1;
+      for (int64_t t = h.cf_ptr[c]; t < h.cf_ptr[c + 1]; ++t) {
+        const int32_t f = h.cf_idx[t];
+        resolve[h.c0[f]] = 1;
+        resolve[h.c1[f]] = 1;
+      }
+    }
+  }
   // duplicate faces (same cell pair and the same oriented normal), then the
   // upstream cell and sign for both flow directions of every face, cell by
   // cell: for each face f of cell C, the one other face j of C with
@@ -716,6 +751,7 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
     double nrm[UMAXDEG][3];
     int32_t fl_[UMAXDEG];
     for (int64_t Cc = lo; Cc < hi && !err.set.load(); ++Cc) {
+      if (!resolve[Cc]) continue;
       const int deg = (int)(h.cf_ptr[Cc + 1] - h.cf_ptr[Cc]);
       for (int a = 0; a < deg; ++a) {
         fl_[a] = h.cf_idx[h.cf_ptr[Cc] + a];
@@ -782,6 +818,7 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
       for (int64_t f = lo; f < hi; ++f)
         for (int side = 0; side < 2; ++side) {
           const int32_t Cc = side == 0 ? h.c0[f] : h.c1[f];
+          if (!resolve[Cc]) continue;
           int nz = 0;
           for (int64_t q = h.cf_ptr[Cc]; q < h.cf_ptr[Cc + 1]; ++q) {
             const int32_t j = h.cf_idx[q];
@@ -803,7 +840,7 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
           const size_t base = ((size_t)f * 2 + side) * kg;
           int k = 0;
           int32_t U = -1;
-          for (int64_t q = h.cf_ptr[Cc]; q < h.cf_ptr[Cc + 1]; ++q) {
+          for (int64_t q = h.cf_ptr[Cc]; q < h.cf_ptr[Cc + 1] && resolve[Cc]; ++q) {
             const int32_t j = h.cf_idx[q];
             if (j == f) continue;
             const double w = dot3(&h.n[3 * f], &h.n[3 * (int64_t)j]);
@@ -825,8 +862,19 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   // ---- internal numbering
   std::vector<int32_t> order, blk_cell;
   const bool renum = (flags & FL_RENUMBER) != 0;
+  int nb_interior = 0;
   if (renum && C > 0) {
     renumber_cells(h, order, blk_cell);
+  } else if (local) {
+    // the caller's order; blocks cover the interior cells, then the rim
+    // cells, never both, and no halo cell
+    order.resize(C);
+    std::iota(order.begin(), order.end(), 0);
+    blk_cell.clear();
+    for (int64_t c = 0; c < n_interior; c += UBLOCK) blk_cell.push_back((int32_t)c);
+    nb_interior = (int)blk_cell.size();
+    for (int64_t c = n_interior; c < n_owned; c += UBLOCK) blk_cell.push_back((int32_t)c);
+    blk_cell.push_back((int32_t)n_owned);
   } else {
     order.resize(C);
     std::iota(order.begin(), order.end(), 0);
@@ -834,6 +882,7 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
     for (int64_t c = 0; c < C; c += UBLOCK) blk_cell.push_back((int32_t)c);
     blk_cell.push_back((int32_t)C);
   }
+  if (!local) nb_interior = (int)blk_cell.size() - 1;
   std::vector<int32_t> cell_new(C);
   for (int64_t i = 0; i < C; ++i) cell_new[order[i]] = (int32_t)i;
   // faces: by the lower internal cell, then by user id (a stable counting
@@ -956,6 +1005,8 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   m->kind = 1;
   m->C = C;
   m->F = F;
+  m->n_owned = local ? n_owned : C;
+  m->n_interior = local ? n_interior : C;
   if (const fl_status sst = status_alloc(m); sst != FL_OK) {
     delete m;
     return sst;
@@ -966,6 +1017,7 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   m->face_flip.assign(F, 0);
   UnstructDev &u = m->u;
   u.n_blocks = nb;
+  u.nb_interior = nb_interior;
   u.max_block_entries = max_entries;
   u.n_entries = (int64_t)ent_face.size();
   std::vector<float> area_f(area_i.begin(), area_i.end()), ivol_f(ivol_i.begin(), ivol_i.end());
@@ -1086,7 +1138,8 @@ fl_status unstruct_adjoint_prepare(const fl_mesh *mc) {
 namespace {
 template <class T, int LIM>
 cudaError_t launch_uadj(const fl_mesh *m, const UAParams<T> &p, bool pre, cudaStream_t st) {
-  long long blocks = (m->C + 255) / 256;
+  if (p.C <= p.c0) return cudaSuccess;
+  long long blocks = (p.C - p.c0 + 255) / 256;
   if (blocks > 152LL * 16) blocks = 152LL * 16;
   const unsigned g = (unsigned)std::max<long long>(blocks, 1);
   const bool gen = m->u.kg > 0;
@@ -1129,7 +1182,9 @@ cudaError_t run_uadj(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t s
   p.b = (T)s.b;
   p.bdt = (T)(s.cu_dt ? s.b : s.b * s.dt);
   p.bare = s.bare;
-  p.C = m->C;
+  // every owned cell (all cells of a whole mesh), or the range asked for
+  p.c0 = s.chi >= 0 ? s.clo : 0;
+  p.C = s.chi >= 0 ? s.chi : m->n_owned;
   switch (lim) {
     case LIM_UPWIND: return launch_uadj<T, LIM_UPWIND>(m, p, pre, st);
     case LIM_CENTRAL: return launch_uadj<T, LIM_CENTRAL>(m, p, pre, st);

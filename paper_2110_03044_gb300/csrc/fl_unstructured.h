@@ -8,9 +8,10 @@
 namespace fl {
 
 // distances: face distances d_f of a non-uniform mesh, or null (uniform)
+// n_owned / n_interior: the updated cells of a local mesh (both C for a whole mesh)
 fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const double *normals,
                           const double *areas, const double *volumes, const double *distances,
-                          unsigned flags, fl_mesh **out);
+                          unsigned flags, int64_t n_owned, int64_t n_interior, fl_mesh **out);
 void unstruct_free(fl_mesh *m);
 fl_status unstruct_apply(const fl_mesh *m, int lim, fl_dtype dt, const void *theta, const void *u,
                          void *rhs, void *thf, cudaStream_t st);

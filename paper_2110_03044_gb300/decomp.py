@@ -103,6 +103,21 @@ class Slab:
         P = self.plane
         return x[self.halo * P:(self.halo + self.nz_local) * P]
 
+    def split(self, reach=None):
+        """(interior, rims, whole): the owned local planes at least ``reach``
+        planes from both cuts as one range (None when there are none), the
+        ranges of the other owned planes, and the range of all of them."""
+        reach = REACH if reach is None else reach
+        h, n = self.halo, self.nz_local
+        if n <= 2 * reach:
+            return None, [(h, h + n)], (h, h + n)
+        return ((h + reach, h + n - reach), [(h, h + reach), (h + n - reach, h + n)],
+                (h, h + n))
+
+    def check_adjoint(self):
+        if self.halo < HALO_ADJOINT:
+            raise ValueError("the reverse sweep needs a halo of %d planes" % HALO_ADJOINT)
+
     # ------------------------------------------------------------ set-up
     def local_cells(self, glob):
         """A local cell field (ghost planes included) cut from a global one
@@ -212,22 +227,23 @@ HALO_ADJOINT = 3
 REACH = 2
 
 
-def exchange_and_run(slab: Slab, transport, x, run, overlap=True, reach=REACH):
-    """Exchange x's halo and run ``run(z0, z1)`` over every owned local plane
-    (z0, z1 local plane indices).  With ``overlap`` the planes at least
-    ``reach`` planes from both cuts run while the exchange is in flight and
-    the planes next to the cuts after it ends; without it (or when the slab
-    has no such interior) everything runs after the exchange."""
-    h, n = slab.halo, slab.nz_local
-    if not overlap or n <= 2 * reach:
+def exchange_and_run(slab, transport, x, run, overlap=True, reach=None):
+    """Exchange x's halo and run ``run(lo, hi)`` over every owned local range
+    of the domain ``slab`` (a Slab: plane ranges; a partition.GraphPart: cell
+    ranges).  With ``overlap`` the part that reads no halo value (for a slab,
+    the planes at least ``reach`` planes from both cuts) runs while the
+    exchange is in flight and the rest after it ends; without it (or when
+    there is no such interior) everything runs after the exchange."""
+    interior, rims, whole = slab.split(reach)
+    if not overlap or interior is None:
         transport.exchange(slab, x)
-        run(h, h + n)
+        run(*whole)
         return
     pending = start_exchange(transport, slab, x)
-    run(h + reach, h + n - reach)
+    run(*interior)
     pending.wait()
-    run(h, h + reach)
-    run(h + n - reach, h + n)
+    for lo, hi in rims:
+        run(lo, hi)
 
 
 def step_rk(slab: Slab, transport, stage: StageFn, rk_order: int, nsteps: int, theta, a, b=None,
@@ -273,8 +289,7 @@ def gradient_rk(slab: Slab, transport, stage: StageFn, stage_adjoint: StageAdjoi
     local mesh; ``new()`` gives a fresh local field.  The slab needs
     ``halo >= HALO_ADJOINT``.  Returns the local dJ/dtheta_0 (owned planes
     valid)."""
-    if slab.halo < HALO_ADJOINT:
-        raise ValueError("the reverse sweep needs a halo of %d planes" % HALO_ADJOINT)
+    slab.check_adjoint()
     if rk_order not in (1, 3):
         raise ValueError("rk_order must be 1 or 3")
 
