@@ -661,6 +661,76 @@ def run_config_unstructured(args):
                        "faces": F}}
 
 
+def run_config_partition(args):
+    """The 256^3 hex Taylor-Green mesh as a face-based mesh (user order),
+    SMART, SSP-RK3, FP64, cut into --parts parts by the graph partitioner.
+    One GPU runs part 0's three stages (its interior and rim launches on its
+    local mesh; the halo exchange, a transport between GPUs, is left out) and
+    fl_step_rk on the whole face-based mesh; the part's time against 1/P of
+    the whole step is the compute price of the partition (faces on a cut
+    evaluated by both parts, two launches per stage)."""
+    import torch
+
+    import paper_2110_03044_gb300 as fl
+    import workloads as W
+    from paper_2110_03044_gb300.partition import (GraphRollout, LocalGraphTransport, build_parts,
+                                                  partition_graph)
+    fl.build()
+    n, P = args.n, args.parts
+    wl = W.config_taylor_green(n=n, seed=1, nsteps=50, limiter="smart")
+    mesh = wl.mesh
+    t0 = time.perf_counter()
+    part = partition_graph(mesh.n_cells, mesh.face_cells, P)
+    parts = build_parts(mesh.n_cells, mesh.face_cells, part)
+    t_part = time.perf_counter() - t0
+    gp = parts[0]
+    ug = torch.tensor(wl.u, device="cuda")
+    thg = torch.tensor(wl.theta0, device="cuda")
+    e0, e1 = _events()
+    # the whole mesh, the caller's order (no renumbering, like the parts)
+    m = fl.Mesh.from_faces(mesh.n_cells, mesh.face_cells, mesh.normals, mesh.areas, mesh.volumes)
+    nb = fl.fl_workspace_size(m.handle, torch.float64, 3)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    th = thg.clone()
+    fl.fl_step_rk(m.handle, "smart", torch.float64, 3, wl.dt, args.warmup, th, ug, ws, nb)
+    torch.cuda.synchronize()
+    e0.record()
+    fl.fl_step_rk(m.handle, "smart", torch.float64, 3, wl.dt, args.steps, th, ug, ws, nb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_whole = e0.elapsed_time(e1) / args.steps
+    m.close()
+    del ws
+    # part 0 alone: its rollout loop with an exchange that moves nothing
+    class NoExchange(LocalGraphTransport):
+        def exchange(self, gp_, x):
+            return None
+
+    ro = GraphRollout(mesh, gp, ug, "smart", torch.float64, wl.dt, transport=NoExchange())
+    tl = ro.local_field(thg)
+    ro.step(tl, 3, args.warmup)
+    torch.cuda.synchronize()
+    e0.record()
+    ro.step(tl, 3, args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_part = e0.elapsed_time(e1) / args.steps
+    n_faces_local = int(gp.face_ids.shape[0])
+    ro.close()
+    F = mesh.n_faces
+    return {"metric": "partitioned face-based SSP-RK3: one part's step time against 1/P of the "
+                      "whole mesh's", "value": ms_part / (ms_whole / P), "unit": "ratio",
+            "higher_is_better": False, "dtype": "f64",
+            "whole_mesh_ms_per_step": ms_whole, "part_ms_per_step": ms_part,
+            "whole_face_updates_per_s": F * 3 / (ms_whole * 1e-3),
+            "partition_s": t_part,
+            "part": {"owned": gp.n_owned, "interior": gp.n_interior, "halo": int(gp.halo_ids.shape[0]),
+                     "local_faces": n_faces_local, "faces_per_part_ideal": F // P},
+            "config": {"workload": "hex%d^3_faces_smart_ssprk3_%dparts" % (n, P),
+                       "cells": mesh.n_cells, "faces": F, "parts": P,
+                       "exchange": "not timed (no second GPU)"}}
+
+
 def run_config_batched(args):
     """64 periodic boxes, sizes seeded in [32, 128]^3, each with its own
     solenoidal velocity and scalar, van Leer, SSP-RK3: one persistent launch
@@ -1181,11 +1251,14 @@ def main():
                     help="--config batched: the dtypes to run (comma-separated)")
     ap.add_argument("--tiling-sweep", action="store_true",
                     help="--config batched: also time every decomposition the autotuner tries")
+    ap.add_argument("--parts", type=int, default=4,
+                    help="--config partition: the number of parts")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu DRAM bytes per stage launch of the current kernel, if measured")
     ap.add_argument("--config", default="tg256",
                     choices=["tg256", "1d", "unstructured", "batched", "adjoint", "deformation",
-                             "algebraic", "blocked", "stretched", "polyhedra", "decomp"])
+                             "algebraic", "blocked", "stretched", "polyhedra", "decomp",
+                             "partition"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -1198,7 +1271,8 @@ def main():
               "deformation": run_config_deformation,
               "algebraic": run_config_algebraic, "blocked": run_config_blocked,
               "stretched": run_config_stretched,
-              "polyhedra": run_config_polyhedra, "decomp": run_config_decomp}[args.config]
+              "polyhedra": run_config_polyhedra, "decomp": run_config_decomp,
+              "partition": run_config_partition}[args.config]
         line = fn(args)
         if line is not None:
             print(json.dumps(line))

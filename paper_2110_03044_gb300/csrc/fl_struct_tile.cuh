@@ -36,6 +36,17 @@ struct SParams {
 
 enum { SEED_PLAIN = 0, SEED_COMBINE = 1, SEED_APPLY = 2 };
 
+// FP64 cell differences: 1 forms the exact ones on the integer pipe
+// (FT<double>::sub_exact), 0 takes the FP64 subtraction for all
+#ifndef FL_SUB_INT
+#define FL_SUB_INT 0
+#endif
+template <class T>
+__device__ __forceinline__ T cell_diff(T a, T b) {
+  if constexpr (FL_SUB_INT && sizeof(T) == 8) return FT<T>::sub_exact(a, b);
+  else return FT<T>::sub(a, b);
+}
+
 // Keeps a value as computed: the compiler may no longer recompute it from
 // its operands at a later use.  Under the register cap it otherwise
 // rematerialised the z-window differences, spending FP64 pipe slots.
@@ -220,18 +231,22 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
       for (int it = tid; it < TY * (TX + 3); it += NT) {
         const int r = it / (TX + 3), q = it - r * (TX + 3);
         const T *row = &s_th[(r + 2) * SW];
-        s_dx[it] = F::sub(row[q + 1], row[q]);
+        s_dx[it] = cell_diff<T>(row[q + 1], row[q]);
       }
     }
     if (need_y) {
       for (int it = tid; it < (TY + 3) * TX; it += NT) {
         const int r = it / TX, c = it - r * TX;
-        s_dy[it] = F::sub(s_th[(r + 1) * SW + c + 2], s_th[r * SW + c + 2]);
+        s_dy[it] = cell_diff<T>(s_th[(r + 1) * SW + c + 2], s_th[r * SW + c + 2]);
       }
     }
     T dz_p1 = T(0);
     if (need_z) {
+#if FL_SUB_INT >= 2
+      dz_p1 = cell_diff<T>(thp2, thp1);
+#else
       dz_p1 = F::sub(thp2, thp1);
+#endif
       keep(dz_p1);
     }
     __syncthreads();

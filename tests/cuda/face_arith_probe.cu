@@ -1,7 +1,9 @@
 // Test probe (not part of the library): runs building blocks of the stage
 // kernels on arrays -- FT<double>::quot and FT<float>::quot (the van Leer
 // quotient by Newton-Raphson) beside CUDA's IEEE divisions __ddiv_rn and
-// __fdiv_rn, and smart_piece (SMART's exact integer piece test).
+// __fdiv_rn, smart_piece (SMART's exact integer piece test), and
+// FT<double>::sub_exact (exact differences on the integer pipe) beside
+// __dsub_rn.
 #include <cuda_runtime.h>
 
 #include "fl_face.cuh"
@@ -43,6 +45,14 @@ __global__ void k_smart_mid(const double *p, const double *q, unsigned long long
   if (i >= count) return;
   using F = fl::FT<double>;
   g[i] = F::smart_mid(F::bits(p[i]), F::bits(q[i]));
+}
+
+__global__ void k_sub_exact(const double *a, const double *b, double *d, double *ref,
+                            int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  d[i] = fl::FT<double>::sub_exact(a[i], b[i]);
+  ref[i] = __dsub_rn(a[i], b[i]);
 }
 
 template <class T>
@@ -123,5 +133,24 @@ extern "C" int probe_limiter_term(const double *p, const double *q, unsigned lon
   cudaFree(dp);
   cudaFree(dq);
   cudaFree(dg);
+  return rc;
+}
+
+// d = sub_exact(a, b); ref = __dsub_rn(a, b).  Host arrays of count.
+extern "C" int probe_sub_exact(const double *a, const double *b, double *d, double *ref,
+                               int count) {
+  double *da = nullptr, *db = nullptr, *dd = nullptr, *dr = nullptr;
+  int rc = to_device(a, &da, count) | to_device(b, &db, count) |
+           to_device<double>(nullptr, &dd, count) | to_device<double>(nullptr, &dr, count);
+  if (rc == 0) {
+    k_sub_exact<<<(count + 255) / 256, 256>>>(da, db, dd, dr, count);
+    rc = cudaMemcpy(d, dd, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess;
+    rc |= cudaMemcpy(ref, dr, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost) !=
+          cudaSuccess;
+  }
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dd);
+  cudaFree(dr);
   return rc;
 }

@@ -42,6 +42,7 @@ def probe(tmp_path_factory):
     lib.probe_quot32.argtypes = [P, P, P, P, ctypes.c_int]
     lib.probe_smart.argtypes = [P, P, P, ctypes.c_int]
     lib.probe_limiter_term.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int]
+    lib.probe_sub_exact.argtypes = [P, P, P, P, ctypes.c_int]
     return lib
 
 
@@ -204,3 +205,31 @@ def test_smart_middle_piece_is_correctly_rounded(probe):
                      for a, b in zip(p, q)])
     bad = np.nonzero(g != want)[0]
     assert bad.size == 0, [(p[i], q[i], g[i], want[i]) for i in bad[:5]]
+
+
+def test_integer_pipe_difference_has_the_bits_of_the_fp64_subtraction(probe):
+    # sub_exact forms exact differences (Sterbenz pairs) on the integer pipe
+    # and hands every other pair to __dsub_rn: all results carry the bits of
+    # __dsub_rn, zeros' signs included
+    rng = np.random.default_rng(41)
+    n = 200_000
+    base = rng.uniform(-4, 4, n) * 2.0 ** rng.integers(-40, 40, n)
+    near = base * rng.uniform(0.45, 2.2, n)                 # ratios around Sterbenz's range
+    ulps = np.nextafter(base, np.inf) + rng.integers(-3, 4, n) * np.spacing(base)
+    pw = 2.0 ** rng.integers(-1000, 1000, n)
+    edge = np.array([0.0, -0.0, 1.0, -1.0, 2.0, 0.5, 1.5, 3.0, 2.0 ** -1022, 2.0 ** -1021,
+                     2.0 ** -1074, 5e-324 * 7, 1.7976931348623157e308, np.inf, -np.inf, np.nan,
+                     2.0 ** 53, 2.0 ** 53 + 2, 1 + 2.0 ** -52, 2 - 2.0 ** -52, 4 - 2.0 ** -51])
+    ea, eb = np.meshgrid(edge, edge)
+    a = np.concatenate([base, base, base, pw, pw * 1.5, ea.ravel()])
+    b = np.concatenate([near, ulps, -near, pw * (1 + 2.0 ** -52), pw * 0.75, eb.ravel()])
+    a = np.ascontiguousarray(a)
+    b = np.ascontiguousarray(b)
+    d = np.empty_like(a)
+    ref = np.empty_like(a)
+    assert probe.probe_sub_exact(_ptr(a), _ptr(b), _ptr(d), _ptr(ref), len(a)) == 0
+    assert np.array_equal(d.view(np.uint64), ref.view(np.uint64))
+    # most of the near pairs are Sterbenz pairs: the integer path is exercised
+    exact = (np.sign(base) == np.sign(near)) & (np.abs(near) <= 2 * np.abs(base)) & \
+            (np.abs(base) <= 2 * np.abs(near))
+    assert exact.mean() > 0.5
