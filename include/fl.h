@@ -163,22 +163,28 @@ fl_status fl_mesh_create_weighted(int64_t n_cells, int64_t n_faces, const int32_
  * A stencil of an owned cell reaches two cells deep (the face's other cell,
  * and the upstream cell behind the upwind one), so the caller gives:
  *   - every face of every owned cell and of every halo cell adjacent to an
- *     owned cell, in the relative order of the whole mesh's faces (a cell
- *     then sums its faces in the whole mesh's order and gets its bits);
+ *     owned cell (without FL_RENUMBER, in the relative order of the whole
+ *     mesh's faces: a cell then sums its faces in the whole mesh's order
+ *     and gets its bits);
  *   - the cells of those faces (the second halo ring may have cut face
  *     lists: no stencil of an owned cell is taken at them).
- * face_distances: NULL, or as in fl_mesh_create_weighted.  Other arguments
- * and errors as fl_mesh_create (no renumbering: the caller's cell order
- * keeps its locality); FL_EINVAL unless 0 <= n_interior <= n_owned <=
- * n_cells.  Multi-stage calls (fl_step_rk ...) on a local mesh run with the
- * halo as it stands; a decomposed run calls the stage entry points and
- * refreshes the halo before each.  fl_reduce_mass sums the owned cells.
+ * face_distances: NULL, or as in fl_mesh_create_weighted.  flags: 0 or
+ * FL_RENUMBER, which reorders the interior cells among themselves and the
+ * rim cells among themselves into compact blocks (the halo cells and their
+ * order stay as given); fl_mesh_permutation then gives the internal order,
+ * in which the compute calls take their fields (a caller can build its
+ * local fields in that order directly), and the cells then sum their faces
+ * in the internal face order.  Other arguments and errors as
+ * fl_mesh_create; FL_EINVAL unless 0 <= n_interior <= n_owned <= n_cells.
+ * Multi-stage calls (fl_step_rk ...) on a local mesh run with the halo as it
+ * stands; a decomposed run calls the stage entry points and refreshes the
+ * halo before each.  fl_reduce_mass sums the owned cells.
  */
 fl_status fl_mesh_create_local(int64_t n_cells, int64_t n_owned, int64_t n_interior,
                                int64_t n_faces, const int32_t *face_cells,
                                const double *face_normals, const double *face_areas,
                                const double *cell_volumes, const double *face_distances,
-                               fl_mesh **out);
+                               unsigned flags, fl_mesh **out);
 
 /* n_owned and n_interior of a mesh (both n_cells for a whole mesh). */
 fl_status fl_mesh_local_info(const fl_mesh *mesh, int64_t *n_owned, int64_t *n_interior);

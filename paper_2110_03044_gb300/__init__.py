@@ -91,7 +91,7 @@ def lib():
             "fl_mesh_create_structured": (I, [I, I, I, D, D, D, U, PP]),
             "fl_mesh_create": (I, [I64, I64, P, P, P, P, U, PP]),
             "fl_mesh_create_weighted": (I, [I64, I64, P, P, P, P, P, U, PP]),
-            "fl_mesh_create_local": (I, [I64, I64, I64, I64, P, P, P, P, P, PP]),
+            "fl_mesh_create_local": (I, [I64, I64, I64, I64, P, P, P, P, P, U, PP]),
             "fl_mesh_local_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
             "fl_halo_pack": (I, [P, I, P, P, I64, P, P]),
             "fl_mesh_permutation": (I, [P, P, P, P]),
@@ -233,7 +233,7 @@ def fl_mesh_create(n_cells, face_cells, face_normals, face_areas, cell_volumes, 
 
 
 def fl_mesh_create_local(n_cells, n_owned, n_interior, face_cells, face_normals, face_areas,
-                         cell_volumes, face_distances=None):
+                         cell_volumes, face_distances=None, flags=0):
     """The local mesh of one part of a partitioned face-based mesh (see fl.h)."""
     import numpy as np
     fc = np.ascontiguousarray(face_cells, dtype=np.int32)
@@ -249,7 +249,7 @@ def fl_mesh_create_local(n_cells, n_owned, n_interior, face_cells, face_normals,
     _check(lib().fl_mesh_create_local(int(n_cells), int(n_owned), int(n_interior), int(fc.shape[0]),
                                       fc.ctypes.data, nrm.ctypes.data, ar.ctypes.data,
                                       vol.ctypes.data, None if dist is None else dist.ctypes.data,
-                                      ctypes.byref(h)))
+                                      int(flags), ctypes.byref(h)))
     return h.value
 
 

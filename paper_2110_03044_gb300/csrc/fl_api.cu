@@ -314,13 +314,13 @@ fl_status fl_mesh_create_local(int64_t n_cells, int64_t n_owned, int64_t n_inter
                                int64_t n_faces, const int32_t *face_cells,
                                const double *face_normals, const double *face_areas,
                                const double *cell_volumes, const double *face_distances,
-                               fl_mesh **out) {
+                               unsigned flags, fl_mesh **out) {
   if (out == nullptr) return fail(FL_EINVAL, "out is NULL");
   *out = nullptr;
   if (n_interior < 0 || n_owned < n_interior || n_cells < n_owned)
     return fail(FL_EINVAL, "need 0 <= n_interior <= n_owned <= n_cells");
   return unstruct_create(n_cells, n_faces, face_cells, face_normals, face_areas, cell_volumes,
-                         face_distances, 0u, n_owned, n_interior, out);
+                         face_distances, flags, n_owned, n_interior, out);
 }
 
 fl_status fl_mesh_create_weighted(int64_t n_cells, int64_t n_faces, const int32_t *face_cells,

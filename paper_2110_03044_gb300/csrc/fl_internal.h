@@ -95,6 +95,9 @@ struct UnstructDev {
   int n_blocks = 0;
   int nb_interior = 0;  // local meshes: blocks [0, nb_interior) hold the interior cells
   int max_block_entries = 0;
+  // the same over the interior blocks and over the rim blocks of a local
+  // mesh: a launch over one range sizes its shared memory by that range
+  int max_entries_interior = 0, max_entries_rim = 0;
   int64_t n_entries = 0;
   int32_t *blk_cell = nullptr;   // [n_blocks + 1] cell range of each block
   int32_t *blk_entry = nullptr;  // [n_blocks + 1] entry range of each block

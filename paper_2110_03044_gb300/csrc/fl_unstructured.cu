@@ -338,7 +338,11 @@ __global__ void k_scale_area_t(const T *u, const T *area, T *w, long long nf, T 
 template <class T, int SEED, bool PRE, bool GEN, bool MOD = false>
 cudaError_t launch_lim(int lim, const fl_mesh *m, const UParams<T> &p, cudaStream_t st) {
   const int nb = p.nblk;
-  const size_t smem = (size_t)m->u.max_block_entries * sizeof(T) * (PRE ? 2 : 1);
+  const int ents = (p.blk0 == 0 && nb == m->u.nb_interior && nb < m->u.n_blocks)
+                       ? m->u.max_entries_interior
+                   : (p.blk0 > 0 && p.blk0 == m->u.nb_interior) ? m->u.max_entries_rim
+                                                                : m->u.max_block_entries;
+  const size_t smem = (size_t)ents * sizeof(T) * (PRE ? 2 : 1);
   if (nb == 0) return cudaSuccess;
 #define FL_U_CASE(L)                                                                           \
   case L: {                                                                                    \
@@ -863,18 +867,57 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   std::vector<int32_t> order, blk_cell;
   const bool renum = (flags & FL_RENUMBER) != 0;
   int nb_interior = 0;
-  if (renum && C > 0) {
-    renumber_cells(h, order, blk_cell);
-  } else if (local) {
-    // the caller's order; blocks cover the interior cells, then the rim
-    // cells, never both, and no halo cell
-    order.resize(C);
-    std::iota(order.begin(), order.end(), 0);
+  if (local) {
+    // blocks cover the interior cells, then the rim cells, never both, and
+    // no halo cell.  With FL_RENUMBER the interior and the rim each take the
+    // order of the whole local mesh's renumbering (compact tiles or balls);
+    // the halo cells keep the caller's order (a neighbour's values arrive as
+    // one slice).  Otherwise the caller's order.
+    std::vector<int32_t> full, full_blk;
+    if (renum && C > 0) {
+      renumber_cells(h, full, full_blk);
+    } else {
+      full.resize(C);
+      std::iota(full.begin(), full.end(), 0);
+      for (int64_t c = 0; c <= C; c += UBLOCK) full_blk.push_back((int32_t)c);
+      if (full_blk.back() != C) full_blk.push_back((int32_t)C);
+    }
+    order.clear();
+    order.reserve(C);
     blk_cell.clear();
-    for (int64_t c = 0; c < n_interior; c += UBLOCK) blk_cell.push_back((int32_t)c);
+    // interior: a new block where the whole-mesh order starts one (a tile)
+    // or after UBLOCK cells, so the interior's blocks stay whole tiles
+    // where no rim cell was taken out
+    {
+      size_t b = 0;
+      int64_t prev = -1, count = 0;
+      for (int64_t i = 0; i < C; ++i) {
+        while (b + 1 < full_blk.size() && full_blk[b + 1] <= i) ++b;
+        const int32_t c = full[i];
+        if (c >= n_interior) continue;
+        if ((int64_t)b != prev || count == UBLOCK) {
+          blk_cell.push_back((int32_t)order.size());
+          prev = (int64_t)b;
+          count = 0;
+        }
+        order.push_back(c);
+        ++count;
+      }
+    }
     nb_interior = (int)blk_cell.size();
-    for (int64_t c = n_interior; c < n_owned; c += UBLOCK) blk_cell.push_back((int32_t)c);
+    // rim cells lie in a thin shell: runs of them are scattered in space, so
+    // their blocks are kept small (fewer faces per block, less shared memory)
+    for (int64_t i = 0; i < C; ++i) {
+      const int32_t c = full[i];
+      if (c < n_interior || c >= n_owned) continue;
+      if ((order.size() - (size_t)n_interior) % (UBLOCK / 4) == 0)
+        blk_cell.push_back((int32_t)order.size());
+      order.push_back(c);
+    }
+    for (int64_t c = n_owned; c < C; ++c) order.push_back((int32_t)c);
     blk_cell.push_back((int32_t)n_owned);
+  } else if (renum && C > 0) {
+    renumber_cells(h, order, blk_cell);
   } else {
     order.resize(C);
     std::iota(order.begin(), order.end(), 0);
@@ -965,11 +1008,13 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
       blk_entry[b + 1] = (int32_t)list.size();
     }
   });
-  int max_entries = 0;
+  int max_entries = 0, max_int = 0, max_rim = 0;
   for (int b = 0; b < nb; ++b) {
     if (blk_entry[b + 1] > 0x7FFF)
       return fail(FL_EUNSUPPORTED, "block %d has %d faces", b, blk_entry[b + 1]);
     max_entries = std::max(max_entries, (int)blk_entry[b + 1]);
+    if (b < nb_interior) max_int = std::max(max_int, (int)blk_entry[b + 1]);
+    else max_rim = std::max(max_rim, (int)blk_entry[b + 1]);
     blk_entry[b + 1] += blk_entry[b];
   }
   std::vector<int32_t> ent_face(blk_entry[nb]);
@@ -1019,6 +1064,8 @@ fl_status unstruct_create(int64_t C, int64_t F, const int32_t *face_cells, const
   u.n_blocks = nb;
   u.nb_interior = nb_interior;
   u.max_block_entries = max_entries;
+  u.max_entries_interior = max_int;
+  u.max_entries_rim = max_rim;
   u.n_entries = (int64_t)ent_face.size();
   std::vector<float> area_f(area_i.begin(), area_i.end()), ivol_f(ivol_i.begin(), ivol_i.end());
   fl_status st = FL_OK;

@@ -164,6 +164,28 @@ class GraphPart:
         """A local face field cut from a global one."""
         return glob[_index_like(glob, self.face_ids)]
 
+    def reordered(self, cell_perm, face_perm) -> "GraphPart":
+        """This part in the internal order of its local mesh, created with
+        FL_RENUMBER: cell_perm[i] / face_perm[f] (fl_mesh_permutation) is the
+        internal index of local cell i / face f.  The library reorders the
+        interior and the rim among themselves and keeps the halo, so the
+        receive slices stand; the send lists and the local ids follow."""
+        cp = np.asarray(cell_perm, dtype=np.int64)
+        fp = np.asarray(face_perm, dtype=np.int64)
+        n_o = self.n_owned
+        if not np.array_equal(cp[n_o:], np.arange(n_o, self.n_cells)):
+            raise ValueError("the halo cells must keep their places")
+        inv = np.empty_like(cp)
+        inv[cp] = np.arange(cp.shape[0])
+        invf = np.empty_like(fp)
+        invf[fp] = np.arange(fp.shape[0])
+        return GraphPart(rank=self.rank, world=self.world,
+                         owned_ids=self.owned_ids[inv[:n_o]], n_interior=self.n_interior,
+                         halo_ids=self.halo_ids, face_ids=self.face_ids[invf],
+                         face_cells=cp[self.face_cells[invf]].astype(np.int32),
+                         recv=list(self.recv),
+                         send=[(d, cp[ids].astype(np.int32)) for d, ids in self.send])
+
 
 def _index_like(x, ids):
     try:
@@ -353,16 +375,25 @@ class GraphRollout:
     """A rank's part of a partitioned rollout on the GPU: the local mesh
     (fl_mesh_create_local), its face velocities (and, in FP64, the
     pre-scaled velocity fl_step_rk uses), and the library's cell-range stage
-    kernels; the halo goes through fl_halo_pack and torch.distributed."""
+    kernels; the halo goes through fl_halo_pack and torch.distributed.
+    ``renumber`` lets the library reorder the interior and the rim into
+    compact blocks (the part's lists follow its internal order); without it
+    the owned cells give the whole mesh's bits."""
 
     def __init__(self, mesh, gp: GraphPart, u_global, limiter, dtype, dt, transport=None,
-                 overlap=True):
+                 overlap=True, renumber=False):
         import torch
 
-        from . import Mesh, fl_halo_pack, fl_mesh_create_local, fl_velocity_prescale
+        from . import (FL_RENUMBER, Mesh, fl_halo_pack, fl_mesh_create_local,
+                       fl_mesh_permutation, fl_velocity_prescale)
         C, n_o, n_i, fcl, nrm, ar, vol, dist = local_mesh_arrays(mesh, gp)
+        self.mesh = Mesh(fl_mesh_create_local(C, n_o, n_i, fcl, nrm, ar, vol, dist,
+                                              FL_RENUMBER if renumber else 0))
+        if renumber:
+            # fields are built in the library's internal order directly
+            cp, fp, _ = fl_mesh_permutation(self.mesh.handle)
+            gp = gp.reordered(cp, fp)
         self.gp = gp
-        self.mesh = Mesh(fl_mesh_create_local(C, n_o, n_i, fcl, nrm, ar, vol, dist))
         self.u = gp.local_faces(u_global).to(dtype).contiguous()
         self.w = None
         if dtype == torch.float64 and dt > 0:

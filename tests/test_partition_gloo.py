@@ -244,3 +244,39 @@ def test_gloo_partitioned_gradient_equals_whole_mesh_oracle(name, world, lim, rk
     tgt = np.random.default_rng(7).normal(size=mesh.n_cells)
     _, g_ref = oracle.gradient(mesh, lim, rk, dt, 3, u, th, tgt)
     assert np.max(np.abs(got - g_ref)) <= 1e-13 * np.max(np.abs(g_ref))
+
+
+@pytest.mark.parametrize("name", ["hex", "tet"])
+def test_reordered_part_follows_an_internal_order(name):
+    # a renumbered local mesh permutes the interior and the rim among
+    # themselves and keeps the halo: the part's lists follow that order and
+    # still name the same global cells, faces and exchange values
+    mesh = MESHES[name]()
+    fc = np.asarray(mesh.face_cells, dtype=np.int64)
+    part = partition_graph(mesh.n_cells, fc, 3)
+    parts = build_parts(mesh.n_cells, fc, part)
+    rng = np.random.default_rng(11)
+    new = []
+    for gp in parts:
+        n_i, n_o, C = gp.n_interior, gp.n_owned, gp.n_cells
+        cp = np.concatenate([rng.permutation(n_i), n_i + rng.permutation(n_o - n_i),
+                             np.arange(n_o, C)])
+        fp = rng.permutation(gp.face_ids.shape[0])
+        r = gp.reordered(cp, fp)
+        # the cell at internal index cp[i] is the cell at local index i
+        assert np.array_equal(r.owned_ids[cp[:n_o]], gp.owned_ids)
+        assert np.array_equal(r.face_ids[fp], gp.face_ids)
+        assert np.array_equal(r.cell_ids[r.face_cells], fc[r.face_ids])
+        assert np.array_equal(np.sort(r.owned_ids[:n_i]), np.sort(gp.owned_ids[:n_i]))
+        new.append(r)
+        with pytest.raises(ValueError):  # the halo must stay in place
+            bad = cp.copy()
+            if C > n_o + 1:
+                bad[[n_o, n_o + 1]] = bad[[n_o + 1, n_o]]
+                gp.reordered(bad, fp)
+            else:
+                raise ValueError
+    for q in new:
+        for src, off, cnt in q.recv:
+            sent = dict(new[src].send)[q.rank]
+            assert np.array_equal(new[src].owned_ids[sent], q.halo_ids[off:off + cnt])
