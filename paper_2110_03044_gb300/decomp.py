@@ -366,6 +366,8 @@ class SlabRollout:
         self.limiter, self.dtype, self.dt = limiter, dtype, dt
         self.transport = transport or TorchTransport()
         self.overlap = overlap
+        self.h = tuple(h)
+        self._owned_mesh = None
 
     def local_field(self, theta_global):
         return self.slab.local_cells(theta_global).to(self.dtype).contiguous()
@@ -402,5 +404,38 @@ class SlabRollout:
                            rk_order, nsteps, every, theta_local, lam_T_local,
                            lambda: torch.empty_like(theta_local), overlap=self.overlap)
 
+    def mass(self, theta_local):
+        """sum_c V_c theta_c over the whole mesh (the conservation
+        diagnostic): fl_reduce_mass over this rank's owned planes, summed
+        over the ranks."""
+        import torch
+
+        from . import Mesh, fl_reduce_mass, fl_reduce_workspace_size
+        from .replicas import sum_over_ranks
+        if self._owned_mesh is None:
+            nx, ny, _ = self.slab.dims
+            self._owned_mesh = Mesh.structured(nx, ny, self.slab.nz_local, *self.h)
+        ws = torch.empty(max(fl_reduce_workspace_size(), 1), dtype=torch.uint8,
+                         device=theta_local.device)
+        own = fl_reduce_mass(self._owned_mesh.handle, self.dtype, self.slab.owned(theta_local), ws)
+        return sum_over_ranks(own, theta_local.device)
+
+    def max_abs_velocity(self):
+        """max_f |u_f| over the whole mesh (the CFL diagnostic): this rank's
+        local faces (copies of ghost-plane faces change no maximum), then
+        the maximum over the ranks."""
+        return _max_abs_faces(self.u)
+
     def close(self):
+        if self._owned_mesh is not None:
+            self._owned_mesh.close()
         self.mesh.close()
+
+
+def _max_abs_faces(u):
+    import torch
+
+    from . import fl_reduce_max_abs, fl_reduce_workspace_size
+    from .replicas import max_over_ranks
+    ws = torch.empty(max(fl_reduce_workspace_size(), 1), dtype=torch.uint8, device=u.device)
+    return max_over_ranks(fl_reduce_max_abs(u.dtype, u, u.numel(), ws), u.device)

@@ -456,6 +456,12 @@ class GraphRollout:
         return sum_over_ranks(fl_reduce_mass(self.mesh.handle, self.dtype, theta_local, ws),
                               theta_local.device)
 
+    def max_abs_velocity(self):
+        """max_f |u_f| over the whole mesh: this rank's local faces, then the
+        maximum over the ranks."""
+        from .decomp import _max_abs_faces
+        return _max_abs_faces(self.u)
+
     def close(self):
         self.mesh.close()
 

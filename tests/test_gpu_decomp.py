@@ -347,3 +347,28 @@ def test_stage_planes_argument_errors(fl):
                                    xf, torch.empty_like(xf), uf)
     assert e.value.status == fl.FL_EUNSUPPORTED
     fm.close()
+
+
+def test_decomposed_diagnostics(fl):
+    # mass: the ranks' owned-plane sums (fl_reduce_mass on the owned planes)
+    # add up to the whole mesh's; max |u_f|: every rank's local faces give the
+    # global maximum (a single process: no group, each rank's own value)
+    import math
+    dims = (40, 12, 24)
+    h = tuple(0.7 / d for d in dims)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(31)
+    th = rng.uniform(-1, 1, mesh.n_cells)
+    u = 0.3 * W.mixed_sign_velocity(mesh.n_faces, 32)
+    ug = torch.tensor(u, device="cuda")
+    shares, maxima = [], []
+    for r in range(3):
+        slab = Slab(dims, r, 3)
+        ro = SlabRollout(slab, h, ug, "superbee", torch.float64, 0.01)
+        tl = ro.local_field(torch.tensor(th, device="cuda"))
+        shares.append(ro.mass(tl))
+        maxima.append(ro.max_abs_velocity())
+        ro.close()
+    want = math.fsum((th * mesh.volumes).tolist())
+    assert abs(math.fsum(shares) - want) <= 1e-13 * max(1.0, abs(want))
+    assert max(maxima) == float(np.max(np.abs(u)))
