@@ -644,7 +644,7 @@ def run_config_unstructured(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     C, F = pm.n_cells, pm.n_faces
-    # SURVEY-style algorithmic bytes of the face-based step: per stage theta
+    # algorithmic bytes of the face-based step: per stage theta
     # in/out, u_f, the face records (c0, c1, up0, up1) and the cell -> 6 faces
     # lists, plus theta^n in stages 2-3 (352 B per cell and SSP-RK3 step)
     hbm_peak, peak_kind = peaks()
