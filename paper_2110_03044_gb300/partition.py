@@ -197,10 +197,13 @@ def _index_like(x, ids):
     return ids
 
 
-def build_parts(n_cells: int, face_cells, part: np.ndarray) -> List[GraphPart]:
-    """The local part of every rank for the partition ``part``."""
+def build_parts(n_cells: int, face_cells, part: np.ndarray, world: int = None) -> List[GraphPart]:
+    """The local part of every rank for the partition ``part`` (ranks
+    0 .. world - 1; by default the highest rank ``part`` names); a rank that
+    owns no cell gets an empty part."""
     fc = np.asarray(face_cells, dtype=np.int64).reshape(-1, 2)
-    world = int(part.max()) + 1 if n_cells else 1
+    if world is None:
+        world = int(part.max()) + 1 if n_cells else 1
     ptr, nbr, fid = cell_graph(n_cells, fc)
     deg = np.diff(ptr)
     owner_of_edge = np.repeat(np.arange(n_cells), deg)

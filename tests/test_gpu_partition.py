@@ -31,6 +31,7 @@ MESHES = {
     "hex": lambda: W.structured_mesh(12, 10, 8, 0.7 / 12, 0.9 / 10, 1.1 / 8),
     "tet": lambda: W.tet_mesh(5),
     "prism": lambda: W.prism_mesh(5),
+    "tiny": lambda: W.structured_mesh(4, 3, 2, 0.25, 0.3, 0.5),
 }
 
 
@@ -47,7 +48,7 @@ def _partitioned(fl, name, world, lim, dtype, rk, nsteps, overlap=True, grad=Non
                  renumber=False):
     mesh, th, u, dt = _case(name)
     part = partition_graph(mesh.n_cells, mesh.face_cells, world)
-    parts = build_parts(mesh.n_cells, mesh.face_cells, part)
+    parts = build_parts(mesh.n_cells, mesh.face_cells, part, world)
     tr = ThreadGroupGraphTransport(world)
     ug = torch.tensor(u, dtype=dtype, device="cuda")
     rollouts = [GraphRollout(mesh, gp, ug, lim, dtype, dt, transport=tr, overlap=overlap,
@@ -95,7 +96,8 @@ def _whole_mesh(fl, mesh):
 
 @pytest.mark.parametrize("name,world,overlap", [("hex", 1, True), ("hex", 2, True),
                                                 ("hex", 3, True), ("hex", 4, False),
-                                                ("tet", 3, True), ("prism", 2, True)])
+                                                ("tet", 3, True), ("prism", 2, True),
+                                                ("tiny", 7, True), ("tiny", 30, True)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1), ("smart", 3)])
 def test_partitioned_rollout_equals_whole_mesh_bitwise(fl, name, world, overlap, dtype, lim, rk):

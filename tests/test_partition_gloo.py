@@ -33,6 +33,7 @@ MESHES = {
     "hex": lambda: W.structured_mesh(9, 7, 6, 0.7 / 9, 0.9 / 7, 1.1 / 6),
     "tet": lambda: W.tet_mesh(4),
     "prism": lambda: W.prism_mesh(4),
+    "tiny": lambda: W.structured_mesh(4, 3, 2, 0.25, 0.3, 0.5),
 }
 
 
@@ -161,7 +162,7 @@ class _LocalOracle:
 def _rank_run(name, rank, world, lim, rk, nsteps, transport, overlap, grad):
     mesh, th, u, dt = _case(name)
     part = partition_graph(mesh.n_cells, mesh.face_cells, world)
-    gp = build_parts(mesh.n_cells, mesh.face_cells, part)[rank]
+    gp = build_parts(mesh.n_cells, mesh.face_cells, part, world)[rank]
     lo = _LocalOracle(mesh, gp, lim, rk, dt, gp.local_faces(torch.from_numpy(u)))
     tl = gp.local_cells(torch.from_numpy(th)).clone()
     if grad:
@@ -280,3 +281,32 @@ def test_reordered_part_follows_an_internal_order(name):
         for src, off, cnt in q.recv:
             sent = dict(new[src].send)[q.rank]
             assert np.array_equal(new[src].owned_ids[sent], q.halo_ids[off:off + cnt])
+
+
+def test_more_ranks_than_cells_gives_empty_parts():
+    # 24 cells over 30 ranks: six ranks own nothing and hold no halo; every
+    # other part is one cell, all rim (no interior), its halo two rings deep
+    mesh = MESHES["tiny"]()
+    fc = np.asarray(mesh.face_cells, dtype=np.int64)
+    part = partition_graph(mesh.n_cells, fc, 30)
+    parts = build_parts(mesh.n_cells, fc, part, 30)
+    assert len(parts) == 30
+    sizes = [p.n_owned for p in parts]
+    assert sorted(sizes) == [0] * 6 + [1] * 24
+    for gp in parts:
+        if gp.n_owned == 0:
+            assert gp.n_cells == 0 and gp.face_ids.shape == (0,) and not gp.send and not gp.recv
+            assert gp.split() == (None, [(0, 0)], (0, 0))
+        else:
+            assert gp.n_interior == 0 and gp.split()[0] is None
+    # trailing empty ranks are kept when the world is given
+    assert len(build_parts(mesh.n_cells, fc, np.zeros(mesh.n_cells, np.int32), 3)) == 3
+
+
+@pytest.mark.parametrize("world", [7, 30])
+def test_gloo_tiny_parts_equal_whole_mesh_oracle(world):
+    # parts of a few cells (no interior) and empty parts: the exchange-first
+    # path, and ranks that only pass messages on
+    mesh, th, u, dt = _case("tiny")
+    got = _gloo("tiny", world, "superbee", 3, 2)
+    assert np.array_equal(got, oracle.step(mesh, "superbee", 3, dt, 2, u, th))
