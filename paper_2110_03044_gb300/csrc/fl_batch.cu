@@ -87,9 +87,16 @@ __global__ void __launch_bounds__(TX *BTY, 4)
   }
 }
 
-// FP32: items are (box, run + runs-per-plane x z chunk) of the flat tile
+// FP32: items are (box, run + runs-per-plane x z chunk) of the flat tile.
+// FL_FLAT_MINB: CTAs of 256 threads the register budget must allow per SM.
+// 4 caps the tile at 64 registers without spills (74 uncapped): 8 CTAs of 4
+// warps per SM instead of 6, and the 64-box van Leer step ran 1.18 ms
+// against 1.50 (5: 48 registers with spills, 1.26 ms).
+#ifndef FL_FLAT_MINB
+#define FL_FLAT_MINB 4
+#endif
 template <int LIM, int SEED, int CX>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, FL_FLAT_MINB)
     k_batch_flat(const SParams<float> *__restrict__ params, const int2 *__restrict__ items,
                  int n_items, unsigned *counter) {
   __shared__ int s_next;
