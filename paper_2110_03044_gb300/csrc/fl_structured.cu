@@ -68,8 +68,11 @@ __global__ void __launch_bounds__(TX *TY, CODES ? FL_CODES_MINB
 #ifndef FL_FP32_REG
 #define FL_FP32_REG 1
 #endif
+#ifndef FL_REG_MINB
+#define FL_REG_MINB 3
+#endif
 template <int LIM, int SEED>
-__global__ void __launch_bounds__(TX *8, 3) k_struct_stage_reg(const SParams<float> p) {
+__global__ void __launch_bounds__(TX *8, FL_REG_MINB) k_struct_stage_reg(const SParams<float> p) {
   stage_tile_reg<LIM, SEED>(p, blockIdx.x);
 }
 
