@@ -1072,6 +1072,27 @@ def run_config_decomp(args):
             "face_updates_per_s": rate, "ms_per_step": ms / args.steps,
             "launches_per_stage": 3 if overlap and slab.nz_local > 4 else 1}
         ro.close()
+    # pencils over (y, z): ranks in a near-square grid; one rank exchanges
+    # with itself through the pack and unpack kernels
+    from paper_2110_03044_gb300.decomp import Pencil, PencilRollout
+    py = max(d for d in range(1, int(ws_ ** 0.5) + 1) if ws_ % d == 0)
+    grid = (py, ws_ // py)
+    pencil = Pencil(dims, rank, grid)
+    for overlap in (True, False):
+        ro = PencilRollout(pencil, wl.mesh.h, ug, lim, torch.float64, wl.dt, overlap=overlap)
+        tl = ro.local_field(thg)
+        ro.step(tl, 3, args.warmup)
+        torch.cuda.synchronize()
+        if ws_ > 1:
+            dist.barrier()
+        e0.record()
+        ro.step(tl, 3, args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        rate, ms = whole_job_rate(F * 3 * args.steps / ws_, e0.elapsed_time(e1), device="cuda")
+        out["pencil_" + ("overlap" if overlap else "exchange_first")] = {
+            "face_updates_per_s": rate, "ms_per_step": ms / args.steps, "grid": list(grid)}
+        ro.close()
     if ws_ == 1:
         m = fl.Mesh.structured(n, n, n, *wl.mesh.h)
         ws, nb = fl.workspace_for(m, torch.float64, 3)

@@ -201,6 +201,17 @@ fl_status fl_halo_pack(const fl_mesh *mesh, fl_dtype dtype, const void *src,
                        const int32_t *index, int64_t n, void *dst, void *stream);
 
 /*
+ * The receiving side of fl_halo_pack: dst[index[i]] = src[i] for i < n (src:
+ * [n] device; index: int32 [n] device, distinct entries; dst: a cell field
+ * [n_cells] of the mesh, device, not overlapping src): the received halo
+ * values of a decomposition whose ghost cells are not one slice (the rows
+ * of a pencil).  An index outside [0, n_cells) records FL_EINDEX in the
+ * mesh's status word and writes nothing for it.  One kernel launch.
+ */
+fl_status fl_halo_unpack(const fl_mesh *mesh, fl_dtype dtype, const void *src,
+                         const int32_t *index, int64_t n, void *dst, void *stream);
+
+/*
  * Internal numbering of a mesh created with FL_RENUMBER (host arrays):
  * cell_perm[user_cell] = internal cell, face_perm[user_face] = internal face,
  * face_flip[user_face] = 1 if the internal face has the opposite orientation
@@ -362,6 +373,20 @@ fl_status fl_step_rk_stage_planes(const fl_mesh *mesh, fl_limiter limiter, fl_dt
                                   const void *w_f, void *stream);
 
 /*
+ * fl_step_rk_stage over the rows [y_begin, y_end) of the planes [z_begin,
+ * z_end) of a structured mesh only (the cells i + nx (j + ny k) with j and k
+ * in range, every i): a pencil decomposition's interior and rim boxes.  Each
+ * updated cell reads x within two cells of itself along each axis (periodic).
+ * Arguments as fl_step_rk_stage_planes; FL_EINVAL unless 0 <= y_begin <=
+ * y_end <= ny and 0 <= z_begin <= z_end <= nz (an empty box runs nothing).
+ * One kernel launch.
+ */
+fl_status fl_step_rk_stage_box(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                               int rk_order, int stage, double dt, int y_begin, int y_end,
+                               int z_begin, int z_end, const void *theta_n, const void *x, void *y,
+                               const void *u_f, const void *w_f, void *stream);
+
+/*
  * fl_step_rk_stage over the owned cells [c_begin, c_end) of a local mesh
  * (fl_mesh_create_local) only; each end is 0, n_interior or n_owned, so a
  * partitioned run can update its interior cells while the halo exchange is
@@ -497,6 +522,18 @@ fl_status fl_step_rk_stage_adjoint_planes(const fl_mesh *mesh, fl_limiter limite
                                           int z_begin, int z_end, const void *x, const void *mu,
                                           const void *lam_a, const void *lam_b, void *out,
                                           const void *u_f, const void *w_f, void *stream);
+
+/*
+ * fl_step_rk_stage_adjoint over the rows [y_begin, y_end) of the planes
+ * [z_begin, z_end) of a structured mesh only: an updated cell reads mu
+ * within two cells and x within three cells of itself along each axis.
+ * Errors as fl_step_rk_stage_box.
+ */
+fl_status fl_step_rk_stage_adjoint_box(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype,
+                                       int rk_order, int stage, double dt, int y_begin,
+                                       int y_end, int z_begin, int z_end, const void *x,
+                                       const void *mu, const void *lam_a, const void *lam_b,
+                                       void *out, const void *u_f, const void *w_f, void *stream);
 
 /*
  * fl_step_rk_stage_adjoint over the owned cells [c_begin, c_end) of a local

@@ -35,15 +35,16 @@ ABI_SYMBOLS = [
     "fl_mesh_create_weighted",
     "fl_mesh_permutation", "fl_mesh_info", "fl_mesh_status", "fl_mesh_destroy",
     "fl_mesh_to_internal", "fl_mesh_to_user", "fl_mesh_create_local", "fl_mesh_local_info",
-    "fl_halo_pack",
+    "fl_halo_pack", "fl_halo_unpack",
     "fl_conv_limited_apply",
     "fl_face_selection", "fl_workspace_size", "fl_step_rk", "fl_step_rk_modulated",
     "fl_step_rk_noalloc", "fl_step_rk_blocked", "fl_step_rk_stage", "fl_step_rk_stage_planes",
-    "fl_step_rk_stage_cells",
+    "fl_step_rk_stage_cells", "fl_step_rk_stage_box",
     "fl_velocity_prescale",
     "fl_conv_limited_adjoint",
     "fl_adjoint_workspace_size", "fl_step_rk_adjoint", "fl_step_rk_stage_adjoint",
-    "fl_step_rk_stage_adjoint_planes", "fl_step_rk_stage_adjoint_cells", "fl_step_rk_checkpointed",
+    "fl_step_rk_stage_adjoint_planes", "fl_step_rk_stage_adjoint_cells",
+    "fl_step_rk_stage_adjoint_box", "fl_step_rk_checkpointed",
     "fl_step_rk_adjoint_from_checkpoints", "fl_batch_create",
     "fl_batch_workspace_size", "fl_batch_step_rk", "fl_batch_tiling", "fl_batch_set_tiling",
     "fl_batch_destroy",
@@ -94,6 +95,7 @@ def lib():
             "fl_mesh_create_local": (I, [I64, I64, I64, I64, P, P, P, P, P, U, PP]),
             "fl_mesh_local_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
             "fl_halo_pack": (I, [P, I, P, P, I64, P, P]),
+            "fl_halo_unpack": (I, [P, I, P, P, I64, P, P]),
             "fl_mesh_permutation": (I, [P, P, P, P]),
             "fl_mesh_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                  ctypes.POINTER(I)]),
@@ -111,6 +113,7 @@ def lib():
             "fl_step_rk_stage": (I, [P, I, I, I, I, D, P, P, P, P, P, P]),
             "fl_step_rk_stage_planes": (I, [P, I, I, I, I, D, I, I, P, P, P, P, P, P]),
             "fl_step_rk_stage_cells": (I, [P, I, I, I, I, D, I64, I64, P, P, P, P, P, P]),
+            "fl_step_rk_stage_box": (I, [P, I, I, I, I, D, I, I, I, I, P, P, P, P, P, P]),
             "fl_velocity_prescale": (I, [P, I, D, P, P, P]),
             "fl_conv_limited_adjoint": (I, [P, I, I, P, P, P, P, P]),
             "fl_adjoint_workspace_size": (I, [P, I, I, I64, I64, ctypes.POINTER(SZ)]),
@@ -119,6 +122,8 @@ def lib():
                                                     P]),
             "fl_step_rk_stage_adjoint_cells": (I, [P, I, I, I, I, D, I64, I64, P, P, P, P, P, P,
                                                    P, P]),
+            "fl_step_rk_stage_adjoint_box": (I, [P, I, I, I, I, D, I, I, I, I, P, P, P, P, P, P,
+                                                 P, P]),
             "fl_step_rk_adjoint": (I, [P, I, I, I, D, I64, I64, P, P, P, P, P, SZ, P]),
             "fl_step_rk_checkpointed": (I, [P, I, I, I, D, I64, I64, P, P, P, SZ, P]),
             "fl_step_rk_adjoint_from_checkpoints": (I, [P, I, I, I, D, I64, I64, P, P, P, P,
@@ -267,6 +272,13 @@ def fl_halo_pack(mesh, dtype, src, index, n, dst, stream=None):
                               _stream(stream)))
 
 
+def fl_halo_unpack(mesh, dtype, src, index, n, dst, stream=None):
+    """dst[index[i]] = src[i] for i < n (device arrays; index int32)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_halo_unpack(mesh, c, _fptr(src, c), _ptr(index), int(n), _fptr(dst, c),
+                                _stream(stream)))
+
+
 def fl_mesh_create_weighted(n_cells, face_cells, face_normals, face_areas, cell_volumes,
                             face_distances, flags=0):
     import numpy as np
@@ -387,6 +399,17 @@ def fl_step_rk_stage_cells(mesh, limiter, dtype, rk_order, stage, dt, c_begin, c
                                         _stream(stream)))
 
 
+def fl_step_rk_stage_box(mesh, limiter, dtype, rk_order, stage, dt, y_begin, y_end, z_begin,
+                         z_end, theta_n, x, y, u_f, w_f=None, stream=None):
+    """fl_step_rk_stage over the rows [y_begin, y_end) of the planes
+    [z_begin, z_end) of a structured mesh only (see fl.h)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_stage_box(mesh, _lim(limiter), c, int(rk_order), int(stage),
+                                      float(dt), int(y_begin), int(y_end), int(z_begin),
+                                      int(z_end), _fptr(theta_n, c), _fptr(x, c), _fptr(y, c),
+                                      _fptr(u_f, c), _fptr(w_f, c), _stream(stream)))
+
+
 def fl_velocity_prescale(mesh, dtype, dt, u_f, w_f, stream=None):
     """w_f = dt (A/V) u_f, the velocity fl_step_rk_stage takes in FP64."""
     c = dtype_code(dtype)
@@ -466,6 +489,18 @@ def fl_step_rk_stage_adjoint_cells(mesh, limiter, dtype, rk_order, stage, dt, c_
         mesh, _lim(limiter), c, int(rk_order), int(stage), float(dt), int(c_begin), int(c_end),
         _fptr(x, c), _fptr(mu, c), _fptr(lam_a, c), _fptr(lam_b, c), _fptr(out, c),
         _fptr(u_f, c), _fptr(w_f, c), _stream(stream)))
+
+
+def fl_step_rk_stage_adjoint_box(mesh, limiter, dtype, rk_order, stage, dt, y_begin, y_end,
+                                 z_begin, z_end, x, mu, lam_a, lam_b, out, u_f, w_f=None,
+                                 stream=None):
+    """fl_step_rk_stage_adjoint over the rows [y_begin, y_end) of the planes
+    [z_begin, z_end) of a structured mesh only (see fl.h)."""
+    c = dtype_code(dtype)
+    _check(lib().fl_step_rk_stage_adjoint_box(
+        mesh, _lim(limiter), c, int(rk_order), int(stage), float(dt), int(y_begin), int(y_end),
+        int(z_begin), int(z_end), _fptr(x, c), _fptr(mu, c), _fptr(lam_a, c), _fptr(lam_b, c),
+        _fptr(out, c), _fptr(u_f, c), _fptr(w_f, c), _stream(stream)))
 
 
 def fl_adjoint_workspace_size(mesh, dtype, rk_order, nsteps, checkpoint_every):

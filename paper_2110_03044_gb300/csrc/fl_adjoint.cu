@@ -38,6 +38,7 @@ fl_status check_buffer(const void *p, size_t bytes, const char *name);
 fl_status check_mesh(const fl_mesh *m);
 fl_status check_enums(int lim, fl_dtype dt);
 fl_status check_cell_range(const fl_mesh *m, int64_t c_begin, int64_t c_end);
+fl_status check_box(const fl_mesh *m, int y_begin, int y_end, int z_begin, int z_end);
 
 namespace {
 
@@ -65,6 +66,7 @@ struct AParams {
   int bare;      // 1: out = R'^T mu only
   int tiles_x, tiles_y, zchunk;
   int zlo, zhi;  // the tiles cover planes [zlo, zhi)
+  int ylo, yhi;  // and rows [ylo, yhi) of them
 };
 
 // asynchronous global -> shared copy of one element (no register staging)
@@ -293,14 +295,14 @@ __global__ void __launch_bounds__(TX *TY, FL_ADJ_MINB) k_struct_adjoint(const AP
   bid /= p.tiles_x;
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
-  const int x0 = bx * TX, y0 = by * TY;
+  const int x0 = bx * TX, y0 = p.ylo + by * TY;
   const int z0 = p.zlo + bz * p.zchunk;
   const int z1 = min(z0 + p.zchunk, p.zhi);
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (tid < TX + 6) s_wx[tid] = wrapi(x0 - 3 + tid, nx);
   if (tid < TY + 6) s_wy[tid] = wrapi(y0 - 3 + tid, ny);
   __syncthreads();
-  const bool valid = (x0 + tx < nx) && (y0 + ty < ny);
+  const bool valid = (x0 + tx < nx) && (y0 + ty < p.yhi);
   // wrap table index w <-> coordinate x0-3+w
   const long long col = (long long)s_wx[tx + 3] + (long long)nx * s_wy[ty + 3];
 
@@ -536,14 +538,14 @@ __global__ void __launch_bounds__(TX *TY, 4) k_struct_adjoint_codes(const AParam
   bid /= p.tiles_x;
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
-  const int x0 = bx * TX, y0 = by * TY;
+  const int x0 = bx * TX, y0 = p.ylo + by * TY;
   const int z0 = p.zlo + bz * p.zchunk;
   const int z1 = min(z0 + p.zchunk, p.zhi);
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   if (tid < TX + 6) s_wx[tid] = wrapi(x0 - 3 + tid, nx);
   if (tid < TY + 6) s_wy[tid] = wrapi(y0 - 3 + tid, ny);
   __syncthreads();
-  const bool valid = (x0 + tx < nx) && (y0 + ty < ny);
+  const bool valid = (x0 + tx < nx) && (y0 + ty < p.yhi);
   // addressing: 64-bit base pointers per stream, 32-bit offsets (cell and
   // plane offsets are below n_cells < 2^31): one wide multiply-add a load
   const unsigned plane = (unsigned)p.plane;
@@ -751,7 +753,9 @@ cudaError_t run_adj_t(const fl_mesh *m, int lim, const AdjArgs &s, cudaStream_t 
   p.bare = s.bare;
   p.codes = static_cast<const unsigned char *>(s.codes);
   p.tiles_x = (m->nx + TX - 1) / TX;
-  p.tiles_y = (m->ny + TY - 1) / TY;
+  p.ylo = s.yhi < 0 ? 0 : s.ylo;
+  p.yhi = s.yhi < 0 ? m->ny : s.yhi;
+  p.tiles_y = (p.yhi - p.ylo + TY - 1) / TY;
   p.zlo = s.zhi < 0 ? 0 : s.zlo;
   p.zhi = s.zhi < 0 ? m->nz : s.zhi;
   const int nzr = p.zhi - p.zlo;
@@ -837,8 +841,8 @@ using namespace fl;
 // cell): the shared body of fl_step_rk_stage_adjoint and its _planes and
 // _cells forms.
 static fl_status stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
-                                      int stage, double dtime, int zlo, int zhi, int64_t clo,
-                                      int64_t chi, const void *x, const void *mu,
+                                      int stage, double dtime, int ylo, int yhi, int zlo, int zhi,
+                                      int64_t clo, int64_t chi, const void *x, const void *mu,
                                       const void *lam_a, const void *lam_b, void *out,
                                       const void *u_f, const void *w_f, void *stream) {
   FL_TRY(check_mesh(m));
@@ -869,11 +873,15 @@ static fl_status stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_dtype
         return fail(FL_EINVAL, "out overlaps x or mu (the stage reads their neighbours)");
     }
   }
-  if (m->C == 0 || (zhi >= 0 && zhi == zlo) || (chi >= 0 && chi == clo)) return FL_OK;
+  if (m->C == 0 || (zhi >= 0 && zhi == zlo) || (yhi >= 0 && yhi == ylo) ||
+      (chi >= 0 && chi == clo))
+    return FL_OK;
   if (m->kind == 1) FL_TRY(unstruct_adjoint_prepare(m));
   AdjArgs a;
   a.zlo = zlo;
   a.zhi = zhi;
+  a.ylo = ylo;
+  a.yhi = yhi;
   a.clo = clo;
   a.chi = chi;
   a.x = x;
@@ -930,8 +938,8 @@ fl_status fl_step_rk_stage_adjoint(const fl_mesh *m, fl_limiter lim, fl_dtype dt
                                    int stage, double dtime, const void *x, const void *mu,
                                    const void *lam_a, const void *lam_b, void *out,
                                    const void *u_f, const void *w_f, void *stream) {
-  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, 0, -1, 0, -1, x, mu, lam_a, lam_b,
-                              out, u_f, w_f, stream);
+  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, 0, -1, 0, -1, 0, -1, x, mu, lam_a,
+                              lam_b, out, u_f, w_f, stream);
 }
 
 fl_status fl_step_rk_stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
@@ -940,11 +948,20 @@ fl_status fl_step_rk_stage_adjoint_planes(const fl_mesh *m, fl_limiter lim, fl_d
                                           const void *lam_b, void *out, const void *u_f,
                                           const void *w_f, void *stream) {
   FL_TRY(check_mesh(m));
-  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "a plane range needs a structured mesh");
-  if (z_begin < 0 || z_end < z_begin || z_end > m->nz)
-    return fail(FL_EINVAL, "plane range [%d, %d) is not inside [0, %d]", z_begin, z_end, m->nz);
-  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, z_begin, z_end, 0, -1, x, mu, lam_a,
-                              lam_b, out, u_f, w_f, stream);
+  FL_TRY(check_box(m, 0, m->ny, z_begin, z_end));
+  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, 0, -1, z_begin, z_end, 0, -1, x, mu,
+                              lam_a, lam_b, out, u_f, w_f, stream);
+}
+
+fl_status fl_step_rk_stage_adjoint_box(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
+                                       int stage, double dtime, int y_begin, int y_end,
+                                       int z_begin, int z_end, const void *x, const void *mu,
+                                       const void *lam_a, const void *lam_b, void *out,
+                                       const void *u_f, const void *w_f, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_box(m, y_begin, y_end, z_begin, z_end));
+  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, y_begin, y_end, z_begin, z_end, 0, -1,
+                              x, mu, lam_a, lam_b, out, u_f, w_f, stream);
 }
 
 fl_status fl_step_rk_stage_adjoint_cells(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk,
@@ -954,8 +971,8 @@ fl_status fl_step_rk_stage_adjoint_cells(const fl_mesh *m, fl_limiter lim, fl_dt
                                          const void *w_f, void *stream) {
   FL_TRY(check_mesh(m));
   FL_TRY(check_cell_range(m, c_begin, c_end));
-  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, 0, -1, c_begin, c_end, x, mu, lam_a,
-                              lam_b, out, u_f, w_f, stream);
+  return stage_adjoint_planes(m, lim, dt, rk, stage, dtime, 0, -1, 0, -1, c_begin, c_end, x, mu,
+                              lam_a, lam_b, out, u_f, w_f, stream);
 }
 
 fl_status fl_adjoint_workspace_size(const fl_mesh *m, fl_dtype dt, int rk, int64_t nsteps,

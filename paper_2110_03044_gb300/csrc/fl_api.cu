@@ -174,6 +174,16 @@ fl_status check_mesh(const fl_mesh *m) {
   return FL_OK;
 }
 
+// the rows [y_begin, y_end) of the planes [z_begin, z_end) of a structured mesh
+fl_status check_box(const fl_mesh *m, int y_begin, int y_end, int z_begin, int z_end) {
+  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "a plane or row range needs a structured mesh");
+  if (z_begin < 0 || z_end < z_begin || z_end > m->nz)
+    return fail(FL_EINVAL, "plane range [%d, %d) is not inside [0, %d]", z_begin, z_end, m->nz);
+  if (y_begin < 0 || y_end < y_begin || y_end > m->ny)
+    return fail(FL_EINVAL, "row range [%d, %d) is not inside [0, %d]", y_begin, y_end, m->ny);
+  return FL_OK;
+}
+
 // the cell ranges a stage of a local face-based mesh runs on: block-aligned
 fl_status check_cell_range(const fl_mesh *m, int64_t c_begin, int64_t c_end) {
   if (m->kind != 1) return fail(FL_EUNSUPPORTED, "a cell range needs a face-based mesh");
@@ -468,9 +478,9 @@ fl_status step_rk_impl(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, do
 // shared body of fl_step_rk_stage, fl_step_rk_stage_planes and
 // fl_step_rk_stage_cells.
 static fl_status stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
-                              double dtime, int zlo, int zhi, int64_t clo, int64_t chi,
-                              const void *theta_n, const void *x, void *y, const void *u_f,
-                              const void *w_f, void *stream) {
+                              double dtime, int ylo, int yhi, int zlo, int zhi, int64_t clo,
+                              int64_t chi, const void *theta_n, const void *x, void *y,
+                              const void *u_f, const void *w_f, void *stream) {
   FL_TRY(check_mesh(m));
   FL_TRY(check_enums(lim, dt));
   if (rk != 1 && rk != 3) return fail(FL_EINVAL, "rk_order must be 1 or 3");
@@ -490,10 +500,14 @@ static fl_status stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int
   const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
   if (m->C > 0 && xb < yb + cb && yb < xb + cb)
     return fail(FL_EINVAL, "x and y overlap (a stage reads neighbours of x while writing y)");
-  if (m->C == 0 || (zhi >= 0 && zhi == zlo) || (chi >= 0 && chi == clo)) return FL_OK;
+  if (m->C == 0 || (zhi >= 0 && zhi == zlo) || (yhi >= 0 && yhi == ylo) ||
+      (chi >= 0 && chi == clo))
+    return FL_OK;
   StageArgs s;
   s.zlo = zlo;
   s.zhi = zhi;
+  s.ylo = ylo;
+  s.yhi = yhi;
   s.clo = clo;
   s.chi = chi;
   s.x = x;
@@ -569,8 +583,8 @@ fl_status fl_velocity_prescale(const fl_mesh *m, fl_dtype dt, double dtime, cons
 fl_status fl_step_rk_stage(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
                            double dtime, const void *theta_n, const void *x, void *y,
                            const void *u_f, const void *w_f, void *stream) {
-  return stage_planes(m, lim, dt, rk, stage, dtime, 0, -1, 0, -1, theta_n, x, y, u_f, w_f,
-                      stream);
+  return stage_planes(m, lim, dt, rk, stage, dtime, 0, -1, 0, -1, 0, -1, theta_n, x, y, u_f,
+                      w_f, stream);
 }
 
 fl_status fl_step_rk_stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
@@ -578,11 +592,19 @@ fl_status fl_step_rk_stage_planes(const fl_mesh *m, fl_limiter lim, fl_dtype dt,
                                   const void *x, void *y, const void *u_f, const void *w_f,
                                   void *stream) {
   FL_TRY(check_mesh(m));
-  if (m->kind != 0) return fail(FL_EUNSUPPORTED, "a plane range needs a structured mesh");
-  if (z_begin < 0 || z_end < z_begin || z_end > m->nz)
-    return fail(FL_EINVAL, "plane range [%d, %d) is not inside [0, %d]", z_begin, z_end, m->nz);
-  return stage_planes(m, lim, dt, rk, stage, dtime, z_begin, z_end, 0, -1, theta_n, x, y, u_f,
-                      w_f, stream);
+  FL_TRY(check_box(m, 0, m->ny, z_begin, z_end));
+  return stage_planes(m, lim, dt, rk, stage, dtime, 0, -1, z_begin, z_end, 0, -1, theta_n, x, y,
+                      u_f, w_f, stream);
+}
+
+fl_status fl_step_rk_stage_box(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
+                               double dtime, int y_begin, int y_end, int z_begin, int z_end,
+                               const void *theta_n, const void *x, void *y, const void *u_f,
+                               const void *w_f, void *stream) {
+  FL_TRY(check_mesh(m));
+  FL_TRY(check_box(m, y_begin, y_end, z_begin, z_end));
+  return stage_planes(m, lim, dt, rk, stage, dtime, y_begin, y_end, z_begin, z_end, 0, -1,
+                      theta_n, x, y, u_f, w_f, stream);
 }
 
 fl_status fl_step_rk_stage_cells(const fl_mesh *m, fl_limiter lim, fl_dtype dt, int rk, int stage,
@@ -591,8 +613,8 @@ fl_status fl_step_rk_stage_cells(const fl_mesh *m, fl_limiter lim, fl_dtype dt, 
                                  const void *w_f, void *stream) {
   FL_TRY(check_mesh(m));
   FL_TRY(check_cell_range(m, c_begin, c_end));
-  return stage_planes(m, lim, dt, rk, stage, dtime, 0, -1, c_begin, c_end, theta_n, x, y, u_f,
-                      w_f, stream);
+  return stage_planes(m, lim, dt, rk, stage, dtime, 0, -1, 0, -1, c_begin, c_end, theta_n, x, y,
+                      u_f, w_f, stream);
 }
 
 fl_status fl_mesh_local_info(const fl_mesh *m, int64_t *n_owned, int64_t *n_interior) {

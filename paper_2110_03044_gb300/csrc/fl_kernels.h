@@ -21,6 +21,7 @@ struct StageArgs {
   void *codes = nullptr;  // FP64 pre-scaled stages: branch code per face out (or null)
   int seed = 0;
   int zlo = 0, zhi = -1;  // structured meshes: update planes [zlo, zhi) only (zhi < 0: all)
+  int ylo = 0, yhi = -1;  // ... and rows [ylo, yhi) of them (yhi < 0: all)
   // face-based local meshes: update cells [clo, chi) only (chi < 0: every
   // owned cell); a stage takes 0, n_interior or n_owned as either end
   int64_t clo = 0, chi = -1;
@@ -76,6 +77,7 @@ struct AdjArgs {
   double e1 = 0.0, e2 = 0.0, b = 1.0, dt = 0.0;
   int bare = 0;
   int zlo = 0, zhi = -1;  // structured meshes: update planes [zlo, zhi) only (zhi < 0: all)
+  int ylo = 0, yhi = -1;  // ... and rows [ylo, yhi) of them (yhi < 0: all)
   // face-based local meshes: update cells [clo, chi) only (chi < 0: every
   // owned cell); a stage takes 0, n_interior or n_owned as either end
   int64_t clo = 0, chi = -1;

@@ -1,6 +1,6 @@
 // fl_order.cu -- field order conversions of renumbered face-based meshes
-// (fl_mesh_to_internal / fl_mesh_to_user), and the halo gather of a
-// partitioned mesh (fl_halo_pack).
+// (fl_mesh_to_internal / fl_mesh_to_user), and the halo gather and scatter
+// of a decomposed run (fl_halo_pack / fl_halo_unpack).
 //
 // FL_RENUMBER relabels cells and faces (permutations P_c, P_f) so that the
 // stage kernels read compact blocks; the compute calls then work on fields
@@ -88,9 +88,55 @@ __global__ void k_halo_pack(const T *__restrict__ src, const int32_t *__restrict
   }
 }
 
+// dst[index[i]] = src[i] for index[i] in [0, n_dst); an index outside
+// records FL_EINDEX and writes nothing
+template <class T>
+__global__ void k_halo_unpack(const T *__restrict__ src, const int32_t *__restrict__ index,
+                              long long n, long long n_dst, T *__restrict__ dst, int *status) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long j = index[i];
+    if (j < 0 || j >= n_dst) {
+      fl::record_status(status, (int)FL_EINDEX);
+      continue;
+    }
+    dst[j] = src[i];
+  }
+}
+
 }  // namespace
 
 extern "C" {
+
+fl_status fl_halo_unpack(const fl_mesh *mesh, fl_dtype dtype, const void *src,
+                         const int32_t *index, int64_t n, void *dst, void *stream) {
+  using namespace fl;
+  fl_status st = check_mesh(mesh);
+  if (st != FL_OK) return st;
+  if (dtype != FL_F32 && dtype != FL_F64) return fail(FL_EINVAL, "unknown dtype %d", (int)dtype);
+  if (n < 0) return fail(FL_EINVAL, "n < 0");
+  if (n == 0) return FL_OK;
+  const size_t es = dsize(dtype);
+  if ((st = check_buffer(src, (size_t)n * es, "src")) != FL_OK) return st;
+  if ((st = check_buffer(index, (size_t)n * sizeof(int32_t), "index")) != FL_OK) return st;
+  if ((st = check_buffer(dst, (size_t)mesh->C * es, "dst")) != FL_OK) return st;
+  const char *s0 = static_cast<const char *>(src), *d0 = static_cast<const char *>(dst);
+  const size_t sb = (size_t)n * es, db = (size_t)mesh->C * es;
+  if (s0 < d0 + db && d0 < s0 + sb) return fail(FL_EINVAL, "src and dst overlap");
+  cudaStream_t s = as_stream(stream);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  if (dtype == FL_F64)
+    k_halo_unpack<double><<<(unsigned)blocks, 256, 0, s>>>(
+        static_cast<const double *>(src), index, n, mesh->C, static_cast<double *>(dst),
+        mesh->status);
+  else
+    k_halo_unpack<float><<<(unsigned)blocks, 256, 0, s>>>(
+        static_cast<const float *>(src), index, n, mesh->C, static_cast<float *>(dst),
+        mesh->status);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FL_OK : cuda_fail(e, "halo unpack kernel");
+}
 
 fl_status fl_halo_pack(const fl_mesh *mesh, fl_dtype dtype, const void *src, const int32_t *index,
                        int64_t n, void *dst, void *stream) {

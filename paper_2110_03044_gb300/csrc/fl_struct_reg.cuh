@@ -49,12 +49,12 @@ __device__ __forceinline__ void stage_tile_reg(const SParams<float> &p, int tile
   bid /= p.tiles_x;
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
-  const int x0 = bx * TX, y0 = by * (int)blockDim.y;
+  const int x0 = bx * TX, y0 = p.ylo + by * (int)blockDim.y;
   const int z0 = p.zlo + bz * p.zchunk;
   const int z1 = min(z0 + p.zchunk, min(p.nz, p.zhi));
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int last = min(TX, nx - x0) - 1;  // last lane inside the mesh
-  const bool valid = lane <= last && y0 + ty < ny;
+  const bool valid = lane <= last && y0 + ty < min(ny, p.yhi);
   const int x = x0 + min(lane, last);
   const int y = min(y0 + ty, ny - 1);
   const bool need_x = p.act_x, need_y = p.act_y, need_z = p.act_z;

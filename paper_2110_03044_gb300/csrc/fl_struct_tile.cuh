@@ -32,6 +32,7 @@ struct SParams {
   // the tiles cover planes [zlo, min(zhi, nz)) (a plane range of a
   // decomposed mesh; the whole mesh by default)
   int zlo = 0, zhi = 1 << 30;
+  int ylo = 0, yhi = 1 << 30;  // and rows [ylo, min(yhi, ny)) of them
 };
 
 enum { SEED_PLAIN = 0, SEED_COMBINE = 1, SEED_APPLY = 2 };
@@ -102,7 +103,7 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
   bid /= p.tiles_x;
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
-  const int x0 = bx * TX, y0 = by * TY;
+  const int x0 = bx * TX, y0 = p.ylo + by * TY;
   const int z0 = p.zlo + bz * p.zchunk;
   const int z1 = min(z0 + p.zchunk, min(p.nz, p.zhi));
   const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -113,7 +114,7 @@ __device__ __forceinline__ void stage_tile(const SParams<T> &p, int tile) {
   if (tid < TY + 4) s_wy[tid] = wrap(y0 - 2 + tid, ny);
   __syncthreads();
 
-  const bool valid = (x0 + tx < nx) && (y0 + ty < ny);
+  const bool valid = (x0 + tx < nx) && (y0 + ty < min(ny, p.yhi));
   // Addressing: one 64-bit base pointer per stream and 32-bit element
   // offsets (every cell or plane offset is below n_cells < 2^31), so that a
   // load costs one wide multiply-add rather than 64-bit index arithmetic

@@ -78,6 +78,7 @@ struct TParams {
   int tiles_x, tiles_y, zchunk;
   int *status;
   int zlo, zhi;  // the tiles cover planes [zlo, zhi)
+  int ylo, yhi;  // and rows [ylo, yhi) of them
 };
 
 __device__ __forceinline__ uint32_t sa(const void *p) {
@@ -174,12 +175,12 @@ __global__ void __launch_bounds__(LANES *(TY + 1), MINB) k_struct_stage_tma(
   bid /= p.tiles_x;
   const int by = bid % p.tiles_y;
   const int bz = bid / p.tiles_y;
-  const int x0 = bx * TX, y0 = by * TY;
+  const int x0 = bx * TX, y0 = p.ylo + by * TY;
   const int z0 = p.zlo + bz * p.zchunk;
   const int z1 = min(z0 + p.zchunk, p.zhi);
   const int L = z1 - z0;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
-  const int w = min(TX, nx - x0), h = min(TY, ny - y0);  // w is a multiple of 4
+  const int w = min(TX, nx - x0), h = min(TY, p.yhi - y0);  // w is a multiple of 4
   const bool az = p.act_z;
   auto parity = [](int q) { return (uint32_t)((q / RING) & 1); };
 
@@ -523,7 +524,9 @@ cudaError_t struct_stage_tma(const fl_mesh *m, int lim, const StageArgs &s, cuda
   p.a = blend_a<float>(s.a, s.b);
   p.b = (float)s.b;
   p.tiles_x = (nx + TX - 1) / TX;
-  p.tiles_y = (ny + TY - 1) / TY;
+  p.ylo = s.yhi < 0 ? 0 : s.ylo;
+  p.yhi = s.yhi < 0 ? ny : s.yhi;
+  p.tiles_y = (p.yhi - p.ylo + TY - 1) / TY;
   const long long cols = (long long)p.tiles_x * p.tiles_y;
   // whole waves of co-resident CTAs (the occupancy query needs the kernel's
   // dynamic shared-memory limit raised first)

@@ -158,7 +158,9 @@ cudaError_t run_stage_t(const fl_mesh *m, int lim, const StageArgs &s, cudaStrea
   p.a = blend_a<T>(s.a, s.b);
   p.b = (T)s.b;
   p.tiles_x = (m->nx + TX - 1) / TX;
-  p.tiles_y = (m->ny + STY - 1) / STY;
+  p.ylo = s.yhi < 0 ? 0 : s.ylo;
+  p.yhi = s.yhi < 0 ? m->ny : s.yhi;
+  p.tiles_y = (p.yhi - p.ylo + STY - 1) / STY;
   // z chunks: whole waves of co-resident CTAs (the occupancy of the PLAIN
   // kernel stands for all variants: same block, similar registers)
   const long long cols = (long long)p.tiles_x * p.tiles_y;

@@ -228,9 +228,9 @@ REACH = 2
 
 
 def exchange_and_run(slab, transport, x, run, overlap=True, reach=None):
-    """Exchange x's halo and run ``run(lo, hi)`` over every owned local range
-    of the domain ``slab`` (a Slab: plane ranges; a partition.GraphPart: cell
-    ranges).  With ``overlap`` the part that reads no halo value (for a slab,
+    """Exchange x's halo and run ``run(*r)`` over every owned local range r
+    of the domain ``slab`` (a Slab: plane ranges (z0, z1); a Pencil: boxes
+    (y0, y1, z0, z1); a partition.GraphPart: cell ranges (c0, c1)).  With ``overlap`` the part that reads no halo value (for a slab,
     the planes at least ``reach`` planes from both cuts) runs while the
     exchange is in flight and the rest after it ends; without it (or when
     there is no such interior) everything runs after the exchange."""
@@ -242,8 +242,8 @@ def exchange_and_run(slab, transport, x, run, overlap=True, reach=None):
     pending = start_exchange(transport, slab, x)
     run(*interior)
     pending.wait()
-    for lo, hi in rims:
-        run(lo, hi)
+    for r in rims:
+        run(*r)
 
 
 def step_rk(slab: Slab, transport, stage: StageFn, rk_order: int, nsteps: int, theta, a, b=None,
@@ -257,7 +257,7 @@ def step_rk(slab: Slab, transport, stage: StageFn, rk_order: int, nsteps: int, t
     runs each stage's interior while its input's halo is exchanged.  Returns
     the local field that holds the result (``theta``)."""
     def run_stage(s, thn, x, y):
-        exchange_and_run(slab, transport, x, lambda z0, z1: stage(s, thn, x, y, z0, z1), overlap)
+        exchange_and_run(slab, transport, x, lambda *r: stage(s, thn, x, y, *r), overlap)
 
     if rk_order == 1:
         cur, nxt = theta, a
@@ -294,7 +294,7 @@ def gradient_rk(slab: Slab, transport, stage: StageFn, stage_adjoint: StageAdjoi
         raise ValueError("rk_order must be 1 or 3")
 
     def run_stage(s, thn, x, y, keep):
-        exchange_and_run(slab, transport, x, lambda z0, z1: stage(s, thn, x, y, z0, z1), overlap)
+        exchange_and_run(slab, transport, x, lambda *r: stage(s, thn, x, y, *r), overlap)
         keep.append(x.clone())  # x with its exchanged ghost planes (a stage never writes x)
 
     def fwd_step(th, keep):
@@ -311,7 +311,7 @@ def gradient_rk(slab: Slab, transport, stage: StageFn, stage_adjoint: StageAdjoi
 
     def adj(s, x, mu, lam_a, lam_b, out):
         exchange_and_run(slab, transport, mu,
-                         lambda z0, z1: stage_adjoint(s, x, mu, lam_a, lam_b, out, z0, z1), overlap)
+                         lambda *r: stage_adjoint(s, x, mu, lam_a, lam_b, out, *r), overlap)
 
     # forward, storing a checkpoint every `every` steps
     checkpoints = []
@@ -340,6 +340,211 @@ def gradient_rk(slab: Slab, transport, stage: StageFn, stage_adjoint: StageAdjoi
             adj(0, x0, m1, m2, lam, out)
             lam = out
     return lam
+
+
+# ------------------------------------------------------------------ pencils
+@dataclass
+class Pencil:
+    """Rank ``rank`` of a py x pz grid of ranks (grid = (py, pz), rank =
+    ry + py rz) owns the rows [ylo, yhi) of the planes [zlo, zhi) of a
+    periodic nx x ny x nz box and holds them, with ``halo`` ghost rows and
+    planes on each side, as a local structured mesh of nx x (nyl + 2 halo) x
+    (nzl + 2 halo) cells.  The stencil runs along the axes only, so the
+    corner ghost cells (ghost rows of ghost planes) are never read and never
+    exchanged.  Pencils cut the halo volume of slabs when there are many
+    ranks, and allow more ranks than nz / halo."""
+    dims: tuple
+    rank: int
+    grid: tuple
+    halo: int = HALO
+
+    def __post_init__(self):
+        nx, ny, nz = self.dims
+        py, pz = self.grid
+        if py < 1 or pz < 1 or not 0 <= self.rank < py * pz:
+            raise ValueError("bad rank %d of a %d x %d grid" % (self.rank, py, pz))
+        if ny < 2 or nz < 2:
+            raise ValueError("a pencil decomposition needs ny >= 2 and nz >= 2")
+        self.ry, self.rz = self.rank % py, self.rank // py
+        self.ylo, self.yhi = ny * self.ry // py, ny * (self.ry + 1) // py
+        self.zlo, self.zhi = nz * self.rz // pz, nz * (self.rz + 1) // pz
+        if min(self.yhi - self.ylo, self.zhi - self.zlo) < self.halo:
+            raise ValueError("rank %d would own fewer rows or planes than the halo of %d"
+                             % (self.rank, self.halo))
+        self.y_down = (self.ry - 1) % py + py * self.rz
+        self.y_up = (self.ry + 1) % py + py * self.rz
+        self.z_down = self.ry + py * ((self.rz - 1) % pz)
+        self.z_up = self.ry + py * ((self.rz + 1) % pz)
+        self._idx = None
+
+    @property
+    def world(self) -> int:
+        return self.grid[0] * self.grid[1]
+
+    @property
+    def nyl(self) -> int:
+        return self.yhi - self.ylo
+
+    @property
+    def nzl(self) -> int:
+        return self.zhi - self.zlo
+
+    @property
+    def local_dims(self) -> tuple:
+        return (self.dims[0], self.nyl + 2 * self.halo, self.nzl + 2 * self.halo)
+
+    def _local_ids(self):
+        """Global flat id of every local cell (ghost rows and planes wrap)."""
+        import numpy as np
+        nx, ny, nz = self.dims
+        h = self.halo
+        rows = (self.ylo - h + np.arange(self.nyl + 2 * h)) % ny
+        planes = (self.zlo - h + np.arange(self.nzl + 2 * h)) % nz
+        return ((planes[:, None, None] * ny + rows[None, :, None]) * nx
+                + np.arange(nx)[None, None, :]).ravel()
+
+    def _box(self, j0, j1, k0, k1):
+        """Local flat ids of the rows [j0, j1) of the local planes [k0, k1)."""
+        import numpy as np
+        nx, nyl2 = self.dims[0], self.nyl + 2 * self.halo
+        k = np.arange(k0, k1)[:, None, None]
+        j = np.arange(j0, j1)[None, :, None]
+        return ((k * nyl2 + j) * nx + np.arange(nx)[None, None, :]).ravel().astype(np.int32)
+
+    def exchange_lists(self):
+        """(send, recv) index lists of the four messages: for each of
+        'y_down', 'y_up', 'z_down', 'z_up', the local ids this rank sends to
+        that neighbour and the local ids of the ghost cells it fills from it.
+        The two ends of a message list their cells in the same (plane, row,
+        column) order."""
+        if self._idx is None:
+            h, nyl, nzl = self.halo, self.nyl, self.nzl
+            own_z, own_y = (h, h + nzl), (h, h + nyl)
+            send = {"y_down": self._box(h, 2 * h, *own_z),
+                    "y_up": self._box(nyl, nyl + h, *own_z),
+                    "z_down": self._box(*own_y, h, 2 * h),
+                    "z_up": self._box(*own_y, nzl, nzl + h)}
+            recv = {"y_down": self._box(0, h, *own_z),
+                    "y_up": self._box(h + nyl, nyl + 2 * h, *own_z),
+                    "z_down": self._box(*own_y, 0, h),
+                    "z_up": self._box(*own_y, h + nzl, nzl + 2 * h)}
+            self._idx = (send, recv)
+        return self._idx
+
+    def owned(self, x):
+        """The owned box of a local cell field (a strided view)."""
+        h = self.halo
+        v = x.view(self.nzl + 2 * h, self.nyl + 2 * h, self.dims[0])
+        return v[h:h + self.nzl, h:h + self.nyl, :]
+
+    def split(self, reach=None):
+        """(interior, rims, whole) boxes (y0, y1, z0, z1) of the owned cells:
+        the interior at least ``reach`` rows and planes from every cut, the
+        rims the rest (two slabs of planes and two bands of rows)."""
+        reach = REACH if reach is None else reach
+        h, nyl, nzl = self.halo, self.nyl, self.nzl
+        whole = (h, h + nyl, h, h + nzl)
+        if nyl <= 2 * reach or nzl <= 2 * reach:
+            return None, [whole], whole
+        zi = (h + reach, h + nzl - reach)
+        interior = (h + reach, h + nyl - reach) + zi
+        rims = [(h, h + nyl, h, h + reach), (h, h + nyl, h + nzl - reach, h + nzl),
+                (h, h + reach) + zi, (h + nyl - reach, h + nyl) + zi]
+        return interior, rims, whole
+
+    def check_adjoint(self):
+        if self.halo < HALO_ADJOINT:
+            raise ValueError("the reverse sweep needs a halo of %d" % HALO_ADJOINT)
+
+    def local_cells(self, glob):
+        """A local cell field cut from a global one (torch tensor or numpy
+        array, flat, c = i + nx (j + ny k))."""
+        return glob[_index(glob, self._local_ids())]
+
+    def local_faces(self, glob, n_axes):
+        """The local face field: each of the ``n_axes`` face blocks cut like
+        a cell field."""
+        import numpy as np
+        C = self.dims[0] * self.dims[1] * self.dims[2]
+        ids = self._local_ids()
+        return glob[_index(glob, np.concatenate([ids + b * C for b in range(n_axes)]))]
+
+
+def _index(x, ids):
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            return torch.as_tensor(ids, dtype=torch.long, device=x.device)
+    except ImportError:
+        pass
+    return ids
+
+
+class PencilTransport:
+    """The four-neighbour exchange of a Pencil through the default
+    torch.distributed process group (or, for one rank in a direction, a
+    copy of its own cells).  ``pack(x, index, out)`` gathers x[index] into
+    out and ``unpack(buf, index, x)`` scatters buf into x[index]: the
+    library's fl_halo_pack / fl_halo_unpack for device fields (see
+    PencilRollout), index copies on the host."""
+
+    TAGS = {"y_down": 31, "y_up": 32, "z_down": 33, "z_up": 34}
+    OPP = {"y_down": "y_up", "y_up": "y_down", "z_down": "z_up", "z_up": "z_down"}
+
+    def __init__(self, pack=None, unpack=None):
+        self.pack = pack or (lambda x, idx, out: out.copy_(x[idx.long()]))
+        self.unpack = unpack or (lambda buf, idx, x: x.index_copy_(0, idx.long(), buf))
+        self._dev = {}
+
+    def exchange(self, pc: Pencil, x):
+        self.start(pc, x).wait()
+
+    def _lists(self, pc, x):
+        import torch
+        key = (id(pc), x.dtype, x.device)
+        if key not in self._dev:
+            send, recv = pc.exchange_lists()
+            mk = lambda a: torch.as_tensor(a, dtype=torch.int32, device=x.device)  # noqa: E731
+            self._dev[key] = ({d: mk(a) for d, a in send.items()},
+                              {d: mk(a) for d, a in recv.items()},
+                              {d: torch.empty(a.shape[0], dtype=x.dtype, device=x.device)
+                               for d, a in send.items()},
+                              {d: torch.empty(a.shape[0], dtype=x.dtype, device=x.device)
+                               for d, a in recv.items()})
+        return self._dev[key]
+
+    def start(self, pc: Pencil, x):
+        import torch.distributed as dist
+        send, recv, sbuf, rbuf = self._lists(pc, x)
+        peer = {"y_down": pc.y_down, "y_up": pc.y_up, "z_down": pc.z_down, "z_up": pc.z_up}
+        for d in send:
+            self.pack(x, send[d], sbuf[d])
+        ops, local = [], []
+        for d in send:
+            if peer[d] == pc.rank:
+                local.append(d)  # one rank in this direction: its own cells
+                continue
+            # a message to the neighbour on side d fills its ghost cells on the
+            # opposite side, and carries the tag of that side
+            ops.append(dist.P2POp(dist.isend, sbuf[d], peer[d], tag=self.TAGS[self.OPP[d]]))
+            ops.append(dist.P2POp(dist.irecv, rbuf[d], peer[d], tag=self.TAGS[d]))
+        reqs = dist.batch_isend_irecv(ops) if ops else []
+        return _PencilPending(self, x, recv, sbuf, rbuf, local, reqs)
+
+
+class _PencilPending:
+    def __init__(self, tr, x, recv, sbuf, rbuf, local, reqs):
+        self.args = (tr, x, recv, sbuf, rbuf, local, reqs)
+
+    def wait(self):
+        tr, x, recv, sbuf, rbuf, local, reqs = self.args
+        for r in reqs:
+            r.wait()
+        for d in recv:
+            # a direction served by this rank itself: its ghost cells on side
+            # d are its own cells sent towards the opposite side
+            src = sbuf[PencilTransport.OPP[d]] if d in local else rbuf[d]
+            tr.unpack(src, recv[d], x)
 
 
 class SlabRollout:
@@ -439,3 +644,71 @@ def _max_abs_faces(u):
     from .replicas import max_over_ranks
     ws = torch.empty(max(fl_reduce_workspace_size(), 1), dtype=torch.uint8, device=u.device)
     return max_over_ranks(fl_reduce_max_abs(u.dtype, u, u.numel(), ws), u.device)
+
+
+class PencilRollout(SlabRollout):
+    """SlabRollout for a Pencil: the library's box-range stage kernels
+    (fl_step_rk_stage_box / fl_step_rk_stage_adjoint_box) on the interior
+    and the four rim boxes, and the four-neighbour exchange with its halo
+    gathered and scattered by fl_halo_pack / fl_halo_unpack."""
+
+    def __init__(self, pencil: Pencil, h, u_global, limiter, dtype, dt, transport=None,
+                 overlap=True):
+        from . import fl_halo_pack, fl_halo_unpack
+        super().__init__(pencil, h, u_global, limiter, dtype, dt,
+                         transport=transport or _no_transport, overlap=overlap)
+        if transport is None:
+            hdl = self.mesh.handle
+            self.transport = PencilTransport(
+                pack=lambda x, idx, out: fl_halo_pack(hdl, x.dtype, x, idx, idx.numel(), out),
+                unpack=lambda buf, idx, x: fl_halo_unpack(hdl, x.dtype, buf, idx, idx.numel(),
+                                                          x))
+
+    def _stage_fn(self, rk_order):
+        from . import fl_step_rk_stage_box
+
+        def stage(s, thn, x, y, y0, y1, z0, z1):
+            fl_step_rk_stage_box(self.mesh.handle, self.limiter, self.dtype, rk_order, s, self.dt,
+                                 y0, y1, z0, z1, thn, x, y, self.u, self.w)
+
+        return stage
+
+    def gradient(self, theta_local, lam_T_local, rk_order, nsteps, every):
+        """dJ/dtheta_0 on this rank's pencil (see gradient_rk); the pencil
+        needs a halo of HALO_ADJOINT."""
+        import torch
+
+        from . import fl_step_rk_stage_adjoint_box
+
+        def stage_adjoint(s, x, mu, lam_a, lam_b, out, y0, y1, z0, z1):
+            fl_step_rk_stage_adjoint_box(self.mesh.handle, self.limiter, self.dtype, rk_order, s,
+                                         self.dt, y0, y1, z0, z1, x, mu, lam_a, lam_b, out,
+                                         self.u, self.w)
+
+        return gradient_rk(self.slab, self.transport, self._stage_fn(rk_order), stage_adjoint,
+                           rk_order, nsteps, every, theta_local, lam_T_local,
+                           lambda: torch.empty_like(theta_local), overlap=self.overlap)
+
+    def mass(self, theta_local):
+        """sum_c V_c theta_c over the whole mesh: fl_reduce_mass over this
+        rank's owned box (copied into one block), summed over the ranks."""
+        import torch
+
+        from . import Mesh, fl_reduce_mass, fl_reduce_workspace_size
+        from .replicas import sum_over_ranks
+        pc = self.slab
+        if self._owned_mesh is None:
+            self._owned_mesh = Mesh.structured(pc.dims[0], pc.nyl, pc.nzl, *self.h)
+        ws = torch.empty(max(fl_reduce_workspace_size(), 1), dtype=torch.uint8,
+                         device=theta_local.device)
+        own = fl_reduce_mass(self._owned_mesh.handle, self.dtype,
+                             pc.owned(theta_local).contiguous().view(-1), ws)
+        return sum_over_ranks(own, theta_local.device)
+
+
+class _NoTransport:
+    def exchange(self, slab, x):
+        raise RuntimeError("no transport")
+
+
+_no_transport = _NoTransport()

@@ -268,3 +268,147 @@ def test_gloo_decomposed_gradient_equals_one_rank(world, lim, rk):
     tgt = np.random.default_rng(7).normal(size=mesh.n_cells)
     _, g_ref = oracle.gradient(mesh, lim, rk, dt, nsteps, u, th, tgt)
     assert np.max(np.abs(got - g_ref)) <= 1e-12 * np.max(np.abs(g_ref))
+
+
+# ------------------------------------------------------------------ pencils
+@pytest.mark.parametrize("grid", [(1, 1), (2, 2), (3, 1), (1, 3), (2, 3)])
+def test_pencils_tile_the_box_and_pair_their_messages(grid):
+    from paper_2110_03044_gb300.decomp import Pencil, PencilTransport
+    dims = (5, 9, 12)
+    py, pz = grid
+    pcs = [Pencil(dims, r, grid) for r in range(py * pz)]
+    owner = np.full(dims[0] * dims[1] * dims[2], -1)
+    for pc in pcs:
+        ids = pc._local_ids().reshape(pc.nzl + 2 * pc.halo, pc.nyl + 2 * pc.halo, dims[0])
+        own = ids[pc.halo:pc.halo + pc.nzl, pc.halo:pc.halo + pc.nyl].ravel()
+        assert (owner[own] == -1).all()
+        owner[own] = pc.rank
+    assert (owner >= 0).all()
+    # a message's two ends name the same global cells in the same order
+    for pc in pcs:
+        send, recv = pc.exchange_lists()
+        gid = pc._local_ids()
+        peer = {"y_down": pc.y_down, "y_up": pc.y_up, "z_down": pc.z_down, "z_up": pc.z_up}
+        for d, idx in recv.items():
+            q = pcs[peer[d]]
+            sent = q.exchange_lists()[0][PencilTransport.OPP[d]]
+            assert np.array_equal(q._local_ids()[sent], gid[idx])
+        # the ghost cells filled are exactly the side halos of the owned box
+        h = pc.halo
+        n_side = h * dims[0] * (pc.nyl + pc.nzl) * 2
+        assert sum(v.shape[0] for v in recv.values()) == n_side
+    interior, rims, whole = pcs[-1].split()
+    cells = lambda b: (b[1] - b[0]) * (b[3] - b[2])  # noqa: E731
+    if interior is not None:
+        assert cells(interior) + sum(cells(r) for r in rims) == cells(whole)
+
+
+def _pencil_rank(rank, grid, lim, rk, nsteps, transport, overlap=True, grad=False):
+    from paper_2110_03044_gb300.decomp import HALO_ADJOINT, Pencil
+    dims, h, mesh, th, u, dt = _case()
+    pc = Pencil(dims, rank, grid, halo=HALO_ADJOINT if grad else 2)
+    lm = oracle.OracleMesh(W.structured_mesh(*pc.local_dims, *h))
+    ul = pc.local_faces(torch.from_numpy(u), 3).numpy()
+    nx, nyl2 = dims[0], pc.nyl + 2 * pc.halo
+
+    def box(y, y0, y1, z0, z1):
+        return y.view(-1, nyl2, nx)[z0:z1, y0:y1, :]
+
+    def stage(s, thn, x, y, y0, y1, z0, z1):
+        xn = x.numpy()
+        t = xn if thn is None else thn.numpy()
+        full = torch.from_numpy(oracle.stage(lm, lim, rk, s, dt, t, xn, ul))
+        box(y, y0, y1, z0, z1).copy_(box(full, y0, y1, z0, z1))
+
+    bs = {0: 1.0, 1: 0.25, 2: 2.0 / 3.0}
+
+    def stage_adjoint(s, x, mu, lam_a, lam_b, out, y0, y1, z0, z1):
+        m = mu.numpy()
+        yv = bs[s if rk == 3 else 0] * (m + dt * oracle.rhs_adjoint(lm, lim, x.numpy(), ul, m))
+        if rk == 3 and s == 0:
+            yv = yv + 0.75 * lam_a.numpy() + (1.0 / 3.0) * lam_b.numpy()
+        box(out, y0, y1, z0, z1).copy_(box(torch.from_numpy(yv), y0, y1, z0, z1))
+
+    tl = pc.local_cells(torch.from_numpy(th)).clone()
+    # scratch: a huge finite sentinel rather than NaN.  The pencil's corner
+    # ghost cells (ghost rows of ghost planes) are never exchanged: the
+    # stencil never reads them, but the oracle's upstream sum runs over all
+    # other faces of the upwind cell, orthogonal ones with weight 0, and
+    # 0 x NaN would be NaN; 0 x 1e200 is 0, and any weighted read of an
+    # unwritten cell still blows up
+    nan = lambda: torch.full_like(tl, 1e200)  # noqa: E731
+    if grad:
+        from paper_2110_03044_gb300.decomp import gradient_rk
+        tgt = np.random.default_rng(7).normal(size=mesh.n_cells)
+        thT = oracle.step(mesh, lim, rk, dt, nsteps, u, th)
+        lam = pc.local_cells(torch.from_numpy(thT - tgt)).clone()
+        out = gradient_rk(pc, transport, stage, stage_adjoint, rk, nsteps, 2, tl, lam, nan,
+                          overlap=overlap)
+    else:
+        out = step_rk(pc, transport, stage, rk, nsteps, tl, nan(), nan(), overlap=overlap)
+    ids = pc._local_ids().reshape(pc.nzl + 2 * pc.halo, nyl2, nx)
+    own = ids[pc.halo:pc.halo + pc.nzl, pc.halo:pc.halo + pc.nyl].ravel()
+    return own, pc.owned(out).reshape(-1).numpy().copy()
+
+
+def _pencil_worker(rank, grid, port, lim, rk, nsteps, overlap, grad, q):
+    import torch.distributed as dist
+
+    from paper_2110_03044_gb300.decomp import PencilTransport
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=grid[0] * grid[1])
+    try:
+        q.put((rank,) + _pencil_rank(rank, grid, lim, rk, nsteps, PencilTransport(), overlap,
+                                     grad))
+    finally:
+        dist.destroy_process_group()
+
+
+def _pencil_gloo(grid, lim, rk, nsteps, overlap=True, grad=False):
+    world = grid[0] * grid[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_pencil_worker,
+                         args=(r, grid, port, lim, rk, nsteps, overlap, grad, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    dims = _case()[0]
+    got = np.full(dims[0] * dims[1] * dims[2], np.nan)
+    for _, ids, vals in out:
+        got[ids] = vals
+    return got
+
+
+@pytest.mark.parametrize("grid,overlap", [((2, 2), True), ((3, 2), True), ((2, 1), False)])
+@pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1)])
+def test_gloo_pencil_rollout_equals_one_rank(grid, overlap, lim, rk):
+    from paper_2110_03044_gb300.decomp import PencilTransport
+    dims, h, mesh, th, u, dt = _case()
+    own, vals = _pencil_rank(0, (1, 1), lim, rk, 3, PencilTransport(), overlap=False)
+    one = np.empty(mesh.n_cells)
+    one[own] = vals
+    got = _pencil_gloo(grid, lim, rk, 3, overlap)
+    assert np.array_equal(got, one)  # bit for bit
+    ref = oracle.step(mesh, lim, rk, dt, 3, u, th)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1)])
+def test_gloo_pencil_gradient_equals_one_rank(lim, rk):
+    from paper_2110_03044_gb300.decomp import PencilTransport
+    dims, h, mesh, th, u, dt = _case()
+    own, vals = _pencil_rank(0, (1, 1), lim, rk, 3, PencilTransport(), overlap=False, grad=True)
+    one = np.empty(mesh.n_cells)
+    one[own] = vals
+    got = _pencil_gloo((2, 2), lim, rk, 3, grad=True)
+    assert np.array_equal(got, one)  # bit for bit
+    tgt = np.random.default_rng(7).normal(size=mesh.n_cells)
+    _, g_ref = oracle.gradient(mesh, lim, rk, dt, 3, u, th, tgt)
+    assert np.max(np.abs(got - g_ref)) <= 1e-12 * np.max(np.abs(g_ref))

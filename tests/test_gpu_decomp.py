@@ -372,3 +372,183 @@ def test_decomposed_diagnostics(fl):
     want = math.fsum((th * mesh.volumes).tolist())
     assert abs(math.fsum(shares) - want) <= 1e-13 * max(1.0, abs(want))
     assert max(maxima) == float(np.max(np.abs(u)))
+
+
+# ------------------------------------------------------------------ pencils
+class ThreadPencilTransport:
+    """The four-neighbour exchange of W pencils run by host threads on one
+    GPU: each ghost region is gathered from the neighbour's field with
+    fl_halo_pack on the neighbour's mesh and scattered with fl_halo_unpack,
+    between two barriers."""
+
+    def __init__(self, fl, world):
+        self.fl = fl
+        self.reg = [None] * world
+        self.fields = [None] * world
+        self.bar = threading.Barrier(world)
+        self.idx = {}
+
+    def _dev(self, key, a):
+        if key not in self.idx:
+            self.idx[key] = torch.as_tensor(a, dtype=torch.int32, device="cuda")
+        return self.idx[key]
+
+    def exchange(self, pc, x):
+        from paper_2110_03044_gb300.decomp import PencilTransport
+        self.fields[pc.rank] = x
+        self.bar.wait()
+        peer = {"y_down": pc.y_down, "y_up": pc.y_up, "z_down": pc.z_down, "z_up": pc.z_up}
+        recv = pc.exchange_lists()[1]
+        for d, ridx in recv.items():
+            q = self.reg[peer[d]]
+            sidx = q.slab.exchange_lists()[0][PencilTransport.OPP[d]]
+            tmp = torch.empty(ridx.shape[0], dtype=x.dtype, device="cuda")
+            self.fl.fl_halo_pack(q.mesh.handle, x.dtype, self.fields[peer[d]],
+                                 self._dev(("s", peer[d], d), sidx), sidx.shape[0], tmp)
+            self.fl.fl_halo_unpack(self.reg[pc.rank].mesh.handle, x.dtype, tmp,
+                                   self._dev(("r", pc.rank, d), ridx), ridx.shape[0], x)
+        self.bar.wait()
+
+
+def _pencils(fl, grid, dims, h, th, u, lim, dtype, rk, dt, nsteps, lam_T=None, every=2):
+    from paper_2110_03044_gb300.decomp import HALO_ADJOINT, Pencil, PencilRollout
+    world = grid[0] * grid[1]
+    tr = ThreadPencilTransport(fl, world)
+    ug = torch.tensor(u, device="cuda")
+    halo = HALO_ADJOINT if lam_T is not None else 2
+    ros = [PencilRollout(Pencil(dims, r, grid, halo=halo), h, ug, lim, dtype, dt, transport=tr)
+           for r in range(world)]
+    for r, ro in enumerate(ros):
+        tr.reg[r] = ro
+    out = [None] * world
+    err = []
+
+    def rank(r):
+        try:
+            torch.cuda.set_device(0)
+            ro = ros[r]
+            tl = ro.local_field(torch.tensor(th, device="cuda"))
+            if lam_T is None:
+                res = ro.step(tl, rk, nsteps)
+            else:
+                res = ro.gradient(tl, ro.local_field(torch.tensor(lam_T, device="cuda")), rk,
+                                  nsteps, every)
+            torch.cuda.synchronize()
+            pc = ro.slab
+            ids = pc._local_ids().reshape(pc.nzl + 2 * pc.halo, pc.nyl + 2 * pc.halo, dims[0])
+            own = ids[pc.halo:pc.halo + pc.nzl, pc.halo:pc.halo + pc.nyl].ravel()
+            out[r] = (own, pc.owned(res).reshape(-1).cpu())
+        except BaseException as e:  # noqa: BLE001 -- reported below
+            err.append(e)
+            tr.bar.abort()
+
+    ts = [threading.Thread(target=rank, args=(r,)) for r in range(world)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for ro in ros:
+        ro.close()
+    if err:
+        raise err[0]
+    got = torch.empty(dims[0] * dims[1] * dims[2], dtype=dtype)
+    for own, vals in out:
+        got[torch.as_tensor(own)] = vals
+    return got
+
+
+@pytest.mark.parametrize("grid", [(2, 2), (3, 2), (1, 4)])
+@pytest.mark.parametrize("dims,dtype", [((40, 12, 24), torch.float64),
+                                        ((40, 12, 24), torch.float32),
+                                        ((128, 16, 20), torch.float32)])
+@pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1), ("smart", 3)])
+def test_pencil_rollout_equals_whole_mesh_bitwise(fl, grid, dims, dtype, lim, rk):
+    h = tuple(0.7 / d for d in dims)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(25)
+    th = rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3)
+    u = 0.3 * W.mixed_sign_velocity(mesh.n_faces, 26)
+    dt = 0.3 * min(h) / np.max(np.abs(u)) / 3
+    got = _pencils(fl, grid, dims, h, th, u, lim, dtype, rk, dt, 3)
+    m = fl.Mesh.structured(*dims, *h)
+    ref = torch.tensor(th, dtype=dtype, device="cuda")
+    fl.step_rk(m, lim, ref, torch.tensor(u, dtype=dtype, device="cuda"), dt, 3, rk_order=rk)
+    m.close()
+    assert torch.equal(got, ref.cpu())
+
+
+@pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1)])
+def test_pencil_gradient_matches_whole_mesh(fl, lim, rk):
+    import oracle
+    dims = (24, 14, 18)
+    h = tuple(0.7 / d for d in dims)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(27)
+    th = rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3)
+    u = 0.3 * W.mixed_sign_velocity(mesh.n_faces, 28)
+    dt = 0.3 * min(h) / np.max(np.abs(u)) / 3
+    nsteps, every = 4, 2
+    tgt = rng.normal(size=mesh.n_cells)
+    thT = oracle.step(mesh, lim, rk, dt, nsteps, u, th)
+    got = _pencils(fl, (2, 2), dims, h, th, u, lim, torch.float64, rk, dt, nsteps, thT - tgt,
+                   every).numpy()
+    one = _pencils(fl, (1, 1), dims, h, th, u, lim, torch.float64, rk, dt, nsteps, thT - tgt,
+                   every).numpy()
+    assert np.array_equal(got, one)
+    m = fl.Mesh.structured(*dims, *h)
+    nb = fl.fl_adjoint_workspace_size(m.handle, torch.float64, rk, nsteps, every)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    g = torch.empty(mesh.n_cells, dtype=torch.float64, device="cuda")
+    fl.fl_step_rk_adjoint(m.handle, lim, torch.float64, rk, dt, nsteps, every,
+                          torch.tensor(th, device="cuda"), torch.tensor(u, device="cuda"),
+                          torch.tensor(thT - tgt, device="cuda"), g, ws, nb)
+    m.close()
+    whole = g.cpu().numpy()
+    assert np.max(np.abs(got - whole)) <= 1e-12 * np.max(np.abs(whole))
+
+
+@pytest.mark.parametrize("dims,dtype,pre", [((40, 12, 23), torch.float64, True),
+                                            ((40, 12, 23), torch.float32, False),
+                                            ((128, 16, 21), torch.float32, False)])
+def test_stage_box_composes_and_leaves_other_cells(fl, dims, dtype, pre):
+    h = tuple(0.7 / d for d in dims)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(29)
+    nx, ny, nz = dims
+    th0 = torch.tensor(rng.uniform(-1, 1, mesh.n_cells), dtype=dtype, device="cuda")
+    thn = torch.tensor(rng.uniform(-1, 1, mesh.n_cells), dtype=dtype, device="cuda")
+    u = torch.tensor(0.3 * W.mixed_sign_velocity(mesh.n_faces, 30), dtype=dtype, device="cuda")
+    dt = 0.3 * min(h) / float(u.abs().max()) / 3
+    m = fl.Mesh.structured(*dims, *h)
+    w = None
+    if pre:
+        w = torch.empty_like(u)
+        fl.fl_velocity_prescale(m.handle, dtype, dt, u, w)
+    boxes = [(0, 5, 0, 7), (5, ny, 0, 7), (0, 3, 7, nz), (3, ny - 1, 7, nz), (ny - 1, ny, 7, nz)]
+    for s in range(3):
+        ref = torch.empty_like(th0)
+        fl.fl_step_rk_stage(m.handle, "smart", dtype, 3, s, dt, thn, th0, ref, u, w)
+        y = torch.full_like(th0, 4.5)
+        fl.fl_step_rk_stage_box(m.handle, "smart", dtype, 3, s, dt, *boxes[1], thn, th0, y, u, w)
+        torch.cuda.synchronize()
+        v, vr = y.view(nz, ny, nx), ref.view(nz, ny, nx)
+        assert torch.equal(v[0:7, 5:ny], vr[0:7, 5:ny])
+        assert bool((v[7:] == 4.5).all()) and bool((v[0:7, 0:5] == 4.5).all())
+        for b in boxes[:1] + boxes[2:]:
+            fl.fl_step_rk_stage_box(m.handle, "smart", dtype, 3, s, dt, *b, thn, th0, y, u, w)
+        assert torch.equal(y, ref)
+        # the adjoint box kernel composes the same way
+        mu = torch.sin(th0 * 3).contiguous()
+        oref = torch.empty_like(th0)
+        fl.fl_step_rk_stage_adjoint(m.handle, "smart", dtype, 3, s, dt, th0, mu, thn, th0, oref,
+                                    u)
+        out = torch.full_like(th0, -1.5)
+        for b in boxes:
+            fl.fl_step_rk_stage_adjoint_box(m.handle, "smart", dtype, 3, s, dt, *b, th0, mu, thn,
+                                            th0, out, u)
+        assert torch.equal(out, oref)
+    with pytest.raises(fl.FLError) as e:
+        fl.fl_step_rk_stage_box(m.handle, "smart", dtype, 3, 0, dt, 0, ny + 1, 0, 1, None, th0,
+                                torch.empty_like(th0), u, w)
+    assert e.value.status == fl.FL_EINVAL
+    m.close()
