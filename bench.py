@@ -42,9 +42,9 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 NCU_FP64_PIPE = {
     ("f64", "superbee", 256): (0.842, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
                                "profiles/k_struct_stage_traffic_tg256.md"),
-    ("f64", "vanleer", 256): (0.627, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
+    ("f64", "vanleer", 256): (0.626, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
                               "profiles/k_struct_stage_traffic_tg256.md"),
-    ("f64", "smart", 256): (0.818, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
+    ("f64", "smart", 256): (0.819, "sm__inst_executed_pipe_fp64, RK stage 2 launch, "
                             "profiles/k_struct_stage_traffic_tg256.md"),
 }
 
@@ -54,14 +54,14 @@ NCU_FP64_PIPE = {
 # FP64 superbee, RK stages 2-3 (65 % of the step's kernel time); FP32
 # superbee TMA kernel, RK stage 1.  Keyed by (dtype, limiter, n).
 NCU_TRAFFIC = {
-    ("f64", "superbee", 256): (808.4e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
+    ("f64", "superbee", 256): (808.2e6, "k_struct_stage<double, SUPERBEE, COMBINE, PRE>, "
                                "algorithmic 805.3e6 (48 B x 16.8M cells), "
                                "profiles/k_struct_stage_traffic_tg256.md"),
-    ("f64", "vanleer", 256): (832.5e6, "k_struct_stage<double, VANLEER, COMBINE, PRE>, "
+    ("f64", "vanleer", 256): (832.6e6, "k_struct_stage<double, VANLEER, COMBINE, PRE>, "
                               "algorithmic 805.3e6, profiles/k_struct_stage_traffic_tg256.md"),
-    ("f64", "smart", 256): (830.2e6, "k_struct_stage<double, SMART, COMBINE, PRE>, "
+    ("f64", "smart", 256): (829.6e6, "k_struct_stage<double, SMART, COMBINE, PRE>, "
                             "algorithmic 805.3e6, profiles/k_struct_stage_traffic_tg256.md"),
-    ("f32", "superbee", 256): (330.5e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
+    ("f32", "superbee", 256): (330.8e6, "k_struct_stage_tma<SUPERBEE, PLAIN>, "
                                "algorithmic 335.5e6 (20 B x 16.8M cells), "
                                "profiles/k_struct_stage_traffic_tg256.md"),
 }

@@ -139,6 +139,20 @@ def test_renumbered_local_meshes_match_the_oracle(fl, name, world, dtype):
     assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("name,world", [("hex", 3), ("prism", 2)])
+def test_renumbered_partitioned_gradient_matches_the_oracle(fl, name, world):
+    # the reverse sweep on renumbered local meshes (internal order, cell
+    # ranges of the interior and the rim) against the oracle's gradient
+    import oracle
+    mesh, th, u, dt = _case(name)
+    tgt = np.random.default_rng(10).normal(size=mesh.n_cells)
+    thT = oracle.step(mesh, "smart", 3, dt, 3, u, th)
+    got = _partitioned(fl, name, world, "smart", torch.float64, 3, 3, grad=thT - tgt,
+                       renumber=True).numpy()
+    _, g_ref = oracle.gradient(mesh, "smart", 3, dt, 3, u, th, tgt)
+    assert np.max(np.abs(got - g_ref)) <= 1e-11 * np.max(np.abs(g_ref))
+
+
 @pytest.mark.parametrize("name,world", [("hex", 3), ("tet", 2)])
 @pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1)])
 def test_partitioned_gradient_matches_whole_mesh_and_oracle(fl, name, world, lim, rk):
