@@ -226,6 +226,9 @@ HALO_ADJOINT = 3
 # forward stage reads x, the adjoint stage mu, within two planes.
 REACH = 2
 
+# Rows of a structured stage tile (the kernels' 32 x 8 tiles)
+TILE_ROWS = 8
+
 
 def exchange_and_run(slab, transport, x, run, overlap=True, reach=None):
     """Exchange x's halo and run ``run(*r)`` over every owned local range r
@@ -439,17 +442,22 @@ class Pencil:
 
     def split(self, reach=None):
         """(interior, rims, whole) boxes (y0, y1, z0, z1) of the owned cells:
-        the interior at least ``reach`` rows and planes from every cut, the
-        rims the rest (two slabs of planes and two bands of rows)."""
+        the interior at least ``reach`` planes and ``reach`` rows (a tile's 8
+        rows on pencils of more than 32 rows) from every cut, the rims the
+        rest (two slabs of planes and two bands of rows)."""
         reach = REACH if reach is None else reach
         h, nyl, nzl = self.halo, self.nyl, self.nzl
         whole = (h, h + nyl, h, h + nzl)
-        if nyl <= 2 * reach or nzl <= 2 * reach:
+        # the row bands are as tall as the stage tiles (8 rows) when the
+        # pencil is tall enough: a 2-row band would leave 6 of a tile's 8
+        # rows idle
+        ry = max(reach, TILE_ROWS) if nyl > 4 * TILE_ROWS else reach
+        if nyl <= 2 * ry or nzl <= 2 * reach:
             return None, [whole], whole
         zi = (h + reach, h + nzl - reach)
-        interior = (h + reach, h + nyl - reach) + zi
+        interior = (h + ry, h + nyl - ry) + zi
         rims = [(h, h + nyl, h, h + reach), (h, h + nyl, h + nzl - reach, h + nzl),
-                (h, h + reach) + zi, (h + nyl - reach, h + nyl) + zi]
+                (h, h + ry) + zi, (h + nyl - ry, h + nyl) + zi]
         return interior, rims, whole
 
     def check_adjoint(self):

@@ -412,3 +412,18 @@ def test_gloo_pencil_gradient_equals_one_rank(lim, rk):
     tgt = np.random.default_rng(7).normal(size=mesh.n_cells)
     _, g_ref = oracle.gradient(mesh, lim, rk, dt, 3, u, th, tgt)
     assert np.max(np.abs(got - g_ref)) <= 1e-12 * np.max(np.abs(g_ref))
+
+
+def test_tall_pencil_rims_are_tile_tall():
+    # a pencil of more than 32 rows keeps 8-row bands (whole stage tiles)
+    from paper_2110_03044_gb300.decomp import Pencil
+    pc = Pencil((8, 80, 20), 0, (1, 1))
+    interior, rims, whole = pc.split()
+    h = pc.halo
+    assert interior == (h + 8, h + 72, h + 2, h + 18)
+    cells = lambda b: (b[1] - b[0]) * (b[3] - b[2])  # noqa: E731
+    assert cells(interior) + sum(cells(r) for r in rims) == cells(whole)
+    covered = np.zeros((20 + 2 * h, 80 + 2 * h), dtype=int)
+    for y0, y1, z0, z1 in [interior] + rims:
+        covered[z0:z1, y0:y1] += 1
+    assert (covered[h:h + 20, h:h + 80] == 1).all() and covered.sum() == 80 * 20
