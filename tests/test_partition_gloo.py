@@ -226,10 +226,10 @@ def test_one_part_runs_without_exchange():
     assert np.array_equal(got, oracle.step(mesh, "superbee", 3, dt, 2, u, th))
 
 
-@pytest.mark.parametrize("name,world,overlap", [("hex", 2, True), ("hex", 3, True),
-                                                ("hex", 2, False), ("tet", 3, True),
-                                                ("prism", 2, True)])
-@pytest.mark.parametrize("lim,rk", [("superbee", 3), ("vanleer", 1), ("smart", 3)])
+@pytest.mark.parametrize("name,world,overlap,lim,rk", [
+    ("hex", 2, True, "superbee", 3), ("hex", 3, True, "smart", 3), ("hex", 2, False, "vanleer", 1),
+    ("hex", 3, False, "superbee", 3), ("tet", 3, True, "smart", 3), ("tet", 2, True, "vanleer", 1),
+    ("prism", 2, True, "superbee", 3), ("prism", 3, False, "smart", 3)])
 def test_gloo_partitioned_rollout_equals_whole_mesh_oracle(name, world, overlap, lim, rk):
     mesh, th, u, dt = _case(name)
     got = _gloo(name, world, lim, rk, 3, overlap)
