@@ -1,53 +1,51 @@
-"""Domain decomposition of a structured periodic box into z-slabs, with a
-halo exchange once per RK stage.
+"""Domain decomposition of a structured periodic box, z-slabs or (y, z)
+pencils, with a halo exchange once per RK stage.
 
 The paper's large runs split the mesh across processes and exchange the cells
 next to each cut before every operator application, overlapping the exchange
 with the interior's computation (Section 4, the MareNostrum 4 and
-Lomonosov-2 runs).  Here each rank (one GPU) owns a contiguous range of z
-planes [lo, hi) of an nx x ny x nz periodic box and holds it as its own
-structured mesh of nz_local + 2 HALO planes: HALO ghost planes below, the
-owned planes, HALO ghost planes above.  HALO = 2, because the upstream cell
-of a face is a second neighbour, so the update of a cell reads the planes
-within two of its own.
+Lomonosov-2 runs).  Here each rank (one GPU) owns a block of the box and
+holds it as its own structured mesh with HALO ghost layers on each cut
+side.  HALO = 2: the upstream cell of a face is a second neighbour, so the
+update of a cell reads the cells within two of its own along each axis.
 
-A stage runs the library's ordinary stage kernel (fl_step_rk_stage) on that
-local mesh as if it were periodic in z: every owned plane reads only planes
-inside the local array, so its result is the one the whole mesh would give,
-bit for bit (same inputs, same per-face arithmetic, same order of the six
-face terms of a cell); the ghost planes come out wrong (the local wrap) and
-are overwritten by the next exchange before anything reads them.  A face on
+Slab: rank r owns the z planes [lo, hi) and holds nz_local + 2 HALO planes.
+Planes are contiguous in the cell layout c = i + nx (j + ny k), so a halo is
+one contiguous slice: no packing kernel.  Pencil: rank ry + py rz of a py x
+pz grid owns a box of rows and planes; its ghost rows are strided, so each
+message is gathered and scattered through index lists by the library's
+fl_halo_pack / fl_halo_unpack.  The stencil runs along the axes only, so a
+pencil's corner ghost cells are never read and never exchanged.
+
+A stage updates only the owned cells, through the library's range-limited
+stage kernels (fl_step_rk_stage_planes for a slab's plane ranges,
+fl_step_rk_stage_box for a pencil's boxes), on the local mesh treated as
+periodic: every owned cell reads only cells inside the local array, so its
+result is the one the whole mesh gives, bit for bit (same inputs, same
+per-face arithmetic, same order of the six face terms of a cell).  A face on
 a cut is evaluated by both ranks from the same exchanged values with the
-same code, so both see the same flux and the scheme stays conservative.
-The face velocities of the local mesh (ghost planes included) are copied
-once from the global field at set-up.
+same code, so the scheme stays conservative.  The ghost layers of a stage
+result are never written; the next exchange fills them before anything reads
+them.  The face velocities of the local mesh are cut from the global field
+once at set-up.
 
-Exchange per stage input x: the HALO lowest owned planes go to the rank
-below (they become its upper ghost planes), the HALO highest owned planes to
-the rank above (its lower ghost planes).  Planes are contiguous in the cell
-layout c = i + nx (j + ny k), so a halo is one contiguous slice: no packing
-kernel is needed.  Messages go through torch.distributed point-to-point
-calls (NCCL between GPUs, gloo on the host), sends upward first and
-receives from below first on every rank, with tags, so that with two ranks
-(where the rank below is also the rank above) the messages pair correctly.
-A rank whose neighbours are itself (one rank) copies its own planes.
+Exchange: messages go through torch.distributed point-to-point calls (NCCL
+between GPUs, gloo on the host), posted together and tagged by the side they
+fill, so that two ranks that are each other's neighbours on both sides pair
+them correctly; a rank that is its own neighbour copies its own cells.
 
-The adjoint (gradient_rk) exchanges the adjoint field the same way before
-every adjoint stage; it reads the stage states three planes deep, so a slab
-for the reverse sweep keeps HALO_ADJOINT = 3 ghost planes.
+Overlap: the exchange of a stage input is started first; the owned cells at
+least two cells from every cut (the stage's reach) need no ghost cell and run
+while the halos travel; after the wait, the cells next to the cuts run.  With
+NCCL the messages travel on the communicator's stream while the interior
+kernel runs on the rank's stream, and the wait orders the rim kernels after
+them without blocking the host.
 
-Overlap (the paper's split runs hide the exchange behind the interior's
-work): a stage updates only the owned planes, through the library's
-plane-range stage (fl_step_rk_stage_planes).  The exchange of its input is
-started first; the owned planes at least two planes away from both cuts (the
-stage's reach) need no ghost plane and run while the halos travel; after the
-wait, the two planes next to each cut run.  With NCCL the messages travel on
-the communicator's own stream while the interior kernel runs on the rank's
-stream, and the wait orders the rim kernels after the messages without
-blocking the host.  The ghost planes of a stage result are never written:
-the next exchange fills them before anything reads them.  A slab of fewer
-than 2 x reach planes has no interior and runs its owned planes after the
-wait.
+The reverse sweep (gradient_rk) exchanges the adjoint field the same way
+before every adjoint stage; the adjoint stage reads the stage states three
+cells deep, so a slab or pencil for the reverse sweep keeps HALO_ADJOINT = 3
+ghost layers.  partition.py applies the same loops to graph partitions of
+face-based meshes.
 """
 from __future__ import annotations
 
