@@ -330,7 +330,8 @@ fl_status fl_workspace_size(const fl_mesh *mesh, fl_dtype dtype, int rk_order, s
  * aligned; its contents are scratch.  One fused kernel launch per stage;
  * a structured 1D line of 2 .. 5120 (FP64) or 10240 (FP32) cells runs all
  * nsteps in one launch, held in shared memory (one CTA below 16 cells, a
- * cluster of 8 CTAs from 16 cells on).
+ * cluster of 8 CTAs from 16 cells on, of 16 CTAs from 32 cells on where the
+ * GPU can place such a cluster).
  */
 fl_status fl_step_rk(const fl_mesh *mesh, fl_limiter limiter, fl_dtype dtype, int rk_order,
                      double dt, int64_t nsteps, void *theta, const void *u_f, void *workspace,

@@ -271,15 +271,20 @@ __global__ void __launch_bounds__(1024) k_line_resident(T *theta, const T *u, in
 // writes that reuse the buffer.  The per-face and per-cell arithmetic is
 // that of k_line_resident, operation for operation, so both give the same
 // bits.  Buffers use one stride for all CTAs (LM = ceil(n / LNC) + 4
-// entries) so that a neighbour's buffer sits at the same offset.
-constexpr int LNC = 8;
+// entries) so that a neighbour's buffer sits at the same offset.  The
+// cluster holds FL_LINE_NC CTAs (16, beyond the portable 8, where the GPU
+// can place such a cluster and the line has 2 cells per CTA), else 8.
+#ifndef FL_LINE_NC
+#define FL_LINE_NC 16
+#endif
 
 template <class T, int LIM>
-__global__ void __cluster_dims__(LNC, 1, 1) __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024)
     k_line_cluster(T *theta, const T *u, int n, int64_t nsteps, int rk, T c, int LM) {
   namespace cg = cooperative_groups;
   using F = FT<T>;
   cg::cluster_group cl = cg::this_cluster();
+  const int LNC = (int)cl.num_blocks();
   const int r = (int)cl.block_rank();
   const int lo = (int)(((long long)n * r) / LNC);
   const int hi = (int)(((long long)n * (r + 1)) / LNC);
@@ -356,23 +361,66 @@ __global__ void __cluster_dims__(LNC, 1, 1) __launch_bounds__(1024)
   cl.sync();
 }
 
+// Launch one cluster of nc CTAs (the cluster size given at launch)
+template <class T, int LIM>
+cudaError_t launch_line_cluster(int nc, T *th, const T *uu, int n, int64_t nsteps, int rk, T c,
+                                cudaStream_t st, bool probe_only, bool *fits) {
+  auto k = k_line_cluster<T, LIM>;
+  const int LM = (n + nc - 1) / nc + 4;
+  const size_t smem = 6 * sizeof(T) * (size_t)LM;
+  const int threads = LM >= 1024 ? 1024 : ((LM + 31) / 32) * 32;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (nc > 8) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nc, 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (probe_only) {
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, k, &cfg);
+    *fits = e == cudaSuccess && clusters >= 1;
+    cudaGetLastError();  // a size the GPU cannot place is an answer, not an error
+    return cudaSuccess;
+  }
+  e = cudaLaunchKernelEx(&cfg, k, th, uu, n, nsteps, rk, c, LM);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <class T>
 cudaError_t run_line_cluster_t(int lim, void *theta, const void *u, int n, int64_t nsteps,
                                int rk, double c, cudaStream_t st) {
-  const int LM = (n + LNC - 1) / LNC + 4;
-  const size_t smem = 6 * sizeof(T) * (size_t)LM;
-  const int threads = LM >= 1024 ? 1024 : ((LM + 31) / 32) * 32;
   T *th = static_cast<T *>(theta);
   const T *uu = static_cast<const T *>(u);
-#define FL_LINE_CASE(L)                                                                        \
-  case L: {                                                                                    \
-    auto k = k_line_cluster<T, L>;                                                             \
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                                         (int)smem);                                           \
-    if (e != cudaSuccess) return e;                                                            \
-    k<<<LNC, threads, smem, st>>>(th, uu, n, nsteps, rk, (T)c, LM);                            \
-    return cudaGetLastError();                                                                 \
+  // the larger cluster where the line gives each CTA 2 cells and the GPU
+  // can place it (asked once per device)
+  static int big_ok[64] = {0};  // 0 unknown, 1 yes, 2 no
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int nc = 8;
+  if (FL_LINE_NC > 8 && n >= 2 * FL_LINE_NC && dev >= 0 && dev < 64) {
+    if (big_ok[dev] == 0) {
+      bool fits = false;
+      launch_line_cluster<T, LIM_UPWIND>(FL_LINE_NC, th, uu, n, nsteps, rk, (T)c, st, true, &fits);
+      big_ok[dev] = fits ? 1 : 2;
+    }
+    if (big_ok[dev] == 1) nc = FL_LINE_NC;
   }
+  bool unused = false;
+#define FL_LINE_CASE(L)                                                                        \
+  case L:                                                                                      \
+    return launch_line_cluster<T, L>(nc, th, uu, n, nsteps, rk, (T)c, st, false, &unused);
   switch (lim) {
     FL_LINE_CASE(LIM_UPWIND)
     FL_LINE_CASE(LIM_CENTRAL)
@@ -388,7 +436,7 @@ cudaError_t run_line_cluster_t(int lim, void *theta, const void *u, int n, int64
 template <class T>
 cudaError_t run_line_t(int lim, void *theta, const void *u, int n, int64_t nsteps, int rk, double c,
                        cudaStream_t st) {
-  if (n >= 2 * LNC) return run_line_cluster_t<T>(lim, theta, u, n, nsteps, rk, c, st);
+  if (n >= 2 * 8) return run_line_cluster_t<T>(lim, theta, u, n, nsteps, rk, c, st);
   const size_t smem = 5 * sizeof(T) * (size_t)n;
   const int threads = n >= 1024 ? 1024 : ((n + 31) / 32) * 32;
   T *th = static_cast<T *>(theta);

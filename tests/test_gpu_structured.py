@@ -204,7 +204,7 @@ def test_line_resident_size_limit(fl, dtype, n, lim, rk):
     m.close()
 
 
-# Lines of 16 cells or more run on a cluster of 8 CTAs: each owns a run of
+# Lines of 16 cells or more run on a cluster of 8 (from 32 cells, 16) CTAs: each owns a run of
 # cells and reads the two cells on each side from its neighbours' shared
 # memory; 15 cells take the one-CTA kernel.  Several steps in one launch
 # against the oracle, then the mass over 200 steps: a halo exchange that gave
