@@ -134,7 +134,8 @@ def test_stage_entry_point_composes_to_step_rk(fl):
     m.close()
 
 
-def _decomposed_gradient(fl, world, dims, h, th, u, lam_T, lim, rk, dt, nsteps, every):
+def _decomposed_gradient(fl, world, dims, h, th, u, lam_T, lim, rk, dt, nsteps, every,
+                         dtype=torch.float64):
     from paper_2110_03044_gb300.decomp import HALO_ADJOINT
     out = [None] * world
     err = []
@@ -145,7 +146,7 @@ def _decomposed_gradient(fl, world, dims, h, th, u, lam_T, lim, rk, dt, nsteps, 
         try:
             torch.cuda.set_device(0)
             slab = Slab(dims, r, world, halo=HALO_ADJOINT)
-            ro = SlabRollout(slab, h, ug, lim, torch.float64, dt, transport=tr)
+            ro = SlabRollout(slab, h, ug, lim, dtype, dt, transport=tr)
             tl = ro.local_field(torch.tensor(th, device="cuda"))
             ll = ro.local_field(torch.tensor(lam_T, device="cuda"))
             g = ro.gradient(tl, ll, rk, nsteps, every)
@@ -552,3 +553,33 @@ def test_stage_box_composes_and_leaves_other_cells(fl, dims, dtype, pre):
                                 torch.empty_like(th0), u, w)
     assert e.value.status == fl.FL_EINVAL
     m.close()
+
+
+def test_fp32_decomposed_gradients_equal_one_rank(fl):
+    # FP32 reverse sweeps: three slabs and a 2 x 2 pencil grid give the bits
+    # of the one-rank sweep of the same decomposition, and the FP64 oracle's
+    # gradient to FP32 rounding (inputs cast to FP32 first)
+    import oracle
+    dims = (24, 14, 18)
+    h = tuple(0.7 / d for d in dims)
+    mesh = W.structured_mesh(*dims, *h)
+    rng = np.random.default_rng(33)
+    th = (rng.uniform(-1, 1, mesh.n_cells) + (rng.random(mesh.n_cells) < 0.3))
+    th = th.astype(np.float32).astype(np.float64)
+    u = (0.3 * W.mixed_sign_velocity(mesh.n_faces, 34)).astype(np.float32).astype(np.float64)
+    dt = 0.3 * min(h) / np.max(np.abs(u)) / 3
+    nsteps, every = 3, 2
+    tgt = rng.normal(size=mesh.n_cells)
+    thT = oracle.step(mesh, "superbee", 3, dt, nsteps, u, th)
+    lam = (thT - tgt).astype(np.float32).astype(np.float64)
+    _, g_ref = oracle.gradient(mesh, "superbee", 3, dt, nsteps, u, th, tgt)
+    scale = np.max(np.abs(g_ref))
+    f32 = torch.float32
+    s3 = _decomposed_gradient(fl, 3, dims, h, th, u, lam, "superbee", 3, dt, nsteps, every, f32)
+    s1 = _decomposed_gradient(fl, 1, dims, h, th, u, lam, "superbee", 3, dt, nsteps, every, f32)
+    assert np.array_equal(s3, s1)
+    assert np.max(np.abs(s3 - g_ref)) <= 1e-4 * scale
+    p4 = _pencils(fl, (2, 2), dims, h, th, u, "superbee", f32, 3, dt, nsteps, lam, every)
+    p1 = _pencils(fl, (1, 1), dims, h, th, u, "superbee", f32, 3, dt, nsteps, lam, every)
+    assert torch.equal(p4, p1)
+    assert np.max(np.abs(p4.double().numpy() - g_ref)) <= 1e-4 * scale
