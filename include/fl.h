@@ -620,12 +620,21 @@ fl_status fl_batch_step_rk(fl_batch *batch, fl_limiter limiter, fl_dtype dtype, 
  * as fl_batch_set_tiling fixed it.
  *   kind 0: rectangles of 32 x 8 cells, one cell per thread (FP64 and FP32);
  *   kind 1: runs of 32 x cells_per_thread x warps consecutive cells of a
- *           plane in the flat order c = i + nx j (FP32 only);
+ *           plane in the flat order c = i + nx j, a thread's cells 32 apart
+ *           (FP32 only);
+ *   kind 2: runs of 128 x warps cells of a plane of a padded copy of each
+ *           box (periodic ghost cells, rows padded to a multiple of 4), a
+ *           thread holding 4 consecutive cells (FP32 only).  The call copies
+ *           theta and u_f into the workspace's padded copies before the first
+ *           step and theta back after the last; boxes with nx < 8 stay in
+ *           their own layout and run kind 1's tile with one cell per thread
+ *           over runs of 32 x warps;
  *   z_chunk: planes per work item.
  * fl_batch_tiling returns FL_EINVAL until a decomposition exists; any
  * output pointer may be NULL.  fl_batch_set_tiling validates the choice
  * (kind 0: cells_per_thread 1, warps 8; kind 1: FP32, cells_per_thread 1, 2
- * or 4, warps 1 .. 8; z_chunk 1 .. 255) and skips the autotuner.
+ * or 4, warps 1 .. 8; kind 2: FP32, cells_per_thread 4, warps 1 .. 8;
+ * z_chunk 1 .. 255) and skips the autotuner.
  */
 fl_status fl_batch_tiling(const fl_batch *batch, fl_limiter limiter, fl_dtype dtype, int rk_order,
                           int *kind, int *cells_per_thread, int *warps, int *z_chunk);

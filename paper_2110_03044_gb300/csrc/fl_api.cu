@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <utility>
 
@@ -203,11 +204,12 @@ fl_status check_enums(int lim, fl_dtype dt) {
 
 int resident_ctas(const void *kernel, int threads, size_t smem) {
   static std::mutex mu;
-  static std::map<std::pair<const void *, int>, int> cache;
+  // one entry per launch shape: a kernel may run with several block sizes
+  static std::map<std::tuple<const void *, int, int, size_t>, int> cache;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
   std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_pair(kernel, dev);
+  const auto key = std::make_tuple(kernel, dev, threads, smem);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   int sms = 0, per = 0;

@@ -18,8 +18,13 @@
 //   * 32 x 8 rectangles (the single-mesh stage tile, shared memory, one cell
 //     per thread) with a z chunk of 8, 16, 32 or 64 planes (FP64 and FP32);
 //   * FP32 only: runs of the flat plane (fl_struct_flat.cuh, registers and
-//     warp shuffles, no barriers) with 1, 2 or 4 cells per thread, 4 or 8
-//     warps per CTA and a z chunk of 16, 32 or 64 planes.
+//     warp shuffles, no barriers) with 1, 2 or 4 cells per thread 32 cells
+//     apart, 4 or 8 warps per CTA and a z chunk of 16, 32 or 64 planes;
+//   * FP32 only: runs over padded copies of the boxes (fl_struct_pad4.cuh:
+//     periodic ghost cells, 4 consecutive 16-byte aligned cells per thread,
+//     loads staged a plane ahead with cp.async), 1, 2, 4 or 8 warps per CTA
+//     and a z chunk of 16, 32 or 64 planes; the copies in and out run once
+//     per call.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,6 +36,7 @@
 #include "fl_internal.h"
 #include "fl_kernels.h"
 #include "fl_struct_flat.cuh"
+#include "fl_struct_pad4.cuh"
 #include "fl_struct_tile.cuh"
 
 namespace fl {
@@ -66,6 +72,9 @@ namespace {
 
 constexpr int BTY = 8;
 constexpr int MAXSTAGES = 3;
+// rows of the parameter table: the stages, then the boxes' layout copies
+constexpr int CONV_ROW = MAXSTAGES;
+constexpr int PARAM_ROWS = MAXSTAGES + 1;
 
 // (FP32 boxes run the shared-memory tile here: in this persistent kernel the
 // register tile of fl_struct_reg.cuh measured no faster, 1.61 against 1.60 ms
@@ -112,8 +121,38 @@ __global__ void __launch_bounds__(256, FL_FLAT_MINB)
   }
 }
 
+// FP32 on padded box copies (fl_struct_pad4.cuh): items are (box, run of
+// 128 w cells of a plane's rows + runs-per-plane x z chunk); boxes with
+// nx < 8 keep their own layout and take the one-cell flat tile over runs of
+// 32 w cells.
+#ifndef FL_PAD4_MINB
+#define FL_PAD4_MINB 2
+#endif
+template <int LIM, int SEED>
+__global__ void __launch_bounds__(256, FL_PAD4_MINB)
+    k_batch_pad4(const SParams<float> *__restrict__ params, const int2 *__restrict__ items,
+                 int n_items, unsigned *counter) {
+  __shared__ int s_next;
+  extern __shared__ float4 pad_stage[];  // PAD_STAGE_BYTES per thread
+  for (;;) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_next = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int t = s_next;
+    __syncthreads();
+    if (t >= n_items) break;
+    const int2 bt = items[t];
+    const SParams<float> p = params[bt.x];
+    if (p.pitch > 0)
+      stage_pad4<LIM, SEED>(p, bt.y % p.tiles_x, bt.y / p.tiles_x,
+                            pad_stage + threadIdx.y * blockDim.x + threadIdx.x);
+    else stage_flat<LIM, SEED, 1>(p, bt.y % p.tiles_x, bt.y / p.tiles_x);
+  }
+}
+
 // A work decomposition: kind 0 = 32 x 8 rectangles (z chunk zc), kind 1 =
-// flat runs of 32 cx w cells (FP32), packed into one int for the maps.
+// flat runs of 32 cx w cells (FP32), kind 2 = runs of 128 w cells of the
+// boxes' padded copies, four consecutive cells per thread (FP32), packed
+// into one int for the maps.
 struct Cfg {
   int kind, cx, w, zc;
 };
@@ -139,6 +178,19 @@ void *flat_kernel(int lim, int cx) {
   return nullptr;
 }
 
+template <int SEED>
+void *pad4_kernel(int lim) {
+  switch (lim) {
+    case LIM_UPWIND: return (void *)k_batch_pad4<LIM_UPWIND, SEED>;
+    case LIM_CENTRAL: return (void *)k_batch_pad4<LIM_CENTRAL, SEED>;
+    case LIM_MINMOD: return (void *)k_batch_pad4<LIM_MINMOD, SEED>;
+    case LIM_VANLEER: return (void *)k_batch_pad4<LIM_VANLEER, SEED>;
+    case LIM_SUPERBEE: return (void *)k_batch_pad4<LIM_SUPERBEE, SEED>;
+    case LIM_SMART: return (void *)k_batch_pad4<LIM_SMART, SEED>;
+  }
+  return nullptr;
+}
+
 template <class T, int SEED, bool PRE>
 void *kernel_ptr(int lim) {
   switch (lim) {
@@ -159,6 +211,8 @@ void *batch_kernel(fl_dtype dt, int lim, int seed, bool pre, int cfg) {
   if (dt == FL_F32 && c.kind == 1)
     return seed == SEED_PLAIN ? flat_kernel<SEED_PLAIN>(lim, c.cx)
                               : flat_kernel<SEED_COMBINE>(lim, c.cx);
+  if (dt == FL_F32 && c.kind == 2)
+    return seed == SEED_PLAIN ? pad4_kernel<SEED_PLAIN>(lim) : pad4_kernel<SEED_COMBINE>(lim);
   if (dt == FL_F64) {
     if (pre)
       return seed == SEED_PLAIN ? kernel_ptr<double, SEED_PLAIN, true>(lim)
@@ -172,16 +226,23 @@ void *batch_kernel(fl_dtype dt, int lim, int seed, bool pre, int cfg) {
 
 bool batch_prescales(fl_dtype dt) { return dt == FL_F64; }
 
-// work items of a box: rectangles (kind 0) or flat runs (kind 1) per plane
+// boxes a kind-2 decomposition copies into the padded layout
+bool box_padded(const fl_mesh *m) { return m->nx >= 8; }
+
+// work items of a box: rectangles (kind 0) or flat runs (kinds 1, 2) per plane
 int tiles_x_of(const fl_mesh *m, const Cfg &c) {
-  if (c.kind == 1) {
+  if (c.kind == 2 && box_padded(m)) {
+    const long long run = 128LL * c.w;
+    return (int)(((long long)pad_geom(m->nx, m->ny, m->nz).P * m->ny + run - 1) / run);
+  }
+  if (c.kind != 0) {
     const long long run = 32LL * c.cx * c.w;
     return (int)(((long long)m->nx * m->ny + run - 1) / run);
   }
   return (m->nx + TX - 1) / TX;
 }
 int tiles_y_of(const fl_mesh *m, const Cfg &c) {
-  return c.kind == 1 ? 1 : (m->ny + BTY - 1) / BTY;
+  return c.kind != 0 ? 1 : (m->ny + BTY - 1) / BTY;
 }
 int zchunk_of(const fl_mesh *m, int zc) { return std::min(zc, m->nz); }
 
@@ -252,11 +313,40 @@ SParams<T> box_params(const fl_mesh *m, int cfg, const void *x, const void *thn,
 
 size_t param_size(fl_dtype dt) { return dt == FL_F64 ? sizeof(SParams<double>) : sizeof(SParams<float>); }
 
-// Workspace of box i: its RK stage buffers, then (pre) its w_f.
+// Padded copy of box i for a kind-2 decomposition: theta, the RK stage
+// buffers, then the active velocity components, each block 256-byte aligned.
+size_t pad_block(const fl_mesh *m) {
+  return align256((size_t)pad_geom(m->nx, m->ny, m->nz).vol * sizeof(float));
+}
+size_t pad_bytes(const fl_mesh *m, int rk) {
+  const int na = m->act[0] + m->act[1] + m->act[2];
+  return (rk == 3 ? 3 : 2) * pad_block(m) +
+         align256((size_t)na * pad_geom(m->nx, m->ny, m->nz).vol * sizeof(float));
+}
+
+// Workspace of box i: its RK stage buffers, then (pre) its w_f; for FP32 at
+// least the padded copy of a kind-2 decomposition (both start at the box's
+// offset, one decomposition being in use at a time).
 size_t box_ws_bytes(const fl_mesh *m, fl_dtype dt, int rk) {
   size_t t = (rk == 3 ? 2 : 1) * align256((size_t)m->C * dsize(dt));
   if (batch_prescales(dt)) t += align256((size_t)m->F * dsize(dt));
+  if (dt == FL_F32 && box_padded(m)) t = std::max(t, pad_bytes(m, rk));
   return t;
+}
+
+// Stage parameters p of box m moved onto its padded copy at base (theta,
+// RK stage buffers A and B, velocities): x, thn and y are picked by the
+// caller from those blocks.
+void pad_params(SParams<float> &p, const fl_mesh *m, const char *ubase) {
+  const PadGeom g = pad_geom(m->nx, m->ny, m->nz);
+  p.pitch = g.P;
+  p.gy = g.gy;
+  p.gz = g.gz;
+  p.plane = g.plane;
+  p.u = reinterpret_cast<const float *>(ubase);
+  p.ux_off = m->u_off[0] / m->C * g.vol;
+  p.uy_off = m->u_off[1] / m->C * g.vol;
+  p.uz_off = m->u_off[2] / m->C * g.vol;
 }
 
 // Fill the staging table: stage s of box i at index s * n + i.  With pre,
@@ -265,6 +355,7 @@ template <class T>
 void fill_params(fl_batch *b, int rk, int cfg, const double *dtv, void *const *theta,
                  const void *const *u, char *ws, size_t es, bool pre) {
   SParams<T> *h = static_cast<SParams<T> *>(b->h_params);
+  const bool padded = decode(cfg).kind == 2;
   size_t off = 0;
   for (int i = 0; i < b->n; ++i) {
     const fl_mesh *m = b->meshes[i];
@@ -272,6 +363,34 @@ void fill_params(fl_batch *b, int rk, int cfg, const double *dtv, void *const *t
     void *A = ws + off;
     void *B = ws + off + one;
     const void *uw = pre ? static_cast<const void *>(ws + off + (rk == 3 ? 2 : 1) * one) : u[i];
+    // the box's layout copy (a kind-2 decomposition of a box with nx >= 8)
+    SParams<T> &conv = h[CONV_ROW * b->n + i];
+    conv = SParams<T>();
+    if constexpr (sizeof(T) == 4) {
+      if (padded && box_padded(m)) {
+        const size_t V = pad_block(m);
+        char *tp = ws + off, *ap = ws + off + V, *bp = ws + off + 2 * V;
+        char *up = ws + off + (rk == 3 ? 3 : 2) * V;
+        conv = box_params<T>(m, cfg, theta[i], ap, tp, u[i], dtv[i], SEED_PLAIN, 0.0, 1.0);
+        conv.thf = reinterpret_cast<T *>(up);
+        conv.pitch = pad_geom(m->nx, m->ny, m->nz).P;
+        auto st = [&](const char *x, const char *thn, char *y, int seed, double a, double bc) {
+          SParams<T> q = box_params<T>(m, cfg, x, thn, y, u[i], dtv[i], seed, a, bc);
+          pad_params(q, m, up);
+          return q;
+        };
+        if (rk == 3) {
+          h[0 * b->n + i] = st(tp, tp, ap, SEED_PLAIN, 0.0, 1.0);
+          h[1 * b->n + i] = st(ap, tp, bp, SEED_COMBINE, 0.75, 0.25);
+          h[2 * b->n + i] = st(bp, tp, tp, SEED_COMBINE, 1.0 / 3.0, 2.0 / 3.0);
+        } else {
+          h[0 * b->n + i] = st(tp, tp, ap, SEED_PLAIN, 0.0, 1.0);
+          h[1 * b->n + i] = st(ap, ap, tp, SEED_PLAIN, 0.0, 1.0);
+        }
+        off += box_ws_bytes(m, FL_F32, rk);
+        continue;
+      }
+    }
     off += box_ws_bytes(m, es == 8 ? FL_F64 : FL_F32, rk);
     if (rk == 3) {
       h[0 * b->n + i] = box_params<T>(m, cfg, theta[i], theta[i], A, uw, dtv[i], SEED_PLAIN, 0.0, 1.0);
@@ -307,12 +426,32 @@ cudaError_t prescale_boxes(fl_batch *b, fl_dtype dt, int rk, const double *dtv,
 
 dim3 block_of(int cfg) {
   const Cfg c = decode(cfg);
-  return c.kind == 1 ? dim3(32, c.w) : dim3(TX, BTY);
+  return c.kind != 0 ? dim3(32, c.w) : dim3(TX, BTY);
+}
+
+// dynamic shared memory of a launch: the staging slots of kind 2
+size_t smem_of(fl_dtype dt, int cfg) {
+  const Cfg c = decode(cfg);
+  return dt == FL_F32 && c.kind == 2 ? (size_t)PAD_STAGE_BYTES * 32 * c.w : 0;
+}
+
+// the kernels of a decomposition may take its dynamic shared memory (set
+// before any launch or occupancy query, outside graph capture)
+cudaError_t allow_smem(fl_dtype dt, int lim, bool pre, int cfg) {
+  const size_t smem = smem_of(dt, cfg);
+  if (smem <= 48 * 1024) return cudaSuccess;
+  for (int seed : {SEED_PLAIN, SEED_COMBINE}) {
+    const cudaError_t e = cudaFuncSetAttribute(batch_kernel(dt, lim, seed, pre, cfg),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int persistent_grid(fl_dtype dt, int lim, int seed, bool pre, int cfg) {
   const dim3 b = block_of(cfg);
-  return resident_ctas(batch_kernel(dt, lim, seed, pre, cfg), (int)(b.x * b.y), 0);
+  return resident_ctas(batch_kernel(dt, lim, seed, pre, cfg), (int)(b.x * b.y), smem_of(dt, cfg));
 }
 
 // Enqueue one launch of stage s (seed) on st.
@@ -324,8 +463,23 @@ cudaError_t enqueue_stage(fl_batch *b, fl_dtype dt, int lim, int s, int seed, bo
   unsigned *ctr = b->d_counters + s;
   void *args[] = {(void *)&params, (void *)&tiles, (void *)&nt, (void *)&ctr};
   return cudaLaunchKernel(batch_kernel(dt, lim, seed, pre, cfg),
-                          dim3(persistent_grid(dt, lim, seed, pre, cfg)), block_of(cfg), args, 0,
-                          st);
+                          dim3(persistent_grid(dt, lim, seed, pre, cfg)), block_of(cfg), args,
+                          smem_of(dt, cfg), st);
+}
+
+// Kind 2: copy theta and the velocities of the padded boxes into their
+// padded copies (in), or theta back (out; from the RK stage buffer A when
+// alt is set).  One launch over all boxes, blockIdx.y = box.
+cudaError_t pad_copy(fl_batch *b, bool in, bool alt, cudaStream_t st) {
+  long long most = 1;
+  for (const fl_mesh *m : b->meshes)
+    if (box_padded(m))
+      most = std::max(most, in ? pad_geom(m->nx, m->ny, m->nz).vol : (long long)m->C);
+  const int gx = (int)std::min<long long>((most + 1023) / 1024, 65535);
+  const SParams<float> *conv = static_cast<const SParams<float> *>(b->d_params) + CONV_ROW * b->n;
+  if (in) k_pad_in<<<dim3(gx, b->n), 256, 0, st>>>(conv);
+  else k_pad_out<<<dim3(gx, b->n), 256, 0, st>>>(conv, alt ? 1 : 0);
+  return cudaGetLastError();
 }
 
 // Stage launches of one step (RK3: 3 stages; Euler: 2 steps, even and odd).
@@ -352,7 +506,7 @@ fl_status upload_params(fl_batch *b, fl_dtype dt, int rk, int cfg, const double 
     fill_params<double>(b, rk, cfg, dtv, theta, u, static_cast<char *>(ws), 8, pre);
   else
     fill_params<float>(b, rk, cfg, dtv, theta, u, static_cast<char *>(ws), 4, pre);
-  const size_t bytes = (size_t)MAXSTAGES * b->n * param_size(dt);
+  const size_t bytes = (size_t)PARAM_ROWS * b->n * param_size(dt);
   cudaError_t e = cudaMemcpyAsync(b->d_params, b->h_params, bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(b->params_done, st);
   return e == cudaSuccess ? FL_OK : cuda_fail(e, "parameter upload");
@@ -364,10 +518,13 @@ fl_status tune(fl_batch *b, fl_dtype dt, int lim, int rk, const double *dtv, voi
                const void *const *u, void *ws, bool pre, cudaStream_t st, int *best) {
   std::vector<int> cand;
   for (int zc : {8, 16, 32, 64}) cand.push_back(encode(Cfg{0, 0, BTY, zc}));
-  if (dt == FL_F32)
+  if (dt == FL_F32) {
     for (int cx : {1, 2, 4})
       for (int w : {4, 8})
         for (int zc : {16, 32, 64}) cand.push_back(encode(Cfg{1, cx, w, zc}));
+    for (int w : {1, 2, 4, 8})
+      for (int zc : {16, 32, 64}) cand.push_back(encode(Cfg{2, 1, w, zc}));
+  }
   float best_ms = 1e30f;
   *best = cand[0];
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -381,7 +538,9 @@ fl_status tune(fl_batch *b, fl_dtype dt, int lim, int rk, const double *dtv, voi
     int nt;
     if ((s = get_tiles(b, cfg, &tiles, &nt)) != FL_OK) break;
     if ((s = upload_params(b, dt, rk, cfg, dtv, theta, u, ws, pre, st)) != FL_OK) break;
-    cudaError_t e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, cfg, tiles, nt, st);  // warm-up
+    cudaError_t e = allow_smem(dt, lim, pre, cfg);
+    if (e == cudaSuccess && decode(cfg).kind == 2) e = pad_copy(b, true, false, st);
+    if (e == cudaSuccess) e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, cfg, tiles, nt, st);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r)
       e = enqueue_stage(b, dt, lim, 0, SEED_PLAIN, pre, cfg, tiles, nt, st);
@@ -430,7 +589,7 @@ fl_status fl_batch_create(int n, const fl_mesh *const *meshes, fl_batch **out) {
     b->cells += m->C;
     b->faces += m->F;
   }
-  b->params_bytes = (size_t)MAXSTAGES * n * sizeof(SParams<double>);
+  b->params_bytes = (size_t)PARAM_ROWS * n * sizeof(SParams<double>);
   cudaError_t e = cudaMalloc(&b->d_params, b->params_bytes);
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_params, b->params_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, MAXSTAGES * sizeof(unsigned));
@@ -502,6 +661,12 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
   int nt;
   if ((s = get_tiles(b, cfg, &tiles, &nt)) != FL_OK) return s;
   if ((s = upload_params(b, dt, rk, cfg, dtv, theta, u_f, ws, pre, st)) != FL_OK) return s;
+  const bool padded = dt == FL_F32 && decode(cfg).kind == 2;
+  {
+    cudaError_t e = allow_smem(dt, lim, pre, cfg);
+    if (e == cudaSuccess && padded) e = pad_copy(b, true, false, st);
+    if (e != cudaSuccess) return cuda_fail(e, "padded copy in");
+  }
   // one graph per (limiter, dtype + pre, rk, decomposition): a step's stage launches
   const auto gkey = std::make_tuple((int)lim, (int)dt * 2 + (pre ? 1 : 0), rk, cfg);
   cudaGraphExec_t exec = nullptr;
@@ -537,12 +702,14 @@ fl_status fl_batch_step_rk(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, con
       size_t off = 0;
       for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         const fl_mesh *m = b->meshes[i];
-        e = cudaMemcpyAsync(theta[i], static_cast<char *>(ws) + off, m->C * es,
-                            cudaMemcpyDeviceToDevice, st);
+        if (!(padded && box_padded(m)))
+          e = cudaMemcpyAsync(theta[i], static_cast<char *>(ws) + off, m->C * es,
+                              cudaMemcpyDeviceToDevice, st);
         off += box_ws_bytes(m, dt, rk);
       }
     }
   }
+  if (padded && e == cudaSuccess) e = pad_copy(b, false, rk == 1 && (nsteps & 1), st);
   if (e == cudaSuccess) e = cudaEventRecord(b->last_call, st);
   if (e != cudaSuccess) return cuda_fail(e, "batched step");
   return FL_OK;
@@ -558,7 +725,7 @@ fl_status fl_batch_tiling(const fl_batch *b, fl_limiter lim, fl_dtype dt, int rk
     if (it == b->tuned.end()) continue;
     const Cfg c = decode(it->second);
     if (kind) *kind = c.kind;
-    if (cells_per_thread) *cells_per_thread = c.kind == 1 ? c.cx : 1;
+    if (cells_per_thread) *cells_per_thread = c.kind == 1 ? c.cx : c.kind == 2 ? 4 : 1;
     if (warps) *warps = c.w;
     if (z_chunk) *z_chunk = c.zc;
     return FL_OK;
@@ -583,6 +750,12 @@ fl_status fl_batch_set_tiling(fl_batch *b, fl_limiter lim, fl_dtype dt, int rk, 
       return fail(FL_EINVAL, "cells_per_thread must be 1, 2 or 4");
     if (warps < 1 || warps > 8) return fail(FL_EINVAL, "warps must be in 1 .. 8");
     c.cx = cells_per_thread;
+    c.w = warps;
+  } else if (kind == 2) {
+    if (dt != FL_F32) return fail(FL_EUNSUPPORTED, "flat runs are an FP32 decomposition");
+    if (cells_per_thread != 4) return fail(FL_EINVAL, "kind 2 takes 4 cells per thread");
+    if (warps < 1 || warps > 8) return fail(FL_EINVAL, "warps must be in 1 .. 8");
+    c.cx = 1;
     c.w = warps;
   } else {
     return fail(FL_EINVAL, "unknown decomposition kind %d", kind);

@@ -33,6 +33,9 @@ struct SParams {
   // decomposed mesh; the whole mesh by default)
   int zlo = 0, zhi = 1 << 30;
   int ylo = 0, yhi = 1 << 30;  // and rows [ylo, min(yhi, ny)) of them
+  // padded copy of a batched box (fl_struct_pad4.cuh): row pitch (0 for
+  // the box's own layout) and the ghost rows / planes before the first
+  int pitch = 0, gy = 0, gz = 0;
 };
 
 enum { SEED_PLAIN = 0, SEED_COMBINE = 1, SEED_APPLY = 2 };

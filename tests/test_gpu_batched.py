@@ -13,7 +13,7 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
-SHAPES = [(33, 17, 9), (40, 40, 12), (8, 8, 8), (64, 9, 20), (31, 1, 1), (21, 14, 1)]
+SHAPES = [(33, 17, 9), (40, 40, 12), (8, 8, 8), (64, 9, 20), (31, 1, 1), (21, 14, 1), (5, 12, 6)]
 
 
 def _boxes(seed=0):
@@ -97,16 +97,21 @@ def test_batched_config_equals_single_mesh_path(fl):
 # every work decomposition the autotuner may pick, fixed with
 # fl_batch_set_tiling: (kind, cells per thread, warps, z chunk)
 TILINGS32 = [(0, 1, 8, 16), (1, 1, 8, 16), (1, 2, 4, 32), (1, 4, 8, 64), (1, 4, 4, 3),
-             (1, 2, 1, 7)]
+             (1, 2, 1, 7), (2, 4, 4, 16), (2, 4, 1, 7), (2, 4, 8, 3), (2, 4, 2, 64)]
 
 
 @pytest.mark.parametrize("tiling", TILINGS32)
 @pytest.mark.parametrize("rk", [1, 3])
 @pytest.mark.parametrize("lim", ["minmod", "vanleer", "superbee", "smart"])
 def test_batch_fp32_every_tiling_matches_oracle(fl, lim, rk, tiling):
-    # the flat-run tile and the rectangles give the bits of the single-mesh
+    # the flat-run tiles and the rectangles give the bits of the single-mesh
     # FP32 kernels (the same face flux and cell-sum order), so every box is
-    # checked against the oracle per step and against the single-mesh path
+    # checked against the oracle per step and against the single-mesh path.
+    # The boxes put rows of 5 .. 64 cells, a row start at every position of
+    # a four-cell group, partial last groups and one-row planes through the
+    # tiles; kind 2 runs on padded copies with periodic ghost cells (Euler
+    # with one step ends in the RK buffer, copied back from there), nx < 8
+    # keeping the one-cell tile
     boxes = _boxes(seed=2)
     dtype = torch.float32
     meshes = [fl.Mesh.structured(*b[0].dims, *b[0].h) for b in boxes]
@@ -155,12 +160,16 @@ def test_batch_tiling_query_and_validation(fl):
     fl.fl_batch_step_rk(batch, "superbee", torch.float32, 3, [b[3] for b in boxes], 1, th, us,
                         ws, nb)
     kind, cx, w, zc = fl.fl_batch_tiling(batch, "superbee", torch.float32, 3)
-    assert kind in (0, 1) and cx in (1, 2, 4) and 1 <= w <= 8 and 1 <= zc <= 255
-    for bad in [(2, 1, 8, 16), (1, 3, 8, 16), (1, 2, 9, 16), (0, 2, 8, 16), (1, 2, 4, 0)]:
+    assert kind in (0, 1, 2) and cx in (1, 2, 4) and 1 <= w <= 8 and 1 <= zc <= 255
+    assert kind != 2 or cx == 4
+    for bad in [(2, 1, 8, 16), (1, 3, 8, 16), (1, 2, 9, 16), (0, 2, 8, 16), (1, 2, 4, 0),
+                (2, 4, 9, 16), (2, 4, 0, 16), (3, 4, 4, 16)]:
         with pytest.raises(fl.FLError):
             fl.fl_batch_set_tiling(batch, "superbee", torch.float32, 3, *bad)
     with pytest.raises(fl.FLError):  # flat runs are FP32 only
         fl.fl_batch_set_tiling(batch, "superbee", torch.float64, 3, 1, 2, 4, 16)
+    with pytest.raises(fl.FLError):
+        fl.fl_batch_set_tiling(batch, "superbee", torch.float64, 3, 2, 4, 4, 16)
     fl.fl_batch_destroy(batch)
     for m in meshes:
         m.close()
