@@ -125,11 +125,12 @@ __global__ void __launch_bounds__(256, FL_FLAT_MINB)
 // 128 w cells of a plane's rows + runs-per-plane x z chunk); boxes with
 // nx < 8 keep their own layout and take the one-cell flat tile over runs of
 // 32 w cells.
-#ifndef FL_PAD4_MINB
-#define FL_PAD4_MINB 2
+// FL_PAD4_MAXREG: register cap of the tile (128: 16 warps per SM).
+#ifndef FL_PAD4_MAXREG
+#define FL_PAD4_MAXREG 128
 #endif
 template <int LIM, int SEED>
-__global__ void __launch_bounds__(256, FL_PAD4_MINB)
+__global__ void __maxnreg__(FL_PAD4_MAXREG)
     k_batch_pad4(const SParams<float> *__restrict__ params, const int2 *__restrict__ items,
                  int n_items, unsigned *counter) {
   __shared__ int s_next;
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(256, FL_PAD4_MINB)
     const SParams<float> p = params[bt.x];
     if (p.pitch > 0)
       stage_pad4<LIM, SEED>(p, bt.y % p.tiles_x, bt.y / p.tiles_x,
-                            pad_stage + threadIdx.y * blockDim.x + threadIdx.x);
+                            pad_stage + (threadIdx.y * blockDim.x + threadIdx.x) * PAD_STRIDE);
     else stage_flat<LIM, SEED, 1>(p, bt.y % p.tiles_x, bt.y / p.tiles_x);
   }
 }

@@ -34,6 +34,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "fl_face.cuh"
 #include "fl_struct_reg.cuh"
 #include "fl_struct_tile.cuh"
@@ -68,19 +70,19 @@ __device__ __forceinline__ void stf4(float *a, unsigned o, float4 v) {
   *reinterpret_cast<float4 *>(a + o) = v;
 }
 
-// 16-byte values a thread stages per plane (see stage_pad4) and the bytes of
-// its two staging slots
+// 16-byte values a thread stages per plane (see stage_pad4), and the stride
+// of a thread's staging block: two slots of PAD_NA values plus one, so that
+// the 128-bit reads of eight consecutive threads fall in distinct banks
 constexpr int PAD_NA = 11;
-constexpr int PAD_STAGE_BYTES = 2 * PAD_NA * 16;
+constexpr int PAD_STRIDE = 2 * PAD_NA + 1;
+constexpr int PAD_STAGE_BYTES = PAD_STRIDE * 16;
 
-__device__ __forceinline__ void cpa(void *dst, const void *src, int bytes16) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if (bytes16 == 16)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-  else if (bytes16 == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+// cp.async of `bytes` (16, 8 or 4) into shared address d + OFF
+template <int OFF, int BYTES>
+__device__ __forceinline__ void cpa(unsigned d, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0+%2], [%1], %3;" ::"r"(d), "l"(src), "n"(OFF),
+               "n"(BYTES)
+               : "memory");
 }
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
@@ -90,8 +92,7 @@ __device__ __forceinline__ void cpa_wait0() { asm volatile("cp.async.wait_group 
 // plane) of every plane in z chunk `zc`.  p holds padded pointers (x, thn,
 // y, u with its components p.plane * PZ apart at p.u?_off), p.pitch = P,
 // p.plane = P PY, p.gy, p.gz; p.tiles_x runs per plane.  stage: this
-// thread's first 16-byte staging value in shared memory, the next ones
-// blockDim.x * blockDim.y apart (2 PAD_NA of them).
+// thread's staging block in shared memory (PAD_STRIDE 16-byte values).
 //
 // The loads of plane k + 1 (the velocities, theta^n, the four y neighbour
 // rows, the z-window plane k + 4 and the x halo of lanes 0 and 31) are copied
@@ -128,37 +129,40 @@ __device__ __forceinline__ void stage_pad4(const SParams<float> &p, int seg, int
   const unsigned P1 = (unsigned)P, P2 = 2u * (unsigned)P;
   const unsigned ybase = (unsigned)(p.gy * P + f0);
   auto at = [&](int kz) { return (unsigned)(kz + p.gz) * PP + ybase; };
-  const int ns = (int)(blockDim.x * blockDim.y);  // staging stride (values)
   const bool hal0 = lane == 0 && c0 >= 4, hal31 = lane == 31 && c0 + 4 < P;
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(stage);
 
-  // plane j's loads into slot s; the z-window plane j + 3 (with z) or j
+  // plane j's loads into slot S; the z-window plane j + 3 (with z) or j
   // itself (without z) as value 0
-  auto issue = [&](int j, int s) {
+  auto issue_slot = [&](auto slot, int j) {
+    constexpr int B = decltype(slot)::value * PAD_NA * 16;
     const unsigned o = at(j);
-    float4 *d = stage + s * PAD_NA * ns;
     if (need_z) {
-      if (j + 1 < z1) cpa(d, X + (o + 3u * PP), 16);
+      if (j + 1 < z1) cpa<B, 16>(sbase, X + (o + 3u * PP));
     } else {
-      cpa(d, X + o, 16);
+      cpa<B, 16>(sbase, X + o);
     }
-    cpa(d + ns, Ux + o, 16);
-    if (need_z) cpa(d + 2 * ns, Uz + o, 16);
-    if (SEED == SEED_COMBINE) cpa(d + 3 * ns, p.thn + o, 16);
+    cpa<B + 16, 16>(sbase, Ux + o);
+    if (need_z) cpa<B + 32, 16>(sbase, Uz + o);
+    if (SEED == SEED_COMBINE) cpa<B + 48, 16>(sbase, p.thn + o);
     if (need_y) {
-      cpa(d + 4 * ns, X + (o - P2), 16);
-      cpa(d + 5 * ns, X + (o - P1), 16);
-      cpa(d + 6 * ns, X + (o + P1), 16);
-      cpa(d + 7 * ns, X + (o + P2), 16);
-      cpa(d + 8 * ns, Uy + o, 16);
-      cpa(d + 9 * ns, Uy + (o - P1), 16);
+      cpa<B + 64, 16>(sbase, X + (o - P2));
+      cpa<B + 80, 16>(sbase, X + (o - P1));
+      cpa<B + 96, 16>(sbase, X + (o + P1));
+      cpa<B + 112, 16>(sbase, X + (o + P2));
+      cpa<B + 128, 16>(sbase, Uy + o);
+      cpa<B + 144, 16>(sbase, Uy + (o - P1));
     }
-    float *h = reinterpret_cast<float *>(d + 10 * ns);
     if (hal0) {
-      cpa(h, X + (o - 2u), 8);
-      cpa(h + 2, Ux + (o - 1u), 4);
+      cpa<B + 160, 8>(sbase, X + (o - 2u));
+      cpa<B + 168, 4>(sbase, Ux + (o - 1u));
     }
-    if (hal31) cpa(h, X + (o + 4u), 8);
+    if (hal31) cpa<B + 160, 8>(sbase, X + (o + 4u));
     cpa_commit();
+  };
+  auto issue = [&](int j, int s) {
+    if (s == 0) issue_slot(std::integral_constant<int, 0>(), j);
+    else issue_slot(std::integral_constant<int, 1>(), j);
   };
 
   // ------------------------------------------------ z window
@@ -194,14 +198,14 @@ __device__ __forceinline__ void stage_pad4(const SParams<float> &p, int seg, int
     if (k + 1 < z1) issue(k + 1, s ^ 1);
     else cpa_commit();
     cpa_wait1();  // plane k's copies have landed
-    const float4 *d = stage + s * PAD_NA * ns;
+    const float4 *d = stage + s * PAD_NA;
     if (!need_z) {
       const float4 c = d[0];
       th0[0] = c.x, th0[1] = c.y, th0[2] = c.z, th0[3] = c.w;
     }
     float acc[4];
     if (SEED == SEED_COMBINE) {
-      const float4 tn4 = d[3 * ns];
+      const float4 tn4 = d[3];
       const float tn[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[v] = __fmaf_rn(p.a, tn[v], __fmul_rn(p.b, th0[v]));
@@ -211,8 +215,8 @@ __device__ __forceinline__ void stage_pad4(const SParams<float> &p, int seg, int
     }
     // ---------------------------------------------- x faces -1 .. 3
     {
-      const float4 ux4 = d[ns];
-      const float *h = reinterpret_cast<const float *>(d + 10 * ns);
+      const float4 ux4 = d[1];
+      const float *h = reinterpret_cast<const float *>(d + 10);
       float t[8];  // t[j + 2] = theta at position j, j = -2 .. 5
       const float sl2 = __shfl_up_sync(FULL, th0[2], 1), sl1 = __shfl_up_sync(FULL, th0[3], 1);
       const float sr4 = __shfl_down_sync(FULL, th0[0], 1), sr5 = __shfl_down_sync(FULL, th0[1], 1);
@@ -239,8 +243,8 @@ __device__ __forceinline__ void stage_pad4(const SParams<float> &p, int seg, int
     }
     // ---------------------------------------------- y faces
     if (need_y) {
-      const float4 ym2 = d[4 * ns], ym1 = d[5 * ns], yp1 = d[6 * ns], yp2 = d[7 * ns];
-      const float4 uyp = d[8 * ns], uym = d[9 * ns];
+      const float4 ym2 = d[4], ym1 = d[5], yp1 = d[6], yp2 = d[7];
+      const float4 uyp = d[8], uym = d[9];
       const float a2[4] = {ym2.x, ym2.y, ym2.z, ym2.w}, a1[4] = {ym1.x, ym1.y, ym1.z, ym1.w};
       const float b1[4] = {yp1.x, yp1.y, yp1.z, yp1.w}, b2[4] = {yp2.x, yp2.y, yp2.z, yp2.w};
       const float up[4] = {uyp.x, uyp.y, uyp.z, uyp.w}, um[4] = {uym.x, uym.y, uym.z, uym.w};
@@ -258,7 +262,7 @@ __device__ __forceinline__ void stage_pad4(const SParams<float> &p, int seg, int
     // ---------------------------------------------- z faces
     float fz[4], dzp[4];
     if (need_z) {
-      const float4 uz4 = d[2 * ns];
+      const float4 uz4 = d[2];
       const float uz[4] = {uz4.x, uz4.y, uz4.z, uz4.w};
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
