@@ -833,7 +833,9 @@ def run_config_batched(args):
         torch.cuda.synchronize()
         rate_s, ms_tot = whole_job_rate(F * 3 * args.steps, e0.elapsed_time(e1), device="cuda")
         ms_s = ms_tot / args.steps
+        Cm = sum(mm.n_cells for mm in meshes)
         out[dname] = {"batched_ms_per_step": ms_b, "separate_ms_per_step": ms_s,
+                      "batched_ps_per_cell_step": ms_b * 1e9 / Cm,
                       "batched_face_updates_per_s": rate_b,
                       "separate_face_updates_per_s": rate_s,
                       "speedup": ms_s / ms_b,
@@ -845,6 +847,7 @@ def run_config_batched(args):
             cands = [(0, 1, 8, z) for z in (8, 16, 32, 64)]
             if dt == torch.float32:
                 cands += [(1, c, w, z) for c in (1, 2, 4) for w in (4, 8) for z in (16, 32, 64)]
+                cands += [(2, 4, w, z) for w in (1, 2, 4, 8) for z in (16, 32, 64)]
             for t in cands:
                 fl.fl_batch_set_tiling(batch, "vanleer", dt, 3, *t)
                 fl.fl_batch_step_rk(batch, "vanleer", dt, 3, dts, 2, th, us, ws, nb)

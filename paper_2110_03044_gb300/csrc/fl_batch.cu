@@ -472,14 +472,16 @@ cudaError_t enqueue_stage(fl_batch *b, fl_dtype dt, int lim, int s, int seed, bo
 // padded copies (in), or theta back (out; from the RK stage buffer A when
 // alt is set).  One launch over all boxes, blockIdx.y = box.
 cudaError_t pad_copy(fl_batch *b, bool in, bool alt, cudaStream_t st) {
-  long long most = 1;
+  long long most = 1;  // rows of the largest box
   for (const fl_mesh *m : b->meshes)
-    if (box_padded(m))
-      most = std::max(most, in ? pad_geom(m->nx, m->ny, m->nz).vol : (long long)m->C);
-  const int gx = (int)std::min<long long>((most + 1023) / 1024, 65535);
+    if (box_padded(m)) {
+      const PadGeom g = pad_geom(m->nx, m->ny, m->nz);
+      most = std::max(most, in ? (long long)g.PY * g.PZ : (long long)m->ny * m->nz);
+    }
+  const int gx = (int)std::min<long long>((most + 7) / 8, 1024);
   const SParams<float> *conv = static_cast<const SParams<float> *>(b->d_params) + CONV_ROW * b->n;
-  if (in) k_pad_in<<<dim3(gx, b->n), 256, 0, st>>>(conv);
-  else k_pad_out<<<dim3(gx, b->n), 256, 0, st>>>(conv, alt ? 1 : 0);
+  if (in) k_pad_in<<<dim3(gx, b->n), dim3(32, 8), 0, st>>>(conv);
+  else k_pad_out<<<dim3(gx, b->n), dim3(32, 8), 0, st>>>(conv, alt ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -319,43 +319,56 @@ __device__ __forceinline__ void stage_pad4(const SParams<float> &p, int seg, int
 // The padded copy of box fields (blockIdx.y = box, q = the box's conversion
 // parameters: x = its theta, y = the padded theta, u = its face velocities,
 // thf = the padded velocities): every padded cell, ghosts included, takes
-// the value of its periodic image.
+// the value of its periodic image.  A warp copies a padded row (blocks of
+// 32 x 8 threads, eight rows at a time).
 __global__ void k_pad_in(const SParams<float> *__restrict__ conv) {
   const SParams<float> q = conv[blockIdx.y];
   if (q.pitch == 0) return;
   const PadGeom g = pad_geom(q.nx, q.ny, q.nz);
   const long long C = (long long)q.nx * q.ny * q.nz;
   const int na = q.act_x + q.act_y + q.act_z;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.vol;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int xp = (int)(i % g.P);
-    const long long t = i / g.P;
-    const int yp = (int)(t % g.PY), zp = (int)(t / g.PY);
-    int x = xp - PAD_GX, y = yp - g.gy, z = zp - g.gz;
-    x = x < 0 ? x + q.nx : (x >= q.nx ? x - q.nx : x);
+  const float *__restrict__ sx = q.x;
+  const float *__restrict__ su = q.u;
+  float *__restrict__ dx = q.y;
+  float *__restrict__ du = q.thf;
+  for (int r = blockIdx.x * blockDim.y + threadIdx.y; r < g.PY * g.PZ;
+       r += gridDim.x * blockDim.y) {
+    const int yp = r % g.PY, zp = r / g.PY;
+    int y = yp - g.gy, z = zp - g.gz;
     y = y < 0 ? y + q.ny : (y >= q.ny ? y - q.ny : y);
     z = z < 0 ? z + q.nz : (z >= q.nz ? z - q.nz : z);
-    const long long c = ((long long)z * q.ny + y) * q.nx + x;
-    q.y[i] = q.x[c];
-    for (int a = 0; a < na; ++a) q.thf[a * g.vol + i] = q.u[a * C + c];
+    const long long src = ((long long)z * q.ny + y) * q.nx;
+    const long long dst = (long long)r * g.P;
+    for (int xp = threadIdx.x; xp < g.P; xp += blockDim.x) {
+      int x = xp - PAD_GX;
+      x = x < 0 ? x + q.nx : (x >= q.nx ? x - q.nx : x);
+      const float t = sx[src + x];
+      float uv[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a < na) uv[a] = su[a * C + src + x];
+      dx[dst + xp] = t;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a < na) du[a * g.vol + dst + xp] = uv[a];
+    }
   }
 }
 
 // Back to the box's own layout: theta (q.x) from the padded field q.y, or
-// from q.thn when `alt` is set.
+// from q.thn when `alt` is set; a warp per row of the box.
 __global__ void k_pad_out(const SParams<float> *__restrict__ conv, int alt) {
   const SParams<float> q = conv[blockIdx.y];
   if (q.pitch == 0) return;
   const PadGeom g = pad_geom(q.nx, q.ny, q.nz);
-  const float *src = alt ? q.thn : q.y;
-  float *dst = const_cast<float *>(q.x);
-  const long long C = (long long)q.nx * q.ny * q.nz;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < C;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(c % q.nx);
-    const long long t = c / q.nx;
-    const int y = (int)(t % q.ny), z = (int)(t / q.ny);
-    dst[c] = src[((long long)(z + g.gz) * g.PY + y + g.gy) * g.P + x + PAD_GX];
+  const float *__restrict__ src = alt ? q.thn : q.y;
+  float *__restrict__ dst = const_cast<float *>(q.x);
+  for (int r = blockIdx.x * blockDim.y + threadIdx.y; r < q.ny * q.nz;
+       r += gridDim.x * blockDim.y) {
+    const int y = r % q.ny, z = r / q.ny;
+    const long long from = ((long long)(z + g.gz) * g.PY + y + g.gy) * g.P + PAD_GX;
+    const long long to = (long long)r * q.nx;
+    for (int x = threadIdx.x; x < q.nx; x += blockDim.x) dst[to + x] = src[from + x];
   }
 }
 
