@@ -598,7 +598,7 @@ fl_status fl_batch_create(int n, const fl_mesh *const *meshes, fl_batch **out);
  * Workspace bytes of fl_batch_step_rk: per box its RK stage buffers (and in
  * FP64 its pre-scaled velocities); in FP32 at least the padded copy of
  * decomposition kind 2 (theta, the stage buffers and the velocities of each
- * box with nx >= 8 at (nx + 6 rounded up to 4) x (ny + 4) x (nz + 4) cells,
+ * box with nx >= 8 at (nx + 4 rounded up to 4) x (ny + 4) x (nz + 4) cells,
  * the 4 dropped along an axis of one cell), whichever is larger.
  */
 fl_status fl_batch_workspace_size(const fl_batch *batch, fl_dtype dtype, int rk_order,

@@ -11,8 +11,8 @@
 // The boxes of a batch have any nx, so in their own layout a thread's cells
 // are not 16-byte aligned and rows end anywhere in a warp's run.  For the
 // whole of a call the batch keeps each box with nx >= 8 in a padded copy:
-//   * a row holds P = round_up(nx + 6, 4) cells: four ghost columns (x = -4
-//     .. -1), the nx cells at columns 4 .. nx + 3, and at least two ghost
+//   * a row holds P = round_up(nx + 4, 4) cells: two ghost columns (x = -2,
+//     -1), the nx cells at columns 2 .. nx + 1, and at least two ghost
 //     columns (x = nx, nx + 1) after them;
 //   * two ghost rows before and after the ny rows (when ny > 1), two ghost
 //     planes before and after the nz planes (when nz > 1);
@@ -44,7 +44,7 @@ namespace fl {
 namespace {
 
 constexpr int PAD_RUN = 128;  // cells of one warp's run: 32 lanes x 4
-constexpr int PAD_GX = 4;     // ghost columns before a row's first cell
+constexpr int PAD_GX = 2;     // ghost columns before a row's first cell
 
 // Geometry of a box's padded copy.
 struct PadGeom {
@@ -53,7 +53,7 @@ struct PadGeom {
 };
 __host__ __device__ inline PadGeom pad_geom(int nx, int ny, int nz) {
   PadGeom g;
-  g.P = (nx + 6 + 3) / 4 * 4;
+  g.P = (nx + 4 + 3) / 4 * 4;
   g.gy = ny > 1 ? 2 : 0;
   g.gz = nz > 1 ? 2 : 0;
   g.PY = ny + 2 * g.gy;

@@ -11,11 +11,11 @@ import random
 
 import pytest
 
-RUN, GX = 128, 4
+RUN, GX = 128, 2
 
 
 def geom(nx, ny, nz):
-    P = (nx + 6 + 3) // 4 * 4
+    P = (nx + 4 + 3) // 4 * 4
     gy = 2 if ny > 1 else 0
     gz = 2 if nz > 1 else 0
     PY, PZ = ny + 2 * gy, nz + 2 * gz
@@ -161,5 +161,5 @@ def test_ghost_image_geometry():
     # the row pitch leaves two ghost columns after the cells and is a multiple of 4
     for nx in range(8, 140):
         P, PY, PZ, gy, gz = geom(nx, 5, 1)
-        assert P % 4 == 0 and P >= nx + 6 and P < nx + 10
+        assert P % 4 == 0 and P >= nx + 4 and P < nx + 8
         assert (gy, gz, PY, PZ) == (2, 0, 9, 1)
