@@ -632,9 +632,10 @@ fl_status fl_batch_step_rk(fl_batch *batch, fl_limiter limiter, fl_dtype dtype, 
  *           box (periodic ghost cells, rows padded to a multiple of 4), a
  *           thread holding 4 consecutive cells (FP32 only).  The call copies
  *           theta and u_f into the workspace's padded copies before the first
- *           step and theta back after the last; boxes with nx < 8 stay in
- *           their own layout and run kind 1's tile with one cell per thread
- *           over runs of 32 x warps;
+ *           step and theta back after the last; boxes with nx < 8, or whose
+ *           padded copy would hold 2^31 cells or more, stay in their own
+ *           layout and run kind 1's tile with one cell per thread over runs
+ *           of 32 x warps;
  *   z_chunk: planes per work item.
  * fl_batch_tiling returns FL_EINVAL until a decomposition exists; any
  * output pointer may be NULL.  fl_batch_set_tiling validates the choice

@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(256, FL_FLAT_MINB)
 
 // FP32 on padded box copies (fl_struct_pad4.cuh): items are (box, run of
 // 128 w cells of a plane's rows + runs-per-plane x z chunk); boxes with
-// nx < 8 keep their own layout and take the one-cell flat tile over runs of
-// 32 w cells.
+// nx < 8 (or a padded copy of 2^31 cells or more) keep their own layout and
+// take the one-cell flat tile over runs of 32 w cells.
 // FL_PAD4_MAXREG: register cap of the tile (128: 16 warps per SM).
 #ifndef FL_PAD4_MAXREG
 #define FL_PAD4_MAXREG 128
@@ -227,8 +227,11 @@ void *batch_kernel(fl_dtype dt, int lim, int seed, bool pre, int cfg) {
 
 bool batch_prescales(fl_dtype dt) { return dt == FL_F64; }
 
-// boxes a kind-2 decomposition copies into the padded layout
-bool box_padded(const fl_mesh *m) { return m->nx >= 8; }
+// boxes a kind-2 decomposition copies into the padded layout (the tile's
+// offsets are 32-bit: a copy of 2^31 cells or more stays in the box's layout)
+bool box_padded(const fl_mesh *m) {
+  return m->nx >= 8 && pad_geom(m->nx, m->ny, m->nz).vol < (1LL << 31);
+}
 
 // work items of a box: rectangles (kind 0) or flat runs (kinds 1, 2) per plane
 int tiles_x_of(const fl_mesh *m, const Cfg &c) {
