@@ -23,12 +23,14 @@
 // In this layout the stage has no periodic wrap to handle:
 //   * a warp owns a run of 128 consecutive cells of the ny rows of a plane
 //     (ghost columns included), lane l four consecutive cells of one row,
-//     16-byte aligned: every array is read with one 128-bit load per lane
-//     and plane, the y neighbours at -2P .. +2P, the z window in registers;
+//     16-byte aligned: every array is read with one 16-byte copy per lane
+//     and plane (cp.async into shared memory, a plane ahead), the y
+//     neighbours at -2P .. +2P, the z window in registers;
 //   * the x window (cells -2 .. 5 from the first) comes from the lane's own
 //     four cells and two shuffled from each neighbouring lane, lanes 0 and
-//     31 loading their outer pair; each lane evaluates its five x faces
-//     (-1 .. 3), so no flux crosses lanes and no lane branches;
+//     31 copying their outer pair; each lane evaluates its five x faces
+//     (-1 .. 3), so no flux crosses lanes and no lane evaluates a face
+//     alone while the others wait;
 //   * lanes on ghost columns compute and store nothing of theirs.
 #pragma once
 
