@@ -205,74 +205,93 @@ __device__ __forceinline__ void stage_pad4(const SParams<float> &p, int seg, int
       const float4 c = d[0];
       th0[0] = c.x, th0[1] = c.y, th0[2] = c.z, th0[3] = c.w;
     }
-    float acc[4];
-    if (SEED == SEED_COMBINE) {
-      const float4 tn4 = d[3];
-      const float tn[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
+    // the plane's arithmetic over a face-flux function: first with van
+    // Leer's quotient unchecked, flagging a quotient out of its range; a
+    // warp that flagged one evaluates the plane again with the checked
+    // quotient (both give the checked quotient's bits)
+    float acc[4], fz[4], dzp[4];
+    auto plane_faces = [&](auto flux) {
+      if (SEED == SEED_COMBINE) {
+        const float4 tn4 = d[3];
+        const float tn[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[v] = __fmaf_rn(p.a, tn[v], __fmul_rn(p.b, th0[v]));
+        for (int v = 0; v < 4; ++v) acc[v] = __fmaf_rn(p.a, tn[v], __fmul_rn(p.b, th0[v]));
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] = th0[v];
+      }
+      // ---------------------------------------------- x faces -1 .. 3
+      {
+        const float4 ux4 = d[1];
+        const float *h = reinterpret_cast<const float *>(d + 10);
+        float t[8];  // t[j + 2] = theta at position j, j = -2 .. 5
+        const float sl2 = __shfl_up_sync(FULL, th0[2], 1), sl1 = __shfl_up_sync(FULL, th0[3], 1);
+        const float sr4 = __shfl_down_sync(FULL, th0[0], 1), sr5 = __shfl_down_sync(FULL, th0[1], 1);
+        const float su = __shfl_up_sync(FULL, ux4.w, 1);
+        t[0] = hal0 ? h[0] : sl2;
+        t[1] = hal0 ? h[1] : sl1;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) t[v + 2] = th0[v];
+        t[6] = hal31 ? h[0] : sr4;
+        t[7] = hal31 ? h[1] : sr5;
+        const float uf[5] = {hal0 ? h[2] : su, ux4.x, ux4.y, ux4.z, ux4.w};
+        float dd[7];  // dd[j + 2] = theta(j + 1) - theta(j)
+#pragma unroll
+        for (int j = 0; j < 7; ++j) dd[j] = __fsub_rn(t[j + 1], t[j]);
+        float fx[5];  // fx[m + 1] = flux of face m (between positions m and m + 1)
+#pragma unroll
+        for (int m = -1; m <= 3; ++m)
+          fx[m + 1] = flux(uf[m + 1], t[m + 2], t[m + 3], dd[m + 2], dd[m + 1], dd[m + 3], fl);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          acc[v] = __fmaf_rn(-p.cx, fx[v + 1], acc[v]);
+          acc[v] = __fmaf_rn(p.cx, fx[v], acc[v]);
+        }
+      }
+      // ---------------------------------------------- y faces
+      if (need_y) {
+        const float4 ym2 = d[4], ym1 = d[5], yp1 = d[6], yp2 = d[7];
+        const float4 uyp = d[8], uym = d[9];
+        const float a2[4] = {ym2.x, ym2.y, ym2.z, ym2.w}, a1[4] = {ym1.x, ym1.y, ym1.z, ym1.w};
+        const float b1[4] = {yp1.x, yp1.y, yp1.z, yp1.w}, b2[4] = {yp2.x, yp2.y, yp2.z, yp2.w};
+        const float up[4] = {uyp.x, uyp.y, uyp.z, uyp.w}, um[4] = {uym.x, uym.y, uym.z, uym.w};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float t0 = th0[v];
+          const float dm2 = __fsub_rn(a1[v], a2[v]), dm1 = __fsub_rn(t0, a1[v]);
+          const float d0 = __fsub_rn(b1[v], t0), dp1 = __fsub_rn(b2[v], b1[v]);
+          const float fm = flux(um[v], a1[v], t0, dm1, dm2, d0, fl);
+          const float fp = flux(up[v], t0, b1[v], d0, dm1, dp1, fl);
+          acc[v] = __fmaf_rn(-p.cy, fp, acc[v]);
+          acc[v] = __fmaf_rn(p.cy, fm, acc[v]);
+        }
+      }
+      // ---------------------------------------------- z faces
+      if (need_z) {
+        const float4 uz4 = d[2];
+        const float uz[4] = {uz4.x, uz4.y, uz4.z, uz4.w};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          dzp[v] = __fsub_rn(thp2[v], thp1[v]);
+          fz[v] = flux(uz[v], th0[v], thp1[v], dz0[v], dzm[v], dzp[v], fl);
+          acc[v] = __fmaf_rn(-p.cz, fz[v], acc[v]);
+          acc[v] = __fmaf_rn(p.cz, fzp[v], acc[v]);
+        }
+      }
+    };
+    if (LIM == LIM_VANLEER) {
+      bool far = false;
+      plane_faces([&](float u, float cp, float cn, float a, float bp, float bn, unsigned f) {
+        return reg_flux_unchecked<LIM>(u, cp, cn, a, bp, bn, f, far);
+      });
+      if (__any_sync(FULL, far))
+        plane_faces([&](float u, float cp, float cn, float a, float bp, float bn, unsigned f) {
+          return reg_flux<LIM>(u, cp, cn, a, bp, bn, f);
+        });
     } else {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[v] = th0[v];
-    }
-    // ---------------------------------------------- x faces -1 .. 3
-    {
-      const float4 ux4 = d[1];
-      const float *h = reinterpret_cast<const float *>(d + 10);
-      float t[8];  // t[j + 2] = theta at position j, j = -2 .. 5
-      const float sl2 = __shfl_up_sync(FULL, th0[2], 1), sl1 = __shfl_up_sync(FULL, th0[3], 1);
-      const float sr4 = __shfl_down_sync(FULL, th0[0], 1), sr5 = __shfl_down_sync(FULL, th0[1], 1);
-      const float su = __shfl_up_sync(FULL, ux4.w, 1);
-      t[0] = hal0 ? h[0] : sl2;
-      t[1] = hal0 ? h[1] : sl1;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) t[v + 2] = th0[v];
-      t[6] = hal31 ? h[0] : sr4;
-      t[7] = hal31 ? h[1] : sr5;
-      const float uf[5] = {hal0 ? h[2] : su, ux4.x, ux4.y, ux4.z, ux4.w};
-      float dd[7];  // dd[j + 2] = theta(j + 1) - theta(j)
-#pragma unroll
-      for (int j = 0; j < 7; ++j) dd[j] = __fsub_rn(t[j + 1], t[j]);
-      float fx[5];  // fx[m + 1] = flux of face m (between positions m and m + 1)
-#pragma unroll
-      for (int m = -1; m <= 3; ++m)
-        fx[m + 1] = reg_flux<LIM>(uf[m + 1], t[m + 2], t[m + 3], dd[m + 2], dd[m + 1], dd[m + 3], fl);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        acc[v] = __fmaf_rn(-p.cx, fx[v + 1], acc[v]);
-        acc[v] = __fmaf_rn(p.cx, fx[v], acc[v]);
-      }
-    }
-    // ---------------------------------------------- y faces
-    if (need_y) {
-      const float4 ym2 = d[4], ym1 = d[5], yp1 = d[6], yp2 = d[7];
-      const float4 uyp = d[8], uym = d[9];
-      const float a2[4] = {ym2.x, ym2.y, ym2.z, ym2.w}, a1[4] = {ym1.x, ym1.y, ym1.z, ym1.w};
-      const float b1[4] = {yp1.x, yp1.y, yp1.z, yp1.w}, b2[4] = {yp2.x, yp2.y, yp2.z, yp2.w};
-      const float up[4] = {uyp.x, uyp.y, uyp.z, uyp.w}, um[4] = {uym.x, uym.y, uym.z, uym.w};
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const float t0 = th0[v];
-        const float dm2 = __fsub_rn(a1[v], a2[v]), dm1 = __fsub_rn(t0, a1[v]);
-        const float d0 = __fsub_rn(b1[v], t0), dp1 = __fsub_rn(b2[v], b1[v]);
-        const float fm = reg_flux<LIM>(um[v], a1[v], t0, dm1, dm2, d0, fl);
-        const float fp = reg_flux<LIM>(up[v], t0, b1[v], d0, dm1, dp1, fl);
-        acc[v] = __fmaf_rn(-p.cy, fp, acc[v]);
-        acc[v] = __fmaf_rn(p.cy, fm, acc[v]);
-      }
-    }
-    // ---------------------------------------------- z faces
-    float fz[4], dzp[4];
-    if (need_z) {
-      const float4 uz4 = d[2];
-      const float uz[4] = {uz4.x, uz4.y, uz4.z, uz4.w};
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        dzp[v] = __fsub_rn(thp2[v], thp1[v]);
-        fz[v] = reg_flux<LIM>(uz[v], th0[v], thp1[v], dz0[v], dzm[v], dzp[v], fl);
-        acc[v] = __fmaf_rn(-p.cz, fz[v], acc[v]);
-        acc[v] = __fmaf_rn(p.cz, fzp[v], acc[v]);
-      }
+      plane_faces([&](float u, float cp, float cn, float a, float bp, float bn, unsigned f) {
+        return reg_flux<LIM>(u, cp, cn, a, bp, bn, f);
+      });
     }
     // ---------------------------------------------- store, with the images
     {

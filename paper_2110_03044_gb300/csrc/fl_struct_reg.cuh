@@ -41,6 +41,19 @@ __device__ __forceinline__ float reg_flux(float u, float thC_pos, float thC_neg,
   return native_flux<LIM>(u, sp ? thC_pos : thC_neg, a, sp ? b_pos : b_neg, flip);
 }
 
+// reg_flux with van Leer's quotient unchecked (FT<float>::quot_unchecked):
+// the same value wherever `far` stays clear
+template <int LIM>
+__device__ __forceinline__ float reg_flux_unchecked(float u, float thC_pos, float thC_neg, float a,
+                                                    float b_pos, float b_neg, unsigned flip,
+                                                    bool &far) {
+  const bool sp = __uint_as_float(__float_as_uint(u) ^ flip) > 0.0f;
+  return native_flux_q<LIM>(u, sp ? thC_pos : thC_neg, a, sp ? b_pos : b_neg, flip,
+                            [&far](float n, float s, bool need) {
+                              return FT<float>::quot_unchecked(n, s, need, far);
+                            });
+}
+
 template <int LIM, int SEED>
 __device__ __forceinline__ void stage_tile_reg(const SParams<float> &p, int tile) {
   const int lane = threadIdx.x, ty = threadIdx.y;
